@@ -1,0 +1,227 @@
+"""Pins for oracle.butterfly (Alg. 2, eq. hybrid_butterfly_mat, eq. error).
+
+Nothing here compares the oracle with itself: each check is a closed form,
+an invariant, a theorem of the paper, a library routine or brute force."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import butterfly as ob
+from oracle import operators as oo
+from oracle.tree import depth_for_leaf
+from paper_2002_03400_gb300 import inputs
+
+
+def _nested_U(F, j, sigma, mu):
+    """Explicit column basis U_{sigma,mu} (eq. nested_basis)."""
+    if j == F.L:
+        return F.U[sigma]
+    top = _nested_U(F, j + 1, 2 * sigma, mu >> 1)
+    bot = _nested_U(F, j + 1, 2 * sigma + 1, mu >> 1)
+    R = F.R[j][sigma * (1 << (F.L - j)) + mu]
+    D = np.zeros((top.shape[0] + bot.shape[0], top.shape[1] + bot.shape[1]), dtype=complex)
+    D[:top.shape[0], :top.shape[1]] = top
+    D[top.shape[0]:, top.shape[1]:] = bot
+    return D @ R
+
+
+def _nested_V(F, j, sigma, mu):
+    """Explicit row basis V_{sigma,mu} (eq. nested_basis_col)."""
+    if j == 0:
+        return F.V0[mu]
+    top = _nested_V(F, j - 1, sigma >> 1, 2 * mu)
+    bot = _nested_V(F, j - 1, sigma >> 1, 2 * mu + 1)
+    W = F.W[j][sigma * (1 << (F.L - j)) + mu]
+    D = np.zeros((top.shape[0] + bot.shape[0], top.shape[1] + bot.shape[1]), dtype=complex)
+    D[:top.shape[0], :top.shape[1]] = top
+    D[top.shape[0]:, top.shape[1]:] = bot
+    return D @ W
+
+
+def _exact(n, leaf, r, seed):
+    eb = inputs.exact_butterfly(n, leaf, r, seed)
+    Ft = ob.from_blocks(eb)
+    return eb, Ft, oo.FactorOp(Ft)
+
+
+@pytest.mark.parametrize("n,leaf,r", [(512, 8, 4), (2048, 32, 8), (1024, 16, 6)])
+def test_exact_butterfly_recovery(n, leaf, r):
+    """Sec. 7.1: an exactly-butterfly matrix of rank r is recovered to machine
+    precision with ranks exactly r at every block."""
+    eb, Ft, op = _exact(n, leaf, r, seed=1)
+    F = ob.factor(op, None, None, eb.L, 1e-12, 2, 4, seed=0)
+    A = ob.dense(Ft)
+    assert np.linalg.norm(A - ob.dense(F)) <= 1e-12 * np.linalg.norm(A)
+    assert ob.sketch_error(op, F, seed=9) <= 1e-12
+    for j in F.rV:
+        assert np.all(F.rV[j] == r)
+    for j in F.rU:
+        assert np.all(F.rU[j] == r)
+    # all outer and transfer factors are orthonormal, so ||A||_F^2 = sum ||B||_F^2
+    sB = sum(np.linalg.norm(b) ** 2 for b in F.B)
+    assert abs(sB - np.linalg.norm(A) ** 2) <= 1e-10 * sB
+    sBt = sum(np.linalg.norm(b) ** 2 for b in eb.B)
+    assert abs(sB - sBt) <= 1e-10 * sBt
+    # O(n log n) storage: exact count of stored entries (Sec. 4.5)
+    L, lm, nb = eb.L, eb.lm, 1 << eb.L
+    want = n * r + n * r + nb * r * r + (lm + (L - lm)) * nb * 2 * r * r
+    assert F.stored_entries() == want
+
+
+def test_blackbox_schedule():
+    """Sec. 4.1 / 4.5: level l needs 2^l (r+p) products with A^T and
+    2^(L-l) (r+p) with A, r = max(r1 + r2)."""
+    n, leaf, r, p = 1024, 8, 4, 2
+    eb, Ft, op = _exact(n, leaf, r, seed=2)
+    F = ob.factor(op, None, None, eb.L, 1e-12, p, 4, seed=0)
+    L, lm = eb.L, eb.lm
+    k = 2 * r + p
+    for l in range(1, lm + 1):
+        assert F.bb_cols[f"W{l}"] == (1 << l) * k
+    for l in range(lm, L):
+        assert F.bb_cols[f"R{l}"] == (1 << (L - l)) * k
+    # leaf loops: r0 = 4 = r is not > r, doubling to 8 gives k = 10 >= leaf 8 (saturated)
+    assert F.bb_cols["V0"] == 10 and F.bb_cols["U0"] == 10
+    tot_T = F.bb_cols["V0"] + sum((1 << l) * k for l in range(1, lm + 1))
+    tot_N = F.bb_cols["U0"] + sum((1 << (L - l)) * k for l in range(lm, L))
+    assert op.cols_T == tot_T and op.cols_N == tot_N
+
+
+@pytest.mark.parametrize("eps", [1e-4, 1e-6, 1e-8])
+def test_dense_brute_force_helmholtz(eps):
+    """Thm 5.3: ||A - F||_F <= sqrt(L+2) eps ||A||_F (x2 safety for the
+    high-probability assumption on Alg. 1), with F formed by brute force."""
+    n = 512
+    g = inputs.line_pair(n)
+    A = oo.kernel_entries(oo.HELMHOLTZ_2D, g.wavenumber, g.tgt, g.src)
+    L = depth_for_leaf(n, 16)
+    F = ob.factor(oo.DenseOp(A), g.src, g.tgt, L, eps, 2, 4, seed=0)
+    err = np.linalg.norm(A - ob.dense(F)) / np.linalg.norm(A)
+    assert err <= 2 * math.sqrt(L + 2) * eps
+    assert err >= 1e-3 * eps          # a truncated factorization, not an exact copy
+
+
+def test_theorems_5_1_and_5_2_per_level():
+    """Thm 5.1: sum over level-l blocks of ||K - U U^H K||^2 <= (L-l+1) eps^2 ||A||^2
+    (l_m <= l <= L); Thm 5.2: ||K - K V V^H||^2 <= (l+1) eps^2 ||A||^2 (0 <= l <= l_m)."""
+    n, eps = 256, 1e-5
+    g = inputs.arc_pair(n, seed=4)
+    A = oo.kernel_entries(oo.HELMHOLTZ_2D, g.wavenumber, g.tgt, g.src)
+    L = depth_for_leaf(n, 16)
+    F = ob.factor(oo.DenseOp(A), g.src, g.tgt, L, eps, 2, 4, seed=3)
+    At = A[np.ix_(F.permT, F.permS)]
+    nA2 = np.linalg.norm(A) ** 2
+    for l in range(F.lm, L + 1):
+        tot = 0.0
+        for tau in range(1 << l):
+            for nu in range(1 << (L - l)):
+                K = At[F.offT[l][tau]:F.offT[l][tau + 1], F.offS[L - l][nu]:F.offS[L - l][nu + 1]]
+                U = _nested_U(F, l, tau, nu)
+                assert np.allclose(U.conj().T @ U, np.eye(U.shape[1]), atol=1e-12)
+                tot += np.linalg.norm(K - U @ (U.conj().T @ K)) ** 2
+        assert tot <= 4 * (L - l + 1) * eps ** 2 * nA2
+    for l in range(0, F.lm + 1):
+        tot = 0.0
+        for tau in range(1 << l):
+            for nu in range(1 << (L - l)):
+                K = At[F.offT[l][tau]:F.offT[l][tau + 1], F.offS[L - l][nu]:F.offS[L - l][nu + 1]]
+                V = _nested_V(F, l, tau, nu)
+                assert np.allclose(V.conj().T @ V, np.eye(V.shape[1]), atol=1e-12)
+                tot += np.linalg.norm(K - (K @ V) @ V.conj().T) ** 2
+        assert tot <= 4 * (l + 1) * eps ** 2 * nA2
+
+
+def test_dft_matches_numpy_fft_and_ranks_do_not_grow():
+    """The DFT is a closed-form butterfly (Sec. 1): the factorization applies
+    like numpy.fft.fft, and the block ranks at fixed eps do not grow with n."""
+    eps = 1e-8
+    maxr = []
+    for n in (256, 1024, 4096):
+        g = inputs.dft_points(n)
+        op = oo.KernelOp(oo.DFT, 1.0, g.tgt, g.src)
+        L = depth_for_leaf(n, 16)
+        F = ob.factor(op, g.src, g.tgt, L, eps, 2, 4, seed=1)
+        x = inputs.random_rhs(n, 2, seed=5)
+        y = ob.apply(F, x)
+        assert np.linalg.norm(y - np.fft.fft(x, axis=0)) <= 2 * math.sqrt(L + 2) * eps * np.linalg.norm(np.fft.fft(x, axis=0)) * 3
+        maxr.append(max(max(F.rV[j].max() for j in F.rV), max(F.rU[j].max() for j in F.rU)))
+    assert maxr[-1] <= maxr[0] + 2
+
+
+def test_global_low_rank():
+    """A = X Y^H of rank q: every block has rank <= q and A is recovered."""
+    n, q = 512, 3
+    r = np.random.default_rng(7)
+    X = r.standard_normal((n, q)) + 1j * r.standard_normal((n, q))
+    Y = r.standard_normal((n, q)) + 1j * r.standard_normal((n, q))
+    A = X @ Y.conj().T
+    F = ob.factor(oo.DenseOp(A), None, None, 5, 1e-12, 2, 4, seed=2)
+    for d in (F.rV, F.rU):
+        for j in d:
+            assert d[j].max() <= q
+    assert np.linalg.norm(A - ob.dense(F)) <= 1e-11 * np.linalg.norm(A)
+
+
+def test_apply_adjoint_and_transpose():
+    g = inputs.line_pair(256)
+    A = oo.kernel_entries(oo.HELMHOLTZ_2D, g.wavenumber, g.tgt, g.src)
+    F = ob.factor(oo.DenseOp(A), g.src, g.tgt, 4, 1e-6, 2, 4, seed=0)
+    D = ob.dense(F)
+    x = inputs.random_rhs(256, 3, seed=1)
+    assert np.allclose(ob.apply(F, x, "C"), D.conj().T @ x, atol=1e-12)
+    assert np.allclose(ob.apply(F, x, "T"), D.T @ x, atol=1e-12)
+
+
+def test_error_metric_order_of_magnitude():
+    """Tables 1-2 report errors of 0.2..2 eps; same order here."""
+    n, eps = 1024, 1e-6
+    g = inputs.line_pair(n)
+    op = oo.DenseOp(oo.kernel_entries(oo.HELMHOLTZ_2D, g.wavenumber, g.tgt, g.src))
+    F = ob.factor(op, g.src, g.tgt, 6, eps, 2, 4, seed=0)
+    e = ob.sketch_error(op, F, seed=1)
+    assert 0.05 * eps <= e <= 2 * math.sqrt(8) * eps
+
+
+# --- planted mistakes: each must be caught by one of the pins above ---------
+
+def test_planted_transpose_in_B_is_caught(monkeypatch):
+    """Reading eq. Bij literally (transpose instead of pseudo-inverse) breaks
+    exact recovery."""
+    eb, Ft, op = _exact(512, 8, 4, seed=1)
+    monkeypatch.setattr(ob.np.linalg, "pinv", lambda X: X.conj().T)
+    F = ob.factor(op, None, None, eb.L, 1e-12, 2, 4, seed=0)
+    assert ob.sketch_error(op, F, seed=9) > 1e-3
+
+
+def test_planted_missing_conjugate_is_caught():
+    """Using A^T where A^H is needed (dropping the conjugate of the complex
+    extension) breaks the brute-force bound."""
+    n, eps = 256, 1e-6
+    g = inputs.line_pair(n)
+    A = oo.kernel_entries(oo.HELMHOLTZ_2D, g.wavenumber, g.tgt, g.src)
+
+    class Wrong(oo.DenseOp):
+        def _matvec_T(self, X):
+            return self.A.conj().T @ X
+    F = ob.factor(Wrong(A), g.src, g.tgt, 4, eps, 2, 4, seed=0)
+    err = np.linalg.norm(A - ob.dense(F)) / np.linalg.norm(A)
+    assert err > 100 * eps
+
+
+def test_planted_swapped_stacking_is_caught(monkeypatch):
+    """Stacking the two children of a W block in the wrong order breaks exact
+    recovery (wrong index in the nested basis)."""
+    eb, Ft, op = _exact(512, 8, 4, seed=3)
+    real_VH = ob.VH
+
+    def swapped(F, j, sigma, mu, X):
+        if j >= 1:
+            top = real_VH(F, j - 1, sigma >> 1, 2 * mu + 1, X)
+            bot = real_VH(F, j - 1, sigma >> 1, 2 * mu, X)
+            return F.W[j][sigma * (1 << (F.L - j)) + mu].conj().T @ np.vstack([top, bot])
+        return real_VH(F, j, sigma, mu, X)
+    monkeypatch.setattr(ob, "VH", swapped)
+    F = ob.factor(op, None, None, eb.L, 1e-12, 2, 4, seed=0)
+    monkeypatch.setattr(ob, "VH", real_VH)
+    assert ob.sketch_error(op, F, seed=9) > 1e-3
