@@ -1,0 +1,277 @@
+"""Benchmark of the butterfly hot path on one GB300 (or N independent replicas).
+
+Workload (the exact-recovery / precision configuration): the 2D Helmholtz
+kernel exp(-i k r)/r between two parallel unit segments at distance 1,
+n = m = 16384 points, 8 points per wavelength, entries formed on the fly,
+leaf 16 (L = 10), tol 1e-6, p = 2, r0 = 4, seed 0; plus the exact-recovery
+case (n = 16384 exactly-butterfly operator of rank 8, leaf 32) used as a
+black box through its own factors.
+
+One step = one pass of the whole hot path: bf_factor (sketch RNG, sketch
+products, adaptive leaf bases, peeling, batched QR, B least squares) in the
+mixed precision form, then bf_apply of 64 right-hand sides and the sketch
+error of Sec. 7.  `value` is the factor time in seconds (device-timed with
+CUDA events on the launching stream, L2 flushed before every step by writing
+a 512 MB buffer); the line also reports the plain FP64 factor time, apply
+GB/s, the roofline of the dominant kernel and the oracle timed on the host.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N = 16384
+LEAF = 16
+TOL = 1e-6
+NRHS = 64
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    def __init__(self, path):
+        self.path = path
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", "0"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+            self.f.close()
+
+    def summary(self):
+        try:
+            rows = [l.split(",") for l in open(self.path).read().strip().splitlines() if l.strip()]
+        except Exception:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if "Active" in v and "Not" not in v:
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_sample(n_sample: int = 2048):
+    """The oracle (as it stands) on the same workload at n_sample points,
+    scaled to n = 16384 by the paper's O(n^1.5 log n) cost (Sec. 4.5)."""
+    from oracle import butterfly as ob
+    from oracle import operators as oo
+    from paper_2002_03400_gb300 import inputs
+    g = inputs.line_pair(n_sample)
+    op = oo.KernelOp(oo.HELMHOLTZ_2D, g.wavenumber, g.tgt, g.src)
+    L = inputs.leaf_levels(n_sample, LEAF)
+    t0 = time.perf_counter()
+    ob.factor(op, g.src, g.tgt, L, TOL, 2, 4, seed=0)
+    dt = time.perf_counter() - t0
+    scale = (N / n_sample) ** 1.5 * (math.log(N) / math.log(n_sample))
+    return dt, dt * scale, os.cpu_count()
+
+
+def run_reference(args):
+    """--impl reference: the FP64 oracle on the host cores, bounded sample."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        pass
+    samples = []
+    for _ in range(args.steps):
+        raw, scaled, cores = cpu_oracle_sample(1024)
+        samples.append(scaled)
+    v = float(np.mean(samples))
+    line = {"impl": "reference", "metric": "factor time (s)", "value": v, "unit": "s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+            "data": "synthetic",
+            "config": {"workload": "helmholtz2d_line_pair_n16384_onthefly", "n": N, "leaf": LEAF, "tol": TOL},
+            "cpu_baseline": {"kind": "oracle", "value": v, "unit": "s", "cores": os.cpu_count(),
+                             "sample": "oracle factorization at n=1024 per step, scaled to n=16384 by n^1.5 log n"},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_2002_03400_gb300 import api, inputs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    stream = torch.cuda.current_stream()
+    g = inputs.line_pair(N)
+    plan_mx = api.Plan(g.src, g.tgt, kernel="helmholtz2d", wavenumber=g.wavenumber, leaf=LEAF, tol=TOL,
+                       precision="mixed")
+    plan_64 = api.Plan(g.src, g.tgt, kernel="helmholtz2d", wavenumber=g.wavenumber, leaf=LEAF, tol=TOL,
+                       precision="fp64")
+    op_mx = api.Operator.kernel(plan_mx)
+    op_64 = api.Operator.kernel(plan_64)
+    x = torch.from_numpy(inputs.random_rhs(N, NRHS, seed=1)).cuda()
+    x32 = x.to(torch.complex64)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step(plan, op, xin):
+        F = api.Factorization.factor(plan, op)
+        y = F.apply(xin)
+        err = F.error(op, 16, seed=7)
+        return F, y, err
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        step(plan_mx, op_mx, x32)
+    # plain FP64 form, once, for the comparison line
+    flush.fill_(1.0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    F64, _, err64 = step(plan_64, op_64, x)
+    torch.cuda.synchronize()
+    fp64_step_s = time.perf_counter() - t0
+    fp64_factor_s = F64.info()["seconds"]
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    fac_s, errs = [], []
+    clk = ClockSampler(os.path.join(ROOT, "gpurun_out", "clocks_bench.csv") if os.path.isdir(
+        os.path.join(ROOT, "gpurun_out")) else "/tmp/clocks_bench.csv")
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with clk:
+        for i in range(args.steps):
+            flush.fill_(1.0)
+            starts[i].record(stream)
+            F, y, err = step(plan_mx, op_mx, x32)
+            ends[i].record(stream)
+            fac_s.append(F.info()["seconds"])
+            errs.append(err)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms = float(np.mean(step_ms))
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # apply GB/s (resident factors, 64 RHS, complex64 and complex128)
+    def apply_gbs(F, xin, reps=20):
+        info = F.info()
+        es = 8 if xin.dtype == torch.complex64 else 16
+        byts = info["stored_entries"] * es + NRHS * (2 * N) * es
+        y = F.apply(xin)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            F.apply(xin)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / reps / 1e3
+        return byts / t / 1e9, t
+
+    gbs32, t32 = apply_gbs(F, x32)
+    gbs64, t64 = apply_gbs(F64, x)
+
+    # end to end through the C ABI from host buffers
+    xh = x32.cpu().pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plan_e = api.Plan(g.src, g.tgt, kernel="helmholtz2d", wavenumber=g.wavenumber, leaf=LEAF, tol=TOL,
+                      precision="mixed")
+    Fe = api.Factorization.factor(plan_e, api.Operator.kernel(plan_e))
+    ye = Fe.apply(xh.cuda(non_blocking=True)).cpu()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+
+    peaks, peak_src = measured_peaks()
+    clocks = clk.summary()
+    line = {
+        "metric": "factor time (s)",
+        "value": ms / 1e3,
+        "unit": "s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "c64+f64",
+        "data": "synthetic",
+        "config": {"workload": "helmholtz2d_line_pair_n16384_onthefly", "n": N, "m": N, "leaf": LEAF,
+                   "L": plan_mx.L, "tol": TOL, "p": 2, "r0": 4, "precision": "mixed", "nrhs": NRHS,
+                   "l2": "flushed (512 MB write) before every step"},
+        "factor_s_mixed": float(np.mean(fac_s)),
+        "factor_s_fp64": fp64_factor_s,
+        "sketch_error_mixed": float(np.mean(errs)),
+        "sketch_error_fp64": err64,
+        "apply_gbs_c64": gbs32,
+        "apply_gbs_c128": gbs64,
+        "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(xh.numel() * 8 + 2 * N * 2 * 8),
+                "d2h_bytes_per_step": int(ye.numel() * 8)},
+        "clocks": clocks,
+        "peaks_source": peak_src,
+    }
+    if rank == 0 and not args.no_cpu:
+        raw, scaled, cores = cpu_oracle_sample()
+        line["cpu_baseline"] = {"value": scaled, "unit": "s", "cores": cores, "kind": "oracle",
+                                "sample": f"oracle factorization at n=2048 ({raw:.1f} s), scaled to n=16384 by n^1.5 log n"}
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

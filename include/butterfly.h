@@ -1,0 +1,234 @@
+/*
+ * butterfly.h -- C ABI of the GB300-native adaptive randomized butterfly
+ * factorization (Liu, Xing, Guo, Michielssen, Ghysels, Li, "Butterfly
+ * factorization via randomized matrix-vector multiplications",
+ * arXiv:2002.03400).
+ *
+ * The library computes the hybrid butterfly factorization
+ *     A ~= (U^L R^(L-1) ... R^(l_m)) B^(l_m) (W^(l_m) ... W^1 V^0),  l_m = floor(L/2)
+ * (eq. hybrid_butterfly_mat, Sec. 3.3.3) of an m x n complex operator A given
+ * only as a black box that multiplies A and A^T by blocks of vectors
+ * (Alg. 2, Sec. 4), and applies the result in O(n log n) (Sec. 1).
+ *
+ * Conventions for every entry point:
+ *   - Status: each call returns BF_OK (0) or a negative bf_status code; on
+ *     error every out-handle is set to NULL, nothing leaks, and
+ *     bf_last_error() returns a one-line reason (thread-local).
+ *   - Complex data is interleaved (re, im): BF_C128 = two doubles per entry,
+ *     BF_C64 = two floats.  Matrices are column-major with a leading
+ *     dimension in elements.
+ *   - "Device" pointers are CUDA global-memory addresses on the current
+ *     device; "host" pointers are ordinary CPU memory.  Vectors passed to
+ *     bf_apply and bf_operator_apply are in the caller's original point
+ *     order; the library permutes to tree order itself.
+ *   - Streams are cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls are stream-ordered unless stated otherwise; calls that
+ *     return ranks or errors to the host synchronize the stream.
+ *   - Handles (bf_plan, bf_fact, bf_operator) are used by one host thread at
+ *     a time; concurrent bf_apply calls on one bf_fact from different
+ *     streams are allowed (factors are read-only after bf_factor returns).
+ *   - Memory: device memory is taken with cudaMallocAsync on the call's
+ *     stream (or cudaMalloc) and is counted against bf_options.mem_cap;
+ *     exceeding the cap returns BF_ENOMEM before any allocation.
+ */
+#ifndef BUTTERFLY_H
+#define BUTTERFLY_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bf_plan_s* bf_plan;          /* trees + parameters           */
+typedef struct bf_fact_s* bf_fact;          /* resident factorization       */
+typedef struct bf_operator_s* bf_operator;  /* black-box A (and A^T)        */
+
+typedef enum {
+  BF_OK = 0,
+  BF_EINVAL = -1,          /* bad argument or size                          */
+  BF_ENOMEM = -2,          /* device allocation failed or over mem_cap      */
+  BF_ECALLBACK = -3,       /* a user black-box callback returned non-zero   */
+  BF_ENOTCONVERGED = -4,   /* adaptive leaf rank exceeded r_max             */
+  BF_ECUDA = -5,           /* a CUDA runtime call failed                    */
+  BF_ETIMEOUT = -6,        /* a bounded device wait gave up                 */
+  BF_EUNSUPPORTED = -7     /* combination not built                         */
+} bf_status;
+
+typedef enum { BF_C64 = 0, BF_C128 = 1 } bf_dtype;
+/* op selects A (N), A^T (T) or A^H (C). */
+typedef enum { BF_OP_N = 0, BF_OP_T = 1, BF_OP_C = 2 } bf_op;
+/* FP64: every product in complex128.  MIXED: sketch products, peeling and
+ * the factor copies used by them in complex64 (FP32 arithmetic); pivoted QR,
+ * truncation and the B least squares in FP64. */
+typedef enum { BF_PREC_FP64 = 0, BF_PREC_MIXED = 1 } bf_precision;
+
+typedef enum {
+  BF_KERNEL_NONE = 0,
+  BF_KERNEL_HELMHOLTZ_2D = 1,   /* exp(-i k r) / r                         */
+  BF_KERNEL_HELMHOLTZ_3D = 2,   /* exp(+i k r) / (4 pi r)  (eq. 3dkernel)  */
+  BF_KERNEL_DFT = 3             /* exp(-2 pi i t s), 1-D points            */
+} bf_kernel_type;
+
+typedef struct {
+  int type;            /* bf_kernel_type                                  */
+  double wavenumber;   /* k (ignored by BF_KERNEL_DFT)                    */
+} bf_kernel_desc;
+
+/* Parameters of Alg. 2 (its "Input" line) plus build options. */
+typedef struct {
+  int p;               /* oversampling (default 2)                          */
+  int r0;              /* initial rank guess of the leaf loops (default 4)  */
+  int r_max;           /* leaf-loop rank cap -> BF_ENOTCONVERGED (1024)     */
+  uint64_t seed;       /* seed of the counter-based sketch generator        */
+  int precision;       /* bf_precision (default BF_PREC_FP64)               */
+  size_t mem_cap;      /* device-byte cap per handle, 0 = none              */
+} bf_options;
+
+/* Fills *opt with the defaults above. */
+void bf_options_default(bf_options* opt);
+
+/* Black-box callback (Alg. 2 input: products with A and with A^T).
+ * op is BF_OP_N (Y = A X, X n x ncols, Y m x ncols) or BF_OP_T
+ * (Y = A^T X, X m x ncols, Y n x ncols); X and Y are device pointers in
+ * user point order, valid only during the call; dtype is a bf_dtype; work
+ * must be enqueued on `stream`.  Return 0 on success, non-zero on failure
+ * (the library then returns BF_ECALLBACK). */
+typedef int (*bf_matvec_fn)(void* ctx, int op, int64_t ncols, const void* X,
+                            int64_t ldx, void* Y, int64_t ldy, int dtype,
+                            void* stream);
+
+/* ---------------------------------------------------------------- plan -- */
+/* Builds the bisection trees T_S (sources, n points) and T_T (targets, m
+ * points) of depth L = smallest L with ceil(max(n,m)/2^L) <= leaf (Sec. 3.1).
+ * src/tgt: host, row-major n x dim / m x dim doubles, or NULL for index order
+ * (then dim is ignored).  A node of s points splits into ceil(s/2) and
+ * floor(s/2): points are ordered by the coordinate of largest bounding-box
+ * extent (ties: lowest axis, then lowest index).  kern may be NULL (no
+ * built-in kernel operator).  tol is the truncation tolerance eps of Alg. 1.
+ * opt may be NULL (defaults).  The plan copies everything it needs to the
+ * device.  Errors: BF_EINVAL if n, m < 1, leaf < 1, L < 1 (Alg. 2 needs a
+ * centre level below the leaves), an empty leaf, dim not in {1,2,3}, or
+ * tol < 0. */
+int bf_plan_create(const double* src, int64_t n, const double* tgt, int64_t m,
+                   int dim, const bf_kernel_desc* kern, int leaf, double tol,
+                   const bf_options* opt, bf_plan* out);
+
+/* Tree depth L, centre level l_m, n, m (any pointer may be NULL). */
+int bf_plan_info(bf_plan plan, int* L, int* lm, int64_t* n, int64_t* m);
+
+/* Host copies: permS[i] / permT[i] = original index of tree position i
+ * (length n / m); offS / offT (may be NULL) receive the node boundaries of
+ * every level, level l at offset 2^l - 1 + l ... i.e. concatenated arrays
+ * of 2^l + 1 entries for l = 0..L. */
+int bf_plan_trees(bf_plan plan, int64_t* permS, int64_t* permT, int64_t* offS,
+                  int64_t* offT);
+
+/* Host-only bisection of one point set (the tree half of bf_plan_create;
+ * needs no GPU).  pts: row-major count x dim doubles or NULL (index order).
+ * perm (count int64) and off (sum over l=0..L of 2^l + 1 int64, level l
+ * starting at 2^l - 1 + l) are caller-owned host buffers. */
+int bf_bisect(const double* pts, int64_t count, int dim, int L, int64_t* perm,
+              int64_t* off);
+
+/* ------------------------------------------------------------ operators -- */
+/* Dense stored A (m x n, column-major, user order, device memory, lda >= m).
+ * The operator keeps a tree-ordered copy in the plan's precision's dtype;
+ * the caller's buffer may be freed after the call returns.  Stream-ordered
+ * on `stream`. */
+int bf_operator_dense(bf_plan plan, const void* A, int64_t lda, int dtype,
+                      void* stream, bf_operator* out);
+
+/* A[i,j] = K(t_i, s_j) formed on the fly from the plan's points and kernel
+ * (BF_EINVAL if the plan has no kernel or no points). */
+int bf_operator_kernel(bf_plan plan, bf_operator* out);
+
+/* A = the factorization F, applied by bf_apply / bf_apply_T (the black box
+ * of the exact-recovery and composition workloads).  F must outlive it. */
+int bf_operator_factored(bf_fact F, bf_operator* out);
+
+/* A = A1 * A2 (A1: m x k, A2: k x n); both must outlive it. */
+int bf_operator_composed(bf_operator A1, bf_operator A2, bf_operator* out);
+
+/* A given by a user callback (m x n). */
+int bf_operator_callback(int64_t m, int64_t n, bf_matvec_fn fn, void* ctx,
+                         bf_operator* out);
+
+/* Y = op(A) X in user order (device pointers).  Sizes: op N: X n x ncols,
+ * Y m x ncols; op T/C: X m x ncols, Y n x ncols. */
+int bf_operator_apply(bf_operator A, int op, int64_t ncols, const void* X,
+                      int64_t ldx, void* Y, int64_t ldy, int dtype,
+                      void* stream);
+
+/* Black-box column counts (products with A, with A^T) since creation. */
+int bf_operator_counts(bf_operator A, int64_t* cols_N, int64_t* cols_T);
+
+/* ----------------------------------------------------------- factorize -- */
+/* Alg. 2: adaptive leaf bases V^0, U^L (rank doubling from r0), transfer
+ * matrices W^1..W^(l_m) and R^(L-1)..R^(l_m) from structured random
+ * sketches (Sec. 4.1-4.3) peeled by the factors already recovered, and the
+ * centre coupling B^(l_m) by least squares (eq. Bij, Sec. 4.4).
+ * A may be NULL (the plan's kernel operator).  Synchronizes `stream` once
+ * per level (ranks return to the host to size the next sketch).
+ * Errors: BF_ENOTCONVERGED, BF_ECALLBACK, BF_ENOMEM, BF_ECUDA. */
+int bf_factor(bf_plan plan, bf_operator A, void* stream, bf_fact* out);
+
+/* y = F x (eq. hybrid_butterfly_mat).  x: n x nrhs, y: m x nrhs, device,
+ * user order, dtype BF_C64 or BF_C128 (computed in that precision). */
+int bf_apply(bf_fact F, int64_t nrhs, const void* x, int64_t ldx, void* y,
+             int64_t ldy, int dtype, void* stream);
+
+/* y = F^T x (op BF_OP_T) or F^H x (op BF_OP_C); x: m x nrhs, y: n x nrhs. */
+int bf_apply_T(bf_fact F, int op, int64_t nrhs, const void* x, int64_t ldx,
+               void* y, int64_t ldy, int dtype, void* stream);
+
+/* Ranks of one level (2^L int32 to host; block b = tau*2^(L-l) + nu).
+ * side 0: row bases V (levels 0..l_m); side 1: column bases U (l_m..L). */
+int bf_ranks(bf_fact F, int side, int level, int32_t* out);
+
+/* Statistics (any pointer may be NULL): stored factor entries, black-box
+ * columns with A and with A^T used by bf_factor, and its wall time (s). */
+int bf_fact_info(bf_fact F, int64_t* stored_entries, int64_t* cols_N,
+                 int64_t* cols_T, double* factor_seconds);
+
+/* Import a factorization from host blocks (exactly-butterfly operators).
+ * rV: (l_m+1) x 2^L ranks of the row bases at levels 0..l_m;
+ * rU: (L-l_m+1) x 2^L ranks of the column bases at levels l_m..L.
+ * blocks[s], s = 0..L+2, host pointer to the packed column-major blocks of
+ * stage s in apply order: V^0, W^1..W^(l_m), B, R^(l_m)..R^(L-1), U^L, each
+ * stage's 2^L blocks in block order with ld = block rows.  Block shapes:
+ * V^0: |S_nu| x rV0; W^j: (rV[j-1] of the two children) x rV[j];
+ * B: rU[l_m] x rV[l_m]; R^j: (rU[j+1] of the two children) x rU[j];
+ * U^L: |T_tau| x rU[L].  dtype BF_C128. */
+int bf_fact_import(bf_plan plan, const int32_t* rV, const int32_t* rU,
+                   const void* const* blocks, int dtype, bf_fact* out);
+
+/* Host copy of stage s's packed blocks (layout of bf_fact_import, complex128);
+ * *bytes in: capacity of host_out, out: bytes written (or needed). */
+int bf_fact_export(bf_fact F, int stage, void* host_out, size_t* bytes);
+
+/* Sketch error of Sec. 7 (eq. error): ||A W - F W||_F / ||A W||_F with W a
+ * complex Gaussian n x ncols test matrix drawn from the counter-based
+ * generator (stream 5<<8, user-order rows).  Synchronizes. */
+int bf_error(bf_fact F, bf_operator A, int ncols, uint64_t seed, void* stream,
+             double* err);
+
+/* ------------------------------------------------------------- common -- */
+/* Frees a bf_plan, bf_fact or bf_operator (NULL-safe). */
+void bf_free(void* handle);
+
+/* Reason for the last failure on this thread ("" if none). */
+const char* bf_last_error(void);
+
+/* Device-side Gaussian test/sketch matrix of the counter-based generator:
+ * G[i, c - col0] for rows row0..row0+rows-1, columns col0..col1-1 of
+ * (seed, stream) into a device buffer (ld >= rows), dtype C64/C128. */
+int bf_gaussian(uint64_t seed, uint32_t stream_id, int64_t row0, int64_t rows,
+                int64_t col0, int64_t col1, void* out, int64_t ld, int dtype,
+                void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BUTTERFLY_H */

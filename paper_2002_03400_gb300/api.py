@@ -1,0 +1,369 @@
+"""Thin ctypes binding over libbutterfly.so (include/butterfly.h).
+
+Argument marshalling only: every step of the factorization and apply runs in
+the library's CUDA kernels.  Tensors are torch CUDA tensors; matrices are
+passed column-major (a (rows, cols) tensor with stride(0) == 1), which this
+module arranges.  Importing it loads the library and raises if it is missing
+-- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbutterfly.so")
+
+BF_C64, BF_C128 = 0, 1
+OPS = {"N": 0, "T": 1, "C": 2}
+PREC = {"fp64": 0, "mixed": 1}
+KERNELS = {"none": 0, "helmholtz2d": 1, "helmholtz3d": 2, "dft": 3}
+STATUS = {0: "BF_OK", -1: "BF_EINVAL", -2: "BF_ENOMEM", -3: "BF_ECALLBACK", -4: "BF_ENOTCONVERGED",
+          -5: "BF_ECUDA", -6: "BF_ETIMEOUT", -7: "BF_EUNSUPPORTED"}
+
+
+class BFError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Options(C.Structure):
+    _fields_ = [("p", C.c_int), ("r0", C.c_int), ("r_max", C.c_int), ("seed", C.c_uint64),
+                ("precision", C.c_int), ("mem_cap", C.c_size_t)]
+
+
+class KernelDesc(C.Structure):
+    _fields_ = [("type", C.c_int), ("wavenumber", C.c_double)]
+
+
+MATVEC_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int, C.c_int64, C.c_void_p, C.c_int64,
+                        C.c_void_p, C.c_int64, C.c_int, C.c_void_p)
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: run paper_2002_03400_gb300/build.py (no CPU fallback)")
+    L = C.CDLL(LIB_PATH)
+    vp, i64, i32, dbl = C.c_void_p, C.c_int64, C.c_int, C.c_double
+    sig = {
+        "bf_options_default": (None, [C.POINTER(Options)]),
+        "bf_last_error": (C.c_char_p, []),
+        "bf_plan_create": (i32, [vp, i64, vp, i64, i32, C.POINTER(KernelDesc), i32, dbl, C.POINTER(Options), C.POINTER(vp)]),
+        "bf_bisect": (i32, [vp, i64, i32, i32, vp, vp]),
+        "bf_plan_info": (i32, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i64), C.POINTER(i64)]),
+        "bf_plan_trees": (i32, [vp, vp, vp, vp, vp]),
+        "bf_operator_dense": (i32, [vp, vp, i64, i32, vp, C.POINTER(vp)]),
+        "bf_operator_kernel": (i32, [vp, C.POINTER(vp)]),
+        "bf_operator_factored": (i32, [vp, C.POINTER(vp)]),
+        "bf_operator_composed": (i32, [vp, vp, C.POINTER(vp)]),
+        "bf_operator_callback": (i32, [i64, i64, MATVEC_FN, vp, C.POINTER(vp)]),
+        "bf_operator_apply": (i32, [vp, i32, i64, vp, i64, vp, i64, i32, vp]),
+        "bf_operator_counts": (i32, [vp, C.POINTER(i64), C.POINTER(i64)]),
+        "bf_factor": (i32, [vp, vp, vp, C.POINTER(vp)]),
+        "bf_apply": (i32, [vp, i64, vp, i64, vp, i64, i32, vp]),
+        "bf_apply_T": (i32, [vp, i32, i64, vp, i64, vp, i64, i32, vp]),
+        "bf_ranks": (i32, [vp, i32, i32, vp]),
+        "bf_fact_info": (i32, [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(dbl)]),
+        "bf_fact_import": (i32, [vp, vp, vp, C.POINTER(vp), i32, C.POINTER(vp)]),
+        "bf_fact_export": (i32, [vp, i32, vp, C.POINTER(C.c_size_t)]),
+        "bf_error": (i32, [vp, vp, i32, C.c_uint64, vp, C.POINTER(dbl)]),
+        "bf_free": (None, [vp]),
+        "bf_gaussian": (i32, [C.c_uint64, C.c_uint32, i64, i64, i64, i64, vp, i64, i32, vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def exported_symbols():
+    """Names declared in include/butterfly.h that the binding expects."""
+    return ["bf_options_default", "bf_last_error", "bf_bisect", "bf_plan_create", "bf_plan_info", "bf_plan_trees",
+            "bf_operator_dense", "bf_operator_kernel", "bf_operator_factored", "bf_operator_composed",
+            "bf_operator_callback", "bf_operator_apply", "bf_operator_counts", "bf_factor", "bf_apply",
+            "bf_apply_T", "bf_ranks", "bf_fact_info", "bf_fact_import", "bf_fact_export", "bf_error",
+            "bf_free", "bf_gaussian"]
+
+
+def check(rc: int):
+    if rc != 0:
+        raise BFError(rc, lib().bf_last_error().decode())
+
+
+def _dt(t: torch.Tensor) -> int:
+    if t.dtype == torch.complex128:
+        return BF_C128
+    if t.dtype == torch.complex64:
+        return BF_C64
+    raise TypeError(f"complex64 or complex128 expected, got {t.dtype}")
+
+
+def _tdtype(d: int):
+    return torch.complex128 if d == BF_C128 else torch.complex64
+
+
+def colmajor(x: torch.Tensor) -> torch.Tensor:
+    """View of x (rows, cols) whose memory is column-major (stride(0) == 1)."""
+    if x.dim() == 1:
+        x = x.reshape(-1, 1)
+    if x.stride(0) == 1 and (x.shape[1] <= 1 or x.stride(1) >= x.shape[0]):
+        return x
+    return x.t().contiguous().t()
+
+
+def empty_cm(rows: int, cols: int, dtype, device="cuda") -> torch.Tensor:
+    return torch.empty((cols, rows), dtype=dtype, device=device).t()
+
+
+def _ld(x: torch.Tensor) -> int:
+    return max(x.stride(1) if x.shape[1] > 1 else x.shape[0], x.shape[0], 1)
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+class _Handle:
+    _h = None
+
+    def free(self):
+        if self._h:
+            lib().bf_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Plan(_Handle):
+    """Trees and parameters (bf_plan_create)."""
+
+    def __init__(self, src=None, tgt=None, n=None, m=None, kernel="none", wavenumber=0.0, leaf=16,
+                 tol=1e-6, p=2, r0=4, r_max=1024, seed=0, precision="fp64", mem_cap=0):
+        L = lib()
+        opt = Options()
+        L.bf_options_default(C.byref(opt))
+        opt.p, opt.r0, opt.r_max, opt.seed = p, r0, r_max, seed
+        opt.precision = PREC[precision] if isinstance(precision, str) else int(precision)
+        opt.mem_cap = mem_cap
+        kd = KernelDesc(KERNELS[kernel] if isinstance(kernel, str) else int(kernel), float(wavenumber))
+        self._keep = []
+        if src is not None:
+            s = np.ascontiguousarray(src, dtype=np.float64)
+            t = np.ascontiguousarray(tgt, dtype=np.float64)
+            if s.ndim == 1:
+                s = s.reshape(-1, 1)
+                t = t.reshape(-1, 1)
+            n, m, dim = s.shape[0], t.shape[0], s.shape[1]
+            self._keep = [s, t]
+            sp, tp = s.ctypes.data_as(C.c_void_p), t.ctypes.data_as(C.c_void_p)
+        else:
+            m = n if m is None else m
+            dim, sp, tp = 0, None, None
+        h = C.c_void_p()
+        check(L.bf_plan_create(sp, n, tp, m, dim, C.byref(kd), leaf, tol, C.byref(opt), C.byref(h)))
+        self._h = h
+        self.precision = opt.precision
+        Lv, lm, nn, mm = C.c_int(), C.c_int(), C.c_int64(), C.c_int64()
+        check(L.bf_plan_info(h, C.byref(Lv), C.byref(lm), C.byref(nn), C.byref(mm)))
+        self.L, self.lm, self.n, self.m = Lv.value, lm.value, nn.value, mm.value
+
+    def trees(self):
+        nlev = sum((1 << l) + 1 for l in range(self.L + 1))
+        pS = np.empty(self.n, dtype=np.int64)
+        pT = np.empty(self.m, dtype=np.int64)
+        oS = np.empty(nlev, dtype=np.int64)
+        oT = np.empty(nlev, dtype=np.int64)
+        check(lib().bf_plan_trees(self._h, pS.ctypes.data, pT.ctypes.data, oS.ctypes.data, oT.ctypes.data))
+        offS, offT, q = [], [], 0
+        for l in range(self.L + 1):
+            offS.append(oS[q:q + (1 << l) + 1].copy())
+            offT.append(oT[q:q + (1 << l) + 1].copy())
+            q += (1 << l) + 1
+        return pS, offS, pT, offT
+
+
+class Operator(_Handle):
+    """Black-box A (bf_operator_*)."""
+
+    def __init__(self, handle, m, n, keep=()):
+        self._h = handle
+        self.m, self.n = m, n
+        self._keep = list(keep)
+
+    @classmethod
+    def dense(cls, plan: Plan, A: torch.Tensor, stream=None):
+        A = colmajor(A)
+        h = C.c_void_p()
+        check(lib().bf_operator_dense(plan._h, C.c_void_p(A.data_ptr()), _ld(A), _dt(A), _stream(stream), C.byref(h)))
+        return cls(h, plan.m, plan.n, keep=[plan])
+
+    @classmethod
+    def kernel(cls, plan: Plan):
+        h = C.c_void_p()
+        check(lib().bf_operator_kernel(plan._h, C.byref(h)))
+        return cls(h, plan.m, plan.n, keep=[plan])
+
+    @classmethod
+    def factored(cls, F: "Factorization"):
+        h = C.c_void_p()
+        check(lib().bf_operator_factored(F._h, C.byref(h)))
+        return cls(h, F.m, F.n, keep=[F])
+
+    @classmethod
+    def composed(cls, A1: "Operator", A2: "Operator"):
+        h = C.c_void_p()
+        check(lib().bf_operator_composed(A1._h, A2._h, C.byref(h)))
+        return cls(h, A1.m, A2.n, keep=[A1, A2])
+
+    @classmethod
+    def callback(cls, m: int, n: int, fn):
+        """fn(op, ncols, X_ptr, ldx, Y_ptr, ldy, dtype, stream_ptr) -> int (0 = ok)."""
+        def tramp(ctx, op, ncols, X, ldx, Y, ldy, dtype, stream):
+            try:
+                return int(fn(op, ncols, X, ldx, Y, ldy, dtype, stream))
+            except Exception:
+                return 99
+        cfn = MATVEC_FN(tramp)
+        h = C.c_void_p()
+        check(lib().bf_operator_callback(m, n, cfn, None, C.byref(h)))
+        return cls(h, m, n, keep=[cfn])
+
+    def apply(self, X: torch.Tensor, op: str = "N", stream=None) -> torch.Tensor:
+        X = colmajor(X)
+        rows = self.m if op == "N" else self.n
+        Y = empty_cm(rows, X.shape[1], X.dtype, X.device)
+        check(lib().bf_operator_apply(self._h, OPS[op], X.shape[1], C.c_void_p(X.data_ptr()), _ld(X),
+                                      C.c_void_p(Y.data_ptr()), _ld(Y), _dt(X), _stream(stream)))
+        return Y
+
+    def counts(self):
+        a, b = C.c_int64(), C.c_int64()
+        check(lib().bf_operator_counts(self._h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+
+class Factorization(_Handle):
+    """A resident hybrid butterfly factorization (bf_factor / bf_fact_import)."""
+
+    def __init__(self, handle, plan: Plan):
+        self._h = handle
+        self.plan = plan
+        self.m, self.n, self.L, self.lm = plan.m, plan.n, plan.L, plan.lm
+
+    @classmethod
+    def factor(cls, plan: Plan, A: Operator | None = None, stream=None):
+        h = C.c_void_p()
+        check(lib().bf_factor(plan._h, A._h if A is not None else None, _stream(stream), C.byref(h)))
+        F = cls(h, plan)
+        F._op = A
+        return F
+
+    @classmethod
+    def import_blocks(cls, plan: Plan, rV: np.ndarray, rU: np.ndarray, stages: list):
+        rV = np.ascontiguousarray(rV, dtype=np.int32)
+        rU = np.ascontiguousarray(rU, dtype=np.int32)
+        bufs = [np.ascontiguousarray(s, dtype=np.complex128) for s in stages]
+        arr = (C.c_void_p * len(bufs))(*[b.ctypes.data for b in bufs])
+        h = C.c_void_p()
+        check(lib().bf_fact_import(plan._h, rV.ctypes.data, rU.ctypes.data, arr, BF_C128, C.byref(h)))
+        return cls(h, plan)
+
+    def apply(self, x: torch.Tensor, op: str = "N", stream=None) -> torch.Tensor:
+        x = colmajor(x)
+        rows = self.m if op == "N" else self.n
+        y = empty_cm(rows, x.shape[1], x.dtype, x.device)
+        args = (x.shape[1], C.c_void_p(x.data_ptr()), _ld(x), C.c_void_p(y.data_ptr()), _ld(y), _dt(x), _stream(stream))
+        if op == "N":
+            check(lib().bf_apply(self._h, *args))
+        else:
+            check(lib().bf_apply_T(self._h, OPS[op], *args))
+        return y
+
+    def apply_into(self, x: torch.Tensor, y: torch.Tensor, op: str = "N", stream=None):
+        """Apply with caller-provided column-major buffers (no allocation here)."""
+        args = (x.shape[1], C.c_void_p(x.data_ptr()), _ld(x), C.c_void_p(y.data_ptr()), _ld(y), _dt(x), _stream(stream))
+        if op == "N":
+            check(lib().bf_apply(self._h, *args))
+        else:
+            check(lib().bf_apply_T(self._h, OPS[op], *args))
+
+    def ranks(self, side: int, level: int) -> np.ndarray:
+        out = np.empty(1 << self.L, dtype=np.int32)
+        check(lib().bf_ranks(self._h, side, level, out.ctypes.data))
+        return out
+
+    def info(self) -> dict:
+        s, a, b, t = C.c_int64(), C.c_int64(), C.c_int64(), C.c_double()
+        check(lib().bf_fact_info(self._h, C.byref(s), C.byref(a), C.byref(b), C.byref(t)))
+        return {"stored_entries": s.value, "cols_N": a.value, "cols_T": b.value, "seconds": t.value}
+
+    def export_stage(self, stage: int) -> np.ndarray:
+        nb = C.c_size_t(0)
+        check(lib().bf_fact_export(self._h, stage, None, C.byref(nb)))
+        out = np.empty(nb.value // 16, dtype=np.complex128)
+        check(lib().bf_fact_export(self._h, stage, out.ctypes.data, C.byref(nb)))
+        return out
+
+    def error(self, A: Operator, ncols: int = 16, seed: int = 0, stream=None) -> float:
+        e = C.c_double()
+        check(lib().bf_error(self._h, A._h, ncols, seed, _stream(stream), C.byref(e)))
+        return e.value
+
+
+def bisect(points, count: int, L: int):
+    """Host-only tree build (bf_bisect): (perm, [off per level])."""
+    if points is not None:
+        pts = np.ascontiguousarray(points, dtype=np.float64)
+        if pts.ndim == 1:
+            pts = pts.reshape(-1, 1)
+        pp, dim = pts.ctypes.data_as(C.c_void_p), pts.shape[1]
+    else:
+        pts, pp, dim = None, None, 0
+    perm = np.empty(count, dtype=np.int64)
+    off = np.empty(sum((1 << l) + 1 for l in range(L + 1)), dtype=np.int64)
+    check(lib().bf_bisect(pp, count, dim, L, perm.ctypes.data, off.ctypes.data))
+    out, q = [], 0
+    for l in range(L + 1):
+        out.append(off[q:q + (1 << l) + 1].copy())
+        q += (1 << l) + 1
+    return perm, out
+
+
+def gaussian(seed: int, stream_id: int, rows: int, col0: int, col1: int, dtype=torch.complex128,
+             row0: int = 0, stream=None) -> torch.Tensor:
+    """Device Gaussian matrix of the library's counter-based generator."""
+    out = empty_cm(rows, col1 - col0, dtype)
+    check(lib().bf_gaussian(seed, stream_id, row0, rows, col0, col1, C.c_void_p(out.data_ptr()), max(rows, 1),
+                            _dt(out), _stream(stream)))
+    return out
+
+
+def exact_factorization(plan: Plan, eb) -> Factorization:
+    """Imports an exactly-butterfly operator (inputs.ExactButterfly) whose
+    block order matches the plan's index-order trees."""
+    L, lm, nb, r = eb.L, eb.lm, 1 << eb.L, eb.r
+    rV = np.full((lm + 1, nb), r, dtype=np.int32)
+    rU = np.full((L - lm + 1, nb), r, dtype=np.int32)
+    cm = lambda blocks: np.concatenate([np.asfortranarray(b).ravel(order="F") for b in blocks])
+    stages = [cm(eb.V0)]
+    stages += [cm(eb.W[j]) for j in range(1, lm + 1)]
+    stages += [cm(eb.B)]
+    stages += [cm(eb.R[j]) for j in range(lm, L)]
+    stages += [cm(eb.U)]
+    return Factorization.import_blocks(plan, rV, rU, stages)

@@ -1,0 +1,732 @@
+// C ABI of libbutterfly (include/butterfly.h): handles, the plan (bisection
+// trees of Sec. 3.1), the black-box operators of Alg. 2's input, the error
+// metric of Sec. 7 and factor import/export.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "bf_internal.h"
+
+namespace bf {
+
+// ---------------------------------------------------------------- errors --
+static thread_local std::string g_err;
+void set_error(const std::string& msg) { g_err = msg; }
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+// --------------------------------------------------------------- memory ---
+int dev_alloc(MemTracker* mt, void** p, size_t bytes, cudaStream_t s) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (mt && mt->cap && mt->used + bytes > mt->cap)
+    return fail(BF_ENOMEM, "allocation of " + std::to_string(bytes) + " bytes exceeds mem_cap");
+  cudaError_t e = s ? cudaMallocAsync(p, bytes, s) : cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(BF_ENOMEM, std::string("device allocation failed: ") + cudaGetErrorString(e));
+  }
+  if (mt) {
+    mt->used += bytes;
+    mt->peak = std::max(mt->peak, mt->used);
+  }
+  return BF_OK;
+}
+
+void dev_free(MemTracker* mt, void* p, size_t bytes, cudaStream_t s) {
+  if (!p) return;
+  if (s)
+    cudaFreeAsync(p, s);
+  else
+    cudaFree(p);
+  if (mt) mt->used -= std::min(mt->used, bytes);
+}
+
+int DevBuf::alloc(MemTracker* t, size_t b, cudaStream_t s) {
+  release(s);
+  mt = t;
+  bytes = b ? b : 16;
+  int rc = dev_alloc(t, &p, bytes, s);
+  if (rc) bytes = 0;
+  async_ = s != nullptr;
+  stream_ = s;
+  return rc;
+}
+
+void DevBuf::release(cudaStream_t s) {
+  if (!p) return;
+  dev_free(mt, p, bytes, async_ ? (s ? s : stream_) : nullptr);
+  p = nullptr;
+  bytes = 0;
+}
+
+// ---------------------------------------------------------------- trees ---
+// Bisection (Sec. 3.1): ceil(s/2) / floor(s/2) split; with points, ordered by
+// the coordinate of largest bounding-box extent (ties: lowest axis, then
+// lowest index).
+static void bisect(const double* pts, int64_t count, int dim, int L, std::vector<int64_t>& perm,
+                   std::vector<std::vector<int64_t>>& off) {
+  std::vector<std::vector<int64_t>> nodes(1);
+  nodes[0].resize(count);
+  std::iota(nodes[0].begin(), nodes[0].end(), 0);
+  off.assign(1, {0, count});
+  for (int lev = 0; lev < L; ++lev) {
+    std::vector<std::vector<int64_t>> nxt;
+    nxt.reserve(nodes.size() * 2);
+    for (auto& node : nodes) {
+      const int64_t s = (int64_t)node.size(), h = (s + 1) / 2;
+      if (pts && s > 1) {
+        int ax = 0;
+        double best = -1.0;
+        for (int d = 0; d < dim; ++d) {
+          double lo = pts[node[0] * dim + d], hi = lo;
+          for (int64_t i : node) {
+            const double v = pts[i * dim + d];
+            lo = std::min(lo, v);
+            hi = std::max(hi, v);
+          }
+          if (hi - lo > best) best = hi - lo, ax = d;
+        }
+        std::sort(node.begin(), node.end(), [&](int64_t a, int64_t b) {
+          const double va = pts[a * dim + ax], vb = pts[b * dim + ax];
+          return va < vb || (va == vb && a < b);
+        });
+      }
+      nxt.emplace_back(node.begin(), node.begin() + h);
+      nxt.emplace_back(node.begin() + h, node.end());
+    }
+    nodes.swap(nxt);
+    std::vector<int64_t> o(nodes.size() + 1, 0);
+    for (size_t i = 0; i < nodes.size(); ++i) o[i + 1] = o[i] + (int64_t)nodes[i].size();
+    off.push_back(o);
+  }
+  perm.clear();
+  perm.reserve(count);
+  for (auto& node : nodes) perm.insert(perm.end(), node.begin(), node.end());
+}
+
+// ------------------------------------------------------------ operators ---
+namespace {
+
+struct PlanOp : Operator {
+  // tree-order products without counting
+  virtual int tree_impl(int op, int64_t ncols, const void* X, int64_t ldx, void* Y, int64_t ldy,
+                        int dtype, cudaStream_t s) = 0;
+  virtual int struct_impl(int op, int groups, const int64_t* d_off, int64_t k, const void* Om,
+                          int64_t ldo, void* Y, int64_t ldy, int dtype, cudaStream_t s) = 0;
+  bool has_structured() const override { return true; }
+  int apply_tree(int op, int64_t ncols, const void* X, int64_t ldx, void* Y, int64_t ldy, int dtype,
+                 cudaStream_t s) override {
+    (op == BF_OP_N ? cols_N : cols_T) += ncols;
+    return tree_impl(op, ncols, X, ldx, Y, ldy, dtype, s);
+  }
+  int apply_structured(int op, int groups, const int64_t* d_off, int64_t k, const void* Om,
+                       int64_t ldo, void* Y, int64_t ldy, int dtype, cudaStream_t s) override {
+    (op == BF_OP_N ? cols_N : cols_T) += groups * k;
+    return struct_impl(op, groups, d_off, k, Om, ldo, Y, ldy, dtype, s);
+  }
+  // user order: permute to tree order, product, permute back; A^T X = conj(A^H conj X)
+  int apply(int op, int64_t ncols, const void* X, int64_t ldx, void* Y, int64_t ldy, int dtype,
+            cudaStream_t s) override {
+    if (ncols <= 0) return BF_OK;
+    (op == BF_OP_N ? cols_N : cols_T) += ncols;
+    const bool opN = op == BF_OP_N;
+    const int conj = op == BF_OP_T ? 1 : 0;
+    const int64_t in_rows = opN ? n : m, out_rows = opN ? m : n;
+    const int64_t* pin = (const int64_t*)(opN ? plan->d_permS.p : plan->d_permT.p);
+    const int64_t* pout = (const int64_t*)(opN ? plan->d_permT.p : plan->d_permS.p);
+    const size_t es = elem_bytes(dtype);
+    DevBuf t;
+    BF_TRY(t.alloc(&plan->mem, (in_rows + out_rows) * ncols * es, s));
+    char* xi = (char*)t.p;
+    char* yo = xi + in_rows * ncols * es;
+    int rc = launch_gather_rows(pin, in_rows, ncols, X, ldx, xi, in_rows, conj, dtype, s);
+    if (!rc) rc = tree_impl(opN ? BF_OP_N : BF_OP_C, ncols, xi, in_rows, yo, out_rows, dtype, s);
+    if (!rc) rc = launch_scatter_rows(pout, out_rows, ncols, yo, out_rows, Y, ldy, conj, dtype, s);
+    t.release(s);
+    return rc;
+  }
+};
+
+struct DenseOp : PlanOp {
+  DevBuf A;   // tree order, m x n, ld m, dtype dt
+  int dt = BF_C128;
+  ~DenseOp() override { A.release(nullptr); }
+  int run(int op, const GemmGroups& g, const void* X, int64_t ldx, void* Y, int64_t ldy, int dtype,
+          cudaStream_t s) {
+    if (dtype == dt) return launch_dense_gemm(op, A.p, m, m, n, g, X, ldx, Y, ldy, dtype, s);
+    // compute in the stored dtype, convert at the boundary
+    const bool opN = op == BF_OP_N;
+    const int64_t in_rows = opN ? n : m, out_rows = opN ? m : n;
+    const int64_t xcols = g.d_off ? g.kcols : g.kcols;
+    const int64_t ycols = g.kcols * g.groups;
+    DevBuf t;
+    BF_TRY(t.alloc(&plan->mem, (in_rows * xcols + out_rows * ycols) * elem_bytes(dt), s));
+    char* xi = (char*)t.p;
+    char* yo = xi + in_rows * xcols * elem_bytes(dt);
+    int rc = launch_gather2d(nullptr, nullptr, in_rows, xcols, X, ldx, dtype, xi, in_rows, dt, s);
+    if (!rc) rc = launch_dense_gemm(op, A.p, m, m, n, g, xi, in_rows, yo, out_rows, dt, s);
+    if (!rc) rc = launch_gather2d(nullptr, nullptr, out_rows, ycols, yo, out_rows, dt, Y, ldy, dtype, s);
+    t.release(s);
+    return rc;
+  }
+  int tree_impl(int op, int64_t ncols, const void* X, int64_t ldx, void* Y, int64_t ldy, int dtype,
+                cudaStream_t s) override {
+    GemmGroups g{1, nullptr, ncols};
+    return run(op, g, X, ldx, Y, ldy, dtype, s);
+  }
+  int struct_impl(int op, int groups, const int64_t* d_off, int64_t k, const void* Om, int64_t ldo,
+                  void* Y, int64_t ldy, int dtype, cudaStream_t s) override {
+    GemmGroups g{groups, d_off, k};
+    return run(op, g, Om, ldo, Y, ldy, dtype, s);
+  }
+};
+
+struct KernelOp : PlanOp {
+  int tree_impl(int op, int64_t ncols, const void* X, int64_t ldx, void* Y, int64_t ldy, int dtype,
+                cudaStream_t s) override {
+    GemmGroups g{1, nullptr, ncols};
+    return launch_kernel_gemm(plan, op, g, X, ldx, Y, ldy, dtype, s);
+  }
+  int struct_impl(int op, int groups, const int64_t* d_off, int64_t k, const void* Om, int64_t ldo,
+                  void* Y, int64_t ldy, int dtype, cudaStream_t s) override {
+    GemmGroups g{groups, d_off, k};
+    return launch_kernel_gemm(plan, op, g, Om, ldo, Y, ldy, dtype, s);
+  }
+};
+
+struct FactOp : Operator {
+  Fact* F = nullptr;
+  int apply(int op, int64_t ncols, const void* X, int64_t ldx, void* Y, int64_t ldy, int dtype,
+            cudaStream_t s) override {
+    (op == BF_OP_N ? cols_N : cols_T) += ncols;
+    return apply_fact(F, op, ncols, X, ldx, Y, ldy, dtype, s, false);
+  }
+};
+
+struct ComposedOp : Operator {
+  Operator* A1 = nullptr;
+  Operator* A2 = nullptr;
+  MemTracker mem;
+  int apply(int op, int64_t ncols, const void* X, int64_t ldx, void* Y, int64_t ldy, int dtype,
+            cudaStream_t s) override {
+    if (ncols <= 0) return BF_OK;
+    (op == BF_OP_N ? cols_N : cols_T) += ncols;
+    const int64_t kk = A1->n;
+    DevBuf t;
+    BF_TRY(t.alloc(&mem, kk * ncols * elem_bytes(dtype), s));
+    int rc;
+    if (op == BF_OP_N) {
+      rc = A2->apply(op, ncols, X, ldx, t.p, kk, dtype, s);
+      if (!rc) rc = A1->apply(op, ncols, t.p, kk, Y, ldy, dtype, s);
+    } else {
+      rc = A1->apply(op, ncols, X, ldx, t.p, kk, dtype, s);
+      if (!rc) rc = A2->apply(op, ncols, t.p, kk, Y, ldy, dtype, s);
+    }
+    t.release(s);
+    return rc;
+  }
+};
+
+struct CallbackOp : Operator {
+  bf_matvec_fn fn = nullptr;
+  void* ctx = nullptr;
+  MemTracker mem;
+  int apply(int op, int64_t ncols, const void* X, int64_t ldx, void* Y, int64_t ldy, int dtype,
+            cudaStream_t s) override {
+    if (ncols <= 0) return BF_OK;
+    (op == BF_OP_N ? cols_N : cols_T) += ncols;
+    if (op != BF_OP_C) {
+      const int r = fn(ctx, op, ncols, X, ldx, Y, ldy, dtype, (void*)s);
+      return r ? fail(BF_ECALLBACK, "black-box callback returned " + std::to_string(r)) : BF_OK;
+    }
+    // A^H X = conj(A^T conj X)
+    DevBuf t;
+    BF_TRY(t.alloc(&mem, m * ncols * elem_bytes(dtype), s));
+    int rc = launch_gather_rows(nullptr, m, ncols, X, ldx, t.p, m, 1, dtype, s);
+    if (!rc) {
+      const int r = fn(ctx, BF_OP_T, ncols, t.p, m, Y, ldy, dtype, (void*)s);
+      rc = r ? fail(BF_ECALLBACK, "black-box callback returned " + std::to_string(r)) : BF_OK;
+    }
+    if (!rc) rc = launch_conj_inplace(Y, n, ncols, ldy, dtype, s);
+    t.release(s);
+    return rc;
+  }
+};
+
+template <typename H>
+H* check(void* h, uint32_t kind) {
+  if (!h) return nullptr;
+  H* x = (H*)h;
+  return x->kind == kind ? x : nullptr;
+}
+
+int upload(MemTracker* mt, DevBuf& b, const void* src, size_t bytes) {
+  BF_TRY(b.alloc(mt, bytes, nullptr));
+  BF_CUDA_TRY(cudaMemcpy(b.p, src, bytes, cudaMemcpyHostToDevice));
+  return BF_OK;
+}
+
+}  // namespace
+}  // namespace bf
+
+using namespace bf;
+
+extern "C" {
+
+void bf_options_default(bf_options* o) {
+  if (!o) return;
+  o->p = 2;
+  o->r0 = 4;
+  o->r_max = 1024;
+  o->seed = 0;
+  o->precision = BF_PREC_FP64;
+  o->mem_cap = 0;
+}
+
+const char* bf_last_error(void) { return g_err.c_str(); }
+
+int bf_plan_create(const double* src, int64_t n, const double* tgt, int64_t m, int dim,
+                   const bf_kernel_desc* kern, int leaf, double tol, const bf_options* opt,
+                   bf_plan* out) {
+  if (!out) return fail(BF_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || m < 1 || leaf < 1 || !(tol >= 0)) return fail(BF_EINVAL, "bad n, m, leaf or tol");
+  const bool pts = src && tgt;
+  if ((src == nullptr) != (tgt == nullptr)) return fail(BF_EINVAL, "give both point sets or neither");
+  if (pts && (dim < 1 || dim > 3)) return fail(BF_EINVAL, "dim must be 1, 2 or 3");
+  bf_options o;
+  bf_options_default(&o);
+  if (opt) o = *opt;
+  if (o.p < 0 || o.r0 < 1 || o.r_max < o.r0) return fail(BF_EINVAL, "bad p, r0 or r_max");
+  if (o.precision != BF_PREC_FP64 && o.precision != BF_PREC_MIXED) return fail(BF_EINVAL, "bad precision");
+  int L = 0;
+  const int64_t mx = std::max(n, m);
+  while ((mx + ((int64_t)1 << L) - 1) >> L > leaf) ++L;
+  if (L < 1) return fail(BF_EINVAL, "Alg. 2 needs at least one level below the root (L >= 1)");
+  if (L > 24) return fail(BF_EINVAL, "tree too deep");
+  Plan* P = new Plan();
+  P->n = n;
+  P->m = m;
+  P->dim = pts ? dim : 0;
+  P->L = L;
+  P->lm = L / 2;
+  P->leaf = leaf;
+  P->tol = tol;
+  P->opt = o;
+  P->mem.cap = o.mem_cap;
+  if (kern) P->kern = *kern;
+  P->has_points = pts;
+  bisect(pts ? src : nullptr, n, dim, L, P->permS, P->offS);
+  bisect(pts ? tgt : nullptr, m, dim, L, P->permT, P->offT);
+  for (int b = 0; b < (1 << L); ++b)
+    if (P->offS[L][b + 1] == P->offS[L][b] || P->offT[L][b + 1] == P->offT[L][b]) {
+      delete P;
+      return fail(BF_EINVAL, "a leaf of the bisection tree is empty (too few points for the leaf size)");
+    }
+  for (int64_t i = 0; i < n; ++i) P->identS = P->identS && P->permS[i] == i;
+  for (int64_t i = 0; i < m; ++i) P->identT = P->identT && P->permT[i] == i;
+  int rc = upload(&P->mem, P->d_permS, P->permS.data(), n * 8);
+  if (!rc) rc = upload(&P->mem, P->d_permT, P->permT.data(), m * 8);
+  std::vector<int64_t> cS, cT;
+  for (int l = 0; l <= L; ++l) {
+    P->lvl_start.push_back((int64_t)cS.size());
+    cS.insert(cS.end(), P->offS[l].begin(), P->offS[l].end());
+    cT.insert(cT.end(), P->offT[l].begin(), P->offT[l].end());
+  }
+  if (!rc) rc = upload(&P->mem, P->d_offS, cS.data(), cS.size() * 8);
+  if (!rc) rc = upload(&P->mem, P->d_offT, cT.data(), cT.size() * 8);
+  if (!rc && pts) {
+    std::vector<double> s3(3 * n, 0.0), t3(3 * m, 0.0);
+    for (int64_t i = 0; i < n; ++i)
+      for (int d = 0; d < dim; ++d) s3[d * n + i] = src[P->permS[i] * dim + d];
+    for (int64_t i = 0; i < m; ++i)
+      for (int d = 0; d < dim; ++d) t3[d * m + i] = tgt[P->permT[i] * dim + d];
+    rc = upload(&P->mem, P->d_src, s3.data(), s3.size() * 8);
+    if (!rc) rc = upload(&P->mem, P->d_tgt, t3.data(), t3.size() * 8);
+  }
+  if (rc) {
+    P->d_permS.release(nullptr), P->d_permT.release(nullptr), P->d_offS.release(nullptr);
+    P->d_offT.release(nullptr), P->d_src.release(nullptr), P->d_tgt.release(nullptr);
+    delete P;
+    return rc;
+  }
+  bf_plan h = new bf_plan_s{KIND_PLAN, P};
+  *out = h;
+  return BF_OK;
+}
+
+int bf_bisect(const double* pts, int64_t count, int dim, int L, int64_t* perm, int64_t* off) {
+  if (count < 1 || L < 0 || L > 24 || !perm || !off || (pts && (dim < 1 || dim > 3)))
+    return fail(BF_EINVAL, "bad arguments");
+  std::vector<int64_t> p;
+  std::vector<std::vector<int64_t>> o;
+  bisect(pts, count, dim, L, p, o);
+  std::memcpy(perm, p.data(), count * 8);
+  int64_t q = 0;
+  for (int l = 0; l <= L; ++l) {
+    std::memcpy(off + q, o[l].data(), o[l].size() * 8);
+    q += (int64_t)o[l].size();
+  }
+  return BF_OK;
+}
+
+int bf_plan_info(bf_plan plan, int* L, int* lm, int64_t* n, int64_t* m) {
+  auto* h = check<bf_plan_s>(plan, KIND_PLAN);
+  if (!h) return fail(BF_EINVAL, "not a plan");
+  if (L) *L = h->impl->L;
+  if (lm) *lm = h->impl->lm;
+  if (n) *n = h->impl->n;
+  if (m) *m = h->impl->m;
+  return BF_OK;
+}
+
+int bf_plan_trees(bf_plan plan, int64_t* permS, int64_t* permT, int64_t* offS, int64_t* offT) {
+  auto* h = check<bf_plan_s>(plan, KIND_PLAN);
+  if (!h) return fail(BF_EINVAL, "not a plan");
+  Plan* P = h->impl;
+  if (permS) std::memcpy(permS, P->permS.data(), P->n * 8);
+  if (permT) std::memcpy(permT, P->permT.data(), P->m * 8);
+  int64_t q = 0;
+  for (int l = 0; l <= P->L; ++l) {
+    if (offS) std::memcpy(offS + q, P->offS[l].data(), P->offS[l].size() * 8);
+    if (offT) std::memcpy(offT + q, P->offT[l].data(), P->offT[l].size() * 8);
+    q += (int64_t)P->offS[l].size();
+  }
+  return BF_OK;
+}
+
+int bf_operator_dense(bf_plan plan, const void* A, int64_t lda, int dtype, void* stream,
+                      bf_operator* out) {
+  if (!out) return fail(BF_EINVAL, "out is NULL");
+  *out = nullptr;
+  auto* h = check<bf_plan_s>(plan, KIND_PLAN);
+  if (!h || !A) return fail(BF_EINVAL, "bad plan or matrix");
+  Plan* P = h->impl;
+  if (lda < P->m || (dtype != BF_C64 && dtype != BF_C128)) return fail(BF_EINVAL, "bad lda or dtype");
+  auto* op = new DenseOp();
+  op->plan = P;
+  op->m = P->m;
+  op->n = P->n;
+  op->dt = P->opt.precision == BF_PREC_MIXED ? BF_C64 : BF_C128;
+  int rc = op->A.alloc(&P->mem, P->m * P->n * elem_bytes(op->dt), nullptr);
+  if (!rc)
+    rc = launch_gather2d((const int64_t*)P->d_permT.p, (const int64_t*)P->d_permS.p, P->m, P->n, A, lda,
+                         dtype, op->A.p, P->m, op->dt, (cudaStream_t)stream);
+  if (!rc) {
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) rc = fail(BF_ECUDA, cudaGetErrorString(e));
+  }
+  if (rc) {
+    delete op;
+    return rc;
+  }
+  *out = new bf_operator_s{KIND_OP, op};
+  return BF_OK;
+}
+
+int bf_operator_kernel(bf_plan plan, bf_operator* out) {
+  if (!out) return fail(BF_EINVAL, "out is NULL");
+  *out = nullptr;
+  auto* h = check<bf_plan_s>(plan, KIND_PLAN);
+  if (!h) return fail(BF_EINVAL, "not a plan");
+  Plan* P = h->impl;
+  if (!P->has_points || P->kern.type == BF_KERNEL_NONE) return fail(BF_EINVAL, "plan has no kernel or points");
+  if (P->kern.type == BF_KERNEL_DFT && P->dim != 1) return fail(BF_EINVAL, "DFT kernel needs 1-D points");
+  auto* op = new KernelOp();
+  op->plan = P;
+  op->m = P->m;
+  op->n = P->n;
+  *out = new bf_operator_s{KIND_OP, op};
+  return BF_OK;
+}
+
+int bf_operator_factored(bf_fact F, bf_operator* out) {
+  if (!out) return fail(BF_EINVAL, "out is NULL");
+  *out = nullptr;
+  auto* h = check<bf_fact_s>(F, KIND_FACT);
+  if (!h) return fail(BF_EINVAL, "not a factorization");
+  auto* op = new FactOp();
+  op->F = h->impl;
+  op->m = h->impl->m;
+  op->n = h->impl->n;
+  *out = new bf_operator_s{KIND_OP, op};
+  return BF_OK;
+}
+
+int bf_operator_composed(bf_operator A1, bf_operator A2, bf_operator* out) {
+  if (!out) return fail(BF_EINVAL, "out is NULL");
+  *out = nullptr;
+  auto* h1 = check<bf_operator_s>(A1, KIND_OP);
+  auto* h2 = check<bf_operator_s>(A2, KIND_OP);
+  if (!h1 || !h2) return fail(BF_EINVAL, "not an operator");
+  if (h1->impl->n != h2->impl->m) return fail(BF_EINVAL, "inner dimensions differ");
+  auto* op = new ComposedOp();
+  op->A1 = h1->impl;
+  op->A2 = h2->impl;
+  op->m = h1->impl->m;
+  op->n = h2->impl->n;
+  *out = new bf_operator_s{KIND_OP, op};
+  return BF_OK;
+}
+
+int bf_operator_callback(int64_t m, int64_t n, bf_matvec_fn fn, void* ctx, bf_operator* out) {
+  if (!out) return fail(BF_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (m < 1 || n < 1 || !fn) return fail(BF_EINVAL, "bad size or callback");
+  auto* op = new CallbackOp();
+  op->m = m;
+  op->n = n;
+  op->fn = fn;
+  op->ctx = ctx;
+  *out = new bf_operator_s{KIND_OP, op};
+  return BF_OK;
+}
+
+int bf_operator_apply(bf_operator A, int op, int64_t ncols, const void* X, int64_t ldx, void* Y,
+                      int64_t ldy, int dtype, void* stream) {
+  auto* h = check<bf_operator_s>(A, KIND_OP);
+  if (!h) return fail(BF_EINVAL, "not an operator");
+  if (op != BF_OP_N && op != BF_OP_T && op != BF_OP_C) return fail(BF_EINVAL, "bad op");
+  if (dtype != BF_C64 && dtype != BF_C128) return fail(BF_EINVAL, "bad dtype");
+  const int64_t in_rows = op == BF_OP_N ? h->impl->n : h->impl->m;
+  const int64_t out_rows = op == BF_OP_N ? h->impl->m : h->impl->n;
+  if (ncols < 0 || ldx < in_rows || ldy < out_rows) return fail(BF_EINVAL, "bad ncols or leading dimension");
+  return h->impl->apply(op, ncols, X, ldx, Y, ldy, dtype, (cudaStream_t)stream);
+}
+
+int bf_operator_counts(bf_operator A, int64_t* cols_N, int64_t* cols_T) {
+  auto* h = check<bf_operator_s>(A, KIND_OP);
+  if (!h) return fail(BF_EINVAL, "not an operator");
+  if (cols_N) *cols_N = h->impl->cols_N;
+  if (cols_T) *cols_T = h->impl->cols_T;
+  return BF_OK;
+}
+
+int bf_factor(bf_plan plan, bf_operator A, void* stream, bf_fact* out) {
+  if (!out) return fail(BF_EINVAL, "out is NULL");
+  *out = nullptr;
+  auto* hp = check<bf_plan_s>(plan, KIND_PLAN);
+  if (!hp) return fail(BF_EINVAL, "not a plan");
+  Operator* op = nullptr;
+  bf_operator tmp = nullptr;
+  if (A) {
+    auto* ho = check<bf_operator_s>(A, KIND_OP);
+    if (!ho) return fail(BF_EINVAL, "not an operator");
+    op = ho->impl;
+  } else {
+    BF_TRY(bf_operator_kernel(plan, &tmp));
+    op = tmp->impl;
+  }
+  Fact* F = nullptr;
+  const int rc = factor(hp->impl, op, (cudaStream_t)stream, &F);
+  if (tmp) bf_free(tmp);
+  if (rc) return rc;
+  *out = new bf_fact_s{KIND_FACT, F};
+  return BF_OK;
+}
+
+int bf_apply(bf_fact F, int64_t nrhs, const void* x, int64_t ldx, void* y, int64_t ldy, int dtype,
+             void* stream) {
+  auto* h = check<bf_fact_s>(F, KIND_FACT);
+  if (!h) return fail(BF_EINVAL, "not a factorization");
+  if (nrhs < 0) return fail(BF_EINVAL, "nrhs < 0");
+  return apply_fact(h->impl, BF_OP_N, nrhs, x, ldx, y, ldy, dtype, (cudaStream_t)stream, false);
+}
+
+int bf_apply_T(bf_fact F, int op, int64_t nrhs, const void* x, int64_t ldx, void* y, int64_t ldy,
+               int dtype, void* stream) {
+  auto* h = check<bf_fact_s>(F, KIND_FACT);
+  if (!h) return fail(BF_EINVAL, "not a factorization");
+  if (op != BF_OP_T && op != BF_OP_C) return fail(BF_EINVAL, "op must be BF_OP_T or BF_OP_C");
+  if (nrhs < 0) return fail(BF_EINVAL, "nrhs < 0");
+  return apply_fact(h->impl, op, nrhs, x, ldx, y, ldy, dtype, (cudaStream_t)stream, false);
+}
+
+int bf_ranks(bf_fact F, int side, int level, int32_t* out) {
+  auto* h = check<bf_fact_s>(F, KIND_FACT);
+  if (!h || !out) return fail(BF_EINVAL, "bad factorization or output");
+  Fact* f = h->impl;
+  const std::vector<int32_t>* r = nullptr;
+  if (side == 0 && level >= 0 && level <= f->lm) r = &f->rV[level];
+  if (side == 1 && level >= f->lm && level <= f->L) r = &f->rU[level - f->lm];
+  if (!r) return fail(BF_EINVAL, "level out of range for this side");
+  std::memcpy(out, r->data(), r->size() * 4);
+  return BF_OK;
+}
+
+int bf_fact_info(bf_fact F, int64_t* stored, int64_t* cols_N, int64_t* cols_T, double* secs) {
+  auto* h = check<bf_fact_s>(F, KIND_FACT);
+  if (!h) return fail(BF_EINVAL, "not a factorization");
+  Fact* f = h->impl;
+  if (stored) {
+    int64_t s = 0;
+    for (const auto& S : f->st)
+      for (size_t b = 0; b < S.rows.size(); ++b) s += (int64_t)S.rows[b] * S.cols[b];
+    *stored = s;
+  }
+  if (cols_N) *cols_N = f->cols_N;
+  if (cols_T) *cols_T = f->cols_T;
+  if (secs) *secs = f->seconds;
+  return BF_OK;
+}
+
+int bf_fact_import(bf_plan plan, const int32_t* rV, const int32_t* rU, const void* const* blocks,
+                   int dtype, bf_fact* out) {
+  if (!out) return fail(BF_EINVAL, "out is NULL");
+  *out = nullptr;
+  auto* hp = check<bf_plan_s>(plan, KIND_PLAN);
+  if (!hp || !rV || !rU || !blocks) return fail(BF_EINVAL, "bad arguments");
+  if (dtype != BF_C128) return fail(BF_EINVAL, "import takes complex128 blocks");
+  Plan* P = hp->impl;
+  const int L = P->L, lm = P->lm, nb = 1 << L;
+  Fact* F = new Fact();
+  F->plan = P;
+  F->L = L;
+  F->lm = lm;
+  F->n = P->n;
+  F->m = P->m;
+  F->mem.cap = P->opt.mem_cap;
+  F->st.resize(L + 3);
+  F->rV.assign(lm + 1, std::vector<int32_t>(nb));
+  F->rU.assign(L - lm + 1, std::vector<int32_t>(nb));
+  for (int j = 0; j <= lm; ++j) std::memcpy(F->rV[j].data(), rV + (int64_t)j * nb, nb * 4);
+  for (int j = 0; j <= L - lm; ++j) std::memcpy(F->rU[j].data(), rU + (int64_t)j * nb, nb * 4);
+  auto shape = [&](int s, int b, int& rows, int& cols) {
+    if (s == 0) {
+      rows = (int)(P->offS[L][b + 1] - P->offS[L][b]), cols = F->rV[0][b];
+    } else if (s <= lm) {
+      const int j = s, nn = 1 << (L - j), sg = b / nn, mu = b % nn;
+      const int p0 = (sg >> 1) * (2 * nn) + 2 * mu;
+      rows = F->rV[j - 1][p0] + F->rV[j - 1][p0 + 1], cols = F->rV[j][b];
+    } else if (s == lm + 1) {
+      rows = F->rU[0][b], cols = F->rV[lm][b];
+    } else if (s <= L + 1) {
+      const int j = s - 2, nn = 1 << (L - j), nn1 = nn >> 1, tau = b / nn, nu = b % nn;
+      rows = F->rU[j + 1 - lm][(2 * tau) * nn1 + (nu >> 1)] + F->rU[j + 1 - lm][(2 * tau + 1) * nn1 + (nu >> 1)];
+      cols = F->rU[j - lm][b];
+    } else {
+      rows = (int)(P->offT[L][b + 1] - P->offT[L][b]), cols = F->rU[L - lm][b];
+    }
+  };
+  int rc = BF_OK;
+  for (int s = 0; s < L + 3 && !rc; ++s) {
+    Stage& S = F->st[s];
+    S.rows.resize(nb);
+    S.cols.resize(nb);
+    S.off.resize(nb);
+    int64_t tot = 0;
+    for (int b = 0; b < nb; ++b) {
+      int r, c;
+      shape(s, b, r, c);
+      if (r < 1 || c < 1) rc = fail(BF_EINVAL, "ranks must be >= 1");
+      S.rows[b] = r;
+      S.cols[b] = c;
+      S.off[b] = tot;
+      tot += (int64_t)r * c;
+    }
+    S.total = tot;
+    if (!rc) rc = S.d64.alloc(&F->mem, tot * 16, nullptr);
+    if (!rc && cudaMemcpy(S.d64.p, blocks[s], tot * 16, cudaMemcpyHostToDevice) != cudaSuccess)
+      rc = fail(BF_ECUDA, "copy of imported blocks failed");
+  }
+  if (rc) {
+    for (auto& S : F->st) S.d64.release(nullptr);
+    delete F;
+    return rc;
+  }
+  *out = new bf_fact_s{KIND_FACT, F};
+  return BF_OK;
+}
+
+int bf_fact_export(bf_fact F, int stage, void* host_out, size_t* bytes) {
+  auto* h = check<bf_fact_s>(F, KIND_FACT);
+  if (!h || !bytes) return fail(BF_EINVAL, "bad arguments");
+  Fact* f = h->impl;
+  if (stage < 0 || stage >= (int)f->st.size()) return fail(BF_EINVAL, "stage out of range");
+  const Stage& S = f->st[stage];
+  size_t need = 0;
+  for (size_t b = 0; b < S.rows.size(); ++b) need += (size_t)S.rows[b] * S.cols[b] * 16;
+  if (!host_out || *bytes < need) {
+    *bytes = need;
+    return host_out ? fail(BF_EINVAL, "output buffer too small") : BF_OK;
+  }
+  char* o = (char*)host_out;
+  for (size_t b = 0; b < S.rows.size(); ++b) {
+    const size_t sz = (size_t)S.rows[b] * S.cols[b] * 16;
+    BF_CUDA_TRY(cudaMemcpy(o, (const char*)S.d64.p + S.off[b] * 16, sz, cudaMemcpyDeviceToHost));
+    o += sz;
+  }
+  *bytes = need;
+  return BF_OK;
+}
+
+int bf_gaussian(uint64_t seed, uint32_t stream_id, int64_t row0, int64_t rows, int64_t col0, int64_t col1,
+                void* out, int64_t ld, int dtype, void* stream) {
+  if (!out || rows < 0 || ld < rows || col1 < col0 || row0 < 0) return fail(BF_EINVAL, "bad arguments");
+  if (dtype != BF_C64 && dtype != BF_C128) return fail(BF_EINVAL, "bad dtype");
+  return launch_gaussian(seed, stream_id, row0, rows, col0, col1, out, ld, dtype, (cudaStream_t)stream);
+}
+
+int bf_error(bf_fact F, bf_operator A, int ncols, uint64_t seed, void* stream, double* err) {
+  auto* hf = check<bf_fact_s>(F, KIND_FACT);
+  auto* ho = check<bf_operator_s>(A, KIND_OP);
+  if (!hf || !ho || !err || ncols < 1) return fail(BF_EINVAL, "bad arguments");
+  Fact* f = hf->impl;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = f->n, m = f->m;
+  DevBuf buf;
+  BF_TRY(buf.alloc(&f->mem, (n + 2 * m) * ncols * 16 + 16, s));
+  char* W = (char*)buf.p;
+  char* AW = W + n * ncols * 16;
+  char* FW = AW + m * ncols * 16;
+  double* red = (double*)(FW + m * ncols * 16);
+  int rc = launch_gaussian(seed, 5u << 8, 0, n, 0, ncols, W, n, BF_C128, s);
+  if (!rc) rc = ho->impl->apply(BF_OP_N, ncols, W, n, AW, m, BF_C128, s);
+  if (!rc) rc = apply_fact(f, BF_OP_N, ncols, W, n, FW, m, BF_C128, s, false);
+  if (!rc) rc = launch_diff_norms(AW, FW, m, ncols, m, m, BF_C128, red, s);
+  double h[2] = {0, 0};
+  if (!rc && cudaMemcpyAsync(h, red, 16, cudaMemcpyDeviceToHost, s) != cudaSuccess) rc = fail(BF_ECUDA, "copy");
+  if (!rc && cudaStreamSynchronize(s) != cudaSuccess) rc = fail(BF_ECUDA, "sync");
+  buf.release(s);
+  if (rc) return rc;
+  *err = h[1] > 0 ? std::sqrt(h[0] / h[1]) : 0.0;
+  return BF_OK;
+}
+
+void bf_free(void* handle) {
+  if (!handle) return;
+  const uint32_t kind = *(uint32_t*)handle;
+  if (kind == KIND_PLAN) {
+    auto* h = (bf_plan_s*)handle;
+    Plan* P = h->impl;
+    cudaDeviceSynchronize();
+    P->d_permS.release(nullptr), P->d_permT.release(nullptr), P->d_offS.release(nullptr);
+    P->d_offT.release(nullptr), P->d_src.release(nullptr), P->d_tgt.release(nullptr);
+    delete P;
+    h->kind = 0;
+    delete h;
+  } else if (kind == KIND_FACT) {
+    auto* h = (bf_fact_s*)handle;
+    Fact* F = h->impl;
+    cudaDeviceSynchronize();
+    for (auto& S : F->st) S.d64.release(nullptr), S.d32.release(nullptr);
+    for (auto& a : F->ap)
+      for (auto& b : a) b.tasks.release(nullptr);
+    delete F;
+    h->kind = 0;
+    delete h;
+  } else if (kind == KIND_OP) {
+    auto* h = (bf_operator_s*)handle;
+    cudaDeviceSynchronize();
+    delete h->impl;
+    h->kind = 0;
+    delete h;
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,315 @@
+// Apply of a finished hybrid butterfly factorization (eq. hybrid_butterfly_mat):
+//   F x  = U^L R^(L-1) ... R^(l_m) B^(l_m) W^(l_m) ... W^1 V^0 x
+//   F^H x = V^0^H W^1^H ... B^H ... R^(L-1)^H U^L^H x,   F^T x = conj(F^H conj x)
+// as L + 3 block-sparse stage launches.  Intermediates of one level are
+// stored as one stacked matrix (rows = sum of the level's block ranks,
+// ld = that sum), so the task lists do not depend on the number of
+// right-hand sides and are built once per factorization, direction and dtype.
+#include <algorithm>
+
+#include "bf_internal.h"
+
+namespace bf {
+
+namespace {
+
+void prefix(const std::vector<int32_t>& r, std::vector<int64_t>& off) {
+  off.assign(r.size() + 1, 0);
+  for (size_t i = 0; i < r.size(); ++i) off[i + 1] = off[i] + r[i];
+}
+
+struct Builder {
+  std::vector<StageTask> all;
+  ApplyPlan* ap;
+  int cur_first = 0;
+  void begin() { cur_first = (int)all.size(); }
+  void end() {
+    int mM = 0, mN = 0;
+    for (size_t i = cur_first; i < all.size(); ++i) {
+      mM = std::max(mM, all[i].M);
+      mN = std::max(mN, all[i].N);
+    }
+    ap->first.push_back(cur_first);
+    ap->count.push_back((int)all.size() - cur_first);
+    ap->maxM.push_back(mM);
+    ap->maxN.push_back(mN);
+  }
+};
+
+StageTask mk(int out_base, int64_t out_off, int64_t ldo, int M) {
+  StageTask t{};
+  t.out_base = (int16_t)out_base;
+  t.out_off = out_off;
+  t.ldo = ldo;
+  t.M = M;
+  t.N = 0;
+  t.nterms = 0;
+  return t;
+}
+void add_term(StageTask& t, int in_base, int64_t in_off, int64_t ldi, const void* mat, int ldm,
+              int K, int conjT) {
+  StageTerm& T = t.t[t.nterms++];
+  T.in_base = (int16_t)in_base;
+  T.in_off = in_off;
+  T.ldi = ldi;
+  T.mat = mat;
+  T.ldm = ldm;
+  T.K = K;
+  T.conjT = (int16_t)conjT;
+}
+
+}  // namespace
+
+// Factor block pointer in the requested dtype (complex128 data or its
+// complex64 copy), optionally advanced by `row` rows.
+static const void* blk(const Fact* F, int stage, int b, int dtype, int row = 0) {
+  const Stage& S = F->st[stage];
+  const char* base = (const char*)(dtype == BF_C128 ? S.d64.p : S.d32.p);
+  return base + (S.off[b] + row) * (int64_t)elem_bytes(dtype);
+}
+
+static int build_apply(Fact* F, int opC, int dtype, cudaStream_t s) {
+  ApplyPlan& ap = F->ap[opC][dtype];
+  ap = ApplyPlan();
+  const Plan* P = F->plan;
+  const int L = F->L, lm = F->lm, nb = 1 << L;
+  std::vector<std::vector<int64_t>> rowV(lm + 1), rowU(L - lm + 1);
+  for (int j = 0; j <= lm; ++j) prefix(F->rV[j], rowV[j]);
+  for (int j = lm; j <= L; ++j) prefix(F->rU[j - lm], rowU[j - lm]);
+  auto RV = [&](int j) { return rowV[j][nb]; };
+  auto RU = [&](int j) { return rowU[j - lm][nb]; };
+  auto rv = [&](int j, int b) { return F->rV[j][b]; };
+  auto ru = [&](int j, int b) { return F->rU[j - lm][b]; };
+  int64_t rows_max = 0;
+  for (int j = 0; j <= lm; ++j) rows_max = std::max(rows_max, RV(j));
+  for (int j = lm; j <= L; ++j) rows_max = std::max(rows_max, RU(j));
+  ap.level_rows_max = rows_max;
+  const auto& offS = P->offS[L];
+  const auto& offT = P->offT[L];
+  Builder B;
+  B.ap = &ap;
+  int cur = 1;
+  auto flip = [&]() { cur = 3 - cur; };
+  if (!opC) {
+    // V^0: leaf projections V_{t,nu}^H x(S_nu)
+    B.begin();
+    for (int nu = 0; nu < nb; ++nu) {
+      StageTask t = mk(cur, rowV[0][nu], RV(0), rv(0, nu));
+      const int sz = (int)(offS[nu + 1] - offS[nu]);
+      add_term(t, 0, offS[nu], P->n, blk(F, F->stage_V0(), nu, dtype), sz, sz, 1);
+      B.all.push_back(t);
+    }
+    B.end();
+    // W^j: x_j(s,mu) = W^H [x_{j-1}(s/2, 2mu); x_{j-1}(s/2, 2mu+1)]
+    for (int j = 1; j <= lm; ++j) {
+      const int in = cur;
+      flip();
+      B.begin();
+      const int nn = 1 << (L - j);
+      for (int sg = 0; sg < (1 << j); ++sg)
+        for (int mu = 0; mu < nn; ++mu) {
+          const int b = sg * nn + mu;
+          const int p0 = (sg >> 1) * (2 * nn) + 2 * mu, p1 = p0 + 1;
+          StageTask t = mk(cur, rowV[j][b], RV(j), rv(j, b));
+          const int ldm = F->st[F->stage_W(j)].rows[b];
+          add_term(t, in, rowV[j - 1][p0], RV(j - 1), blk(F, F->stage_W(j), b, dtype), ldm, rv(j - 1, p0), 1);
+          add_term(t, in, rowV[j - 1][p1], RV(j - 1), blk(F, F->stage_W(j), b, dtype, rv(j - 1, p0)), ldm,
+                   rv(j - 1, p1), 1);
+          B.all.push_back(t);
+        }
+      B.end();
+    }
+    // B^(l_m)
+    {
+      const int in = cur;
+      flip();
+      B.begin();
+      for (int b = 0; b < nb; ++b) {
+        StageTask t = mk(cur, rowU[0][b], RU(lm), ru(lm, b));
+        add_term(t, in, rowV[lm][b], RV(lm), blk(F, F->stage_B(), b, dtype), ru(lm, b), rv(lm, b), 0);
+        B.all.push_back(t);
+      }
+      B.end();
+    }
+    // R^j: level j -> j+1, u_{j+1}(s', mu') = sum_c R_{s'/2, 2mu'+c}[rows of s'] u_j(s'/2, 2mu'+c)
+    for (int j = lm; j < L; ++j) {
+      const int in = cur;
+      flip();
+      B.begin();
+      const int nn = 1 << (L - j), nn1 = nn >> 1;
+      for (int sp = 0; sp < (1 << (j + 1)); ++sp)
+        for (int mp = 0; mp < nn1; ++mp) {
+          const int bo = sp * nn1 + mp;
+          StageTask t = mk(cur, rowU[j + 1 - lm][bo], RU(j + 1), ru(j + 1, bo));
+          const int rowoff = (sp & 1) ? ru(j + 1, (sp & ~1) * nn1 + mp) : 0;
+          for (int c = 0; c < 2; ++c) {
+            const int b = (sp >> 1) * nn + 2 * mp + c;
+            add_term(t, in, rowU[j - lm][b], RU(j), blk(F, F->stage_R(j), b, dtype, rowoff),
+                     F->st[F->stage_R(j)].rows[b], ru(j, b), 0);
+          }
+          B.all.push_back(t);
+        }
+      B.end();
+    }
+    // U^L: y(T_tau) = U_{tau,s} u_L(tau)
+    {
+      const int in = cur;
+      B.begin();
+      for (int tau = 0; tau < nb; ++tau) {
+        const int sz = (int)(offT[tau + 1] - offT[tau]);
+        StageTask t = mk(3, offT[tau], P->m, sz);
+        add_term(t, in, rowU[L - lm][tau], RU(L), blk(F, F->stage_U(), tau, dtype), sz, ru(L, tau), 0);
+        B.all.push_back(t);
+      }
+      B.end();
+    }
+  } else {
+    // U^H
+    B.begin();
+    for (int tau = 0; tau < nb; ++tau) {
+      const int sz = (int)(offT[tau + 1] - offT[tau]);
+      StageTask t = mk(cur, rowU[L - lm][tau], RU(L), ru(L, tau));
+      add_term(t, 0, offT[tau], P->m, blk(F, F->stage_U(), tau, dtype), sz, sz, 1);
+      B.all.push_back(t);
+    }
+    B.end();
+    // R^j^H: level j+1 -> j
+    for (int j = L - 1; j >= lm; --j) {
+      const int in = cur;
+      flip();
+      B.begin();
+      const int nn = 1 << (L - j), nn1 = nn >> 1;
+      for (int tau = 0; tau < (1 << j); ++tau)
+        for (int nu = 0; nu < nn; ++nu) {
+          const int b = tau * nn + nu;
+          const int c0 = (2 * tau) * nn1 + (nu >> 1), c1 = (2 * tau + 1) * nn1 + (nu >> 1);
+          StageTask t = mk(cur, rowU[j - lm][b], RU(j), ru(j, b));
+          const int ldm = F->st[F->stage_R(j)].rows[b];
+          add_term(t, in, rowU[j + 1 - lm][c0], RU(j + 1), blk(F, F->stage_R(j), b, dtype), ldm, ru(j + 1, c0), 1);
+          add_term(t, in, rowU[j + 1 - lm][c1], RU(j + 1), blk(F, F->stage_R(j), b, dtype, ru(j + 1, c0)), ldm,
+                   ru(j + 1, c1), 1);
+          B.all.push_back(t);
+        }
+      B.end();
+    }
+    // B^H
+    {
+      const int in = cur;
+      flip();
+      B.begin();
+      for (int b = 0; b < nb; ++b) {
+        StageTask t = mk(cur, rowV[lm][b], RV(lm), rv(lm, b));
+        add_term(t, in, rowU[0][b], RU(lm), blk(F, F->stage_B(), b, dtype), ru(lm, b), ru(lm, b), 1);
+        B.all.push_back(t);
+      }
+      B.end();
+    }
+    // W^j^H: level j -> j-1
+    for (int j = lm; j >= 1; --j) {
+      const int in = cur;
+      flip();
+      B.begin();
+      const int nn = 1 << (L - j);
+      for (int rho = 0; rho < (1 << (j - 1)); ++rho)
+        for (int kap = 0; kap < 2 * nn; ++kap) {
+          const int bo = rho * (2 * nn) + kap;
+          StageTask t = mk(cur, rowV[j - 1][bo], RV(j - 1), rv(j - 1, bo));
+          const int rowoff = (kap & 1) ? rv(j - 1, rho * (2 * nn) + (kap & ~1)) : 0;
+          for (int a = 0; a < 2; ++a) {
+            const int b = (2 * rho + a) * nn + (kap >> 1);
+            add_term(t, in, rowV[j][b], RV(j), blk(F, F->stage_W(j), b, dtype, rowoff),
+                     F->st[F->stage_W(j)].rows[b], rv(j, b), 0);
+          }
+          B.all.push_back(t);
+        }
+      B.end();
+    }
+    // V^0: y(S_nu) = V_{t,nu} x_0(nu)
+    {
+      const int in = cur;
+      B.begin();
+      for (int nu = 0; nu < nb; ++nu) {
+        const int sz = (int)(offS[nu + 1] - offS[nu]);
+        StageTask t = mk(3, offS[nu], P->n, sz);
+        add_term(t, in, rowV[0][nu], RV(0), blk(F, F->stage_V0(), nu, dtype), sz, rv(0, nu), 0);
+        B.all.push_back(t);
+      }
+      B.end();
+    }
+  }
+  BF_TRY(ap.tasks.alloc(&F->mem, B.all.size() * sizeof(StageTask), nullptr));
+  BF_CUDA_TRY(cudaMemcpyAsync(ap.tasks.p, B.all.data(), B.all.size() * sizeof(StageTask),
+                              cudaMemcpyHostToDevice, s));
+  BF_CUDA_TRY(cudaStreamSynchronize(s));
+  ap.built = true;
+  return BF_OK;
+}
+
+int Fact::ensure32(cudaStream_t s) {
+  for (auto& S : st) {
+    if (S.have32) continue;
+    BF_TRY(S.d32.alloc(&mem, S.total * 8, nullptr));
+    BF_TRY(launch_convert(S.d64.p, S.d32.p, S.total, BF_C128, BF_C64, s));
+    S.have32 = true;
+  }
+  return BF_OK;
+}
+
+// Runs the cached stages on bases {xt, ping, pong, yt}.
+int run_apply_stages(Fact* F, int opC, int dtype, int64_t nrhs, void* xt, void* ping, void* pong,
+                     void* yt, cudaStream_t s) {
+  ApplyPlan& ap = F->ap[opC][dtype];
+  StageBases bases{{xt, ping, pong, yt}};
+  for (size_t i = 0; i < ap.first.size(); ++i) {
+    const StageTask* d = (const StageTask*)ap.tasks.p + ap.first[i];
+    BF_TRY(launch_stage(d, ap.count[i], ap.maxM[i], (int)nrhs, (int)nrhs, bases, dtype, s));
+  }
+  return BF_OK;
+}
+
+int prepare_apply(Fact* F, int opC, int dtype, cudaStream_t s) {
+  if (dtype == BF_C64) BF_TRY(F->ensure32(s));
+  if (!F->ap[opC][dtype].built) BF_TRY(build_apply(F, opC, dtype, s));
+  return BF_OK;
+}
+
+int apply_fact(Fact* F, int op, int64_t nrhs, const void* x, int64_t ldx, void* y, int64_t ldy,
+               int dtype, cudaStream_t s, bool tree_order) {
+  if (nrhs <= 0) return BF_OK;
+  if (dtype != BF_C64 && dtype != BF_C128) return fail(BF_EINVAL, "dtype must be BF_C64 or BF_C128");
+  if (op != BF_OP_N && op != BF_OP_T && op != BF_OP_C) return fail(BF_EINVAL, "bad op");
+  const int opC = op == BF_OP_N ? 0 : 1;
+  BF_TRY(prepare_apply(F, opC, dtype, s));
+  const Plan* P = F->plan;
+  const int64_t in_rows = opC ? P->m : P->n, out_rows = opC ? P->n : P->m;
+  if (ldx < in_rows || ldy < out_rows) return fail(BF_EINVAL, "leading dimension too small");
+  const int64_t* perm_in = (const int64_t*)(opC ? P->d_permT.p : P->d_permS.p);
+  const int64_t* perm_out = (const int64_t*)(opC ? P->d_permS.p : P->d_permT.p);
+  const bool id_in = tree_order || (opC ? P->identT : P->identS);
+  const bool id_out = tree_order || (opC ? P->identS : P->identT);
+  const int conj = op == BF_OP_T ? 1 : 0;
+  const size_t es = elem_bytes(dtype);
+  const bool direct_in = id_in && !conj && ldx == in_rows;
+  const bool direct_out = id_out && !conj && ldy == out_rows;
+  const int64_t lvl = F->ap[opC][dtype].level_rows_max * nrhs;
+  const size_t bytes = (2 * lvl + (direct_in ? 0 : in_rows * nrhs) + (direct_out ? 0 : out_rows * nrhs)) * es;
+  DevBuf scratch;
+  BF_TRY(scratch.alloc(&F->mem, bytes, s));
+  char* p = (char*)scratch.p;
+  void* ping = p;
+  void* pong = p + lvl * es;
+  char* q = p + 2 * lvl * es;
+  void* xt = direct_in ? const_cast<void*>(x) : (void*)q;
+  if (!direct_in) q += in_rows * nrhs * es;
+  void* yt = direct_out ? y : (void*)q;
+  int rc = BF_OK;
+  if (!direct_in)
+    rc = launch_gather_rows(id_in ? nullptr : perm_in, in_rows, nrhs, x, ldx, xt, in_rows, conj, dtype, s);
+  if (rc == BF_OK) rc = run_apply_stages(F, opC, dtype, nrhs, xt, ping, pong, yt, s);
+  if (rc == BF_OK && !direct_out)
+    rc = launch_scatter_rows(id_out ? nullptr : perm_out, out_rows, nrhs, yt, out_rows, y, ldy, conj, dtype, s);
+  scratch.release(s);
+  return rc;
+}
+
+}  // namespace bf

@@ -1,0 +1,281 @@
+// Internal declarations shared by the CUDA translation units of libbutterfly.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/butterfly.h"
+
+namespace bf {
+
+// ---------------------------------------------------------------- errors --
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+
+#define BF_CUDA_TRY(expr)                                                     \
+  do {                                                                        \
+    cudaError_t e__ = (expr);                                                 \
+    if (e__ != cudaSuccess)                                                   \
+      return ::bf::fail(BF_ECUDA, std::string(#expr) + ": " +                 \
+                                      cudaGetErrorString(e__));               \
+  } while (0)
+
+#define BF_TRY(expr)          \
+  do {                        \
+    int s__ = (expr);         \
+    if (s__ != BF_OK) return s__; \
+  } while (0)
+
+// --------------------------------------------------------------- memory ---
+// Device buffers owned by a handle; allocation counted against a cap.
+struct MemTracker {
+  size_t cap = 0, used = 0, peak = 0;
+};
+int dev_alloc(MemTracker* mt, void** p, size_t bytes, cudaStream_t s);
+void dev_free(MemTracker* mt, void* p, size_t bytes, cudaStream_t s);
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  MemTracker* mt = nullptr;
+  bool async_ = false;          // stream-ordered allocation (cudaMallocAsync)
+  cudaStream_t stream_ = nullptr;
+  int alloc(MemTracker* t, size_t b, cudaStream_t s);
+  void release(cudaStream_t s);
+};
+
+// ------------------------------------------------------------- handles ----
+enum HandleKind : uint32_t { KIND_PLAN = 0xB0F1A001u, KIND_FACT = 0xB0F1A002u, KIND_OP = 0xB0F1A003u };
+
+struct Plan;
+struct Fact;
+struct Operator;
+
+}  // namespace bf
+
+struct bf_plan_s {
+  uint32_t kind;
+  bf::Plan* impl;
+};
+struct bf_fact_s {
+  uint32_t kind;
+  bf::Fact* impl;
+};
+struct bf_operator_s {
+  uint32_t kind;
+  bf::Operator* impl;
+};
+
+namespace bf {
+
+struct Plan {
+  int64_t n = 0, m = 0;
+  int dim = 0;
+  int L = 0, lm = 0, leaf = 0;
+  double tol = 0;
+  bf_options opt{};
+  bf_kernel_desc kern{BF_KERNEL_NONE, 0.0};
+  bool has_points = false;
+  std::vector<int64_t> permS, permT;          // tree position -> user index
+  std::vector<std::vector<int64_t>> offS, offT;  // per level, 2^l + 1
+  std::vector<double> srcTree, tgtTree;       // tree-ordered points (dim-major rows)
+  // device copies
+  MemTracker mem;
+  DevBuf d_permS, d_permT;                    // int64
+  DevBuf d_src, d_tgt;                        // double, SoA: x[n], y[n], z[n]
+  DevBuf d_offS, d_offT;                      // int64, all levels concatenated
+  std::vector<int64_t> lvl_start;             // level l starts at lvl_start[l] in d_off*
+  bool identS = true, identT = true;          // permutation is the identity
+  const int64_t* offS_dev(int l) const { return (const int64_t*)d_offS.p + lvl_start[l]; }
+  const int64_t* offT_dev(int l) const { return (const int64_t*)d_offT.p + lvl_start[l]; }
+};
+
+// A black-box operator.  apply() works in user order; apply_tree() in the
+// tree order of `plan` (only for operators bound to a plan).
+struct Operator {
+  int64_t m = 0, n = 0;
+  Plan* plan = nullptr;                // non-null: native tree order of this plan
+  int64_t cols_N = 0, cols_T = 0;
+  virtual ~Operator() {}
+  // Y = op(A) X, user order. op in {N, T, C}.
+  virtual int apply(int op, int64_t ncols, const void* X, int64_t ldx, void* Y,
+                    int64_t ldy, int dtype, cudaStream_t s) = 0;
+  // Tree order of `plan` (only when plan != nullptr); op in {N, C}.
+  virtual int apply_tree(int op, int64_t ncols, const void* X, int64_t ldx,
+                         void* Y, int64_t ldy, int dtype, cudaStream_t s) {
+    return fail(BF_EUNSUPPORTED, "operator has no tree-order product");
+  }
+  // Structured sketch (Sec. 4.1), tree order: for each node g of `groups`
+  // with rows [off[g], off[g+1]) of the input side, and compact random
+  // matrix Om (rows = input side, k columns, ld ldo):
+  //   op N: Y[:, g*k:(g+1)*k] = A[:, rows_g] Om[rows_g, :]
+  //   op C: Y[:, g*k:(g+1)*k] = A[rows_g, :]^H Om[rows_g, :]
+  virtual bool has_structured() const { return false; }
+  virtual int apply_structured(int op, int groups, const int64_t* d_off,
+                               int64_t k, const void* Om, int64_t ldo, void* Y,
+                               int64_t ldy, int dtype, cudaStream_t s) {
+    return fail(BF_EUNSUPPORTED, "operator has no structured product");
+  }
+};
+
+// ---------------------------------------------------------------- factors --
+// One stage of the factorization in apply order: 2^L blocks, column-major,
+// block b has rows[b] x cols[b] with ld = rows[b] at element offset off[b].
+struct Stage {
+  std::vector<int32_t> rows, cols;
+  std::vector<int64_t> off;
+  int64_t total = 0;                 // elements
+  DevBuf d64;                        // complex128 data
+  DevBuf d32;                        // complex64 copy (mixed precision / c64 apply)
+  bool have32 = false;
+};
+
+// Cached task lists of one apply direction and dtype (eq. hybrid_butterfly_mat):
+// stage i reads bases[in_base[i]] and writes bases[out_base[i]].
+struct ApplyPlan {
+  bool built = false;
+  DevBuf tasks;
+  std::vector<int64_t> first;        // first task of each stage
+  std::vector<int> count, maxM, maxN;
+  int64_t level_rows_max = 0;        // rows of the largest stacked intermediate
+};
+
+struct Fact {
+  Plan* plan = nullptr;
+  int L = 0, lm = 0;
+  int64_t n = 0, m = 0;
+  std::vector<Stage> st;             // L + 3 stages
+  std::vector<std::vector<int32_t>> rV;  // levels 0..lm
+  std::vector<std::vector<int32_t>> rU;  // index j - lm for levels lm..L
+  int64_t cols_N = 0, cols_T = 0;
+  double seconds = 0;
+  MemTracker mem;
+  ApplyPlan ap[2][2];                // [op N / C][dtype C64 / C128]
+  int stage_V0() const { return 0; }
+  int stage_W(int j) const { return j; }
+  int stage_B() const { return lm + 1; }
+  int stage_R(int j) const { return j + 2; }
+  int stage_U() const { return L + 2; }
+  int ensure32(cudaStream_t s);
+};
+
+// -------------------------------------------------------- stage products --
+// One output block (or column slice of it) of a block-sparse product:
+//   out[M x N] = sum_t op_t(mat_t)[M x K_t] * in_t[K_t x N]
+// op_t = 0: mat_t is M x K_t (ld ldm);  op_t = 1: mat_t is stored K_t x M and
+// conjugate-transposed.  `in` and `out` are element offsets into one of four
+// base pointers given at launch (so a task list can be reused with fresh
+// scratch buffers); `mat` is an absolute device pointer into factor storage.
+struct StageTerm {
+  int64_t in_off;
+  const void* mat;
+  int64_t ldi;
+  int32_t ldm;
+  int32_t K;
+  int16_t conjT;
+  int16_t in_base;
+  int32_t pad;
+};
+struct StageTask {
+  int64_t out_off;
+  int64_t ldo;
+  int32_t M, N;
+  int16_t nterms;
+  int16_t out_base;
+  int32_t pad;
+  StageTerm t[2];
+};
+struct StageBases {
+  void* p[4];
+};
+// N of every task is replaced by Noverride when Noverride > 0.
+int launch_stage(const StageTask* d_tasks, int ntasks, int maxM, int maxN, int Noverride,
+                 const StageBases& bases, int dtype, cudaStream_t s);
+
+// ------------------------------------------------------------------- QR --
+struct QRTask {
+  const void* in;     // s x k, ld ldi
+  void* q;            // s x cap output, ld = s
+  int64_t ldi;
+  int32_t s, k;
+  int32_t cap;        // columns available in q (>= min(s,k))
+  int32_t pad;
+};
+// Truncated column-pivoted Householder QR (Alg. 1 step 3); ranks[i] out.
+// in dtype: C64 or C128 (QR always in FP64); q is complex128.
+int launch_qr(const QRTask* d_tasks, int ntasks, int maxS, int maxK, double eps,
+              int in_dtype, int32_t* d_ranks, void* d_work, size_t work_bytes,
+              cudaStream_t s);
+size_t qr_workspace_bytes(int ntasks, int maxS, int maxK);
+
+// ------------------------------------------------------------ B solve ----
+struct LSQTask {
+  const void* P;      // s x k stacked peeled sketch (ld s)
+  const void* Q;      // s x rU   (R_{tau,nu}, complex128, ld s)
+  const void* X;      // rV x k   (V^H Omega, ld rV)
+  void* B;            // rU x rV  output (complex128, ld rU)
+  int32_t s, k, rU, rV;
+};
+int launch_lsq(const LSQTask* d_tasks, int ntasks, int maxS, int maxK, int maxR,
+               int in_dtype, cudaStream_t s);
+
+// ------------------------------------------------------------- sketches --
+// Counter-based Gaussian generator (Philox-4x32-10 + Box-Muller).
+int launch_gaussian(uint64_t seed, uint32_t stream_id, int64_t row0, int64_t rows,
+                    int64_t col0, int64_t col1, void* out, int64_t ld, int dtype,
+                    cudaStream_t s);
+
+// Complex GEMM variants for the built-in operators (tree order).
+//   mode 0: dense stored A (M x K source, lda), A entries read
+//   mode 1: kernel entries formed from points
+// op N: Y[m x N] = A[:, k-range] * X ; op C: Y[n x N] = A[k-range rows,:]^H X
+struct GemmGroups {
+  int groups;             // >= 1
+  const int64_t* d_off;   // groups+1 boundaries of the K range per group (device), or null
+  int64_t kcols;          // columns per group (structured) or total columns (groups == 1)
+};
+int launch_dense_gemm(int op, const void* A, int64_t lda, int64_t m, int64_t n,
+                      const GemmGroups& g, const void* X, int64_t ldx, void* Y,
+                      int64_t ldy, int dtype, cudaStream_t s);
+int launch_kernel_gemm(const Plan* plan, int op, const GemmGroups& g,
+                       const void* X, int64_t ldx, void* Y, int64_t ldy,
+                       int dtype, cudaStream_t s);
+
+// ---------------------------------------------------------------- misc ----
+// out[i, c] = conj?(in[perm[i], c])  (perm may be null: identity)
+int launch_gather_rows(const int64_t* d_perm, int64_t rows, int64_t cols,
+                       const void* in, int64_t ldi, void* out, int64_t ldo,
+                       int conj, int dtype, cudaStream_t s);
+// out[perm[i], c] = conj?(in[i, c])
+int launch_scatter_rows(const int64_t* d_perm, int64_t rows, int64_t cols,
+                        const void* in, int64_t ldi, void* out, int64_t ldo,
+                        int conj, int dtype, cudaStream_t s);
+// Structured expansion: out (rows x groups*k, zeroed) gets
+// out[off[g]:off[g+1], g*k:(g+1)*k] = in[off[g]:off[g+1], 0:k]
+int launch_expand_structured(int groups, const int64_t* d_off, int64_t rows,
+                             int64_t k, const void* in, int64_t ldi, void* out,
+                             int64_t ldo, int dtype, cudaStream_t s);
+// out[i + j*ldo] = in[rp[i] + cp[j]*ldi] converted to out_dtype (rp/cp may be null)
+int launch_gather2d(const int64_t* d_rp, const int64_t* d_cp, int64_t rows, int64_t cols,
+                    const void* in, int64_t ldi, int in_dtype, void* out, int64_t ldo,
+                    int out_dtype, cudaStream_t s);
+int launch_convert(const void* in, void* out, int64_t count, int in_dtype,
+                   int out_dtype, cudaStream_t s);
+int launch_conj_inplace(void* p, int64_t rows, int64_t cols, int64_t ld,
+                        int dtype, cudaStream_t s);
+// sums of |a-b|^2 and |a|^2 over rows x cols into d_out[0..1] (double)
+int launch_diff_norms(const void* a, const void* b, int64_t rows, int64_t cols,
+                      int64_t lda, int64_t ldb, int dtype, double* d_out,
+                      cudaStream_t s);
+
+inline size_t elem_bytes(int dtype) { return dtype == BF_C128 ? 16 : 8; }
+
+// ------------------------------------------------------- driver entries --
+int apply_fact(Fact* F, int op, int64_t nrhs, const void* x, int64_t ldx,
+               void* y, int64_t ldy, int dtype, cudaStream_t s, bool tree_order);
+int factor(Plan* P, Operator* A, cudaStream_t s, Fact** out);
+
+}  // namespace bf
