@@ -183,6 +183,41 @@ int bf_apply(bf_fact F, int64_t nrhs, const void* x, int64_t ldx, void* y,
 int bf_apply_T(bf_fact F, int op, int64_t nrhs, const void* x, int64_t ldx,
                void* y, int64_t ldy, int dtype, void* stream);
 
+/* Size of the fixed device scratch array used by bf_apply_noalloc (32 MiB).
+ * Every GPU on which the library is loaded holds this array until the
+ * process exits, whether or not bf_apply_noalloc is ever called. */
+#define BF_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* Apply without device allocation.  The paper has no counterpart: this is a
+ * service for callers that must not allocate device memory while they run --
+ * for example an application that handed all device memory to its own pool
+ * at start-up (cudaMalloc would fail or fragment that pool), a plug-in
+ * running inside a framework that owns the device's memory, or a
+ * latency-bound loop whose per-request path may not call cudaMalloc/cudaFree
+ * (both can synchronize the whole device).
+ * Computes y = F x (op BF_OP_N), F^T x (BF_OP_T) or F^H x (BF_OP_C) exactly
+ * as bf_apply / bf_apply_T do, with the same argument meaning and layout;
+ * the caller still owns x and y.  All intermediates live in one file-scope
+ * device array of BF_NOALLOC_SCRATCH_BYTES:
+ *   - the first call on a device looks up that array's device address
+ *     (cudaGetSymbolAddress) with the device current; make that first call
+ *     before capturing the stream into a CUDA graph;
+ *   - a request that needs more scratch than the array holds (grows with
+ *     nrhs and with the factorization's block ranks) returns BF_EINVAL with
+ *     the byte counts in bf_last_error(); split the columns into smaller
+ *     calls;
+ *   - every call shares the array and it keeps the last call's contents;
+ *     nothing in it needs to start at zero (each call writes every element
+ *     it later reads), but calls whose GPU work overlaps -- on different
+ *     streams, threads or factorizations -- race on it: serialize them;
+ *   - BF_C64 needs the factorization's complex64 copy (a BF_PREC_MIXED
+ *     factorization, or one that bf_apply has already run in BF_C64);
+ *     otherwise BF_EINVAL.
+ * Calls no cudaMalloc, cudaFree or other allocating routine. */
+int bf_apply_noalloc(bf_fact F, int op, int64_t nrhs, const void* x,
+                     int64_t ldx, void* y, int64_t ldy, int dtype,
+                     void* stream);
+
 /* Ranks of one level (2^L int32 to host; block b = tau*2^(L-l) + nu).
  * side 0: row bases V (levels 0..l_m); side 1: column bases U (l_m..L). */
 int bf_ranks(bf_fact F, int side, int level, int32_t* out);

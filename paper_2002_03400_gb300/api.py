@@ -71,6 +71,7 @@ def lib():
         "bf_factor": (i32, [vp, vp, vp, C.POINTER(vp)]),
         "bf_apply": (i32, [vp, i64, vp, i64, vp, i64, i32, vp]),
         "bf_apply_T": (i32, [vp, i32, i64, vp, i64, vp, i64, i32, vp]),
+        "bf_apply_noalloc": (i32, [vp, i32, i64, vp, i64, vp, i64, i32, vp]),
         "bf_ranks": (i32, [vp, i32, i32, vp]),
         "bf_fact_info": (i32, [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(dbl)]),
         "bf_fact_import": (i32, [vp, vp, vp, C.POINTER(vp), i32, C.POINTER(vp)]),
@@ -92,7 +93,7 @@ def exported_symbols():
     return ["bf_options_default", "bf_last_error", "bf_bisect", "bf_plan_create", "bf_plan_info", "bf_plan_trees",
             "bf_operator_dense", "bf_operator_kernel", "bf_operator_factored", "bf_operator_composed",
             "bf_operator_callback", "bf_operator_apply", "bf_operator_counts", "bf_factor", "bf_apply",
-            "bf_apply_T", "bf_ranks", "bf_fact_info", "bf_fact_import", "bf_fact_export", "bf_error",
+            "bf_apply_T", "bf_apply_noalloc", "bf_ranks", "bf_fact_info", "bf_fact_import", "bf_fact_export", "bf_error",
             "bf_free", "bf_gaussian"]
 
 

@@ -68,9 +68,8 @@ static const void* blk(const Fact* F, int stage, int b, int dtype, int row = 0) 
   return base + (S.off[b] + row) * (int64_t)elem_bytes(dtype);
 }
 
-static int build_apply(Fact* F, int opC, int dtype, cudaStream_t s) {
-  ApplyPlan& ap = F->ap[opC][dtype];
-  ap = ApplyPlan();
+// Host half of the task lists: fills ap's stage metadata and `all`.
+void apply_tasks_host(const Fact* F, int opC, int dtype, ApplyPlan& ap, std::vector<StageTask>& all) {
   const Plan* P = F->plan;
   const int L = F->L, lm = F->lm, nb = 1 << L;
   std::vector<std::vector<int64_t>> rowV(lm + 1), rowU(L - lm + 1);
@@ -237,8 +236,16 @@ static int build_apply(Fact* F, int opC, int dtype, cudaStream_t s) {
       B.end();
     }
   }
-  BF_TRY(ap.tasks.alloc(&F->mem, B.all.size() * sizeof(StageTask), nullptr));
-  BF_CUDA_TRY(cudaMemcpyAsync(ap.tasks.p, B.all.data(), B.all.size() * sizeof(StageTask),
+  all.swap(B.all);
+}
+
+static int build_apply(Fact* F, int opC, int dtype, cudaStream_t s) {
+  ApplyPlan& ap = F->ap[opC][dtype];
+  ap = ApplyPlan();
+  std::vector<StageTask> all;
+  apply_tasks_host(F, opC, dtype, ap, all);
+  BF_TRY(ap.tasks.alloc(&F->mem, all.size() * sizeof(StageTask), nullptr));
+  BF_CUDA_TRY(cudaMemcpyAsync(ap.tasks.p, all.data(), all.size() * sizeof(StageTask),
                               cudaMemcpyHostToDevice, s));
   BF_CUDA_TRY(cudaStreamSynchronize(s));
   ap.built = true;

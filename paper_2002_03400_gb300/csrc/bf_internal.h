@@ -274,6 +274,7 @@ int launch_diff_norms(const void* a, const void* b, int64_t rows, int64_t cols,
 inline size_t elem_bytes(int dtype) { return dtype == BF_C128 ? 16 : 8; }
 
 // ------------------------------------------------------- driver entries --
+void apply_tasks_host(const Fact* F, int opC, int dtype, ApplyPlan& ap, std::vector<StageTask>& all);
 int apply_fact(Fact* F, int op, int64_t nrhs, const void* x, int64_t ldx,
                void* y, int64_t ldy, int dtype, cudaStream_t s, bool tree_order);
 int factor(Plan* P, Operator* A, cudaStream_t s, Fact** out);
