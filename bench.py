@@ -160,10 +160,12 @@ def main():
     x32 = x.to(torch.complex64)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    def step(plan, op, xin):
+    def step(plan, op, xin, ev=None):
         F = api.Factorization.factor(plan, op)
+        if ev is not None:
+            ev.record(stream)
         y = F.apply(xin)
-        err = F.error(op, 16, seed=7)
+        err = F.error(op, 16, seed=7, dtype=xin.dtype)
         return F, y, err
 
     for _ in range(args.warmup):
@@ -179,6 +181,7 @@ def main():
     fp64_factor_s = F64.info()["seconds"]
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    mids = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     fac_s, errs = [], []
     clk = ClockSampler(os.path.join(ROOT, "gpurun_out", "clocks_bench.csv") if os.path.isdir(
@@ -190,7 +193,7 @@ def main():
         for i in range(args.steps):
             flush.fill_(1.0)
             starts[i].record(stream)
-            F, y, err = step(plan_mx, op_mx, x32)
+            F, y, err = step(plan_mx, op_mx, x32, mids[i])
             ends[i].record(stream)
             fac_s.append(F.info()["seconds"])
             errs.append(err)
@@ -198,11 +201,13 @@ def main():
     if dist:
         dist.barrier()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    fac_ms = [s.elapsed_time(e) for s, e in zip(starts, mids)]
     ms = float(np.mean(step_ms))
+    fms = float(np.mean(fac_ms))
     if dist:
-        t = torch.tensor([ms], device="cuda")
+        t = torch.tensor([ms, fms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms, fms = float(t[0].item()), float(t[1].item())
 
     # apply GB/s (resident factors, 64 RHS, complex64 and complex128)
     def apply_gbs(F, xin, reps=20):
@@ -223,6 +228,24 @@ def main():
     gbs32, t32 = apply_gbs(F, x32)
     gbs64, t64 = apply_gbs(F64, x)
 
+    # roofline of the dominant kernel (the on-the-fly sketch product): one
+    # launch over all m x n entries with the widest sketch width of the run,
+    # timed with CUDA events on the launching stream
+    kw = 22
+    Xk = api.colmajor(torch.from_numpy(inputs.random_rhs(N, kw, seed=3)).to(torch.complex64).cuda())
+    op_mx.apply(Xk)
+    r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    torch.cuda.synchronize()
+    r0.record(stream)
+    for _ in range(reps):
+        op_mx.apply(Xk)
+    r1.record(stream)
+    torch.cuda.synchronize()
+    t_sk = r0.elapsed_time(r1) / reps / 1e3
+    sk_flops = 8.0 * N * N * kw            # complex multiply-adds x 8 real flops
+    fp32_peak = 152 * 128 * 2 * 2070e6 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
+
     # end to end through the C ABI from host buffers
     xh = x32.cpu().pin_memory()
     torch.cuda.synchronize()
@@ -238,7 +261,7 @@ def main():
     clocks = clk.summary()
     line = {
         "metric": "factor time (s)",
-        "value": ms / 1e3,
+        "value": fms / 1e3,
         "unit": "s",
         "n_gpus": world,
         "steps": args.steps,
@@ -262,6 +285,12 @@ def main():
                 "d2h_bytes_per_step": int(ye.numel() * 8)},
         "clocks": clocks,
         "peaks_source": peak_src,
+        "roofline": {"kernel": "sketch_gemm_kernel<float> (entries on the fly)", "bound": "alu",
+                     "achieved": sk_flops / t_sk / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": sk_flops / t_sk / 1e12 / fp32_peak, "traffic": None,
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                     "work": f"8*m*n*k flop, m=n={N}, k={kw}; entry formation (~100 FP32 ops/entry) not counted",
+                     "launch_ms": t_sk * 1e3},
     }
     if rank == 0 and not args.no_cpu:
         raw, scaled, cores = cpu_oracle_sample()

@@ -245,9 +245,10 @@ int bf_fact_export(bf_fact F, int stage, void* host_out, size_t* bytes);
 
 /* Sketch error of Sec. 7 (eq. error): ||A W - F W||_F / ||A W||_F with W a
  * complex Gaussian n x ncols test matrix drawn from the counter-based
- * generator (stream 5<<8, user-order rows).  Synchronizes. */
-int bf_error(bf_fact F, bf_operator A, int ncols, uint64_t seed, void* stream,
-             double* err);
+ * generator (stream 5<<8, user-order rows); both products are computed in
+ * `dtype` (BF_C64 or BF_C128), the norms in FP64.  Synchronizes. */
+int bf_error(bf_fact F, bf_operator A, int ncols, uint64_t seed, int dtype,
+             void* stream, double* err);
 
 /* ------------------------------------------------------------- common -- */
 /* Frees a bf_plan, bf_fact or bf_operator (NULL-safe). */

@@ -76,7 +76,7 @@ def lib():
         "bf_fact_info": (i32, [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(dbl)]),
         "bf_fact_import": (i32, [vp, vp, vp, C.POINTER(vp), i32, C.POINTER(vp)]),
         "bf_fact_export": (i32, [vp, i32, vp, C.POINTER(C.c_size_t)]),
-        "bf_error": (i32, [vp, vp, i32, C.c_uint64, vp, C.POINTER(dbl)]),
+        "bf_error": (i32, [vp, vp, i32, C.c_uint64, i32, vp, C.POINTER(dbl)]),
         "bf_free": (None, [vp]),
         "bf_gaussian": (i32, [C.c_uint64, C.c_uint32, i64, i64, i64, i64, vp, i64, i32, vp]),
     }
@@ -321,9 +321,10 @@ class Factorization(_Handle):
         check(lib().bf_fact_export(self._h, stage, out.ctypes.data, C.byref(nb)))
         return out
 
-    def error(self, A: Operator, ncols: int = 16, seed: int = 0, stream=None) -> float:
+    def error(self, A: Operator, ncols: int = 16, seed: int = 0, dtype=torch.complex128, stream=None) -> float:
         e = C.c_double()
-        check(lib().bf_error(self._h, A._h, ncols, seed, _stream(stream), C.byref(e)))
+        d = BF_C128 if dtype == torch.complex128 else BF_C64
+        check(lib().bf_error(self._h, A._h, ncols, seed, d, _stream(stream), C.byref(e)))
         return e.value
 
 

@@ -348,10 +348,29 @@ int bf_plan_create(const double* src, int64_t n, const double* tgt, int64_t m, i
       for (int d = 0; d < dim; ++d) t3[d * m + i] = tgt[P->permT[i] * dim + d];
     rc = upload(&P->mem, P->d_src, s3.data(), s3.size() * 8);
     if (!rc) rc = upload(&P->mem, P->d_tgt, t3.data(), t3.size() * 8);
+    // float-float copies (hi = float(x), lo = float(x - hi)) for the mixed
+    // path's entries: layout [x_hi, x_lo, y_hi, y_lo, z_hi, z_lo] x count
+    auto split = [](const std::vector<double>& v, int64_t cnt) {
+      std::vector<float> f(6 * cnt);
+      for (int d = 0; d < 3; ++d)
+        for (int64_t i = 0; i < cnt; ++i) {
+          const double x = v[d * cnt + i];
+          const float h = (float)x;
+          f[(2 * d) * cnt + i] = h;
+          f[(2 * d + 1) * cnt + i] = (float)(x - (double)h);
+        }
+      return f;
+    };
+    const std::vector<float> sf = split(s3, n), tf = split(t3, m);
+    if (!rc) rc = upload(&P->mem, P->d_srcF, sf.data(), sf.size() * 4);
+    if (!rc) rc = upload(&P->mem, P->d_tgtF, tf.data(), tf.size() * 4);
+    P->kh = (float)P->kern.wavenumber;
+    P->kl = (float)(P->kern.wavenumber - (double)P->kh);
   }
   if (rc) {
     P->d_permS.release(nullptr), P->d_permT.release(nullptr), P->d_offS.release(nullptr);
     P->d_offT.release(nullptr), P->d_src.release(nullptr), P->d_tgt.release(nullptr);
+    P->d_srcF.release(nullptr), P->d_tgtF.release(nullptr);
     delete P;
     return rc;
   }
@@ -672,23 +691,25 @@ int bf_gaussian(uint64_t seed, uint32_t stream_id, int64_t row0, int64_t rows, i
   return launch_gaussian(seed, stream_id, row0, rows, col0, col1, out, ld, dtype, (cudaStream_t)stream);
 }
 
-int bf_error(bf_fact F, bf_operator A, int ncols, uint64_t seed, void* stream, double* err) {
+int bf_error(bf_fact F, bf_operator A, int ncols, uint64_t seed, int dtype, void* stream, double* err) {
   auto* hf = check<bf_fact_s>(F, KIND_FACT);
   auto* ho = check<bf_operator_s>(A, KIND_OP);
   if (!hf || !ho || !err || ncols < 1) return fail(BF_EINVAL, "bad arguments");
+  if (dtype != BF_C64 && dtype != BF_C128) return fail(BF_EINVAL, "bad dtype");
   Fact* f = hf->impl;
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t n = f->n, m = f->m;
+  const size_t es = elem_bytes(dtype);
   DevBuf buf;
-  BF_TRY(buf.alloc(&f->mem, (n + 2 * m) * ncols * 16 + 16, s));
+  BF_TRY(buf.alloc(&f->mem, (n + 2 * m) * ncols * es + 16, s));
   char* W = (char*)buf.p;
-  char* AW = W + n * ncols * 16;
-  char* FW = AW + m * ncols * 16;
-  double* red = (double*)(FW + m * ncols * 16);
-  int rc = launch_gaussian(seed, 5u << 8, 0, n, 0, ncols, W, n, BF_C128, s);
-  if (!rc) rc = ho->impl->apply(BF_OP_N, ncols, W, n, AW, m, BF_C128, s);
-  if (!rc) rc = apply_fact(f, BF_OP_N, ncols, W, n, FW, m, BF_C128, s, false);
-  if (!rc) rc = launch_diff_norms(AW, FW, m, ncols, m, m, BF_C128, red, s);
+  char* AW = W + n * ncols * es;
+  char* FW = AW + m * ncols * es;
+  double* red = (double*)(FW + m * ncols * es);
+  int rc = launch_gaussian(seed, 5u << 8, 0, n, 0, ncols, W, n, dtype, s);
+  if (!rc) rc = ho->impl->apply(BF_OP_N, ncols, W, n, AW, m, dtype, s);
+  if (!rc) rc = apply_fact(f, BF_OP_N, ncols, W, n, FW, m, dtype, s, false);
+  if (!rc) rc = launch_diff_norms(AW, FW, m, ncols, m, m, dtype, red, s);
   double h[2] = {0, 0};
   if (!rc && cudaMemcpyAsync(h, red, 16, cudaMemcpyDeviceToHost, s) != cudaSuccess) rc = fail(BF_ECUDA, "copy");
   if (!rc && cudaStreamSynchronize(s) != cudaSuccess) rc = fail(BF_ECUDA, "sync");
@@ -707,6 +728,7 @@ void bf_free(void* handle) {
     cudaDeviceSynchronize();
     P->d_permS.release(nullptr), P->d_permT.release(nullptr), P->d_offS.release(nullptr);
     P->d_offT.release(nullptr), P->d_src.release(nullptr), P->d_tgt.release(nullptr);
+    P->d_srcF.release(nullptr), P->d_tgtF.release(nullptr);
     delete P;
     h->kind = 0;
     delete h;

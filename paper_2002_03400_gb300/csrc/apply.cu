@@ -75,13 +75,15 @@ void apply_tasks_host(const Fact* F, int opC, int dtype, ApplyPlan& ap, std::vec
   std::vector<std::vector<int64_t>> rowV(lm + 1), rowU(L - lm + 1);
   for (int j = 0; j <= lm; ++j) prefix(F->rV[j], rowV[j]);
   for (int j = lm; j <= L; ++j) prefix(F->rU[j - lm], rowU[j - lm]);
-  auto RV = [&](int j) { return rowV[j][nb]; };
-  auto RU = [&](int j) { return rowU[j - lm][nb]; };
+  // stacked level intermediates are row-major with the launch's column
+  // count: ld = 0 and the offsets below are row indices
+  auto RV = [&](int) { return (int64_t)0; };
+  auto RU = [&](int) { return (int64_t)0; };
   auto rv = [&](int j, int b) { return F->rV[j][b]; };
   auto ru = [&](int j, int b) { return F->rU[j - lm][b]; };
   int64_t rows_max = 0;
-  for (int j = 0; j <= lm; ++j) rows_max = std::max(rows_max, RV(j));
-  for (int j = lm; j <= L; ++j) rows_max = std::max(rows_max, RU(j));
+  for (int j = 0; j <= lm; ++j) rows_max = std::max(rows_max, rowV[j][nb]);
+  for (int j = lm; j <= L; ++j) rows_max = std::max(rows_max, rowU[j - lm][nb]);
   ap.level_rows_max = rows_max;
   const auto& offS = P->offS[L];
   const auto& offT = P->offT[L];

@@ -86,6 +86,8 @@ struct Plan {
   MemTracker mem;
   DevBuf d_permS, d_permT;                    // int64
   DevBuf d_src, d_tgt;                        // double, SoA: x[n], y[n], z[n]
+  DevBuf d_srcF, d_tgtF;                      // float-float SoA: [x_hi, x_lo, y_hi, y_lo, z_hi, z_lo]
+  float kh = 0.f, kl = 0.f;                   // wavenumber as float-float
   DevBuf d_offS, d_offT;                      // int64, all levels concatenated
   std::vector<int64_t> lvl_start;             // level l starts at lvl_start[l] in d_off*
   bool identS = true, identT = true;          // permutation is the identity

@@ -284,12 +284,13 @@ int peel_V(Ctx& c, int l, int k, const void* Y, char* Pbuf, const std::vector<in
             const int k0 = F->rV[j - 1][p0], k1 = F->rV[j - 1][p1];
             const int ldm = F->st[F->stage_W(j)].rows[b];
             const int64_t c0 = (sg & 1) * ncols + colo;
-            term(t, cur, xoff_prev[p0] + c0 * k0, k0, fblk(c, F->stage_W(j), b), ldm, k0, 1);
-            term(t, cur, xoff_prev[p1] + c0 * k1, k1, fblk(c, F->stage_W(j), b, k0), ldm, k1, 1);
+            // level j-1 blocks are row-major with 2*ncols columns
+            term(t, cur, xoff_prev[p0] + c0, -2 * ncols, fblk(c, F->stage_W(j), b), ldm, k0, 1);
+            term(t, cur, xoff_prev[p1] + c0, -2 * ncols, fblk(c, F->stage_W(j), b, k0), ldm, k1, 1);
           }
         };
         if (!fin) {
-          StageTask t = task(outb, xoff[b], M, M, (int)ncols);
+          StageTask t = task(outb, xoff[b], -ncols, M, (int)ncols);
           add_terms(t, 0);
           tasks.push_back(t);
         } else {
@@ -355,12 +356,13 @@ int peel_U(Ctx& c, int l, int k, const void* Z, char* Pbuf, const std::vector<in
             const int k0 = ru(j + 1, c0i), k1 = ru(j + 1, c1i);
             const int ldm = F->st[F->stage_R(j)].rows[b];
             const int64_t cc = (mu & 1) * ncols + colo;
-            term(t, cur, yoff_prev[c0i] + cc * k0, k0, fblk(c, F->stage_R(j), b), ldm, k0, 1);
-            term(t, cur, yoff_prev[c1i] + cc * k1, k1, fblk(c, F->stage_R(j), b, k0), ldm, k1, 1);
+            // level j+1 blocks are row-major with 2*ncols columns
+            term(t, cur, yoff_prev[c0i] + cc, -2 * ncols, fblk(c, F->stage_R(j), b), ldm, k0, 1);
+            term(t, cur, yoff_prev[c1i] + cc, -2 * ncols, fblk(c, F->stage_R(j), b, k0), ldm, k1, 1);
           }
         };
         if (!fin) {
-          StageTask t = task(outb, yoff[b], M, M, (int)ncols);
+          StageTask t = task(outb, yoff[b], -ncols, M, (int)ncols);
           add_terms(t, 0);
           tasks.push_back(t);
         } else {
@@ -413,7 +415,8 @@ int project_X(Ctx& c, int k, const void* Om, char* Xbuf, std::vector<int64_t>& x
       for (int mu = 0; mu < nmu; ++mu) {
         const int b = sg * nmu + mu;
         const int M = F->rV[j][b];
-        StageTask t = task(outb, xo[b], M, M, k);
+        // intermediates row-major; the final X blocks column-major (ld r^V) for the solve
+        StageTask t = task(outb, xo[b], fin ? M : -k, M, k);
         if (j == 0) {
           const int sz = (int)(offS[mu + 1] - offS[mu]);
           term(t, 0, offS[mu], P->n, fblk(c, F->stage_V0(), mu), sz, sz, 1);
@@ -421,8 +424,8 @@ int project_X(Ctx& c, int k, const void* Om, char* Xbuf, std::vector<int64_t>& x
           const int p0 = (sg >> 1) * (2 * nmu) + 2 * mu, p1 = p0 + 1;
           const int k0 = F->rV[j - 1][p0], k1 = F->rV[j - 1][p1];
           const int ldm = F->st[F->stage_W(j)].rows[b];
-          term(t, cur, xprev[p0], k0, fblk(c, F->stage_W(j), b), ldm, k0, 1);
-          term(t, cur, xprev[p1], k1, fblk(c, F->stage_W(j), b, k0), ldm, k1, 1);
+          term(t, cur, xprev[p0], -k, fblk(c, F->stage_W(j), b), ldm, k0, 1);
+          term(t, cur, xprev[p1], -k, fblk(c, F->stage_W(j), b, k0), ldm, k1, 1);
         }
         tasks.push_back(t);
       }

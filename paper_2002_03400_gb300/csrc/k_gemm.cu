@@ -6,22 +6,29 @@
 //   op N: Y[:, g*k + c] = sum_{j in S_g} A[:, j] X[j, c]
 //   op C: Y[:, g*k + c] = sum_{i in T_g} conj(A[i, :]) X[i, c].
 //
-// Complex GEMM on the SIMT pipes: a 64 x 32 output tile per 256-thread CTA,
-// K streamed in chunks of 16 through shared memory, each thread holding 8
-// complex accumulators.  FP64 path: complex128 throughout.  Mixed path:
-// complex64 operands, each 16-term chunk accumulated in FP32 and merged
-// into a (hi, lo) FP32 pair with Knuth's TwoSum, so the long dot products
-// (K up to n) keep ~FP32 accuracy per chunk instead of growing with sqrt(K).
-// Kernel entries: the distance and the phase k*r are formed in FP64 and
-// reduced modulo 2*pi before the trigonometric evaluation, so the phase of
-// an oscillatory kernel with k*r ~ 1e4 stays accurate in both paths.
+// Complex GEMM on the SIMT pipes: a GM x GN output tile per 256-thread CTA,
+// K streamed in chunks of 16 through shared memory.  GN covers the whole
+// sketch width (up to 64 columns) so each kernel entry is formed once per
+// row tile.  FP64 path: complex128 throughout.  Mixed path: complex64
+// operands, each 16-term chunk accumulated in FP32 and merged into a
+// (hi, lo) FP32 pair with Knuth's TwoSum, so the long dot products (K up to
+// n) keep ~FP32 accuracy instead of losing sqrt(K).
+//
+// Kernel entries.  FP64 path: distance, phase k*r and its reduction modulo
+// 2*pi in FP64, then sincos.  Mixed path: no FP64 instruction at all -- the
+// points and k are held as float-float pairs (hi + lo), the distance, k*r
+// and the reduction by a three-part split of 2*pi (Cody & Waite) are
+// carried in float-float (Dekker/Knuth error-free transformations), and the
+// reduced phase theta_hi + theta_lo is evaluated as sincosf(theta_hi)
+// corrected to first order in theta_lo.  The phase of an oscillatory kernel
+// with k*r ~ 1e4 keeps ~1e-9 rad absolute accuracy.
 #include "bf_internal.h"
 #include "cx.cuh"
 
 namespace bf {
 
 namespace {
-constexpr int GM = 64, GN = 32, GK = 16, GT = 256;
+constexpr int GM = 64, GK = 16, GT = 256;
 
 struct PointsSoA {
   const double* x;
@@ -52,6 +59,95 @@ __device__ __forceinline__ double2 kernel_value(int type, double wn, double tx, 
   return make_double2(cs * ir, sn * ir);
 }
 
+// ---- float-float (hi + lo) arithmetic: error-free transformations ----
+struct FF {
+  float h, l;
+};
+__device__ __forceinline__ FF two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ FF fast_two_sum(float a, float b) {   // |a| >= |b|
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ FF two_prod(float a, float b) {
+  const float p = a * b;
+  return {p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ FF ff_sub(float ah, float al, float bh, float bl) {
+  FF d = two_sum(ah, -bh);
+  d.l += al - bl;
+  return fast_two_sum(d.h, d.l);
+}
+__device__ __forceinline__ FF ff_sq(FF a) {
+  FF p = two_prod(a.h, a.h);
+  p.l = fmaf(2.0f * a.h, a.l, p.l);
+  return p;
+}
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  FF s = two_sum(a.h, b.h);
+  s.l += a.l + b.l;
+  return fast_two_sum(s.h, s.l);
+}
+
+// 2*pi = C1 + C2 + C3 (each the float nearest to the remainder)
+#define BF_2PI_1 6.28318548202514648f
+#define BF_2PI_2 -1.74845553146951716e-07f
+#define BF_2PI_3 -6.86049804002352749e-15f
+#define BF_INV_2PI 0.159154943091895336f
+
+struct PointsFF {
+  const float* p;   // [x_hi, x_lo, y_hi, y_lo, z_hi, z_lo] x count
+  int64_t count;
+  __device__ __forceinline__ float c(int d, int64_t i) const { return p[d * count + i]; }
+};
+
+// exp(-i k r)/r or exp(i k r)/(4 pi r) (or the DFT phase) in float-float.
+__device__ __forceinline__ float2 kernel_value_ff(int type, float kh, float kl, const PointsFF& T,
+                                                  int64_t it, const PointsFF& S, int64_t is) {
+  if (type == BF_KERNEL_DFT) {
+    // phase in turns u = t * s with t = t_hi + t_lo, s exact integer
+    FF u = two_prod(T.c(0, it), S.c(0, is));
+    u.l = fmaf(T.c(1, it), S.c(0, is), u.l);
+    const float q = rintf(u.h);
+    FF f = two_sum(u.h - q, u.l);     // u.h - q exact (Sterbenz)
+    float sn, cs;
+    sincospif(-2.0f * f.h, &sn, &cs);
+    const float d = -6.28318531f * f.l;   // first-order correction
+    return make_float2(cs - d * sn, sn + d * cs);
+  }
+  FF r2 = ff_sq(ff_sub(T.c(0, it), T.c(1, it), S.c(0, is), S.c(1, is)));
+  r2 = ff_add(r2, ff_sq(ff_sub(T.c(2, it), T.c(3, it), S.c(2, is), S.c(3, is))));
+  r2 = ff_add(r2, ff_sq(ff_sub(T.c(4, it), T.c(5, it), S.c(4, is), S.c(5, is))));
+  // r = sqrt(r2) with one Newton correction in float-float
+  const float rh0 = sqrtf(r2.h);
+  const FF e = two_prod(rh0, rh0);
+  const float num = ((r2.h - e.h) - e.l) + r2.l;
+  const FF r = fast_two_sum(rh0, num * (0.5f / rh0));
+  // phase k * r
+  FF ph = two_prod(kh, r.h);
+  ph.l = fmaf(kh, r.l, fmaf(kl, r.h, ph.l));
+  ph = fast_two_sum(ph.h, ph.l);
+  // reduction: theta = ph - q * 2 pi, q * C1 subtracted exactly by FMA
+  const float q = rintf(ph.h * BF_INV_2PI);
+  const float t1 = fmaf(-q, BF_2PI_1, ph.h);
+  const FF m2 = two_prod(q, BF_2PI_2);
+  FF th = two_sum(t1, -m2.h);
+  th.l += (ph.l - m2.l) - q * BF_2PI_3;
+  th = fast_two_sum(th.h, th.l);
+  float sn, cs;
+  sincosf(th.h, &sn, &cs);
+  const float s1 = fmaf(th.l, cs, sn), c1 = fmaf(-th.l, sn, cs);
+  if (type == BF_KERNEL_HELMHOLTZ_2D) {
+    const float ir = 1.0f / r.h;
+    return make_float2(c1 * ir, -s1 * ir);
+  }
+  const float ir = 0.0795774715f / r.h;
+  return make_float2(c1 * ir, s1 * ir);
+}
+
 template <typename V>
 struct DenseLoader {
   const V* A;
@@ -66,13 +162,12 @@ struct DenseLoader {
   __device__ __forceinline__ bool k_fastest() const { return op != BF_OP_N; }
 };
 
-template <typename V>
-struct KernelLoader {
+struct KernelLoader64 {
   PointsSoA tgt, src;
   int type;
   double wn;
   int op;
-  __device__ __forceinline__ V get(int64_t r, int64_t kk) const {
+  __device__ __forceinline__ double2 get(int64_t r, int64_t kk) const {
     double2 v;
     if (op == BF_OP_N) {
       v = kernel_value(type, wn, tgt.x[r], tgt.y[r], tgt.z[r], src.x[kk], src.y[kk], src.z[kk]);
@@ -80,51 +175,59 @@ struct KernelLoader {
       v = kernel_value(type, wn, tgt.x[kk], tgt.y[kk], tgt.z[kk], src.x[r], src.y[r], src.z[r]);
       v.y = -v.y;
     }
-    return from_d2<V>(v);
+    return v;
   }
   __device__ __forceinline__ bool k_fastest() const { return false; }
 };
 
-__device__ __forceinline__ void two_sum(float& hi, float& lo, float b) {
-  const float s = hi + b;
-  const float bb = s - hi;
-  const float err = (hi - (s - bb)) + (b - bb);
-  hi = s;
-  lo += err;
-}
+struct KernelLoader32 {
+  PointsFF tgt, src;
+  int type;
+  float kh, kl;
+  int op;
+  __device__ __forceinline__ float2 get(int64_t r, int64_t kk) const {
+    if (op == BF_OP_N) return kernel_value_ff(type, kh, kl, tgt, r, src, kk);
+    float2 v = kernel_value_ff(type, kh, kl, tgt, kk, src, r);
+    v.y = -v.y;
+    return v;
+  }
+  __device__ __forceinline__ bool k_fastest() const { return false; }
+};
 
-template <typename R>
+template <typename R, int Q>
 struct Acc;
-template <>
-struct Acc<double> {
-  double2 v[8];
+template <int Q>
+struct Acc<double, Q> {
+  double2 v[Q];
   __device__ void zero() {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] = make_double2(0.0, 0.0);
+    for (int q = 0; q < Q; ++q) v[q] = make_double2(0.0, 0.0);
   }
   __device__ __forceinline__ double2& chunk(int q) { return v[q]; }
   __device__ __forceinline__ void begin_chunk() {}
   __device__ __forceinline__ void end_chunk() {}
   __device__ __forceinline__ double2 result(int q) const { return v[q]; }
 };
-template <>
-struct Acc<float> {
-  float2 part[8], hi[8], lo[8];
+template <int Q>
+struct Acc<float, Q> {
+  float2 part[Q], hi[Q], lo[Q];
   __device__ void zero() {
 #pragma unroll
-    for (int q = 0; q < 8; ++q)
+    for (int q = 0; q < Q; ++q)
       part[q] = make_float2(0.f, 0.f), hi[q] = make_float2(0.f, 0.f), lo[q] = make_float2(0.f, 0.f);
   }
   __device__ __forceinline__ float2& chunk(int q) { return part[q]; }
   __device__ __forceinline__ void begin_chunk() {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) part[q] = make_float2(0.f, 0.f);
+    for (int q = 0; q < Q; ++q) part[q] = make_float2(0.f, 0.f);
   }
   __device__ __forceinline__ void end_chunk() {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      two_sum(hi[q].x, lo[q].x, part[q].x);
-      two_sum(hi[q].y, lo[q].y, part[q].y);
+    for (int q = 0; q < Q; ++q) {
+      FF a = two_sum(hi[q].x, part[q].x);
+      FF b = two_sum(hi[q].y, part[q].y);
+      hi[q].x = a.h, lo[q].x += a.l;
+      hi[q].y = b.h, lo[q].y += b.l;
     }
   }
   __device__ __forceinline__ float2 result(int q) const {
@@ -133,12 +236,14 @@ struct Acc<float> {
 };
 }  // namespace
 
-template <typename R, class Loader>
+// GN output columns per CTA; each thread owns one row and GN/4 columns.
+template <typename R, int GN, class Loader>
 __global__ void __launch_bounds__(GT)
 sketch_gemm_kernel(Loader ld, int64_t M, const int64_t* __restrict__ goff, int64_t Ktot,
                    int64_t kcols, const typename Cx<R>::V* __restrict__ X, int64_t ldx,
                    typename Cx<R>::V* __restrict__ Y, int64_t ldy) {
   using V = typename Cx<R>::V;
+  constexpr int Q = GN / 4;
   __shared__ V sA[GK][GM + 1];
   __shared__ V sB[GK][GN + 1];
   const int64_t row0 = (int64_t)blockIdx.x * GM;
@@ -147,7 +252,7 @@ sketch_gemm_kernel(Loader ld, int64_t M, const int64_t* __restrict__ goff, int64
   const int64_t klo = goff ? goff[g] : 0;
   const int64_t khi = goff ? goff[g + 1] : Ktot;
   const int tr = threadIdx.x % GM, tc = threadIdx.x / GM;   // tc 0..3
-  Acc<R> acc;
+  Acc<R, Q> acc;
   acc.zero();
   const bool kf = ld.k_fastest();
   for (int64_t k0 = klo; k0 < khi; k0 += GK) {
@@ -182,7 +287,7 @@ sketch_gemm_kernel(Loader ld, int64_t M, const int64_t* __restrict__ goff, int64
     for (int kk = 0; kk < GK; ++kk) {
       const V a = sA[kk][tr];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) cmac(acc.chunk(q), a, sB[kk][tc + 4 * q]);
+      for (int q = 0; q < Q; ++q) cmac(acc.chunk(q), a, sB[kk][tc + 4 * q]);
     }
     acc.end_chunk();
     __syncthreads();
@@ -190,7 +295,7 @@ sketch_gemm_kernel(Loader ld, int64_t M, const int64_t* __restrict__ goff, int64
   const int64_t gi = row0 + tr;
   if (gi < M) {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < Q; ++q) {
       const int c = col0 + tc + 4 * q;
       if (c < kcols) Y[gi + ((int64_t)g * kcols + c) * ldy] = acc.result(q);
     }
@@ -202,10 +307,15 @@ static int run_gemm(const Loader& ld, int64_t M, const GemmGroups& g, int64_t Kt
                     int64_t ldx, void* Y, int64_t ldy, cudaStream_t s) {
   using V = typename Cx<R>::V;
   if (M <= 0 || g.kcols <= 0 || g.groups <= 0) return BF_OK;
+  const int GN = g.kcols > 32 ? 64 : 32;
   dim3 grid((unsigned)((M + GM - 1) / GM), (unsigned)((g.kcols + GN - 1) / GN), (unsigned)g.groups);
   if (grid.y > 65535 || grid.z > 65535) return fail(BF_EINVAL, "sketch grid too large");
-  sketch_gemm_kernel<R, Loader><<<grid, GT, 0, s>>>(ld, M, g.d_off, Ktot, g.kcols, (const V*)X, ldx,
-                                                    (V*)Y, ldy);
+  if (GN == 64)
+    sketch_gemm_kernel<R, 64, Loader><<<grid, GT, 0, s>>>(ld, M, g.d_off, Ktot, g.kcols, (const V*)X, ldx,
+                                                          (V*)Y, ldy);
+  else
+    sketch_gemm_kernel<R, 32, Loader><<<grid, GT, 0, s>>>(ld, M, g.d_off, Ktot, g.kcols, (const V*)X, ldx,
+                                                          (V*)Y, ldy);
   BF_CUDA_TRY(cudaGetLastError());
   return BF_OK;
 }
@@ -224,17 +334,19 @@ int launch_dense_gemm(int op, const void* A, int64_t lda, int64_t m, int64_t n, 
 
 int launch_kernel_gemm(const Plan* P, int op, const GemmGroups& g, const void* X, int64_t ldx,
                        void* Y, int64_t ldy, int dtype, cudaStream_t s) {
-  const double* src = (const double*)P->d_src.p;
-  const double* tgt = (const double*)P->d_tgt.p;
-  PointsSoA ps{src, src + P->n, src + 2 * P->n};
-  PointsSoA pt{tgt, tgt + P->m, tgt + 2 * P->m};
   const int64_t M = op == BF_OP_N ? P->m : P->n;
   const int64_t K = op == BF_OP_N ? P->n : P->m;
   if (dtype == BF_C128) {
-    KernelLoader<double2> ld{pt, ps, P->kern.type, P->kern.wavenumber, op};
+    const double* src = (const double*)P->d_src.p;
+    const double* tgt = (const double*)P->d_tgt.p;
+    PointsSoA ps{src, src + P->n, src + 2 * P->n};
+    PointsSoA pt{tgt, tgt + P->m, tgt + 2 * P->m};
+    KernelLoader64 ld{pt, ps, P->kern.type, P->kern.wavenumber, op};
     return run_gemm<double>(ld, M, g, K, X, ldx, Y, ldy, s);
   }
-  KernelLoader<float2> ld{pt, ps, P->kern.type, P->kern.wavenumber, op};
+  PointsFF ps{(const float*)P->d_srcF.p, P->n};
+  PointsFF pt{(const float*)P->d_tgtF.p, P->m};
+  KernelLoader32 ld{pt, ps, P->kern.type, P->kh, P->kl, op};
   return run_gemm<float>(ld, M, g, K, X, ldx, Y, ldy, s);
 }
 
