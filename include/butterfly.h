@@ -174,6 +174,16 @@ int bf_operator_counts(bf_operator A, int64_t* cols_N, int64_t* cols_T);
  * Errors: BF_ENOTCONVERGED, BF_ECALLBACK, BF_ENOMEM, BF_ECUDA. */
 int bf_factor(bf_plan plan, bf_operator A, void* stream, bf_fact* out);
 
+/* Alg. 2 for `count` operators at once, level-synchronously: every phase
+ * (leaf passes, each W^l and R^l level, the B solve) runs one launch per
+ * kernel covering all blocks of all operators, whatever their size, depth
+ * and ranks.  plans[i] (all of one precision) with ops[i] (ops may be NULL
+ * or hold NULL entries: the plan's kernel operator).  out: count handles,
+ * each identical to what bf_factor would return for that entry; on error all
+ * are NULL.  Synchronizes once per phase. */
+int bf_factor_batch(int count, const bf_plan* plans, const bf_operator* ops,
+                    void* stream, bf_fact* out);
+
 /* y = F x (eq. hybrid_butterfly_mat).  x: n x nrhs, y: m x nrhs, device,
  * user order, dtype BF_C64 or BF_C128 (computed in that precision). */
 int bf_apply(bf_fact F, int64_t nrhs, const void* x, int64_t ldx, void* y,

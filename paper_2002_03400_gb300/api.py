@@ -69,6 +69,7 @@ def lib():
         "bf_operator_apply": (i32, [vp, i32, i64, vp, i64, vp, i64, i32, vp]),
         "bf_operator_counts": (i32, [vp, C.POINTER(i64), C.POINTER(i64)]),
         "bf_factor": (i32, [vp, vp, vp, C.POINTER(vp)]),
+        "bf_factor_batch": (i32, [i32, C.POINTER(vp), C.POINTER(vp), vp, C.POINTER(vp)]),
         "bf_apply": (i32, [vp, i64, vp, i64, vp, i64, i32, vp]),
         "bf_apply_T": (i32, [vp, i32, i64, vp, i64, vp, i64, i32, vp]),
         "bf_apply_noalloc": (i32, [vp, i32, i64, vp, i64, vp, i64, i32, vp]),
@@ -92,7 +93,8 @@ def exported_symbols():
     """Names declared in include/butterfly.h that the binding expects."""
     return ["bf_options_default", "bf_last_error", "bf_bisect", "bf_plan_create", "bf_plan_info", "bf_plan_trees",
             "bf_operator_dense", "bf_operator_kernel", "bf_operator_factored", "bf_operator_composed",
-            "bf_operator_callback", "bf_operator_apply", "bf_operator_counts", "bf_factor", "bf_apply",
+            "bf_operator_callback", "bf_operator_apply", "bf_operator_counts", "bf_factor",
+            "bf_factor_batch", "bf_apply",
             "bf_apply_T", "bf_apply_noalloc", "bf_ranks", "bf_fact_info", "bf_fact_import", "bf_fact_export", "bf_error",
             "bf_free", "bf_gaussian"]
 
@@ -274,6 +276,24 @@ class Factorization(_Handle):
         F = cls(h, plan)
         F._op = A
         return F
+
+    @classmethod
+    def factor_batch(cls, plans: list, ops: list | None = None, stream=None) -> list:
+        """bf_factor_batch: all operators level-synchronously, one launch per
+        kernel per phase."""
+        cnt = len(plans)
+        ph = (C.c_void_p * cnt)(*[p._h.value for p in plans])
+        oh = None
+        if ops is not None:
+            oh = (C.c_void_p * cnt)(*[(o._h.value if o is not None else None) for o in ops])
+        out = (C.c_void_p * cnt)()
+        check(lib().bf_factor_batch(cnt, ph, oh, _stream(stream), out))
+        res = []
+        for i in range(cnt):
+            F = cls(C.c_void_p(out[i]), plans[i])
+            F._op = ops[i] if ops is not None else None
+            res.append(F)
+        return res
 
     @classmethod
     def import_blocks(cls, plan: Plan, rV: np.ndarray, rU: np.ndarray, stages: list):

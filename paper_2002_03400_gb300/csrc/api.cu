@@ -119,6 +119,15 @@ struct PlanOp : Operator {
   virtual int struct_impl(int op, int groups, const int64_t* d_off, int64_t k, const void* Om,
                           int64_t ldo, void* Y, int64_t ldy, int dtype, cudaStream_t s) = 0;
   bool has_structured() const override { return true; }
+  // this operator's structured product as a batched-launch job (no launch)
+  virtual bool make_job(int op, const GemmGroups& g, const void* X, int64_t ldx, void* Y, int64_t ldy,
+                        int dtype, SketchJob* job) = 0;
+  bool sketch_job(int op, int groups, const int64_t* d_off, int64_t k, const void* Om, int64_t ldo,
+                  void* Y, int64_t ldy, int dtype, SketchJob* job) override {
+    if (!make_job(op, GemmGroups{groups, d_off, k}, Om, ldo, Y, ldy, dtype, job)) return false;
+    (op == BF_OP_N ? cols_N : cols_T) += groups * k;
+    return true;
+  }
   int apply_tree(int op, int64_t ncols, const void* X, int64_t ldx, void* Y, int64_t ldy, int dtype,
                  cudaStream_t s) override {
     (op == BF_OP_N ? cols_N : cols_T) += ncols;
@@ -156,6 +165,12 @@ struct DenseOp : PlanOp {
   DevBuf A;   // tree order, m x n, ld m, dtype dt
   int dt = BF_C128;
   ~DenseOp() override { A.release(nullptr); }
+  bool make_job(int op, const GemmGroups& g, const void* X, int64_t ldx, void* Y, int64_t ldy, int dtype,
+                SketchJob* job) override {
+    if (dtype != dt) return false;
+    *job = dense_job(op, A.p, m, m, n, g, X, ldx, Y, ldy);
+    return true;
+  }
   int run(int op, const GemmGroups& g, const void* X, int64_t ldx, void* Y, int64_t ldy, int dtype,
           cudaStream_t s) {
     if (dtype == dt) return launch_dense_gemm(op, A.p, m, m, n, g, X, ldx, Y, ldy, dtype, s);
@@ -187,6 +202,11 @@ struct DenseOp : PlanOp {
 };
 
 struct KernelOp : PlanOp {
+  bool make_job(int op, const GemmGroups& g, const void* X, int64_t ldx, void* Y, int64_t ldy, int dtype,
+                SketchJob* job) override {
+    *job = kernel_job(plan, op, g, X, ldx, Y, ldy);
+    return true;
+  }
   int tree_impl(int op, int64_t ncols, const void* X, int64_t ldx, void* Y, int64_t ldy, int dtype,
                 cudaStream_t s) override {
     GemmGroups g{1, nullptr, ncols};
@@ -546,6 +566,41 @@ int bf_factor(bf_plan plan, bf_operator A, void* stream, bf_fact* out) {
   if (tmp) bf_free(tmp);
   if (rc) return rc;
   *out = new bf_fact_s{KIND_FACT, F};
+  return BF_OK;
+}
+
+int bf_factor_batch(int count, const bf_plan* plans, const bf_operator* ops, void* stream, bf_fact* out) {
+  if (!out || !plans || count < 1) return fail(BF_EINVAL, "bad batch arguments");
+  for (int i = 0; i < count; ++i) out[i] = nullptr;
+  std::vector<Plan*> P(count);
+  std::vector<Operator*> A(count);
+  std::vector<bf_operator> tmp;
+  int rc = BF_OK;
+  for (int i = 0; i < count && !rc; ++i) {
+    auto* hp = check<bf_plan_s>(plans[i], KIND_PLAN);
+    if (!hp) {
+      rc = fail(BF_EINVAL, "batch entry " + std::to_string(i) + " is not a plan");
+      break;
+    }
+    P[i] = hp->impl;
+    if (ops && ops[i]) {
+      auto* ho = check<bf_operator_s>(ops[i], KIND_OP);
+      if (!ho) {
+        rc = fail(BF_EINVAL, "batch entry " + std::to_string(i) + " is not an operator");
+        break;
+      }
+      A[i] = ho->impl;
+    } else {
+      bf_operator t = nullptr;
+      rc = bf_operator_kernel(plans[i], &t);
+      if (!rc) tmp.push_back(t), A[i] = t->impl;
+    }
+  }
+  std::vector<Fact*> F(count, nullptr);
+  if (!rc) rc = factor_batch(count, P.data(), A.data(), (cudaStream_t)stream, F.data());
+  for (auto t : tmp) bf_free(t);
+  if (rc) return rc;
+  for (int i = 0; i < count; ++i) out[i] = new bf_fact_s{KIND_FACT, F[i]};
   return BF_OK;
 }
 

@@ -53,6 +53,7 @@ enum HandleKind : uint32_t { KIND_PLAN = 0xB0F1A001u, KIND_FACT = 0xB0F1A002u, K
 struct Plan;
 struct Fact;
 struct Operator;
+struct SketchJob;
 
 }  // namespace bf
 
@@ -116,6 +117,13 @@ struct Operator {
   //   op N: Y[:, g*k:(g+1)*k] = A[:, rows_g] Om[rows_g, :]
   //   op C: Y[:, g*k:(g+1)*k] = A[rows_g, :]^H Om[rows_g, :]
   virtual bool has_structured() const { return false; }
+  // Describes the structured product as a SketchJob for a batched launch
+  // (plan-bound operators whose stored dtype matches); counts its columns.
+  // Returns false when the operator cannot run batched.
+  virtual bool sketch_job(int op, int groups, const int64_t* d_off, int64_t k, const void* Om,
+                          int64_t ldo, void* Y, int64_t ldy, int dtype, SketchJob* job) {
+    return false;
+  }
   virtual int apply_structured(int op, int groups, const int64_t* d_off,
                                int64_t k, const void* Om, int64_t ldo, void* Y,
                                int64_t ldy, int dtype, cudaStream_t s) {
@@ -205,12 +213,12 @@ struct QRTask {
   int32_t s, k;
   int32_t cap;        // columns available in q (>= min(s,k))
   int32_t pad;
+  double eps;         // truncation tolerance of this block's factorization
 };
 // Truncated column-pivoted Householder QR (Alg. 1 step 3); ranks[i] out.
 // in dtype: C64 or C128 (QR always in FP64); q is complex128.
-int launch_qr(const QRTask* d_tasks, int ntasks, int maxS, int maxK, double eps,
-              int in_dtype, int32_t* d_ranks, void* d_work, size_t work_bytes,
-              cudaStream_t s);
+int launch_qr(const QRTask* d_tasks, int ntasks, int maxS, int maxK, int in_dtype,
+              int32_t* d_ranks, void* d_work, size_t work_bytes, cudaStream_t s);
 size_t qr_workspace_bytes(int ntasks, int maxS, int maxK);
 
 // ------------------------------------------------------------ B solve ----
@@ -230,9 +238,42 @@ int launch_gaussian(uint64_t seed, uint32_t stream_id, int64_t row0, int64_t row
                     int64_t col0, int64_t col1, void* out, int64_t ld, int dtype,
                     cudaStream_t s);
 
-// Complex GEMM variants for the built-in operators (tree order).
-//   mode 0: dense stored A (M x K source, lda), A entries read
-//   mode 1: kernel entries formed from points
+// One built-in operator's sketch product (tree order), a unit of a batched
+// launch: for each group g (node of the input-side tree, rows
+// [off[g], off[g+1]) or all rows when d_off is null)
+//   op N: Y[:, g*kcols + c] = sum_{j in rows_g} A[:, j] X[j, c]     (M = m)
+//   op C: Y[:, g*kcols + c] = sum_{i in rows_g} conj(A[i, :]) X[i, c] (M = n)
+// with A a dense stored tree-order matrix (kind 0) or kernel entries formed
+// from the plan's points (kind 1).
+struct SketchJob {
+  int32_t kind, op, ktype, groups;
+  int64_t M, Ktot, kcols;
+  const int64_t* d_off;
+  const void* A;
+  int64_t lda;
+  const double* tgt;      // FP64 points, [x | y | z] blocks of length m
+  const double* src;      //                                          n
+  const float* tgtF;      // float-float points, 6 blocks of length m
+  const float* srcF;      //                                        n
+  int64_t m, n;
+  double wn;
+  float kh, kl;
+  const void* X;
+  int64_t ldx;
+  void* Y;
+  int64_t ldy;
+};
+// Runs all jobs (same dtype) in one launch: one CTA per (job, group, row tile,
+// column tile).  Job and tile lists are uploaded to stream-ordered scratch.
+int launch_sketch_jobs(const std::vector<SketchJob>& jobs, int dtype, MemTracker* mt,
+                       cudaStream_t s);
+struct GemmGroups;
+SketchJob dense_job(int op, const void* A, int64_t lda, int64_t m, int64_t n, const GemmGroups& g,
+                    const void* X, int64_t ldx, void* Y, int64_t ldy);
+SketchJob kernel_job(const Plan* P, int op, const GemmGroups& g, const void* X, int64_t ldx, void* Y,
+                     int64_t ldy);
+
+// Complex GEMM variants for the built-in operators (tree order), one job each.
 // op N: Y[m x N] = A[:, k-range] * X ; op C: Y[n x N] = A[k-range rows,:]^H X
 struct GemmGroups {
   int groups;             // >= 1
@@ -280,5 +321,8 @@ void apply_tasks_host(const Fact* F, int opC, int dtype, ApplyPlan& ap, std::vec
 int apply_fact(Fact* F, int op, int64_t nrhs, const void* x, int64_t ldx,
                void* y, int64_t ldy, int dtype, cudaStream_t s, bool tree_order);
 int factor(Plan* P, Operator* A, cudaStream_t s, Fact** out);
+// Alg. 2 for `count` operators in lockstep (one launch per kernel per phase
+// across all of them); all plans must share one precision.
+int factor_batch(int count, Plan* const* P, Operator* const* A, cudaStream_t s, Fact** out);
 
 }  // namespace bf

@@ -1,11 +1,21 @@
 // Alg. 2 -- adaptive randomized hybrid butterfly factorization -- as a host
-// scheduler over the device kernels.  Per level: draw the compact random
-// matrix (counter-based generator), one black-box product for all blocks of
-// the level (structured sketch, Sec. 4.1), peel the recovered factors along
-// the ancestor paths (one stage launch per tree level), batched truncated
-// pivoted QR (Alg. 1 step 3) and, at l_m, X = V^H Omega and the B least
-// squares (eq. Bij).  Ranks return to the host once per level to size the
-// next sketch (its width is max(r1 + r2) + p over the level's blocks).
+// scheduler over the device kernels, for a batch of operators in lockstep.
+//
+// Phases (each one launch per kernel for every operator of the batch):
+//   V^0 leaf loop (Alg. 2 loop "V"), U^L leaf loop (loop "U"): draw the new
+//     random columns, one black-box sketch, batched truncated QR per leaf,
+//     ranks to the host, double r where not converged;
+//   W^l, l = 1, 2, ...: structured sketch Y = A^H Gamma-bar of level l (Sec.
+//     4.1), peeling of V^0, W^1..W^(l-1) along the ancestor paths (one stage
+//     launch per tree level), batched QR -> W^l (Sec. 4.3);
+//   R^l, l = L-1, L-2, ...: structured sketch Z = A Omega-bar, peeling of
+//     U^L, R^(L-1)..R^(l+1), batched QR -> R^l (Sec. 4.2); at the centre
+//     level l_m also X = V^H Omega and the B least squares (eq. Bij).
+// Operators with different tree depths take part in the phases that exist
+// for them (W step t runs level t where t <= l_m; R step t runs level L - t
+// where L - t >= l_m).  Per-phase buffers of all operators live in shared
+// arenas so that one task list addresses every operator.  Ranks come back to
+// the host once per phase to size the next sketch (width max(r1 + r2) + p).
 //
 // Readings (shared with the oracle): r restarts at r0 for each leaf loop;
 // each leaf pass appends r new random columns; a leaf loop also stops once
@@ -13,6 +23,7 @@
 // width also covers max r^V + p; B = (U^H K Omega)(V^H Omega)^+.
 #include <algorithm>
 #include <chrono>
+#include <memory>
 
 #include "bf_internal.h"
 
@@ -23,40 +34,50 @@ namespace {
 enum { STAGE_V0 = 1, STAGE_U0 = 2, STAGE_W = 3, STAGE_R = 4 };
 inline uint32_t sid(int stage, int level) { return (uint32_t)((stage << 8) | level); }
 
-struct Ctx {
-  Plan* P;
-  Operator* A;
-  Fact* F;
-  cudaStream_t s;
-  int dt;
-  size_t es;
-};
-
-// RAII scratch (stream-ordered)
+// RAII stream-ordered scratch
 struct Scratch {
   DevBuf b;
   cudaStream_t s;
   explicit Scratch(cudaStream_t st) : s(st) {}
+  Scratch(const Scratch&) = delete;
   ~Scratch() { b.release(s); }
-  int alloc(MemTracker* mt, size_t bytes) { return b.alloc(mt, bytes, s); }
+  int alloc(MemTracker* mt, size_t bytes) { return b.alloc(mt, bytes ? bytes : 16, s); }
   char* p() const { return (char*)b.p; }
 };
 
-int upload_tasks(Ctx& c, const std::vector<StageTask>& tasks, Scratch& buf) {
-  BF_TRY(buf.alloc(&c.F->mem, std::max<size_t>(1, tasks.size()) * sizeof(StageTask)));
-  BF_CUDA_TRY(cudaMemcpyAsync(buf.p(), tasks.data(), tasks.size() * sizeof(StageTask),
-                              cudaMemcpyHostToDevice, c.s));
-  return BF_OK;
-}
+struct OpState {
+  Plan* P;
+  Operator* A;
+  Fact* F;
+  int L, lm, nb;
+  // leaf loops
+  int r = 0, k = 0;
+  int64_t kcap = 0;
+  bool done = false;
+  DevBuf Y;
+  std::vector<int32_t> ranks;
+  // level phases
+  int l = 0;
+  std::vector<int32_t> Ps;
+  std::vector<int64_t> Poff;
+  int64_t goff = 0, yoff = 0, poff = 0, soff = 0, xoff = 0;   // element offsets into arenas
+  std::vector<int64_t> prev, cur;                              // peel block offsets
+  int in_base = -1;
+};
 
-int run_tasks(Ctx& c, const std::vector<StageTask>& tasks, const StageBases& bases) {
-  if (tasks.empty()) return BF_OK;
-  Scratch d(c.s);
-  BF_TRY(upload_tasks(c, tasks, d));
-  int mM = 0, mN = 0;
-  for (const auto& t : tasks) mM = std::max(mM, t.M), mN = std::max(mN, t.N);
-  return launch_stage((const StageTask*)d.p(), (int)tasks.size(), mM, mN, 0, bases, c.dt, c.s);
-}
+struct Batch {
+  std::vector<OpState> ops;
+  cudaStream_t s;
+  int dt;
+  size_t es;
+  MemTracker mem;   // shared arenas
+
+  const void* fblk(OpState& o, int stage, int b, int row = 0) const {
+    const Stage& S = o.F->st[stage];
+    const char* base = (const char*)(dt == BF_C128 ? S.d64.p : S.d32.p);
+    return base + (S.off[b] + row) * (int64_t)es;
+  }
+};
 
 StageTask task(int out_base, int64_t out_off, int64_t ldo, int M, int N) {
   StageTask t{};
@@ -79,44 +100,76 @@ void term(StageTask& t, int in_base, int64_t in_off, int64_t ldi, const void* ma
   T.conjT = (int16_t)conjT;
 }
 
-// factor block in the sketch dtype
-const void* fblk(Ctx& c, int stage, int b, int row = 0) {
-  const Stage& S = c.F->st[stage];
-  const char* base = (const char*)(c.dt == BF_C128 ? S.d64.p : S.d32.p);
-  return base + (S.off[b] + row) * (int64_t)c.es;
+int run_tasks(Batch& B, const std::vector<StageTask>& tasks, const StageBases& bases) {
+  if (tasks.empty()) return BF_OK;
+  Scratch d(B.s);
+  BF_TRY(d.alloc(&B.mem, tasks.size() * sizeof(StageTask)));
+  BF_CUDA_TRY(cudaMemcpyAsync(d.p(), tasks.data(), tasks.size() * sizeof(StageTask),
+                              cudaMemcpyHostToDevice, B.s));
+  int mM = 0, mN = 0;
+  for (const auto& t : tasks) mM = std::max(mM, t.M), mN = std::max(mN, t.N);
+  return launch_stage((const StageTask*)d.p(), (int)tasks.size(), mM, mN, 0, bases, B.dt, B.s);
 }
 
-// Sketch of Sec. 4.1: Y = op(A) Omega-bar with Omega-bar the block-diagonal
-// expansion over the nodes at `level` of the input-side tree of the compact
-// random matrix Om (input rows x k).  Tree order in and out.
-int sketch(Ctx& c, int op, int level, int64_t k, const void* Om, void* Y) {
-  Plan* P = c.P;
-  Operator* A = c.A;
-  const bool opN = op == BF_OP_N;
-  const int groups = 1 << level;
+// One structured sketch request (Sec. 4.1): Y = op(A) Omega-bar for the
+// block-diagonal expansion over the nodes at `level` of the input-side tree
+// of the compact random matrix Om (input rows x k).  Tree order.
+struct SketchReq {
+  OpState* o;
+  int op, level;
+  int64_t k;
+  const void* Om;
+  void* Y;
+};
+
+// Products that cannot run batched (user callbacks, factored or composed
+// operators, dtype mismatch): expand Omega-bar and call the black box.
+int sketch_one(Batch& B, const SketchReq& q) {
+  Plan* P = q.o->P;
+  Operator* A = q.o->A;
+  const bool opN = q.op == BF_OP_N;
+  const int groups = 1 << q.level;
   const int64_t in_rows = opN ? P->n : P->m, out_rows = opN ? P->m : P->n;
-  const int64_t* d_off = opN ? P->offS_dev(level) : P->offT_dev(level);
-  const int64_t ncols = groups * k;
+  const int64_t* d_off = opN ? P->offS_dev(q.level) : P->offT_dev(q.level);
+  const int64_t ncols = groups * q.k;
   if (A->plan == P && A->has_structured())
-    return A->apply_structured(op, groups, d_off, k, Om, in_rows, Y, out_rows, c.dt, c.s);
-  Scratch ex(c.s);
-  BF_TRY(ex.alloc(&c.F->mem, in_rows * ncols * c.es));
-  BF_TRY(launch_expand_structured(groups, d_off, in_rows, k, Om, in_rows, ex.p(), in_rows, c.dt, c.s));
-  if (A->plan == P) return A->apply_tree(op, ncols, ex.p(), in_rows, Y, out_rows, c.dt, c.s);
-  // user-order black box
-  Scratch u(c.s);
-  BF_TRY(u.alloc(&c.F->mem, (in_rows + out_rows) * ncols * c.es));
+    return A->apply_structured(q.op, groups, d_off, q.k, q.Om, in_rows, q.Y, out_rows, B.dt, B.s);
+  Scratch ex(B.s);
+  BF_TRY(ex.alloc(&q.o->F->mem, in_rows * ncols * B.es));
+  BF_TRY(launch_expand_structured(groups, d_off, in_rows, q.k, q.Om, in_rows, ex.p(), in_rows, B.dt, B.s));
+  if (A->plan == P) return A->apply_tree(q.op, ncols, ex.p(), in_rows, q.Y, out_rows, B.dt, B.s);
+  Scratch u(B.s);
+  BF_TRY(u.alloc(&q.o->F->mem, (in_rows + out_rows) * ncols * B.es));
   char* ui = u.p();
-  char* uo = u.p() + in_rows * ncols * c.es;
+  char* uo = u.p() + in_rows * ncols * B.es;
   const int64_t* pin = (const int64_t*)(opN ? P->d_permS.p : P->d_permT.p);
   const int64_t* pout = (const int64_t*)(opN ? P->d_permT.p : P->d_permS.p);
-  BF_TRY(launch_scatter_rows(pin, in_rows, ncols, ex.p(), in_rows, ui, in_rows, 0, c.dt, c.s));
-  BF_TRY(A->apply(op, ncols, ui, in_rows, uo, out_rows, c.dt, c.s));
-  return launch_gather_rows(pout, out_rows, ncols, uo, out_rows, Y, out_rows, 0, c.dt, c.s);
+  BF_TRY(launch_scatter_rows(pin, in_rows, ncols, ex.p(), in_rows, ui, in_rows, 0, B.dt, B.s));
+  BF_TRY(A->apply(q.op, ncols, ui, in_rows, uo, out_rows, B.dt, B.s));
+  return launch_gather_rows(pout, out_rows, ncols, uo, out_rows, q.Y, out_rows, 0, B.dt, B.s);
+}
+
+// All requests of a phase: built-in operators in one batched launch, the
+// rest one by one.
+int sketch_all(Batch& B, const std::vector<SketchReq>& reqs) {
+  std::vector<SketchJob> jobs;
+  for (const auto& q : reqs) {
+    Plan* P = q.o->P;
+    const bool opN = q.op == BF_OP_N;
+    const int groups = 1 << q.level;
+    const int64_t in_rows = opN ? P->n : P->m, out_rows = opN ? P->m : P->n;
+    const int64_t* d_off = opN ? P->offS_dev(q.level) : P->offT_dev(q.level);
+    SketchJob j{};
+    if (q.o->A->plan == P && q.o->A->sketch_job(q.op, groups, d_off, q.k, q.Om, in_rows, q.Y, out_rows, B.dt, &j))
+      jobs.push_back(j);
+    else
+      BF_TRY(sketch_one(B, q));
+  }
+  return launch_sketch_jobs(jobs, B.dt, &B.mem, B.s);
 }
 
 // Lays out a stage: rows[b] x cap[b] blocks, allocates complex128 storage.
-int layout_stage(Ctx& c, Stage& S, const std::vector<int32_t>& rows, const std::vector<int32_t>& cap) {
+int layout_stage(OpState& o, Stage& S, const std::vector<int32_t>& rows, const std::vector<int32_t>& cap) {
   S.d64.release(nullptr);
   S.d32.release(nullptr);
   S.have32 = false;
@@ -130,456 +183,557 @@ int layout_stage(Ctx& c, Stage& S, const std::vector<int32_t>& rows, const std::
     tot += (int64_t)rows[b] * cap[b];
   }
   S.total = tot;
-  return S.d64.alloc(&c.F->mem, std::max<int64_t>(tot, 1) * 16, nullptr);
+  return S.d64.alloc(&o.F->mem, std::max<int64_t>(tot, 1) * 16, nullptr);
 }
 
-int make32(Ctx& c, Stage& S) {
-  if (c.dt != BF_C64) return BF_OK;
-  BF_TRY(S.d32.alloc(&c.F->mem, std::max<int64_t>(S.total, 1) * 8, nullptr));
-  BF_TRY(launch_convert(S.d64.p, S.d32.p, S.total, BF_C128, BF_C64, c.s));
+int make32(Batch& B, OpState& o, Stage& S) {
+  if (B.dt != BF_C64) return BF_OK;
+  BF_TRY(S.d32.alloc(&o.F->mem, std::max<int64_t>(S.total, 1) * 8, nullptr));
+  BF_TRY(launch_convert(S.d64.p, S.d32.p, S.total, BF_C128, BF_C64, B.s));
   S.have32 = true;
   return BF_OK;
 }
 
-// Batched truncated QR of blocks in[b] (rows[b] x k, ld ldin[b]) into stage S.
-int qr_into(Ctx& c, Stage& S, const std::vector<const void*>& in, const std::vector<int64_t>& ldin,
-            int k, std::vector<int32_t>& ranks) {
-  const int nb = (int)S.rows.size();
-  std::vector<QRTask> tasks(nb);
-  int maxS = 1;
-  for (int b = 0; b < nb; ++b) {
-    QRTask& t = tasks[b];
-    t.in = in[b];
-    t.ldi = ldin[b];
-    t.s = S.rows[b];
-    t.k = k;
-    t.cap = std::min(S.rows[b], k);
-    t.q = (char*)S.d64.p + S.off[b] * 16;
-    maxS = std::max(maxS, S.rows[b]);
-  }
-  const size_t wbytes = qr_workspace_bytes(nb, maxS, k);
-  Scratch d(c.s), w(c.s);
-  BF_TRY(d.alloc(&c.F->mem, nb * sizeof(QRTask) + nb * sizeof(int32_t)));
-  BF_CUDA_TRY(cudaMemcpyAsync(d.p(), tasks.data(), nb * sizeof(QRTask), cudaMemcpyHostToDevice, c.s));
-  int32_t* d_r = (int32_t*)(d.p() + nb * sizeof(QRTask));
-  if (wbytes) BF_TRY(w.alloc(&c.F->mem, wbytes));
-  BF_TRY(launch_qr((const QRTask*)d.p(), nb, maxS, k, c.P->tol, c.dt, d_r, w.p(), wbytes, c.s));
-  ranks.assign(nb, 0);
-  BF_CUDA_TRY(cudaMemcpyAsync(ranks.data(), d_r, nb * sizeof(int32_t), cudaMemcpyDeviceToHost, c.s));
-  BF_CUDA_TRY(cudaStreamSynchronize(c.s));
-  S.cols = ranks;
-  return make32(c, S);
-}
-
-// Adaptive leaf loop (Alg. 2 loops "V" and "U").  Vside: Y = A^H Gamma_t,
-// leaves of T_S; else Z = A Omega_s, leaves of T_T.
-int leaf_loop(Ctx& c, bool Vside) {
-  Plan* P = c.P;
-  Fact* F = c.F;
-  const int L = P->L, nb = 1 << L;
-  const int op = Vside ? BF_OP_C : BF_OP_N;
-  const int64_t in_rows = Vside ? P->m : P->n, out_rows = Vside ? P->n : P->m;
-  const auto& off = Vside ? P->offS[L] : P->offT[L];
-  Stage& S = F->st[Vside ? F->stage_V0() : F->stage_U()];
-  const uint32_t id = sid(Vside ? STAGE_V0 : STAGE_U0, 0);
-  int maxleaf = 0;
-  std::vector<int32_t> rows(nb);
-  for (int b = 0; b < nb; ++b) rows[b] = (int32_t)(off[b + 1] - off[b]), maxleaf = std::max(maxleaf, rows[b]);
-  int r = P->opt.r0;
-  int64_t kcap = 0;
-  DevBuf Y;
-  int rc = BF_OK;
-  std::vector<int32_t> ranks;
-  int k = 0;
-  for (;;) {
-    k = r + P->opt.p;
-    if (k > kcap) {
-      DevBuf Yn;
-      rc = Yn.alloc(&F->mem, out_rows * k * c.es, c.s);
-      if (rc) break;
-      if (kcap > 0) {
-        cudaError_t e = cudaMemcpyAsync(Yn.p, Y.p, out_rows * kcap * c.es, cudaMemcpyDeviceToDevice, c.s);
-        if (e != cudaSuccess) {
-          Yn.release(c.s);
-          rc = fail(BF_ECUDA, cudaGetErrorString(e));
-          break;
-        }
-      }
-      {
-        Scratch G(c.s);
-        rc = G.alloc(&F->mem, in_rows * (k - kcap) * c.es);
-        if (!rc) rc = launch_gaussian(P->opt.seed, id, 0, in_rows, kcap, k, G.p(), in_rows, c.dt, c.s);
-        if (!rc) rc = sketch(c, op, 0, k - kcap, G.p(), (char*)Yn.p + out_rows * kcap * c.es);
-      }
-      Y.release(c.s);
-      Y = Yn;
-      kcap = k;
-      if (rc) break;
+// One batched truncated QR over blocks of several operators.
+struct QRJob {
+  OpState* o;
+  Stage* S;
+  std::vector<const void*> in;
+  std::vector<int64_t> ld;
+  int k;
+  std::vector<int32_t>* ranks;
+};
+int qr_all(Batch& B, std::vector<QRJob>& jobs) {
+  std::vector<QRTask> tasks;
+  int maxS = 1, maxK = 1;
+  for (auto& J : jobs) {
+    const int nb = (int)J.S->rows.size();
+    for (int b = 0; b < nb; ++b) {
+      QRTask t{};
+      t.in = J.in[b];
+      t.ldi = J.ld[b];
+      t.s = J.S->rows[b];
+      t.k = J.k;
+      t.cap = std::min(J.S->rows[b], J.k);
+      t.q = (char*)J.S->d64.p + J.S->off[b] * 16;
+      t.eps = J.o->P->tol;
+      tasks.push_back(t);
+      maxS = std::max(maxS, t.s);
     }
-    std::vector<int32_t> cap(nb);
-    for (int b = 0; b < nb; ++b) cap[b] = std::min(rows[b], k);
-    rc = layout_stage(c, S, rows, cap);
-    if (rc) break;
-    std::vector<const void*> in(nb);
-    std::vector<int64_t> ld(nb, out_rows);
-    for (int b = 0; b < nb; ++b) in[b] = (const char*)Y.p + off[b] * c.es;
-    rc = qr_into(c, S, in, ld, k, ranks);
-    if (rc) break;
-    const int maxr = *std::max_element(ranks.begin(), ranks.end());
-    if (r > maxr || k >= maxleaf) break;
-    r *= 2;
-    if (r > P->opt.r_max) {
-      rc = fail(BF_ENOTCONVERGED, "adaptive leaf rank exceeds r_max");
-      break;
-    }
+    maxK = std::max(maxK, J.k);
   }
-  Y.release(c.s);
-  if (rc) return rc;
-  if (Vside)
-    F->rV[0] = ranks;
-  else
-    F->rU[L - F->lm] = ranks;
+  if (tasks.empty()) return BF_OK;
+  const int nt = (int)tasks.size();
+  const size_t wbytes = qr_workspace_bytes(nt, maxS, maxK);
+  Scratch d(B.s), w(B.s);
+  BF_TRY(d.alloc(&B.mem, nt * sizeof(QRTask) + nt * sizeof(int32_t)));
+  BF_CUDA_TRY(cudaMemcpyAsync(d.p(), tasks.data(), nt * sizeof(QRTask), cudaMemcpyHostToDevice, B.s));
+  int32_t* d_r = (int32_t*)(d.p() + nt * sizeof(QRTask));
+  if (wbytes) BF_TRY(w.alloc(&B.mem, wbytes));
+  BF_TRY(launch_qr((const QRTask*)d.p(), nt, maxS, maxK, B.dt, d_r, w.p(), wbytes, B.s));
+  std::vector<int32_t> h(nt);
+  BF_CUDA_TRY(cudaMemcpyAsync(h.data(), d_r, nt * sizeof(int32_t), cudaMemcpyDeviceToHost, B.s));
+  BF_CUDA_TRY(cudaStreamSynchronize(B.s));
+  size_t q = 0;
+  for (auto& J : jobs) {
+    const size_t nb = J.S->rows.size();
+    J.ranks->assign(h.begin() + q, h.begin() + q + nb);
+    J.S->cols = *J.ranks;
+    q += nb;
+    BF_TRY(make32(B, *J.o, *J.S));
+  }
   return BF_OK;
 }
 
-// Peels V_{p tau, nu'}^H off the W-side sketch Y (n x 2^l k) into the QR
-// inputs P_{tau,nu} = [V_{p tau,2nu}^H Y_tau(S_2nu); V_{p tau,2nu+1}^H Y_tau(S_2nu+1)].
-int peel_V(Ctx& c, int l, int k, const void* Y, char* Pbuf, const std::vector<int64_t>& Poff,
-           const std::vector<int32_t>& Ps) {
-  Plan* P = c.P;
-  Fact* F = c.F;
-  const int L = P->L, nb = 1 << L, nn = 1 << (L - l);
-  const auto& offS = P->offS[L];
-  Scratch bufA(c.s), bufB(c.s);
-  std::vector<int64_t> xoff_prev, xoff(nb + 1);
-  int cur = -1;
-  size_t maxbytes = 0;
-  for (int j = 0; j < l - 1; ++j) {
-    int64_t tot = 0;
-    for (int b = 0; b < nb; ++b) tot += (int64_t)F->rV[j][b] * ((int64_t)k << (l - j));
-    maxbytes = std::max(maxbytes, (size_t)tot * c.es);
+// Adaptive leaf loops (Alg. 2 loops "V" and "U") for all operators.  Vside:
+// Y = A^H Gamma_t, leaves of T_S; else Z = A Omega_s, leaves of T_T.
+int leaf_phase(Batch& B, bool Vside) {
+  for (auto& o : B.ops) {
+    o.r = o.P->opt.r0;
+    o.kcap = 0;
+    o.done = false;
   }
-  if (maxbytes) {
-    BF_TRY(bufA.alloc(&F->mem, maxbytes));
-    BF_TRY(bufB.alloc(&F->mem, maxbytes));
+  int rc = BF_OK;
+  for (;;) {
+    std::vector<OpState*> act;
+    for (auto& o : B.ops)
+      if (!o.done) act.push_back(&o);
+    if (act.empty()) break;
+    {
+      std::vector<SketchReq> reqs;
+      std::vector<std::unique_ptr<Scratch>> G;
+      for (OpState* o : act) {
+        Plan* P = o->P;
+        const int64_t in_rows = Vside ? P->m : P->n, out_rows = Vside ? P->n : P->m;
+        o->k = o->r + P->opt.p;
+        if (o->k <= o->kcap) continue;
+        DevBuf Yn;
+        BF_TRY(Yn.alloc(&o->F->mem, out_rows * o->k * B.es, B.s));
+        if (o->kcap > 0)
+          BF_CUDA_TRY(cudaMemcpyAsync(Yn.p, o->Y.p, out_rows * o->kcap * B.es, cudaMemcpyDeviceToDevice, B.s));
+        o->Y.release(B.s);
+        o->Y = Yn;
+        G.emplace_back(new Scratch(B.s));
+        BF_TRY(G.back()->alloc(&o->F->mem, in_rows * (o->k - o->kcap) * B.es));
+        BF_TRY(launch_gaussian(P->opt.seed, sid(Vside ? STAGE_V0 : STAGE_U0, 0), 0, in_rows, o->kcap, o->k,
+                               G.back()->p(), in_rows, B.dt, B.s));
+        reqs.push_back({o, Vside ? BF_OP_C : BF_OP_N, 0, o->k - o->kcap, G.back()->p(),
+                        (char*)o->Y.p + out_rows * o->kcap * B.es});
+        o->kcap = o->k;
+      }
+      BF_TRY(sketch_all(B, reqs));
+    }
+    std::vector<QRJob> jobs;
+    for (OpState* o : act) {
+      Plan* P = o->P;
+      const int L = P->L, nb = 1 << L;
+      const int64_t out_rows = Vside ? P->n : P->m;
+      const auto& off = Vside ? P->offS[L] : P->offT[L];
+      Stage& S = o->F->st[Vside ? o->F->stage_V0() : o->F->stage_U()];
+      std::vector<int32_t> rows(nb), cap(nb);
+      for (int b = 0; b < nb; ++b) rows[b] = (int32_t)(off[b + 1] - off[b]), cap[b] = std::min(rows[b], o->k);
+      BF_TRY(layout_stage(*o, S, rows, cap));
+      QRJob J{o, &S, std::vector<const void*>(nb), std::vector<int64_t>(nb, out_rows), o->k, &o->ranks};
+      for (int b = 0; b < nb; ++b) J.in[b] = (const char*)o->Y.p + off[b] * B.es;
+      jobs.push_back(std::move(J));
+    }
+    BF_TRY(qr_all(B, jobs));
+    for (OpState* o : act) {
+      Plan* P = o->P;
+      const int L = P->L, nb = 1 << L;
+      const auto& off = Vside ? P->offS[L] : P->offT[L];
+      int maxleaf = 0;
+      for (int b = 0; b < nb; ++b) maxleaf = std::max<int>(maxleaf, (int)(off[b + 1] - off[b]));
+      const int maxr = *std::max_element(o->ranks.begin(), o->ranks.end());
+      if (o->r > maxr || o->k >= maxleaf) {
+        o->done = true;
+        o->Y.release(B.s);
+        if (Vside)
+          o->F->rV[0] = o->ranks;
+        else
+          o->F->rU[o->L - o->lm] = o->ranks;
+        continue;
+      }
+      o->r *= 2;
+      if (o->r > P->opt.r_max) rc = fail(BF_ENOTCONVERGED, "adaptive leaf rank exceeds r_max");
+    }
+    if (rc) return rc;
   }
+  return BF_OK;
+}
+
+// W^l for every operator with l_m >= t (l = t).
+int w_phase(Batch& B, int t) {
+  std::vector<OpState*> act;
+  for (auto& o : B.ops)
+    if (o.lm >= t) act.push_back(&o);
+  if (act.empty()) return BF_OK;
+  const int l = t;
+  int64_t gtot = 0, ytot = 0, ptot = 0, stot = 0;
+  for (OpState* o : act) {
+    Plan* P = o->P;
+    const int L = o->L, nb = o->nb, nt = 1 << l, nn = 1 << (L - l);
+    const auto& prev = o->F->rV[l - 1];
+    o->l = l;
+    o->Ps.assign(nb, 0);
+    int k = 0;
+    for (int tau = 0; tau < nt; ++tau)
+      for (int nu = 0; nu < nn; ++nu) {
+        const int base = (tau >> 1) * (2 * nn);
+        o->Ps[tau * nn + nu] = prev[base + 2 * nu] + prev[base + 2 * nu + 1];
+        k = std::max(k, o->Ps[tau * nn + nu]);
+      }
+    o->k = k + P->opt.p;
+    o->Poff.assign(nb + 1, 0);
+    for (int b = 0; b < nb; ++b) o->Poff[b + 1] = o->Poff[b] + (int64_t)o->Ps[b] * o->k;
+    o->goff = gtot, gtot += P->m * (int64_t)o->k;
+    o->yoff = ytot, ytot += P->n * (int64_t)nt * o->k;
+    o->poff = ptot, ptot += o->Poff[nb];
+    int64_t mx = 0;   // largest non-final peel level of this operator
+    for (int j = 0; j < l - 1; ++j) {
+      int64_t tot = 0;
+      for (int b = 0; b < nb; ++b) tot += (int64_t)o->F->rV[j][b] * ((int64_t)o->k << (l - j));
+      mx = std::max(mx, tot);
+    }
+    o->soff = stot, stot += mx;
+  }
+  Scratch G(B.s), Y(B.s), Pb(B.s), SA(B.s), SB(B.s);
+  BF_TRY(G.alloc(&B.mem, gtot * B.es));
+  BF_TRY(Y.alloc(&B.mem, ytot * B.es));
+  BF_TRY(Pb.alloc(&B.mem, ptot * B.es));
+  BF_TRY(SA.alloc(&B.mem, stot * B.es));
+  BF_TRY(SB.alloc(&B.mem, stot * B.es));
+  std::vector<SketchReq> reqs;
+  for (OpState* o : act) {
+    BF_TRY(launch_gaussian(o->P->opt.seed, sid(STAGE_W, l), 0, o->P->m, 0, o->k, G.p() + o->goff * B.es, o->P->m,
+                           B.dt, B.s));
+    reqs.push_back({o, BF_OP_C, l, o->k, G.p() + o->goff * B.es, Y.p() + o->yoff * B.es});
+  }
+  BF_TRY(sketch_all(B, reqs));
+
+  // peel V_{p tau, nu'}^H off Y into P_{tau,nu} = [V^H Y_tau(S_2nu); V^H Y_tau(S_2nu+1)]
+  for (OpState* o : act) o->in_base = 0;
   for (int j = 0; j < l; ++j) {
-    const int64_t ncols = (int64_t)k << (l - j);
     const bool fin = (j == l - 1);
-    const int outb = fin ? 3 : (cur == 1 ? 2 : 1);
-    const int nmu = 1 << (L - j);
-    xoff[0] = 0;
-    for (int b = 0; b < nb; ++b) xoff[b + 1] = xoff[b] + (int64_t)F->rV[j][b] * ncols;
     std::vector<StageTask> tasks;
-    for (int sg = 0; sg < (1 << j); ++sg)
-      for (int mu = 0; mu < nmu; ++mu) {
-        const int b = sg * nmu + mu;
-        const int M = F->rV[j][b];
-        auto add_terms = [&](StageTask& t, int64_t colo) {
+    for (OpState* o : act) {
+      Plan* P = o->P;
+      Fact* F = o->F;
+      const int L = o->L, nb = o->nb, nn = 1 << (L - l);
+      const int64_t ncols = (int64_t)o->k << (l - j);
+      const int outb = fin ? 3 : (o->in_base == 1 ? 2 : 1);
+      const int nmu = 1 << (L - j);
+      const auto& offS = P->offS[L];
+      o->cur.assign(nb + 1, 0);
+      for (int b = 0; b < nb; ++b) o->cur[b + 1] = o->cur[b] + (int64_t)F->rV[j][b] * ncols;
+      for (int sg = 0; sg < (1 << j); ++sg)
+        for (int mu = 0; mu < nmu; ++mu) {
+          const int b = sg * nmu + mu;
+          const int M = F->rV[j][b];
+          auto add_terms = [&](StageTask& tk, int64_t colo) {
+            if (j == 0) {
+              const int sz = (int)(offS[mu + 1] - offS[mu]);
+              term(tk, 0, o->yoff + offS[mu] + colo * P->n, P->n, B.fblk(*o, F->stage_V0(), mu), sz, sz, 1);
+            } else {
+              // level j-1 blocks are row-major with 2*ncols columns
+              const int p0 = (sg >> 1) * (2 * nmu) + 2 * mu, p1 = p0 + 1;
+              const int k0 = F->rV[j - 1][p0], k1 = F->rV[j - 1][p1];
+              const int ldm = F->st[F->stage_W(j)].rows[b];
+              const int64_t c0 = (sg & 1) * ncols + colo;
+              term(tk, o->in_base, o->soff + o->prev[p0] + c0, -2 * ncols, B.fblk(*o, F->stage_W(j), b), ldm, k0, 1);
+              term(tk, o->in_base, o->soff + o->prev[p1] + c0, -2 * ncols, B.fblk(*o, F->stage_W(j), b, k0), ldm,
+                   k1, 1);
+            }
+          };
+          if (!fin) {
+            StageTask tk = task(outb, o->soff + o->cur[b], -ncols, M, (int)ncols);
+            add_terms(tk, 0);
+            tasks.push_back(tk);
+          } else {
+            const int nu = mu >> 1;
+            const int rowoff = (mu & 1) ? F->rV[l - 1][sg * (2 * nn) + (mu & ~1)] : 0;
+            for (int a = 0; a < 2; ++a) {
+              const int bp = (2 * sg + a) * nn + nu;
+              StageTask tk = task(3, o->poff + o->Poff[bp] + rowoff, o->Ps[bp], M, o->k);
+              add_terms(tk, (int64_t)a * o->k);
+              tasks.push_back(tk);
+            }
+          }
+        }
+      o->prev.swap(o->cur);
+      o->in_base = outb;
+    }
+    StageBases bases{{Y.p(), SA.p(), SB.p(), Pb.p()}};
+    BF_TRY(run_tasks(B, tasks, bases));
+  }
+  std::vector<QRJob> jobs;
+  for (OpState* o : act) {
+    Stage& S = o->F->st[o->F->stage_W(l)];
+    std::vector<int32_t> cap(o->nb);
+    for (int b = 0; b < o->nb; ++b) cap[b] = std::min(o->Ps[b], o->k);
+    BF_TRY(layout_stage(*o, S, o->Ps, cap));
+    QRJob J{o, &S, std::vector<const void*>(o->nb), std::vector<int64_t>(o->nb), o->k, &o->F->rV[l]};
+    for (int b = 0; b < o->nb; ++b) J.in[b] = Pb.p() + (o->poff + o->Poff[b]) * B.es, J.ld[b] = o->Ps[b];
+    jobs.push_back(std::move(J));
+  }
+  return qr_all(B, jobs);
+}
+
+// R^l for every operator with L - t >= l_m (l = L - t); X and B at l_m.
+int r_phase(Batch& B, int t) {
+  std::vector<OpState*> act;
+  for (auto& o : B.ops)
+    if (o.L - t >= o.lm) act.push_back(&o);
+  if (act.empty()) return BF_OK;
+  int64_t gtot = 0, ztot = 0, ptot = 0, stot = 0;
+  for (OpState* o : act) {
+    Plan* P = o->P;
+    const int L = o->L, lm = o->lm, nb = o->nb, l = L - t, nt = 1 << l, nn = 1 << (L - l), nn1 = nn >> 1;
+    const auto& nxt = o->F->rU[l + 1 - lm];
+    o->l = l;
+    o->Ps.assign(nb, 0);
+    int k = 0;
+    for (int tau = 0; tau < nt; ++tau)
+      for (int nu = 0; nu < nn; ++nu) {
+        o->Ps[tau * nn + nu] = nxt[(2 * tau) * nn1 + (nu >> 1)] + nxt[(2 * tau + 1) * nn1 + (nu >> 1)];
+        k = std::max(k, o->Ps[tau * nn + nu]);
+      }
+    if (l == lm) k = std::max(k, *std::max_element(o->F->rV[lm].begin(), o->F->rV[lm].end()));
+    o->k = k + P->opt.p;
+    o->Poff.assign(nb + 1, 0);
+    for (int b = 0; b < nb; ++b) o->Poff[b + 1] = o->Poff[b] + (int64_t)o->Ps[b] * o->k;
+    o->goff = gtot, gtot += P->n * (int64_t)o->k;
+    o->yoff = ztot, ztot += P->m * (int64_t)nn * o->k;
+    o->poff = ptot, ptot += o->Poff[nb];
+    int64_t mx = 0;
+    for (int j = L; j > l + 1; --j) {
+      int64_t tot = 0;
+      for (int b = 0; b < nb; ++b) tot += (int64_t)o->F->rU[j - lm][b] * ((int64_t)o->k << (j - l));
+      mx = std::max(mx, tot);
+    }
+    if (l == lm)   // project_X intermediates (k columns per block)
+      for (int j = 0; j < lm; ++j) {
+        int64_t tot = 0;
+        for (int b = 0; b < nb; ++b) tot += (int64_t)o->F->rV[j][b] * o->k;
+        mx = std::max(mx, tot);
+      }
+    o->soff = stot, stot += mx;
+  }
+  Scratch G(B.s), Z(B.s), Pb(B.s), SA(B.s), SB(B.s);
+  BF_TRY(G.alloc(&B.mem, gtot * B.es));
+  BF_TRY(Z.alloc(&B.mem, ztot * B.es));
+  BF_TRY(Pb.alloc(&B.mem, ptot * B.es));
+  BF_TRY(SA.alloc(&B.mem, stot * B.es));
+  BF_TRY(SB.alloc(&B.mem, stot * B.es));
+  std::vector<SketchReq> reqs;
+  for (OpState* o : act) {
+    BF_TRY(launch_gaussian(o->P->opt.seed, sid(STAGE_R, o->l), 0, o->P->n, 0, o->k, G.p() + o->goff * B.es,
+                           o->P->n, B.dt, B.s));
+    reqs.push_back({o, BF_OP_N, o->L - o->l, o->k, G.p() + o->goff * B.es, Z.p() + o->yoff * B.es});
+  }
+  BF_TRY(sketch_all(B, reqs));
+
+  // peel U_{tau', p nu}^H off Z into P_{tau,nu} = [U^H Z_nu(T_2tau); U^H Z_nu(T_2tau+1)]
+  for (OpState* o : act) o->in_base = 0;
+  for (int st = 0; st < t; ++st) {
+    std::vector<StageTask> tasks;
+    for (OpState* o : act) {
+      Plan* P = o->P;
+      Fact* F = o->F;
+      const int L = o->L, lm = o->lm, nb = o->nb, l = o->l, nn = 1 << (L - l);
+      const int j = L - st;
+      const bool fin = (j == l + 1);
+      auto ru = [&](int jj, int b) { return F->rU[jj - lm][b]; };
+      const int64_t ncols = (int64_t)o->k << (j - l);
+      const int outb = fin ? 3 : (o->in_base == 1 ? 2 : 1);
+      const int nmu = 1 << (L - j);
+      const auto& offT = P->offT[L];
+      o->cur.assign(nb + 1, 0);
+      for (int b = 0; b < nb; ++b) o->cur[b + 1] = o->cur[b] + (int64_t)ru(j, b) * ncols;
+      for (int sg = 0; sg < (1 << j); ++sg)
+        for (int mu = 0; mu < nmu; ++mu) {
+          const int b = sg * nmu + mu;
+          const int M = ru(j, b);
+          auto add_terms = [&](StageTask& tk, int64_t colo) {
+            if (j == L) {
+              const int sz = (int)(offT[sg + 1] - offT[sg]);
+              term(tk, 0, o->yoff + offT[sg] + colo * P->m, P->m, B.fblk(*o, F->stage_U(), sg), sz, sz, 1);
+            } else {
+              // level j+1 blocks are row-major with 2*ncols columns
+              const int nm1 = nmu >> 1;
+              const int c0i = (2 * sg) * nm1 + (mu >> 1), c1i = (2 * sg + 1) * nm1 + (mu >> 1);
+              const int k0 = ru(j + 1, c0i), k1 = ru(j + 1, c1i);
+              const int ldm = F->st[F->stage_R(j)].rows[b];
+              const int64_t cc = (mu & 1) * ncols + colo;
+              term(tk, o->in_base, o->soff + o->prev[c0i] + cc, -2 * ncols, B.fblk(*o, F->stage_R(j), b), ldm, k0, 1);
+              term(tk, o->in_base, o->soff + o->prev[c1i] + cc, -2 * ncols, B.fblk(*o, F->stage_R(j), b, k0), ldm,
+                   k1, 1);
+            }
+          };
+          if (!fin) {
+            StageTask tk = task(outb, o->soff + o->cur[b], -ncols, M, (int)ncols);
+            add_terms(tk, 0);
+            tasks.push_back(tk);
+          } else {
+            const int tau = sg >> 1;
+            const int rowoff = (sg & 1) ? ru(l + 1, (sg & ~1) * nmu + mu) : 0;
+            for (int cc = 0; cc < 2; ++cc) {
+              const int bp = tau * nn + 2 * mu + cc;
+              StageTask tk = task(3, o->poff + o->Poff[bp] + rowoff, o->Ps[bp], M, o->k);
+              add_terms(tk, (int64_t)cc * o->k);
+              tasks.push_back(tk);
+            }
+          }
+        }
+      o->prev.swap(o->cur);
+      o->in_base = outb;
+    }
+    StageBases bases{{Z.p(), SA.p(), SB.p(), Pb.p()}};
+    BF_TRY(run_tasks(B, tasks, bases));
+  }
+  std::vector<QRJob> jobs;
+  for (OpState* o : act) {
+    Stage& S = o->F->st[o->F->stage_R(o->l)];
+    std::vector<int32_t> cap(o->nb);
+    for (int b = 0; b < o->nb; ++b) cap[b] = std::min(o->Ps[b], o->k);
+    BF_TRY(layout_stage(*o, S, o->Ps, cap));
+    QRJob J{o, &S, std::vector<const void*>(o->nb), std::vector<int64_t>(o->nb), o->k, &o->F->rU[o->l - o->lm]};
+    for (int b = 0; b < o->nb; ++b) J.in[b] = Pb.p() + (o->poff + o->Poff[b]) * B.es, J.ld[b] = o->Ps[b];
+    jobs.push_back(std::move(J));
+  }
+  BF_TRY(qr_all(B, jobs));
+
+  // centre level: X_{tau,nu} = V_{tau,nu}^H Omega_nu through V^0, W^1..W^(l_m)
+  std::vector<OpState*> ctr;
+  for (OpState* o : act)
+    if (o->l == o->lm) ctr.push_back(o);
+  if (ctr.empty()) return BF_OK;
+  int64_t xtot = 0, jmax = 0;
+  for (OpState* o : ctr) {
+    int64_t x = 0;
+    for (int b = 0; b < o->nb; ++b) x += (int64_t)o->F->rV[o->lm][b] * o->k;
+    o->xoff = xtot, xtot += x;
+    jmax = std::max<int64_t>(jmax, o->lm);
+    o->in_base = 0;
+  }
+  Scratch Xb(B.s);
+  BF_TRY(Xb.alloc(&B.mem, xtot * B.es));
+  for (int j = 0; j <= jmax; ++j) {
+    std::vector<StageTask> tasks;
+    for (OpState* o : ctr) {
+      if (j > o->lm) continue;
+      Plan* P = o->P;
+      Fact* F = o->F;
+      const int L = o->L, nb = o->nb, k = o->k;
+      const bool fin = j == o->lm;
+      const int outb = fin ? 3 : (o->in_base == 1 ? 2 : 1);
+      const int nmu = 1 << (L - j);
+      const auto& offS = P->offS[L];
+      o->cur.assign(nb + 1, 0);
+      for (int b = 0; b < nb; ++b) o->cur[b + 1] = o->cur[b] + (int64_t)F->rV[j][b] * k;
+      const int64_t obase = fin ? o->xoff : o->soff;
+      for (int sg = 0; sg < (1 << j); ++sg)
+        for (int mu = 0; mu < nmu; ++mu) {
+          const int b = sg * nmu + mu;
+          const int M = F->rV[j][b];
+          // intermediates row-major; the final X blocks column-major (ld r^V) for the solve
+          StageTask tk = task(outb, obase + o->cur[b], fin ? M : -k, M, k);
           if (j == 0) {
             const int sz = (int)(offS[mu + 1] - offS[mu]);
-            term(t, 0, offS[mu] + colo * P->n, P->n, fblk(c, F->stage_V0(), mu), sz, sz, 1);
+            term(tk, 0, o->goff + offS[mu], P->n, B.fblk(*o, F->stage_V0(), mu), sz, sz, 1);
           } else {
             const int p0 = (sg >> 1) * (2 * nmu) + 2 * mu, p1 = p0 + 1;
             const int k0 = F->rV[j - 1][p0], k1 = F->rV[j - 1][p1];
             const int ldm = F->st[F->stage_W(j)].rows[b];
-            const int64_t c0 = (sg & 1) * ncols + colo;
-            // level j-1 blocks are row-major with 2*ncols columns
-            term(t, cur, xoff_prev[p0] + c0, -2 * ncols, fblk(c, F->stage_W(j), b), ldm, k0, 1);
-            term(t, cur, xoff_prev[p1] + c0, -2 * ncols, fblk(c, F->stage_W(j), b, k0), ldm, k1, 1);
+            term(tk, o->in_base, o->soff + o->prev[p0], -k, B.fblk(*o, F->stage_W(j), b), ldm, k0, 1);
+            term(tk, o->in_base, o->soff + o->prev[p1], -k, B.fblk(*o, F->stage_W(j), b, k0), ldm, k1, 1);
           }
-        };
-        if (!fin) {
-          StageTask t = task(outb, xoff[b], -ncols, M, (int)ncols);
-          add_terms(t, 0);
-          tasks.push_back(t);
-        } else {
-          const int nu = mu >> 1;
-          const int rowoff = (mu & 1) ? F->rV[l - 1][sg * (2 * nn) + (mu & ~1)] : 0;
-          for (int a = 0; a < 2; ++a) {
-            const int bp = (2 * sg + a) * nn + nu;
-            StageTask t = task(3, Poff[bp] + rowoff, Ps[bp], M, k);
-            add_terms(t, (int64_t)a * k);
-            tasks.push_back(t);
-          }
+          tasks.push_back(tk);
         }
-      }
-    StageBases bases{{const_cast<void*>(Y), bufA.p(), bufB.p(), Pbuf}};
-    BF_TRY(run_tasks(c, tasks, bases));
-    xoff_prev = xoff;
-    cur = outb;
-  }
-  return BF_OK;
-}
-
-// Peels U_{tau', p nu}^H off the R-side sketch Z (m x 2^(L-l) k) into
-// P_{tau,nu} = [U_{2tau,p nu}^H Z_nu(T_2tau); U_{2tau+1,p nu}^H Z_nu(T_2tau+1)].
-int peel_U(Ctx& c, int l, int k, const void* Z, char* Pbuf, const std::vector<int64_t>& Poff,
-           const std::vector<int32_t>& Ps) {
-  Plan* P = c.P;
-  Fact* F = c.F;
-  const int L = P->L, lm = F->lm, nb = 1 << L, nn = 1 << (L - l);
-  const auto& offT = P->offT[L];
-  auto ru = [&](int j, int b) { return F->rU[j - lm][b]; };
-  Scratch bufA(c.s), bufB(c.s);
-  std::vector<int64_t> yoff_prev, yoff(nb + 1);
-  int cur = -1;
-  size_t maxbytes = 0;
-  for (int j = L; j > l + 1; --j) {
-    int64_t tot = 0;
-    for (int b = 0; b < nb; ++b) tot += (int64_t)ru(j, b) * ((int64_t)k << (j - l));
-    maxbytes = std::max(maxbytes, (size_t)tot * c.es);
-  }
-  if (maxbytes) {
-    BF_TRY(bufA.alloc(&F->mem, maxbytes));
-    BF_TRY(bufB.alloc(&F->mem, maxbytes));
-  }
-  for (int j = L; j >= l + 1; --j) {
-    const int64_t ncols = (int64_t)k << (j - l);
-    const bool fin = (j == l + 1);
-    const int outb = fin ? 3 : (cur == 1 ? 2 : 1);
-    const int nmu = 1 << (L - j);
-    yoff[0] = 0;
-    for (int b = 0; b < nb; ++b) yoff[b + 1] = yoff[b] + (int64_t)ru(j, b) * ncols;
-    std::vector<StageTask> tasks;
-    for (int sg = 0; sg < (1 << j); ++sg)
-      for (int mu = 0; mu < nmu; ++mu) {
-        const int b = sg * nmu + mu;
-        const int M = ru(j, b);
-        auto add_terms = [&](StageTask& t, int64_t colo) {
-          if (j == L) {
-            const int sz = (int)(offT[sg + 1] - offT[sg]);
-            term(t, 0, offT[sg] + colo * P->m, P->m, fblk(c, F->stage_U(), sg), sz, sz, 1);
-          } else {
-            const int nm1 = nmu >> 1;
-            const int c0i = (2 * sg) * nm1 + (mu >> 1), c1i = (2 * sg + 1) * nm1 + (mu >> 1);
-            const int k0 = ru(j + 1, c0i), k1 = ru(j + 1, c1i);
-            const int ldm = F->st[F->stage_R(j)].rows[b];
-            const int64_t cc = (mu & 1) * ncols + colo;
-            // level j+1 blocks are row-major with 2*ncols columns
-            term(t, cur, yoff_prev[c0i] + cc, -2 * ncols, fblk(c, F->stage_R(j), b), ldm, k0, 1);
-            term(t, cur, yoff_prev[c1i] + cc, -2 * ncols, fblk(c, F->stage_R(j), b, k0), ldm, k1, 1);
-          }
-        };
-        if (!fin) {
-          StageTask t = task(outb, yoff[b], -ncols, M, (int)ncols);
-          add_terms(t, 0);
-          tasks.push_back(t);
-        } else {
-          const int tau = sg >> 1;
-          const int rowoff = (sg & 1) ? ru(l + 1, (sg & ~1) * nmu + mu) : 0;
-          for (int cc = 0; cc < 2; ++cc) {
-            const int bp = tau * nn + 2 * mu + cc;
-            StageTask t = task(3, Poff[bp] + rowoff, Ps[bp], M, k);
-            add_terms(t, (int64_t)cc * k);
-            tasks.push_back(t);
-          }
-        }
-      }
-    StageBases bases{{const_cast<void*>(Z), bufA.p(), bufB.p(), Pbuf}};
-    BF_TRY(run_tasks(c, tasks, bases));
-    yoff_prev = yoff;
-    cur = outb;
-  }
-  return BF_OK;
-}
-
-// X_{tau,nu} = V_{tau,nu}^H Omega_nu at level l_m for every block, through
-// V^0, W^1 .. W^(l_m) with the block-diagonal input (k columns per block).
-int project_X(Ctx& c, int k, const void* Om, char* Xbuf, std::vector<int64_t>& xfin) {
-  Plan* P = c.P;
-  Fact* F = c.F;
-  const int L = P->L, lm = F->lm, nb = 1 << L;
-  const auto& offS = P->offS[L];
-  Scratch bufA(c.s), bufB(c.s);
-  size_t maxbytes = 0;
-  for (int j = 0; j < lm; ++j) {
-    int64_t tot = 0;
-    for (int b = 0; b < nb; ++b) tot += (int64_t)F->rV[j][b] * k;
-    maxbytes = std::max(maxbytes, (size_t)tot * c.es);
-  }
-  if (maxbytes) {
-    BF_TRY(bufA.alloc(&F->mem, maxbytes));
-    BF_TRY(bufB.alloc(&F->mem, maxbytes));
-  }
-  std::vector<int64_t> xprev, xo(nb + 1);
-  int cur = -1;
-  for (int j = 0; j <= lm; ++j) {
-    const bool fin = j == lm;
-    const int outb = fin ? 3 : (cur == 1 ? 2 : 1);
-    const int nmu = 1 << (L - j);
-    xo[0] = 0;
-    for (int b = 0; b < nb; ++b) xo[b + 1] = xo[b] + (int64_t)F->rV[j][b] * k;
-    std::vector<StageTask> tasks;
-    for (int sg = 0; sg < (1 << j); ++sg)
-      for (int mu = 0; mu < nmu; ++mu) {
-        const int b = sg * nmu + mu;
-        const int M = F->rV[j][b];
-        // intermediates row-major; the final X blocks column-major (ld r^V) for the solve
-        StageTask t = task(outb, xo[b], fin ? M : -k, M, k);
-        if (j == 0) {
-          const int sz = (int)(offS[mu + 1] - offS[mu]);
-          term(t, 0, offS[mu], P->n, fblk(c, F->stage_V0(), mu), sz, sz, 1);
-        } else {
-          const int p0 = (sg >> 1) * (2 * nmu) + 2 * mu, p1 = p0 + 1;
-          const int k0 = F->rV[j - 1][p0], k1 = F->rV[j - 1][p1];
-          const int ldm = F->st[F->stage_W(j)].rows[b];
-          term(t, cur, xprev[p0], -k, fblk(c, F->stage_W(j), b), ldm, k0, 1);
-          term(t, cur, xprev[p1], -k, fblk(c, F->stage_W(j), b, k0), ldm, k1, 1);
-        }
-        tasks.push_back(t);
-      }
-    StageBases bases{{const_cast<void*>(Om), bufA.p(), bufB.p(), Xbuf}};
-    BF_TRY(run_tasks(c, tasks, bases));
-    xprev = xo;
-    cur = outb;
-  }
-  xfin = xprev;
-  return BF_OK;
-}
-
-int w_level(Ctx& c, int l) {
-  Plan* P = c.P;
-  Fact* F = c.F;
-  const int L = P->L, nb = 1 << L, nt = 1 << l, nn = 1 << (L - l);
-  const auto& prev = F->rV[l - 1];
-  std::vector<int32_t> Ps(nb);
-  int k = 0;
-  for (int tau = 0; tau < nt; ++tau)
-    for (int nu = 0; nu < nn; ++nu) {
-      const int base = (tau >> 1) * (2 * nn);
-      Ps[tau * nn + nu] = prev[base + 2 * nu] + prev[base + 2 * nu + 1];
-      k = std::max(k, Ps[tau * nn + nu]);
+      o->prev.swap(o->cur);
+      o->in_base = outb;
     }
-  k += P->opt.p;
-  std::vector<int64_t> Poff(nb + 1, 0);
-  for (int b = 0; b < nb; ++b) Poff[b + 1] = Poff[b] + (int64_t)Ps[b] * k;
-  Scratch G(c.s), Y(c.s), Pb(c.s);
-  BF_TRY(G.alloc(&F->mem, P->m * (int64_t)k * c.es));
-  BF_TRY(launch_gaussian(P->opt.seed, sid(STAGE_W, l), 0, P->m, 0, k, G.p(), P->m, c.dt, c.s));
-  BF_TRY(Y.alloc(&F->mem, P->n * (int64_t)nt * k * c.es));
-  BF_TRY(sketch(c, BF_OP_C, l, k, G.p(), Y.p()));
-  BF_TRY(Pb.alloc(&F->mem, Poff[nb] * c.es));
-  BF_TRY(peel_V(c, l, k, Y.p(), Pb.p(), Poff, Ps));
-  Stage& S = F->st[F->stage_W(l)];
-  std::vector<int32_t> cap(nb);
-  for (int b = 0; b < nb; ++b) cap[b] = std::min(Ps[b], k);
-  BF_TRY(layout_stage(c, S, Ps, cap));
-  std::vector<const void*> in(nb);
-  std::vector<int64_t> ld(nb);
-  for (int b = 0; b < nb; ++b) in[b] = Pb.p() + Poff[b] * c.es, ld[b] = Ps[b];
-  return qr_into(c, S, in, ld, k, F->rV[l]);
+    StageBases bases{{G.p(), SA.p(), SB.p(), Xb.p()}};
+    BF_TRY(run_tasks(B, tasks, bases));
+  }
+  // B = argmin ||C - B X||_F, C = R^H P (eq. Bij)
+  std::vector<LSQTask> lt;
+  int maxR = 1, maxS = 1, maxK = 1;
+  for (OpState* o : ctr) {
+    Fact* F = o->F;
+    const int lm = o->lm, nb = o->nb;
+    Stage& S = F->st[F->stage_R(lm)];
+    Stage& SBs = F->st[F->stage_B()];
+    std::vector<int32_t> rows(nb), cols(nb);
+    for (int b = 0; b < nb; ++b) {
+      rows[b] = F->rU[0][b];
+      cols[b] = F->rV[lm][b];
+      maxR = std::max({maxR, rows[b], cols[b]});
+      maxS = std::max(maxS, o->Ps[b]);
+    }
+    maxK = std::max(maxK, o->k);
+    BF_TRY(layout_stage(*o, SBs, rows, cols));
+    SBs.cols = cols;
+    for (int b = 0; b < nb; ++b) {
+      LSQTask tk{};
+      tk.P = Pb.p() + (o->poff + o->Poff[b]) * B.es;
+      tk.Q = (const char*)S.d64.p + S.off[b] * 16;
+      tk.X = Xb.p() + (o->xoff + o->prev[b]) * B.es;
+      tk.B = (char*)SBs.d64.p + SBs.off[b] * 16;
+      tk.s = o->Ps[b];
+      tk.k = o->k;
+      tk.rU = rows[b];
+      tk.rV = cols[b];
+      lt.push_back(tk);
+    }
+  }
+  Scratch d(B.s);
+  BF_TRY(d.alloc(&B.mem, lt.size() * sizeof(LSQTask)));
+  BF_CUDA_TRY(cudaMemcpyAsync(d.p(), lt.data(), lt.size() * sizeof(LSQTask), cudaMemcpyHostToDevice, B.s));
+  BF_TRY(launch_lsq((const LSQTask*)d.p(), (int)lt.size(), maxS, maxK, maxR, B.dt, B.s));
+  for (OpState* o : ctr) BF_TRY(make32(B, *o, o->F->st[o->F->stage_B()]));
+  BF_CUDA_TRY(cudaStreamSynchronize(B.s));
+  return BF_OK;
 }
 
-int r_level(Ctx& c, int l) {
-  Plan* P = c.P;
-  Fact* F = c.F;
-  const int L = P->L, lm = F->lm, nb = 1 << L, nt = 1 << l, nn = 1 << (L - l), nn1 = nn >> 1;
-  const auto& nxt = F->rU[l + 1 - lm];
-  std::vector<int32_t> Ps(nb);
-  int k = 0;
-  for (int tau = 0; tau < nt; ++tau)
-    for (int nu = 0; nu < nn; ++nu) {
-      Ps[tau * nn + nu] = nxt[(2 * tau) * nn1 + (nu >> 1)] + nxt[(2 * tau + 1) * nn1 + (nu >> 1)];
-      k = std::max(k, Ps[tau * nn + nu]);
-    }
-  if (l == lm) k = std::max(k, *std::max_element(F->rV[lm].begin(), F->rV[lm].end()));
-  k += P->opt.p;
-  std::vector<int64_t> Poff(nb + 1, 0);
-  for (int b = 0; b < nb; ++b) Poff[b + 1] = Poff[b] + (int64_t)Ps[b] * k;
-  Scratch G(c.s), Z(c.s), Pb(c.s);
-  BF_TRY(G.alloc(&F->mem, P->n * (int64_t)k * c.es));
-  BF_TRY(launch_gaussian(P->opt.seed, sid(STAGE_R, l), 0, P->n, 0, k, G.p(), P->n, c.dt, c.s));
-  BF_TRY(Z.alloc(&F->mem, P->m * (int64_t)nn * k * c.es));
-  BF_TRY(sketch(c, BF_OP_N, L - l, k, G.p(), Z.p()));
-  BF_TRY(Pb.alloc(&F->mem, Poff[nb] * c.es));
-  BF_TRY(peel_U(c, l, k, Z.p(), Pb.p(), Poff, Ps));
-  Stage& S = F->st[F->stage_R(l)];
-  std::vector<int32_t> cap(nb);
-  for (int b = 0; b < nb; ++b) cap[b] = std::min(Ps[b], k);
-  BF_TRY(layout_stage(c, S, Ps, cap));
-  std::vector<const void*> in(nb);
-  std::vector<int64_t> ld(nb);
-  for (int b = 0; b < nb; ++b) in[b] = Pb.p() + Poff[b] * c.es, ld[b] = Ps[b];
-  BF_TRY(qr_into(c, S, in, ld, k, F->rU[l - lm]));
-  if (l != lm) return BF_OK;
-
-  // centre level: X = V^H Omega, then B (eq. Bij)
-  Scratch Xb(c.s);
-  int64_t xtot = 0;
-  for (int b = 0; b < nb; ++b) xtot += (int64_t)F->rV[lm][b] * k;
-  BF_TRY(Xb.alloc(&F->mem, xtot * c.es));
-  std::vector<int64_t> xo;
-  BF_TRY(project_X(c, k, G.p(), Xb.p(), xo));
-  Stage& SB = F->st[F->stage_B()];
-  std::vector<int32_t> rows(nb), cols(nb);
-  int maxR = 1, maxS = 1;
-  for (int b = 0; b < nb; ++b) {
-    rows[b] = F->rU[0][b];
-    cols[b] = F->rV[lm][b];
-    maxR = std::max({maxR, rows[b], cols[b]});
-    maxS = std::max(maxS, Ps[b]);
-  }
-  BF_TRY(layout_stage(c, SB, rows, cols));
-  SB.cols = cols;
-  std::vector<LSQTask> lt(nb);
-  for (int b = 0; b < nb; ++b) {
-    LSQTask& t = lt[b];
-    t.P = Pb.p() + Poff[b] * c.es;
-    t.Q = (const char*)S.d64.p + S.off[b] * 16;
-    t.X = Xb.p() + xo[b] * c.es;
-    t.B = (char*)SB.d64.p + SB.off[b] * 16;
-    t.s = Ps[b];
-    t.k = k;
-    t.rU = rows[b];
-    t.rV = cols[b];
-  }
-  Scratch d(c.s);
-  BF_TRY(d.alloc(&F->mem, nb * sizeof(LSQTask)));
-  BF_CUDA_TRY(cudaMemcpyAsync(d.p(), lt.data(), nb * sizeof(LSQTask), cudaMemcpyHostToDevice, c.s));
-  BF_TRY(launch_lsq((const LSQTask*)d.p(), nb, maxS, k, maxR, c.dt, c.s));
-  BF_TRY(make32(c, SB));
-  BF_CUDA_TRY(cudaStreamSynchronize(c.s));
-  return BF_OK;
+void destroy(Fact* F) {
+  for (auto& S : F->st) S.d64.release(nullptr), S.d32.release(nullptr);
+  delete F;
 }
 
 }  // namespace
 
-int factor(Plan* P, Operator* A, cudaStream_t s, Fact** out) {
-  *out = nullptr;
-  if (A->m != P->m || A->n != P->n) return fail(BF_EINVAL, "operator shape does not match the plan");
+int factor_batch(int count, Plan* const* P, Operator* const* A, cudaStream_t s, Fact** out) {
+  for (int i = 0; i < count; ++i) out[i] = nullptr;
+  if (count < 1) return fail(BF_EINVAL, "empty batch");
+  const int prec = P[0]->opt.precision;
+  for (int i = 0; i < count; ++i) {
+    if (A[i]->m != P[i]->m || A[i]->n != P[i]->n)
+      return fail(BF_EINVAL, "operator shape does not match its plan (batch entry " + std::to_string(i) + ")");
+    if (P[i]->opt.precision != prec) return fail(BF_EINVAL, "all plans of a batch must share one precision");
+  }
   const auto t0 = std::chrono::steady_clock::now();
-  Fact* F = new Fact();
-  F->plan = P;
-  F->L = P->L;
-  F->lm = P->lm;
-  F->n = P->n;
-  F->m = P->m;
-  F->mem.cap = P->opt.mem_cap;
-  F->st.resize(P->L + 3);
-  F->rV.assign(P->lm + 1, {});
-  F->rU.assign(P->L - P->lm + 1, {});
-  Ctx c{P, A, F, s, P->opt.precision == BF_PREC_MIXED ? BF_C64 : BF_C128, 0};
-  c.es = elem_bytes(c.dt);
-  const int64_t n0 = A->cols_N, t0c = A->cols_T;
-  int rc = leaf_loop(c, true);
-  if (!rc) rc = leaf_loop(c, false);
-  for (int l = 1; !rc && l <= P->lm; ++l) rc = w_level(c, l);
-  for (int l = P->L - 1; !rc && l >= P->lm; --l) rc = r_level(c, l);
+  Batch B;
+  B.s = s;
+  B.dt = prec == BF_PREC_MIXED ? BF_C64 : BF_C128;
+  B.es = elem_bytes(B.dt);
+  size_t cap = 0;
+  bool capped = true;
+  for (int i = 0; i < count; ++i) capped = capped && P[i]->opt.mem_cap > 0, cap += P[i]->opt.mem_cap;
+  B.mem.cap = capped ? cap : 0;
+  B.ops.resize(count);
+  std::vector<int64_t> n0(count), t0c(count);
+  int maxlm = 0, maxr = 0;
+  for (int i = 0; i < count; ++i) {
+    OpState& o = B.ops[i];
+    o.P = P[i];
+    o.A = A[i];
+    o.L = P[i]->L;
+    o.lm = P[i]->lm;
+    o.nb = 1 << o.L;
+    Fact* F = new Fact();
+    F->plan = P[i];
+    F->L = o.L;
+    F->lm = o.lm;
+    F->n = P[i]->n;
+    F->m = P[i]->m;
+    F->mem.cap = P[i]->opt.mem_cap;
+    F->st.resize(o.L + 3);
+    F->rV.assign(o.lm + 1, {});
+    F->rU.assign(o.L - o.lm + 1, {});
+    o.F = F;
+    n0[i] = A[i]->cols_N;
+    t0c[i] = A[i]->cols_T;
+    maxlm = std::max(maxlm, o.lm);
+    maxr = std::max(maxr, o.L - o.lm);
+  }
+  int rc = leaf_phase(B, true);
+  if (!rc) rc = leaf_phase(B, false);
+  for (int t = 1; !rc && t <= maxlm; ++t) rc = w_phase(B, t);
+  for (int t = 1; !rc && t <= maxr; ++t) rc = r_phase(B, t);
   if (!rc) {
-    cudaError_t e = cudaStreamSynchronize(s);
+    const cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) rc = fail(BF_ECUDA, cudaGetErrorString(e));
   }
+  for (auto& o : B.ops) o.Y.release(s);
   if (rc) {
-    for (auto& S : F->st) S.d64.release(nullptr), S.d32.release(nullptr);
-    delete F;
+    for (auto& o : B.ops) destroy(o.F);
     return rc;
   }
-  F->cols_N = A->cols_N - n0;
-  F->cols_T = A->cols_T - t0c;
-  F->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-  *out = F;
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  for (int i = 0; i < count; ++i) {
+    Fact* F = B.ops[i].F;
+    F->cols_N = A[i]->cols_N - n0[i];
+    F->cols_T = A[i]->cols_T - t0c[i];
+    F->seconds = secs;
+    out[i] = F;
+  }
   return BF_OK;
+}
+
+int factor(Plan* P, Operator* A, cudaStream_t s, Fact** out) {
+  *out = nullptr;
+  return factor_batch(1, &P, &A, s, out);
 }
 
 }  // namespace bf

@@ -22,6 +22,8 @@
 // reduced phase theta_hi + theta_lo is evaluated as sincosf(theta_hi)
 // corrected to first order in theta_lo.  The phase of an oscillatory kernel
 // with k*r ~ 1e4 keeps ~1e-9 rad absolute accuracy.
+#include <algorithm>
+
 #include "bf_internal.h"
 #include "cx.cuh"
 
@@ -29,12 +31,6 @@ namespace bf {
 
 namespace {
 constexpr int GM = 64, GK = 16, GT = 256;
-
-struct PointsSoA {
-  const double* x;
-  const double* y;
-  const double* z;
-};
 
 __device__ __forceinline__ double2 kernel_value(int type, double wn, double tx, double ty,
                                                 double tz, double sx, double sy, double sz) {
@@ -148,52 +144,6 @@ __device__ __forceinline__ float2 kernel_value_ff(int type, float kh, float kl, 
   return make_float2(c1 * ir, s1 * ir);
 }
 
-template <typename V>
-struct DenseLoader {
-  const V* A;
-  int64_t lda;
-  int op;
-  __device__ __forceinline__ V get(int64_t r, int64_t kk) const {
-    if (op == BF_OP_N) return A[r + kk * lda];
-    V v = A[kk + r * lda];
-    v.y = -v.y;
-    return v;
-  }
-  __device__ __forceinline__ bool k_fastest() const { return op != BF_OP_N; }
-};
-
-struct KernelLoader64 {
-  PointsSoA tgt, src;
-  int type;
-  double wn;
-  int op;
-  __device__ __forceinline__ double2 get(int64_t r, int64_t kk) const {
-    double2 v;
-    if (op == BF_OP_N) {
-      v = kernel_value(type, wn, tgt.x[r], tgt.y[r], tgt.z[r], src.x[kk], src.y[kk], src.z[kk]);
-    } else {
-      v = kernel_value(type, wn, tgt.x[kk], tgt.y[kk], tgt.z[kk], src.x[r], src.y[r], src.z[r]);
-      v.y = -v.y;
-    }
-    return v;
-  }
-  __device__ __forceinline__ bool k_fastest() const { return false; }
-};
-
-struct KernelLoader32 {
-  PointsFF tgt, src;
-  int type;
-  float kh, kl;
-  int op;
-  __device__ __forceinline__ float2 get(int64_t r, int64_t kk) const {
-    if (op == BF_OP_N) return kernel_value_ff(type, kh, kl, tgt, r, src, kk);
-    float2 v = kernel_value_ff(type, kh, kl, tgt, kk, src, r);
-    v.y = -v.y;
-    return v;
-  }
-  __device__ __forceinline__ bool k_fastest() const { return false; }
-};
-
 template <typename R, int Q>
 struct Acc;
 template <int Q>
@@ -236,25 +186,78 @@ struct Acc<float, Q> {
 };
 }  // namespace
 
-// GN output columns per CTA; each thread owns one row and GN/4 columns.
-template <typename R, int GN, class Loader>
+// Element (r, kk) of the job's operator in the orientation of its product.
+template <typename R>
+struct JobElem;
+template <>
+struct JobElem<double> {
+  static __device__ __forceinline__ double2 get(const SketchJob& J, int64_t r, int64_t kk) {
+    double2 v;
+    if (J.kind == 0) {
+      const double2* A = (const double2*)J.A;
+      if (J.op == BF_OP_N) return A[r + kk * J.lda];
+      v = A[kk + r * J.lda];
+    } else {
+      const int64_t it = J.op == BF_OP_N ? r : kk, is = J.op == BF_OP_N ? kk : r;
+      v = kernel_value(J.ktype, J.wn, J.tgt[it], J.tgt[J.m + it], J.tgt[2 * J.m + it], J.src[is],
+                       J.src[J.n + is], J.src[2 * J.n + is]);
+      if (J.op == BF_OP_N) return v;
+    }
+    v.y = -v.y;
+    return v;
+  }
+};
+template <>
+struct JobElem<float> {
+  static __device__ __forceinline__ float2 get(const SketchJob& J, int64_t r, int64_t kk) {
+    float2 v;
+    if (J.kind == 0) {
+      const float2* A = (const float2*)J.A;
+      if (J.op == BF_OP_N) return A[r + kk * J.lda];
+      v = A[kk + r * J.lda];
+    } else {
+      const PointsFF T{J.tgtF, J.m}, S{J.srcF, J.n};
+      if (J.op == BF_OP_N) return kernel_value_ff(J.ktype, J.kh, J.kl, T, r, S, kk);
+      v = kernel_value_ff(J.ktype, J.kh, J.kl, T, kk, S, r);
+    }
+    v.y = -v.y;
+    return v;
+  }
+};
+
+struct SketchTile {
+  int32_t job, group, col0, pad;
+  int64_t row0;
+};
+
+// One CTA computes a GM x GN tile of one job's group; each thread owns one
+// row and GN/4 columns.
+template <typename R, int GN>
 __global__ void __launch_bounds__(GT)
-sketch_gemm_kernel(Loader ld, int64_t M, const int64_t* __restrict__ goff, int64_t Ktot,
-                   int64_t kcols, const typename Cx<R>::V* __restrict__ X, int64_t ldx,
-                   typename Cx<R>::V* __restrict__ Y, int64_t ldy) {
+sketch_job_kernel(const SketchJob* __restrict__ jobs, const SketchTile* __restrict__ tiles) {
   using V = typename Cx<R>::V;
   constexpr int Q = GN / 4;
   __shared__ V sA[GK][GM + 1];
   __shared__ V sB[GK][GN + 1];
-  const int64_t row0 = (int64_t)blockIdx.x * GM;
-  const int col0 = blockIdx.y * GN;
-  const int g = blockIdx.z;
-  const int64_t klo = goff ? goff[g] : 0;
-  const int64_t khi = goff ? goff[g + 1] : Ktot;
+  __shared__ SketchJob J;
+  __shared__ SketchTile T;
+  if (threadIdx.x == 0) {
+    T = tiles[blockIdx.x];
+    J = jobs[T.job];
+  }
+  __syncthreads();
+  const int64_t row0 = T.row0;
+  const int col0 = T.col0, g = T.group;
+  const int64_t M = J.M, kcols = J.kcols;
+  const int64_t klo = J.d_off ? J.d_off[g] : 0;
+  const int64_t khi = J.d_off ? J.d_off[g + 1] : J.Ktot;
+  const V* __restrict__ X = (const V*)J.X;
+  V* __restrict__ Y = (V*)J.Y;
+  const int64_t ldx = J.ldx, ldy = J.ldy;
   const int tr = threadIdx.x % GM, tc = threadIdx.x / GM;   // tc 0..3
   Acc<R, Q> acc;
   acc.zero();
-  const bool kf = ld.k_fastest();
+  const bool kf = J.kind == 0 && J.op != BF_OP_N;   // dense adjoint: K is contiguous
   for (int64_t k0 = klo; k0 < khi; k0 += GK) {
     acc.begin_chunk();
 #pragma unroll
@@ -270,7 +273,7 @@ sketch_gemm_kernel(Loader ld, int64_t M, const int64_t* __restrict__ goff, int64
       }
       const int64_t gi = row0 + i, gk = k0 + kk;
       V v = Cx<R>::make(0, 0);
-      if (gi < M && gk < khi) v = ld.get(gi, gk);
+      if (gi < M && gk < khi) v = JobElem<R>::get(J, gi, gk);
       sA[kk][i] = v;
     }
 #pragma unroll
@@ -302,52 +305,105 @@ sketch_gemm_kernel(Loader ld, int64_t M, const int64_t* __restrict__ goff, int64
   }
 }
 
-template <typename R, class Loader>
-static int run_gemm(const Loader& ld, int64_t M, const GemmGroups& g, int64_t Ktot, const void* X,
-                    int64_t ldx, void* Y, int64_t ldy, cudaStream_t s) {
-  using V = typename Cx<R>::V;
-  if (M <= 0 || g.kcols <= 0 || g.groups <= 0) return BF_OK;
-  const int GN = g.kcols > 32 ? 64 : 32;
-  dim3 grid((unsigned)((M + GM - 1) / GM), (unsigned)((g.kcols + GN - 1) / GN), (unsigned)g.groups);
-  if (grid.y > 65535 || grid.z > 65535) return fail(BF_EINVAL, "sketch grid too large");
-  if (GN == 64)
-    sketch_gemm_kernel<R, 64, Loader><<<grid, GT, 0, s>>>(ld, M, g.d_off, Ktot, g.kcols, (const V*)X, ldx,
-                                                          (V*)Y, ldy);
-  else
-    sketch_gemm_kernel<R, 32, Loader><<<grid, GT, 0, s>>>(ld, M, g.d_off, Ktot, g.kcols, (const V*)X, ldx,
-                                                          (V*)Y, ldy);
-  BF_CUDA_TRY(cudaGetLastError());
-  return BF_OK;
+int launch_sketch_jobs(const std::vector<SketchJob>& jobs, int dtype, MemTracker* mt, cudaStream_t s) {
+  if (jobs.empty()) return BF_OK;
+  int64_t maxk = 0;
+  for (const auto& j : jobs) maxk = std::max(maxk, j.kcols);
+  const int GN = maxk > 32 ? 64 : 32;
+  std::vector<SketchTile> tiles;
+  for (size_t ji = 0; ji < jobs.size(); ++ji) {
+    const SketchJob& j = jobs[ji];
+    if (j.M <= 0 || j.kcols <= 0) continue;
+    for (int g = 0; g < j.groups; ++g)
+      for (int64_t r0 = 0; r0 < j.M; r0 += GM)
+        for (int c0 = 0; c0 < j.kcols; c0 += GN) tiles.push_back({(int32_t)ji, g, c0, 0, r0});
+  }
+  if (tiles.empty()) return BF_OK;
+  const size_t jb = jobs.size() * sizeof(SketchJob), tb = tiles.size() * sizeof(SketchTile);
+  DevBuf d;
+  BF_TRY(d.alloc(mt, jb + tb, s));
+  int rc = BF_OK;
+  if (cudaMemcpyAsync(d.p, jobs.data(), jb, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync((char*)d.p + jb, tiles.data(), tb, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    rc = fail(BF_ECUDA, "upload of sketch jobs failed");
+  const SketchJob* dj = (const SketchJob*)d.p;
+  const SketchTile* dt = (const SketchTile*)((char*)d.p + jb);
+  const unsigned nt = (unsigned)tiles.size();
+  if (!rc) {
+    if (dtype == BF_C128) {
+      if (GN == 64)
+        sketch_job_kernel<double, 64><<<nt, GT, 0, s>>>(dj, dt);
+      else
+        sketch_job_kernel<double, 32><<<nt, GT, 0, s>>>(dj, dt);
+    } else {
+      if (GN == 64)
+        sketch_job_kernel<float, 64><<<nt, GT, 0, s>>>(dj, dt);
+      else
+        sketch_job_kernel<float, 32><<<nt, GT, 0, s>>>(dj, dt);
+    }
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) rc = fail(BF_ECUDA, std::string("sketch launch: ") + cudaGetErrorString(e));
+  }
+  d.release(s);
+  return rc;
+}
+
+SketchJob dense_job(int op, const void* A, int64_t lda, int64_t m, int64_t n, const GemmGroups& g,
+                    const void* X, int64_t ldx, void* Y, int64_t ldy) {
+  SketchJob j{};
+  j.kind = 0;
+  j.op = op;
+  j.groups = g.groups;
+  j.M = op == BF_OP_N ? m : n;
+  j.Ktot = op == BF_OP_N ? n : m;
+  j.kcols = g.kcols;
+  j.d_off = g.d_off;
+  j.A = A;
+  j.lda = lda;
+  j.m = m;
+  j.n = n;
+  j.X = X;
+  j.ldx = ldx;
+  j.Y = Y;
+  j.ldy = ldy;
+  return j;
+}
+
+SketchJob kernel_job(const Plan* P, int op, const GemmGroups& g, const void* X, int64_t ldx, void* Y,
+                     int64_t ldy) {
+  SketchJob j{};
+  j.kind = 1;
+  j.op = op;
+  j.ktype = P->kern.type;
+  j.groups = g.groups;
+  j.M = op == BF_OP_N ? P->m : P->n;
+  j.Ktot = op == BF_OP_N ? P->n : P->m;
+  j.kcols = g.kcols;
+  j.d_off = g.d_off;
+  j.tgt = (const double*)P->d_tgt.p;
+  j.src = (const double*)P->d_src.p;
+  j.tgtF = (const float*)P->d_tgtF.p;
+  j.srcF = (const float*)P->d_srcF.p;
+  j.m = P->m;
+  j.n = P->n;
+  j.wn = P->kern.wavenumber;
+  j.kh = P->kh;
+  j.kl = P->kl;
+  j.X = X;
+  j.ldx = ldx;
+  j.Y = Y;
+  j.ldy = ldy;
+  return j;
 }
 
 int launch_dense_gemm(int op, const void* A, int64_t lda, int64_t m, int64_t n, const GemmGroups& g,
                       const void* X, int64_t ldx, void* Y, int64_t ldy, int dtype, cudaStream_t s) {
-  const int64_t M = op == BF_OP_N ? m : n;
-  const int64_t K = op == BF_OP_N ? n : m;
-  if (dtype == BF_C128) {
-    DenseLoader<double2> ld{(const double2*)A, lda, op};
-    return run_gemm<double>(ld, M, g, K, X, ldx, Y, ldy, s);
-  }
-  DenseLoader<float2> ld{(const float2*)A, lda, op};
-  return run_gemm<float>(ld, M, g, K, X, ldx, Y, ldy, s);
+  return launch_sketch_jobs({dense_job(op, A, lda, m, n, g, X, ldx, Y, ldy)}, dtype, nullptr, s);
 }
 
 int launch_kernel_gemm(const Plan* P, int op, const GemmGroups& g, const void* X, int64_t ldx,
                        void* Y, int64_t ldy, int dtype, cudaStream_t s) {
-  const int64_t M = op == BF_OP_N ? P->m : P->n;
-  const int64_t K = op == BF_OP_N ? P->n : P->m;
-  if (dtype == BF_C128) {
-    const double* src = (const double*)P->d_src.p;
-    const double* tgt = (const double*)P->d_tgt.p;
-    PointsSoA ps{src, src + P->n, src + 2 * P->n};
-    PointsSoA pt{tgt, tgt + P->m, tgt + 2 * P->m};
-    KernelLoader64 ld{pt, ps, P->kern.type, P->kern.wavenumber, op};
-    return run_gemm<double>(ld, M, g, K, X, ldx, Y, ldy, s);
-  }
-  PointsFF ps{(const float*)P->d_srcF.p, P->n};
-  PointsFF pt{(const float*)P->d_tgtF.p, P->m};
-  KernelLoader32 ld{pt, ps, P->kern.type, P->kh, P->kl, op};
-  return run_gemm<float>(ld, M, g, K, X, ldx, Y, ldy, s);
+  return launch_sketch_jobs({kernel_job(P, op, g, X, ldx, Y, ldy)}, dtype, nullptr, s);
 }
 
 }  // namespace bf
