@@ -102,6 +102,35 @@ def cpu_oracle_sample(n_sample: int = 2048):
     return dt, dt * scale, os.cpu_count()
 
 
+def profile_case(args):
+    """Small cases of one kernel family, sized for ncu captures (inputs of a
+    few hundred MB at most): the on-the-fly sketch product (n = 8192, 22
+    columns, all rows against all sources), the apply of a factorization
+    (n = 16384, 64 right-hand sides) or one factorization (its QR levels)."""
+    import torch
+    from paper_2002_03400_gb300 import api, inputs
+    api.set_sketch_engine(args.engine)
+    if args.profile_case == "sketch":
+        n = 8192
+        g = inputs.line_pair(n)
+        plan = api.Plan(g.src, g.tgt, kernel="helmholtz2d", wavenumber=g.wavenumber, leaf=16, precision="mixed")
+        op = api.Operator.kernel(plan)
+        X = api.colmajor(torch.from_numpy(inputs.random_rhs(n, 22, seed=3)).to(torch.complex64).cuda())
+        for _ in range(3):
+            op.apply(X)
+    else:
+        g = inputs.line_pair(N)
+        plan = api.Plan(g.src, g.tgt, kernel="helmholtz2d", wavenumber=g.wavenumber, leaf=LEAF, tol=TOL,
+                        precision="mixed")
+        F = api.Factorization.factor(plan, api.Operator.kernel(plan))
+        if args.profile_case == "apply":
+            x = torch.from_numpy(inputs.random_rhs(N, NRHS, seed=1)).to(torch.complex64).cuda()
+            for _ in range(3):
+                F.apply(x)
+    torch.cuda.synchronize()
+    print("profile case done")
+
+
 def run_reference(args):
     """--impl reference: the FP64 oracle on the host cores, bounded sample."""
     rank = int(os.environ.get("RANK", "0"))
@@ -132,9 +161,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--profile-case", choices=["sketch", "apply", "qr"], default=None,
+                    help="run only a small case of one kernel family (for ncu captures)")
+    ap.add_argument("--engine", default="tensor")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_case:
+        return profile_case(args)
 
     import torch
     from paper_2002_03400_gb300 import api, inputs
@@ -244,6 +278,18 @@ def main():
     torch.cuda.synchronize()
     t_sk = r0.elapsed_time(r1) / reps / 1e3
     sk_flops = 8.0 * N * N * kw            # complex multiply-adds x 8 real flops
+    engine_ms = {}
+    for eng in ("tensor-3xtf32", "tensor-split3", "simt"):
+        api.set_sketch_engine(eng)
+        op_mx.apply(Xk)
+        torch.cuda.synchronize()
+        r0.record(stream)
+        for _ in range(reps):
+            op_mx.apply(Xk)
+        r1.record(stream)
+        torch.cuda.synchronize()
+        engine_ms[eng] = r0.elapsed_time(r1) / reps
+    api.set_sketch_engine("tensor")
     fp32_peak = 152 * 128 * 2 * 2070e6 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 
     # end to end through the C ABI from host buffers
@@ -290,7 +336,7 @@ def main():
                      "frac": sk_flops / t_sk / 1e12 / fp32_peak, "traffic": None,
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
                      "work": f"8*m*n*k flop, m=n={N}, k={kw}; entry formation (~100 FP32 ops/entry) not counted",
-                     "launch_ms": t_sk * 1e3},
+                     "launch_ms": t_sk * 1e3, "engine_ms": engine_ms},
     }
     if rank == 0 and not args.no_cpu:
         raw, scaled, cores = cpu_oracle_sample()

@@ -79,6 +79,7 @@ def lib():
         "bf_fact_export": (i32, [vp, i32, vp, C.POINTER(C.c_size_t)]),
         "bf_error": (i32, [vp, vp, i32, C.c_uint64, i32, vp, C.POINTER(dbl)]),
         "bf_free": (None, [vp]),
+        "bf_set_sketch_engine": (i32, [i32]),
         "bf_gaussian": (i32, [C.c_uint64, C.c_uint32, i64, i64, i64, i64, vp, i64, i32, vp]),
     }
     for name, (res, args) in sig.items():
@@ -96,7 +97,13 @@ def exported_symbols():
             "bf_operator_callback", "bf_operator_apply", "bf_operator_counts", "bf_factor",
             "bf_factor_batch", "bf_apply",
             "bf_apply_T", "bf_apply_noalloc", "bf_ranks", "bf_fact_info", "bf_fact_import", "bf_fact_export", "bf_error",
-            "bf_free", "bf_gaussian"]
+            "bf_free", "bf_gaussian", "bf_set_sketch_engine"]
+
+
+def set_sketch_engine(engine: str):
+    """'tensor' (default: tcgen05 where it applies, split depth by tolerance),
+    'simt', 'tensor-3xtf32' or 'tensor-split3' (split depth forced)."""
+    check(lib().bf_set_sketch_engine({"tensor": 0, "simt": 1, "tensor-3xtf32": 2, "tensor-split3": 3}[engine]))
 
 
 def check(rc: int):

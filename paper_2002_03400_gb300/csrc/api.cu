@@ -569,6 +569,8 @@ int bf_factor(bf_plan plan, bf_operator A, void* stream, bf_fact* out) {
   return BF_OK;
 }
 
+int bf_set_sketch_engine(int engine) { return set_sketch_engine(engine); }
+
 int bf_factor_batch(int count, const bf_plan* plans, const bf_operator* ops, void* stream, bf_fact* out) {
   if (!out || !plans || count < 1) return fail(BF_EINVAL, "bad batch arguments");
   for (int i = 0; i < count; ++i) out[i] = nullptr;

@@ -247,6 +247,8 @@ int launch_gaussian(uint64_t seed, uint32_t stream_id, int64_t row0, int64_t row
 // from the plan's points (kind 1).
 struct SketchJob {
   int32_t kind, op, ktype, groups;
+  int32_t split;          // tensor-core path: 2 = 3xTF32, 3 = exact three-way TF32 split
+  int32_t pad_;
   int64_t M, Ktot, kcols;
   const int64_t* d_off;
   const void* A;
@@ -267,6 +269,15 @@ struct SketchJob {
 // column tile).  Job and tile lists are uploaded to stream-ordered scratch.
 int launch_sketch_jobs(const std::vector<SketchJob>& jobs, int dtype, MemTracker* mt,
                        cudaStream_t s);
+int launch_sketch_jobs_simt(const std::vector<SketchJob>& jobs, int dtype, MemTracker* mt,
+                            cudaStream_t s);
+// tcgen05 3xTF32 path (complex64 jobs with sketch width <= 64)
+bool sketch_tc_applies(const std::vector<SketchJob>& jobs);
+int launch_sketch_jobs_tc(const std::vector<SketchJob>& jobs, MemTracker* mt, cudaStream_t s);
+// BF_ETIMEOUT if a tensor-core kernel's bounded wait gave up since the last reset
+int tc_status(bool reset);
+// 0: tensor-core sketch where it applies (default), 1: SIMT sketch only
+int set_sketch_engine(int e);
 struct GemmGroups;
 SketchJob dense_job(int op, const void* A, int64_t lda, int64_t m, int64_t n, const GemmGroups& g,
                     const void* X, int64_t ldx, void* Y, int64_t ldy);

@@ -160,9 +160,13 @@ int sketch_all(Batch& B, const std::vector<SketchReq>& reqs) {
     const int64_t in_rows = opN ? P->n : P->m, out_rows = opN ? P->m : P->n;
     const int64_t* d_off = opN ? P->offS_dev(q.level) : P->offT_dev(q.level);
     SketchJob j{};
-    if (q.o->A->plan == P && q.o->A->sketch_job(q.op, groups, d_off, q.k, q.Om, in_rows, q.Y, out_rows, B.dt, &j))
+    if (q.o->A->plan == P && q.o->A->sketch_job(q.op, groups, d_off, q.k, q.Om, in_rows, q.Y, out_rows, B.dt, &j)) {
+      // tensor-core split depth: 3xTF32 (~2^-21 per product) suffices when the
+      // truncation tolerance is well above it; tighter tolerances take the
+      // exact three-way split (FP32-level products)
+      j.split = P->tol < 5e-6 ? 3 : 2;
       jobs.push_back(j);
-    else
+    } else
       BF_TRY(sketch_one(B, q));
   }
   return launch_sketch_jobs(jobs, B.dt, &B.mem, B.s);
@@ -234,6 +238,7 @@ int qr_all(Batch& B, std::vector<QRJob>& jobs) {
   std::vector<int32_t> h(nt);
   BF_CUDA_TRY(cudaMemcpyAsync(h.data(), d_r, nt * sizeof(int32_t), cudaMemcpyDeviceToHost, B.s));
   BF_CUDA_TRY(cudaStreamSynchronize(B.s));
+  BF_TRY(tc_status(true));
   size_t q = 0;
   for (auto& J : jobs) {
     const size_t nb = J.S->rows.size();

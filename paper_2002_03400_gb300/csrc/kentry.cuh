@@ -1,0 +1,230 @@
+// Kernel-entry formulas of the built-in operators, shared by the sketch kernels.
+//
+// FP64 path: distance, phase k*r and its reduction modulo 2*pi in FP64, then
+// sincos.  Mixed path, no FP64 instruction: points and k are float-float
+// pairs (hi + lo); the distance is formed in float-float with Dekker/Knuth
+// error-free transformations (its square root from an rsqrt estimate, one
+// Newton step and a float-float correction), the phase k*r in float-float is
+// reduced by pi/2 with a three-part split of pi/2 (Cody & Waite; the first
+// product subtracted exactly by FMA), and sin/cos of the reduced argument
+// |t| <= pi/4 come from their Taylor series (terms to t^9 and t^10; the
+// truncation is below 2e-9) with the quadrant applied afterwards.  Entries
+// keep ~1.5e-7 relative accuracy at k*r ~ 2e4.
+#pragma once
+#include "bf_internal.h"
+#include "cx.cuh"
+
+namespace bf {
+namespace dev {
+
+__device__ __forceinline__ double2 kernel_value(int type, double wn, double tx, double ty,
+                                                double tz, double sx, double sy, double sz) {
+  if (type == BF_KERNEL_DFT) {
+    double sn, cs;
+    sincospi(-2.0 * tx * sx, &sn, &cs);
+    return make_double2(cs, sn);
+  }
+  const double dx = tx - sx, dy = ty - sy, dz = tz - sz;
+  const double r = sqrt(dx * dx + dy * dy + dz * dz);
+  const double ph = wn * r;
+  // reduce the phase to [-pi, pi] before the trigonometric evaluation
+  const double q = rint(ph * 0.15915494309189535);
+  const double red = fma(-q, 6.283185307179586, ph) - q * 2.4492935982947064e-16;
+  double sn, cs;
+  sincos(red, &sn, &cs);
+  if (type == BF_KERNEL_HELMHOLTZ_2D) {   // exp(-i k r) / r
+    const double ir = 1.0 / r;
+    return make_double2(cs * ir, -sn * ir);
+  }
+  const double ir = 0.07957747154594767 / r;   // exp(i k r) / (4 pi r)
+  return make_double2(cs * ir, sn * ir);
+}
+
+// ---- float-float (hi + lo) arithmetic: error-free transformations ----
+struct FF {
+  float h, l;
+};
+__device__ __forceinline__ FF two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ FF fast_two_sum(float a, float b) {   // |a| >= |b|
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ FF two_prod(float a, float b) {
+  const float p = a * b;
+  return {p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ FF ff_sub(float ah, float al, float bh, float bl) {
+  FF d = two_sum(ah, -bh);
+  d.l += al - bl;
+  return fast_two_sum(d.h, d.l);
+}
+__device__ __forceinline__ FF ff_sq(FF a) {
+  FF p = two_prod(a.h, a.h);
+  p.l = fmaf(2.0f * a.h, a.l, p.l);
+  return p;
+}
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  FF s = two_sum(a.h, b.h);
+  s.l += a.l + b.l;
+  return fast_two_sum(s.h, s.l);
+}
+
+// pi/2 = C1 + C2 + C3 (each the float nearest to the remainder) and 2/pi
+#define BF_PIO2_1 1.57079637050628662e+00f
+#define BF_PIO2_2 -4.37113882867379289e-08f
+#define BF_PIO2_3 -1.71512451000588187e-15f
+#define BF_2OPI 6.36619746685028076e-01f
+
+// sin t and cos t for |t| <= pi/4 from their Taylor series
+__device__ __forceinline__ void sincos_taylor(float t, float& s, float& c) {
+  const float t2 = t * t;
+  float ps = fmaf(t2, 1.0f / 362880.0f, -1.0f / 5040.0f);
+  ps = fmaf(t2, ps, 1.0f / 120.0f);
+  ps = fmaf(t2, ps, -1.0f / 6.0f);
+  s = fmaf(t * t2, ps, t);
+  float pc = fmaf(t2, -1.0f / 3628800.0f, 1.0f / 40320.0f);
+  pc = fmaf(t2, pc, -1.0f / 720.0f);
+  pc = fmaf(t2, pc, 1.0f / 24.0f);
+  pc = fmaf(t2, pc, -0.5f);
+  c = fmaf(t2, pc, 1.0f);
+}
+
+// Per-thread evaluation context of one job's entries, held in registers so
+// that the entry loop neither reloads the job descriptor nor the thread's row
+// point.  The kernels depend on the points only through |t - s| (the DFT
+// through the symmetric product t*s), so the adjoint (op C) evaluates the same
+// formula with sources as rows and targets as columns, then conjugates.
+template <typename R>
+struct Entry;
+
+template <>
+struct Entry<float> {
+  int kind, type, conj;
+  float kh, kl;
+  const float* colp;   // float-float SoA of the column point set
+  int64_t coln;
+  const float2* A;
+  int64_t lda;
+  int opN;
+  float rp[6];         // this thread's row point (x, y, z as hi/lo)
+
+  __device__ __forceinline__ void init(const SketchJob& J, int64_t row, bool valid) {
+    kind = J.kind;
+    type = J.ktype;
+    opN = J.op == BF_OP_N;
+    conj = !opN;
+    kh = J.kh;
+    kl = J.kl;
+    A = (const float2*)J.A;
+    lda = J.lda;
+    const float* rowp = opN ? J.tgtF : J.srcF;
+    const int64_t rown = opN ? J.m : J.n;
+    colp = opN ? J.srcF : J.tgtF;
+    coln = opN ? J.n : J.m;
+#pragma unroll
+    for (int d = 0; d < 6; ++d) rp[d] = (kind == 1 && valid) ? rowp[d * rown + row] : 0.f;
+  }
+
+  __device__ __forceinline__ float2 get(int64_t row, int64_t kk) const {
+    float2 v;
+    if (kind == 0) {
+      if (opN) return A[row + kk * lda];
+      v = A[kk + row * lda];
+    } else {
+      v = value(kk);
+    }
+    if (conj) v.y = -v.y;
+    return v;
+  }
+
+  // K(row point, column point kk)
+  __device__ __forceinline__ float2 value(int64_t kk) const {
+    const float* c = colp + kk;
+    if (type == BF_KERNEL_DFT) {
+      FF u = two_prod(rp[0], c[0]);
+      u.l = fmaf(rp[0], c[coln], fmaf(rp[1], c[0], u.l));
+      const float q = rintf(u.h);
+      const FF f = two_sum(u.h - q, u.l);     // u.h - q exact (Sterbenz)
+      float sn, cs;
+      sincospif(-2.0f * f.h, &sn, &cs);
+      const float d = -6.28318531f * f.l;     // first-order correction
+      return make_float2(cs - d * sn, sn + d * cs);
+    }
+    FF r2 = ff_sq(ff_sub(rp[0], rp[1], c[0], c[coln]));
+    r2 = ff_add(r2, ff_sq(ff_sub(rp[2], rp[3], c[2 * coln], c[3 * coln])));
+    if (type == BF_KERNEL_HELMHOLTZ_3D) r2 = ff_add(r2, ff_sq(ff_sub(rp[4], rp[5], c[4 * coln], c[5 * coln])));
+    // 1/sqrt(r2): estimate and one Newton step; r = sqrt(r2) corrected in float-float
+    float rs = rsqrtf(r2.h);
+    rs = rs * fmaf(-0.5f * r2.h * rs, rs, 1.5f);
+    const float rh0 = r2.h * rs;
+    const FF e = two_prod(rh0, rh0);
+    const float num = ((r2.h - e.h) - e.l) + r2.l;
+    const FF r = fast_two_sum(rh0, num * (0.5f * rs));
+    // phase k * r
+    FF ph = two_prod(kh, r.h);
+    ph.l = fmaf(kh, r.l, fmaf(kl, r.h, ph.l));
+    ph = fast_two_sum(ph.h, ph.l);
+    // t = ph - q pi/2 with q * C1 subtracted exactly by FMA
+    const float q = rintf(ph.h * BF_2OPI);
+    const float t1 = fmaf(-q, BF_PIO2_1, ph.h);
+    const FF m2 = two_prod(q, BF_PIO2_2);
+    const FF th = two_sum(t1, -m2.h);
+    const float t = th.h + ((th.l + (ph.l - m2.l)) - q * BF_PIO2_3);
+    float sv, cv;
+    sincos_taylor(t, sv, cv);
+    const int qi = (int)q & 3;
+    float sn = (qi & 1) ? cv : sv, cs = (qi & 1) ? sv : cv;
+    if (qi & 2) sn = -sn;
+    if ((qi + 1) & 2) cs = -cs;
+    if (type == BF_KERNEL_HELMHOLTZ_2D) return make_float2(cs * rs, -sn * rs);
+    const float ir = 0.0795774715f * rs;
+    return make_float2(cs * ir, sn * ir);
+  }
+};
+
+template <>
+struct Entry<double> {
+  int kind, type, opN;
+  double wn;
+  const double* colp;
+  int64_t coln;
+  const double2* A;
+  int64_t lda;
+  double rp[3];
+
+  __device__ __forceinline__ void init(const SketchJob& J, int64_t row, bool valid) {
+    kind = J.kind;
+    type = J.ktype;
+    opN = J.op == BF_OP_N;
+    wn = J.wn;
+    A = (const double2*)J.A;
+    lda = J.lda;
+    const double* rowp = opN ? J.tgt : J.src;
+    const int64_t rown = opN ? J.m : J.n;
+    colp = opN ? J.src : J.tgt;
+    coln = opN ? J.n : J.m;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) rp[d] = (kind == 1 && valid) ? rowp[d * rown + row] : 0.0;
+  }
+
+  __device__ __forceinline__ double2 get(int64_t row, int64_t kk) const {
+    double2 v;
+    if (kind == 0) {
+      if (opN) return A[row + kk * lda];
+      v = A[kk + row * lda];
+    } else {
+      const double* c = colp + kk;
+      v = kernel_value(type, wn, rp[0], rp[1], rp[2], c[0], c[coln], c[2 * coln]);
+      if (opN) return v;
+    }
+    v.y = -v.y;
+    return v;
+  }
+};
+
+}  // namespace dev
+}  // namespace bf

@@ -54,7 +54,11 @@ def test_batch_equals_individual(precision, tol):
             assert np.array_equal(F.ranks(1, j), Fi.ranks(1, j))
         x = inputs.random_rhs(p.n, 3, seed=p.n)
         yb, yi = H(F.apply(T(x))), H(Fi.apply(T(x)))
-        assert np.linalg.norm(yb - yi) <= 1e-13 * np.linalg.norm(yi)
+        # FP64: identical arithmetic per block.  Mixed: the tensor-core sketch
+        # splits K across CTAs according to the launch's total tile count, so
+        # a batch sums in another order -- equal to FP32 rounding
+        agree = 1e-13 if precision == "fp64" else 2e-6
+        assert np.linalg.norm(yb - yi) <= agree * np.linalg.norm(yi)
         assert F.error(op, 16, seed=2) <= 2 * math.sqrt(p.L + 2) * tol
 
 
