@@ -131,6 +131,60 @@ def profile_case(args):
     print("profile case done")
 
 
+def serving_measure(seconds: float = 4.0):
+    """Serving: resident factorizations (arcs n = 4096 and 16384, caps
+    n = 4096), Poisson requests (80% applies of 1..64 complex64/complex128
+    right-hand sides, 20% factor requests n in {4096, 16384} on arcs/caps)
+    at 0.5x and 2x the capacity of a one-request-at-a-time plain FP64
+    baseline; p50/p99 latency and applies/s of both."""
+    import torch
+    from paper_2002_03400_gb300 import inputs, serve
+    sizes = {"arc4k": (4096, "arc"), "arc16k": (16384, "arc"), "cap4k": (4096, "cap")}
+    res = {k: serve.build_factor(serve.factor_spec(n, geo, seed=i)) for i, (k, (n, geo)) in enumerate(sizes.items())}
+    names = list(res)
+    nof = {k: sizes[k][0] for k in res}
+
+    def baseline(jobs):
+        """one request at a time, FP64 factors and complex128 products"""
+        t0 = time.perf_counter()
+        for j in jobs:
+            while time.perf_counter() - t0 < j.t_arrive:
+                time.sleep(0.0002)
+            if j.kind == "apply":
+                x = torch.from_numpy(j.x.astype(np.complex128)).cuda()
+                j.result = res[j.target].apply(x).cpu().numpy()
+            else:
+                spec = dict(j.spec, precision="fp64")
+                j.result = serve.build_factor(spec)
+                j.result.free()
+            torch.cuda.synchronize()
+            j.t_done = time.perf_counter() - t0
+        return jobs
+
+    # capacity of the baseline: mean service time on a short sample
+    probe = serve.make_jobs(inputs.serving_trace(1.0, 40.0, seed=11, resident=3, factor_sizes=(4096, 16384)),
+                            names, nof, seed=5)
+    for j in probe:
+        j.t_arrive = 0.0
+    t0 = time.perf_counter()
+    baseline(probe)
+    cap = len(probe) / (time.perf_counter() - t0)
+    out = {"baseline_capacity_req_per_s": cap, "seconds": seconds}
+    for mult in (0.5, 2.0):
+        rate = cap * mult
+        tr = inputs.serving_trace(seconds, rate, seed=21, resident=3, factor_sizes=(4096, 16384))
+        jobs = serve.make_jobs(tr, names, nof, seed=6)
+        srv = serve.Server(mem_cap=150e9, factor_workers=2)
+        for k, F in res.items():
+            srv.add_resident(k, F)
+        done = srv.run(jobs, realtime=True)
+        srv.close()
+        bjobs = baseline(serve.make_jobs(tr, names, nof, seed=6))
+        out[f"rate_{mult}x"] = {"rate_req_per_s": rate, "requests": len(jobs),
+                                "served": serve.latency_stats(done), "baseline": serve.latency_stats(bjobs)}
+    return out
+
+
 def run_reference(args):
     """--impl reference: the FP64 oracle on the host cores, bounded sample."""
     rank = int(os.environ.get("RANK", "0"))
@@ -161,6 +215,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--profile-case", choices=["sketch", "apply", "qr"], default=None,
                     help="run only a small case of one kernel family (for ncu captures)")
     ap.add_argument("--engine", default="tensor")
@@ -303,6 +358,7 @@ def main():
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
 
+    serving = serving_measure() if not args.no_serve else None
     peaks, peak_src = measured_peaks()
     clocks = clk.summary()
     line = {
@@ -331,6 +387,7 @@ def main():
                 "d2h_bytes_per_step": int(ye.numel() * 8)},
         "clocks": clocks,
         "peaks_source": peak_src,
+        "serving": serving,
         "roofline": {"kernel": "sketch_gemm_kernel<float> (entries on the fly)", "bound": "alu",
                      "achieved": sk_flops / t_sk / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": sk_flops / t_sk / 1e12 / fp32_peak, "traffic": None,
