@@ -34,6 +34,10 @@ N = 16384
 LEAF = 16
 TOL = 1e-6
 NRHS = 64
+# FP32 operations of one 2-D kernel entry in the mixed path (the float-float
+# formula: distance, rsqrt + Newton, float-float phase, pi/2 reduction,
+# Taylor sin/cos, quadrant and scaling), counted from its source
+ALU_OPS_PER_ENTRY = 99
 
 
 def measured_peaks():
@@ -118,6 +122,18 @@ def profile_case(args):
         X = api.colmajor(torch.from_numpy(inputs.random_rhs(n, 22, seed=3)).to(torch.complex64).cuda())
         for _ in range(3):
             op.apply(X)
+    elif args.profile_case == "step":
+        # the bench step (mixed factorization, apply of 64 right-hand sides,
+        # sketch error), once per --steps
+        g = inputs.line_pair(N)
+        plan = api.Plan(g.src, g.tgt, kernel="helmholtz2d", wavenumber=g.wavenumber, leaf=LEAF, tol=TOL,
+                        precision="mixed")
+        op = api.Operator.kernel(plan)
+        x = torch.from_numpy(inputs.random_rhs(N, NRHS, seed=1)).to(torch.complex64).cuda()
+        for _ in range(args.steps):
+            F = api.Factorization.factor(plan, op)
+            F.apply(x)
+            F.error(op, 16, seed=7, dtype=x.dtype)
     else:
         g = inputs.line_pair(N)
         plan = api.Plan(g.src, g.tgt, kernel="helmholtz2d", wavenumber=g.wavenumber, leaf=LEAF, tol=TOL,
@@ -216,7 +232,7 @@ def main():
     ap.add_argument("--impl", default="gb300")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--profile-case", choices=["sketch", "apply", "qr"], default=None,
+    ap.add_argument("--profile-case", choices=["sketch", "apply", "qr", "step"], default=None,
                     help="run only a small case of one kernel family (for ncu captures)")
     ap.add_argument("--engine", default="tensor")
     args = ap.parse_args()
@@ -278,6 +294,7 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    launches0 = api.launch_count()
     with clk:
         for i in range(args.steps):
             flush.fill_(1.0)
@@ -287,6 +304,7 @@ def main():
             fac_s.append(F.info()["seconds"])
             errs.append(err)
         torch.cuda.synchronize()
+    gpu_launches = api.launch_count() - launches0
     if dist:
         dist.barrier()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
@@ -346,6 +364,11 @@ def main():
         engine_ms[eng] = r0.elapsed_time(r1) / reps
     api.set_sketch_engine("tensor")
     fp32_peak = 152 * 128 * 2 * 2070e6 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
+    alu_peak = 152 * 128 * 2070e6 / 1e12        # FP32 lane operations per second (one per clock)
+    # the standalone product uses the exact three-way split: 6 TF32 products per
+    # real product, 4 real products per complex multiply-add
+    tc_flops = sk_flops * 6
+    tf32_peak = measured_peaks()[0].get("bf16_tflops", 1900.0) * 1.1 / 2.25
 
     # end to end through the C ABI from host buffers
     xh = x32.cpu().pin_memory()
@@ -386,14 +409,20 @@ def main():
         "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(xh.numel() * 8 + 2 * N * 2 * 8),
                 "d2h_bytes_per_step": int(ye.numel() * 8)},
         "clocks": clocks,
+        "gpu_launches": gpu_launches,
+        "gpu_launches_per_step": gpu_launches / max(1, args.steps),
         "peaks_source": peak_src,
         "serving": serving,
-        "roofline": {"kernel": "sketch_gemm_kernel<float> (entries on the fly)", "bound": "alu",
-                     "achieved": sk_flops / t_sk / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
-                     "frac": sk_flops / t_sk / 1e12 / fp32_peak, "traffic": None,
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
-                     "work": f"8*m*n*k flop, m=n={N}, k={kw}; entry formation (~100 FP32 ops/entry) not counted",
-                     "launch_ms": t_sk * 1e3, "engine_ms": engine_ms},
+        "roofline": {"kernel": "sketch_tc_kernel (tcgen05 split-TF32, entries on the fly)", "bound": "alu",
+                     "achieved": ALU_OPS_PER_ENTRY * N * N / t_sk / 1e12, "peak": alu_peak, "unit": "Tops/s",
+                     "frac": ALU_OPS_PER_ENTRY * N * N / t_sk / 1e12 / alu_peak, "traffic": None,
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz (one op per lane per clock)",
+                     "work": f"{ALU_OPS_PER_ENTRY} FP32 ops per kernel entry (the float-float entry formula), "
+                             f"m=n={N} entries; the {kw}-column product runs on the tensor pipe",
+                     "launch_ms": t_sk * 1e3, "engine_ms": engine_ms,
+                     "tensor_pipe": {"achieved_tflops": tc_flops / t_sk / 1e12, "peak_tflops": tf32_peak,
+                                     "frac": tc_flops / t_sk / 1e12 / tf32_peak,
+                                     "peak_source": "measured bf16 x 1.1/2.25 (nominal tf32/bf16 ratio)"}},
     }
     if rank == 0 and not args.no_cpu:
         raw, scaled, cores = cpu_oracle_sample()

@@ -277,6 +277,12 @@ void bf_free(void* handle);
 /* Reason for the last failure on this thread ("" if none). */
 const char* bf_last_error(void);
 
+/* Number of kernels this library has launched in this process so far
+ * (all threads, all devices; monotone).  Diagnostic: the difference of two
+ * readings around a region is the number of library kernels launched in it.
+ * Never fails. */
+unsigned long long bf_launch_count(void);
+
 /* Device-side Gaussian test/sketch matrix of the counter-based generator:
  * G[i, c - col0] for rows row0..row0+rows-1, columns col0..col1-1 of
  * (seed, stream) into a device buffer (ld >= rows), dtype C64/C128. */

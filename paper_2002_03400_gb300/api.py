@@ -80,6 +80,7 @@ def lib():
         "bf_error": (i32, [vp, vp, i32, C.c_uint64, i32, vp, C.POINTER(dbl)]),
         "bf_free": (None, [vp]),
         "bf_set_sketch_engine": (i32, [i32]),
+        "bf_launch_count": (C.c_ulonglong, []),
         "bf_gaussian": (i32, [C.c_uint64, C.c_uint32, i64, i64, i64, i64, vp, i64, i32, vp]),
     }
     for name, (res, args) in sig.items():
@@ -97,7 +98,12 @@ def exported_symbols():
             "bf_operator_callback", "bf_operator_apply", "bf_operator_counts", "bf_factor",
             "bf_factor_batch", "bf_apply",
             "bf_apply_T", "bf_apply_noalloc", "bf_ranks", "bf_fact_info", "bf_fact_import", "bf_fact_export", "bf_error",
-            "bf_free", "bf_gaussian", "bf_set_sketch_engine"]
+            "bf_free", "bf_gaussian", "bf_set_sketch_engine", "bf_launch_count"]
+
+
+def launch_count() -> int:
+    """Kernels the library has launched in this process so far."""
+    return int(lib().bf_launch_count())
 
 
 def set_sketch_engine(engine: str):

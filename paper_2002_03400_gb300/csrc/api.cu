@@ -3,6 +3,7 @@
 // metric of Sec. 7 and factor import/export.
 #include <algorithm>
 #include <cmath>
+#include <atomic>
 #include <cstring>
 #include <numeric>
 
@@ -292,6 +293,10 @@ int upload(MemTracker* mt, DevBuf& b, const void* src, size_t bytes) {
 }
 
 }  // namespace
+
+static std::atomic<unsigned long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+unsigned long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 }  // namespace bf
 
 using namespace bf;
@@ -570,6 +575,8 @@ int bf_factor(bf_plan plan, bf_operator A, void* stream, bf_fact* out) {
 }
 
 int bf_set_sketch_engine(int engine) { return set_sketch_engine(engine); }
+
+unsigned long long bf_launch_count(void) { return bf::launches_so_far(); }
 
 int bf_factor_batch(int count, const bf_plan* plans, const bf_operator* ops, void* stream, bf_fact* out) {
   if (!out || !plans || count < 1) return fail(BF_EINVAL, "bad batch arguments");

@@ -276,6 +276,9 @@ bool sketch_tc_applies(const std::vector<SketchJob>& jobs);
 int launch_sketch_jobs_tc(const std::vector<SketchJob>& jobs, MemTracker* mt, cudaStream_t s);
 // BF_ETIMEOUT if a tensor-core kernel's bounded wait gave up since the last reset
 int tc_status(bool reset);
+// counts one kernel launch of this library (bf_launch_count)
+void note_launch();
+unsigned long long launches_so_far();
 // 0: tensor-core sketch where it applies (default), 1: SIMT sketch only
 int set_sketch_engine(int e);
 struct GemmGroups;

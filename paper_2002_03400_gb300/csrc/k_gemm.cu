@@ -198,6 +198,7 @@ int launch_sketch_jobs_simt(const std::vector<SketchJob>& jobs, int dtype, MemTr
   const SketchTile* dt = (const SketchTile*)((char*)d.p + jb);
   const unsigned nt = (unsigned)tiles.size();
   if (!rc) {
+    note_launch();
     if (dtype == BF_C128) {
       if (GN == 64)
         sketch_job_kernel<double, 64><<<nt, GT, 0, s>>>(dj, dt);

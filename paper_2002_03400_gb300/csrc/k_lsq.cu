@@ -135,6 +135,7 @@ int launch_lsq(const LSQTask* d_tasks, int ntasks, int maxS, int maxK, int maxR,
   if (ntasks <= 0) return BF_OK;
   const size_t smem = (size_t)2 * maxK * maxR * sizeof(double2) + (size_t)maxR * (2 * sizeof(double) + sizeof(double2));
   if (smem > 220 * 1024) return fail(BF_EUNSUPPORTED, "B least-squares block too large for shared memory");
+  note_launch();
   if (in_dtype == BF_C128) {
     BF_CUDA_TRY(cudaFuncSetAttribute(lsq_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     lsq_kernel<double2><<<ntasks, LSQ_THREADS, smem, s>>>(d_tasks, maxK, maxR);

@@ -70,6 +70,7 @@ int launch_gaussian(uint64_t seed, uint32_t sid, int64_t row0, int64_t rows,
   if (rows <= 0 || col1 <= col0) return BF_OK;
   const int64_t npairs = ((row0 + rows + 1) >> 1) - (row0 >> 1);
   const int g = grid_for(npairs * (col1 - col0));
+  note_launch();
   if (dtype == BF_C128)
     gaussian_kernel<double><<<g, 256, 0, s>>>(seed, sid, row0, rows, col0, col1 - col0,
                                               (double2*)out, ld);
@@ -104,6 +105,7 @@ int launch_gather_rows(const int64_t* d_perm, int64_t rows, int64_t cols,
                        int conj, int dtype, cudaStream_t s) {
   if (rows <= 0 || cols <= 0) return BF_OK;
   const int g = grid_for(rows * cols);
+  note_launch();
   if (dtype == BF_C128)
     permute_rows_kernel<double2, false><<<g, 256, 0, s>>>(d_perm, rows, cols, (const double2*)in, ldi,
                                                            (double2*)out, ldo, conj);
@@ -119,6 +121,7 @@ int launch_scatter_rows(const int64_t* d_perm, int64_t rows, int64_t cols,
                         int conj, int dtype, cudaStream_t s) {
   if (rows <= 0 || cols <= 0) return BF_OK;
   const int g = grid_for(rows * cols);
+  note_launch();
   if (dtype == BF_C128)
     permute_rows_kernel<double2, true><<<g, 256, 0, s>>>(d_perm, rows, cols, (const double2*)in, ldi,
                                                           (double2*)out, ldo, conj);
@@ -152,6 +155,7 @@ int launch_expand_structured(int groups, const int64_t* d_off, int64_t rows, int
                              const void* in, int64_t ldi, void* out, int64_t ldo,
                              int dtype, cudaStream_t s) {
   const int g = grid_for(rows * k * groups);
+  note_launch();
   if (dtype == BF_C128)
     expand_kernel<double2><<<g, 256, 0, s>>>(groups, d_off, rows, k, (const double2*)in, ldi,
                                              (double2*)out, ldo);
@@ -183,6 +187,7 @@ int launch_gather2d(const int64_t* d_rp, const int64_t* d_cp, int64_t rows, int6
                     int out_dtype, cudaStream_t s) {
   if (rows <= 0 || cols <= 0) return BF_OK;
   const int g = grid_for(rows * cols);
+  note_launch();
   if (in_dtype == BF_C128 && out_dtype == BF_C128)
     gather2d_kernel<double2, double2><<<g, 256, 0, s>>>(d_rp, d_cp, rows, cols, (const double2*)in, ldi,
                                                          (double2*)out, ldo);
@@ -219,6 +224,7 @@ int launch_convert(const void* in, void* out, int64_t count, int in_dtype, int o
     BF_CUDA_TRY(cudaMemcpyAsync(out, in, count * elem_bytes(in_dtype), cudaMemcpyDeviceToDevice, s));
     return BF_OK;
   }
+  note_launch();
   if (in_dtype == BF_C128)
     convert_kernel<double2, float2><<<g, 256, 0, s>>>((const double2*)in, (float2*)out, count);
   else
@@ -241,6 +247,7 @@ int launch_conj_inplace(void* p, int64_t rows, int64_t cols, int64_t ld, int dty
                         cudaStream_t s) {
   if (rows <= 0 || cols <= 0) return BF_OK;
   const int g = grid_for(rows * cols);
+  note_launch();
   if (dtype == BF_C128)
     conj_kernel<double2><<<g, 256, 0, s>>>((double2*)p, rows, cols, ld);
   else
@@ -290,6 +297,7 @@ int launch_diff_norms(const void* a, const void* b, int64_t rows, int64_t cols, 
                       int64_t ldb, int dtype, double* d_out, cudaStream_t s) {
   BF_CUDA_TRY(cudaMemsetAsync(d_out, 0, 2 * sizeof(double), s));
   const int g = grid_for(rows * cols);
+  note_launch();
   if (dtype == BF_C128)
     diff_norms_kernel<double2><<<g, 256, 0, s>>>((const double2*)a, (const double2*)b, rows, cols,
                                                  lda, ldb, d_out);

@@ -199,6 +199,7 @@ int launch_qr(const QRTask* d_tasks, int ntasks, int maxS, int maxK, int in_dtyp
     return fail(BF_EINVAL, "QR workspace too small");
   const int64_t stride = (int64_t)(blk / sizeof(double2));
   const int nthr = threads_for(maxK);
+  note_launch();
   if (in_dtype == BF_C128) {
     BF_CUDA_TRY(cudaFuncSetAttribute(qr_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)(QR_SMEM_LIMIT + 4096)));

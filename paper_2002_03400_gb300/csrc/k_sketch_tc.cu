@@ -432,6 +432,7 @@ static int launch_nr(const SketchJob* dj, const TcTile* dt, unsigned ntiles, flo
   static_assert(smem <= 220 * 1024, "sketch tile exceeds shared memory");
   BF_CUDA_TRY(cudaFuncSetAttribute(sketch_tc_kernel<NR, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)smem));
+  note_launch();
   sketch_tc_kernel<NR, SPLIT><<<ntiles, THREADS, smem, s>>>(dj, dt, ws);
   BF_CUDA_TRY(cudaGetLastError());
   return BF_OK;
@@ -516,6 +517,7 @@ int launch_sketch_jobs_tc(const std::vector<SketchJob>& jobs, MemTracker* mt, cu
   if (!rc) rc = split == 3 ? launch_split<3>(nr, dj, dt, nt, (float4*)w.p, s) : launch_split<2>(nr, dj, dt, nt, (float4*)w.p, s);
   if (!rc && !regs.empty()) {
     dim3 grid(64, (unsigned)regs.size());
+    note_launch();
     tc_reduce_kernel<<<grid, 256, 0, s>>>((const TcRegion*)(p + jb + tb), (int)regs.size(), (const float4*)w.p);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) rc = fail(BF_ECUDA, std::string("sketch reduce: ") + cudaGetErrorString(e));

@@ -116,6 +116,7 @@ int launch_stage(const StageTask* d_tasks, int ntasks, int maxM, int maxN, int N
   if (ntasks <= 0 || maxM <= 0 || maxN <= 0) return BF_OK;
   int blocks = (ntasks + WARPS - 1) / WARPS;
   if (blocks > 152 * 16) blocks = 152 * 16;
+  note_launch();
   if (dtype == BF_C128)
     stage_kernel<double><<<blocks, THREADS, 0, s>>>(d_tasks, ntasks, bases, Noverride);
   else

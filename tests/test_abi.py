@@ -20,7 +20,7 @@ def libpath():
 def _declared():
     src = open(os.path.join(ROOT, "include", "butterfly.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:int|void|const char\*)\s+\**(bf_\w+)\s*\(", src, flags=re.M)))
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char\*|unsigned long long)\s+\**(bf_\w+)\s*\(", src, flags=re.M)))
 
 
 def test_header_declares_the_planned_entry_points():
