@@ -264,6 +264,8 @@ struct SketchJob {
   int64_t ldx;
   void* Y;
   int64_t ldy;
+  int64_t ygs;            // Y columns between groups (0: kcols); set when a job is split by columns
+  const int64_t* h_off;   // host copy of d_off (groups + 1 entries) or null
 };
 // Runs all jobs (same dtype) in one launch: one CTA per (job, group, row tile,
 // column tile).  Job and tile lists are uploaded to stream-ordered scratch.

@@ -165,6 +165,7 @@ int sketch_all(Batch& B, const std::vector<SketchReq>& reqs) {
       // truncation tolerance is well above it; tighter tolerances take the
       // exact three-way split (FP32-level products)
       j.split = P->tol < 5e-6 ? 3 : 2;
+      j.h_off = (opN ? P->offS[q.level] : P->offT[q.level]).data();
       jobs.push_back(j);
     } else
       BF_TRY(sketch_one(B, q));

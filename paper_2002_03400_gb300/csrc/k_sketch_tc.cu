@@ -9,21 +9,27 @@
 //   SPLIT 2 (3xTF32):  a0 b0 + a0 b1 + a1 b0                 (~2^-21 relative)
 //   SPLIT 3 (6 terms): ... + a0 b2 + a1 b1 + a2 b0, the split exact (~FP32)
 //
-// Per CTA (one job, one group, 128 rows, one K range, all 2k real columns):
-//   * 16 warps form the entries of a K chunk (the float-float formulas of
-//     kentry.cuh, or loads of a stored complex64 A) and write their TF32
-//     parts straight into one of two shared-memory A buffers (K-major,
-//     no-swizzle core-matrix layout: 8 rows x 16 B per core matrix, 128 B
-//     between K-adjacent, 8*KCH B between 8-row groups) while the tensor
-//     core works on the previous chunk;
-//   * the next chunk's rows of X are staged with cp.async meanwhile;
-//   * after the previous chunk's MMAs complete (mbarrier, bounded wait),
-//     warps 0-3 move the FP32 accumulator from tensor memory into a
+// Per CTA (one job, one group, 128 rows, one K range, all 2k real columns),
+// K advances in chunks of 16 complex columns through double-buffered shared
+// memory, with one CTA barrier per chunk:
+//   * every thread forms 4 consecutive entries of one row (the float-float
+//     formulas of kentry.cuh on column points staged in shared memory, or
+//     loads of a stored complex64 A), splits them into TF32 parts and writes
+//     each part with one 16-byte store into the K-major, no-swizzle
+//     core-matrix layout (8 rows x 16 B per core matrix; 8 lanes fill one
+//     core matrix, so stores are free of bank conflicts);
+//   * the B operand [[Xr, Xi], [-Xi, Xr]] of the chunk is built from X rows
+//     staged by cp.async two chunks ahead (column stride padded by 16 B so
+//     the 16-byte loads of 8 lanes hit distinct banks);
+//   * one thread waits (bounded) for the previous chunk's MMAs, then after
+//     the barrier issues this chunk's tcgen05.mma (M = 128, N = 2k, K = 8)
+//     and commits them to an mbarrier; the a0*b0 products accumulate in one
+//     tensor-memory accumulator, the cross terms (~2^-11 smaller) in a
+//     second one over the whole K range;
+//   * every 64 complex K all 16 warps move the main accumulator into a
 //     (hi, lo) pair kept in tensor memory with Knuth's TwoSum (so sums over
-//     n = 16384 points keep FP32 accuracy), the B operand
-//     [[Xr, Xi], [-Xi, Xr]] parts are built from the staged rows, and one
-//     thread issues the chunk's tcgen05.mma (M = 128, N = 2k, K = 8) and
-//     commits them to the mbarrier;
+//     n = 16384 points keep FP32 accuracy); the correction accumulator is
+//     added to lo once, at the end;
 //   * launches with few row tiles split K across CTAs; partial (hi, lo)
 //     sums go to a workspace and a second kernel adds them with TwoSum;
 //   * a wait that exceeds 1 s of %globaltimer records a device flag
@@ -41,9 +47,17 @@ using namespace dev;
 __device__ int g_tc_status;   // 1 once a bounded wait has given up
 
 namespace {
-constexpr int TM = 128;        // rows per CTA (MMA M)
-constexpr int THREADS = 512;
-constexpr uint32_t CORE = 128; // bytes of one 8 x 16 B core matrix
+constexpr int TM = 128;            // rows per CTA (MMA M)
+constexpr int NWARP = 8;           // producer warps (entries, B operand, staging, drains)
+constexpr int ISSUER_WARP = 0;     // 1: a ninth warp waits for and issues the MMAs; 0: thread 0 does
+constexpr int THREADS = 32 * (NWARP + ISSUER_WARP);
+constexpr int XS = 2;              // buffers of staged X rows and points (prefetch depth)
+constexpr uint32_t CORE = 128;     // bytes of one 8 x 16 B core matrix
+constexpr int NR_MAX = 96;         // widest tile: 48 complex columns
+
+// entry kinds of a job
+constexpr int EK_DENSE = 0, EK_H2D = 1, EK_H3D = 2, EK_DFT = 3;
+__device__ __forceinline__ int point_arrays(int ek) { return ek == EK_H3D ? 6 : ek == EK_H2D ? 4 : ek == EK_DFT ? 2 : 0; }
 
 struct TcTile {
   int32_t job, group;
@@ -57,18 +71,59 @@ struct TcRegion {              // one (job, group) region to reduce
   float2* Y;
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-template <int KR>
-__device__ __forceinline__ uint32_t kmaj(int row, int kr) {
-  return (uint32_t)((row >> 3) * (KR / 4) * CORE + (kr >> 2) * CORE + (row & 7) * 16 + (kr & 3) * 4);
+// tensor-memory columns: two main accumulators [0, NR) and [NR, 2NR) (the
+// a0*b0 products of alternate groups of DR chunks, so one is drained while
+// the other accumulates), the correction accumulator [2NR, 3NR) (the cross
+// terms, ~2^-11 smaller, so their roundings do not reach the total), and
+// the TwoSum pair hi [3NR, 4NR), lo [4NR, 5NR); a power of two with 16
+// spare columns for the epilogue's last 16-column slice (it may pass the
+// end of lo by 8)
+__host__ __device__ constexpr int tmem_cols(int nr) {
+  return 5 * nr + 16 <= 32 ? 32 : 5 * nr + 16 <= 64 ? 64 : 5 * nr + 16 <= 128 ? 128 : 5 * nr + 16 <= 256 ? 256 : 512;
 }
+static_assert(5 * NR_MAX + 16 <= 512, "accumulators of the widest tile fit in tensor memory");
+
+// Shape of one tile configuration: K advances in chunks of KCH complex
+// columns (8 with the three-way split, 16 with 3xTF32); S stages of the A
+// and B operands (the MMAs of a chunk may run while the next S-1 chunks are
+// formed); XS buffers of staged X rows and column points.  Shared memory
+// in byte offsets.
+template <int NR, int SPLIT>
+struct Cfg {
+  static constexpr int KCH = SPLIT == 3 ? 8 : 16;
+  static constexpr int KR = 2 * KCH;           // real K per chunk: real parts of A, then imaginary parts
+  static constexpr int KG = KR / 4;            // core matrices along K
+  static constexpr int G = KCH / 4;            // groups of 4 columns per chunk
+  static constexpr int PT = G / 2;             // groups per thread per chunk
+  static constexpr int DR = 64 / KCH;          // chunks between drains of a main accumulator (64 complex K)
+  static constexpr int KP = NR / 2;
+  static constexpr bool TWO = tmem_cols(NR) <= 256;   // two CTAs per SM fit in tensor memory
+  static constexpr uint32_t XCOL = KCH * 8 + 16;      // bytes per staged X column (16 B pad)
+  static constexpr uint32_t A_PART = TM * KR * 4, A_BUF = SPLIT * A_PART;
+  static constexpr uint32_t B_PART = NR * KR * 4, B_BUF = SPLIT * B_PART;
+  static constexpr uint32_t X_BUF = KP * XCOL, P_BUF = 6 * KCH * 4;
+  static constexpr uint32_t LIMIT = TWO ? 112 * 1024 : 226 * 1024;   // per CTA, static part aside
+  static constexpr uint32_t total(int s) { return s * (A_BUF + B_BUF) + XS * (X_BUF + P_BUF); }
+  static constexpr int S = total(4) <= LIMIT ? 4 : total(3) <= LIMIT ? 3 : 2;
+  static constexpr uint32_t A0 = 0, B0 = S * A_BUF, X0 = B0 + S * B_BUF, P0 = X0 + XS * X_BUF;
+  static constexpr uint32_t TOTAL = P0 + XS * P_BUF;
+  // one CTA per SM for wide tiles (their tensor memory is the SM's)
+  static constexpr uint32_t LAUNCH_SMEM = TWO ? TOTAL : (TOTAL > 120 * 1024 ? TOTAL : 120 * 1024);
+  static constexpr int IW = NR * KG / NWARP;   // B items per warp
+  static constexpr int BIT = (IW + 31) / 32;
+  static constexpr int XW = KP * KCH / NWARP;  // X copies per warp
+  static constexpr int XIT = (XW + 31) / 32;
+  static_assert(TOTAL <= LIMIT, "tile exceeds shared memory");
+  static_assert(IW % 8 == 0 && S - 2 < DR, "B items by 8-lane groups; drains before reuse");
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 // shared-memory matrix descriptor: start, LBO (K-adjacent core matrices),
 // SBO (8-row groups), in 16-byte units; version 1 at bits 46-47; no swizzle
-template <int KR>
+template <int KG>
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
-  constexpr uint32_t SBO = (KR / 4) * CORE;
+  constexpr uint32_t SBO = KG * CORE;
   return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((CORE >> 4) & 0x3FFFu) << 16) |
          ((uint64_t)((SBO >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
 }
@@ -79,22 +134,46 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int n) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 }
 
-__device__ __forceinline__ uint32_t tf32_bits(float x) {
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
   return r;
 }
 
+// TF32 parts of four values.  SPLIT 3: truncation to the leading 11
+// significant bits twice; x = p0 + p1 + p2 exactly (x - p0 has at most 13
+// significant bits, its remainder at most 2), every part a valid TF32 value.
+// SPLIT 2: round-to-nearest parts, x - p0 - p1 ~ 2^-22 |x|.
 template <int SPLIT>
-__device__ __forceinline__ void split_parts(float x, uint32_t (&p)[3]) {
-  p[0] = tf32_bits(x);
-  const float r1 = x - __uint_as_float(p[0]);
-  p[1] = tf32_bits(r1);
-  if (SPLIT == 3) p[2] = tf32_bits(r1 - __uint_as_float(p[1]));
+__device__ __forceinline__ void split4(const float (&x)[4], uint4 (&p)[3]) {
+  uint32_t a[4], b[4], c[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (SPLIT == 3) {
+      a[j] = __float_as_uint(x[j]) & 0xFFFFE000u;
+      const float r1 = x[j] - __uint_as_float(a[j]);
+      b[j] = __float_as_uint(r1) & 0xFFFFE000u;
+      c[j] = __float_as_uint(r1 - __uint_as_float(b[j]));
+    } else {
+      a[j] = tf32_rna(x[j]);
+      b[j] = tf32_rna(x[j] - __uint_as_float(a[j]));
+      c[j] = 0u;
+    }
+  }
+  p[0] = make_uint4(a[0], a[1], a[2], a[3]);
+  p[1] = make_uint4(b[0], b[1], b[2], b[3]);
+  p[2] = make_uint4(c[0], c[1], c[2], c[3]);
 }
 
-__device__ __forceinline__ void st_shared(uint32_t addr, uint32_t v) {
-  asm volatile("st.shared.b32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint4 v) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+               : "memory");
+}
+__device__ __forceinline__ float4 ld_shared_v4(uint32_t addr) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr)
+               : "memory");
+  return v;
 }
 
 __device__ __forceinline__ uint64_t now_ns() {
@@ -146,76 +225,121 @@ __device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t a, uint64_t b,
       : "memory");
 }
 
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(valid ? 4 : 0) : "memory");
+}
 __device__ __forceinline__ void cp_async8(uint32_t dst, const void* src, bool valid) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(valid ? 8 : 0) : "memory");
 }
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory");
-}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// tensor-memory columns: main accumulator [0, NR) (the a0*b0 products),
-// correction accumulator [NR, 2NR) (the cross terms, ~2^-11 smaller, so
-// their roundings do not reach the total), and the TwoSum pair hi
-// [2NR, 3NR), lo [3NR, 4NR); a power of two >= 32 with 16 spare columns for
-// the epilogue's last 16-column slice (it may pass the end of lo by 8)
-__host__ __device__ constexpr int tmem_cols(int nr) {
-  return 4 * nr + 16 <= 32 ? 32 : 4 * nr + 16 <= 64 ? 64 : 4 * nr + 16 <= 128 ? 128 : 4 * nr + 16 <= 256 ? 256 : 512;
-}
-static_assert(4 * 128 + 8 <= 512 + 8, "epilogue reads stay inside 512 columns for NR = 128 (KP = 64)");
-
-template <int SPLIT>
-__host__ __device__ constexpr int kch() { return SPLIT == 3 ? 16 : 32; }   // complex K per chunk
-
-template <int NR, int SPLIT>
-constexpr size_t smem_bytes() {
-  constexpr int KR = 2 * kch<SPLIT>();
-  return 2 * (size_t)SPLIT * TM * KR * 4       // A, two buffers
-         + (size_t)SPLIT * NR * KR * 4         // B
-         + (size_t)kch<SPLIT>() * (NR / 2) * 8;// staged X rows
-}
 }  // namespace
 
-// TwoSum the main accumulator into the pair (hi, lo) and add the correction
-// accumulator to lo, for this warp's 32 lanes (warps 0-3 only).
-template <int NR>
-__device__ __forceinline__ void drain(uint32_t tlane) {
+// This thread's row of the tile: its point (float-float, in registers), the
+// wavenumber, the sign of imaginary parts (exp(-i k r) in 2D; conjugation
+// for the adjoint) and, for stored operators, the matrix.
+struct RowCtx {
+  float rp[6];
+  float kh, kl, isg;
+  const float2* A;
+  int64_t lda;
+  int opN;
+};
+
+// Four entries of row gi at columns gk0 .. gk0+3 (kernel entries use the
+// chunk's column points staged at pts: array d at pts + ps d bytes).
+// Columns at or past kend are not read (their entries are zeroed by the caller).
+__device__ __forceinline__ void form4(int ek, const RowCtx& R, uint32_t pts, uint32_t ps, int64_t gi,
+                                      int64_t gk0, int64_t kend, float (&re)[4], float (&im)[4]) {
+  if (ek == EK_DENSE) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t gk = gk0 + j < kend ? gk0 + j : kend - 1;
+      const float2 v = R.opN ? R.A[gi + gk * R.lda] : R.A[gk + gi * R.lda];
+      re[j] = v.x;
+      im[j] = v.y * R.isg;
+    }
+    return;
+  }
+  const float4 xh = ld_shared_v4(pts), xl = ld_shared_v4(pts + ps);
+  const float cxh[4] = {xh.x, xh.y, xh.z, xh.w}, cxl[4] = {xl.x, xl.y, xl.z, xl.w};
+  if (ek == EK_DFT) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float2 v = dft_ff(R.rp[0], R.rp[1], cxh[j], cxl[j]);
+      re[j] = v.x;
+      im[j] = v.y * R.isg;
+    }
+    return;
+  }
+  const float4 yh = ld_shared_v4(pts + 2 * ps), yl = ld_shared_v4(pts + 3 * ps);
+  const float cyh[4] = {yh.x, yh.y, yh.z, yh.w}, cyl[4] = {yl.x, yl.y, yl.z, yl.w};
+  if (ek == EK_H2D) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float2 v = helmholtz_ff<false>(R.rp, cxh[j], cxl[j], cyh[j], cyl[j], 0.f, 0.f, R.kh, R.kl);
+      re[j] = v.x;
+      im[j] = v.y * R.isg;
+    }
+    return;
+  }
+  const float4 zh = ld_shared_v4(pts + 4 * ps), zl = ld_shared_v4(pts + 5 * ps);
+  const float czh[4] = {zh.x, zh.y, zh.z, zh.w}, czl[4] = {zl.x, zl.y, zl.z, zl.w};
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float2 v = helmholtz_ff<true>(R.rp, cxh[j], cxl[j], cyh[j], cyl[j], czh[j], czl[j], R.kh, R.kl);
+    re[j] = v.x;
+    im[j] = v.y * R.isg;
+  }
+}
+
+// TwoSum the main accumulator at column moff into the pair (hi, lo) (and,
+// at the end, add the correction accumulator to lo) for this warp's 32
+// tensor-memory lanes; the warps sharing a lane quadrant take alternate
+// 16-column slices.
+template <int NR, bool CORR>
+__device__ __forceinline__ void drain(uint32_t tq, int sub, uint32_t moff) {
 #pragma unroll 1
-  for (int s = 0; s < NR / 16; ++s) {
-    uint32_t d[16], e[16], h[16], l[16];
-    tmem_ld16(tlane + s * 16, d);
-    tmem_ld16(tlane + NR + s * 16, e);
-    tmem_ld16(tlane + 2 * NR + s * 16, h);
-    tmem_ld16(tlane + 3 * NR + s * 16, l);
+  for (int s = sub; s < NR / 16; s += NWARP / 4) {
+    uint32_t d[16], h[16], l[16], e[16];
+    tmem_ld16(tq + moff + s * 16, d);
+    tmem_ld16(tq + 3 * NR + s * 16, h);
+    tmem_ld16(tq + 4 * NR + s * 16, l);
+    if (CORR) tmem_ld16(tq + 2 * NR + s * 16, e);
     tmem_wait_ld();
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
       const FF t = two_sum(__uint_as_float(h[i]), __uint_as_float(d[i]));
       h[i] = __float_as_uint(t.h);
-      l[i] = __float_as_uint(__uint_as_float(l[i]) + (t.l + __uint_as_float(e[i])));
+      const float add = CORR ? t.l + __uint_as_float(e[i]) : t.l;
+      l[i] = __float_as_uint(__uint_as_float(l[i]) + add);
     }
-    tmem_st16(tlane + 2 * NR + s * 16, h);
-    tmem_st16(tlane + 3 * NR + s * 16, l);
+    tmem_st16(tq + 3 * NR + s * 16, h);
+    tmem_st16(tq + 4 * NR + s * 16, l);
   }
   tmem_wait_st();
 }
 
 template <int NR, int SPLIT>
-__global__ void __launch_bounds__(THREADS, 1)
+__global__ void __launch_bounds__(THREADS, 2)
 sketch_tc_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__ tiles, float4* __restrict__ ws) {
-  extern __shared__ __align__(1024) uint8_t smem[];
-  constexpr int KCH = kch<SPLIT>(), KR = 2 * KCH, KP = NR / 2;
+  using C = Cfg<NR, SPLIT>;
+  constexpr int S = C::S, KCH = C::KCH, KG = C::KG, G = C::G, DR = C::DR, KP = C::KP;
   constexpr int COLS = tmem_cols(NR);
-  constexpr uint32_t A_PART = TM * KR * 4, A_BUF = SPLIT * A_PART, B_PART = NR * KR * 4;
-  constexpr int EPT = KCH * TM / THREADS;        // entries per thread per chunk
+  extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ SketchJob J;
   __shared__ TcTile T;
-  __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t mbar[S];   // MMA completion of chunks c with c % S = s
   __shared__ uint32_t tmem_slot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
     T = tiles[blockIdx.x];
     J = jobs[T.job];
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1) : "memory");
+    for (int s = 0; s < S; ++s)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[s])), "r"(1) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -228,152 +352,268 @@ sketch_tc_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__ 
   __syncthreads();
   tc_fence_after();
   const uint32_t tm = tmem_slot;
-  const uint32_t tlane = tm + ((uint32_t)(warp & 3) * 32u << 16);
-  if (warp < 4) {
+  // tensor memory: warp w reaches lanes 32 (w % 4) .. + 31; the two warps of
+  // a lane quadrant share its column slices
+  const bool producer = warp < NWARP, issuer = tid == 32 * NWARP * ISSUER_WARP;
+  const int quad = warp & 3, sub = warp >> 2;
+  const uint32_t tq = tm + ((uint32_t)(quad * 32) << 16);
+  if (producer) {
     uint32_t z[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) z[i] = 0u;
 #pragma unroll 1
-    for (int s = 0; s < 2 * NR / 16; ++s) tmem_st16(tlane + 2 * NR + s * 16, z);
+    for (int s = sub; s < 2 * NR / 16; s += 2) tmem_st16(tq + 3 * NR + s * 16, z);
     tmem_wait_st();
   }
 
-  const int64_t row0 = T.row0, M = J.M, kcols = J.kcols;
+  const int64_t row0 = T.row0, M = J.M, kcols = J.kcols, ygs = J.ygs;
   // K range: this CTA's split, or the whole group
   const int64_t k0 = T.k0 >= 0 ? T.k0 : (J.d_off ? J.d_off[T.group] : 0);
   const int64_t k1 = T.k0 >= 0 ? T.k1 : (J.d_off ? J.d_off[T.group + 1] : J.Ktot);
   const float2* __restrict__ X = (const float2*)J.X;
   const int64_t ldx = J.ldx;
-  const uint32_t aBase = smem_u32(smem), bBase = aBase + 2 * A_BUF, xBase = bBase + SPLIT * B_PART;
-  const float2* xs = (const float2*)(smem + 2 * A_BUF + SPLIT * B_PART);
-  constexpr uint32_t idesc = idesc_tf32(NR);
   const int nch = (int)((k1 - k0 + KCH - 1) / KCH);
-  // entry mapping: warp w forms rows 8w..8w+7, lane l row 8w + l/4 at K
-  // offsets 4j + l%4, so every store of a warp fills one 128-byte core
-  // matrix (no shared-memory bank conflicts)
-  const int r = 8 * warp + (lane >> 2), kq = lane & 3;
-  const int64_t gi = row0 + r;
-  const uint32_t a_off = (uint32_t)warp * (KR / 4) * CORE + (uint32_t)(lane >> 2) * 16 + (uint32_t)kq * 4;
-  constexpr int DR = KCH >= 64 ? 1 : 64 / KCH;   // chunks between accumulator drains (64 complex K)
-  Entry<float> en;   // this thread's row of every chunk, in registers
-  en.init(J, gi, gi < M);
+  const uint32_t sb = smem_u32(smem);
 
-  auto stage_x = [&](int c) {   // rows k0 + c*KCH .. of X, KP columns, zero filled
+  // entry kind and this thread's row context
+  const int opN = J.op == BF_OP_N;
+  const int ek = J.kind == 0 ? EK_DENSE
+                 : J.ktype == BF_KERNEL_HELMHOLTZ_2D ? EK_H2D
+                 : J.ktype == BF_KERNEL_HELMHOLTZ_3D ? EK_H3D
+                                                     : EK_DFT;
+  const int npt = point_arrays(ek);
+  // producer mapping: warp w forms rows 16w .. 16w+15; each 8-lane group
+  // fills one core matrix (8 rows x 4 columns) per store; a thread's groups
+  // of 4 columns are kg0, kg0 + 2, ...
+  const int prow = 16 * warp + (lane & 7) + 8 * ((lane >> 4) & 1), kg0 = (lane >> 3) & 1;
+  const int64_t gi = row0 + prow;
+  const bool rvalid = producer && gi < M;
+  const uint32_t a_st = (uint32_t)(prow >> 3) * KG * CORE + (uint32_t)(prow & 7) * 16;
+  RowCtx R;
+  {
+    const float* rowp = opN ? J.tgtF : J.srcF;
+    const int64_t rown = opN ? J.m : J.n;
+#pragma unroll
+    for (int d = 0; d < 6; ++d) R.rp[d] = (d < npt && rvalid) ? rowp[d * rown + gi] : 0.f;
+    R.kh = J.kh;
+    R.kl = J.kl;
+    R.opN = opN;
+    R.A = (const float2*)J.A;
+    R.lda = J.lda;
+    // imaginary sign: exp(-i k r) in 2D, then conjugation for the adjoint
+    const float base = ek == EK_H2D ? -1.f : 1.f;
+    R.isg = opN ? base : -base;
+  }
+  const float* colp = opN ? J.srcF : J.tgtF;
+  const int64_t coln = opN ? J.n : J.m;
+
+  // B operand items of this thread: item (nr, kg) = 4 consecutive K of row
+  // nr; packed as B offset | X offset << 16 | (reads imaginary parts) << 30
+  // | (negated) << 31; all-ones for none
+  uint32_t bdesc[C::BIT];
+#pragma unroll
+  for (int q = 0; q < C::BIT; ++q) {
+    const int li = lane + 32 * q, it = warp * C::IW + li;
+    const int nr = ((it / (8 * KG)) << 3) | (it & 7), kg = (it >> 3) & (KG - 1);
+    const int part = kg >= G ? 1 : 0;          // 0: rows of Ar, 1: rows of Ai
+    const int kk0 = (kg & (G - 1)) * 4;
+    const int col = nr % KP, blk = nr / KP;    // blk 0: a column of Yr, 1: of Yi
+    // B = [[Xr, Xi], [-Xi, Xr]]: (part, blk) = (0,0) Xr, (0,1) Xi, (1,0) -Xi, (1,1) Xr
+    const uint32_t im = (uint32_t)((part ^ blk) & 1), neg = (part == 1 && blk == 0) ? 1u : 0u;
+    const uint32_t o = (uint32_t)(nr >> 3) * KG * CORE + (uint32_t)kg * CORE + (uint32_t)(nr & 7) * 16;
+    const uint32_t xo = (uint32_t)col * C::XCOL + (uint32_t)kk0 * 8;
+    bdesc[q] = li < C::IW ? (o | (xo << 16) | (im << 30) | (neg << 31)) : 0xFFFFFFFFu;
+  }
+
+  // rows kb .. kb+KCH-1 of X (columns < KP, zero filled) and of the column
+  // point arrays into buffer c % XS; one cp.async group per chunk (empty
+  // past the end), so that waiting for all but the newest XS-2 groups
+  // completes the next chunk
+  auto stage = [&](int c) {
+    if (!producer || c >= nch) {
+      cp_async_commit();
+      return;
+    }
     const int64_t kb = k0 + (int64_t)c * KCH;
-    for (int idx = tid; idx < KCH * KP; idx += THREADS) {
-      const int kk = idx % KCH, col = idx / KCH;
+    const uint32_t xb = sb + C::X0 + (uint32_t)(c % XS) * C::X_BUF;
+#pragma unroll
+    for (int q = 0; q < C::XIT; ++q) {
+      const int li = lane + 32 * q;
+      if (li >= C::XW) break;
+      const int x = warp * C::XW + li, col = x / KCH, kk = x % KCH;
       const int64_t gk = kb + kk;
       const bool v = gk < k1 && col < kcols;
-      cp_async8(xBase + (uint32_t)(kk * KP + col) * 8, v ? (const void*)(X + gk + (int64_t)col * ldx) : (const void*)X,
-                v);
+      cp_async8(xb + (uint32_t)col * C::XCOL + (uint32_t)kk * 8,
+                v ? (const void*)(X + gk + (int64_t)col * ldx) : (const void*)X, v);
     }
+    const int pidx = lane * NWARP + warp;
+    if (pidx < npt * KCH) {
+      const uint32_t pb = sb + C::P0 + (uint32_t)(c % XS) * C::P_BUF;
+      const int d = pidx / KCH, kk = pidx % KCH;
+      const int64_t gk = kb + kk;
+      const bool v = gk < k1;
+      cp_async4(pb + (uint32_t)(d * KCH + kk) * 4, v ? (const void*)(colp + d * coln + gk) : (const void*)colp, v);
+    }
+    cp_async_commit();
   };
 
-  uint32_t parity = 0;
+  const uint32_t mb0 = smem_u32(&mbar[0]);   // mbar[s] at mb0 + 8 s
+  constexpr uint32_t idesc = idesc_tf32(NR);
+  uint32_t mph = 0;    // bit s: parity of the next phase of mbar[s] to wait for
   bool ok = true;
-  if (nch > 0) stage_x(0);
-  for (int c = 0; c < nch && ok; ++c) {
+  int drained = 0;     // groups of DR chunks whose main accumulator is in (hi, lo)
+  int issued = -1;     // last chunk whose MMAs were issued
+#pragma unroll
+  for (int c = 0; c < XS; ++c) stage(c);
+  cp_async_wait<XS - 1>();
+  __syncthreads();
+  for (int c = 0; c < nch; ++c) {
+    const uint32_t s = (uint32_t)(c % S), xbuf = (uint32_t)(c % XS);
     const int64_t kb = k0 + (int64_t)c * KCH;
-    const uint32_t aBuf = aBase + (uint32_t)(c & 1) * A_BUF;
-    // entries of this chunk, straight into the free A buffer (its last
-    // reader, the MMAs of chunk c-2, completed before chunk c-1 was issued)
+    const uint32_t aB = sb + C::A0 + s * C::A_BUF, bB = sb + C::B0 + s * C::B_BUF;
+    // 1. entries of chunk c into A[s] (its last reader, the MMAs of chunk
+    //    c-S, completed before the previous barrier)
 #pragma unroll
-    for (int q = 0; q < EPT; ++q) {
-      const int kk = 4 * q + kq;
-      const int64_t gk = kb + kk;
-      const float2 e = (gi < M && gk < k1) ? en.get(gi, gk) : make_float2(0.f, 0.f);
-      uint32_t pr[3], pm[3];
-      split_parts<SPLIT>(e.x, pr);
-      split_parts<SPLIT>(e.y, pm);
-      const uint32_t ar = aBuf + a_off + (uint32_t)q * CORE;   // real part: K column kk
-      const uint32_t ai = ar + (KCH / 4) * CORE;               // imaginary part: KCH + kk
+    for (int r = 0; r < C::PT; ++r) {
+      if (!producer) break;
+      const int kg = kg0 + 2 * r;
+      float re[4], im[4];
+      const int64_t gk0 = kb + 4 * kg;
+      form4(ek, R, sb + C::P0 + xbuf * C::P_BUF + 16u * (uint32_t)kg, KCH * 4, rvalid ? gi : row0, gk0, k1, re,
+            im);
+      if (kb + KCH > k1) {   // ragged last chunk: columns past k1 are zero
 #pragma unroll
-      for (int s = 0; s < SPLIT; ++s) {
-        st_shared(ar + s * A_PART, pr[s]);
-        st_shared(ai + s * A_PART, pm[s]);
+        for (int j = 0; j < 4; ++j)
+          if (gk0 + j >= k1) re[j] = 0.f, im[j] = 0.f;
+      }
+      uint4 pr[3], pm[3];
+      split4<SPLIT>(re, pr);
+      split4<SPLIT>(im, pm);
+      const uint32_t ar = aB + a_st + (uint32_t)kg * CORE, ai = ar + (uint32_t)G * CORE;
+#pragma unroll
+      for (int q = 0; q < SPLIT; ++q) {
+        st_shared_v4(ar + q * C::A_PART, pr[q]);
+        st_shared_v4(ai + q * C::A_PART, pm[q]);
       }
     }
-    static_assert(EPT == KCH / 4, "one K column group of four per entry step");
-    if (c > 0) {
-      const bool w = mbar_wait(smem_u32(&mbar), parity);
-      if (__syncthreads_or(!w)) {
-        ok = false;
-        break;
-      }
-      parity ^= 1u;
-      tc_fence_after();
-      if (warp < 4 && c % DR == 0) drain<NR>(tlane);
-    }
-    cp_async_wait_all();
-    __syncthreads();
-    // B = [[Xr, Xi], [-Xi, Xr]] (N x K, K-major) from the staged rows; one
-    // warp instruction per 8 x 4 core matrix
-    constexpr int KC4 = KR / 4;
-    for (int cell = warp; cell < (NR / 8) * KC4; cell += THREADS / 32) {
-      const int nr = 8 * (cell / KC4) + (lane >> 2), kr = 4 * (cell % KC4) + kq;
-      const int kk = kr % KCH, part = kr / KCH;
-      const int col = nr % KP, blk = nr / KP;
-      const float2 x = xs[kk * KP + col];
-      const float v = part == 0 ? (blk == 0 ? x.x : x.y) : (blk == 0 ? -x.y : x.x);
-      uint32_t pv[3];
-      split_parts<SPLIT>(v, pv);
-      const uint32_t o = (uint32_t)cell * CORE + (uint32_t)(lane >> 2) * 16 + (uint32_t)kq * 4;
+    // 2. B = [[Xr, Xi], [-Xi, Xr]] (N x K, K-major) of chunk c into B[s]
+    {
+      const uint32_t xb = sb + C::X0 + xbuf * C::X_BUF;
 #pragma unroll
-      for (int s = 0; s < SPLIT; ++s) st_shared(bBase + s * B_PART + o, pv[s]);
+      for (int q = 0; q < C::BIT; ++q) {
+        const uint32_t d = bdesc[q];
+        if (!producer || d == 0xFFFFFFFFu) continue;
+        const uint32_t xa = xb + ((d >> 16) & 0x3FFFu);
+        const float4 u = ld_shared_v4(xa), w = ld_shared_v4(xa + 16);
+        const bool im = (d >> 30) & 1u;
+        const uint32_t neg = d & 0x80000000u;
+        float v[4] = {im ? u.y : u.x, im ? u.w : u.z, im ? w.y : w.x, im ? w.w : w.z};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[j] = __uint_as_float(__float_as_uint(v[j]) ^ neg);
+        uint4 pv[3];
+        split4<SPLIT>(v, pv);
+#pragma unroll
+        for (int p = 0; p < SPLIT; ++p) st_shared_v4(bB + p * C::B_PART + (d & 0xFFFFu), pv[p]);
+      }
+    }
+    // 3. this thread's copies of chunk c+1 have landed
+    cp_async_wait<XS - 2>();
+    // 4. the MMAs of chunk c-S+1 have completed (chunk c+1 rewrites its A and B)
+    const int cw = c - S + 1;
+    bool gave_up = false;
+    if (cw >= 0 && issuer) {
+      const uint32_t sw = (uint32_t)(cw % S);
+      gave_up = !mbar_wait(mb0 + 8u * sw, (mph >> sw) & 1u);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_fence_before();
-    __syncthreads();
-    if (c + 1 < nch) stage_x(c + 1);   // lands while the next entries are formed
-    if (tid == 0) {
+    if (__syncthreads_or(gave_up)) {
+      ok = false;
+      break;
+    }
+    if (cw >= 0) mph ^= 1u << (cw % S);
+    tc_fence_after();
+    // 5. a group of DR chunks whose MMAs have all completed moves into
+    //    (hi, lo) while the other main accumulator takes the next group; it
+    //    is drained before the MMAs of the group after next reuse it
+    if (cw >= 0 && (drained + 1) * DR - 1 <= cw) {
+      if (producer) drain<NR, false>(tq, sub, (uint32_t)(drained & 1) * NR);
+      ++drained;
+      tc_fence_before();
+      __syncthreads();
       tc_fence_after();
+    }
+    // 6. stage chunk c+XS into the X / point buffers chunk c has finished reading
+    stage(c + XS);
+    // 7. the issuing thread issues the chunk's MMAs and commits them to mbar[s]
+    if (issuer) {
       // descriptors advance by (byte offset >> 4) in their start-address field
-      const uint64_t dA = sdesc<KR>(aBuf), dB = sdesc<KR>(bBase);
-      constexpr uint64_t pa = A_PART >> 4, pb = B_PART >> 4;
-      // the accumulator restarts right after each drain
-      const uint32_t carry = (c % DR) != 0 ? 1u : 0u;
+      const uint64_t dA = sdesc<KG>(aB), dB = sdesc<KG>(bB);
+      constexpr uint64_t pa = C::A_PART >> 4, pb = C::B_PART >> 4;
+      const uint32_t tmain = tm + (uint32_t)((c / DR) & 1) * NR, tcorr = tm + 2 * NR;
+      const uint32_t carry = (c % DR) != 0 ? 1u : 0u;   // a main accumulator restarts with its group
+      const uint32_t cacc = c > 0 ? 1u : 0u;             // the correction runs over all K
 #pragma unroll
-      for (int ks = 0; ks < KR / 8; ++ks) {
+      for (int ks = 0; ks < C::KR / 8; ++ks) {
         const uint64_t o = (uint64_t)(ks * 2 * CORE) >> 4;
-        const uint32_t first = (ks > 0) ? 1u : carry;
-        mma_tf32(tm, dA + o, dB + o, idesc, first);                // a0 b0 -> main
-        mma_tf32(tm + NR, dA + o, dB + pb + o, idesc, first);      // cross terms -> correction
-        mma_tf32(tm + NR, dA + pa + o, dB + o, idesc, 1u);
+        mma_tf32(tmain, dA + o, dB + o, idesc, ks > 0 ? 1u : carry);           // a0 b0 -> main
+        mma_tf32(tcorr, dA + o, dB + pb + o, idesc, ks > 0 ? 1u : cacc);       // cross terms -> correction
+        mma_tf32(tcorr, dA + pa + o, dB + o, idesc, 1u);
         if (SPLIT == 3) {
-          mma_tf32(tm + NR, dA + o, dB + 2 * pb + o, idesc, 1u);
-          mma_tf32(tm + NR, dA + pa + o, dB + pb + o, idesc, 1u);
-          mma_tf32(tm + NR, dA + 2 * pa + o, dB + o, idesc, 1u);
+          mma_tf32(tcorr, dA + o, dB + 2 * pb + o, idesc, 1u);
+          mma_tf32(tcorr, dA + pa + o, dB + pb + o, idesc, 1u);
+          mma_tf32(tcorr, dA + 2 * pa + o, dB + o, idesc, 1u);
         }
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       smem_u32(&mbar))
+                       mb0 + 8u * s)
                    : "memory");
     }
+    issued = c;
   }
   if (ok && nch > 0) {
-    const bool w = mbar_wait(smem_u32(&mbar), parity);
-    if (__syncthreads_or(!w)) {
+    bool gave_up = false;
+    if (issuer) {
+      const uint32_t sl = (uint32_t)((nch - 1) % S);
+      gave_up = !mbar_wait(mb0 + 8u * sl, (mph >> sl) & 1u);
+    }
+    if (__syncthreads_or(gave_up)) {
       ok = false;
     } else {
       tc_fence_after();
-      if (warp < 4) drain<NR>(tlane);
+      const int ngroups = (nch + DR - 1) / DR;
+      for (; drained < ngroups && producer; ++drained) {
+        if (drained + 1 < ngroups)
+          drain<NR, false>(tq, sub, (uint32_t)(drained & 1) * NR);
+        else
+          drain<NR, true>(tq, sub, (uint32_t)(drained & 1) * NR);
+      }
     }
   }
   cp_async_wait_all();
   if (!ok) {
-    if (tid == 0) atomicExch(&g_tc_status, 1);
-    mbar_wait(smem_u32(&mbar), parity);   // bounded chance for MMAs in flight
-  } else if (warp < 4) {
-    const int64_t row = row0 + warp * 32 + lane;
+    if (issuer) {
+      atomicExch(&g_tc_status, 1);
+      if (issued >= 0) {   // bounded chance for the MMAs in flight
+        const uint32_t sl = (uint32_t)(issued % S);
+        mbar_wait(mb0 + 8u * sl, (mph >> sl) & 1u);
+      }
+    }
+    __syncthreads();
+  } else {
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const int64_t row = row0 + quad * 32 + lane;
 #pragma unroll 1
-    for (int s = 0; s < (KP + 15) / 16; ++s) {
+    for (int s = sub; s < (KP + 15) / 16 && producer; s += NWARP / 4) {
       uint32_t hr[16], lr[16], hm[16], lm[16];
       // columns beyond KP read allocated but unused tensor memory; skipped below
       const int c0 = s * 16;
-      tmem_ld16(tlane + 2 * NR + c0, hr);
-      tmem_ld16(tlane + 3 * NR + c0, lr);
-      tmem_ld16(tlane + 2 * NR + KP + c0, hm);
-      tmem_ld16(tlane + 3 * NR + KP + c0, lm);
+      tmem_ld16(tq + 3 * NR + c0, hr);
+      tmem_ld16(tq + 4 * NR + c0, lr);
+      tmem_ld16(tq + 3 * NR + KP + c0, hm);
+      tmem_ld16(tq + 4 * NR + KP + c0, lm);
       tmem_wait_ld();
       if (row < M) {
 #pragma unroll
@@ -382,7 +622,7 @@ sketch_tc_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__ 
           if (col >= kcols || col >= KP) continue;
           if (T.ws < 0) {
             float2* __restrict__ Y = (float2*)J.Y;
-            Y[row + ((int64_t)T.group * kcols + col) * J.ldy] =
+            Y[row + ((int64_t)T.group * ygs + col) * J.ldy] =
                 make_float2(__uint_as_float(hr[i]) + __uint_as_float(lr[i]),
                             __uint_as_float(hm[i]) + __uint_as_float(lm[i]));
           } else {
@@ -422,14 +662,15 @@ __global__ void tc_reduce_kernel(const TcRegion* __restrict__ regs, int nreg, co
 
 bool sketch_tc_applies(const std::vector<SketchJob>& jobs) {
   for (const auto& j : jobs)
-    if (j.kcols > 64 || j.kcols < 1) return false;
+    if (j.kcols < 1) return false;
   return true;
 }
 
 template <int NR, int SPLIT>
 static int launch_nr(const SketchJob* dj, const TcTile* dt, unsigned ntiles, float4* ws, cudaStream_t s) {
-  constexpr size_t smem = smem_bytes<NR, SPLIT>();
-  static_assert(smem <= 220 * 1024, "sketch tile exceeds shared memory");
+  constexpr size_t smem = Cfg<NR, SPLIT>::LAUNCH_SMEM;
+  BF_CUDA_TRY(cudaFuncSetAttribute(sketch_tc_kernel<NR, SPLIT>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                   (int)cudaSharedmemCarveoutMaxShared));
   BF_CUDA_TRY(cudaFuncSetAttribute(sketch_tc_kernel<NR, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)smem));
   note_launch();
@@ -445,61 +686,101 @@ static int launch_split(int nr, const SketchJob* dj, const TcTile* dt, unsigned 
     case 32: return launch_nr<32, SPLIT>(dj, dt, nt, ws, s);
     case 48: return launch_nr<48, SPLIT>(dj, dt, nt, ws, s);
     case 64: return launch_nr<64, SPLIT>(dj, dt, nt, ws, s);
-    case 80: return launch_nr<80, SPLIT>(dj, dt, nt, ws, s);
-    case 96: return launch_nr<96, SPLIT>(dj, dt, nt, ws, s);
-    case 112: return launch_nr<112, SPLIT>(dj, dt, nt, ws, s);
-    default: return launch_nr<128, SPLIT>(dj, dt, nt, ws, s);
+    default: return launch_nr<96, SPLIT>(dj, dt, nt, ws, s);
   }
 }
 
-int launch_sketch_jobs_tc(const std::vector<SketchJob>& jobs, MemTracker* mt, cudaStream_t s) {
+// Split-K factor of one job: minimises (waves of CTAs) x (16-column K
+// chunks per CTA + a fixed per-CTA cost) for the job alone, so a job sums in the same order
+// whether it runs alone or in a batch.
+static int job_splits(int64_t base_tiles, int64_t max_chunks) {
+  int best = 1;
+  double best_cost = 1e300;
+  for (int ns = 1; ns <= 32; ++ns) {
+    if (ns > 1 && max_chunks < 4 * ns) break;
+    const double waves = (double)((base_tiles * ns + 303) / 304);   // two CTAs per SM
+    const double cost = waves * (double)((max_chunks + ns - 1) / ns + 6);
+    if (cost < best_cost * 0.999) best = ns, best_cost = cost;
+  }
+  return best;
+}
+
+int launch_sketch_jobs_tc(const std::vector<SketchJob>& jobs_in, MemTracker* mt, cudaStream_t s) {
+  // jobs wider than the widest tile run as column slices (entries formed once
+  // per slice); every job keeps its Y group stride
+  std::vector<SketchJob> jobs;
+  const int64_t WMAX = NR_MAX / 2;
+  for (SketchJob j : jobs_in) {
+    if (j.ygs == 0) j.ygs = j.kcols;
+    const int64_t kc = j.kcols;
+    for (int64_t c0 = 0; c0 < kc; c0 += WMAX) {
+      SketchJob q = j;
+      q.kcols = std::min(WMAX, kc - c0);
+      q.X = (const float2*)j.X + c0 * j.ldx;
+      q.Y = (float2*)j.Y + c0 * j.ldy;
+      jobs.push_back(q);
+    }
+  }
   int64_t maxk = 0;
   int split = 2;
   for (const auto& j : jobs) maxk = std::max(maxk, j.kcols), split = std::max(split, j.split);
-  const int kp = (int)((maxk + 7) / 8 * 8);   // padded width, multiple of 8
-  const int nr = 2 * kp;                       // real columns, multiple of 16, <= 128
-  const int KCH = split == 3 ? 16 : 32;
-  // rows tiles without splitting K; split K until the launch fills the GPU
-  int64_t base_tiles = 0;
+  // jobs of both split depths: one launch per depth, so that every job's
+  // arithmetic is the same as when it runs alone
   for (const auto& j : jobs)
-    if (j.M > 0 && j.kcols > 0) base_tiles += (int64_t)j.groups * ((j.M + TM - 1) / TM);
-  if (base_tiles == 0) return BF_OK;
-  int nsplit = 1;
-  while (base_tiles * nsplit < 2 * 152 && nsplit < 16) nsplit *= 2;
+    if (j.split != split) {
+      std::vector<SketchJob> lo, hi;
+      for (const auto& q : jobs) (q.split == split ? hi : lo).push_back(q);
+      BF_TRY(launch_sketch_jobs_tc(lo, mt, s));
+      return launch_sketch_jobs_tc(hi, mt, s);
+    }
+  // real columns N = 2 x padded sketch width, one of the compiled tile widths
+  const int kp = (int)((maxk + 7) / 8 * 8);
+  const int nr = kp <= 8 ? 16 : kp <= 16 ? 32 : kp <= 24 ? 48 : kp <= 32 ? 64 : 96;
+  const int kch = split == 3 ? Cfg<16, 3>::KCH : Cfg<16, 2>::KCH;   // complex K per chunk
   std::vector<TcTile> tiles;
   std::vector<TcRegion> regs;
   int64_t wsz = 0;
   for (size_t ji = 0; ji < jobs.size(); ++ji) {
     const SketchJob& j = jobs[ji];
     if (j.M <= 0 || j.kcols <= 0) continue;
+    // K ranges of the groups (host copy of the node boundaries when given)
+    auto krange = [&](int g, int64_t& a, int64_t& b) {
+      if (j.groups == 1) a = 0, b = j.Ktot;
+      else if (j.h_off) a = j.h_off[g], b = j.h_off[g + 1];
+      else a = -1, b = -1;
+    };
+    int64_t maxk_g = 0;
+    bool known = true;
     for (int g = 0; g < j.groups; ++g) {
-      // K range of the group (host copy of the node boundaries is not kept
-      // here, so splits are decided per group from the job's total K)
-      const int64_t ktot = j.groups == 1 ? j.Ktot : -1;
-      int ns = nsplit;
-      if (ktot >= 0 && ktot < (int64_t)KCH * 4 * ns) ns = 1;
-      if (ktot < 0) ns = 1;   // grouped launches have enough tiles
+      int64_t a, b;
+      krange(g, a, b);
+      if (a < 0) known = false;
+      else maxk_g = std::max(maxk_g, b - a);
+    }
+    const int64_t rt = (j.M + TM - 1) / TM;
+    const int ns = known ? job_splits(rt * j.groups, (maxk_g + 15) / 16) : 1;
+    for (int g = 0; g < j.groups; ++g) {
+      int64_t ga, gb;
+      krange(g, ga, gb);
       int64_t ws0 = -1;
       if (ns > 1) {
         ws0 = wsz;
-        regs.push_back({wsz, j.M, j.kcols, j.ldy, (int64_t)g * j.kcols, ns, 0, (float2*)j.Y});
+        regs.push_back({wsz, j.M, j.kcols, j.ldy, (int64_t)g * j.ygs, ns, 0, (float2*)j.Y});
         wsz += (int64_t)ns * j.M * j.kcols;
       }
-      const int64_t ks = ns > 1 ? ((ktot + ns - 1) / ns + KCH - 1) / KCH * KCH : 0;
+      const int64_t ks = ns > 1 ? ((gb - ga + ns - 1) / ns + kch - 1) / kch * kch : 0;
       for (int sp = 0; sp < ns; ++sp) {
-        int64_t a = 0, b = 0;
+        int64_t a = -1, b = -1;   // whole group range, resolved on the device
         if (ns > 1) {
-          a = std::min<int64_t>(ktot, sp * ks);
-          b = std::min<int64_t>(ktot, a + ks);
+          a = std::min<int64_t>(gb, ga + sp * ks);
+          b = std::min<int64_t>(gb, a + ks);
         }
-        for (int64_t r0 = 0; r0 < j.M; r0 += TM) {
-          TcTile t{(int32_t)ji, g, r0, a, b, ns > 1 ? ws0 + (int64_t)sp * j.M * j.kcols : -1};
-          if (ns == 1) t.k0 = -1, t.k1 = -1;   // whole group range, resolved on the device
-          tiles.push_back(t);
-        }
+        for (int64_t r0 = 0; r0 < j.M; r0 += TM)
+          tiles.push_back(TcTile{(int32_t)ji, g, r0, a, b, ns > 1 ? ws0 + (int64_t)sp * j.M * j.kcols : -1});
       }
     }
   }
+  if (tiles.empty()) return BF_OK;
   const size_t jb = jobs.size() * sizeof(SketchJob), tb = tiles.size() * sizeof(TcTile),
                rb = regs.size() * sizeof(TcRegion);
   DevBuf d, w;

@@ -93,6 +93,68 @@ __device__ __forceinline__ void sincos_taylor(float t, float& s, float& c) {
   c = fmaf(t2, pc, 1.0f);
 }
 
+// Magic constant 1.5 * 2^23: for |v| < 2^22, fmaf(x, y, MAGIC) - MAGIC is
+// x*y rounded to the nearest integer, and the low bits of the sum's encoding
+// hold that integer modulo 2^22 (two's complement).
+#define BF_RND_MAGIC 12582912.0f
+
+// e^{i phi} for a float-float phase ph: phi = q pi/2 + t with q * C1
+// subtracted exactly by FMA, |t| <= pi/4, then the quadrant q mod 4 applied
+// (sin/cos swapped for odd q, signs from q).  Returns (cos phi, sin phi).
+__device__ __forceinline__ float2 expi_ff(FF ph) {
+  const float qm = fmaf(ph.h, BF_2OPI, BF_RND_MAGIC);
+  const float q = qm - BF_RND_MAGIC;
+  const unsigned qi = (unsigned)__float_as_int(qm);
+  const float t1 = fmaf(-q, BF_PIO2_1, ph.h);
+  const FF m2 = two_prod(q, BF_PIO2_2);
+  const FF th = two_sum(t1, -m2.h);
+  const float t = th.h + ((th.l + (ph.l - m2.l)) - q * BF_PIO2_3);
+  float sv, cv;
+  sincos_taylor(t, sv, cv);
+  float sn = (qi & 1) ? cv : sv, cs = (qi & 1) ? sv : cv;
+  sn = __uint_as_float(__float_as_uint(sn) ^ ((qi & 2u) << 30));
+  cs = __uint_as_float(__float_as_uint(cs) ^ (((qi + 1u) & 2u) << 30));
+  return make_float2(cs, sn);
+}
+
+// Helmholtz kernel entry at the float-float row point rp = (x, y, z as
+// hi/lo pairs) and column point (cxh + cxl, cyh + cyl, czh + czl):
+// returns (cos(k r) a, sin(k r) a) with a = 1/r (2D) or 1/(4 pi r) (3D);
+// the caller fixes the sign of the imaginary part (exp(-i k r) in 2D).
+template <bool D3>
+__device__ __forceinline__ float2 helmholtz_ff(const float (&rp)[6], float cxh, float cxl, float cyh, float cyl,
+                                               float czh, float czl, float kh, float kl) {
+  FF r2 = ff_sq(ff_sub(rp[0], rp[1], cxh, cxl));
+  r2 = ff_add(r2, ff_sq(ff_sub(rp[2], rp[3], cyh, cyl)));
+  if (D3) r2 = ff_add(r2, ff_sq(ff_sub(rp[4], rp[5], czh, czl)));
+  // 1/sqrt(r2): estimate and one Newton step; r = sqrt(r2) corrected in float-float
+  float rs = rsqrtf(r2.h);
+  rs = rs * fmaf(-0.5f * r2.h * rs, rs, 1.5f);
+  const float rh0 = r2.h * rs;
+  const FF e = two_prod(rh0, rh0);
+  const float num = ((r2.h - e.h) - e.l) + r2.l;
+  const FF r = fast_two_sum(rh0, num * (0.5f * rs));
+  // phase k * r
+  FF ph = two_prod(kh, r.h);
+  ph.l = fmaf(kh, r.l, fmaf(kl, r.h, ph.l));
+  ph = fast_two_sum(ph.h, ph.l);
+  const float2 c = expi_ff(ph);
+  const float a = D3 ? 0.0795774715f * rs : rs;
+  return make_float2(c.x * a, c.y * a);
+}
+
+// DFT entry exp(-2 pi i t s) at float-float t = th + tl, s = sh + sl.
+__device__ __forceinline__ float2 dft_ff(float th, float tl, float sh, float sl) {
+  FF u = two_prod(th, sh);
+  u.l = fmaf(th, sl, fmaf(tl, sh, u.l));
+  const float q = rintf(u.h);
+  const FF f = two_sum(u.h - q, u.l);     // u.h - q exact (Sterbenz)
+  float sn, cs;
+  sincospif(-2.0f * f.h, &sn, &cs);
+  const float d = -6.28318531f * f.l;     // first-order correction
+  return make_float2(cs - d * sn, sn + d * cs);
+}
+
 // Per-thread evaluation context of one job's entries, held in registers so
 // that the entry loop neither reloads the job descriptor nor the thread's row
 // point.  The kernels depend on the points only through |t - s| (the DFT
@@ -144,45 +206,11 @@ struct Entry<float> {
   // K(row point, column point kk)
   __device__ __forceinline__ float2 value(int64_t kk) const {
     const float* c = colp + kk;
-    if (type == BF_KERNEL_DFT) {
-      FF u = two_prod(rp[0], c[0]);
-      u.l = fmaf(rp[0], c[coln], fmaf(rp[1], c[0], u.l));
-      const float q = rintf(u.h);
-      const FF f = two_sum(u.h - q, u.l);     // u.h - q exact (Sterbenz)
-      float sn, cs;
-      sincospif(-2.0f * f.h, &sn, &cs);
-      const float d = -6.28318531f * f.l;     // first-order correction
-      return make_float2(cs - d * sn, sn + d * cs);
-    }
-    FF r2 = ff_sq(ff_sub(rp[0], rp[1], c[0], c[coln]));
-    r2 = ff_add(r2, ff_sq(ff_sub(rp[2], rp[3], c[2 * coln], c[3 * coln])));
-    if (type == BF_KERNEL_HELMHOLTZ_3D) r2 = ff_add(r2, ff_sq(ff_sub(rp[4], rp[5], c[4 * coln], c[5 * coln])));
-    // 1/sqrt(r2): estimate and one Newton step; r = sqrt(r2) corrected in float-float
-    float rs = rsqrtf(r2.h);
-    rs = rs * fmaf(-0.5f * r2.h * rs, rs, 1.5f);
-    const float rh0 = r2.h * rs;
-    const FF e = two_prod(rh0, rh0);
-    const float num = ((r2.h - e.h) - e.l) + r2.l;
-    const FF r = fast_two_sum(rh0, num * (0.5f * rs));
-    // phase k * r
-    FF ph = two_prod(kh, r.h);
-    ph.l = fmaf(kh, r.l, fmaf(kl, r.h, ph.l));
-    ph = fast_two_sum(ph.h, ph.l);
-    // t = ph - q pi/2 with q * C1 subtracted exactly by FMA
-    const float q = rintf(ph.h * BF_2OPI);
-    const float t1 = fmaf(-q, BF_PIO2_1, ph.h);
-    const FF m2 = two_prod(q, BF_PIO2_2);
-    const FF th = two_sum(t1, -m2.h);
-    const float t = th.h + ((th.l + (ph.l - m2.l)) - q * BF_PIO2_3);
-    float sv, cv;
-    sincos_taylor(t, sv, cv);
-    const int qi = (int)q & 3;
-    float sn = (qi & 1) ? cv : sv, cs = (qi & 1) ? sv : cv;
-    if (qi & 2) sn = -sn;
-    if ((qi + 1) & 2) cs = -cs;
-    if (type == BF_KERNEL_HELMHOLTZ_2D) return make_float2(cs * rs, -sn * rs);
-    const float ir = 0.0795774715f * rs;
-    return make_float2(cs * ir, sn * ir);
+    if (type == BF_KERNEL_DFT) return dft_ff(rp[0], rp[1], c[0], c[coln]);
+    if (type == BF_KERNEL_HELMHOLTZ_3D)
+      return helmholtz_ff<true>(rp, c[0], c[coln], c[2 * coln], c[3 * coln], c[4 * coln], c[5 * coln], kh, kl);
+    const float2 v = helmholtz_ff<false>(rp, c[0], c[coln], c[2 * coln], c[3 * coln], 0.f, 0.f, kh, kl);
+    return make_float2(v.x, -v.y);   // exp(-i k r) / r
   }
 };
 

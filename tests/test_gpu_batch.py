@@ -3,8 +3,8 @@ operators of uneven size, depth and rank.
 
 Batching changes only how blocks are grouped into launches, not the
 arithmetic of any block, so every batched factorization must equal the one
-bf_factor computes for the same plan and operator (same ranks, same apply
-to rounding), and must stay within the oracle tolerances."""
+bf_factor computes for the same plan and operator (same ranks, bit-identical
+apply), and must stay within the oracle tolerances."""
 import math
 
 import numpy as np
@@ -54,12 +54,26 @@ def test_batch_equals_individual(precision, tol):
             assert np.array_equal(F.ranks(1, j), Fi.ranks(1, j))
         x = inputs.random_rhs(p.n, 3, seed=p.n)
         yb, yi = H(F.apply(T(x))), H(Fi.apply(T(x)))
-        # FP64: identical arithmetic per block.  Mixed: the tensor-core sketch
-        # splits K across CTAs according to the launch's total tile count, so
-        # a batch sums in another order -- equal to FP32 rounding
-        agree = 1e-13 if precision == "fp64" else 2e-6
-        assert np.linalg.norm(yb - yi) <= agree * np.linalg.norm(yi)
+        # every launch takes the same arithmetic per job and block whatever
+        # else it carries (split-K and split depth are decided per job)
+        assert np.array_equal(yb, yi)
         assert F.error(op, 16, seed=2) <= 2 * math.sqrt(p.L + 2) * tol
+
+
+def test_batch_of_both_split_depths_equals_individual():
+    """Mixed-precision plans with tolerances on both sides of the split-depth
+    switch (3xTF32 at 1e-5, the three-way split at 1e-6) and uneven sketch
+    widths in one batch: each result is bit-identical to bf_factor's."""
+    plans = []
+    for i, (n, tol) in enumerate([(1024, 1e-5), (1024, 1e-6), (2048, 1e-5), (768, 1e-6)]):
+        g = inputs.arc_pair(n, seed=30 + i)
+        plans.append(api.Plan(g.src, g.tgt, kernel=g.kernel, wavenumber=g.wavenumber, leaf=32, tol=tol,
+                              precision="mixed", seed=i))
+    Fb = api.Factorization.factor_batch(plans, [api.Operator.kernel(p) for p in plans])
+    for p, F in zip(plans, Fb):
+        Fi = api.Factorization.factor(p, api.Operator.kernel(p))
+        x = T(inputs.random_rhs(p.n, 2, seed=1))
+        assert np.array_equal(H(F.apply(x)), H(Fi.apply(x)))
 
 
 def test_batch_mixed_operator_kinds_and_oracle():
