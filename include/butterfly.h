@@ -193,6 +193,18 @@ int bf_apply(bf_fact F, int64_t nrhs, const void* x, int64_t ldx, void* y,
 int bf_apply_T(bf_fact F, int op, int64_t nrhs, const void* x, int64_t ldx,
                void* y, int64_t ldy, int dtype, void* stream);
 
+/* Apply autotuner.  Each stage of an apply of F (op BF_OP_N, BF_OP_T or
+ * BF_OP_C; dtype BF_C64 or BF_C128; nrhs right-hand sides) is a batched
+ * block product of eq. hybrid_butterfly_mat that the library can run with
+ * several kernel shapes; all compute bit-identical results.  This call times
+ * every shape on every stage (on internal scratch operands; no user data is
+ * read or written), keeps the fastest per stage for all later applies of F
+ * with a right-hand-side count in the same class (1, 2-4, 5-16, 17-32,
+ * 33-64, >64), and writes the tuned device time of one apply in ms to
+ * *ms_out (may be NULL).  Synchronises the stream; allocates scratch for
+ * its duration.  BF_EINVAL for a bad op/dtype/nrhs, BF_ENOMEM, BF_ECUDA. */
+int bf_apply_tune(bf_fact F, int op, int64_t nrhs, int dtype, void* stream, float* ms_out);
+
 /* Size of the fixed device scratch array used by bf_apply_noalloc (32 MiB).
  * Every GPU on which the library is loaded holds this array until the
  * process exits, whether or not bf_apply_noalloc is ever called. */

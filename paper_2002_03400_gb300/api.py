@@ -81,6 +81,7 @@ def lib():
         "bf_free": (None, [vp]),
         "bf_set_sketch_engine": (i32, [i32]),
         "bf_launch_count": (C.c_ulonglong, []),
+        "bf_apply_tune": (i32, [vp, i32, i64, i32, vp, C.POINTER(C.c_float)]),
         "bf_gaussian": (i32, [C.c_uint64, C.c_uint32, i64, i64, i64, i64, vp, i64, i32, vp]),
     }
     for name, (res, args) in sig.items():
@@ -98,7 +99,7 @@ def exported_symbols():
             "bf_operator_callback", "bf_operator_apply", "bf_operator_counts", "bf_factor",
             "bf_factor_batch", "bf_apply",
             "bf_apply_T", "bf_apply_noalloc", "bf_ranks", "bf_fact_info", "bf_fact_import", "bf_fact_export", "bf_error",
-            "bf_free", "bf_gaussian", "bf_set_sketch_engine", "bf_launch_count"]
+            "bf_free", "bf_gaussian", "bf_set_sketch_engine", "bf_launch_count", "bf_apply_tune"]
 
 
 def launch_count() -> int:
@@ -336,6 +337,14 @@ class Factorization(_Handle):
             check(lib().bf_apply(self._h, *args))
         else:
             check(lib().bf_apply_T(self._h, OPS[op], *args))
+
+    def tune(self, nrhs: int, dtype=torch.complex64, op: str = "N", stream=None) -> float:
+        """Autotunes the apply's stage kernels for this right-hand-side class;
+        returns the tuned device time of one apply in ms."""
+        ms = C.c_float()
+        dt = 0 if dtype == torch.complex64 else 1
+        check(lib().bf_apply_tune(self._h, OPS[op], nrhs, dt, _stream(stream), C.byref(ms)))
+        return ms.value
 
     def ranks(self, side: int, level: int) -> np.ndarray:
         out = np.empty(1 << self.L, dtype=np.int32)

@@ -262,7 +262,7 @@ struct CallbackOp : Operator {
     if (ncols <= 0) return BF_OK;
     (op == BF_OP_N ? cols_N : cols_T) += ncols;
     if (op != BF_OP_C) {
-      const int r = fn(ctx, op, ncols, X, ldx, Y, ldy, dtype, (void*)s);
+      const int r = fn(ctx, op, ncols, X, ldx, Y, ldy, dtype, api_stream(s));
       return r ? fail(BF_ECALLBACK, "black-box callback returned " + std::to_string(r)) : BF_OK;
     }
     // A^H X = conj(A^T conj X)
@@ -270,7 +270,7 @@ struct CallbackOp : Operator {
     BF_TRY(t.alloc(&mem, m * ncols * elem_bytes(dtype), s));
     int rc = launch_gather_rows(nullptr, m, ncols, X, ldx, t.p, m, 1, dtype, s);
     if (!rc) {
-      const int r = fn(ctx, BF_OP_T, ncols, t.p, m, Y, ldy, dtype, (void*)s);
+      const int r = fn(ctx, BF_OP_T, ncols, t.p, m, Y, ldy, dtype, api_stream(s));
       rc = r ? fail(BF_ECALLBACK, "black-box callback returned " + std::to_string(r)) : BF_OK;
     }
     if (!rc) rc = launch_conj_inplace(Y, n, ncols, ldy, dtype, s);
@@ -460,9 +460,9 @@ int bf_operator_dense(bf_plan plan, const void* A, int64_t lda, int dtype, void*
   int rc = op->A.alloc(&P->mem, P->m * P->n * elem_bytes(op->dt), nullptr);
   if (!rc)
     rc = launch_gather2d((const int64_t*)P->d_permT.p, (const int64_t*)P->d_permS.p, P->m, P->n, A, lda,
-                         dtype, op->A.p, P->m, op->dt, (cudaStream_t)stream);
+                         dtype, op->A.p, P->m, op->dt, user_stream(stream));
   if (!rc) {
-    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    cudaError_t e = cudaStreamSynchronize(user_stream(stream));
     if (e != cudaSuccess) rc = fail(BF_ECUDA, cudaGetErrorString(e));
   }
   if (rc) {
@@ -540,7 +540,7 @@ int bf_operator_apply(bf_operator A, int op, int64_t ncols, const void* X, int64
   const int64_t in_rows = op == BF_OP_N ? h->impl->n : h->impl->m;
   const int64_t out_rows = op == BF_OP_N ? h->impl->m : h->impl->n;
   if (ncols < 0 || ldx < in_rows || ldy < out_rows) return fail(BF_EINVAL, "bad ncols or leading dimension");
-  return h->impl->apply(op, ncols, X, ldx, Y, ldy, dtype, (cudaStream_t)stream);
+  return h->impl->apply(op, ncols, X, ldx, Y, ldy, dtype, user_stream(stream));
 }
 
 int bf_operator_counts(bf_operator A, int64_t* cols_N, int64_t* cols_T) {
@@ -567,7 +567,7 @@ int bf_factor(bf_plan plan, bf_operator A, void* stream, bf_fact* out) {
     op = tmp->impl;
   }
   Fact* F = nullptr;
-  const int rc = factor(hp->impl, op, (cudaStream_t)stream, &F);
+  const int rc = factor(hp->impl, op, user_stream(stream), &F);
   if (tmp) bf_free(tmp);
   if (rc) return rc;
   *out = new bf_fact_s{KIND_FACT, F};
@@ -606,7 +606,7 @@ int bf_factor_batch(int count, const bf_plan* plans, const bf_operator* ops, voi
     }
   }
   std::vector<Fact*> F(count, nullptr);
-  if (!rc) rc = factor_batch(count, P.data(), A.data(), (cudaStream_t)stream, F.data());
+  if (!rc) rc = factor_batch(count, P.data(), A.data(), user_stream(stream), F.data());
   for (auto t : tmp) bf_free(t);
   if (rc) return rc;
   for (int i = 0; i < count; ++i) out[i] = new bf_fact_s{KIND_FACT, F[i]};
@@ -618,7 +618,13 @@ int bf_apply(bf_fact F, int64_t nrhs, const void* x, int64_t ldx, void* y, int64
   auto* h = check<bf_fact_s>(F, KIND_FACT);
   if (!h) return fail(BF_EINVAL, "not a factorization");
   if (nrhs < 0) return fail(BF_EINVAL, "nrhs < 0");
-  return apply_fact(h->impl, BF_OP_N, nrhs, x, ldx, y, ldy, dtype, (cudaStream_t)stream, false);
+  return apply_fact(h->impl, BF_OP_N, nrhs, x, ldx, y, ldy, dtype, user_stream(stream), false);
+}
+
+int bf_apply_tune(bf_fact F, int op, int64_t nrhs, int dtype, void* stream, float* ms_out) {
+  auto* h = check<bf_fact_s>(F, KIND_FACT);
+  if (!h) return fail(BF_EINVAL, "not a factorization");
+  return tune_apply(h->impl, op, dtype, nrhs, user_stream(stream), ms_out);
 }
 
 int bf_apply_T(bf_fact F, int op, int64_t nrhs, const void* x, int64_t ldx, void* y, int64_t ldy,
@@ -627,7 +633,7 @@ int bf_apply_T(bf_fact F, int op, int64_t nrhs, const void* x, int64_t ldx, void
   if (!h) return fail(BF_EINVAL, "not a factorization");
   if (op != BF_OP_T && op != BF_OP_C) return fail(BF_EINVAL, "op must be BF_OP_T or BF_OP_C");
   if (nrhs < 0) return fail(BF_EINVAL, "nrhs < 0");
-  return apply_fact(h->impl, op, nrhs, x, ldx, y, ldy, dtype, (cudaStream_t)stream, false);
+  return apply_fact(h->impl, op, nrhs, x, ldx, y, ldy, dtype, user_stream(stream), false);
 }
 
 int bf_ranks(bf_fact F, int side, int level, int32_t* out) {
@@ -752,7 +758,7 @@ int bf_gaussian(uint64_t seed, uint32_t stream_id, int64_t row0, int64_t rows, i
                 void* out, int64_t ld, int dtype, void* stream) {
   if (!out || rows < 0 || ld < rows || col1 < col0 || row0 < 0) return fail(BF_EINVAL, "bad arguments");
   if (dtype != BF_C64 && dtype != BF_C128) return fail(BF_EINVAL, "bad dtype");
-  return launch_gaussian(seed, stream_id, row0, rows, col0, col1, out, ld, dtype, (cudaStream_t)stream);
+  return launch_gaussian(seed, stream_id, row0, rows, col0, col1, out, ld, dtype, user_stream(stream));
 }
 
 int bf_error(bf_fact F, bf_operator A, int ncols, uint64_t seed, int dtype, void* stream, double* err) {
@@ -761,7 +767,7 @@ int bf_error(bf_fact F, bf_operator A, int ncols, uint64_t seed, int dtype, void
   if (!hf || !ho || !err || ncols < 1) return fail(BF_EINVAL, "bad arguments");
   if (dtype != BF_C64 && dtype != BF_C128) return fail(BF_EINVAL, "bad dtype");
   Fact* f = hf->impl;
-  cudaStream_t s = (cudaStream_t)stream;
+  cudaStream_t s = user_stream(stream);
   const int64_t n = f->n, m = f->m;
   const size_t es = elem_bytes(dtype);
   DevBuf buf;

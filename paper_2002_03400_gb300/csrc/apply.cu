@@ -250,6 +250,7 @@ static int build_apply(Fact* F, int opC, int dtype, cudaStream_t s) {
   BF_CUDA_TRY(cudaMemcpyAsync(ap.tasks.p, all.data(), all.size() * sizeof(StageTask),
                               cudaMemcpyHostToDevice, s));
   BF_CUDA_TRY(cudaStreamSynchronize(s));
+  ap.variant.assign(ap.first.size(), std::array<int8_t, NRHS_CLASSES>{-1, -1, -1, -1, -1, -1});
   ap.built = true;
   return BF_OK;
 }
@@ -271,7 +272,7 @@ int run_apply_stages(Fact* F, int opC, int dtype, int64_t nrhs, void* xt, void* 
   StageBases bases{{xt, ping, pong, yt}};
   for (size_t i = 0; i < ap.first.size(); ++i) {
     const StageTask* d = (const StageTask*)ap.tasks.p + ap.first[i];
-    BF_TRY(launch_stage(d, ap.count[i], ap.maxM[i], (int)nrhs, (int)nrhs, bases, dtype, s));
+    BF_TRY(launch_stage(d, ap.count[i], ap.maxM[i], (int)nrhs, (int)nrhs, bases, dtype, s, ap.variant_of(i, nrhs)));
   }
   return BF_OK;
 }
@@ -318,6 +319,58 @@ int apply_fact(Fact* F, int op, int64_t nrhs, const void* x, int64_t ldx, void* 
   if (rc == BF_OK && !direct_out)
     rc = launch_scatter_rows(id_out ? nullptr : perm_out, out_rows, nrhs, yt, out_rows, y, ldy, conj, dtype, s);
   scratch.release(s);
+  return rc;
+}
+
+// Apply tuner: each stage of the cached task lists, each stage-kernel
+// variant, a warm-up launch and three timed launches on scratch operands
+// (the variants compute identical sums, so timing on any data is timing on
+// all data); the fastest variant per stage is kept for this right-hand-side
+// class.  Synchronises the stream.
+int tune_apply(Fact* F, int op, int dtype, int64_t nrhs, cudaStream_t s, float* ms) {
+  if (nrhs <= 0) return fail(BF_EINVAL, "nrhs must be positive");
+  if (dtype != BF_C64 && dtype != BF_C128) return fail(BF_EINVAL, "dtype must be BF_C64 or BF_C128");
+  if (op != BF_OP_N && op != BF_OP_T && op != BF_OP_C) return fail(BF_EINVAL, "bad op");
+  const int opC = op == BF_OP_N ? 0 : 1;
+  BF_TRY(prepare_apply(F, opC, dtype, s));
+  ApplyPlan& ap = F->ap[opC][dtype];
+  const Plan* P = F->plan;
+  const size_t es = elem_bytes(dtype);
+  const int64_t rows = std::max(P->n, P->m), lvl = ap.level_rows_max * nrhs;
+  DevBuf scratch;
+  BF_TRY(scratch.alloc(&F->mem, (2 * lvl + 2 * rows * nrhs) * es, s));
+  char* p = (char*)scratch.p;
+  BF_CUDA_TRY(cudaMemsetAsync(p, 0, (2 * lvl + 2 * rows * nrhs) * es, s));
+  StageBases bases{{p + 2 * lvl * es, p, p + lvl * es, p + 2 * lvl * es + rows * nrhs * es}};
+  cudaEvent_t e[2];
+  BF_CUDA_TRY(cudaEventCreate(&e[0]));
+  BF_CUDA_TRY(cudaEventCreate(&e[1]));
+  int rc = BF_OK;
+  float total = 0.f;
+  const int cls = nrhs_class(nrhs);
+  for (size_t i = 0; i < ap.first.size() && !rc; ++i) {
+    const StageTask* d = (const StageTask*)ap.tasks.p + ap.first[i];
+    float best = 1e30f;
+    int bv = stage_variant_default((int)nrhs, dtype);
+    for (int v = 0; v < STAGE_VARIANTS && !rc; ++v) {
+      rc = launch_stage(d, ap.count[i], ap.maxM[i], (int)nrhs, (int)nrhs, bases, dtype, s, v);
+      if (!rc && cudaEventRecord(e[0], s) != cudaSuccess) rc = fail(BF_ECUDA, "event record failed");
+      for (int r = 0; r < 3 && !rc; ++r) rc = launch_stage(d, ap.count[i], ap.maxM[i], (int)nrhs, (int)nrhs, bases, dtype, s, v);
+      if (!rc && (cudaEventRecord(e[1], s) != cudaSuccess || cudaEventSynchronize(e[1]) != cudaSuccess))
+        rc = fail(BF_ECUDA, "event timing failed");
+      float t = 0.f;
+      if (!rc && cudaEventElapsedTime(&t, e[0], e[1]) != cudaSuccess) rc = fail(BF_ECUDA, "event timing failed");
+      if (!rc && t < best) best = t, bv = v;
+    }
+    if (!rc) {
+      ap.variant[i][cls] = (int8_t)bv;
+      total += best / 3.f;
+    }
+  }
+  cudaEventDestroy(e[0]);
+  cudaEventDestroy(e[1]);
+  scratch.release(s);
+  if (ms) *ms = total;
   return rc;
 }
 

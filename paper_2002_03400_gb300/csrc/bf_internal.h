@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <array>
 #include <string>
 #include <vector>
 
@@ -28,6 +29,13 @@ int fail(int code, const std::string& msg);
     int s__ = (expr);         \
     if (s__ != BF_OK) return s__; \
   } while (0)
+
+// --------------------------------------------------------------- streams --
+// A NULL stream at the C ABI is the legacy default stream; it is carried as
+// cudaStreamLegacy inside the library so that scratch buffers are always
+// stream-ordered (cudaMallocAsync), and handed back as NULL to callbacks.
+inline cudaStream_t user_stream(void* s) { return s ? (cudaStream_t)s : cudaStreamLegacy; }
+inline void* api_stream(cudaStream_t s) { return s == cudaStreamLegacy ? nullptr : (void*)s; }
 
 // --------------------------------------------------------------- memory ---
 // Device buffers owned by a handle; allocation counted against a cap.
@@ -145,12 +153,20 @@ struct Stage {
 
 // Cached task lists of one apply direction and dtype (eq. hybrid_butterfly_mat):
 // stage i reads bases[in_base[i]] and writes bases[out_base[i]].
+constexpr int NRHS_CLASSES = 6;      // right-hand-side counts 1, 2-4, 5-16, 17-32, 33-64, >64
+inline int nrhs_class(int64_t n) { return n <= 1 ? 0 : n <= 4 ? 1 : n <= 16 ? 2 : n <= 32 ? 3 : n <= 64 ? 4 : 5; }
 struct ApplyPlan {
   bool built = false;
   DevBuf tasks;
   std::vector<int64_t> first;        // first task of each stage
   std::vector<int> count, maxM, maxN;
   int64_t level_rows_max = 0;        // rows of the largest stacked intermediate
+  // stage-kernel variant per stage and right-hand-side class, -1 untuned
+  std::vector<std::array<int8_t, NRHS_CLASSES>> variant;
+  int variant_of(size_t stage, int64_t nrhs) const {
+    const int v = stage < variant.size() ? variant[stage][nrhs_class(nrhs)] : -1;
+    return v >= 0 ? v : -1;
+  }
 };
 
 struct Fact {
@@ -201,9 +217,16 @@ struct StageTask {
 struct StageBases {
   void* p[4];
 };
-// N of every task is replaced by Noverride when Noverride > 0.
+// N of every task is replaced by Noverride when Noverride > 0.  variant:
+// kernel shape (0, 1 or 2, same results), -1 for the default for Noverride.
 int launch_stage(const StageTask* d_tasks, int ntasks, int maxM, int maxN, int Noverride,
-                 const StageBases& bases, int dtype, cudaStream_t s);
+                 const StageBases& bases, int dtype, cudaStream_t s, int variant = -1);
+// Times every stage-kernel variant on each stage of F's apply (direction,
+// dtype, nrhs) and keeps the fastest per stage for that right-hand-side
+// class; returns the tuned apply time in *ms (device, one call).
+int tune_apply(Fact* F, int op, int dtype, int64_t nrhs, cudaStream_t s, float* ms);
+int stage_variant_default(int nrhs, int dtype);
+constexpr int STAGE_VARIANTS = 3;
 
 // ------------------------------------------------------------------- QR --
 struct QRTask {

@@ -5,27 +5,41 @@
 // lines that project K(T_tau,S_nu)^T Gamma_tau and K(T_tau,S_nu) Omega_nu
 // and form V^T Omega_nu) and the projection of the centre level.
 //
-// Each task is one output block (or a column slice of it):
+// Each task is one output block:
 //   out[M x N] = sum_t op_t(mat_t)[M x K_t] * in_t[K_t x N],  t < nterms <= 2
-// One warp owns one task at a time (blocks have ranks ~10-60, far too small
-// for a CTA each).  Lanes own output columns; the factor block is staged in
-// 16 x 16 tiles through the warp's slice of shared memory, where every lane
-// reads the same element (broadcast), with the conjugate transpose folded
-// into that load; each lane keeps 16 input values and 16 accumulators in
-// registers.  Operand layouts (per StageTerm/StageTask):
+// Blocks have ranks ~10-60, far too small for a CTA each, and a stage is
+// bound by memory latency (each block's entries and inputs are a few KB).
+// Two kernel shapes compute the same sums (every output is one lane's
+// sequential FMA chain over the terms and k, so they agree bit for bit and
+// the result does not depend on N or on the lane layout):
+//   variant 0: one warp per (task, column slice, group of RT rows) --
+//     thousands of warps; each K step issues its KC input and RT x KC factor
+//     loads together, so their latencies overlap;
+//   variant 1: one warp per (task, column slice) keeping RT1 rows per lane
+//     and walking K one element at a time -- fewer instructions per output;
+//   variant 2: one warp per (task, column slice) that copies the factor
+//     block whole into shared memory first (coalesced) and stages its inputs
+//     KC2 rows at a time -- no factor-load latency inside the K loop.
+// In both, the warp's lanes cover CW columns x 32/CW rows, CW the smallest
+// power of two >= N (at most 32), so small numbers of right-hand sides still
+// use every lane.  The apply picks the variant per stage and column count
+// as measured by the apply tuner, else by stage_variant_default.
+// Operand layouts (per StageTerm/StageTask):
 //   ld > 0: column-major, element (k, c) at off + k + c*ld
 //   ld < 0: row-major,    element (k, c) at off + k*(-ld) + c
 //   ld = 0: row-major with the launch's column count N: off is a row index,
 //           element (k, c) at (off + k)*N + c  (apply intermediates)
-// Row-major intermediates make the loads of a K-chunk and the stores of an
-// output row contiguous across the warp's lanes.
+// Row-major intermediates make the loads of one k and the stores of one
+// output row contiguous across the lanes.
 #include "bf_internal.h"
 #include "cx.cuh"
 
 namespace bf {
 
 namespace {
-constexpr int MT = 16, KC = 16, WARPS = 4, THREADS = 32 * WARPS;
+constexpr int WARPS = 8, THREADS = 32 * WARPS;
+constexpr int RT = 2;    // output rows per lane
+constexpr int KC = 8;    // K per step: KC inputs and RT x KC factor entries loaded together
 
 struct Strides {
   int64_t off, rs, cs;
@@ -37,90 +51,304 @@ __device__ __forceinline__ Strides strides(int64_t off, int64_t ld, int N) {
 }
 }  // namespace
 
+// Variant 0 ("mlp"): one warp per (task, column slice, RT-row group); K in
+// steps of KC whose KC input and RT x KC factor loads are issued together.
 template <typename R>
-__global__ void __launch_bounds__(THREADS)
-stage_kernel(const StageTask* __restrict__ tasks, int ntasks, StageBases bases, int Noverride) {
+__global__ void __launch_bounds__(THREADS, 2)
+stage_mlp_kernel(const StageTask* __restrict__ tasks, int ntasks, StageBases bases, int Noverride, int lcw,
+                 int rgroups) {
   using V = typename Cx<R>::V;
-  __shared__ V smat[WARPS][MT][KC + 1];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  V (*sm)[KC + 1] = smat[warp];
-  for (int ti = blockIdx.x * WARPS + warp; ti < ntasks; ti += gridDim.x * WARPS) {
+  const int CW = 1 << lcw, RW = 32 >> lcw, GR = RW * RT;   // GR: rows per warp item
+  const int lane = threadIdx.x & 31;
+  const int ci = lane & (CW - 1), ri = lane >> lcw;
+  const int nwarps = gridDim.x * WARPS;
+  // work items: (task, column slice, row group); slices per task from the
+  // launch's N, row groups from the launch's largest M (the host keeps the
+  // item count below 2^31)
+  const int Nl = Noverride;
+  const int slices = Nl > 0 ? (Nl + CW - 1) / CW : 1;
+  const int per_task = slices * rgroups;
+  const int items = ntasks * per_task;
+  for (int w = blockIdx.x * WARPS + (threadIdx.x >> 5); w < items; w += nwarps) {
+    const int ti = w / per_task, tw = w - ti * per_task;
+    const int sl = tw / rgroups, rg = tw - sl * rgroups;
     const StageTask& tk = tasks[ti];
     const int M = tk.M, nterms = tk.nterms;
-    const int N = Noverride > 0 ? Noverride : tk.N;
+    const int i0 = rg * GR;
+    if (i0 >= M) continue;
+    const int N = Nl > 0 ? Nl : tk.N;
     const Strides so = strides(tk.out_off, tk.ldo, N);
     V* __restrict__ out = (V*)bases.p[tk.out_base] + so.off;
-    for (int c0 = 0; c0 < N; c0 += 32) {
-      const int c = c0 + lane;
-      const bool cv = c < N;
-      for (int i0 = 0; i0 < M; i0 += MT) {
-        V acc[MT];
+    // column slices of this warp: sl (fixed N) or all of them (per-task N)
+    const int c_first = Nl > 0 ? sl * CW : 0, c_last = Nl > 0 ? c_first + CW : N;
+    bool rv[RT];
 #pragma unroll
-        for (int i = 0; i < MT; ++i) acc[i] = Cx<R>::make(0, 0);
+    for (int r = 0; r < RT; ++r) rv[r] = i0 + ri + r * RW < M;
+    for (int c0 = c_first; c0 < c_last; c0 += CW) {
+      const int c = c0 + ci;
+      const bool cv = c < N;
+      V acc[RT];
+#pragma unroll
+      for (int r = 0; r < RT; ++r) acc[r] = Cx<R>::make(0, 0);
+      for (int term = 0; term < nterms; ++term) {
+        const StageTerm& T = tk.t[term];
+        const V* __restrict__ mat = (const V*)T.mat;
+        const int K = T.K, ldm = T.ldm, cj = T.conjT;
+        const Strides si = strides(T.in_off, T.ldi, N);
+        const V* __restrict__ in = (const V*)bases.p[T.in_base] + si.off + (int64_t)c * si.cs;
+        // element (i, k) of op(mat): mat[i + k ldm], or conj(mat[k + i ldm])
+        const int istep = cj ? ldm : 1, kstep = cj ? 1 : ldm;   // blocks are small: 32-bit offsets
+        const V* __restrict__ mrow = mat + (int64_t)(i0 + ri) * istep;
+        for (int k0 = 0; k0 < K; k0 += KC) {
+          V x[KC], a[RT][KC];
+#pragma unroll
+          for (int u = 0; u < KC; ++u) {
+            const bool kv = k0 + u < K;
+            x[u] = (cv && kv) ? in[(int64_t)(k0 + u) * si.rs] : Cx<R>::make(0, 0);
+#pragma unroll
+            for (int r = 0; r < RT; ++r)
+              a[r][u] = (rv[r] && kv) ? mrow[r * RW * istep + (k0 + u) * kstep]
+                                      : Cx<R>::make(0, 0);
+          }
+#pragma unroll
+          for (int u = 0; u < KC; ++u)
+#pragma unroll
+            for (int r = 0; r < RT; ++r) {
+              if (cj) a[r][u].y = -a[r][u].y;
+              cmac(acc[r], a[r][u], x[u]);
+            }
+        }
+      }
+      if (cv) {
+#pragma unroll
+        for (int r = 0; r < RT; ++r)
+          if (rv[r]) out[(int64_t)(i0 + ri + r * RW) * so.rs + (int64_t)c * so.cs] = acc[r];
+      }
+    }
+  }
+}
+
+// Variant 1 ("rows"): one warp per (task, column slice); each lane keeps
+// RT1 rows and walks K one element at a time (fewer, longer warps: cheaper
+// per output when the number of columns is large).
+constexpr int RT1 = 8;
+template <typename R>
+__global__ void __launch_bounds__(THREADS)
+stage_rows_kernel(const StageTask* __restrict__ tasks, int ntasks, StageBases bases, int Noverride, int lcw) {
+  using V = typename Cx<R>::V;
+  const int CW = 1 << lcw, RW = 32 >> lcw;
+  const int lane = threadIdx.x & 31;
+  const int ci = lane & (CW - 1), ri = lane >> lcw;
+  const int nwarps = gridDim.x * WARPS;
+  const int Nl = Noverride;
+  const int slices = Nl > 0 ? (Nl + CW - 1) / CW : 1;
+  const int items = ntasks * slices;
+  for (int w = blockIdx.x * WARPS + (threadIdx.x >> 5); w < items; w += nwarps) {
+    const int ti = w / slices, sl = w - ti * slices;
+    const StageTask& tk = tasks[ti];
+    const int M = tk.M, nterms = tk.nterms;
+    const int N = Nl > 0 ? Nl : tk.N;
+    const Strides so = strides(tk.out_off, tk.ldo, N);
+    V* __restrict__ out = (V*)bases.p[tk.out_base] + so.off;
+    const int c_first = Nl > 0 ? sl * CW : 0, c_last = Nl > 0 ? c_first + CW : N;
+    for (int c0 = c_first; c0 < c_last; c0 += CW) {
+      const int c = c0 + ci;
+      const bool cv = c < N;
+      for (int i0 = 0; i0 < M; i0 += RW * RT1) {
+        V acc[RT1];
+#pragma unroll
+        for (int r = 0; r < RT1; ++r) acc[r] = Cx<R>::make(0, 0);
         for (int term = 0; term < nterms; ++term) {
           const StageTerm& T = tk.t[term];
           const V* __restrict__ mat = (const V*)T.mat;
-          const int K = T.K, ldm = T.ldm, conjT = T.conjT;
+          const int K = T.K, ldm = T.ldm, cj = T.conjT;
           const Strides si = strides(T.in_off, T.ldi, N);
           const V* __restrict__ in = (const V*)bases.p[T.in_base] + si.off + (int64_t)c * si.cs;
-          for (int k0 = 0; k0 < K; k0 += KC) {
-            // factor tile (MT x KC) of op(mat) into shared memory
+          const int istep = cj ? ldm : 1, kstep = cj ? 1 : ldm;
+          const V* __restrict__ mrow = mat + (int64_t)(i0 + ri) * istep;
+          for (int k = 0; k < K; ++k) {
+            const V x = cv ? in[(int64_t)k * si.rs] : Cx<R>::make(0, 0);
+            const V* __restrict__ mk = mrow + k * kstep;
 #pragma unroll
-            for (int e = 0; e < (MT * KC) / 32; ++e) {
-              const int idx = lane + 32 * e;
-              int i, kk;
-              if (!conjT) {
-                i = idx % MT;
-                kk = idx / MT;
-              } else {
-                kk = idx % KC;
-                i = idx / KC;
+            for (int r = 0; r < RT1; ++r)
+              if (i0 + ri + r * RW < M) {
+                V a = mk[r * RW * istep];
+                if (cj) a.y = -a.y;
+                cmac(acc[r], a, x);
               }
-              const int gi = i0 + i, gk = k0 + kk;
-              V v = Cx<R>::make(0, 0);
-              if (gi < M && gk < K) {
-                if (!conjT) {
-                  v = mat[gi + (int64_t)gk * ldm];
-                } else {
-                  v = mat[gk + (int64_t)gi * ldm];
-                  v.y = -v.y;
-                }
-              }
-              sm[i][kk] = v;
-            }
-            V x[KC];
-#pragma unroll
-            for (int kk = 0; kk < KC; ++kk)
-              x[kk] = (cv && k0 + kk < K) ? in[(int64_t)(k0 + kk) * si.rs] : Cx<R>::make(0, 0);
-            __syncwarp();
-#pragma unroll
-            for (int i = 0; i < MT; ++i)
-#pragma unroll
-              for (int kk = 0; kk < KC; ++kk) cmac(acc[i], sm[i][kk], x[kk]);
-            __syncwarp();
           }
         }
         if (cv) {
 #pragma unroll
-          for (int i = 0; i < MT; ++i)
-            if (i0 + i < M) out[(int64_t)(i0 + i) * so.rs + (int64_t)c * so.cs] = acc[i];
+          for (int r = 0; r < RT1; ++r) {
+            const int i = i0 + ri + r * RW;
+            if (i < M) out[(int64_t)i * so.rs + (int64_t)c * so.cs] = acc[r];
+          }
         }
       }
     }
   }
 }
 
+// Variant 2 ("block"): one warp per (task, column slice); each factor block
+// (when it has at most FLAT entries) is copied whole into the warp's slice of
+// shared memory, CB stored columns at a time with consecutive lanes on
+// consecutive entries, the inputs follow KC2 rows at a time, and the
+// products read shared memory (larger blocks: chunks of KC2 columns).
+constexpr int RT2 = 16, KC2 = 8, PR2 = 64, FLAT2 = KC2 * PR2, CB2 = 8;
+template <typename R>
+constexpr size_t block_smem() {
+  return sizeof(typename Cx<R>::V) * WARPS * KC2 * (32 + PR2);
+}
+template <typename R>
+__global__ void __launch_bounds__(THREADS, 2)
+stage_block_kernel(const StageTask* __restrict__ tasks, int ntasks, StageBases bases, int Noverride, int lcw) {
+  using V = typename Cx<R>::V;
+  extern __shared__ __align__(16) uint8_t stage_smem_raw[];
+  const int CW = 1 << lcw, RW = 32 >> lcw;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ci = lane & (CW - 1), ri = lane >> lcw;
+  const int prows = RT2 * RW < PR2 ? RT2 * RW : PR2;
+  V (*xs)[32] = (V(*)[32])(stage_smem_raw + sizeof(V) * warp * KC2 * (32 + PR2));
+  V (*ms)[PR2] = (V(*)[PR2])((uint8_t*)xs + sizeof(V) * KC2 * 32);
+  V* __restrict__ fl = &ms[0][0];
+  const int nwarps = gridDim.x * WARPS;
+  const int Nl = Noverride;
+  const int slices = Nl > 0 ? (Nl + CW - 1) / CW : 1;
+  const int items = ntasks * slices;
+  for (int w = blockIdx.x * WARPS + warp; w < items; w += nwarps) {
+    const int ti = w / slices, sl = w - ti * slices;
+    const StageTask& tk = tasks[ti];
+    const int M = tk.M, nterms = tk.nterms;
+    const int N = Nl > 0 ? Nl : tk.N;
+    const Strides so = strides(tk.out_off, tk.ldo, N);
+    V* __restrict__ out = (V*)bases.p[tk.out_base] + so.off;
+    const int c_first = Nl > 0 ? sl * CW : 0, c_last = Nl > 0 ? c_first + CW : N;
+    for (int c0 = c_first; c0 < c_last; c0 += CW) {
+      const int c = c0 + ci;
+      const bool cv = c < N;
+      for (int i0 = 0; i0 < M; i0 += prows) {
+        const int mrows = M - i0 < prows ? M - i0 : prows;
+        V acc[RT2];
+#pragma unroll
+        for (int r = 0; r < RT2; ++r) acc[r] = Cx<R>::make(0, 0);
+        for (int term = 0; term < nterms; ++term) {
+          const StageTerm& T = tk.t[term];
+          const V* __restrict__ mat = (const V*)T.mat;
+          const int K = T.K, ldm = T.ldm, cj = T.conjT;
+          const Strides si = strides(T.in_off, T.ldi, N);
+          const V* __restrict__ in = (const V*)bases.p[T.in_base] + si.off + (int64_t)c * si.cs;
+          const bool whole = M * K <= FLAT2;
+          if (whole) {
+            // stored columns (length sl_, count sc) of M x K (or K x M, conj)
+            __syncwarp();
+            const int sl_ = cj ? K : M, sc = cj ? M : K;
+            for (int e0 = 0; e0 < sl_; e0 += 32) {
+              const int e = e0 + lane;
+              for (int j0 = 0; j0 < sc; j0 += CB2) {
+                V t[CB2];
+#pragma unroll
+                for (int u = 0; u < CB2; ++u)
+                  t[u] = (e < sl_ && j0 + u < sc) ? mat[e + (int64_t)(j0 + u) * ldm] : Cx<R>::make(0, 0);
+#pragma unroll
+                for (int u = 0; u < CB2; ++u)
+                  if (e < sl_ && j0 + u < sc) {
+                    if (cj) t[u].y = -t[u].y;
+                    fl[e + (j0 + u) * sl_] = t[u];
+                  }
+              }
+            }
+          }
+          for (int k0 = 0; k0 < K; k0 += KC2) {
+            const int kn = K - k0 < KC2 ? K - k0 : KC2;
+            if (!whole) __syncwarp();
+#pragma unroll
+            for (int kk = 0; kk < KC2; ++kk)
+              xs[kk][lane] = (cv && kk < kn) ? in[(int64_t)(k0 + kk) * si.rs] : Cx<R>::make(0, 0);
+            if (!whole) {
+#pragma unroll
+              for (int j = 0; j < KC2 * PR2 / 32; ++j) {
+                const int e = lane + 32 * j;
+                const int i = cj ? e / KC2 : e % PR2, kk = cj ? e % KC2 : e / PR2;
+                V a = Cx<R>::make(0, 0);
+                if (i < mrows && kk < kn) {
+                  a = cj ? mat[(k0 + kk) + (int64_t)(i0 + i) * ldm] : mat[(i0 + i) + (int64_t)(k0 + kk) * ldm];
+                  if (cj) a.y = -a.y;
+                }
+                ms[kk][i] = a;
+              }
+            }
+            __syncwarp();
+            // element (i, kk) of the chunk: whole block fl[i + k M] / fl[k + i K],
+            // chunk ms[kk][i - i0]
+            const int fi = whole ? (cj ? K : 1) : 1, fk = whole ? (cj ? 1 : M) : PR2;
+            const V* __restrict__ fb = whole ? fl + (i0 + ri) * fi + k0 * fk : &ms[0][ri];
+#pragma unroll 2
+            for (int kk = 0; kk < kn; ++kk) {
+              const V x = xs[kk][lane];
+              const V* __restrict__ fr = fb + kk * fk;
+#pragma unroll
+              for (int r = 0; r < RT2; ++r)
+                if (ri + r * RW < mrows) cmac(acc[r], fr[r * RW * fi], x);
+            }
+            __syncwarp();
+          }
+        }
+        if (cv) {
+#pragma unroll
+          for (int r = 0; r < RT2; ++r) {
+            const int i = ri + r * RW;
+            if (i < mrows) out[(int64_t)(i0 + i) * so.rs + (int64_t)c * so.cs] = acc[r];
+          }
+        }
+      }
+    }
+  }
+}
+
+// Untuned choice: the many-warp variant for up to 16 complex64 columns, the
+// whole-block variant otherwise (and for per-task column counts: peeling).
+int stage_variant_default(int nrhs, int dtype) { return dtype == BF_C64 && nrhs > 0 && nrhs <= 16 ? 0 : 2; }
+
 int launch_stage(const StageTask* d_tasks, int ntasks, int maxM, int maxN, int Noverride,
-                 const StageBases& bases, int dtype, cudaStream_t s) {
+                 const StageBases& bases, int dtype, cudaStream_t s, int variant) {
   if (Noverride > 0) maxN = Noverride;
   if (ntasks <= 0 || maxM <= 0 || maxN <= 0) return BF_OK;
-  int blocks = (ntasks + WARPS - 1) / WARPS;
-  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (variant < 0) variant = stage_variant_default(Noverride, dtype);
+  // lanes along columns: the smallest power of two >= N, at most 32 (per-task
+  // N without an override: 32)
+  int lcw = 5;
+  if (Noverride > 0) {
+    lcw = 0;
+    while ((1 << lcw) < Noverride && lcw < 5) ++lcw;
+  }
+  const int64_t slices = Noverride > 0 ? (Noverride + (1 << lcw) - 1) >> lcw : 1;
+  const int gr = (32 >> lcw) * RT;
+  const int rgroups = variant == 0 ? (maxM + gr - 1) / gr : 1;
+  const int64_t warps = (int64_t)ntasks * slices * rgroups;
+  if (warps >= ((int64_t)1 << 31)) return fail(BF_EINVAL, "stage launch too large");
+  int64_t blocks = (warps + WARPS - 1) / WARPS;
+  if (blocks > 152 * 32) blocks = 152 * 32;
   note_launch();
-  if (dtype == BF_C128)
-    stage_kernel<double><<<blocks, THREADS, 0, s>>>(d_tasks, ntasks, bases, Noverride);
-  else
-    stage_kernel<float><<<blocks, THREADS, 0, s>>>(d_tasks, ntasks, bases, Noverride);
+  if (variant == 0) {
+    if (dtype == BF_C128)
+      stage_mlp_kernel<double><<<(unsigned)blocks, THREADS, 0, s>>>(d_tasks, ntasks, bases, Noverride, lcw, rgroups);
+    else
+      stage_mlp_kernel<float><<<(unsigned)blocks, THREADS, 0, s>>>(d_tasks, ntasks, bases, Noverride, lcw, rgroups);
+  } else if (variant == 1) {
+    if (dtype == BF_C128)
+      stage_rows_kernel<double><<<(unsigned)blocks, THREADS, 0, s>>>(d_tasks, ntasks, bases, Noverride, lcw);
+    else
+      stage_rows_kernel<float><<<(unsigned)blocks, THREADS, 0, s>>>(d_tasks, ntasks, bases, Noverride, lcw);
+  } else if (dtype == BF_C128) {
+    constexpr size_t sm = block_smem<double>();
+    BF_CUDA_TRY(cudaFuncSetAttribute(stage_block_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    stage_block_kernel<double><<<(unsigned)blocks, THREADS, sm, s>>>(d_tasks, ntasks, bases, Noverride, lcw);
+  } else {
+    constexpr size_t sm = block_smem<float>();
+    BF_CUDA_TRY(cudaFuncSetAttribute(stage_block_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    stage_block_kernel<float><<<(unsigned)blocks, THREADS, sm, s>>>(d_tasks, ntasks, bases, Noverride, lcw);
+  }
   BF_CUDA_TRY(cudaGetLastError());
   return BF_OK;
 }

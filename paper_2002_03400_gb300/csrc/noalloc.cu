@@ -61,7 +61,7 @@ extern "C" int bf_apply_noalloc(bf_fact Fh, int op, int64_t nrhs, const void* x,
         return fail(BF_EINVAL,
                     "BF_C64 needs the factorization's complex64 copy: factor with BF_PREC_MIXED or call "
                     "bf_apply once with BF_C64 first");
-  cudaStream_t s = (cudaStream_t)stream;
+  cudaStream_t s = user_stream(stream);
   const size_t es = elem_bytes(dtype);
 
   // task lists: the factorization's cached device copy if bf_apply built it,
@@ -116,7 +116,8 @@ extern "C" int bf_apply_noalloc(bf_fact Fh, int op, int64_t nrhs, const void* x,
     BF_TRY(launch_gather_rows(id_in ? nullptr : perm_in, in_rows, nrhs, x, ldx, xt, in_rows, conj, dtype, s));
   StageBases bases{{xt, ping, pong, yt}};
   for (size_t i = 0; i < ap->first.size(); ++i)
-    BF_TRY(launch_stage(d_tasks + ap->first[i], ap->count[i], ap->maxM[i], (int)nrhs, (int)nrhs, bases, dtype, s));
+    BF_TRY(launch_stage(d_tasks + ap->first[i], ap->count[i], ap->maxM[i], (int)nrhs, (int)nrhs, bases, dtype, s,
+                        ap->variant_of(i, nrhs)));
   if (!direct_out)
     BF_TRY(launch_scatter_rows(id_out ? nullptr : perm_out, out_rows, nrhs, yt, out_rows, y, ldy, conj, dtype, s));
   return BF_OK;
