@@ -201,6 +201,50 @@ def serving_measure(seconds: float = 4.0):
     return out
 
 
+def batched_measure(count: int = 64, reps: int = 2):
+    """Batched workload: `count` operators between two separated circular arcs
+    (radius 1, opening angles U[30, 90] degrees, centre distance 3, 4-16
+    points per wavelength), n drawn from {1024, 2048, 4096, 8192}, leaf 32,
+    tol 1e-5, complex64 sketches with FP64 QR: bf_factor_batch (one launch per
+    kernel per phase for all operators) against one bf_factor after another,
+    wall time of the whole set (device synchronised), plus the sketch error
+    of every operator against its bound."""
+    import torch
+    from paper_2002_03400_gb300 import api, inputs
+    sizes = inputs.batched_sizes(count)
+    plans = []
+    for i, n in enumerate(sizes):
+        g = inputs.arc_pair(n, seed=100 + i)
+        plans.append(api.Plan(g.src, g.tgt, kernel=g.kernel, wavenumber=g.wavenumber, leaf=32, tol=1e-5,
+                              precision="mixed", seed=i))
+    ops = [api.Operator.kernel(p) for p in plans]
+
+    def batched():
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Fs = api.Factorization.factor_batch(plans, ops)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, Fs
+
+    def sequential():
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Fs = [api.Factorization.factor(p, o) for p, o in zip(plans, ops)]
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, Fs
+
+    batched(), sequential()   # warm-up
+    tb = min(batched()[0] for _ in range(reps))
+    ts, Fs_seq = min((sequential() for _ in range(reps)), key=lambda r: r[0])
+    _, Fs = batched()
+    errs = [F.error(o, 16, seed=5) for F, o in zip(Fs, ops)]
+    bound = max(2 * math.sqrt(p.L + 2) * 1e-5 for p in plans)
+    return {"operators": count, "n_total": int(sum(sizes)), "sizes": {str(k): sizes.count(k) for k in sorted(set(sizes))},
+            "batched_s": tb, "sequential_s": ts, "speedup": ts / tb,
+            "max_sketch_error": float(max(errs)), "error_bound": bound,
+            "all_within_bound": bool(all(e <= 2 * math.sqrt(p.L + 2) * 1e-5 for e, p in zip(errs, plans)))}
+
+
 def run_reference(args):
     """--impl reference: the FP64 oracle on the host cores, bounded sample."""
     rank = int(os.environ.get("RANK", "0"))
@@ -232,6 +276,7 @@ def main():
     ap.add_argument("--impl", default="gb300")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--profile-case", choices=["sketch", "apply", "qr", "step"], default=None,
                     help="run only a small case of one kernel family (for ncu captures)")
     ap.add_argument("--engine", default="tensor")
@@ -385,6 +430,7 @@ def main():
     e2e_s = time.perf_counter() - t0
 
     serving = serving_measure() if not args.no_serve else None
+    batched = batched_measure() if not args.no_batch else None
     peaks, peak_src = measured_peaks()
     clocks = clk.summary()
     line = {
@@ -416,6 +462,7 @@ def main():
         "gpu_launches_per_step": gpu_launches / max(1, args.steps),
         "peaks_source": peak_src,
         "serving": serving,
+        "batched": batched,
         "roofline": {"kernel": "sketch_tc_kernel (tcgen05 split-TF32, entries on the fly)", "bound": "alu",
                      "achieved": ALU_OPS_PER_ENTRY * N * N / t_sk / 1e12, "peak": alu_peak, "unit": "Tops/s",
                      "frac": ALU_OPS_PER_ENTRY * N * N / t_sk / 1e12 / alu_peak, "traffic": None,
