@@ -244,6 +244,7 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 struct RowCtx {
   float rp[6];
   float kh, kl, isg;
+  unsigned neg;   // sign bit when imaginary parts are negated (isg < 0)
   const float2* A;
   int64_t lda;
   int opN;
@@ -280,9 +281,9 @@ __device__ __forceinline__ void form4(int ek, const RowCtx& R, uint32_t pts, uin
   if (ek == EK_H2D) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const float2 v = helmholtz_ff<false>(R.rp, cxh[j], cxl[j], cyh[j], cyl[j], 0.f, 0.f, R.kh, R.kl);
+      const float2 v = helmholtz_ff<false>(R.rp, cxh[j], cxl[j], cyh[j], cyl[j], 0.f, 0.f, R.kh, R.kl, R.neg);
       re[j] = v.x;
-      im[j] = v.y * R.isg;
+      im[j] = v.y;
     }
     return;
   }
@@ -290,9 +291,9 @@ __device__ __forceinline__ void form4(int ek, const RowCtx& R, uint32_t pts, uin
   const float czh[4] = {zh.x, zh.y, zh.z, zh.w}, czl[4] = {zl.x, zl.y, zl.z, zl.w};
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    const float2 v = helmholtz_ff<true>(R.rp, cxh[j], cxl[j], cyh[j], cyl[j], czh[j], czl[j], R.kh, R.kl);
+    const float2 v = helmholtz_ff<true>(R.rp, cxh[j], cxl[j], cyh[j], cyl[j], czh[j], czl[j], R.kh, R.kl, R.neg);
     re[j] = v.x;
-    im[j] = v.y * R.isg;
+    im[j] = v.y;
   }
 }
 
@@ -403,6 +404,7 @@ sketch_tc_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__ 
     // imaginary sign: exp(-i k r) in 2D, then conjugation for the adjoint
     const float base = ek == EK_H2D ? -1.f : 1.f;
     R.isg = opN ? base : -base;
+    R.neg = R.isg < 0.f ? 0x80000000u : 0u;
   }
   const float* colp = opN ? J.srcF : J.tgtF;
   const int64_t coln = opN ? J.n : J.m;

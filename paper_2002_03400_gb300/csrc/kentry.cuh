@@ -5,11 +5,11 @@
 // pairs (hi + lo); the distance is formed in float-float with Dekker/Knuth
 // error-free transformations (its square root from an rsqrt estimate, one
 // Newton step and a float-float correction), the phase k*r in float-float is
-// reduced by pi/2 with a three-part split of pi/2 (Cody & Waite; the first
-// product subtracted exactly by FMA), and sin/cos of the reduced argument
-// |t| <= pi/4 come from their Taylor series (terms to t^9 and t^10; the
-// truncation is below 2e-9) with the quadrant applied afterwards.  Entries
-// keep ~1.5e-7 relative accuracy at k*r ~ 2e4.
+// reduced by pi/2 (Cody & Waite: the first product subtracted exactly by
+// FMA, the second in float32), and sin/cos of the reduced argument
+// |t| <= pi/4 come from near-minimax polynomials (degree 7 and 8, errors
+// below 2e-9) with the quadrant applied afterwards.  Entries keep ~1.5e-7
+// relative accuracy at k*r ~ 2e4.
 #pragma once
 #include "bf_internal.h"
 #include "cx.cuh"
@@ -49,48 +49,48 @@ __device__ __forceinline__ FF two_sum(float a, float b) {
   const float bb = s - a;
   return {s, (a - (s - bb)) + (b - bb)};
 }
-__device__ __forceinline__ FF fast_two_sum(float a, float b) {   // |a| >= |b|
-  const float s = a + b;
-  return {s, b - (s - a)};
-}
 __device__ __forceinline__ FF two_prod(float a, float b) {
   const float p = a * b;
   return {p, fmaf(a, b, -p)};
-}
-__device__ __forceinline__ FF ff_sub(float ah, float al, float bh, float bl) {
-  FF d = two_sum(ah, -bh);
-  d.l += al - bl;
-  return fast_two_sum(d.h, d.l);
 }
 __device__ __forceinline__ FF ff_sq(FF a) {
   FF p = two_prod(a.h, a.h);
   p.l = fmaf(2.0f * a.h, a.l, p.l);
   return p;
 }
-__device__ __forceinline__ FF ff_add(FF a, FF b) {
-  FF s = two_sum(a.h, b.h);
-  s.l += a.l + b.l;
-  return fast_two_sum(s.h, s.l);
-}
 
-// pi/2 = C1 + C2 + C3 (each the float nearest to the remainder) and 2/pi
+// pi/2 ~ C1 + C2 (each the float nearest to the remainder; the next term,
+// -1.7e-15, is below what the reduction needs) and 2/pi
 #define BF_PIO2_1 1.57079637050628662e+00f
 #define BF_PIO2_2 -4.37113882867379289e-08f
-#define BF_PIO2_3 -1.71512451000588187e-15f
 #define BF_2OPI 6.36619746685028076e-01f
 
-// sin t and cos t for |t| <= pi/4 from their Taylor series
-__device__ __forceinline__ void sincos_taylor(float t, float& s, float& c) {
+// sin t and cos t for |t| <= pi/4: near-minimax polynomials (absolute error
+// 1.8e-9 and 5.4e-11 before float32 rounding; coefficients from a Remez
+// exchange, fit_sincos.py)
+#define BF_S3 -1.666665077e-01f
+#define BF_S5 8.331978694e-03f
+#define BF_S7 -1.949563593e-04f
+#define BF_C2 -5.000000000e-01f
+#define BF_C4 4.166662320e-02f
+#define BF_C6 -1.388676348e-03f
+#define BF_C8 2.439045056e-05f
+__device__ __forceinline__ void sincos_poly(float t, float& s, float& c) {
   const float t2 = t * t;
-  float ps = fmaf(t2, 1.0f / 362880.0f, -1.0f / 5040.0f);
-  ps = fmaf(t2, ps, 1.0f / 120.0f);
-  ps = fmaf(t2, ps, -1.0f / 6.0f);
+  float ps = fmaf(t2, BF_S7, BF_S5);
+  ps = fmaf(t2, ps, BF_S3);
   s = fmaf(t * t2, ps, t);
-  float pc = fmaf(t2, -1.0f / 3628800.0f, 1.0f / 40320.0f);
-  pc = fmaf(t2, pc, -1.0f / 720.0f);
-  pc = fmaf(t2, pc, 1.0f / 24.0f);
-  pc = fmaf(t2, pc, -0.5f);
+  float pc = fmaf(t2, BF_C8, BF_C6);
+  pc = fmaf(t2, pc, BF_C4);
+  pc = fmaf(t2, pc, BF_C2);
   c = fmaf(t2, pc, 1.0f);
+}
+
+// 1/sqrt(x), the hardware approximation (PTX rsqrt.approx.ftz.f32)
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
 }
 
 // Magic constant 1.5 * 2^23: for |v| < 2^22, fmaf(x, y, MAGIC) - MAGIC is
@@ -98,47 +98,62 @@ __device__ __forceinline__ void sincos_taylor(float t, float& s, float& c) {
 // hold that integer modulo 2^22 (two's complement).
 #define BF_RND_MAGIC 12582912.0f
 
-// e^{i phi} for a float-float phase ph: phi = q pi/2 + t with q * C1
-// subtracted exactly by FMA, |t| <= pi/4, then the quadrant q mod 4 applied
-// (sin/cos swapped for odd q, signs from q).  Returns (cos phi, sin phi).
-__device__ __forceinline__ float2 expi_ff(FF ph) {
+// e^{i phi} for a float-float phase ph (|ph.l| <= ulp(ph.h)): phi = q pi/2
+// + t.  ph.h - q C1 is exact in one FMA (C1, the float nearest pi/2, is a
+// multiple of 2^-23 and |result| < 1); the C2 term and ph.l are ~1e-3 and
+// added in float32 (error ~1e-10), the C3 term (< 1e-10) is dropped; t then
+// carries one rounding (<= 4.7e-8).  The quadrant q mod 4 swaps sin/cos and
+// sets signs; `neg` (0 or the sign bit) also flips sin.  Returns
+// (cos phi, +-sin phi).
+__device__ __forceinline__ float2 expi_ff(FF ph, unsigned neg) {
   const float qm = fmaf(ph.h, BF_2OPI, BF_RND_MAGIC);
   const float q = qm - BF_RND_MAGIC;
   const unsigned qi = (unsigned)__float_as_int(qm);
-  const float t1 = fmaf(-q, BF_PIO2_1, ph.h);
-  const FF m2 = two_prod(q, BF_PIO2_2);
-  const FF th = two_sum(t1, -m2.h);
-  const float t = th.h + ((th.l + (ph.l - m2.l)) - q * BF_PIO2_3);
+  const float t = fmaf(-q, BF_PIO2_1, ph.h) + fmaf(-q, BF_PIO2_2, ph.l);
   float sv, cv;
-  sincos_taylor(t, sv, cv);
+  sincos_poly(t, sv, cv);
   float sn = (qi & 1) ? cv : sv, cs = (qi & 1) ? sv : cv;
-  sn = __uint_as_float(__float_as_uint(sn) ^ ((qi & 2u) << 30));
+  sn = __uint_as_float(__float_as_uint(sn) ^ (((qi & 2u) << 30) ^ neg));
   cs = __uint_as_float(__float_as_uint(cs) ^ (((qi + 1u) & 2u) << 30));
   return make_float2(cs, sn);
 }
 
+// Float-float difference and sum left unnormalised (hi + lo with |lo| a
+// few ulps of hi): their consumers below (squares, the square root's
+// correction, the phase) use both parts.
+__device__ __forceinline__ FF ff_sub_u(float ah, float al, float bh, float bl) {
+  FF d = two_sum(ah, -bh);
+  d.l += al - bl;
+  return d;
+}
+__device__ __forceinline__ FF ff_add_u(FF a, FF b) {
+  FF s = two_sum(a.h, b.h);
+  s.l += a.l + b.l;
+  return s;
+}
+
 // Helmholtz kernel entry at the float-float row point rp = (x, y, z as
 // hi/lo pairs) and column point (cxh + cxl, cyh + cyl, czh + czl):
-// returns (cos(k r) a, sin(k r) a) with a = 1/r (2D) or 1/(4 pi r) (3D);
-// the caller fixes the sign of the imaginary part (exp(-i k r) in 2D).
+// returns (cos(k r) a, +-sin(k r) a) with a = 1/r (2D) or 1/(4 pi r) (3D),
+// the sine negated when neg is the sign bit (exp(-i k r) in 2D, conjugates).
 template <bool D3>
 __device__ __forceinline__ float2 helmholtz_ff(const float (&rp)[6], float cxh, float cxl, float cyh, float cyl,
-                                               float czh, float czl, float kh, float kl) {
-  FF r2 = ff_sq(ff_sub(rp[0], rp[1], cxh, cxl));
-  r2 = ff_add(r2, ff_sq(ff_sub(rp[2], rp[3], cyh, cyl)));
-  if (D3) r2 = ff_add(r2, ff_sq(ff_sub(rp[4], rp[5], czh, czl)));
-  // 1/sqrt(r2): estimate and one Newton step; r = sqrt(r2) corrected in float-float
-  float rs = rsqrtf(r2.h);
+                                               float czh, float czl, float kh, float kl, unsigned neg) {
+  FF r2 = ff_sq(ff_sub_u(rp[0], rp[1], cxh, cxl));
+  r2 = ff_add_u(r2, ff_sq(ff_sub_u(rp[2], rp[3], cyh, cyl)));
+  if (D3) r2 = ff_add_u(r2, ff_sq(ff_sub_u(rp[4], rp[5], czh, czl)));
+  // 1/sqrt(r2): estimate and one Newton step; r = sqrt(r2) = rh0 + rl
+  // corrected in float-float
+  float rs = rsqrt_approx(r2.h);
   rs = rs * fmaf(-0.5f * r2.h * rs, rs, 1.5f);
   const float rh0 = r2.h * rs;
   const FF e = two_prod(rh0, rh0);
   const float num = ((r2.h - e.h) - e.l) + r2.l;
-  const FF r = fast_two_sum(rh0, num * (0.5f * rs));
+  const float rl = num * (0.5f * rs);
   // phase k * r
-  FF ph = two_prod(kh, r.h);
-  ph.l = fmaf(kh, r.l, fmaf(kl, r.h, ph.l));
-  ph = fast_two_sum(ph.h, ph.l);
-  const float2 c = expi_ff(ph);
+  FF ph = two_prod(kh, rh0);
+  ph.l = fmaf(kh, rl, fmaf(kl, rh0, ph.l));
+  const float2 c = expi_ff(ph, neg);
   const float a = D3 ? 0.0795774715f * rs : rs;
   return make_float2(c.x * a, c.y * a);
 }
@@ -208,9 +223,9 @@ struct Entry<float> {
     const float* c = colp + kk;
     if (type == BF_KERNEL_DFT) return dft_ff(rp[0], rp[1], c[0], c[coln]);
     if (type == BF_KERNEL_HELMHOLTZ_3D)
-      return helmholtz_ff<true>(rp, c[0], c[coln], c[2 * coln], c[3 * coln], c[4 * coln], c[5 * coln], kh, kl);
-    const float2 v = helmholtz_ff<false>(rp, c[0], c[coln], c[2 * coln], c[3 * coln], 0.f, 0.f, kh, kl);
-    return make_float2(v.x, -v.y);   // exp(-i k r) / r
+      return helmholtz_ff<true>(rp, c[0], c[coln], c[2 * coln], c[3 * coln], c[4 * coln], c[5 * coln], kh, kl, 0u);
+    // exp(-i k r) / r
+    return helmholtz_ff<false>(rp, c[0], c[coln], c[2 * coln], c[3 * coln], 0.f, 0.f, kh, kl, 0x80000000u);
   }
 };
 
