@@ -3,7 +3,7 @@
 Workload (the exact-recovery / precision configuration): the 2D Helmholtz
 kernel exp(-i k r)/r between two parallel unit segments at distance 1,
 n = m = 16384 points, 8 points per wavelength, entries formed on the fly,
-leaf 16 (L = 10), tol 1e-6, p = 2, r0 = 4, seed 0; plus the exact-recovery
+leaf 16 (L = 10), tol 1e-6, p = 2, r0 = 16, seed 0; plus the exact-recovery
 case (n = 16384 exactly-butterfly operator of rank 8, leaf 32) used as a
 black box through its own factors.
 
@@ -34,6 +34,11 @@ N = 16384
 LEAF = 16
 TOL = 1e-6
 NRHS = 64
+# initial rank guess of the adaptive leaf loops: the leaf size, so each loop
+# ends after one pass (a sketch pass costs the same for any width up to 48
+# columns on the tensor-core path; the ranks are still found by the
+# truncated QR, Alg. 2)
+R0 = 16
 # FP32 operations of one 2-D kernel entry in the mixed path (the float-float
 # formula: distance, rsqrt + Newton, float-float phase, pi/2 reduction,
 # Taylor sin/cos, quadrant and scaling), counted from its source
@@ -100,7 +105,7 @@ def cpu_oracle_sample(n_sample: int = 2048):
     op = oo.KernelOp(oo.HELMHOLTZ_2D, g.wavenumber, g.tgt, g.src)
     L = inputs.leaf_levels(n_sample, LEAF)
     t0 = time.perf_counter()
-    ob.factor(op, g.src, g.tgt, L, TOL, 2, 4, seed=0)
+    ob.factor(op, g.src, g.tgt, L, TOL, 2, R0, seed=0)
     dt = time.perf_counter() - t0
     scale = (N / n_sample) ** 1.5 * (math.log(N) / math.log(n_sample))
     return dt, dt * scale, os.cpu_count()
@@ -127,9 +132,9 @@ def profile_case(args):
         # sketch error), once per --steps
         g = inputs.line_pair(N)
         plan = api.Plan(g.src, g.tgt, kernel="helmholtz2d", wavenumber=g.wavenumber, leaf=LEAF, tol=TOL,
-                        precision="mixed")
+                        precision="mixed", r0=R0)
         op = api.Operator.kernel(plan)
-        x = torch.from_numpy(inputs.random_rhs(N, NRHS, seed=1)).to(torch.complex64).cuda()
+        x = api.colmajor(torch.from_numpy(inputs.random_rhs(N, NRHS, seed=1)).to(torch.complex64).cuda())
         for _ in range(args.steps):
             F = api.Factorization.factor(plan, op)
             F.apply(x)
@@ -137,7 +142,7 @@ def profile_case(args):
     else:
         g = inputs.line_pair(N)
         plan = api.Plan(g.src, g.tgt, kernel="helmholtz2d", wavenumber=g.wavenumber, leaf=LEAF, tol=TOL,
-                        precision="mixed")
+                        precision="mixed", r0=R0)
         F = api.Factorization.factor(plan, api.Operator.kernel(plan))
         if args.profile_case == "apply":
             x = torch.from_numpy(inputs.random_rhs(N, NRHS, seed=1)).to(torch.complex64).cuda()
@@ -301,9 +306,9 @@ def main():
     stream = torch.cuda.current_stream()
     g = inputs.line_pair(N)
     plan_mx = api.Plan(g.src, g.tgt, kernel="helmholtz2d", wavenumber=g.wavenumber, leaf=LEAF, tol=TOL,
-                       precision="mixed")
+                       precision="mixed", r0=R0)
     plan_64 = api.Plan(g.src, g.tgt, kernel="helmholtz2d", wavenumber=g.wavenumber, leaf=LEAF, tol=TOL,
-                       precision="fp64")
+                       precision="fp64", r0=R0)
     op_mx = api.Operator.kernel(plan_mx)
     op_64 = api.Operator.kernel(plan_64)
     # right-hand sides column-major, the library's layout (no copy per call)
@@ -423,7 +428,7 @@ def main():
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     plan_e = api.Plan(g.src, g.tgt, kernel="helmholtz2d", wavenumber=g.wavenumber, leaf=LEAF, tol=TOL,
-                      precision="mixed")
+                      precision="mixed", r0=R0)
     Fe = api.Factorization.factor(plan_e, api.Operator.kernel(plan_e))
     ye = Fe.apply(xh.cuda(non_blocking=True)).cpu()
     torch.cuda.synchronize()
@@ -447,7 +452,7 @@ def main():
         "dtype": "c64+f64",
         "data": "synthetic",
         "config": {"workload": "helmholtz2d_line_pair_n16384_onthefly", "n": N, "m": N, "leaf": LEAF,
-                   "L": plan_mx.L, "tol": TOL, "p": 2, "r0": 4, "precision": "mixed", "nrhs": NRHS,
+                   "L": plan_mx.L, "tol": TOL, "p": 2, "r0": R0, "precision": "mixed", "nrhs": NRHS,
                    "l2": "flushed (512 MB write) before every step"},
         "factor_s_mixed": float(np.mean(fac_s)),
         "factor_s_fp64": fp64_factor_s,
