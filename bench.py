@@ -250,6 +250,72 @@ def batched_measure(count: int = 64, reps: int = 2):
             "all_within_bound": bool(all(e <= 2 * math.sqrt(p.L + 2) * 1e-5 for e, p in zip(errs, plans)))}
 
 
+def configs_measure():
+    """The other measured configurations, each factorization device-synchronised
+    wall time (plan and operator construction excluded), after one warm-up:
+    C1 plain FP64 with a dense stored operator (line pair n = m = 1024, A
+    materialised on the device by the library's FP64 kernel entries, c128,
+    leaf 16, tol 1e-6, p 2, r0 4); C2a exact recovery (random butterfly n =
+    16384, leaf 32, rank 8, seed 1, black box = apply of its own factors, FP64,
+    tol 1e-12, error must be <= 1e-11); C4 composition (60-degree caps P1, P2,
+    P3 on unit spheres at x = -3, 0, 3, n = 65536 each, 8 points per
+    wavelength, exp(i k r)/(4 pi r); K1 = K(P2<-P1) and K2 = K(P3<-P2)
+    factorized from entries on the fly, then A = K2 K1 recompressed through
+    applies only; complex64 sketches, FP64 QR, tol 1e-6, p 4, r0 64, leaf 64)."""
+    import torch
+    from paper_2002_03400_gb300 import api, inputs
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, out
+
+    res = {}
+    # C1
+    g = inputs.line_pair(1024)
+    p1 = api.Plan(g.src, g.tgt, kernel="helmholtz2d", wavenumber=g.wavenumber, leaf=16, tol=1e-6,
+                  precision="fp64", p=2, r0=4)
+    eye = torch.eye(1024, dtype=torch.complex128, device="cuda")
+    A = api.Operator.kernel(p1).apply(eye)            # dense A, user order, FP64 entries
+    opd = api.Operator.dense(p1, A)
+    timed(lambda: api.Factorization.factor(p1, opd))
+    t1, F1 = timed(lambda: api.Factorization.factor(p1, opd))
+    res["c1_plain_fp64"] = {"factor_s": t1, "sketch_error": F1.error(opd, 16, seed=7),
+                            "bound": 2 * math.sqrt(p1.L + 2) * 1e-6, "ranks_max": int(max(F1.ranks(0, 0)))}
+    # C2a
+    eb = inputs.exact_butterfly(16384, 32, 8, seed=1)
+    Fx = api.exact_factorization(api.Plan(n=16384, leaf=32), eb)
+    opx = api.Operator.factored(Fx)
+    p2 = api.Plan(n=16384, leaf=32, tol=1e-12, precision="fp64")
+    timed(lambda: api.Factorization.factor(p2, opx))
+    t2, F2 = timed(lambda: api.Factorization.factor(p2, opx))
+    res["c2a_exact"] = {"factor_s": t2, "recovery_error": F2.error(opx, 16, seed=7), "required": 1e-11,
+                        "ranks": sorted(set(int(r) for r in F2.ranks(0, 0)))}
+    # C4
+    n = 65536
+    P1 = inputs.cap_points(n, (-3.0, 0.0, 0.0), 60.0, axis=(1.0, 0.0, 0.0))
+    P2 = inputs.cap_points(n, (0.0, 0.0, 0.0), 60.0, axis=(-1.0, 0.0, 0.0))
+    P3 = inputs.cap_points(n, (3.0, 0.0, 0.0), 60.0, axis=(-1.0, 0.0, 0.0))
+    k = 2.0 * math.pi / (8.0 * math.sqrt(math.pi / n))
+    kw = dict(leaf=64, tol=1e-6, precision="mixed", p=4, r0=64)
+    pk1 = api.Plan(P1, P2, kernel="helmholtz3d", wavenumber=k, **kw)
+    pk2 = api.Plan(P2, P3, kernel="helmholtz3d", wavenumber=k, **kw)
+    ok1, ok2 = api.Operator.kernel(pk1), api.Operator.kernel(pk2)
+    tk1, K1 = timed(lambda: api.Factorization.factor(pk1, ok1))
+    tk2, K2 = timed(lambda: api.Factorization.factor(pk2, ok2))
+    comp = api.Operator.composed(api.Operator.factored(K2), api.Operator.factored(K1))
+    pa = api.Plan(P1, P3, **kw)
+    ta, FA = timed(lambda: api.Factorization.factor(pa, comp))
+    res["c4_composition"] = {"n": n, "k1_factor_s": tk1, "k2_factor_s": tk2, "recompress_s": ta,
+                             "k1_error": K1.error(ok1, 16, seed=7), "k2_error": K2.error(ok2, 16, seed=7),
+                             "recompress_error": FA.error(comp, 16, seed=7),
+                             "bound": 2 * math.sqrt(pa.L + 2) * 1e-6,
+                             "black_box_columns": list(comp.counts())}
+    return res
+
+
 def run_reference(args):
     """--impl reference: the FP64 oracle on the host cores, bounded sample."""
     rank = int(os.environ.get("RANK", "0"))
@@ -282,6 +348,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-configs", action="store_true")
     ap.add_argument("--profile-case", choices=["sketch", "apply", "qr", "step"], default=None,
                     help="run only a small case of one kernel family (for ncu captures)")
     ap.add_argument("--engine", default="tensor")
@@ -436,6 +503,7 @@ def main():
 
     serving = serving_measure() if not args.no_serve else None
     batched = batched_measure() if not args.no_batch else None
+    configs = configs_measure() if not args.no_configs else None
     peaks, peak_src = measured_peaks()
     clocks = clk.summary()
     line = {
@@ -468,6 +536,7 @@ def main():
         "peaks_source": peak_src,
         "serving": serving,
         "batched": batched,
+        "configs": configs,
         "roofline": {"kernel": "sketch_tc_kernel (tcgen05 split-TF32, entries on the fly)", "bound": "alu",
                      "achieved": ALU_OPS_PER_ENTRY * N * N / t_sk / 1e12, "peak": alu_peak, "unit": "Tops/s",
                      "frac": ALU_OPS_PER_ENTRY * N * N / t_sk / 1e12 / alu_peak, "traffic": None,
