@@ -20,11 +20,30 @@ int fail(int code, const std::string& msg) {
 }
 
 // --------------------------------------------------------------- memory ---
+// Stream-ordered allocations come from the device's default memory pool; its
+// release threshold is raised once per device (per process) so that freed
+// blocks stay cached instead of going back to the driver at every
+// synchronisation.
+static void keep_pool(cudaStream_t s) {
+  static std::atomic<uint64_t> done{0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+  if (done.load() & (1ull << dev)) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  done.fetch_or(1ull << dev);
+  (void)s;
+}
+
 int dev_alloc(MemTracker* mt, void** p, size_t bytes, cudaStream_t s) {
   *p = nullptr;
   if (bytes == 0) bytes = 16;
   if (mt && mt->cap && mt->used + bytes > mt->cap)
     return fail(BF_ENOMEM, "allocation of " + std::to_string(bytes) + " bytes exceeds mem_cap");
+  if (s) keep_pool(s);
   cudaError_t e = s ? cudaMallocAsync(p, bytes, s) : cudaMalloc(p, bytes);
   if (e != cudaSuccess) {
     *p = nullptr;
@@ -56,6 +75,19 @@ int DevBuf::alloc(MemTracker* t, size_t b, cudaStream_t s) {
   async_ = s != nullptr;
   stream_ = s;
   return rc;
+}
+
+int DevBuf::alloc_kept(MemTracker* t, size_t b, cudaStream_t s) {
+  const int rc = alloc(t, b, s);
+  async_ = false;   // owned past the stream: freed with cudaFree
+  return rc;
+}
+
+void DevBuf::release_on(cudaStream_t s) {
+  if (!p) return;
+  dev_free(mt, p, bytes, s);
+  p = nullptr;
+  bytes = 0;
 }
 
 void DevBuf::release(cudaStream_t s) {

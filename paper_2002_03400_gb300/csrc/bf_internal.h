@@ -52,7 +52,12 @@ struct DevBuf {
   bool async_ = false;          // stream-ordered allocation (cudaMallocAsync)
   cudaStream_t stream_ = nullptr;
   int alloc(MemTracker* t, size_t b, cudaStream_t s);
+  // stream-ordered allocation on s (no device synchronisation) of storage
+  // that outlives the stream's work: released with cudaFree
+  int alloc_kept(MemTracker* t, size_t b, cudaStream_t s);
   void release(cudaStream_t s);
+  // stream-ordered free on s of a pool allocation (alloc or alloc_kept)
+  void release_on(cudaStream_t s);
 };
 
 // ------------------------------------------------------------- handles ----
@@ -289,6 +294,14 @@ struct SketchJob {
   int64_t ldy;
   int64_t ygs;            // Y columns between groups (0: kcols); set when a job is split by columns
   const int64_t* h_off;   // host copy of d_off (groups + 1 entries) or null
+  // Second output segment (tensor-core path, built-in operators): columns
+  // [kcols0, kcols) of X are the random matrix of a finer level of the same
+  // input-side tree (groups1 = groups << shift1 nodes, host offsets h_off1);
+  // their products go to Y1 (ld ldy1, group stride ygs1).  nseg = 1: none.
+  int32_t nseg, shift1;
+  int64_t kcols0, groups1, ldy1, ygs1;
+  void* Y1;
+  const int64_t* h_off1;
 };
 // Runs all jobs (same dtype) in one launch: one CTA per (job, group, row tile,
 // column tile).  Job and tile lists are uploaded to stream-ordered scratch.

@@ -174,9 +174,9 @@ int sketch_all(Batch& B, const std::vector<SketchReq>& reqs) {
 }
 
 // Lays out a stage: rows[b] x cap[b] blocks, allocates complex128 storage.
-int layout_stage(OpState& o, Stage& S, const std::vector<int32_t>& rows, const std::vector<int32_t>& cap) {
-  S.d64.release(nullptr);
-  S.d32.release(nullptr);
+int layout_stage(Batch& B, OpState& o, Stage& S, const std::vector<int32_t>& rows, const std::vector<int32_t>& cap) {
+  S.d64.release_on(B.s);   // an earlier layout of this stage (leaf passes): pool storage
+  S.d32.release_on(B.s);
   S.have32 = false;
   const size_t nb = rows.size();
   S.rows = rows;
@@ -188,12 +188,12 @@ int layout_stage(OpState& o, Stage& S, const std::vector<int32_t>& rows, const s
     tot += (int64_t)rows[b] * cap[b];
   }
   S.total = tot;
-  return S.d64.alloc(&o.F->mem, std::max<int64_t>(tot, 1) * 16, nullptr);
+  return S.d64.alloc_kept(&o.F->mem, std::max<int64_t>(tot, 1) * 16, B.s);
 }
 
 int make32(Batch& B, OpState& o, Stage& S) {
   if (B.dt != BF_C64) return BF_OK;
-  BF_TRY(S.d32.alloc(&o.F->mem, std::max<int64_t>(S.total, 1) * 8, nullptr));
+  BF_TRY(S.d32.alloc_kept(&o.F->mem, std::max<int64_t>(S.total, 1) * 8, B.s));
   BF_TRY(launch_convert(S.d64.p, S.d32.p, S.total, BF_C128, BF_C64, B.s));
   S.have32 = true;
   return BF_OK;
@@ -298,7 +298,7 @@ int leaf_phase(Batch& B, bool Vside) {
       Stage& S = o->F->st[Vside ? o->F->stage_V0() : o->F->stage_U()];
       std::vector<int32_t> rows(nb), cap(nb);
       for (int b = 0; b < nb; ++b) rows[b] = (int32_t)(off[b + 1] - off[b]), cap[b] = std::min(rows[b], o->k);
-      BF_TRY(layout_stage(*o, S, rows, cap));
+      BF_TRY(layout_stage(B, *o, S, rows, cap));
       QRJob J{o, &S, std::vector<const void*>(nb), std::vector<int64_t>(nb, out_rows), o->k, &o->ranks};
       for (int b = 0; b < nb; ++b) J.in[b] = (const char*)o->Y.p + off[b] * B.es;
       jobs.push_back(std::move(J));
@@ -437,7 +437,7 @@ int w_phase(Batch& B, int t) {
     Stage& S = o->F->st[o->F->stage_W(l)];
     std::vector<int32_t> cap(o->nb);
     for (int b = 0; b < o->nb; ++b) cap[b] = std::min(o->Ps[b], o->k);
-    BF_TRY(layout_stage(*o, S, o->Ps, cap));
+    BF_TRY(layout_stage(B, *o, S, o->Ps, cap));
     QRJob J{o, &S, std::vector<const void*>(o->nb), std::vector<int64_t>(o->nb), o->k, &o->F->rV[l]};
     for (int b = 0; b < o->nb; ++b) J.in[b] = Pb.p() + (o->poff + o->Poff[b]) * B.es, J.ld[b] = o->Ps[b];
     jobs.push_back(std::move(J));
@@ -562,7 +562,7 @@ int r_phase(Batch& B, int t) {
     Stage& S = o->F->st[o->F->stage_R(o->l)];
     std::vector<int32_t> cap(o->nb);
     for (int b = 0; b < o->nb; ++b) cap[b] = std::min(o->Ps[b], o->k);
-    BF_TRY(layout_stage(*o, S, o->Ps, cap));
+    BF_TRY(layout_stage(B, *o, S, o->Ps, cap));
     QRJob J{o, &S, std::vector<const void*>(o->nb), std::vector<int64_t>(o->nb), o->k, &o->F->rU[o->l - o->lm]};
     for (int b = 0; b < o->nb; ++b) J.in[b] = Pb.p() + (o->poff + o->Poff[b]) * B.es, J.ld[b] = o->Ps[b];
     jobs.push_back(std::move(J));
@@ -638,7 +638,7 @@ int r_phase(Batch& B, int t) {
       maxS = std::max(maxS, o->Ps[b]);
     }
     maxK = std::max(maxK, o->k);
-    BF_TRY(layout_stage(*o, SBs, rows, cols));
+    BF_TRY(layout_stage(B, *o, SBs, rows, cols));
     SBs.cols = cols;
     for (int b = 0; b < nb; ++b) {
       LSQTask tk{};

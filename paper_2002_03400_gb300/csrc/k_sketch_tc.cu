@@ -60,10 +60,11 @@ constexpr int EK_DENSE = 0, EK_H2D = 1, EK_H3D = 2, EK_DFT = 3;
 __device__ __forceinline__ int point_arrays(int ek) { return ek == EK_H3D ? 6 : ek == EK_H2D ? 4 : ek == EK_DFT ? 2 : 0; }
 
 struct TcTile {
-  int32_t job, group;
+  int32_t job, group;          // group of the output (segment 0)
   int64_t row0;
   int64_t k0, k1;              // K range of this CTA
   int64_t ws;                  // float4 offset of this (job, group, split) partial, or -1
+  int64_t g1, ws1;             // the same for segment 1 of a two-level job
 };
 struct TcRegion {              // one (job, group) region to reduce
   int64_t ws, M, kcols, ldy, ycol0;
@@ -618,18 +619,21 @@ sketch_tc_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__ 
       tmem_ld16(tq + 4 * NR + KP + c0, lm);
       tmem_wait_ld();
       if (row < M) {
+        const int64_t kc0 = J.nseg == 2 ? J.kcols0 : kcols;   // columns of segment 0
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           const int col = c0 + i;
           if (col >= kcols || col >= KP) continue;
-          if (T.ws < 0) {
-            float2* __restrict__ Y = (float2*)J.Y;
-            Y[row + ((int64_t)T.group * ygs + col) * J.ldy] =
-                make_float2(__uint_as_float(hr[i]) + __uint_as_float(lr[i]),
-                            __uint_as_float(hm[i]) + __uint_as_float(lm[i]));
+          const bool s1 = col >= kc0;
+          const int64_t cl = s1 ? col - kc0 : col, wsx = s1 ? T.ws1 : T.ws;
+          if (wsx < 0) {
+            float2* __restrict__ Y = (float2*)(s1 ? J.Y1 : J.Y);
+            const int64_t g = s1 ? T.g1 : T.group, gs = s1 ? J.ygs1 : ygs, ld = s1 ? J.ldy1 : J.ldy;
+            Y[row + (g * gs + cl) * ld] = make_float2(__uint_as_float(hr[i]) + __uint_as_float(lr[i]),
+                                                       __uint_as_float(hm[i]) + __uint_as_float(lm[i]));
           } else {
-            ws[T.ws + (int64_t)col * M + row] = make_float4(__uint_as_float(hr[i]), __uint_as_float(lr[i]),
-                                                             __uint_as_float(hm[i]), __uint_as_float(lm[i]));
+            ws[wsx + cl * M + row] = make_float4(__uint_as_float(hr[i]), __uint_as_float(lr[i]),
+                                                 __uint_as_float(hm[i]), __uint_as_float(lm[i]));
           }
         }
       }
@@ -714,6 +718,12 @@ int launch_sketch_jobs_tc(const std::vector<SketchJob>& jobs_in, MemTracker* mt,
   const int64_t WMAX = NR_MAX / 2;
   for (SketchJob j : jobs_in) {
     if (j.ygs == 0) j.ygs = j.kcols;
+    if (j.nseg == 2) {   // two-level jobs are built within the widest tile
+      if (j.kcols > WMAX || j.kcols0 < 1 || j.kcols0 >= j.kcols || !j.h_off1 || !j.h_off)
+        return fail(BF_EINVAL, "two-level sketch job out of range");
+      jobs.push_back(j);
+      continue;
+    }
     const int64_t kc = j.kcols;
     for (int64_t c0 = 0; c0 < kc; c0 += WMAX) {
       SketchJob q = j;
@@ -745,6 +755,41 @@ int launch_sketch_jobs_tc(const std::vector<SketchJob>& jobs_in, MemTracker* mt,
   for (size_t ji = 0; ji < jobs.size(); ++ji) {
     const SketchJob& j = jobs[ji];
     if (j.M <= 0 || j.kcols <= 0) continue;
+    const int64_t rt = (j.M + TM - 1) / TM;
+    if (j.nseg == 2) {
+      // CTAs cover (row tile, fine node f at the second level, K split);
+      // segment 0 (node f >> shift1) sums over all of a coarse node's fine
+      // nodes and splits, segment 1 over the splits of f
+      const int64_t G1 = j.groups1, sh = j.shift1, w0 = j.kcols0, w1 = j.kcols - j.kcols0;
+      int64_t maxk_f = 0;
+      for (int64_t f = 0; f < G1; ++f) maxk_f = std::max(maxk_f, j.h_off1[f + 1] - j.h_off1[f]);
+      const int ns = job_splits(rt * G1, (maxk_f + 15) / 16);
+      const int64_t n0 = ((int64_t)1 << sh) * ns;   // partials per coarse node
+      std::vector<int64_t> ws0(j.groups), ws1(G1, -1);
+      for (int g = 0; g < j.groups; ++g) {
+        ws0[g] = wsz;
+        regs.push_back({wsz, j.M, w0, j.ldy, (int64_t)g * j.ygs, (int32_t)n0, 0, (float2*)j.Y});
+        wsz += n0 * j.M * w0;
+      }
+      if (ns > 1)
+        for (int64_t f = 0; f < G1; ++f) {
+          ws1[f] = wsz;
+          regs.push_back({wsz, j.M, w1, j.ldy1, f * j.ygs1, ns, 0, (float2*)j.Y1});
+          wsz += (int64_t)ns * j.M * w1;
+        }
+      for (int64_t f = 0; f < G1; ++f) {
+        const int64_t ga = j.h_off1[f], gb = j.h_off1[f + 1], g0 = f >> sh;
+        const int64_t ks = ((gb - ga + ns - 1) / ns + kch - 1) / kch * kch;
+        for (int sp = 0; sp < ns; ++sp) {
+          const int64_t a = std::min<int64_t>(gb, ga + sp * ks), b = std::min<int64_t>(gb, a + ks);
+          const int64_t p0 = ws0[g0] + ((f - (g0 << sh)) * ns + sp) * j.M * w0;
+          const int64_t p1 = ns > 1 ? ws1[f] + (int64_t)sp * j.M * w1 : -1;
+          for (int64_t r0 = 0; r0 < j.M; r0 += TM)
+            tiles.push_back(TcTile{(int32_t)ji, (int32_t)g0, r0, a, b, p0, f, p1});
+        }
+      }
+      continue;
+    }
     // K ranges of the groups (host copy of the node boundaries when given)
     auto krange = [&](int g, int64_t& a, int64_t& b) {
       if (j.groups == 1) a = 0, b = j.Ktot;
@@ -759,7 +804,6 @@ int launch_sketch_jobs_tc(const std::vector<SketchJob>& jobs_in, MemTracker* mt,
       if (a < 0) known = false;
       else maxk_g = std::max(maxk_g, b - a);
     }
-    const int64_t rt = (j.M + TM - 1) / TM;
     const int ns = known ? job_splits(rt * j.groups, (maxk_g + 15) / 16) : 1;
     for (int g = 0; g < j.groups; ++g) {
       int64_t ga, gb;
@@ -778,7 +822,7 @@ int launch_sketch_jobs_tc(const std::vector<SketchJob>& jobs_in, MemTracker* mt,
           b = std::min<int64_t>(gb, a + ks);
         }
         for (int64_t r0 = 0; r0 < j.M; r0 += TM)
-          tiles.push_back(TcTile{(int32_t)ji, g, r0, a, b, ns > 1 ? ws0 + (int64_t)sp * j.M * j.kcols : -1});
+          tiles.push_back(TcTile{(int32_t)ji, g, r0, a, b, ns > 1 ? ws0 + (int64_t)sp * j.M * j.kcols : -1, 0, -1});
       }
     }
   }
