@@ -273,13 +273,13 @@ int bf_error(bf_fact F, bf_operator A, int ncols, uint64_t seed, int dtype,
              void* stream, double* err);
 
 /* Selects the engine of the complex64 sketch products for the whole process:
- * 0 (default) -- tcgen05 tensor cores wherever the sketch width is <= 64
- * (SIMT FP32 otherwise), with split-precision TF32 products: 3xTF32 when the
- * plan's tolerance is >= 5e-6, the exact three-way TF32 split (6 products,
- * FP32-level) below that and for standalone operator products;
- * 1 -- SIMT FP32 only; 2 / 3 -- tensor cores with 3xTF32 / the three-way
- * split forced.  For comparisons and diagnostics; not thread-safe against
- * running factorizations. */
+ * 0 (default) -- tcgen05 tensor cores with the exact three-way bf16 split
+ * (operands split into three bf16 parts, 6 products kept: FP32-level);
+ * 1 -- SIMT FP32 only; 2 -- tensor cores with split-precision 3xTF32
+ * (two TF32 parts, 3 products, ~2^-21 per product); 3 -- the three-way
+ * split forced (as 0).  Sketches wider than 48 columns run as column slices.
+ * For comparisons and diagnostics; not thread-safe against running
+ * factorizations. */
 int bf_set_sketch_engine(int engine);
 
 /* ------------------------------------------------------------- common -- */

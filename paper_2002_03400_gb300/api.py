@@ -108,8 +108,9 @@ def launch_count() -> int:
 
 
 def set_sketch_engine(engine: str):
-    """'tensor' (default: tcgen05 where it applies, split depth by tolerance),
-    'simt', 'tensor-3xtf32' or 'tensor-split3' (split depth forced)."""
+    """'tensor' (default: tcgen05 with the exact three-way bf16 split),
+    'simt', 'tensor-3xtf32' (two TF32 parts) or 'tensor-split3' (the
+    exact three-way bf16 split, as the default)."""
     check(lib().bf_set_sketch_engine({"tensor": 0, "simt": 1, "tensor-3xtf32": 2, "tensor-split3": 3}[engine]))
 
 

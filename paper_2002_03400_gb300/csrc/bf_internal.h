@@ -275,7 +275,7 @@ int launch_gaussian(uint64_t seed, uint32_t stream_id, int64_t row0, int64_t row
 // from the plan's points (kind 1).
 struct SketchJob {
   int32_t kind, op, ktype, groups;
-  int32_t split;          // tensor-core path: 2 = 3xTF32, 3 = exact three-way TF32 split
+  int32_t split;          // tensor-core path: 2 = 3xTF32, 3 = exact three-way bf16 split
   int32_t pad_;
   int64_t M, Ktot, kcols;
   const int64_t* d_off;

@@ -161,10 +161,11 @@ int sketch_all(Batch& B, const std::vector<SketchReq>& reqs) {
     const int64_t* d_off = opN ? P->offS_dev(q.level) : P->offT_dev(q.level);
     SketchJob j{};
     if (q.o->A->plan == P && q.o->A->sketch_job(q.op, groups, d_off, q.k, q.Om, in_rows, q.Y, out_rows, B.dt, &j)) {
-      // tensor-core split depth: 3xTF32 (~2^-21 per product) suffices when the
-      // truncation tolerance is well above it; tighter tolerances take the
-      // exact three-way split (FP32-level products)
-      j.split = P->tol < 5e-6 ? 3 : 2;
+      // tensor-core products: the exact three-way bf16 split (FP32-level
+      // products) at every tolerance -- on this GPU it is also faster than
+      // 3xTF32 (half the operand bytes and MMA instructions), which stays
+      // selectable through bf_set_sketch_engine
+      j.split = 3;
       j.h_off = (opN ? P->offS[q.level] : P->offT[q.level]).data();
       jobs.push_back(j);
     } else

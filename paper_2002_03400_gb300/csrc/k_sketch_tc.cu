@@ -1,37 +1,42 @@
 // Mixed-precision sketch products on the 5th-generation tensor cores
-// (tcgen05, kind::tf32) with split-precision TF32 products:
+// (tcgen05) with split-precision operands:
 //   Y[:, g*k + c] = sum_{j in rows_g} A[:, j] X[j, c]   (or the adjoint form)
 // for the built-in operators (Alg. 2 input, structured sketches of Sec. 4.1),
 // computed as one real GEMM per 128-row tile:
 //   [Yr | Yi] = [Ar | Ai] * [[Xr, Xi], [-Xi, Xr]].
-// Operands are split into TF32 parts a = a0 + a1 (+ a2) and the products
-// kept down to the FP32 level:
-//   SPLIT 2 (3xTF32):  a0 b0 + a0 b1 + a1 b0                 (~2^-21 relative)
-//   SPLIT 3 (6 terms): ... + a0 b2 + a1 b1 + a2 b0, the split exact (~FP32)
+// Operands are split into parts a = a0 + a1 (+ a2) and the products kept
+// down to the FP32 level:
+//   SPLIT 3 (default, kind::f16 with bf16 parts): the split is exact (8 + 8
+//     + 8 significant bits); a0 b0 + a0 b1 + a1 b0 + a0 b2 + a1 b1 + a2 b0,
+//     the dropped terms below 2^-24 |a b|;
+//   SPLIT 2 (3xTF32, kind::tf32): a0 b0 + a0 b1 + a1 b0 (~2^-21 relative).
 //
 // Per CTA (one job, one group, 128 rows, one K range, all 2k real columns),
-// K advances in chunks of 16 complex columns through double-buffered shared
-// memory, with one CTA barrier per chunk:
-//   * every thread forms 4 consecutive entries of one row (the float-float
-//     formulas of kentry.cuh on column points staged in shared memory, or
-//     loads of a stored complex64 A), splits them into TF32 parts and writes
-//     each part with one 16-byte store into the K-major, no-swizzle
-//     core-matrix layout (8 rows x 16 B per core matrix; 8 lanes fill one
-//     core matrix, so stores are free of bank conflicts);
+// K advances in chunks of 16 complex columns through an S-stage ring in
+// shared memory, with one CTA barrier per chunk:
+//   * every thread forms one row's entries for one or two 16-byte
+//     core-matrix rows of the chunk (8 bf16 or 4 TF32 values each; the
+//     float-float formulas of kentry.cuh on column points staged in shared
+//     memory, or loads of a stored complex64 A), splits them and writes each
+//     part with one 16-byte store into the K-major, no-swizzle core-matrix
+//     layout (8 rows x 16 B per core matrix; 8 lanes fill one core matrix,
+//     so stores are free of bank conflicts);
 //   * the B operand [[Xr, Xi], [-Xi, Xr]] of the chunk is built from X rows
 //     staged by cp.async two chunks ahead (column stride padded by 16 B so
 //     the 16-byte loads of 8 lanes hit distinct banks);
-//   * one thread waits (bounded) for the previous chunk's MMAs, then after
-//     the barrier issues this chunk's tcgen05.mma (M = 128, N = 2k, K = 8)
-//     and commits them to an mbarrier; the a0*b0 products accumulate in one
-//     tensor-memory accumulator, the cross terms (~2^-11 smaller) in a
-//     second one over the whole K range;
-//   * every 64 complex K all 16 warps move the main accumulator into a
+//   * one thread waits (bounded) for the MMAs of chunk c-S+1, then after the
+//     barrier issues this chunk's tcgen05.mma (M = 128, N = 2k, 32 bytes of
+//     K each) and commits them to the stage's mbarrier; the a0*b0 products
+//     accumulate in one of two tensor-memory main accumulators, the cross
+//     terms (~2^-8 smaller or less) in a correction accumulator over the
+//     whole K range;
+//   * every 64 complex K the warps move the resting main accumulator into a
 //     (hi, lo) pair kept in tensor memory with Knuth's TwoSum (so sums over
-//     n = 16384 points keep FP32 accuracy); the correction accumulator is
-//     added to lo once, at the end;
-//   * launches with few row tiles split K across CTAs; partial (hi, lo)
-//     sums go to a workspace and a second kernel adds them with TwoSum;
+//     n = 16384 points keep FP32 accuracy) while the other accumulates; the
+//     correction accumulator is added to lo once, at the end;
+//   * launches with few row tiles split K across CTAs (decided per job);
+//     partial (hi, lo) sums go to a workspace and a second kernel adds them
+//     with TwoSum;
 //   * a wait that exceeds 1 s of %globaltimer records a device flag
 //     (reported as BF_ETIMEOUT), frees the tensor memory and returns.
 #include <algorithm>
@@ -84,24 +89,28 @@ __host__ __device__ constexpr int tmem_cols(int nr) {
 }
 static_assert(5 * NR_MAX + 16 <= 512, "accumulators of the widest tile fit in tensor memory");
 
-// Shape of one tile configuration: K advances in chunks of KCH complex
-// columns (8 with the three-way split, 16 with 3xTF32); S stages of the A
+// Shape of one tile configuration: K advances in chunks of KCH = 16 complex
+// columns, operands in bf16 parts (three-way split) or TF32 parts (3xTF32);
+// S stages of the A
 // and B operands (the MMAs of a chunk may run while the next S-1 chunks are
 // formed); XS buffers of staged X rows and column points.  Shared memory
 // in byte offsets.
 template <int NR, int SPLIT>
 struct Cfg {
-  static constexpr int KCH = SPLIT == 3 ? 8 : 16;
+  static constexpr int EB = SPLIT == 3 ? 2 : 4;   // operand bytes: bf16 parts (exact split) or TF32 parts
+  static constexpr int VS = 16 / EB;              // values per 16-byte core-matrix row
+  static constexpr int KCH = 16;
   static constexpr int KR = 2 * KCH;           // real K per chunk: real parts of A, then imaginary parts
-  static constexpr int KG = KR / 4;            // core matrices along K
-  static constexpr int G = KCH / 4;            // groups of 4 columns per chunk
+  static constexpr int KG = KR * EB / 16;      // core matrices along K
+  static constexpr int G = KCH / VS;           // groups of VS columns per chunk (real or imaginary part)
   static constexpr int PT = G / 2;             // groups per thread per chunk
+  static constexpr int KSTEPS = KR * EB / 32;  // MMAs along K per chunk (32 bytes of K each)
   static constexpr int DR = 64 / KCH;          // chunks between drains of a main accumulator (64 complex K)
   static constexpr int KP = NR / 2;
   static constexpr bool TWO = tmem_cols(NR) <= 256;   // two CTAs per SM fit in tensor memory
   static constexpr uint32_t XCOL = KCH * 8 + 16;      // bytes per staged X column (16 B pad)
-  static constexpr uint32_t A_PART = TM * KR * 4, A_BUF = SPLIT * A_PART;
-  static constexpr uint32_t B_PART = NR * KR * 4, B_BUF = SPLIT * B_PART;
+  static constexpr uint32_t A_PART = TM * KR * EB, A_BUF = SPLIT * A_PART;
+  static constexpr uint32_t B_PART = NR * KR * EB, B_BUF = SPLIT * B_PART;
   static constexpr uint32_t X_BUF = KP * XCOL, P_BUF = 6 * KCH * 4;
   static constexpr uint32_t LIMIT = TWO ? 112 * 1024 : 226 * 1024;   // per CTA, static part aside
   static constexpr uint32_t total(int s) { return s * (A_BUF + B_BUF) + XS * (X_BUF + P_BUF); }
@@ -134,6 +143,10 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
 __host__ __device__ constexpr uint32_t idesc_tf32(int n) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 }
+// the same for kind::f16 with bf16 A and B (type 1)
+__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+}
 
 __device__ __forceinline__ uint32_t tf32_rna(float x) {
   uint32_t r;
@@ -141,21 +154,33 @@ __device__ __forceinline__ uint32_t tf32_rna(float x) {
   return r;
 }
 
-// TF32 parts of four values.  SPLIT 3: truncation to the leading 11
-// significant bits twice; x = p0 + p1 + p2 exactly (x - p0 has at most 13
-// significant bits, its remainder at most 2), every part a valid TF32 value.
-// SPLIT 2: round-to-nearest parts, x - p0 - p1 ~ 2^-22 |x|.
-template <int SPLIT>
-__device__ __forceinline__ void split4(const float (&x)[4], uint4 (&p)[3]) {
+// two floats -> bf16x2 (round to nearest even; x0 in the low half)
+__device__ __forceinline__ uint32_t bf16x2_rn(float x0, float x1) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(x1), "f"(x0));
+  return r;
+}
+
+// Operand parts of one 16-byte core-matrix row.
+// SPLIT 2 (4 values, TF32): round-to-nearest parts, x - p0 - p1 ~ 2^-22 |x|.
+// SPLIT 3 (8 values, bf16): x = p0 + p1 + p2 exactly -- each part rounds the
+// remainder to 8 significant bits (x has 24; x - p0 has at most 16, its
+// remainder at most 8), so the six products kept (i + j <= 2) miss only
+// terms below 2^-24 |x y|.
+template <int SPLIT, int V>
+__device__ __forceinline__ void split_row(const float (&x)[V], uint4 (&p)[3]) {
   uint32_t a[4], b[4], c[4];
+  if (SPLIT == 3) {
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    if (SPLIT == 3) {
-      a[j] = __float_as_uint(x[j]) & 0xFFFFE000u;
-      const float r1 = x[j] - __uint_as_float(a[j]);
-      b[j] = __float_as_uint(r1) & 0xFFFFE000u;
-      c[j] = __float_as_uint(r1 - __uint_as_float(b[j]));
-    } else {
+    for (int i = 0; i < 4; ++i) {
+      a[i] = bf16x2_rn(x[2 * i], x[2 * i + 1]);
+      const float r0 = x[2 * i] - __uint_as_float(a[i] << 16), r1 = x[2 * i + 1] - __uint_as_float(a[i] & 0xFFFF0000u);
+      b[i] = bf16x2_rn(r0, r1);
+      c[i] = bf16x2_rn(r0 - __uint_as_float(b[i] << 16), r1 - __uint_as_float(b[i] & 0xFFFF0000u));
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
       a[j] = tf32_rna(x[j]);
       b[j] = tf32_rna(x[j] - __uint_as_float(a[j]));
       c[j] = 0u;
@@ -218,12 +243,22 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
-__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(
-          dtmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc)
-      : "memory");
+// one MMA step: kind::tf32 for 4-byte operands, kind::f16 (bf16 A and B)
+// for 2-byte ones
+template <int EB>
+__device__ __forceinline__ void mma_step(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  if (EB == 2)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+            dtmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  else
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(
+            dtmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
 }
 
 __device__ __forceinline__ void cp_async4(uint32_t dst, const void* src, bool valid) {
@@ -255,7 +290,7 @@ struct RowCtx {
 // chunk's column points staged at pts: array d at pts + ps d bytes).
 // Columns at or past kend are not read (their entries are zeroed by the caller).
 __device__ __forceinline__ void form4(int ek, const RowCtx& R, uint32_t pts, uint32_t ps, int64_t gi,
-                                      int64_t gk0, int64_t kend, float (&re)[4], float (&im)[4]) {
+                                      int64_t gk0, int64_t kend, float* re, float* im) {
   if (ek == EK_DENSE) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -298,6 +333,14 @@ __device__ __forceinline__ void form4(int ek, const RowCtx& R, uint32_t pts, uin
   }
 }
 
+// V (4 or 8) entries of row gi at columns gk0 .. gk0+V-1, four at a time.
+template <int V>
+__device__ __forceinline__ void form_row(int ek, const RowCtx& R, uint32_t pts, uint32_t ps, int64_t gi,
+                                         int64_t gk0, int64_t kend, float (&re)[V], float (&im)[V]) {
+#pragma unroll
+  for (int h = 0; h < V / 4; ++h) form4(ek, R, pts + 16u * h, ps, gi, gk0 + 4 * h, kend, re + 4 * h, im + 4 * h);
+}
+
 // TwoSum the main accumulator at column moff into the pair (hi, lo) (and,
 // at the end, add the correction accumulator to lo) for this warp's 32
 // tensor-memory lanes; the warps sharing a lane quadrant take alternate
@@ -329,7 +372,7 @@ template <int NR, int SPLIT>
 __global__ void __launch_bounds__(THREADS, 2)
 sketch_tc_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__ tiles, float4* __restrict__ ws) {
   using C = Cfg<NR, SPLIT>;
-  constexpr int S = C::S, KCH = C::KCH, KG = C::KG, G = C::G, DR = C::DR, KP = C::KP;
+  constexpr int S = C::S, KCH = C::KCH, KG = C::KG, G = C::G, DR = C::DR, KP = C::KP, VS = C::VS;
   constexpr int COLS = tmem_cols(NR);
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ SketchJob J;
@@ -419,7 +462,7 @@ sketch_tc_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__ 
     const int li = lane + 32 * q, it = warp * C::IW + li;
     const int nr = ((it / (8 * KG)) << 3) | (it & 7), kg = (it >> 3) & (KG - 1);
     const int part = kg >= G ? 1 : 0;          // 0: rows of Ar, 1: rows of Ai
-    const int kk0 = (kg & (G - 1)) * 4;
+    const int kk0 = (kg & (G - 1)) * VS;
     const int col = nr % KP, blk = nr / KP;    // blk 0: a column of Yr, 1: of Yi
     // B = [[Xr, Xi], [-Xi, Xr]]: (part, blk) = (0,0) Xr, (0,1) Xi, (1,0) -Xi, (1,1) Xr
     const uint32_t im = (uint32_t)((part ^ blk) & 1), neg = (part == 1 && blk == 0) ? 1u : 0u;
@@ -461,7 +504,7 @@ sketch_tc_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__ 
   };
 
   const uint32_t mb0 = smem_u32(&mbar[0]);   // mbar[s] at mb0 + 8 s
-  constexpr uint32_t idesc = idesc_tf32(NR);
+  constexpr uint32_t idesc = C::EB == 2 ? idesc_bf16(NR) : idesc_tf32(NR);
   uint32_t mph = 0;    // bit s: parity of the next phase of mbar[s] to wait for
   bool ok = true;
   int drained = 0;     // groups of DR chunks whose main accumulator is in (hi, lo)
@@ -480,18 +523,18 @@ sketch_tc_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__ 
     for (int r = 0; r < C::PT; ++r) {
       if (!producer) break;
       const int kg = kg0 + 2 * r;
-      float re[4], im[4];
-      const int64_t gk0 = kb + 4 * kg;
-      form4(ek, R, sb + C::P0 + xbuf * C::P_BUF + 16u * (uint32_t)kg, KCH * 4, rvalid ? gi : row0, gk0, k1, re,
-            im);
+      float re[VS], im[VS];
+      const int64_t gk0 = kb + VS * kg;
+      form_row<VS>(ek, R, sb + C::P0 + xbuf * C::P_BUF + 4u * VS * (uint32_t)kg, KCH * 4, rvalid ? gi : row0, gk0,
+                   k1, re, im);
       if (kb + KCH > k1) {   // ragged last chunk: columns past k1 are zero
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
+        for (int j = 0; j < VS; ++j)
           if (gk0 + j >= k1) re[j] = 0.f, im[j] = 0.f;
       }
       uint4 pr[3], pm[3];
-      split4<SPLIT>(re, pr);
-      split4<SPLIT>(im, pm);
+      split_row<SPLIT, VS>(re, pr);
+      split_row<SPLIT, VS>(im, pm);
       const uint32_t ar = aB + a_st + (uint32_t)kg * CORE, ai = ar + (uint32_t)G * CORE;
 #pragma unroll
       for (int q = 0; q < SPLIT; ++q) {
@@ -507,14 +550,17 @@ sketch_tc_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__ 
         const uint32_t d = bdesc[q];
         if (!producer || d == 0xFFFFFFFFu) continue;
         const uint32_t xa = xb + ((d >> 16) & 0x3FFFu);
-        const float4 u = ld_shared_v4(xa), w = ld_shared_v4(xa + 16);
         const bool im = (d >> 30) & 1u;
         const uint32_t neg = d & 0x80000000u;
-        float v[4] = {im ? u.y : u.x, im ? u.w : u.z, im ? w.y : w.x, im ? w.w : w.z};
+        float v[VS];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) v[j] = __uint_as_float(__float_as_uint(v[j]) ^ neg);
+        for (int h = 0; h < VS / 2; ++h) {   // two complex X values per 16-byte load
+          const float4 u = ld_shared_v4(xa + 16u * h);
+          v[2 * h] = __uint_as_float(__float_as_uint(im ? u.y : u.x) ^ neg);
+          v[2 * h + 1] = __uint_as_float(__float_as_uint(im ? u.w : u.z) ^ neg);
+        }
         uint4 pv[3];
-        split4<SPLIT>(v, pv);
+        split_row<SPLIT, VS>(v, pv);
 #pragma unroll
         for (int p = 0; p < SPLIT; ++p) st_shared_v4(bB + p * C::B_PART + (d & 0xFFFFu), pv[p]);
       }
@@ -557,15 +603,17 @@ sketch_tc_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__ 
       const uint32_t carry = (c % DR) != 0 ? 1u : 0u;   // a main accumulator restarts with its group
       const uint32_t cacc = c > 0 ? 1u : 0u;             // the correction runs over all K
 #pragma unroll
-      for (int ks = 0; ks < C::KR / 8; ++ks) {
+      constexpr int EB = C::EB;
+#pragma unroll
+      for (int ks = 0; ks < C::KSTEPS; ++ks) {
         const uint64_t o = (uint64_t)(ks * 2 * CORE) >> 4;
-        mma_tf32(tmain, dA + o, dB + o, idesc, ks > 0 ? 1u : carry);           // a0 b0 -> main
-        mma_tf32(tcorr, dA + o, dB + pb + o, idesc, ks > 0 ? 1u : cacc);       // cross terms -> correction
-        mma_tf32(tcorr, dA + pa + o, dB + o, idesc, 1u);
+        mma_step<EB>(tmain, dA + o, dB + o, idesc, ks > 0 ? 1u : carry);           // a0 b0 -> main
+        mma_step<EB>(tcorr, dA + o, dB + pb + o, idesc, ks > 0 ? 1u : cacc);       // cross terms -> correction
+        mma_step<EB>(tcorr, dA + pa + o, dB + o, idesc, 1u);
         if (SPLIT == 3) {
-          mma_tf32(tcorr, dA + o, dB + 2 * pb + o, idesc, 1u);
-          mma_tf32(tcorr, dA + pa + o, dB + pb + o, idesc, 1u);
-          mma_tf32(tcorr, dA + 2 * pa + o, dB + o, idesc, 1u);
+          mma_step<EB>(tcorr, dA + o, dB + 2 * pb + o, idesc, 1u);
+          mma_step<EB>(tcorr, dA + pa + o, dB + pb + o, idesc, 1u);
+          mma_step<EB>(tcorr, dA + 2 * pa + o, dB + o, idesc, 1u);
         }
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
