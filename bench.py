@@ -39,10 +39,11 @@ NRHS = 64
 # columns on the tensor-core path; the ranks are still found by the
 # truncated QR, Alg. 2)
 R0 = 16
-# FP32 operations of one 2-D kernel entry in the mixed path (the float-float
-# formula: distance, rsqrt + Newton, float-float phase, pi/2 reduction,
-# Taylor sin/cos, quadrant and scaling), counted from its source
-ALU_OPS_PER_ENTRY = 99
+# FP32/ALU operations of one 2-D kernel entry in the mixed path, counted from
+# its source: float-float differences 16, squares 8, sum 8, rsqrt + Newton 5,
+# float-float square-root correction 8, phase 4, pi/2 reduction 5,
+# polynomial sin/cos 9, quadrant 6, scaling 2
+ALU_OPS_PER_ENTRY = 71
 
 
 def measured_peaks():
