@@ -224,8 +224,10 @@ struct StageBases {
 };
 // N of every task is replaced by Noverride when Noverride > 0.  variant:
 // kernel shape (0, 1 or 2, same results), -1 for the default for Noverride.
+// pdl: launch with a programmatic dependency on the previous kernel in s
+// (only when that kernel is itself a stage launch of the same chain).
 int launch_stage(const StageTask* d_tasks, int ntasks, int maxM, int maxN, int Noverride,
-                 const StageBases& bases, int dtype, cudaStream_t s, int variant = -1);
+                 const StageBases& bases, int dtype, cudaStream_t s, int variant = -1, bool pdl = false);
 // Times every stage-kernel variant on each stage of F's apply (direction,
 // dtype, nrhs) and keeps the fastest per stage for that right-hand-side
 // class; returns the tuned apply time in *ms (device, one call).

@@ -49,6 +49,27 @@ __device__ __forceinline__ Strides strides(int64_t off, int64_t ld, int N) {
   if (ld < 0) return {off, -ld, 1};
   return {off * N, N, 1};
 }
+
+// Programmatic dependent launch: let the next stage's grid start, warm L2
+// with this warp's first factor blocks (they do not depend on the previous
+// stage), then wait until the previous grid has completed and its writes are
+// visible.  Every read of a stage input and every write comes after the
+// wait.  Without a programmatic dependency the wait returns at once.
+template <typename V>
+__device__ __forceinline__ void stage_prologue(const StageTask* __restrict__ tasks, int ti, int lane) {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  if (ti >= 0) {
+    const StageTask& tk = tasks[ti];
+    for (int t = 0; t < tk.nterms; ++t) {
+      const StageTerm& T = tk.t[t];
+      const int64_t rows = T.conjT ? T.K : tk.M, cols = T.conjT ? tk.M : T.K;
+      const int64_t bytes = ((cols - 1) * (int64_t)T.ldm + rows) * (int64_t)sizeof(V);
+      for (int64_t off = (int64_t)lane * 128; off < bytes; off += 32 * 128)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"((const char*)T.mat + off));
+    }
+  }
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
 }  // namespace
 
 // Variant 0 ("mlp"): one warp per (task, column slice, RT-row group); K in
@@ -69,6 +90,10 @@ stage_mlp_kernel(const StageTask* __restrict__ tasks, int ntasks, StageBases bas
   const int slices = Nl > 0 ? (Nl + CW - 1) / CW : 1;
   const int per_task = slices * rgroups;
   const int items = ntasks * per_task;
+  {
+    const int w0 = blockIdx.x * WARPS + (threadIdx.x >> 5);
+    stage_prologue<V>(tasks, w0 < items ? w0 / per_task : -1, lane);
+  }
   for (int w = blockIdx.x * WARPS + (threadIdx.x >> 5); w < items; w += nwarps) {
     const int ti = w / per_task, tw = w - ti * per_task;
     const int sl = tw / rgroups, rg = tw - sl * rgroups;
@@ -143,6 +168,10 @@ stage_rows_kernel(const StageTask* __restrict__ tasks, int ntasks, StageBases ba
   const int Nl = Noverride;
   const int slices = Nl > 0 ? (Nl + CW - 1) / CW : 1;
   const int items = ntasks * slices;
+  {
+    const int w0 = blockIdx.x * WARPS + (threadIdx.x >> 5);
+    stage_prologue<V>(tasks, w0 < items ? w0 / slices : -1, lane);
+  }
   for (int w = blockIdx.x * WARPS + (threadIdx.x >> 5); w < items; w += nwarps) {
     const int ti = w / slices, sl = w - ti * slices;
     const StageTask& tk = tasks[ti];
@@ -216,6 +245,10 @@ stage_block_kernel(const StageTask* __restrict__ tasks, int ntasks, StageBases b
   const int Nl = Noverride;
   const int slices = Nl > 0 ? (Nl + CW - 1) / CW : 1;
   const int items = ntasks * slices;
+  {
+    const int w0 = blockIdx.x * WARPS + warp;
+    stage_prologue<V>(tasks, w0 < items ? w0 / slices : -1, lane);
+  }
   for (int w = blockIdx.x * WARPS + warp; w < items; w += nwarps) {
     const int ti = w / slices, sl = w - ti * slices;
     const StageTask& tk = tasks[ti];
@@ -311,7 +344,7 @@ stage_block_kernel(const StageTask* __restrict__ tasks, int ntasks, StageBases b
 int stage_variant_default(int nrhs, int dtype) { return dtype == BF_C64 && nrhs > 0 && nrhs <= 16 ? 0 : 2; }
 
 int launch_stage(const StageTask* d_tasks, int ntasks, int maxM, int maxN, int Noverride,
-                 const StageBases& bases, int dtype, cudaStream_t s, int variant) {
+                 const StageBases& bases, int dtype, cudaStream_t s, int variant, bool pdl) {
   if (Noverride > 0) maxN = Noverride;
   if (ntasks <= 0 || maxM <= 0 || maxN <= 0) return BF_OK;
   if (variant < 0) variant = stage_variant_default(Noverride, dtype);
@@ -329,26 +362,39 @@ int launch_stage(const StageTask* d_tasks, int ntasks, int maxM, int maxN, int N
   if (warps >= ((int64_t)1 << 31)) return fail(BF_EINVAL, "stage launch too large");
   int64_t blocks = (warps + WARPS - 1) / WARPS;
   if (blocks > 152 * 32) blocks = 152 * 32;
+  // launch with a programmatic dependency on the previous kernel when asked
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)blocks);
+  cfg.blockDim = dim3(THREADS);
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
   note_launch();
+  cudaError_t e = cudaSuccess;
   if (variant == 0) {
-    if (dtype == BF_C128)
-      stage_mlp_kernel<double><<<(unsigned)blocks, THREADS, 0, s>>>(d_tasks, ntasks, bases, Noverride, lcw, rgroups);
-    else
-      stage_mlp_kernel<float><<<(unsigned)blocks, THREADS, 0, s>>>(d_tasks, ntasks, bases, Noverride, lcw, rgroups);
+    cfg.dynamicSmemBytes = 0;
+    e = dtype == BF_C128
+            ? cudaLaunchKernelEx(&cfg, stage_mlp_kernel<double>, d_tasks, ntasks, bases, Noverride, lcw, rgroups)
+            : cudaLaunchKernelEx(&cfg, stage_mlp_kernel<float>, d_tasks, ntasks, bases, Noverride, lcw, rgroups);
   } else if (variant == 1) {
-    if (dtype == BF_C128)
-      stage_rows_kernel<double><<<(unsigned)blocks, THREADS, 0, s>>>(d_tasks, ntasks, bases, Noverride, lcw);
-    else
-      stage_rows_kernel<float><<<(unsigned)blocks, THREADS, 0, s>>>(d_tasks, ntasks, bases, Noverride, lcw);
+    cfg.dynamicSmemBytes = 0;
+    e = dtype == BF_C128 ? cudaLaunchKernelEx(&cfg, stage_rows_kernel<double>, d_tasks, ntasks, bases, Noverride, lcw)
+                         : cudaLaunchKernelEx(&cfg, stage_rows_kernel<float>, d_tasks, ntasks, bases, Noverride, lcw);
   } else if (dtype == BF_C128) {
     constexpr size_t sm = block_smem<double>();
     BF_CUDA_TRY(cudaFuncSetAttribute(stage_block_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    stage_block_kernel<double><<<(unsigned)blocks, THREADS, sm, s>>>(d_tasks, ntasks, bases, Noverride, lcw);
+    cfg.dynamicSmemBytes = sm;
+    e = cudaLaunchKernelEx(&cfg, stage_block_kernel<double>, d_tasks, ntasks, bases, Noverride, lcw);
   } else {
     constexpr size_t sm = block_smem<float>();
     BF_CUDA_TRY(cudaFuncSetAttribute(stage_block_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    stage_block_kernel<float><<<(unsigned)blocks, THREADS, sm, s>>>(d_tasks, ntasks, bases, Noverride, lcw);
+    cfg.dynamicSmemBytes = sm;
+    e = cudaLaunchKernelEx(&cfg, stage_block_kernel<float>, d_tasks, ntasks, bases, Noverride, lcw);
   }
+  if (e != cudaSuccess) return fail(BF_ECUDA, std::string("stage launch: ") + cudaGetErrorString(e));
   BF_CUDA_TRY(cudaGetLastError());
   return BF_OK;
 }

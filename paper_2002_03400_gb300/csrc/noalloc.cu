@@ -117,7 +117,7 @@ extern "C" int bf_apply_noalloc(bf_fact Fh, int op, int64_t nrhs, const void* x,
   StageBases bases{{xt, ping, pong, yt}};
   for (size_t i = 0; i < ap->first.size(); ++i)
     BF_TRY(launch_stage(d_tasks + ap->first[i], ap->count[i], ap->maxM[i], (int)nrhs, (int)nrhs, bases, dtype, s,
-                        ap->variant_of(i, nrhs)));
+                        ap->variant_of(i, nrhs), i > 0 && dtype == BF_C64));
   if (!direct_out)
     BF_TRY(launch_scatter_rows(id_out ? nullptr : perm_out, out_rows, nrhs, yt, out_rows, y, ldy, conj, dtype, s));
   return BF_OK;
