@@ -205,6 +205,25 @@ int bf_apply_T(bf_fact F, int op, int64_t nrhs, const void* x, int64_t ldx,
  * its duration.  BF_EINVAL for a bad op/dtype/nrhs, BF_ENOMEM, BF_ECUDA. */
 int bf_apply_tune(bf_fact F, int op, int64_t nrhs, int dtype, void* stream, float* ms_out);
 
+/* Graph-captured apply (eq. hybrid_butterfly_mat).  bf_applier_create
+ * captures the stage chain of y = F x (op BF_OP_N), F^T x (BF_OP_T) or
+ * F^H x (BF_OP_C) for nrhs right-hand sides of dtype BF_C64/BF_C128, on
+ * buffers the applier owns, once into a CUDA graph (stage-kernel shapes as
+ * tuned by bf_apply_tune before the call, else the defaults).  F must
+ * outlive the applier; free it with bf_free.  BF_EINVAL, BF_ENOMEM,
+ * BF_ECUDA. */
+typedef struct bf_applier_s* bf_applier;
+int bf_applier_create(bf_fact F, int op, int64_t nrhs, int dtype, bf_applier* out);
+
+/* One apply through the captured graph: x (device, user order, ld ldx,
+ * in_rows x nrhs as for bf_apply / bf_apply_T) is gathered into the
+ * applier's input, the graph runs, the result is scattered into y (ld ldy).
+ * Results equal bf_apply's bit for bit.  Runs of one applier are serialised
+ * (a run on another stream waits for the previous one); different appliers
+ * of one factorization may run concurrently.  BF_EINVAL for short leading
+ * dimensions, BF_ECUDA. */
+int bf_applier_run(bf_applier A, const void* x, int64_t ldx, void* y, int64_t ldy, void* stream);
+
 /* Size of the fixed device scratch array used by bf_apply_noalloc (32 MiB).
  * Every GPU on which the library is loaded holds this array until the
  * process exits, whether or not bf_apply_noalloc is ever called. */
@@ -283,7 +302,7 @@ int bf_error(bf_fact F, bf_operator A, int ncols, uint64_t seed, int dtype,
 int bf_set_sketch_engine(int engine);
 
 /* ------------------------------------------------------------- common -- */
-/* Frees a bf_plan, bf_fact or bf_operator (NULL-safe). */
+/* Frees a bf_plan, bf_fact, bf_operator or bf_applier (NULL-safe). */
 void bf_free(void* handle);
 
 /* Reason for the last failure on this thread ("" if none). */

@@ -82,6 +82,8 @@ def lib():
         "bf_set_sketch_engine": (i32, [i32]),
         "bf_launch_count": (C.c_ulonglong, []),
         "bf_apply_tune": (i32, [vp, i32, i64, i32, vp, C.POINTER(C.c_float)]),
+        "bf_applier_create": (i32, [vp, i32, i64, i32, C.POINTER(vp)]),
+        "bf_applier_run": (i32, [vp, vp, i64, vp, i64, vp]),
         "bf_gaussian": (i32, [C.c_uint64, C.c_uint32, i64, i64, i64, i64, vp, i64, i32, vp]),
     }
     for name, (res, args) in sig.items():
@@ -99,7 +101,8 @@ def exported_symbols():
             "bf_operator_callback", "bf_operator_apply", "bf_operator_counts", "bf_factor",
             "bf_factor_batch", "bf_apply",
             "bf_apply_T", "bf_apply_noalloc", "bf_ranks", "bf_fact_info", "bf_fact_import", "bf_fact_export", "bf_error",
-            "bf_free", "bf_gaussian", "bf_set_sketch_engine", "bf_launch_count", "bf_apply_tune"]
+            "bf_free", "bf_gaussian", "bf_set_sketch_engine", "bf_launch_count", "bf_apply_tune",
+            "bf_applier_create", "bf_applier_run"]
 
 
 def launch_count() -> int:
@@ -347,6 +350,10 @@ class Factorization(_Handle):
         check(lib().bf_apply_tune(self._h, OPS[op], nrhs, dt, _stream(stream), C.byref(ms)))
         return ms.value
 
+    def applier(self, nrhs: int, dtype=torch.complex64, op: str = "N") -> "Applier":
+        """A graph-captured apply for nrhs right-hand sides (bf_applier)."""
+        return Applier(self, nrhs, dtype, op)
+
     def ranks(self, side: int, level: int) -> np.ndarray:
         out = np.empty(1 << self.L, dtype=np.int32)
         check(lib().bf_ranks(self._h, side, level, out.ctypes.data))
@@ -412,3 +419,27 @@ def exact_factorization(plan: Plan, eb) -> Factorization:
     stages += [cm(eb.R[j]) for j in range(lm, L)]
     stages += [cm(eb.U)]
     return Factorization.import_blocks(plan, rV, rU, stages)
+
+
+class Applier(_Handle):
+    """bf_applier: the apply's stage chain captured once into a CUDA graph;
+    run() gathers x, launches the graph and scatters into y."""
+
+    def __init__(self, F: Factorization, nrhs: int, dtype=torch.complex64, op: str = "N"):
+        h = C.c_void_p()
+        dt = BF_C64 if dtype == torch.complex64 else BF_C128
+        check(lib().bf_applier_create(F._h, OPS[op], nrhs, dt, C.byref(h)))
+        self._h = h
+        self._keep = [F]
+        self.nrhs, self.dtype, self.op = nrhs, dtype, op
+        self.rows_out = F.m if op == "N" else F.n
+
+    def run(self, x: torch.Tensor, y: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        x = colmajor(x)
+        if x.shape[1] != self.nrhs or x.dtype != self.dtype:
+            raise ValueError("x does not match the applier's column count or dtype")
+        if y is None:
+            y = empty_cm(self.rows_out, self.nrhs, x.dtype, x.device)
+        check(lib().bf_applier_run(self._h, C.c_void_p(x.data_ptr()), _ld(x), C.c_void_p(y.data_ptr()), _ld(y),
+                                   _stream(stream)))
+        return y

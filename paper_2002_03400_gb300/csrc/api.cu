@@ -653,6 +653,22 @@ int bf_apply(bf_fact F, int64_t nrhs, const void* x, int64_t ldx, void* y, int64
   return apply_fact(h->impl, BF_OP_N, nrhs, x, ldx, y, ldy, dtype, user_stream(stream), false);
 }
 
+int bf_applier_create(bf_fact F, int op, int64_t nrhs, int dtype, bf_applier* out) {
+  auto* h = check<bf_fact_s>(F, KIND_FACT);
+  if (!h || !out) return fail(BF_EINVAL, "not a factorization");
+  *out = nullptr;
+  Applier* A = nullptr;
+  BF_TRY(applier_create(h->impl, op, nrhs, dtype, &A));
+  *out = new bf_applier_s{KIND_APPLIER, A};
+  return BF_OK;
+}
+
+int bf_applier_run(bf_applier A, const void* x, int64_t ldx, void* y, int64_t ldy, void* stream) {
+  auto* h = check<bf_applier_s>(A, KIND_APPLIER);
+  if (!h) return fail(BF_EINVAL, "not an applier");
+  return applier_run(h->impl, x, ldx, y, ldy, user_stream(stream));
+}
+
 int bf_apply_tune(bf_fact F, int op, int64_t nrhs, int dtype, void* stream, float* ms_out) {
   auto* h = check<bf_fact_s>(F, KIND_FACT);
   if (!h) return fail(BF_EINVAL, "not a factorization");
@@ -842,6 +858,11 @@ void bf_free(void* handle) {
     for (auto& a : F->ap)
       for (auto& b : a) b.tasks.release(nullptr);
     delete F;
+    h->kind = 0;
+    delete h;
+  } else if (kind == KIND_APPLIER) {
+    auto* h = (bf_applier_s*)handle;
+    applier_destroy(h->impl);
     h->kind = 0;
     delete h;
   } else if (kind == KIND_OP) {

@@ -379,4 +379,88 @@ int tune_apply(Fact* F, int op, int dtype, int64_t nrhs, cudaStream_t s, float* 
   return rc;
 }
 
+// ------------------------------------------------------- graph applier --
+// The stage chain of an apply (eq. hybrid_butterfly_mat) never touches user
+// memory when it runs on internal input/output buffers, so it is captured
+// once into a CUDA graph; a run is then a gather of x into the internal input
+// (user order -> tree order, conjugation for F^T), one graph launch, and a
+// scatter of the internal output into y.
+int applier_create(Fact* F, int op, int64_t nrhs, int dtype, Applier** out) {
+  *out = nullptr;
+  if (nrhs <= 0) return fail(BF_EINVAL, "nrhs must be positive");
+  if (dtype != BF_C64 && dtype != BF_C128) return fail(BF_EINVAL, "dtype must be BF_C64 or BF_C128");
+  if (op != BF_OP_N && op != BF_OP_T && op != BF_OP_C) return fail(BF_EINVAL, "bad op");
+  Applier* A = new Applier();
+  A->F = F;
+  A->op = op;
+  A->opC = op == BF_OP_N ? 0 : 1;
+  A->dtype = dtype;
+  A->nrhs = nrhs;
+  const Plan* P = F->plan;
+  A->in_rows = A->opC ? P->m : P->n;
+  A->out_rows = A->opC ? P->n : P->m;
+  cudaStream_t cs = nullptr;
+  int rc = BF_OK;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) rc = fail(BF_ECUDA, "stream create failed");
+  if (!rc) rc = prepare_apply(F, A->opC, dtype, cs);
+  const size_t es = elem_bytes(dtype);
+  const int64_t lvl = rc ? 0 : F->ap[A->opC][dtype].level_rows_max * nrhs;
+  if (!rc) rc = A->scratch.alloc(&F->mem, (size_t)(A->in_rows * nrhs + A->out_rows * nrhs + 2 * lvl) * es, nullptr);
+  if (!rc) {
+    char* p = (char*)A->scratch.p;
+    A->xt = p;
+    A->yt = p + A->in_rows * nrhs * es;
+    char* ping = p + (A->in_rows + A->out_rows) * nrhs * es;
+    char* pong = ping + lvl * es;
+    if (cudaStreamSynchronize(cs) != cudaSuccess ||
+        cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      rc = fail(BF_ECUDA, "graph capture could not start");
+    } else {
+      rc = run_apply_stages(F, A->opC, dtype, nrhs, A->xt, ping, pong, A->yt, cs);
+      cudaGraph_t g = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(cs, &g);
+      if (!rc && e != cudaSuccess) rc = fail(BF_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+      A->graph = g;
+      if (!rc && cudaGraphInstantiate(&A->exec, g, 0) != cudaSuccess) rc = fail(BF_ECUDA, "graph instantiate failed");
+    }
+  }
+  if (!rc && cudaEventCreateWithFlags(&A->done, cudaEventDisableTiming) != cudaSuccess)
+    rc = fail(BF_ECUDA, "event create failed");
+  if (cs) cudaStreamDestroy(cs);
+  if (rc) {
+    applier_destroy(A);
+    return rc;
+  }
+  *out = A;
+  return BF_OK;
+}
+
+int applier_run(Applier* A, const void* x, int64_t ldx, void* y, int64_t ldy, cudaStream_t s) {
+  if (ldx < A->in_rows || ldy < A->out_rows) return fail(BF_EINVAL, "leading dimension too small");
+  const Plan* P = A->F->plan;
+  const int64_t* perm_in = (const int64_t*)(A->opC ? P->d_permT.p : P->d_permS.p);
+  const int64_t* perm_out = (const int64_t*)(A->opC ? P->d_permS.p : P->d_permT.p);
+  const bool id_in = A->opC ? P->identT : P->identS, id_out = A->opC ? P->identS : P->identT;
+  const int conj = A->op == BF_OP_T ? 1 : 0;
+  if (A->ran) BF_CUDA_TRY(cudaStreamWaitEvent(s, A->done, 0));
+  BF_TRY(launch_gather_rows(id_in ? nullptr : perm_in, A->in_rows, A->nrhs, x, ldx, A->xt, A->in_rows, conj, A->dtype,
+                            s));
+  BF_CUDA_TRY(cudaGraphLaunch(A->exec, s));
+  BF_TRY(launch_scatter_rows(id_out ? nullptr : perm_out, A->out_rows, A->nrhs, A->yt, A->out_rows, y, ldy, conj,
+                             A->dtype, s));
+  BF_CUDA_TRY(cudaEventRecord(A->done, s));
+  A->ran = true;
+  return BF_OK;
+}
+
+void applier_destroy(Applier* A) {
+  if (!A) return;
+  cudaDeviceSynchronize();
+  if (A->exec) cudaGraphExecDestroy(A->exec);
+  if (A->graph) cudaGraphDestroy(A->graph);
+  if (A->done) cudaEventDestroy(A->done);
+  A->scratch.release(nullptr);
+  delete A;
+}
+
 }  // namespace bf

@@ -61,7 +61,12 @@ struct DevBuf {
 };
 
 // ------------------------------------------------------------- handles ----
-enum HandleKind : uint32_t { KIND_PLAN = 0xB0F1A001u, KIND_FACT = 0xB0F1A002u, KIND_OP = 0xB0F1A003u };
+enum HandleKind : uint32_t {
+  KIND_PLAN = 0xB0F1A001u,
+  KIND_FACT = 0xB0F1A002u,
+  KIND_OP = 0xB0F1A003u,
+  KIND_APPLIER = 0xB0F1A004u
+};
 
 struct Plan;
 struct Fact;
@@ -81,6 +86,13 @@ struct bf_fact_s {
 struct bf_operator_s {
   uint32_t kind;
   bf::Operator* impl;
+};
+namespace bf {
+struct Applier;
+}
+struct bf_applier_s {
+  uint32_t kind;
+  bf::Applier* impl;
 };
 
 namespace bf {
@@ -232,6 +244,23 @@ int launch_stage(const StageTask* d_tasks, int ntasks, int maxM, int maxN, int N
 // dtype, nrhs) and keeps the fastest per stage for that right-hand-side
 // class; returns the tuned apply time in *ms (device, one call).
 int tune_apply(Fact* F, int op, int dtype, int64_t nrhs, cudaStream_t s, float* ms);
+
+// Graph-captured apply (bf_applier): the stage chain of one (F, op, dtype,
+// nrhs) on internal buffers, captured once into a CUDA graph.
+struct Applier {
+  Fact* F = nullptr;
+  int op = 0, opC = 0, dtype = 0;
+  int64_t nrhs = 0, in_rows = 0, out_rows = 0;
+  DevBuf scratch;                      // xt | yt | ping | pong
+  void *xt = nullptr, *yt = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t done = nullptr;          // end of the last run: runs are serialised
+  bool ran = false;
+};
+int applier_create(Fact* F, int op, int64_t nrhs, int dtype, Applier** out);
+int applier_run(Applier* A, const void* x, int64_t ldx, void* y, int64_t ldy, cudaStream_t s);
+void applier_destroy(Applier* A);
 int stage_variant_default(int nrhs, int dtype);
 constexpr int STAGE_VARIANTS = 3;
 
