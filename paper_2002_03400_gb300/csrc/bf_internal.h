@@ -275,10 +275,11 @@ struct QRTask {
   double eps;         // truncation tolerance of this block's factorization
 };
 // Truncated column-pivoted Householder QR (Alg. 1 step 3); ranks[i] out.
-// in dtype: C64 or C128 (QR always in FP64); q is complex128.
+// in dtype: C128 (factored in FP64) or C64 (factored in float-float);
+// q is complex128 either way.
 int launch_qr(const QRTask* d_tasks, int ntasks, int maxS, int maxK, int in_dtype,
               int32_t* d_ranks, void* d_work, size_t work_bytes, cudaStream_t s);
-size_t qr_workspace_bytes(int ntasks, int maxS, int maxK);
+size_t qr_workspace_bytes(int ntasks, int maxS, int maxK, int in_dtype);
 
 // ------------------------------------------------------------ B solve ----
 struct LSQTask {

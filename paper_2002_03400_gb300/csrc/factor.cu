@@ -230,7 +230,7 @@ int qr_all(Batch& B, std::vector<QRJob>& jobs) {
   }
   if (tasks.empty()) return BF_OK;
   const int nt = (int)tasks.size();
-  const size_t wbytes = qr_workspace_bytes(nt, maxS, maxK);
+  const size_t wbytes = qr_workspace_bytes(nt, maxS, maxK, B.dt);
   Scratch d(B.s), w(B.s);
   BF_TRY(d.alloc(&B.mem, nt * sizeof(QRTask) + nt * sizeof(int32_t)));
   BF_CUDA_TRY(cudaMemcpyAsync(d.p(), tasks.data(), nt * sizeof(QRTask), cudaMemcpyHostToDevice, B.s));

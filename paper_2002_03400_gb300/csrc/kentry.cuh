@@ -13,6 +13,7 @@
 #pragma once
 #include "bf_internal.h"
 #include "cx.cuh"
+#include "ff.cuh"
 
 namespace bf {
 namespace dev {
@@ -38,25 +39,6 @@ __device__ __forceinline__ double2 kernel_value(int type, double wn, double tx, 
   }
   const double ir = 0.07957747154594767 / r;   // exp(i k r) / (4 pi r)
   return make_double2(cs * ir, sn * ir);
-}
-
-// ---- float-float (hi + lo) arithmetic: error-free transformations ----
-struct FF {
-  float h, l;
-};
-__device__ __forceinline__ FF two_sum(float a, float b) {
-  const float s = a + b;
-  const float bb = s - a;
-  return {s, (a - (s - bb)) + (b - bb)};
-}
-__device__ __forceinline__ FF two_prod(float a, float b) {
-  const float p = a * b;
-  return {p, fmaf(a, b, -p)};
-}
-__device__ __forceinline__ FF ff_sq(FF a) {
-  FF p = two_prod(a.h, a.h);
-  p.l = fmaf(2.0f * a.h, a.l, p.l);
-  return p;
 }
 
 // pi/2 ~ C1 + C2 (each the float nearest to the remainder; the next term,
