@@ -456,6 +456,23 @@ def main():
     gbs32, t32, b32 = apply_gbs(F, x32)
     gbs64, t64, b64 = apply_gbs(F64, x)
 
+    # the mixed path with its pivoted QR and truncation in FP64
+    # (bf_options.qr_fp64) instead of float-float: factor time and error
+    plan_q = api.Plan(g.src, g.tgt, kernel="helmholtz2d", wavenumber=g.wavenumber, leaf=LEAF, tol=TOL,
+                      precision="mixed", r0=R0, qr_fp64=True)
+    op_q = api.Operator.kernel(plan_q)
+    q_s = []
+    for _ in range(3):
+        flush.fill_(1.0)
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        Fq = api.Factorization.factor(plan_q, op_q)
+        q1.record(stream)
+        torch.cuda.synchronize()
+        q_s.append(q0.elapsed_time(q1) / 1e3)
+    qr64 = {"factor_s": float(np.mean(q_s[1:])),
+            "sketch_error": Fq.error(op_q, 16, seed=7, dtype=torch.complex64)}
+
     # roofline of the dominant kernel (the on-the-fly sketch product): one
     # launch over all m x n entries with the widest sketch width of the run,
     # timed with CUDA events on the launching stream
@@ -525,6 +542,7 @@ def main():
                    "l2": "flushed (512 MB write) before every step"},
         "factor_s_mixed": float(np.mean(fac_s)),
         "factor_s_fp64": fp64_factor_s,
+        "mixed_with_fp64_qr": qr64,
         "sketch_error_mixed": float(np.mean(errs)),
         "sketch_error_fp64": err64,
         "apply_gbs_c64": gbs32,

@@ -60,8 +60,9 @@ typedef enum { BF_C64 = 0, BF_C128 = 1 } bf_dtype;
 /* op selects A (N), A^T (T) or A^H (C). */
 typedef enum { BF_OP_N = 0, BF_OP_T = 1, BF_OP_C = 2 } bf_op;
 /* FP64: every product in complex128.  MIXED: sketch products, peeling and
- * the factor copies used by them in complex64 (FP32 arithmetic); pivoted QR,
- * truncation and the B least squares in FP64. */
+ * the factor copies used by them in complex64 (FP32 arithmetic); the B least
+ * squares in FP64; pivoted QR and truncation in float-float (~2^-46, on the
+ * FP32 pipe), or in FP64 when bf_options.qr_fp64 is set. */
 typedef enum { BF_PREC_FP64 = 0, BF_PREC_MIXED = 1 } bf_precision;
 
 typedef enum {
@@ -84,6 +85,8 @@ typedef struct {
   uint64_t seed;       /* seed of the counter-based sketch generator        */
   int precision;       /* bf_precision (default BF_PREC_FP64)               */
   size_t mem_cap;      /* device-byte cap per handle, 0 = none              */
+  int qr_fp64;         /* MIXED only: 1 = pivoted QR and truncation in FP64
+                          instead of float-float (default 0)                */
 } bf_options;
 
 /* Fills *opt with the defaults above. */

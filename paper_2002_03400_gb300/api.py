@@ -33,7 +33,7 @@ class BFError(RuntimeError):
 
 class Options(C.Structure):
     _fields_ = [("p", C.c_int), ("r0", C.c_int), ("r_max", C.c_int), ("seed", C.c_uint64),
-                ("precision", C.c_int), ("mem_cap", C.c_size_t)]
+                ("precision", C.c_int), ("mem_cap", C.c_size_t), ("qr_fp64", C.c_int)]
 
 
 class KernelDesc(C.Structure):
@@ -175,13 +175,15 @@ class Plan(_Handle):
     """Trees and parameters (bf_plan_create)."""
 
     def __init__(self, src=None, tgt=None, n=None, m=None, kernel="none", wavenumber=0.0, leaf=16,
-                 tol=1e-6, p=2, r0=4, r_max=1024, seed=0, precision="fp64", mem_cap=0):
+                 tol=1e-6, p=2, r0=4, r_max=1024, seed=0, precision="fp64", mem_cap=0,
+                 qr_fp64=False):
         L = lib()
         opt = Options()
         L.bf_options_default(C.byref(opt))
         opt.p, opt.r0, opt.r_max, opt.seed = p, r0, r_max, seed
         opt.precision = PREC[precision] if isinstance(precision, str) else int(precision)
         opt.mem_cap = mem_cap
+        opt.qr_fp64 = 1 if qr_fp64 else 0
         kd = KernelDesc(KERNELS[kernel] if isinstance(kernel, str) else int(kernel), float(wavenumber))
         self._keep = []
         if src is not None:

@@ -343,6 +343,7 @@ void bf_options_default(bf_options* o) {
   o->seed = 0;
   o->precision = BF_PREC_FP64;
   o->mem_cap = 0;
+  o->qr_fp64 = 0;
 }
 
 const char* bf_last_error(void) { return g_err.c_str(); }
@@ -361,6 +362,7 @@ int bf_plan_create(const double* src, int64_t n, const double* tgt, int64_t m, i
   if (opt) o = *opt;
   if (o.p < 0 || o.r0 < 1 || o.r_max < o.r0) return fail(BF_EINVAL, "bad p, r0 or r_max");
   if (o.precision != BF_PREC_FP64 && o.precision != BF_PREC_MIXED) return fail(BF_EINVAL, "bad precision");
+  if (o.qr_fp64 != 0 && o.qr_fp64 != 1) return fail(BF_EINVAL, "bad qr_fp64");
   int L = 0;
   const int64_t mx = std::max(n, m);
   while ((mx + ((int64_t)1 << L) - 1) >> L > leaf) ++L;

@@ -275,11 +275,11 @@ struct QRTask {
   double eps;         // truncation tolerance of this block's factorization
 };
 // Truncated column-pivoted Householder QR (Alg. 1 step 3); ranks[i] out.
-// in dtype: C128 (factored in FP64) or C64 (factored in float-float);
-// q is complex128 either way.
-int launch_qr(const QRTask* d_tasks, int ntasks, int maxS, int maxK, int in_dtype,
+// in dtype: C128 (factored in FP64) or C64 (factored in float-float, or in
+// FP64 when fp64 is set); q is complex128 either way.
+int launch_qr(const QRTask* d_tasks, int ntasks, int maxS, int maxK, int in_dtype, bool fp64,
               int32_t* d_ranks, void* d_work, size_t work_bytes, cudaStream_t s);
-size_t qr_workspace_bytes(int ntasks, int maxS, int maxK, int in_dtype);
+size_t qr_workspace_bytes(int ntasks, int maxS, int maxK, int in_dtype, bool fp64);
 
 // ------------------------------------------------------------ B solve ----
 struct LSQTask {

@@ -230,13 +230,14 @@ int qr_all(Batch& B, std::vector<QRJob>& jobs) {
   }
   if (tasks.empty()) return BF_OK;
   const int nt = (int)tasks.size();
-  const size_t wbytes = qr_workspace_bytes(nt, maxS, maxK, B.dt);
+  const bool fp64 = B.ops[0].P->opt.qr_fp64 != 0;
+  const size_t wbytes = qr_workspace_bytes(nt, maxS, maxK, B.dt, fp64);
   Scratch d(B.s), w(B.s);
   BF_TRY(d.alloc(&B.mem, nt * sizeof(QRTask) + nt * sizeof(int32_t)));
   BF_CUDA_TRY(cudaMemcpyAsync(d.p(), tasks.data(), nt * sizeof(QRTask), cudaMemcpyHostToDevice, B.s));
   int32_t* d_r = (int32_t*)(d.p() + nt * sizeof(QRTask));
   if (wbytes) BF_TRY(w.alloc(&B.mem, wbytes));
-  BF_TRY(launch_qr((const QRTask*)d.p(), nt, maxS, maxK, B.dt, d_r, w.p(), wbytes, B.s));
+  BF_TRY(launch_qr((const QRTask*)d.p(), nt, maxS, maxK, B.dt, fp64, d_r, w.p(), wbytes, B.s));
   std::vector<int32_t> h(nt);
   BF_CUDA_TRY(cudaMemcpyAsync(h.data(), d_r, nt * sizeof(int32_t), cudaMemcpyDeviceToHost, B.s));
   BF_CUDA_TRY(cudaStreamSynchronize(B.s));
@@ -678,6 +679,7 @@ int factor_batch(int count, Plan* const* P, Operator* const* A, cudaStream_t s, 
     if (A[i]->m != P[i]->m || A[i]->n != P[i]->n)
       return fail(BF_EINVAL, "operator shape does not match its plan (batch entry " + std::to_string(i) + ")");
     if (P[i]->opt.precision != prec) return fail(BF_EINVAL, "all plans of a batch must share one precision");
+    if (P[i]->opt.qr_fp64 != P[0]->opt.qr_fp64) return fail(BF_EINVAL, "all plans of a batch must share qr_fp64");
   }
   const auto t0 = std::chrono::steady_clock::now();
   Batch B;

@@ -23,8 +23,9 @@
 // busy while the trailing matrix shrinks.  Q is formed in place of the
 // reflectors, backwards, one barrier per reflector.
 //
-// The complex128 blocks use the FP64 kernel (qr_kernel): one thread per
-// column, dot products and updates sequential over the rows.  Either
+// The complex128 blocks (and complex64 ones when FP64 is asked for) use the
+// FP64 kernel (qr_kernel): one thread per column, dot products and updates
+// sequential over the rows.  Either
 // kernel keeps its block in shared memory when it fits, else in a per-task
 // global workspace (same code, pointer switch).
 #include "bf_internal.h"
@@ -477,8 +478,8 @@ int launch_qr_ff(const QRTask* d_tasks, int ntasks, int maxS, int maxK, int32_t*
 }
 }  // namespace
 
-size_t qr_workspace_bytes(int ntasks, int maxS, int maxK, int in_dtype) {
-  if (in_dtype == BF_C64) {
+size_t qr_workspace_bytes(int ntasks, int maxS, int maxK, int in_dtype, bool fp64) {
+  if (in_dtype == BF_C64 && !fp64) {
     const size_t blk = block_ff_bytes(maxS, maxK, rg_for(maxS));
     if (blk + (size_t)meta_ff_bytes(maxS, maxK) <= QR_SMEM_LIMIT) return 0;
     return blk * (size_t)ntasks;
@@ -488,10 +489,10 @@ size_t qr_workspace_bytes(int ntasks, int maxS, int maxK, int in_dtype) {
   return blk * (size_t)ntasks;
 }
 
-int launch_qr(const QRTask* d_tasks, int ntasks, int maxS, int maxK, int in_dtype, int32_t* d_ranks,
+int launch_qr(const QRTask* d_tasks, int ntasks, int maxS, int maxK, int in_dtype, bool fp64, int32_t* d_ranks,
               void* d_work, size_t work_bytes, cudaStream_t s) {
   if (ntasks <= 0) return BF_OK;
-  if (in_dtype == BF_C64) {
+  if (in_dtype == BF_C64 && !fp64) {
     switch (rg_for(maxS)) {
       case 2: return launch_qr_ff<2>(d_tasks, ntasks, maxS, maxK, d_ranks, d_work, work_bytes, s);
       case 4: return launch_qr_ff<4>(d_tasks, ntasks, maxS, maxK, d_ranks, d_work, work_bytes, s);
@@ -505,10 +506,16 @@ int launch_qr(const QRTask* d_tasks, int ntasks, int maxS, int maxK, int in_dtyp
     return fail(BF_EINVAL, "QR workspace too small");
   const int64_t stride = (int64_t)(blk / sizeof(double2));
   const int nthr = threads_for(maxK);
-  BF_CUDA_TRY(cudaFuncSetAttribute(qr_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)(QR_SMEM_LIMIT + 4096)));
   note_launch();
-  qr_kernel<double2><<<ntasks, nthr, smem, s>>>(d_tasks, d_ranks, (double2*)d_work, stride, maxK, use_smem);
+  if (in_dtype == BF_C128) {
+    BF_CUDA_TRY(cudaFuncSetAttribute(qr_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(QR_SMEM_LIMIT + 4096)));
+    qr_kernel<double2><<<ntasks, nthr, smem, s>>>(d_tasks, d_ranks, (double2*)d_work, stride, maxK, use_smem);
+  } else {
+    BF_CUDA_TRY(cudaFuncSetAttribute(qr_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(QR_SMEM_LIMIT + 4096)));
+    qr_kernel<float2><<<ntasks, nthr, smem, s>>>(d_tasks, d_ranks, (double2*)d_work, stride, maxK, use_smem);
+  }
   BF_CUDA_TRY(cudaGetLastError());
   return BF_OK;
 }

@@ -41,7 +41,7 @@ def test_options_defaults_and_error_string(libpath):
     from paper_2002_03400_gb300 import api
     o = api.Options()
     api.lib().bf_options_default(ctypes.byref(o))
-    assert (o.p, o.r0, o.r_max, o.seed, o.precision, o.mem_cap) == (2, 4, 1024, 0, 0, 0)
+    assert (o.p, o.r0, o.r_max, o.seed, o.precision, o.mem_cap, o.qr_fp64) == (2, 4, 1024, 0, 0, 0, 0)
     rc = api.lib().bf_bisect(None, 0, 0, 3, None, None)
     assert rc == -1 and b"bad arguments" in api.lib().bf_last_error()
 

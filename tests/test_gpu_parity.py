@@ -101,21 +101,22 @@ def test_apply_strided_and_empty():
 
 # ------------------------------------------------------------------- factorization
 
-def _dense_case(n, leaf, eps, precision, geom="line", seed=0):
+def _dense_case(n, leaf, eps, precision, geom="line", seed=0, qr_fp64=False):
     g = {"line": lambda: inputs.line_pair(n), "arc": lambda: inputs.arc_pair(n, seed=5),
          "cap": lambda: inputs.cap_pair(n)}[geom]()
     kern = oo.HELMHOLTZ_3D if geom == "cap" else oo.HELMHOLTZ_2D
     A = oo.kernel_entries(kern, g.wavenumber, g.tgt, g.src)
     plan = api.Plan(g.src, g.tgt, kernel=int(kern), wavenumber=g.wavenumber, leaf=leaf, tol=eps,
-                    precision=precision, seed=seed)
+                    precision=precision, seed=seed, qr_fp64=qr_fp64)
     return g, A, plan
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_factor_dense_line_matches_oracle(precision):
-    """Plain FP64 method on the 1024-point parallel-lines workload."""
+@pytest.mark.parametrize("precision,qr_fp64", [("fp64", False), ("mixed", False), ("mixed", True)])
+def test_factor_dense_line_matches_oracle(precision, qr_fp64):
+    """Plain FP64 method on the 1024-point parallel-lines workload; the mixed
+    path with its float-float QR (default) and with the FP64 QR."""
     n, leaf, eps = 1024, 16, 1e-6
-    g, A, plan = _dense_case(n, leaf, eps, precision)
+    g, A, plan = _dense_case(n, leaf, eps, precision, qr_fp64=qr_fp64)
     pS, offS, pT, offT = plan.trees()
     op = api.Operator.dense(plan, T(A))
     F = api.Factorization.factor(plan, op)
@@ -133,6 +134,29 @@ def test_factor_dense_line_matches_oracle(precision):
     e = F.error(op, 16, seed=5)
     eo = ob.sketch_error(dop, Fo, seed=5)
     assert e <= bound(plan.L, eps) and abs(e - eo) <= 1e-6
+
+
+def test_mixed_qr_float_float_vs_fp64():
+    """The mixed path's float-float QR and its FP64 QR reveal the same ranks
+    (up to +-1 at the threshold) and the same sketch-error level."""
+    n, leaf, eps = 4096, 16, 1e-6
+    g = inputs.line_pair(n)
+    out = {}
+    for q in (False, True):
+        plan = api.Plan(g.src, g.tgt, kernel="helmholtz2d", wavenumber=g.wavenumber, leaf=leaf, tol=eps,
+                        precision="mixed", r0=16, qr_fp64=q)
+        op = api.Operator.kernel(plan)
+        F = api.Factorization.factor(plan, op)
+        out[q] = (F, F.error(op, 16, seed=3, dtype=torch.complex64), plan)
+    (Ff, ef, plan), (Fd, ed, _) = out[False], out[True]
+    worst = 0
+    for j in range(plan.lm + 1):
+        worst = max(worst, int(np.max(np.abs(Ff.ranks(0, j) - Fd.ranks(0, j)))))
+    for j in range(plan.lm, plan.L + 1):
+        worst = max(worst, int(np.max(np.abs(Ff.ranks(1, j) - Fd.ranks(1, j)))))
+    assert worst <= 1
+    assert ef <= bound(plan.L, eps) and ed <= bound(plan.L, eps)
+    assert abs(ef - ed) <= 0.1 * bound(plan.L, eps)
 
 
 @pytest.mark.parametrize("geom,n,m,leaf", [("arc", 1000, 900, 16), ("cap", 777, 700, 24), ("line", 300, 300, 8)])
