@@ -304,6 +304,19 @@ int bf_error(bf_fact F, bf_operator A, int ncols, uint64_t seed, int dtype,
  * factorizations. */
 int bf_set_sketch_engine(int engine);
 
+/* Entry images for the whole process (mixed precision, built-in kernel
+ * operators): on = 1 (default) -- a factorization first forms every kernel
+ * entry once per orientation (A and A^H), already split into the three bf16
+ * parts in the tensor-core operand layout (24 bytes per entry and
+ * orientation, e.g. 6.4 GB for n = m = 16384), and every structured sketch
+ * of Alg. 2 reads that image instead of re-forming the m x n entries;
+ * products are bit-identical either way.  Used while both images fit in
+ * half of the free device memory and under mem_cap; freed when the
+ * factorization returns.  on = 0 -- entries formed on the fly in every
+ * sketch.  Errors: BF_EINVAL unless on is 0 or 1.  Not thread-safe against
+ * running factorizations. */
+int bf_set_entry_images(int on);
+
 /* ------------------------------------------------------------- common -- */
 /* Frees a bf_plan, bf_fact, bf_operator or bf_applier (NULL-safe). */
 void bf_free(void* handle);

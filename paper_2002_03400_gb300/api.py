@@ -80,6 +80,7 @@ def lib():
         "bf_error": (i32, [vp, vp, i32, C.c_uint64, i32, vp, C.POINTER(dbl)]),
         "bf_free": (None, [vp]),
         "bf_set_sketch_engine": (i32, [i32]),
+        "bf_set_entry_images": (i32, [i32]),
         "bf_launch_count": (C.c_ulonglong, []),
         "bf_apply_tune": (i32, [vp, i32, i64, i32, vp, C.POINTER(C.c_float)]),
         "bf_applier_create": (i32, [vp, i32, i64, i32, C.POINTER(vp)]),
@@ -101,7 +102,7 @@ def exported_symbols():
             "bf_operator_callback", "bf_operator_apply", "bf_operator_counts", "bf_factor",
             "bf_factor_batch", "bf_apply",
             "bf_apply_T", "bf_apply_noalloc", "bf_ranks", "bf_fact_info", "bf_fact_import", "bf_fact_export", "bf_error",
-            "bf_free", "bf_gaussian", "bf_set_sketch_engine", "bf_launch_count", "bf_apply_tune",
+            "bf_free", "bf_gaussian", "bf_set_sketch_engine", "bf_set_entry_images", "bf_launch_count", "bf_apply_tune",
             "bf_applier_create", "bf_applier_run"]
 
 
@@ -115,6 +116,13 @@ def set_sketch_engine(engine: str):
     'simt', 'tensor-3xtf32' (two TF32 parts) or 'tensor-split3' (the
     exact three-way bf16 split, as the default)."""
     check(lib().bf_set_sketch_engine({"tensor": 0, "simt": 1, "tensor-3xtf32": 2, "tensor-split3": 3}[engine]))
+
+
+def set_entry_images(on: bool):
+    """Entry images on (default: a mixed-precision factorization of a built-in
+    kernel operator forms its entries once, bf16-split, and every sketch reads
+    them) or off (entries formed on the fly in every sketch)."""
+    check(lib().bf_set_entry_images(1 if on else 0))
 
 
 def check(rc: int):

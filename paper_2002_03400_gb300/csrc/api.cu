@@ -235,6 +235,7 @@ struct DenseOp : PlanOp {
 };
 
 struct KernelOp : PlanOp {
+  bool builtin_kernel() const override { return true; }
   bool make_job(int op, const GemmGroups& g, const void* X, int64_t ldx, void* Y, int64_t ldy, int dtype,
                 SketchJob* job) override {
     *job = kernel_job(plan, op, g, X, ldx, Y, ldy);
@@ -609,6 +610,7 @@ int bf_factor(bf_plan plan, bf_operator A, void* stream, bf_fact* out) {
 }
 
 int bf_set_sketch_engine(int engine) { return set_sketch_engine(engine); }
+int bf_set_entry_images(int on) { return set_entry_images(on); }
 
 unsigned long long bf_launch_count(void) { return bf::launches_so_far(); }
 

@@ -136,6 +136,8 @@ struct Operator {
                          void* Y, int64_t ldy, int dtype, cudaStream_t s) {
     return fail(BF_EUNSUPPORTED, "operator has no tree-order product");
   }
+  // built-in kernel operator (its entries have a closed form)
+  virtual bool builtin_kernel() const { return false; }
   // Structured sketch (Sec. 4.1), tree order: for each node g of `groups`
   // with rows [off[g], off[g+1]) of the input side, and compact random
   // matrix Om (rows = input side, k columns, ld ldo):
@@ -334,6 +336,14 @@ struct SketchJob {
   int64_t kcols0, groups1, ldy1, ygs1;
   void* Y1;
   const int64_t* h_off1;
+  // Entry image (tensor-core path, split 3, built-in operators): the A
+  // operand of every (128-row tile rt, 16-column chunk kc) preformed as the
+  // kernel's shared-memory image at img + (rt * img_nch + kc) * 24576 bytes
+  // (launch_entry_image); null: entries are formed on the fly.  Used only
+  // when every K range of the job starts on a chunk boundary and ends on one
+  // or at Ktot.
+  const void* img;
+  int64_t img_nch;
 };
 // Runs all jobs (same dtype) in one launch: one CTA per (job, group, row tile,
 // column tile).  Job and tile lists are uploaded to stream-ordered scratch.
@@ -346,6 +356,19 @@ bool sketch_tc_applies(const std::vector<SketchJob>& jobs);
 int launch_sketch_jobs_tc(const std::vector<SketchJob>& jobs, MemTracker* mt, cudaStream_t s);
 // BF_ETIMEOUT if a tensor-core kernel's bounded wait gave up since the last reset
 int tc_status(bool reset);
+// Entry images (see SketchJob::img): bytes for an M x K orientation, and the
+// launch that fills one for kernel job j (j.op, j.M, j.Ktot, points; X, Y
+// and groups ignored).  img: device, 16-byte aligned, entry_image_bytes.
+size_t entry_image_bytes(int64_t M, int64_t K);
+int64_t entry_image_chunks(int64_t K);
+int launch_entry_image(const SketchJob& j, void* img, cudaStream_t s);
+// whether job j may read an image: split 3, one segment, and every K range
+// (groups and their split-K parts) on chunk boundaries
+bool entry_image_fits(const SketchJob& j);
+// 1: factorizations of built-in operators in mixed precision form entry
+// images when they fit in device memory (default); 0: never
+int set_entry_images(int on);
+int entry_images_enabled();
 // counts one kernel launch of this library (bf_launch_count)
 void note_launch();
 unsigned long long launches_so_far();

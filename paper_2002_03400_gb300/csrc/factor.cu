@@ -63,6 +63,9 @@ struct OpState {
   int64_t goff = 0, yoff = 0, poff = 0, soff = 0, xoff = 0;   // element offsets into arenas
   std::vector<int64_t> prev, cur;                              // peel block offsets
   int in_base = -1;
+  // entry images of a built-in operator for this factorization (op N:
+  // m x n, op C: n x m), or null
+  DevBuf imgN, imgC;
 };
 
 struct Batch {
@@ -167,11 +170,47 @@ int sketch_all(Batch& B, const std::vector<SketchReq>& reqs) {
       // selectable through bf_set_sketch_engine
       j.split = 3;
       j.h_off = (opN ? P->offS[q.level] : P->offT[q.level]).data();
+      const DevBuf& img = opN ? q.o->imgN : q.o->imgC;
+      if ((q.op == BF_OP_N || q.op == BF_OP_C) && img.p && entry_image_fits(j)) {
+        j.img = img.p;
+        j.img_nch = entry_image_chunks(j.Ktot);
+      }
       jobs.push_back(j);
     } else
       BF_TRY(sketch_one(B, q));
   }
   return launch_sketch_jobs(jobs, B.dt, &B.mem, B.s);
+}
+
+// Entry images (mixed precision, built-in operators): every sketch of the
+// factorization reads its tensor-core A operand preformed instead of forming
+// m x n kernel entries per sketch.  Both orientations are formed once, here;
+// operators are served in batch order while the images fit in half of the
+// free device memory (and under the batch's memory cap); the rest form
+// entries on the fly.
+int make_images(Batch& B) {
+  if (B.dt != BF_C64 || !entry_images_enabled()) return BF_OK;
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return BF_OK;
+  size_t budget = free_b / 2;
+  for (auto& o : B.ops) {
+    Plan* P = o.P;
+    if (o.A->plan != P || !o.A->builtin_kernel()) continue;
+    const size_t bN = entry_image_bytes(P->m, P->n), bC = entry_image_bytes(P->n, P->m);
+    if (bN + bC > budget) continue;
+    if (B.mem.cap && B.mem.used + bN + bC > B.mem.cap) continue;
+    if (o.imgN.alloc(&B.mem, bN, B.s) != BF_OK || o.imgC.alloc(&B.mem, bC, B.s) != BF_OK) {
+      o.imgN.release(B.s);
+      o.imgC.release(B.s);
+      continue;
+    }
+    budget -= bN + bC;
+    for (int op : {BF_OP_N, BF_OP_C}) {
+      const SketchJob j = kernel_job(P, op, GemmGroups{1, nullptr, 1}, nullptr, 0, nullptr, 0);
+      BF_TRY(launch_entry_image(j, op == BF_OP_N ? o.imgN.p : o.imgC.p, B.s));
+    }
+  }
+  return BF_OK;
 }
 
 // Lays out a stage: rows[b] x cap[b] blocks, allocates complex128 storage.
@@ -716,7 +755,8 @@ int factor_batch(int count, Plan* const* P, Operator* const* A, cudaStream_t s, 
     maxlm = std::max(maxlm, o.lm);
     maxr = std::max(maxr, o.L - o.lm);
   }
-  int rc = leaf_phase(B, true);
+  int rc = make_images(B);
+  if (!rc) rc = leaf_phase(B, true);
   if (!rc) rc = leaf_phase(B, false);
   for (int t = 1; !rc && t <= maxlm; ++t) rc = w_phase(B, t);
   for (int t = 1; !rc && t <= maxr; ++t) rc = r_phase(B, t);
@@ -724,7 +764,11 @@ int factor_batch(int count, Plan* const* P, Operator* const* A, cudaStream_t s, 
     const cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) rc = fail(BF_ECUDA, cudaGetErrorString(e));
   }
-  for (auto& o : B.ops) o.Y.release(s);
+  for (auto& o : B.ops) {
+    o.Y.release(s);
+    o.imgN.release(s);
+    o.imgC.release(s);
+  }
   if (rc) {
     for (auto& o : B.ops) destroy(o.F);
     return rc;

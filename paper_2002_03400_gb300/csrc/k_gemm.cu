@@ -155,6 +155,14 @@ sketch_job_kernel(const SketchJob* __restrict__ jobs, const SketchTile* __restri
 // 0: tensor cores where they apply (split depth from each job), 1: SIMT only,
 // 2 / 3: tensor cores with the split depth forced to 2 / 3
 static int g_sketch_engine = 0;
+static int g_entry_images = 1;
+
+int set_entry_images(int on) {
+  if (on != 0 && on != 1) return fail(BF_EINVAL, "entry images: 0 (off) or 1 (on)");
+  g_entry_images = on;
+  return BF_OK;
+}
+int entry_images_enabled() { return g_entry_images; }
 
 int set_sketch_engine(int e) {
   if (e < 0 || e > 3) return fail(BF_EINVAL, "sketch engine must be 0 (auto), 1 (SIMT), 2 or 3 (tensor split)");
@@ -167,7 +175,10 @@ int launch_sketch_jobs(const std::vector<SketchJob>& jobs, int dtype, MemTracker
   if (dtype == BF_C64 && g_sketch_engine != 1 && sketch_tc_applies(jobs)) {
     if (g_sketch_engine == 0) return launch_sketch_jobs_tc(jobs, mt, s);
     std::vector<SketchJob> forced(jobs);
-    for (auto& j : forced) j.split = g_sketch_engine;
+    for (auto& j : forced) {
+      if (j.split != g_sketch_engine) j.img = nullptr;   // images hold the bf16 split only
+      j.split = g_sketch_engine;
+    }
     return launch_sketch_jobs_tc(forced, mt, s);
   }
   return launch_sketch_jobs_simt(jobs, dtype, mt, s);

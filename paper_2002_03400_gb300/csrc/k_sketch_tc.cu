@@ -60,8 +60,8 @@ constexpr int XS = 2;              // buffers of staged X rows and points (prefe
 constexpr uint32_t CORE = 128;     // bytes of one 8 x 16 B core matrix
 constexpr int NR_MAX = 96;         // widest tile: 48 complex columns
 
-// entry kinds of a job
-constexpr int EK_DENSE = 0, EK_H2D = 1, EK_H3D = 2, EK_DFT = 3;
+// entry kinds of a job (EK_IMAGE: the A operand arrives preformed, by bulk copy)
+constexpr int EK_DENSE = 0, EK_H2D = 1, EK_H3D = 2, EK_DFT = 3, EK_IMAGE = 4;
 __device__ __forceinline__ int point_arrays(int ek) { return ek == EK_H3D ? 6 : ek == EK_H2D ? 4 : ek == EK_DFT ? 2 : 0; }
 
 struct TcTile {
@@ -272,6 +272,15 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
+// bytes (a multiple of 16, both addresses 16-byte aligned) from global memory
+// into shared memory by the bulk-copy engine, completing on mbarrier bar
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
 }  // namespace
 
 // This thread's row of the tile: its point (float-float, in registers), the
@@ -285,6 +294,32 @@ struct RowCtx {
   int64_t lda;
   int opN;
 };
+
+// entry kind of a job's formula (stored matrix or built-in kernel)
+__device__ __forceinline__ int formula_kind(const SketchJob& J) {
+  return J.kind == 0 ? EK_DENSE
+         : J.ktype == BF_KERNEL_HELMHOLTZ_2D ? EK_H2D
+         : J.ktype == BF_KERNEL_HELMHOLTZ_3D ? EK_H3D
+                                             : EK_DFT;
+}
+
+__device__ __forceinline__ void row_ctx(const SketchJob& J, int ek, int64_t gi, bool rvalid, RowCtx& R) {
+  const int opN = J.op == BF_OP_N;
+  const int npt = point_arrays(ek);
+  const float* rowp = opN ? J.tgtF : J.srcF;
+  const int64_t rown = opN ? J.m : J.n;
+#pragma unroll
+  for (int d = 0; d < 6; ++d) R.rp[d] = (d < npt && rvalid) ? rowp[d * rown + gi] : 0.f;
+  R.kh = J.kh;
+  R.kl = J.kl;
+  R.opN = opN;
+  R.A = (const float2*)J.A;
+  R.lda = J.lda;
+  // imaginary sign: exp(-i k r) in 2D, then conjugation for the adjoint
+  const float base = ek == EK_H2D ? -1.f : 1.f;
+  R.isg = opN ? base : -base;
+  R.neg = R.isg < 0.f ? 0x80000000u : 0u;
+}
 
 // Four entries of row gi at columns gk0 .. gk0+3 (kernel entries use the
 // chunk's column points staged at pts: array d at pts + ps d bytes).
@@ -378,6 +413,7 @@ sketch_tc_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__ 
   __shared__ SketchJob J;
   __shared__ TcTile T;
   __shared__ __align__(8) uint64_t mbar[S];   // MMA completion of chunks c with c % S = s
+  __shared__ __align__(8) uint64_t lbar[S];   // image loads of chunks c with c % S = s
   __shared__ uint32_t tmem_slot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
@@ -385,6 +421,8 @@ sketch_tc_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__ 
     J = jobs[T.job];
     for (int s = 0; s < S; ++s)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[s])), "r"(1) : "memory");
+    for (int s = 0; s < S; ++s)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&lbar[s])), "r"(1) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -422,10 +460,7 @@ sketch_tc_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__ 
 
   // entry kind and this thread's row context
   const int opN = J.op == BF_OP_N;
-  const int ek = J.kind == 0 ? EK_DENSE
-                 : J.ktype == BF_KERNEL_HELMHOLTZ_2D ? EK_H2D
-                 : J.ktype == BF_KERNEL_HELMHOLTZ_3D ? EK_H3D
-                                                     : EK_DFT;
+  const int ek = J.img ? EK_IMAGE : formula_kind(J);
   const int npt = point_arrays(ek);
   // producer mapping: warp w forms rows 16w .. 16w+15; each 8-lane group
   // fills one core matrix (8 rows x 4 columns) per store; a thread's groups
@@ -435,21 +470,7 @@ sketch_tc_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__ 
   const bool rvalid = producer && gi < M;
   const uint32_t a_st = (uint32_t)(prow >> 3) * KG * CORE + (uint32_t)(prow & 7) * 16;
   RowCtx R;
-  {
-    const float* rowp = opN ? J.tgtF : J.srcF;
-    const int64_t rown = opN ? J.m : J.n;
-#pragma unroll
-    for (int d = 0; d < 6; ++d) R.rp[d] = (d < npt && rvalid) ? rowp[d * rown + gi] : 0.f;
-    R.kh = J.kh;
-    R.kl = J.kl;
-    R.opN = opN;
-    R.A = (const float2*)J.A;
-    R.lda = J.lda;
-    // imaginary sign: exp(-i k r) in 2D, then conjugation for the adjoint
-    const float base = ek == EK_H2D ? -1.f : 1.f;
-    R.isg = opN ? base : -base;
-    R.neg = R.isg < 0.f ? 0x80000000u : 0u;
-  }
+  row_ctx(J, ek, gi, rvalid, R);
   const float* colp = opN ? J.srcF : J.tgtF;
   const int64_t coln = opN ? J.n : J.m;
 
@@ -504,11 +525,22 @@ sketch_tc_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__ 
   };
 
   const uint32_t mb0 = smem_u32(&mbar[0]);   // mbar[s] at mb0 + 8 s
+  const uint32_t lb0 = smem_u32(&lbar[0]);   // lbar[s] at lb0 + 8 s
   constexpr uint32_t idesc = C::EB == 2 ? idesc_bf16(NR) : idesc_tf32(NR);
   uint32_t mph = 0;    // bit s: parity of the next phase of mbar[s] to wait for
   bool ok = true;
   int drained = 0;     // groups of DR chunks whose main accumulator is in (hi, lo)
   int issued = -1;     // last chunk whose MMAs were issued
+  // image: chunk c of this CTA's K range at imgp + c * A_BUF (K ranges start
+  // on chunk boundaries); loads run one chunk ahead of the MMAs
+  const uint8_t* imgp = ek == EK_IMAGE ? (const uint8_t*)J.img + ((row0 / TM) * J.img_nch + k0 / KCH) * (int64_t)C::A_BUF
+                                       : nullptr;
+  int loaded = -1, lwaited = -1;   // last chunk whose image load was issued / waited for
+  bool load_gave_up = false;
+  if (ek == EK_IMAGE && issuer && nch > 0) {
+    bulk_load(sb + C::A0, imgp, C::A_BUF, lb0);
+    loaded = 0;
+  }
 #pragma unroll
   for (int c = 0; c < XS; ++c) stage(c);
   cp_async_wait<XS - 1>();
@@ -521,7 +553,7 @@ sketch_tc_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__ 
     //    c-S, completed before the previous barrier)
 #pragma unroll
     for (int r = 0; r < C::PT; ++r) {
-      if (!producer) break;
+      if (!producer || ek == EK_IMAGE) break;
       const int kg = kg0 + 2 * r;
       float re[VS], im[VS];
       const int64_t gk0 = kb + VS * kg;
@@ -569,8 +601,8 @@ sketch_tc_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__ 
     cp_async_wait<XS - 2>();
     // 4. the MMAs of chunk c-S+1 have completed (chunk c+1 rewrites its A and B)
     const int cw = c - S + 1;
-    bool gave_up = false;
-    if (cw >= 0 && issuer) {
+    bool gave_up = load_gave_up;
+    if (cw >= 0 && issuer && !load_gave_up) {
       const uint32_t sw = (uint32_t)(cw % S);
       gave_up = !mbar_wait(mb0 + 8u * sw, (mph >> sw) & 1u);
     }
@@ -594,8 +626,20 @@ sketch_tc_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__ 
     }
     // 6. stage chunk c+XS into the X / point buffers chunk c has finished reading
     stage(c + XS);
-    // 7. the issuing thread issues the chunk's MMAs and commits them to mbar[s]
-    if (issuer) {
+    // 7. the issuing thread starts the image load of chunk c+1 (its buffer's
+    //    last MMAs, those of chunk c+1-S, completed before step 4's barrier),
+    //    waits for chunk c's, then issues the chunk's MMAs and commits them
+    //    to mbar[s]
+    if (issuer && ek == EK_IMAGE) {
+      if (c + 1 < nch) {
+        const uint32_t s1 = (uint32_t)((c + 1) % S);
+        bulk_load(sb + C::A0 + s1 * C::A_BUF, imgp + (int64_t)(c + 1) * C::A_BUF, C::A_BUF, lb0 + 8u * s1);
+        loaded = c + 1;
+      }
+      load_gave_up = !mbar_wait(lb0 + 8u * s, (uint32_t)((c / S) & 1));
+      lwaited = c;
+    }
+    if (issuer && !load_gave_up) {
       // descriptors advance by (byte offset >> 4) in their start-address field
       const uint64_t dA = sdesc<KG>(aB), dB = sdesc<KG>(bB);
       constexpr uint64_t pa = C::A_PART >> 4, pb = C::B_PART >> 4;
@@ -620,11 +664,11 @@ sketch_tc_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__ 
                        mb0 + 8u * s)
                    : "memory");
     }
-    issued = c;
+    if (!load_gave_up) issued = c;
   }
   if (ok && nch > 0) {
-    bool gave_up = false;
-    if (issuer) {
+    bool gave_up = load_gave_up;
+    if (issuer && !load_gave_up) {
       const uint32_t sl = (uint32_t)((nch - 1) % S);
       gave_up = !mbar_wait(mb0 + 8u * sl, (mph >> sl) & 1u);
     }
@@ -649,6 +693,8 @@ sketch_tc_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__ 
         const uint32_t sl = (uint32_t)(issued % S);
         mbar_wait(mb0 + 8u * sl, (mph >> sl) & 1u);
       }
+      for (int c = lwaited + 1; c <= loaded; ++c)   // and for the image loads in flight
+        mbar_wait(lb0 + 8u * (uint32_t)(c % S), (uint32_t)((c / S) & 1));
     }
     __syncthreads();
   } else {
@@ -712,6 +758,97 @@ __global__ void tc_reduce_kernel(const TcRegion* __restrict__ regs, int nreg, co
     }
     R.Y[row + (R.ycol0 + col) * R.ldy] = make_float2(rh + rl, ih + il);
   }
+}
+
+// Entry image of one orientation of a built-in operator: block (row tile
+// rt, chunk kc) at img + (rt * nchi + kc) * A_BUF holds exactly what the
+// sketch kernel's producers write into its A operand for that tile and chunk
+// (the same thread mapping, formula and three-way bf16 split), so products
+// read from the image are bit-identical to products formed on the fly.
+// Rows past M and columns past K hold zeros.  Grid: (row tiles, groups of
+// IMG_CPB chunks), 256 threads.
+constexpr int IMG_CPB = 32;
+__global__ void __launch_bounds__(256) entry_image_kernel(const SketchJob J, uint8_t* __restrict__ img,
+                                                          int64_t nchi) {
+  using C = Cfg<16, 3>;
+  constexpr int KCH = C::KCH, KG = C::KG, G = C::G, VS = C::VS;
+  static_assert(NWARP * 32 == 256, "producer mapping of 8 warps");
+  __shared__ __align__(16) float pts[IMG_CPB * 6 * KCH];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ek = formula_kind(J);
+  const int npt = point_arrays(ek);
+  const int opN = J.op == BF_OP_N;
+  const int64_t row0 = (int64_t)blockIdx.x * TM, M = J.M, K = J.Ktot;
+  const int prow = 16 * warp + (lane & 7) + 8 * ((lane >> 4) & 1), kg0 = (lane >> 3) & 1;
+  const int64_t gi = row0 + prow;
+  const bool rvalid = gi < M;
+  RowCtx R;
+  row_ctx(J, ek, gi, rvalid, R);
+  const float* colp = opN ? J.srcF : J.tgtF;
+  const int64_t coln = opN ? J.n : J.m;
+  const int64_t c0 = (int64_t)blockIdx.y * IMG_CPB;
+  const int nc = (int)(nchi - c0 < IMG_CPB ? nchi - c0 : IMG_CPB);
+  for (int idx = tid; idx < nc * npt * KCH; idx += 256) {
+    const int c = idx / (npt * KCH), d = (idx / KCH) % npt, kk = idx % KCH;
+    const int64_t gk = (c0 + c) * KCH + kk;
+    pts[(c * 6 + d) * KCH + kk] = gk < K ? colp[d * coln + gk] : 0.f;
+  }
+  __syncthreads();
+  const uint32_t pb = smem_u32(pts);
+  const uint32_t a_st = (uint32_t)(prow >> 3) * KG * CORE + (uint32_t)(prow & 7) * 16;
+#pragma unroll 1
+  for (int c = 0; c < nc; ++c) {
+    const int64_t kb = (c0 + c) * KCH;
+    uint8_t* blk = img + ((int64_t)blockIdx.x * nchi + c0 + c) * C::A_BUF;
+#pragma unroll
+    for (int r = 0; r < C::PT; ++r) {
+      const int kg = kg0 + 2 * r;
+      float re[VS], im[VS];
+      const int64_t gk0 = kb + VS * kg;
+      form_row<VS>(ek, R, pb + (uint32_t)(c * 6 * KCH * 4) + 4u * VS * (uint32_t)kg, KCH * 4, rvalid ? gi : row0,
+                   gk0, K, re, im);
+      if (kb + KCH > K || !rvalid) {
+#pragma unroll
+        for (int j = 0; j < VS; ++j)
+          if (!rvalid || gk0 + j >= K) re[j] = 0.f, im[j] = 0.f;
+      }
+      uint4 pr[3], pm[3];
+      split_row<3, VS>(re, pr);
+      split_row<3, VS>(im, pm);
+      uint8_t* ar = blk + a_st + (uint32_t)kg * CORE;
+      uint8_t* ai = ar + (uint32_t)G * CORE;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        *(uint4*)(ar + q * C::A_PART) = pr[q];
+        *(uint4*)(ai + q * C::A_PART) = pm[q];
+      }
+    }
+  }
+}
+
+size_t entry_image_bytes(int64_t M, int64_t K) {
+  return (size_t)((M + TM - 1) / TM) * (size_t)entry_image_chunks(K) * Cfg<16, 3>::A_BUF;
+}
+int64_t entry_image_chunks(int64_t K) { return (K + Cfg<16, 3>::KCH - 1) / Cfg<16, 3>::KCH; }
+
+int launch_entry_image(const SketchJob& j, void* img, cudaStream_t s) {
+  if (j.kind != 1 || j.M <= 0 || j.Ktot <= 0 || !img) return fail(BF_EINVAL, "entry image of a non-kernel job");
+  const int64_t nchi = entry_image_chunks(j.Ktot);
+  const dim3 grid((unsigned)((j.M + TM - 1) / TM), (unsigned)((nchi + IMG_CPB - 1) / IMG_CPB));
+  note_launch();
+  entry_image_kernel<<<grid, 256, 0, s>>>(j, (uint8_t*)img, nchi);
+  BF_CUDA_TRY(cudaGetLastError());
+  return BF_OK;
+}
+
+bool entry_image_fits(const SketchJob& j) {
+  constexpr int64_t KCH = Cfg<16, 3>::KCH;
+  if (j.split != 3 || j.nseg == 2 || j.kind != 1) return false;
+  if (j.groups == 1) return true;
+  if (!j.h_off) return false;
+  for (int g = 0; g < j.groups; ++g)
+    if (j.h_off[g] % KCH != 0) return false;
+  return j.h_off[j.groups] % KCH == 0 || j.h_off[j.groups] == j.Ktot;
 }
 
 bool sketch_tc_applies(const std::vector<SketchJob>& jobs) {
