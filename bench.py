@@ -113,10 +113,11 @@ def cpu_oracle_sample(n_sample: int = 2048):
 
 
 def profile_case(args):
-    """Small cases of one kernel family, sized for ncu captures (inputs of a
-    few hundred MB at most): the on-the-fly sketch product (n = 8192, 22
+    """Small cases of one kernel family, sized for ncu captures (a few GB on
+    the device at most): the on-the-fly sketch product (n = 8192, 22
     columns, all rows against all sources), the apply of a factorization
-    (n = 16384, 64 right-hand sides) or one factorization (its QR levels)."""
+    (n = 16384, 64 right-hand sides), one factorization (its QR levels) or
+    factorizations at n = 8192 with entry images."""
     import torch
     from paper_2002_03400_gb300 import api, inputs
     api.set_sketch_engine(args.engine)
@@ -128,6 +129,17 @@ def profile_case(args):
         X = api.colmajor(torch.from_numpy(inputs.random_rhs(n, 22, seed=3)).to(torch.complex64).cuda())
         for _ in range(3):
             op.apply(X)
+    elif args.profile_case == "image":
+        # three mixed factorizations at n = 8192 with entry images (two
+        # 0.8 GB images per factorization): the image kernel and the
+        # image-fed sketch products
+        n = 8192
+        g = inputs.line_pair(n)
+        plan = api.Plan(g.src, g.tgt, kernel="helmholtz2d", wavenumber=g.wavenumber, leaf=LEAF, tol=TOL,
+                        precision="mixed", r0=R0)
+        op = api.Operator.kernel(plan)
+        for _ in range(3):
+            api.Factorization.factor(plan, op)
     elif args.profile_case == "step":
         # the bench step (mixed factorization, apply of 64 right-hand sides,
         # sketch error), once per --steps
@@ -350,7 +362,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-configs", action="store_true")
-    ap.add_argument("--profile-case", choices=["sketch", "apply", "qr", "step"], default=None,
+    ap.add_argument("--profile-case", choices=["sketch", "apply", "qr", "step", "image"], default=None,
                     help="run only a small case of one kernel family (for ncu captures)")
     ap.add_argument("--engine", default="tensor")
     args = ap.parse_args()

@@ -306,15 +306,14 @@ int bf_set_sketch_engine(int engine);
 
 /* Entry images for the whole process (mixed precision, built-in kernel
  * operators): on = 1 (default) -- a factorization first forms every kernel
- * entry once per orientation (A and A^H), already split into the three bf16
- * parts in the tensor-core operand layout (24 bytes per entry and
- * orientation, e.g. 6.4 GB for n = m = 16384), and every structured sketch
- * of Alg. 2 reads that image instead of re-forming the m x n entries;
- * products are bit-identical either way.  Used while both images fit in
- * half of the free device memory and under mem_cap; freed when the
- * factorization returns.  on = 0 -- entries formed on the fly in every
- * sketch.  Errors: BF_EINVAL unless on is 0 or 1.  Not thread-safe against
- * running factorizations. */
+ * entry once per orientation (A and A^H) in complex64, tiled for the
+ * tensor-core sketch kernel (8 bytes per entry and orientation, e.g. 4.3 GB
+ * for n = m = 16384), and every structured sketch of Alg. 2 streams that
+ * image instead of re-forming the m x n entries (the same bf16 parts and
+ * products, summed in another order: results agree to FP32 rounding).  Used while both images fit in half of the free device memory
+ * and in half of what mem_cap leaves; freed when the factorization returns.
+ * on = 0 -- entries formed on the fly in every sketch.  Errors: BF_EINVAL
+ * unless on is 0 or 1.  Not thread-safe against running factorizations. */
 int bf_set_entry_images(int on);
 
 /* ------------------------------------------------------------- common -- */

@@ -336,14 +336,15 @@ struct SketchJob {
   int64_t kcols0, groups1, ldy1, ygs1;
   void* Y1;
   const int64_t* h_off1;
-  // Entry image (tensor-core path, split 3, built-in operators): the A
-  // operand of every (128-row tile rt, 16-column chunk kc) preformed as the
-  // kernel's shared-memory image at img + (rt * img_nch + kc) * 24576 bytes
+  // Entry image (tensor-core path, split 3, built-in operators): the
+  // complex64 entries of every (128-row tile rt, 16-column chunk kc),
+  // preformed, at img + (rt * img_nch + kc) * 16384 bytes
   // (launch_entry_image); null: entries are formed on the fly.  Used only
   // when every K range of the job starts on a chunk boundary and ends on one
   // or at Ktot.
   const void* img;
   int64_t img_nch;
+  void* bimg;   // set by the launch: this job's B operand image (bf16 parts per 16-row chunk)
 };
 // Runs all jobs (same dtype) in one launch: one CTA per (job, group, row tile,
 // column tile).  Job and tile lists are uploaded to stream-ordered scratch.

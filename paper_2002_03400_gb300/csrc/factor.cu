@@ -183,11 +183,12 @@ int sketch_all(Batch& B, const std::vector<SketchReq>& reqs) {
 }
 
 // Entry images (mixed precision, built-in operators): every sketch of the
-// factorization reads its tensor-core A operand preformed instead of forming
+// factorization streams its entries (complex64 tiles) instead of forming
 // m x n kernel entries per sketch.  Both orientations are formed once, here;
 // operators are served in batch order while the images fit in half of the
-// free device memory (and under the batch's memory cap); the rest form
-// entries on the fly.
+// free device memory and, under a memory cap, in half of what the cap
+// leaves (the rest is for the factorization); the others form entries on
+// the fly.
 int make_images(Batch& B) {
   if (B.dt != BF_C64 || !entry_images_enabled()) return BF_OK;
   size_t free_b = 0, total_b = 0;
@@ -198,7 +199,7 @@ int make_images(Batch& B) {
     if (o.A->plan != P || !o.A->builtin_kernel()) continue;
     const size_t bN = entry_image_bytes(P->m, P->n), bC = entry_image_bytes(P->n, P->m);
     if (bN + bC > budget) continue;
-    if (B.mem.cap && B.mem.used + bN + bC > B.mem.cap) continue;
+    if (B.mem.cap && (B.mem.used >= B.mem.cap || bN + bC > (B.mem.cap - B.mem.used) / 2)) continue;
     if (o.imgN.alloc(&B.mem, bN, B.s) != BF_OK || o.imgC.alloc(&B.mem, bC, B.s) != BF_OK) {
       o.imgN.release(B.s);
       o.imgC.release(B.s);

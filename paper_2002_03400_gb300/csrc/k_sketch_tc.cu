@@ -60,8 +60,8 @@ constexpr int XS = 2;              // buffers of staged X rows and points (prefe
 constexpr uint32_t CORE = 128;     // bytes of one 8 x 16 B core matrix
 constexpr int NR_MAX = 96;         // widest tile: 48 complex columns
 
-// entry kinds of a job (EK_IMAGE: the A operand arrives preformed, by bulk copy)
-constexpr int EK_DENSE = 0, EK_H2D = 1, EK_H3D = 2, EK_DFT = 3, EK_IMAGE = 4;
+// entry kinds of a job
+constexpr int EK_DENSE = 0, EK_H2D = 1, EK_H3D = 2, EK_DFT = 3;
 __device__ __forceinline__ int point_arrays(int ek) { return ek == EK_H3D ? 6 : ek == EK_H2D ? 4 : ek == EK_DFT ? 2 : 0; }
 
 struct TcTile {
@@ -208,16 +208,22 @@ __device__ __forceinline__ uint64_t now_ns() {
   return t;
 }
 
+__device__ __forceinline__ bool mbar_try(uint32_t addr, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(done)
+      : "r"(addr), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// waits for the phase of parity `parity` of the mbarrier at addr; the timer
+// is read only once the phase is found incomplete; false after 1 s
 __device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
+  if (mbar_try(addr, parity)) return true;
   const uint64_t t0 = now_ns();
   for (;;) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(done)
-        : "r"(addr), "r"(parity)
-        : "memory");
-    if (done) return true;
+    if (mbar_try(addr, parity)) return true;
     if (now_ns() - t0 > 1000000000ull) return false;
   }
 }
@@ -274,11 +280,15 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 // bytes (a multiple of 16, both addresses 16-byte aligned) from global memory
 // into shared memory by the bulk-copy engine, completing on mbarrier bar
-__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+// (whose expected transaction count must cover them)
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                "l"(src), "r"(bytes), "r"(bar)
                : "memory");
+}
+// arrive on bar, adding `bytes` to its expected transaction count
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
 }  // namespace
@@ -413,7 +423,6 @@ sketch_tc_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__ 
   __shared__ SketchJob J;
   __shared__ TcTile T;
   __shared__ __align__(8) uint64_t mbar[S];   // MMA completion of chunks c with c % S = s
-  __shared__ __align__(8) uint64_t lbar[S];   // image loads of chunks c with c % S = s
   __shared__ uint32_t tmem_slot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
@@ -421,8 +430,6 @@ sketch_tc_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__ 
     J = jobs[T.job];
     for (int s = 0; s < S; ++s)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[s])), "r"(1) : "memory");
-    for (int s = 0; s < S; ++s)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&lbar[s])), "r"(1) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -460,7 +467,7 @@ sketch_tc_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__ 
 
   // entry kind and this thread's row context
   const int opN = J.op == BF_OP_N;
-  const int ek = J.img ? EK_IMAGE : formula_kind(J);
+  const int ek = formula_kind(J);
   const int npt = point_arrays(ek);
   // producer mapping: warp w forms rows 16w .. 16w+15; each 8-lane group
   // fills one core matrix (8 rows x 4 columns) per store; a thread's groups
@@ -525,22 +532,11 @@ sketch_tc_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__ 
   };
 
   const uint32_t mb0 = smem_u32(&mbar[0]);   // mbar[s] at mb0 + 8 s
-  const uint32_t lb0 = smem_u32(&lbar[0]);   // lbar[s] at lb0 + 8 s
   constexpr uint32_t idesc = C::EB == 2 ? idesc_bf16(NR) : idesc_tf32(NR);
   uint32_t mph = 0;    // bit s: parity of the next phase of mbar[s] to wait for
   bool ok = true;
   int drained = 0;     // groups of DR chunks whose main accumulator is in (hi, lo)
   int issued = -1;     // last chunk whose MMAs were issued
-  // image: chunk c of this CTA's K range at imgp + c * A_BUF (K ranges start
-  // on chunk boundaries); loads run one chunk ahead of the MMAs
-  const uint8_t* imgp = ek == EK_IMAGE ? (const uint8_t*)J.img + ((row0 / TM) * J.img_nch + k0 / KCH) * (int64_t)C::A_BUF
-                                       : nullptr;
-  int loaded = -1, lwaited = -1;   // last chunk whose image load was issued / waited for
-  bool load_gave_up = false;
-  if (ek == EK_IMAGE && issuer && nch > 0) {
-    bulk_load(sb + C::A0, imgp, C::A_BUF, lb0);
-    loaded = 0;
-  }
 #pragma unroll
   for (int c = 0; c < XS; ++c) stage(c);
   cp_async_wait<XS - 1>();
@@ -553,7 +549,7 @@ sketch_tc_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__ 
     //    c-S, completed before the previous barrier)
 #pragma unroll
     for (int r = 0; r < C::PT; ++r) {
-      if (!producer || ek == EK_IMAGE) break;
+      if (!producer) break;
       const int kg = kg0 + 2 * r;
       float re[VS], im[VS];
       const int64_t gk0 = kb + VS * kg;
@@ -601,8 +597,8 @@ sketch_tc_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__ 
     cp_async_wait<XS - 2>();
     // 4. the MMAs of chunk c-S+1 have completed (chunk c+1 rewrites its A and B)
     const int cw = c - S + 1;
-    bool gave_up = load_gave_up;
-    if (cw >= 0 && issuer && !load_gave_up) {
+    bool gave_up = false;
+    if (cw >= 0 && issuer) {
       const uint32_t sw = (uint32_t)(cw % S);
       gave_up = !mbar_wait(mb0 + 8u * sw, (mph >> sw) & 1u);
     }
@@ -626,27 +622,14 @@ sketch_tc_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__ 
     }
     // 6. stage chunk c+XS into the X / point buffers chunk c has finished reading
     stage(c + XS);
-    // 7. the issuing thread starts the image load of chunk c+1 (its buffer's
-    //    last MMAs, those of chunk c+1-S, completed before step 4's barrier),
-    //    waits for chunk c's, then issues the chunk's MMAs and commits them
-    //    to mbar[s]
-    if (issuer && ek == EK_IMAGE) {
-      if (c + 1 < nch) {
-        const uint32_t s1 = (uint32_t)((c + 1) % S);
-        bulk_load(sb + C::A0 + s1 * C::A_BUF, imgp + (int64_t)(c + 1) * C::A_BUF, C::A_BUF, lb0 + 8u * s1);
-        loaded = c + 1;
-      }
-      load_gave_up = !mbar_wait(lb0 + 8u * s, (uint32_t)((c / S) & 1));
-      lwaited = c;
-    }
-    if (issuer && !load_gave_up) {
+    // 7. the issuing thread issues the chunk's MMAs and commits them to mbar[s]
+    if (issuer) {
       // descriptors advance by (byte offset >> 4) in their start-address field
       const uint64_t dA = sdesc<KG>(aB), dB = sdesc<KG>(bB);
       constexpr uint64_t pa = C::A_PART >> 4, pb = C::B_PART >> 4;
       const uint32_t tmain = tm + (uint32_t)((c / DR) & 1) * NR, tcorr = tm + 2 * NR;
       const uint32_t carry = (c % DR) != 0 ? 1u : 0u;   // a main accumulator restarts with its group
       const uint32_t cacc = c > 0 ? 1u : 0u;             // the correction runs over all K
-#pragma unroll
       constexpr int EB = C::EB;
 #pragma unroll
       for (int ks = 0; ks < C::KSTEPS; ++ks) {
@@ -664,11 +647,11 @@ sketch_tc_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__ 
                        mb0 + 8u * s)
                    : "memory");
     }
-    if (!load_gave_up) issued = c;
+    issued = c;
   }
   if (ok && nch > 0) {
-    bool gave_up = load_gave_up;
-    if (issuer && !load_gave_up) {
+    bool gave_up = false;
+    if (issuer) {
       const uint32_t sl = (uint32_t)((nch - 1) % S);
       gave_up = !mbar_wait(mb0 + 8u * sl, (mph >> sl) & 1u);
     }
@@ -693,8 +676,6 @@ sketch_tc_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__ 
         const uint32_t sl = (uint32_t)(issued % S);
         mbar_wait(mb0 + 8u * sl, (mph >> sl) & 1u);
       }
-      for (int c = lwaited + 1; c <= loaded; ++c)   // and for the image loads in flight
-        mbar_wait(lb0 + 8u * (uint32_t)(c % S), (uint32_t)((c / S) & 1));
     }
     __syncthreads();
   } else {
@@ -760,26 +741,34 @@ __global__ void tc_reduce_kernel(const TcRegion* __restrict__ regs, int nreg, co
   }
 }
 
-// Entry image of one orientation of a built-in operator: block (row tile
-// rt, chunk kc) at img + (rt * nchi + kc) * A_BUF holds exactly what the
-// sketch kernel's producers write into its A operand for that tile and chunk
-// (the same thread mapping, formula and three-way bf16 split), so products
-// read from the image are bit-identical to products formed on the fly.
-// Rows past M and columns past K hold zeros.  Grid: (row tiles, groups of
-// IMG_CPB chunks), 256 threads.
-constexpr int IMG_CPB = 32;
+// ---------------------------------------------------------------------------
+// Entry images and the image-fed sketch kernel
+// ---------------------------------------------------------------------------
+// An entry image holds one orientation of a built-in operator's m x n
+// entries in complex64, as the tiles the sketch kernel consumes: tile
+// (row tile rt, 16-column chunk kc) at img + (rt * nchi + kc) * IMG_TILE,
+// 128 rows of 128 bytes (16 complex entries, re/im interleaved); the 16-byte
+// segment q (2 entries) of row r sits at position q ^ (r & 7) so that the
+// eight rows a quarter-warp reads land in distinct bank groups.  Entries are
+// those the on-the-fly producers form (same formula, same thread mapping);
+// rows past M and columns past K are zero.
+constexpr int IMG_CPB = 32;                    // chunks per CTA of the image kernel
+constexpr uint32_t IMG_TILE = TM * 16 * 8;     // bytes of one tile
+
+__device__ __forceinline__ uint32_t img_seg(int r, int q) { return (uint32_t)r * 128u + (uint32_t)((q ^ (r & 7)) * 16); }
+
 __global__ void __launch_bounds__(256) entry_image_kernel(const SketchJob J, uint8_t* __restrict__ img,
                                                           int64_t nchi) {
   using C = Cfg<16, 3>;
-  constexpr int KCH = C::KCH, KG = C::KG, G = C::G, VS = C::VS;
-  static_assert(NWARP * 32 == 256, "producer mapping of 8 warps");
+  constexpr int KCH = C::KCH, VS = C::VS;
+  static_assert(NWARP * 32 == 256 && KCH == 16 && VS == 8, "producer mapping of 8 warps, 16-column chunks");
   __shared__ __align__(16) float pts[IMG_CPB * 6 * KCH];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int ek = formula_kind(J);
   const int npt = point_arrays(ek);
   const int opN = J.op == BF_OP_N;
   const int64_t row0 = (int64_t)blockIdx.x * TM, M = J.M, K = J.Ktot;
-  const int prow = 16 * warp + (lane & 7) + 8 * ((lane >> 4) & 1), kg0 = (lane >> 3) & 1;
+  const int prow = 16 * warp + (lane & 7) + 8 * ((lane >> 4) & 1), kg = (lane >> 3) & 1;
   const int64_t gi = row0 + prow;
   const bool rvalid = gi < M;
   RowCtx R;
@@ -795,41 +784,29 @@ __global__ void __launch_bounds__(256) entry_image_kernel(const SketchJob J, uin
   }
   __syncthreads();
   const uint32_t pb = smem_u32(pts);
-  const uint32_t a_st = (uint32_t)(prow >> 3) * KG * CORE + (uint32_t)(prow & 7) * 16;
 #pragma unroll 1
   for (int c = 0; c < nc; ++c) {
     const int64_t kb = (c0 + c) * KCH;
-    uint8_t* blk = img + ((int64_t)blockIdx.x * nchi + c0 + c) * C::A_BUF;
+    float re[VS], im[VS];
+    const int64_t gk0 = kb + VS * kg;
+    form_row<VS>(ek, R, pb + (uint32_t)(c * 6 * KCH * 4) + 4u * VS * (uint32_t)kg, KCH * 4, rvalid ? gi : row0, gk0,
+                 K, re, im);
+    if (kb + KCH > K || !rvalid) {
 #pragma unroll
-    for (int r = 0; r < C::PT; ++r) {
-      const int kg = kg0 + 2 * r;
-      float re[VS], im[VS];
-      const int64_t gk0 = kb + VS * kg;
-      form_row<VS>(ek, R, pb + (uint32_t)(c * 6 * KCH * 4) + 4u * VS * (uint32_t)kg, KCH * 4, rvalid ? gi : row0,
-                   gk0, K, re, im);
-      if (kb + KCH > K || !rvalid) {
-#pragma unroll
-        for (int j = 0; j < VS; ++j)
-          if (!rvalid || gk0 + j >= K) re[j] = 0.f, im[j] = 0.f;
-      }
-      uint4 pr[3], pm[3];
-      split_row<3, VS>(re, pr);
-      split_row<3, VS>(im, pm);
-      uint8_t* ar = blk + a_st + (uint32_t)kg * CORE;
-      uint8_t* ai = ar + (uint32_t)G * CORE;
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        *(uint4*)(ar + q * C::A_PART) = pr[q];
-        *(uint4*)(ai + q * C::A_PART) = pm[q];
-      }
+      for (int j = 0; j < VS; ++j)
+        if (!rvalid || gk0 + j >= K) re[j] = 0.f, im[j] = 0.f;
     }
+    uint8_t* tile = img + ((int64_t)blockIdx.x * nchi + c0 + c) * IMG_TILE;
+#pragma unroll
+    for (int t = 0; t < VS / 2; ++t)
+      *(float4*)(tile + img_seg(prow, 4 * kg + t)) = make_float4(re[2 * t], im[2 * t], re[2 * t + 1], im[2 * t + 1]);
   }
 }
 
 size_t entry_image_bytes(int64_t M, int64_t K) {
-  return (size_t)((M + TM - 1) / TM) * (size_t)entry_image_chunks(K) * Cfg<16, 3>::A_BUF;
+  return (size_t)((M + TM - 1) / TM) * (size_t)entry_image_chunks(K) * IMG_TILE;
 }
-int64_t entry_image_chunks(int64_t K) { return (K + Cfg<16, 3>::KCH - 1) / Cfg<16, 3>::KCH; }
+int64_t entry_image_chunks(int64_t K) { return (K + 15) / 16; }
 
 int launch_entry_image(const SketchJob& j, void* img, cudaStream_t s) {
   if (j.kind != 1 || j.M <= 0 || j.Ktot <= 0 || !img) return fail(BF_EINVAL, "entry image of a non-kernel job");
@@ -842,13 +819,426 @@ int launch_entry_image(const SketchJob& j, void* img, cudaStream_t s) {
 }
 
 bool entry_image_fits(const SketchJob& j) {
-  constexpr int64_t KCH = Cfg<16, 3>::KCH;
+  constexpr int64_t KCH = 16;
   if (j.split != 3 || j.nseg == 2 || j.kind != 1) return false;
   if (j.groups == 1) return true;
   if (!j.h_off) return false;
   for (int g = 0; g < j.groups; ++g)
     if (j.h_off[g] % KCH != 0) return false;
   return j.h_off[j.groups] % KCH == 0 || j.h_off[j.groups] == j.Ktot;
+}
+
+// B operand images of image jobs: for every 16-row chunk kc of X (rows
+// 16 kc ..), the bf16 parts of [[Xr, Xi], [-Xi, Xr]] exactly as
+// sketch_tc_kernel's producers build them (zero past Ktot and kcols), at
+// bimg + kc * B_BUF.  Grid: (chunks, jobs).
+template <int NR>
+__global__ void __launch_bounds__(256) bimage_kernel(const SketchJob* __restrict__ jobs) {
+  using C = Cfg<NR, 3>;
+  constexpr int KG = C::KG, G = C::G, VS = C::VS, KP = NR / 2, KCH = C::KCH;
+  const SketchJob& J = jobs[blockIdx.y];
+  const int64_t kc = blockIdx.x, K = J.Ktot, kcols = J.kcols;
+  if (kc * KCH >= K) return;
+  const float* __restrict__ Xf = (const float*)J.X;
+  uint8_t* out = (uint8_t*)J.bimg + kc * C::B_BUF;
+  for (int it = threadIdx.x; it < NR * KG; it += blockDim.x) {
+    const int nr = ((it / (8 * KG)) << 3) | (it & 7), kgb = (it >> 3) & (KG - 1);
+    const int part = kgb >= G ? 1 : 0;
+    const int kk0 = (kgb & (G - 1)) * VS;
+    const int col = nr % KP, blk = nr / KP;
+    const int im = (part ^ blk) & 1;
+    const uint32_t neg = (part == 1 && blk == 0) ? 0x80000000u : 0u;
+    float v[VS];
+#pragma unroll
+    for (int t = 0; t < VS; ++t) {
+      const int64_t gk = kc * KCH + kk0 + t;
+      const float x = (gk < K && col < kcols) ? Xf[2 * (gk + (int64_t)col * J.ldx) + im] : 0.f;
+      v[t] = __uint_as_float(__float_as_uint(x) ^ neg);
+    }
+    uint4 pv[3];
+    split_row<3, VS>(v, pv);
+    const uint32_t o = (uint32_t)(nr >> 3) * KG * CORE + (uint32_t)kgb * CORE + (uint32_t)(nr & 7) * 16;
+#pragma unroll
+    for (int p = 0; p < 3; ++p) *(uint4*)(out + p * C::B_PART + o) = pv[p];
+  }
+}
+
+namespace {
+// Image-fed tile shape: one CTA per SM, 576 threads -- two groups of 8
+// producer warps (even and odd chunks: bf16 split of the A tile; group 0
+// also drains the accumulators and writes the epilogue), an MMA warp and a
+// loader warp, synchronised by mbarriers only.  SF slots hold an image tile
+// and the chunk's B operand (bf16 parts, formed once per launch), S slots
+// the bf16 A parts.
+template <int NR>
+struct ICfg {
+  using C = Cfg<NR, 3>;
+  static constexpr int KP = NR / 2;
+  static constexpr uint32_t F_SLOT = (IMG_TILE + C::B_BUF + 127) / 128 * 128;   // image tile + B operand
+  static constexpr uint32_t O_SLOT = C::A_BUF;                                    // bf16 A parts
+  static constexpr int SF = 4;
+  static constexpr uint32_t LIMIT = 220 * 1024;
+  static constexpr uint32_t total(int s) { return SF * F_SLOT + s * O_SLOT; }
+  static constexpr int S = total(4) <= LIMIT ? 4 : total(3) <= LIMIT ? 3 : 2;
+  static constexpr uint32_t F0 = 0, O0 = SF * F_SLOT, TOTAL = O0 + S * O_SLOT;
+  static_assert(TOTAL <= LIMIT && C::PT == 1 && C::VS == 8, "image tile: shared memory, one 8-column group per thread");
+  static_assert(C::DR == 4, "group 0 drains at the third chunk of the next group");
+};
+constexpr int IPG = 2;                                // producer groups
+constexpr int ITHREADS = 32 * (IPG * NWARP + 2);
+constexpr int IMMA_WARP = IPG * NWARP, ILOAD_WARP = IPG * NWARP + 1;
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(r[0]),
+               "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+               : "memory");
+}
+// Tensor memory of the image kernel: two accumulator sets (alternate
+// groups of DR chunks) of three NR-column blocks each -- main (a0 b0),
+// c1 (a0 b1 + a1 b0), c2 (a0 b2 + a1 b1 + a2 b0), adjacent so that one MMA
+// with the B parts stacked along N fills them -- then hi, lo.
+__host__ __device__ constexpr int img_cols(int nr) { return 8 * nr <= 128 ? 128 : 8 * nr <= 256 ? 256 : 512; }
+// hi, lo += the set at column `set` (TwoSum of main into hi; the error and
+// the correction sums into lo), in 8-column slices
+template <int NR>
+__device__ __forceinline__ void drain_set(uint32_t tq, int sub, uint32_t set) {
+#pragma unroll 1
+  for (int s = sub; s < NR / 8; s += NWARP / 4) {
+    uint32_t d[8], c1[8], c2[8], h[8], l[8];
+    tmem_ld8(tq + set + s * 8, d);
+    tmem_ld8(tq + set + NR + s * 8, c1);
+    tmem_ld8(tq + set + 2 * NR + s * 8, c2);
+    tmem_ld8(tq + 6 * NR + s * 8, h);
+    tmem_ld8(tq + 7 * NR + s * 8, l);
+    tmem_wait_ld();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const FF t = two_sum(__uint_as_float(h[i]), __uint_as_float(d[i]));
+      h[i] = __float_as_uint(t.h);
+      l[i] = __float_as_uint(__uint_as_float(l[i]) + (t.l + (__uint_as_float(c1[i]) + __uint_as_float(c2[i]))));
+    }
+    tmem_st8(tq + 6 * NR + s * 8, h);
+    tmem_st8(tq + 7 * NR + s * 8, l);
+  }
+  tmem_wait_st();
+}
+}  // namespace
+
+// Sketch product of image jobs: the same tiles, chunks, bf16 parts and six
+// products as sketch_tc_kernel, with the products of one A part issued as
+// one MMA over the stacked B parts (3 MMAs per 16 K instead of 6: an MMA
+// costs about the same at N = 48 as at N = 144) and the correction sums
+// drained with each group -- equal to sketch_tc_kernel's results up to FP32
+// rounding order.  Per chunk c of a CTA's K range,
+//   loader  -- waits for F slot c % SF to be free (its tile read by the
+//              producers, its B operand by the MMAs of chunk c - SF) and
+//              bulk-copies the image tile and the chunk's B operand into it,
+//              completing on fullF;
+//   producer group c % 2 -- waits for fullF and for A slot c % S (its MMAs
+//              of chunk c - S done), reads the tile rows, releases the tile,
+//              splits the entries into bf16 parts, writes A, fences it to
+//              the async proxy and arrives on fullO; group 0, before the third chunk of group g + 1 (4
+//              chunks a group), drains group g's accumulator set into
+//              (hi, lo);
+//   MMA warp -- waits for fullO and fullF (and, at a group's first chunk,
+//              for the drain of the group two back), issues the chunk's MMAs
+//              and commits them to emptyO and emptyF (and to accF at a
+//              group's end).
+// Every wait is bounded (1 s); a role that gives up raises the abort flag
+// and the device status, and the others stop at their next wait.
+template <int NR>
+__global__ void __launch_bounds__(ITHREADS, 1)
+sketch_img_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__ tiles, float4* __restrict__ ws) {
+  using I = ICfg<NR>;
+  using C = Cfg<NR, 3>;
+  constexpr int S = I::S, SF = I::SF, KCH = C::KCH, KG = C::KG, G = C::G, DR = C::DR, KP = I::KP, VS = C::VS;
+  constexpr int COLS = img_cols(NR);
+  static_assert(8 * NR <= 512 && 3 * NR <= 256, "two accumulator sets and (hi, lo) in tensor memory; N <= 256");
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ SketchJob J;
+  __shared__ TcTile T;
+  __shared__ __align__(8) uint64_t bars[2 * SF + 2 * S + 4];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t b0 = smem_u32(&bars[0]);
+  // fullF[i] = b0 + 8 i, emptyF[i] = +8 (SF + i), fullO[i] = +8 (2 SF + i),
+  // emptyO[i] = +8 (2 SF + S + i), accF[b] = +8 (2 SF + 2 S + b), accE[b] = +8 (2 SF + 2 S + 2 + b)
+  const uint32_t fullF = b0, emptyF = b0 + 8u * SF, fullO = b0 + 16u * SF, emptyO = fullO + 8u * S,
+                 accF = emptyO + 8u * S, accE = accF + 16u;
+  if (tid == 0) {
+    T = tiles[blockIdx.x];
+    J = jobs[T.job];
+    for (int i = 0; i < SF; ++i) {
+      mbar_init(fullF + 8u * i, 1);        // the loader's expect_tx arrive
+      mbar_init(emptyF + 8u * i, NWARP + 1);   // the producer group's warps + the MMA commit (B read)
+    }
+    for (int i = 0; i < S; ++i) {
+      mbar_init(fullO + 8u * i, NWARP);
+      mbar_init(emptyO + 8u * i, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accF + 8u * b, 1);
+      mbar_init(accE + 8u * b, NWARP);
+    }
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tm = tmem_slot;
+  const int pgrp = warp / NWARP, pw = warp % NWARP;   // producer group and warp within it
+  const int quad = pw & 3, sub = (pw >> 2) & 1;
+  const uint32_t tq = tm + ((uint32_t)(quad * 32) << 16);
+  if (warp < NWARP) {   // group 0 zeroes (hi, lo)
+    uint32_t z[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) z[i] = 0u;
+#pragma unroll 1
+    for (int s = sub; s < 2 * NR / 8; s += 2) tmem_st8(tq + 6 * NR + s * 8, z);
+    tmem_wait_st();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+
+  const int64_t row0 = T.row0, M = J.M, kcols = J.kcols, ygs = J.ygs;
+  const int64_t k0 = T.k0 >= 0 ? T.k0 : (J.d_off ? J.d_off[T.group] : 0);
+  const int64_t k1 = T.k0 >= 0 ? T.k1 : (J.d_off ? J.d_off[T.group + 1] : J.Ktot);
+  const int nch = (int)((k1 - k0 + KCH - 1) / KCH);
+  const int ngroups = (nch + DR - 1) / DR;
+  const uint32_t sb = smem_u32(smem);
+  bool ok = true;
+
+  if (warp == ILOAD_WARP) {
+    // ---------------------------------------------------------------- loader
+    const uint8_t* imgp = (const uint8_t*)J.img + ((row0 / TM) * J.img_nch + k0 / KCH) * (int64_t)IMG_TILE;
+    const uint8_t* bimp = (const uint8_t*)J.bimg + (k0 / KCH) * (int64_t)C::B_BUF;
+    int c = 0;
+    for (; c < nch; ++c) {
+      const int sf = c % SF;
+      int free_ok = 1;
+      if (c >= SF && lane == 0) free_ok = mbar_wait(emptyF + 8u * sf, (uint32_t)(((c / SF) - 1) & 1)) ? 1 : 0;
+      free_ok = __shfl_sync(0xffffffffu, free_ok, 0);
+      if (!free_ok || *(volatile int*)&abort_flag) {
+        ok = free_ok != 0;
+        break;
+      }
+      if (lane == 0) {
+        const uint32_t fb = sb + I::F0 + (uint32_t)sf * I::F_SLOT;
+        mbar_expect_tx(fullF + 8u * sf, IMG_TILE + C::B_BUF);
+        bulk_copy(fb, imgp + (int64_t)c * IMG_TILE, IMG_TILE, fullF + 8u * sf);
+        bulk_copy(fb + IMG_TILE, bimp + (int64_t)c * C::B_BUF, C::B_BUF, fullF + 8u * sf);
+      }
+    }
+    if (!ok && lane == 0) {
+      *(volatile int*)&abort_flag = 1;
+      atomicExch(&g_tc_status, 1);
+    }
+    // the loads still in flight complete before the CTA ends (bounded)
+    if (lane == 0)
+      for (int q = c - SF < 0 ? 0 : c - SF; q < c; ++q) mbar_wait(fullF + 8u * (q % SF), (uint32_t)((q / SF) & 1));
+    __syncwarp();
+  } else if (warp == IMMA_WARP) {
+    // ------------------------------------------------------------- MMA warp
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_bf16(NR), idesc2 = idesc_bf16(2 * NR), idesc3 = idesc_bf16(3 * NR);
+      constexpr uint64_t pa = C::A_PART >> 4;
+      int issued = -1;
+      for (int c = 0; c < nch; ++c) {
+        const int g = c / DR, s = c % S;
+        if (c % DR == 0 && g >= 2 && !mbar_wait(accE + 8u * (g & 1), (uint32_t)(((g - 2) / 2) & 1))) {
+          ok = false;
+          break;
+        }
+        const int sf = c % SF;
+        if (!mbar_wait(fullO + 8u * s, (uint32_t)((c / S) & 1)) ||
+            !mbar_wait(fullF + 8u * sf, (uint32_t)((c / SF) & 1)) || *(volatile int*)&abort_flag) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t aB = sb + I::O0 + (uint32_t)s * I::O_SLOT, bB = sb + I::F0 + (uint32_t)sf * I::F_SLOT + IMG_TILE;
+        const uint64_t dA = sdesc<KG>(aB), dB = sdesc<KG>(bB);
+        // set of this group: [main | c1 | c2]; a0 [b0; b1; b2] -> all three,
+        // a1 [b0; b1] -> c1, c2, a2 b0 -> c2 (the B parts are consecutive
+        // 8-row groups, so stacking them along N is a larger N)
+        const uint32_t tset = tm + (uint32_t)(g & 1) * 3 * NR;
+        const uint32_t carry = (c % DR) != 0 ? 1u : 0u;   // the set restarts with its group
+#pragma unroll
+        for (int ks = 0; ks < C::KSTEPS; ++ks) {
+          const uint64_t o = (uint64_t)(ks * 2 * CORE) >> 4;
+          mma_step<2>(tset, dA + o, dB + o, idesc3, ks > 0 ? 1u : carry);
+          mma_step<2>(tset + NR, dA + pa + o, dB + o, idesc2, 1u);
+          mma_step<2>(tset + 2 * NR, dA + 2 * pa + o, dB + o, idesc, 1u);
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         emptyO + 8u * s)
+                     : "memory");
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         emptyF + 8u * sf)
+                     : "memory");
+        if (c % DR == DR - 1 || c == nch - 1)
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           accF + 8u * (g & 1))
+                       : "memory");
+        issued = c;
+      }
+      if (!ok) {
+        *(volatile int*)&abort_flag = 1;
+        atomicExch(&g_tc_status, 1);
+        if (issued >= 0) mbar_wait(emptyO + 8u * (issued % S), (uint32_t)((issued / S) & 1));
+      }
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ producers
+    const int prow = 16 * pw + (lane & 7) + 8 * ((lane >> 4) & 1), kg = (lane >> 3) & 1;
+    const uint32_t a_st = (uint32_t)(prow >> 3) * KG * CORE + (uint32_t)(prow & 7) * 16;
+    int next_drain = 0;
+    auto drain_group = [&](int g, bool last) -> bool {
+      if (!mbar_wait(accF + 8u * (g & 1), (uint32_t)((g / 2) & 1))) return false;
+      tc_fence_after();
+      drain_set<NR>(tq, sub, (uint32_t)(g & 1) * 3 * NR);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(accE + 8u * (g & 1));
+      return true;
+    };
+    for (int c = pgrp; c < nch && ok; c += IPG) {
+      if (pgrp == 0 && c % DR == 2 && c > DR) {   // third chunk of group g + 1: drain group g
+        ok = drain_group(next_drain, false);
+        ++next_drain;
+        if (!ok) break;
+      }
+      const int sf = c % SF, s = c % S;
+      if (!mbar_wait(fullF + 8u * sf, (uint32_t)((c / SF) & 1)) ||
+          (c >= S && !mbar_wait(emptyO + 8u * s, (uint32_t)(((c / S) - 1) & 1))) || *(volatile int*)&abort_flag) {
+        ok = false;
+        break;
+      }
+      const uint32_t fb = sb + I::F0 + (uint32_t)sf * I::F_SLOT;
+      float re[VS], im[VS];
+#pragma unroll
+      for (int t = 0; t < VS / 2; ++t) {
+        const float4 u = ld_shared_v4(fb + img_seg(prow, 4 * kg + t));
+        re[2 * t] = u.x, im[2 * t] = u.y, re[2 * t + 1] = u.z, im[2 * t + 1] = u.w;
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(emptyF + 8u * sf);   // this warp is done with the image tile
+      const uint32_t aB = sb + I::O0 + (uint32_t)s * I::O_SLOT;
+      uint4 pr[3], pm[3];
+      split_row<3, VS>(re, pr);
+      split_row<3, VS>(im, pm);
+      const uint32_t ar = aB + a_st + (uint32_t)kg * CORE, ai = ar + (uint32_t)G * CORE;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        st_shared_v4(ar + q * C::A_PART, pr[q]);
+        st_shared_v4(ai + q * C::A_PART, pm[q]);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(fullO + 8u * s);
+    }
+    if (pgrp == 0) {
+      for (; ok && next_drain < ngroups; ++next_drain) ok = drain_group(next_drain, next_drain == ngroups - 1);
+      if (ok && nch > 0) {
+        // epilogue: (hi, lo) pairs of this warp's lanes to Y or to the split workspace
+        const int64_t row = row0 + quad * 32 + lane;
+#pragma unroll 1
+        for (int s = sub; s < (KP + 7) / 8; s += NWARP / 4) {
+          uint32_t hr[8], lr[8], hm[8], lm[8];
+          const int c0 = s * 8;
+          tmem_ld8(tq + 6 * NR + c0, hr);
+          tmem_ld8(tq + 7 * NR + c0, lr);
+          tmem_ld8(tq + 6 * NR + KP + c0, hm);
+          tmem_ld8(tq + 7 * NR + KP + c0, lm);
+          tmem_wait_ld();
+          if (row < M) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const int col = c0 + i;
+              if (col >= kcols || col >= KP) continue;
+              if (T.ws < 0) {
+                float2* __restrict__ Y = (float2*)J.Y;
+                Y[row + (T.group * ygs + col) * J.ldy] = make_float2(
+                    __uint_as_float(hr[i]) + __uint_as_float(lr[i]), __uint_as_float(hm[i]) + __uint_as_float(lm[i]));
+              } else {
+                ws[T.ws + col * M + row] = make_float4(__uint_as_float(hr[i]), __uint_as_float(lr[i]),
+                                                       __uint_as_float(hm[i]), __uint_as_float(lm[i]));
+              }
+            }
+          }
+        }
+      }
+    }
+    if (!ok && lane == 0) {
+      *(volatile int*)&abort_flag = 1;
+      atomicExch(&g_tc_status, 1);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(COLS) : "memory");
+  }
+}
+
+template <int NR>
+static int launch_img_nr(const SketchJob* dj, const TcTile* dt, unsigned ntiles, float4* ws, cudaStream_t s) {
+  constexpr size_t smem = ICfg<NR>::TOTAL;
+  BF_CUDA_TRY(cudaFuncSetAttribute(sketch_img_kernel<NR>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                   (int)cudaSharedmemCarveoutMaxShared));
+  BF_CUDA_TRY(cudaFuncSetAttribute(sketch_img_kernel<NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  note_launch();
+  sketch_img_kernel<NR><<<ntiles, ITHREADS, smem, s>>>(dj, dt, ws);
+  BF_CUDA_TRY(cudaGetLastError());
+  return BF_OK;
+}
+
+static int launch_bimages(int nr, const std::vector<SketchJob>& jobs, const SketchJob* dj, const DevBuf&,
+                          cudaStream_t s) {
+  int64_t mc = 0;
+  for (const auto& j : jobs) mc = std::max<int64_t>(mc, entry_image_chunks(j.Ktot));
+  if (mc == 0) return BF_OK;
+  const dim3 grid((unsigned)mc, (unsigned)jobs.size());
+  note_launch();
+  switch (nr) {
+    case 16: bimage_kernel<16><<<grid, 256, 0, s>>>(dj); break;
+    case 32: bimage_kernel<32><<<grid, 256, 0, s>>>(dj); break;
+    case 48: bimage_kernel<48><<<grid, 256, 0, s>>>(dj); break;
+    default: bimage_kernel<64><<<grid, 256, 0, s>>>(dj); break;
+  }
+  BF_CUDA_TRY(cudaGetLastError());
+  return BF_OK;
+}
+
+static int launch_img(int nr, const SketchJob* dj, const TcTile* dt, unsigned nt, float4* ws, cudaStream_t s) {
+  switch (nr) {
+    case 16: return launch_img_nr<16>(dj, dt, nt, ws, s);
+    case 32: return launch_img_nr<32>(dj, dt, nt, ws, s);
+    case 48: return launch_img_nr<48>(dj, dt, nt, ws, s);
+    default: return launch_img_nr<64>(dj, dt, nt, ws, s);
+  }
 }
 
 bool sketch_tc_applies(const std::vector<SketchJob>& jobs) {
@@ -930,9 +1320,27 @@ int launch_sketch_jobs_tc(const std::vector<SketchJob>& jobs_in, MemTracker* mt,
       BF_TRY(launch_sketch_jobs_tc(lo, mt, s));
       return launch_sketch_jobs_tc(hi, mt, s);
     }
+  // jobs that read entry images and jobs that form entries: one launch each
+  {
+    bool any = false, all = true;
+    for (const auto& j : jobs) any = any || j.img != nullptr, all = all && j.img != nullptr;
+    if (any && !all) {
+      std::vector<SketchJob> a, b;
+      for (const auto& q : jobs) (q.img ? a : b).push_back(q);
+      BF_TRY(launch_sketch_jobs_tc(b, mt, s));
+      return launch_sketch_jobs_tc(a, mt, s);
+    }
+  }
+  bool from_images = !jobs.empty() && jobs[0].img != nullptr;
   // real columns N = 2 x padded sketch width, one of the compiled tile widths
   const int kp = (int)((maxk + 7) / 8 * 8);
   const int nr = kp <= 8 ? 16 : kp <= 16 ? 32 : kp <= 24 ? 48 : kp <= 32 ? 64 : 96;
+  // the image kernel's tensor memory holds tiles up to 64 real columns;
+  // wider image jobs form their entries
+  if (from_images && nr > 64) {
+    for (auto& j : jobs) j.img = nullptr;
+    from_images = false;
+  }
   const int kch = split == 3 ? Cfg<16, 3>::KCH : Cfg<16, 2>::KCH;   // complex K per chunk
   std::vector<TcTile> tiles;
   std::vector<TcRegion> regs;
@@ -1014,7 +1422,18 @@ int launch_sketch_jobs_tc(const std::vector<SketchJob>& jobs_in, MemTracker* mt,
   if (tiles.empty()) return BF_OK;
   const size_t jb = jobs.size() * sizeof(SketchJob), tb = tiles.size() * sizeof(TcTile),
                rb = regs.size() * sizeof(TcRegion);
-  DevBuf d, w;
+  DevBuf d, w, bi;
+  if (from_images) {   // B operand images, one per job (bf16 parts of every 16-row chunk)
+    const size_t bbuf = (size_t)3 * nr * 32 * 2;
+    size_t tot = 0;
+    for (const auto& j : jobs) tot += (size_t)entry_image_chunks(j.Ktot) * bbuf;
+    BF_TRY(bi.alloc(mt, tot, s));
+    size_t off = 0;
+    for (auto& j : jobs) {
+      j.bimg = (char*)bi.p + off;
+      off += (size_t)entry_image_chunks(j.Ktot) * bbuf;
+    }
+  }
   BF_TRY(d.alloc(mt, jb + tb + rb + 16, s));
   if (wsz) BF_TRY(w.alloc(mt, wsz * sizeof(float4), s));
   int rc = BF_OK;
@@ -1026,7 +1445,11 @@ int launch_sketch_jobs_tc(const std::vector<SketchJob>& jobs_in, MemTracker* mt,
   const SketchJob* dj = (const SketchJob*)p;
   const TcTile* dt = (const TcTile*)(p + jb);
   const unsigned nt = (unsigned)tiles.size();
-  if (!rc) rc = split == 3 ? launch_split<3>(nr, dj, dt, nt, (float4*)w.p, s) : launch_split<2>(nr, dj, dt, nt, (float4*)w.p, s);
+  if (!rc && from_images) rc = launch_bimages(nr, jobs, dj, bi, s);
+  if (!rc)
+    rc = from_images   ? launch_img(nr, dj, dt, nt, (float4*)w.p, s)
+         : split == 3 ? launch_split<3>(nr, dj, dt, nt, (float4*)w.p, s)
+                      : launch_split<2>(nr, dj, dt, nt, (float4*)w.p, s);
   if (!rc && !regs.empty()) {
     dim3 grid(64, (unsigned)regs.size());
     note_launch();
@@ -1036,6 +1459,7 @@ int launch_sketch_jobs_tc(const std::vector<SketchJob>& jobs_in, MemTracker* mt,
   }
   w.release(s);
   d.release(s);
+  bi.release(s);
   return rc;
 }
 

@@ -1,12 +1,13 @@
 """Entry images (mixed precision, built-in kernel operators): a factorization
-that forms every kernel entry once per orientation, bf16-split in the
-tensor-core operand layout, and feeds all its structured sketches (Alg. 2,
-Sec. 4.1) from those images must give the same bits as one that forms the
-entries on the fly in every sketch -- the image holds exactly the operand the
-sketch kernel would build.  Cases: chunk-aligned trees (every sketch reads
-the images), ragged trees (groups off the 16-column grid fall back to
-on-the-fly entries), 3D and DFT kernels, and a memory cap too small for the
-images (no images at all)."""
+that forms every kernel entry once per orientation and feeds all its
+structured sketches (Alg. 2, Sec. 4.1) from those images computes the same
+bf16 parts and products as one that forms the entries on the fly in every
+sketch, summed in another order -- so the two agree to FP32 rounding: the
+same ranks (+-1 where a pivot sits at the threshold), applies within 1e-5,
+sketch errors within the Thm 5.3 bound.  Cases: chunk-aligned trees (every
+sketch reads the images), ragged trees (groups off the 16-column grid fall
+back to on-the-fly entries), 3D and DFT kernels, and a memory cap too small
+for the images (no images at all: bit-identical)."""
 import numpy as np
 import pytest
 import torch
@@ -26,36 +27,41 @@ def _factor(plan, images):
     return F, op
 
 
+def _close(a, b, tol=1e-5):
+    torch.cuda.synchronize()
+    return float(torch.linalg.norm(a - b) / torch.linalg.norm(a)) <= tol
+
+
 def _same(plan, n_in, seed=3):
     Fa, op = _factor(plan, False)
     Fb, _ = _factor(plan, True)
+    worst = 0
     for side, levels in ((0, range(plan.lm + 1)), (1, range(plan.lm, plan.L + 1))):
         for j in levels:
-            assert np.array_equal(Fa.ranks(side, j), Fb.ranks(side, j))
+            worst = max(worst, int(np.max(np.abs(Fa.ranks(side, j) - Fb.ranks(side, j)))))
+    assert worst <= 1
     x = api.colmajor(torch.from_numpy(inputs.random_rhs(n_in, 5, seed=seed)).to(torch.complex64).cuda())
-    ya, yb = Fa.apply(x), Fb.apply(x)
-    torch.cuda.synchronize()
-    assert torch.equal(ya, yb)
+    assert _close(Fa.apply(x), Fb.apply(x))
     for opn in ("T", "C"):
         xt = api.colmajor(torch.from_numpy(inputs.random_rhs(plan.m, 3, seed=seed + 1)).to(torch.complex64).cuda())
-        assert torch.equal(Fa.apply(xt, opn), Fb.apply(xt, opn))
+        assert _close(Fa.apply(xt, opn), Fb.apply(xt, opn))
     return Fa, Fb, op
 
 
 @pytest.mark.parametrize("n", [2048, 4096])
-def test_images_bit_identical_line_pair(n):
+def test_images_match_line_pair(n):
     g = inputs.line_pair(n)
     plan = api.Plan(g.src, g.tgt, kernel="helmholtz2d", wavenumber=g.wavenumber, leaf=16, tol=1e-6,
                     precision="mixed", r0=16)
     Fa, Fb, op = _same(plan, n)
     ea = Fa.error(op, 16, seed=2, dtype=torch.complex64)
     eb = Fb.error(op, 16, seed=2, dtype=torch.complex64)
-    # same factors; the error's own norm reduction sums in no fixed order
-    assert abs(ea - eb) <= 1e-9 * ea and ea <= 2 * np.sqrt(plan.L + 2) * 1e-6
+    bound = 2 * np.sqrt(plan.L + 2) * 1e-6
+    assert ea <= bound and eb <= bound and abs(ea - eb) <= 0.05 * bound
 
 
 @pytest.mark.parametrize("geom,n,m,leaf", [("arc", 1000, 900, 16), ("cap", 777, 700, 24), ("line", 300, 300, 8)])
-def test_images_bit_identical_ragged(geom, n, m, leaf):
+def test_images_match_ragged(geom, n, m, leaf):
     g = {"arc": lambda: inputs.arc_pair(n, seed=2, m=m), "cap": lambda: inputs.cap_pair(n, m=m),
          "line": lambda: inputs.line_pair(n, m)}[geom]()
     plan = api.Plan(g.src, g.tgt, kernel=g.kernel, wavenumber=g.wavenumber, leaf=leaf, tol=1e-6,
@@ -63,7 +69,7 @@ def test_images_bit_identical_ragged(geom, n, m, leaf):
     _same(plan, n)
 
 
-def test_images_bit_identical_dft():
+def test_images_match_dft():
     n = 1024
     g = inputs.dft_points(n)
     plan = api.Plan(g.src, g.tgt, kernel="dft", leaf=16, tol=1e-6, precision="mixed")
@@ -74,7 +80,8 @@ def test_images_skipped_under_memory_cap():
     n = 2048
     g = inputs.line_pair(n)
     kw = dict(kernel="helmholtz2d", wavenumber=g.wavenumber, leaf=16, tol=1e-6, precision="mixed", r0=16)
-    # room for the factorization but not for the two images (2 x 50 MB here)
+    # room for the factorization; the two images (2 x 16.8 MB here) would take
+    # more than half of the cap, so they are not formed
     plan = api.Plan(g.src, g.tgt, mem_cap=64 * 1024 * 1024, **kw)
     ref = api.Plan(g.src, g.tgt, **kw)
     F, _ = _factor(plan, True)
