@@ -1271,15 +1271,29 @@ static int launch_split(int nr, const SketchJob* dj, const TcTile* dt, unsigned 
   }
 }
 
+static int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+      n = v;
+    else
+      n = 152;
+  }
+  return n;
+}
+
 // Split-K factor of one job: minimises (waves of CTAs) x (16-column K
-// chunks per CTA + a fixed per-CTA cost) for the job alone, so a job sums in the same order
-// whether it runs alone or in a batch.
-static int job_splits(int64_t base_tiles, int64_t max_chunks) {
+// chunks per CTA + a fixed per-CTA cost) for the job alone, so a job sums
+// in the same order whether it runs alone or in a batch.  per_sm: CTAs
+// resident per SM (2 for sketch_tc_kernel, 1 for the image kernel).
+static int job_splits(int64_t base_tiles, int64_t max_chunks, int per_sm) {
+  const int64_t wave = (int64_t)sm_count() * per_sm;
   int best = 1;
   double best_cost = 1e300;
   for (int ns = 1; ns <= 32; ++ns) {
     if (ns > 1 && max_chunks < 4 * ns) break;
-    const double waves = (double)((base_tiles * ns + 303) / 304);   // two CTAs per SM
+    const double waves = (double)((base_tiles * ns + wave - 1) / wave);
     const double cost = waves * (double)((max_chunks + ns - 1) / ns + 6);
     if (cost < best_cost * 0.999) best = ns, best_cost = cost;
   }
@@ -1299,10 +1313,12 @@ int launch_sketch_jobs_tc(const std::vector<SketchJob>& jobs_in, MemTracker* mt,
       jobs.push_back(j);
       continue;
     }
-    const int64_t kc = j.kcols;
-    for (int64_t c0 = 0; c0 < kc; c0 += WMAX) {
+    // image jobs run in slices of at most 32 columns (the image kernel's
+    // widest tile), whatever they are batched with
+    const int64_t kc = j.kcols, wmax = j.img ? 32 : WMAX;
+    for (int64_t c0 = 0; c0 < kc; c0 += wmax) {
       SketchJob q = j;
-      q.kcols = std::min(WMAX, kc - c0);
+      q.kcols = std::min(wmax, kc - c0);
       q.X = (const float2*)j.X + c0 * j.ldx;
       q.Y = (float2*)j.Y + c0 * j.ldy;
       jobs.push_back(q);
@@ -1331,16 +1347,11 @@ int launch_sketch_jobs_tc(const std::vector<SketchJob>& jobs_in, MemTracker* mt,
       return launch_sketch_jobs_tc(a, mt, s);
     }
   }
-  bool from_images = !jobs.empty() && jobs[0].img != nullptr;
+  const bool from_images = !jobs.empty() && jobs[0].img != nullptr;
   // real columns N = 2 x padded sketch width, one of the compiled tile widths
   const int kp = (int)((maxk + 7) / 8 * 8);
   const int nr = kp <= 8 ? 16 : kp <= 16 ? 32 : kp <= 24 ? 48 : kp <= 32 ? 64 : 96;
-  // the image kernel's tensor memory holds tiles up to 64 real columns;
-  // wider image jobs form their entries
-  if (from_images && nr > 64) {
-    for (auto& j : jobs) j.img = nullptr;
-    from_images = false;
-  }
+  if (from_images && nr > 64) return fail(BF_EINVAL, "image sketch job wider than 32 columns");
   const int kch = split == 3 ? Cfg<16, 3>::KCH : Cfg<16, 2>::KCH;   // complex K per chunk
   std::vector<TcTile> tiles;
   std::vector<TcRegion> regs;
@@ -1356,7 +1367,7 @@ int launch_sketch_jobs_tc(const std::vector<SketchJob>& jobs_in, MemTracker* mt,
       const int64_t G1 = j.groups1, sh = j.shift1, w0 = j.kcols0, w1 = j.kcols - j.kcols0;
       int64_t maxk_f = 0;
       for (int64_t f = 0; f < G1; ++f) maxk_f = std::max(maxk_f, j.h_off1[f + 1] - j.h_off1[f]);
-      const int ns = job_splits(rt * G1, (maxk_f + 15) / 16);
+      const int ns = job_splits(rt * G1, (maxk_f + 15) / 16, 2);
       const int64_t n0 = ((int64_t)1 << sh) * ns;   // partials per coarse node
       std::vector<int64_t> ws0(j.groups), ws1(G1, -1);
       for (int g = 0; g < j.groups; ++g) {
@@ -1397,7 +1408,7 @@ int launch_sketch_jobs_tc(const std::vector<SketchJob>& jobs_in, MemTracker* mt,
       if (a < 0) known = false;
       else maxk_g = std::max(maxk_g, b - a);
     }
-    const int ns = known ? job_splits(rt * j.groups, (maxk_g + 15) / 16) : 1;
+    const int ns = known ? job_splits(rt * j.groups, (maxk_g + 15) / 16, from_images ? 1 : 2) : 1;
     for (int g = 0; g < j.groups; ++g) {
       int64_t ga, gb;
       krange(g, ga, gb);
