@@ -236,7 +236,10 @@ struct StageTask {
 struct StageBases {
   void* p[4];
 };
-// N of every task is replaced by Noverride when Noverride > 0.  variant:
+// N of every task is replaced by Noverride when Noverride > 0; Noverride < 0:
+// per-task N, each task cut into 32-column slices (-Noverride the widest N)
+// so that wide tasks spread over many warps; 0: per-task N, one warp per
+// task.  variant:
 // kernel shape (0, 1 or 2, same results), -1 for the default for Noverride.
 // pdl: launch with a programmatic dependency on the previous kernel in s
 // (only when that kernel is itself a stage launch of the same chain).

@@ -111,7 +111,9 @@ int run_tasks(Batch& B, const std::vector<StageTask>& tasks, const StageBases& b
                               cudaMemcpyHostToDevice, B.s));
   int mM = 0, mN = 0;
   for (const auto& t : tasks) mM = std::max(mM, t.M), mN = std::max(mN, t.N);
-  return launch_stage((const StageTask*)d.p(), (int)tasks.size(), mM, mN, 0, bases, B.dt, B.s);
+  // per-task N in 32-column slices: the first peel stages of a level carry
+  // k 2^(l-j) columns per block
+  return launch_stage((const StageTask*)d.p(), (int)tasks.size(), mM, mN, -mN, bases, B.dt, B.s);
 }
 
 // One structured sketch request (Sec. 4.1): Y = op(A) Omega-bar for the

@@ -28,7 +28,8 @@ __device__ __forceinline__ void philox4x32_10(uint32_t& c0, uint32_t& c1,
 }
 
 // Entry (g, c): counter (g>>1, c, stream, 0), key = seed; words (0,1) for
-// even g, (2,3) for odd g; Box-Muller z = sqrt(-ln u1) exp(2 pi i u2).
+// even g, (2,3) for odd g; Box-Muller z = sqrt(-ln u1) exp(2 pi i u2) with
+// u = (word + 1/2) 2^-32 (FP64 for complex128 output, FP32 for complex64).
 template <typename R>
 __global__ void gaussian_kernel(uint64_t seed, uint32_t sid, int64_t row0,
                                 int64_t rows, int64_t col0, int64_t ncols,
@@ -47,12 +48,24 @@ __global__ void gaussian_kernel(uint64_t seed, uint32_t sid, int64_t row0,
       const int64_t g = 2 * pr + h;
       if (g < row0 || g >= row0 + rows) continue;
       const uint32_t a = h ? w2 : w0, b = h ? w3 : w1;
-      const double u1 = ((double)a + 0.5) * 2.3283064365386963e-10;
-      const double u2 = ((double)b + 0.5) * 2.3283064365386963e-10;
-      const double rad = sqrt(-log(u1));
-      double sn, cs;
-      sincospi(2.0 * u2, &sn, &cs);
-      out[(g - row0) + (c - col0) * ld] = Cx<R>::make((R)(rad * cs), (R)(rad * sn));
+      if (sizeof(R) == 8) {
+        const double u1 = ((double)a + 0.5) * 2.3283064365386963e-10;
+        const double u2 = ((double)b + 0.5) * 2.3283064365386963e-10;
+        const double rad = sqrt(-log(u1));
+        double sn, cs;
+        sincospi(2.0 * u2, &sn, &cs);
+        out[(g - row0) + (c - col0) * ld] = Cx<R>::make((R)(rad * cs), (R)(rad * sn));
+      } else {
+        // complex64: the same variates in FP32 (this GPU's FP64 pipe is
+        // 1/64 of its FP32 rate); -ln u1 from u1 itself below 1/2 and from
+        // 1 - u1 (exact in 32-bit integers) above, so no cancellation
+        const float l = a < 0x80000000u ? -logf(((float)a + 0.5f) * 2.3283064e-10f)
+                                        : -log1pf(-((float)(0xFFFFFFFFu - a) + 0.5f) * 2.3283064e-10f);
+        const float rad = sqrtf(l);
+        float sn, cs;
+        sincospif(2.0f * (((float)b + 0.5f) * 2.3283064e-10f), &sn, &cs);
+        out[(g - row0) + (c - col0) * ld] = Cx<R>::make((R)(rad * cs), (R)(rad * sn));
+      }
     }
   }
 }

@@ -87,7 +87,8 @@ stage_mlp_kernel(const StageTask* __restrict__ tasks, int ntasks, StageBases bas
   // launch's N, row groups from the launch's largest M (the host keeps the
   // item count below 2^31)
   const int Nl = Noverride;
-  const int slices = Nl > 0 ? (Nl + CW - 1) / CW : 1;
+  const int Nmax = Nl > 0 ? Nl : -Nl;   // Nl < 0: per-task N, -Nl the widest
+  const int slices = Nmax > 0 ? (Nmax + CW - 1) / CW : 1;
   const int per_task = slices * rgroups;
   const int items = ntasks * per_task;
   {
@@ -105,7 +106,8 @@ stage_mlp_kernel(const StageTask* __restrict__ tasks, int ntasks, StageBases bas
     const Strides so = strides(tk.out_off, tk.ldo, N);
     V* __restrict__ out = (V*)bases.p[tk.out_base] + so.off;
     // column slices of this warp: sl (fixed N) or all of them (per-task N)
-    const int c_first = Nl > 0 ? sl * CW : 0, c_last = Nl > 0 ? c_first + CW : N;
+    const int c_first = Nmax > 0 ? sl * CW : 0;
+    const int c_last = Nl > 0 ? c_first + CW : (Nmax > 0 ? (c_first + CW < N ? c_first + CW : N) : N);
     bool rv[RT];
 #pragma unroll
     for (int r = 0; r < RT; ++r) rv[r] = i0 + ri + r * RW < M;
@@ -166,7 +168,8 @@ stage_rows_kernel(const StageTask* __restrict__ tasks, int ntasks, StageBases ba
   const int ci = lane & (CW - 1), ri = lane >> lcw;
   const int nwarps = gridDim.x * WARPS;
   const int Nl = Noverride;
-  const int slices = Nl > 0 ? (Nl + CW - 1) / CW : 1;
+  const int Nmax = Nl > 0 ? Nl : -Nl;   // Nl < 0: per-task N, -Nl the widest
+  const int slices = Nmax > 0 ? (Nmax + CW - 1) / CW : 1;
   const int items = ntasks * slices;
   {
     const int w0 = blockIdx.x * WARPS + (threadIdx.x >> 5);
@@ -179,7 +182,8 @@ stage_rows_kernel(const StageTask* __restrict__ tasks, int ntasks, StageBases ba
     const int N = Nl > 0 ? Nl : tk.N;
     const Strides so = strides(tk.out_off, tk.ldo, N);
     V* __restrict__ out = (V*)bases.p[tk.out_base] + so.off;
-    const int c_first = Nl > 0 ? sl * CW : 0, c_last = Nl > 0 ? c_first + CW : N;
+    const int c_first = Nmax > 0 ? sl * CW : 0;
+    const int c_last = Nl > 0 ? c_first + CW : (Nmax > 0 ? (c_first + CW < N ? c_first + CW : N) : N);
     for (int c0 = c_first; c0 < c_last; c0 += CW) {
       const int c = c0 + ci;
       const bool cv = c < N;
@@ -243,7 +247,8 @@ stage_block_kernel(const StageTask* __restrict__ tasks, int ntasks, StageBases b
   V* __restrict__ fl = &ms[0][0];
   const int nwarps = gridDim.x * WARPS;
   const int Nl = Noverride;
-  const int slices = Nl > 0 ? (Nl + CW - 1) / CW : 1;
+  const int Nmax = Nl > 0 ? Nl : -Nl;   // Nl < 0: per-task N, -Nl the widest
+  const int slices = Nmax > 0 ? (Nmax + CW - 1) / CW : 1;
   const int items = ntasks * slices;
   {
     const int w0 = blockIdx.x * WARPS + warp;
@@ -256,7 +261,8 @@ stage_block_kernel(const StageTask* __restrict__ tasks, int ntasks, StageBases b
     const int N = Nl > 0 ? Nl : tk.N;
     const Strides so = strides(tk.out_off, tk.ldo, N);
     V* __restrict__ out = (V*)bases.p[tk.out_base] + so.off;
-    const int c_first = Nl > 0 ? sl * CW : 0, c_last = Nl > 0 ? c_first + CW : N;
+    const int c_first = Nmax > 0 ? sl * CW : 0;
+    const int c_last = Nl > 0 ? c_first + CW : (Nmax > 0 ? (c_first + CW < N ? c_first + CW : N) : N);
     for (int c0 = c_first; c0 < c_last; c0 += CW) {
       const int c = c0 + ci;
       const bool cv = c < N;
@@ -355,7 +361,7 @@ int launch_stage(const StageTask* d_tasks, int ntasks, int maxM, int maxN, int N
     lcw = 0;
     while ((1 << lcw) < Noverride && lcw < 5) ++lcw;
   }
-  const int64_t slices = Noverride > 0 ? (Noverride + (1 << lcw) - 1) >> lcw : 1;
+  const int64_t slices = Noverride != 0 ? ((Noverride > 0 ? Noverride : -Noverride) + (1 << lcw) - 1) >> lcw : 1;
   const int gr = (32 >> lcw) * RT;
   const int rgroups = variant == 0 ? (maxM + gr - 1) / gr : 1;
   const int64_t warps = (int64_t)ntasks * slices * rgroups;
