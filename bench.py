@@ -345,7 +345,7 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
             "data": "synthetic",
-            "config": {"workload": "helmholtz2d_line_pair_n16384_onthefly", "n": N, "leaf": LEAF, "tol": TOL},
+            "config": {"workload": "helmholtz2d_line_pair_n16384_kernel", "n": N, "leaf": LEAF, "tol": TOL},
             "cpu_baseline": {"kind": "oracle", "value": v, "unit": "s", "cores": os.cpu_count(),
                              "sample": "oracle factorization at n=1024 per step, scaled to n=16384 by n^1.5 log n"},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -485,14 +485,43 @@ def main():
     qr64 = {"factor_s": float(np.mean(q_s[1:])),
             "sketch_error": Fq.error(op_q, 16, seed=7, dtype=torch.complex64)}
 
-    # roofline of the dominant kernel (the on-the-fly sketch product): one
-    # launch over all m x n entries with the widest sketch width of the run,
-    # timed with CUDA events on the launching stream
+    # roofline of the dominant kernel of the factorization: the sketch
+    # product fed by the complex64 entry image (sketch_img_kernel), one
+    # product over all m x n entries at the widest sketch width of the run,
+    # timed with CUDA events on the launching stream through an operator
+    # whose images are resident; the image formation (entry_image_kernel,
+    # two launches) is timed when that operator is built
     kw = 22
     Xk = api.colmajor(torch.from_numpy(inputs.random_rhs(N, kw, seed=3)).to(torch.complex64).cuda())
-    op_mx.apply(Xk)
     r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     reps = 5
+    torch.cuda.synchronize()
+    r0.record(stream)
+    op_img = api.Operator.kernel(plan_mx, cached=True)
+    r1.record(stream)
+    torch.cuda.synchronize()
+    t_form = r0.elapsed_time(r1) / 2 / 1e3          # one orientation
+    op_img.apply(Xk)
+    torch.cuda.synchronize()
+    r0.record(stream)
+    for _ in range(reps):
+        op_img.apply(Xk)
+    r1.record(stream)
+    torch.cuda.synchronize()
+    t_img = r0.elapsed_time(r1) / reps / 1e3
+    del op_img
+    torch.cuda.synchronize()
+    kp = (kw + 7) // 8 * 8
+    nr_img = 16 if kp <= 8 else 32 if kp <= 16 else 48 if kp <= 24 else 64
+    img_bytes = 8.0 * N * N + 8.0 * N * kw * 2          # the image (8 B per entry) + X + Y
+    chunks = (N // 128) * (N // 16)
+    img_mma_flops = chunks * 2 * (2.0 * 128 * 16 * 6 * nr_img)   # 2 K steps x 3 MMAs (N = 3, 2, 1 x NR)
+    # one tcgen05.mma (M = 128, K = 16) occupies the tensor pipe ~153 cycles at
+    # any N <= 256 (measured, profiles/sketch_img_kernel_helmholtz2d_n8192.md)
+    mma_issue_s = chunks * 6 * 153.0 / (152 * 2070e6)
+    # the on-the-fly product (entries formed in every sketch; still used by
+    # products of plain kernel operators and when images do not fit)
+    op_mx.apply(Xk)
     torch.cuda.synchronize()
     r0.record(stream)
     for _ in range(reps):
@@ -549,7 +578,7 @@ def main():
         "vs_baseline": None,
         "dtype": "c64+f64",
         "data": "synthetic",
-        "config": {"workload": "helmholtz2d_line_pair_n16384_onthefly", "n": N, "m": N, "leaf": LEAF,
+        "config": {"workload": "helmholtz2d_line_pair_n16384_kernel", "n": N, "m": N, "leaf": LEAF,
                    "L": plan_mx.L, "tol": TOL, "p": 2, "r0": R0, "precision": "mixed", "nrhs": NRHS,
                    "l2": "flushed (512 MB write) before every step"},
         "factor_s_mixed": float(np.mean(fac_s)),
@@ -568,16 +597,31 @@ def main():
         "serving": serving,
         "batched": batched,
         "configs": configs,
-        "roofline": {"kernel": "sketch_tc_kernel (tcgen05, exact three-way bf16 split, entries on the fly)", "bound": "alu",
-                     "achieved": ALU_OPS_PER_ENTRY * N * N / t_sk / 1e12, "peak": alu_peak, "unit": "Tops/s",
-                     "frac": ALU_OPS_PER_ENTRY * N * N / t_sk / 1e12 / alu_peak, "traffic": None,
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz (one op per lane per clock)",
-                     "work": f"{ALU_OPS_PER_ENTRY} FP32 ops per kernel entry (the float-float entry formula), "
-                             f"m=n={N} entries; the {kw}-column product runs on the tensor pipe",
-                     "launch_ms": t_sk * 1e3, "engine_ms": engine_ms,
-                     "tensor_pipe": {"achieved_tflops": tc_flops / t_sk / 1e12, "peak_tflops": tc_peak,
-                                     "frac": tc_flops / t_sk / 1e12 / tc_peak,
-                                     "peak_source": "measured bf16 (burst)"},
+        "roofline": {"kernel": "sketch_img_kernel (tcgen05, complex64 entry image streamed, exact three-way "
+                               "bf16 split, B parts stacked along N)", "bound": "hbm",
+                     "achieved": img_bytes / t_img / 1e9, "peak": peaks.get("hbm_gbs", 6800.0), "unit": "GB/s",
+                     "frac": img_bytes / t_img / 1e9 / peaks.get("hbm_gbs", 6800.0), "traffic": None,
+                     "peak_source": peak_src + " (burst copy)",
+                     "work": f"8 B per entry of the m=n={N} image + the {kw}-column X and Y, once each; "
+                             "the timed product is 3 launches (B operand, image sketch, split-K reduce)",
+                     "launch_ms": t_img * 1e3,
+                     "tensor_pipe": {"achieved_tflops": img_mma_flops / t_img / 1e12, "peak_tflops": tc_peak,
+                                     "frac": img_mma_flops / t_img / 1e12 / tc_peak,
+                                     "peak_source": "measured bf16 (burst)",
+                                     "mma_issue_bound_ms": mma_issue_s * 1e3,
+                                     "frac_of_issue_bound": mma_issue_s / t_img},
+                     "entry_image_kernel": {"bound": "alu", "ms_per_orientation": t_form * 1e3,
+                                            "achieved": ALU_OPS_PER_ENTRY * N * N / t_form / 1e12,
+                                            "peak": alu_peak, "unit": "Tops/s",
+                                            "frac": ALU_OPS_PER_ENTRY * N * N / t_form / 1e12 / alu_peak,
+                                            "work": f"{ALU_OPS_PER_ENTRY} FP32 ops per entry (the float-float "
+                                                    "formula) + 8 B written"},
+                     "on_the_fly": {"kernel": "sketch_tc_kernel (entries formed in the product)", "bound": "alu",
+                                    "launch_ms": t_sk * 1e3, "engine_ms": engine_ms,
+                                    "achieved": ALU_OPS_PER_ENTRY * N * N / t_sk / 1e12, "peak": alu_peak,
+                                    "unit": "Tops/s", "frac": ALU_OPS_PER_ENTRY * N * N / t_sk / 1e12 / alu_peak,
+                                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz",
+                                    "tensor_frac": tc_flops / t_sk / 1e12 / tc_peak},
                      "apply": {"bound": "hbm (latency-bound in practice: L+3 dependent stage launches)",
                                "achieved_gbs_c64": gbs32, "peak_gbs": peaks.get("hbm_gbs"),
                                "frac_c64": gbs32 / peaks.get("hbm_gbs", 6800.0),

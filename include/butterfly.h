@@ -147,6 +147,17 @@ int bf_operator_dense(bf_plan plan, const void* A, int64_t lda, int dtype,
  * (BF_EINVAL if the plan has no kernel or no points). */
 int bf_operator_kernel(bf_plan plan, bf_operator* out);
 
+/* The same operator with its entries resident: both orientations (A and
+ * A^H) are formed once, on `stream`, as complex64 entry images (the layout
+ * bf_set_entry_images describes; 16 bytes per entry of A in all, counted
+ * against the plan's mem_cap), and its complex64 products with A and A^H
+ * -- bf_operator_apply and the structured sketches of a factorization --
+ * stream them instead of re-forming the entries (complex128 products form
+ * entries as bf_operator_kernel does).  A factorization of this operator
+ * reuses the images instead of forming its own.  Errors: as
+ * bf_operator_kernel; BF_ENOMEM when the images do not fit. */
+int bf_operator_kernel_cached(bf_plan plan, void* stream, bf_operator* out);
+
 /* A = the factorization F, applied by bf_apply / bf_apply_T (the black box
  * of the exact-recovery and composition workloads).  F must outlive it. */
 int bf_operator_factored(bf_fact F, bf_operator* out);

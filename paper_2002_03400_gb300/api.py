@@ -63,6 +63,7 @@ def lib():
         "bf_plan_trees": (i32, [vp, vp, vp, vp, vp]),
         "bf_operator_dense": (i32, [vp, vp, i64, i32, vp, C.POINTER(vp)]),
         "bf_operator_kernel": (i32, [vp, C.POINTER(vp)]),
+        "bf_operator_kernel_cached": (i32, [vp, vp, C.POINTER(vp)]),
         "bf_operator_factored": (i32, [vp, C.POINTER(vp)]),
         "bf_operator_composed": (i32, [vp, vp, C.POINTER(vp)]),
         "bf_operator_callback": (i32, [i64, i64, MATVEC_FN, vp, C.POINTER(vp)]),
@@ -98,7 +99,7 @@ def lib():
 def exported_symbols():
     """Names declared in include/butterfly.h that the binding expects."""
     return ["bf_options_default", "bf_last_error", "bf_bisect", "bf_plan_create", "bf_plan_info", "bf_plan_trees",
-            "bf_operator_dense", "bf_operator_kernel", "bf_operator_factored", "bf_operator_composed",
+            "bf_operator_dense", "bf_operator_kernel", "bf_operator_kernel_cached", "bf_operator_factored", "bf_operator_composed",
             "bf_operator_callback", "bf_operator_apply", "bf_operator_counts", "bf_factor",
             "bf_factor_batch", "bf_apply",
             "bf_apply_T", "bf_apply_noalloc", "bf_ranks", "bf_fact_info", "bf_fact_import", "bf_fact_export", "bf_error",
@@ -245,9 +246,14 @@ class Operator(_Handle):
         return cls(h, plan.m, plan.n, keep=[plan])
 
     @classmethod
-    def kernel(cls, plan: Plan):
+    def kernel(cls, plan: Plan, cached: bool = False, stream=None):
+        """Built-in kernel operator; cached=True keeps its entries resident
+        as complex64 entry images (bf_operator_kernel_cached)."""
         h = C.c_void_p()
-        check(lib().bf_operator_kernel(plan._h, C.byref(h)))
+        if cached:
+            check(lib().bf_operator_kernel_cached(plan._h, _stream(stream), C.byref(h)))
+        else:
+            check(lib().bf_operator_kernel(plan._h, C.byref(h)))
         return cls(h, plan.m, plan.n, keep=[plan])
 
     @classmethod

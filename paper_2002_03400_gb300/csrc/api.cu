@@ -235,7 +235,15 @@ struct DenseOp : PlanOp {
 };
 
 struct KernelOp : PlanOp {
+  DevBuf imgN, imgC;   // resident entry images (bf_operator_kernel_cached), or empty
+  ~KernelOp() override {
+    imgN.release(nullptr);
+    imgC.release(nullptr);
+  }
   bool builtin_kernel() const override { return true; }
+  const void* entry_image(int op) const override {
+    return op == BF_OP_N ? imgN.p : op == BF_OP_C ? imgC.p : nullptr;
+  }
   bool make_job(int op, const GemmGroups& g, const void* X, int64_t ldx, void* Y, int64_t ldy, int dtype,
                 SketchJob* job) override {
     *job = kernel_job(plan, op, g, X, ldx, Y, ldy);
@@ -244,12 +252,12 @@ struct KernelOp : PlanOp {
   int tree_impl(int op, int64_t ncols, const void* X, int64_t ldx, void* Y, int64_t ldy, int dtype,
                 cudaStream_t s) override {
     GemmGroups g{1, nullptr, ncols};
-    return launch_kernel_gemm(plan, op, g, X, ldx, Y, ldy, dtype, s);
+    return launch_kernel_gemm(plan, op, g, X, ldx, Y, ldy, dtype, s, entry_image(op));
   }
   int struct_impl(int op, int groups, const int64_t* d_off, int64_t k, const void* Om, int64_t ldo,
                   void* Y, int64_t ldy, int dtype, cudaStream_t s) override {
     GemmGroups g{groups, d_off, k};
-    return launch_kernel_gemm(plan, op, g, Om, ldo, Y, ldy, dtype, s);
+    return launch_kernel_gemm(plan, op, g, Om, ldo, Y, ldy, dtype, s, entry_image(op));
   }
 };
 
@@ -522,6 +530,25 @@ int bf_operator_kernel(bf_plan plan, bf_operator* out) {
   op->n = P->n;
   *out = new bf_operator_s{KIND_OP, op};
   return BF_OK;
+}
+
+int bf_operator_kernel_cached(bf_plan plan, void* stream, bf_operator* out) {
+  BF_TRY(bf_operator_kernel(plan, out));
+  auto* op = (KernelOp*)(*out)->impl;
+  Plan* P = op->plan;
+  cudaStream_t s = user_stream(stream);
+  int rc = op->imgN.alloc(&P->mem, entry_image_bytes(P->m, P->n), s);
+  if (!rc) rc = op->imgC.alloc(&P->mem, entry_image_bytes(P->n, P->m), s);
+  for (int o : {BF_OP_N, BF_OP_C}) {
+    if (rc) break;
+    const SketchJob j = kernel_job(P, o, GemmGroups{1, nullptr, 1}, nullptr, 0, nullptr, 0);
+    rc = launch_entry_image(j, o == BF_OP_N ? op->imgN.p : op->imgC.p, s);
+  }
+  if (rc) {
+    bf_free(*out);
+    *out = nullptr;
+  }
+  return rc;
 }
 
 int bf_operator_factored(bf_fact F, bf_operator* out) {

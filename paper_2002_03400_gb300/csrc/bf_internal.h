@@ -138,6 +138,9 @@ struct Operator {
   }
   // built-in kernel operator (its entries have a closed form)
   virtual bool builtin_kernel() const { return false; }
+  // resident entry image of op (BF_OP_N or BF_OP_C) in the tensor-core
+  // layout (see SketchJob::img), or null
+  virtual const void* entry_image(int op) const { return nullptr; }
   // Structured sketch (Sec. 4.1), tree order: for each node g of `groups`
   // with rows [off[g], off[g+1]) of the input side, and compact random
   // matrix Om (rows = input side, k columns, ld ldo):
@@ -394,9 +397,11 @@ struct GemmGroups {
 int launch_dense_gemm(int op, const void* A, int64_t lda, int64_t m, int64_t n,
                       const GemmGroups& g, const void* X, int64_t ldx, void* Y,
                       int64_t ldy, int dtype, cudaStream_t s);
+// img: the operator's resident entry image for op, or null (complex64
+// products of N and C read it when the job's K ranges allow)
 int launch_kernel_gemm(const Plan* plan, int op, const GemmGroups& g,
                        const void* X, int64_t ldx, void* Y, int64_t ldy,
-                       int dtype, cudaStream_t s);
+                       int dtype, cudaStream_t s, const void* img = nullptr);
 
 // ---------------------------------------------------------------- misc ----
 // out[i, c] = conj?(in[perm[i], c])  (perm may be null: identity)

@@ -64,8 +64,10 @@ struct OpState {
   std::vector<int64_t> prev, cur;                              // peel block offsets
   int in_base = -1;
   // entry images of a built-in operator for this factorization (op N:
-  // m x n, op C: n x m), or null
+  // m x n, op C: n x m): the operator's resident ones, or formed here
   DevBuf imgN, imgC;
+  const void* img_n = nullptr;
+  const void* img_c = nullptr;
 };
 
 struct Batch {
@@ -172,9 +174,9 @@ int sketch_all(Batch& B, const std::vector<SketchReq>& reqs) {
       // selectable through bf_set_sketch_engine
       j.split = 3;
       j.h_off = (opN ? P->offS[q.level] : P->offT[q.level]).data();
-      const DevBuf& img = opN ? q.o->imgN : q.o->imgC;
-      if ((q.op == BF_OP_N || q.op == BF_OP_C) && img.p && entry_image_fits(j)) {
-        j.img = img.p;
+      const void* img = opN ? q.o->img_n : q.o->img_c;
+      if ((q.op == BF_OP_N || q.op == BF_OP_C) && img && entry_image_fits(j)) {
+        j.img = img;
         j.img_nch = entry_image_chunks(j.Ktot);
       }
       jobs.push_back(j);
@@ -199,6 +201,11 @@ int make_images(Batch& B) {
   for (auto& o : B.ops) {
     Plan* P = o.P;
     if (o.A->plan != P || !o.A->builtin_kernel()) continue;
+    if (o.A->entry_image(BF_OP_N) && o.A->entry_image(BF_OP_C)) {   // resident in the operator
+      o.img_n = o.A->entry_image(BF_OP_N);
+      o.img_c = o.A->entry_image(BF_OP_C);
+      continue;
+    }
     const size_t bN = entry_image_bytes(P->m, P->n), bC = entry_image_bytes(P->n, P->m);
     if (bN + bC > budget) continue;
     if (B.mem.cap && (B.mem.used >= B.mem.cap || bN + bC > (B.mem.cap - B.mem.used) / 2)) continue;
@@ -212,6 +219,8 @@ int make_images(Batch& B) {
       const SketchJob j = kernel_job(P, op, GemmGroups{1, nullptr, 1}, nullptr, 0, nullptr, 0);
       BF_TRY(launch_entry_image(j, op == BF_OP_N ? o.imgN.p : o.imgC.p, B.s));
     }
+    o.img_n = o.imgN.p;
+    o.img_c = o.imgC.p;
   }
   return BF_OK;
 }

@@ -284,8 +284,13 @@ int launch_dense_gemm(int op, const void* A, int64_t lda, int64_t m, int64_t n, 
 }
 
 int launch_kernel_gemm(const Plan* P, int op, const GemmGroups& g, const void* X, int64_t ldx,
-                       void* Y, int64_t ldy, int dtype, cudaStream_t s) {
-  return launch_sketch_jobs({kernel_job(P, op, g, X, ldx, Y, ldy)}, dtype, nullptr, s);
+                       void* Y, int64_t ldy, int dtype, cudaStream_t s, const void* img) {
+  SketchJob j = kernel_job(P, op, g, X, ldx, Y, ldy);
+  if (img && dtype == BF_C64 && (op == BF_OP_N || op == BF_OP_C) && entry_image_fits(j)) {
+    j.img = img;
+    j.img_nch = entry_image_chunks(j.Ktot);
+  }
+  return launch_sketch_jobs({j}, dtype, nullptr, s);
 }
 
 }  // namespace bf

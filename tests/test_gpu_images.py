@@ -93,3 +93,29 @@ def test_images_skipped_under_memory_cap():
 def test_set_entry_images_rejects_bad_values():
     assert api.lib().bf_set_entry_images(2) == -1
     assert api.lib().bf_set_entry_images(1) == 0
+
+
+def test_cached_kernel_operator_products_and_factorization():
+    """bf_operator_kernel_cached: products with A, A^T, A^H stream the
+    resident images and match the FP64 kernel entries to FP32 level; a
+    factorization of the cached operator reuses them and matches one of the
+    plain operator."""
+    from oracle import operators as oo
+    n = 1536
+    g = inputs.line_pair(n)
+    plan = api.Plan(g.src, g.tgt, kernel="helmholtz2d", wavenumber=g.wavenumber, leaf=16, tol=1e-6,
+                    precision="mixed", r0=16)
+    A = oo.kernel_entries(oo.HELMHOLTZ_2D, g.wavenumber, g.tgt, g.src)
+    opc = api.Operator.kernel(plan, cached=True)
+    x = inputs.random_rhs(n, 7, seed=2)
+    xt = torch.from_numpy(x).to(torch.complex64).cuda()
+    for opn, ref in (("N", A @ x), ("T", A.T @ x), ("C", A.conj().T @ x)):
+        y = opc.apply(api.colmajor(xt), opn)
+        torch.cuda.synchronize()
+        got = y.cpu().numpy().astype(np.complex128)
+        assert np.linalg.norm(got - ref) <= 2e-6 * np.linalg.norm(ref)
+    Fc = api.Factorization.factor(plan, opc)
+    Fp, _ = _factor(plan, True)
+    xr = api.colmajor(torch.from_numpy(inputs.random_rhs(n, 3, seed=5)).to(torch.complex64).cuda())
+    assert _close(Fc.apply(xr), Fp.apply(xr))
+    assert Fc.error(opc, 16, seed=3, dtype=torch.complex64) <= 2 * np.sqrt(plan.L + 2) * 1e-6
