@@ -882,6 +882,12 @@ struct ICfg {
   static constexpr int S = total(4) <= LIMIT ? 4 : total(3) <= LIMIT ? 3 : 2;
   static constexpr uint32_t F0 = 0, O0 = SF * F_SLOT, TOTAL = O0 + S * O_SLOT;
   static_assert(TOTAL <= LIMIT && C::PT == 1 && C::VS == 8, "image tile: shared memory, one 8-column group per thread");
+  // a producer group waits on a slot's mbarrier by phase parity; with an
+  // odd slot count, consecutive uses of a slot alternate between the two
+  // groups, and a group could see the phase two back (same parity) and pass
+  // early.  Slot counts that are multiples of the group count make every
+  // group observe every phase of the slots it uses.
+  static_assert(S % 2 == 0 && SF % 2 == 0, "slot counts must be multiples of the producer groups");
   static_assert(C::DR == 4, "group 0 drains at the third chunk of the next group");
 };
 constexpr int IPG = 2;                                // producer groups
