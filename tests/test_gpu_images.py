@@ -119,3 +119,23 @@ def test_cached_kernel_operator_products_and_factorization():
     xr = api.colmajor(torch.from_numpy(inputs.random_rhs(n, 3, seed=5)).to(torch.complex64).cuda())
     assert _close(Fc.apply(xr), Fp.apply(xr))
     assert Fc.error(opc, 16, seed=3, dtype=torch.complex64) <= 2 * np.sqrt(plan.L + 2) * 1e-6
+
+
+def test_repeated_factorizations_stay_within_bound():
+    """Eight factorizations of the n = 16384 workload (entry images, the
+    warp-specialized sketch kernel's pipeline under varying timing): every
+    sketch error stays within the Thm 5.3 bound and the ranks repeat."""
+    n = 16384
+    g = inputs.line_pair(n)
+    plan = api.Plan(g.src, g.tgt, kernel="helmholtz2d", wavenumber=g.wavenumber, leaf=16, tol=1e-6,
+                    precision="mixed", r0=16)
+    op = api.Operator.kernel(plan)
+    bound = 2 * np.sqrt(plan.L + 2) * 1e-6
+    first = None
+    for _ in range(8):
+        F = api.Factorization.factor(plan, op)
+        assert F.error(op, 16, seed=3, dtype=torch.complex64) <= bound
+        r = np.concatenate([F.ranks(0, j) for j in range(plan.lm + 1)])
+        if first is None:
+            first = r
+        assert np.array_equal(r, first)
