@@ -539,10 +539,9 @@ int bf_operator_kernel_cached(bf_plan plan, void* stream, bf_operator* out) {
   cudaStream_t s = user_stream(stream);
   int rc = op->imgN.alloc(&P->mem, entry_image_bytes(P->m, P->n), s);
   if (!rc) rc = op->imgC.alloc(&P->mem, entry_image_bytes(P->n, P->m), s);
-  for (int o : {BF_OP_N, BF_OP_C}) {
-    if (rc) break;
-    const SketchJob j = kernel_job(P, o, GemmGroups{1, nullptr, 1}, nullptr, 0, nullptr, 0);
-    rc = launch_entry_image(j, o == BF_OP_N ? op->imgN.p : op->imgC.p, s);
+  if (!rc) {
+    const SketchJob j = kernel_job(P, BF_OP_N, GemmGroups{1, nullptr, 1}, nullptr, 0, nullptr, 0);
+    rc = launch_entry_images(j, op->imgN.p, op->imgC.p, s);
   }
   if (rc) {
     bf_free(*out);

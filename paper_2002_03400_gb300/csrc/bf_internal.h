@@ -345,7 +345,7 @@ struct SketchJob {
   // Entry image (tensor-core path, split 3, built-in operators): the
   // complex64 entries of every (128-row tile rt, 16-column chunk kc),
   // preformed, at img + (rt * img_nch + kc) * 16384 bytes
-  // (launch_entry_image); null: entries are formed on the fly.  Used only
+  // (launch_entry_images); null: entries are formed on the fly.  Used only
   // when every K range of the job starts on a chunk boundary and ends on one
   // or at Ktot.
   const void* img;
@@ -364,11 +364,13 @@ int launch_sketch_jobs_tc(const std::vector<SketchJob>& jobs, MemTracker* mt, cu
 // BF_ETIMEOUT if a tensor-core kernel's bounded wait gave up since the last reset
 int tc_status(bool reset);
 // Entry images (see SketchJob::img): bytes for an M x K orientation, and the
-// launch that fills one for kernel job j (j.op, j.M, j.Ktot, points; X, Y
-// and groups ignored).  img: device, 16-byte aligned, entry_image_bytes.
+// launch that fills both of kernel job jn (op N: M = m targets, Ktot = n
+// sources; X, Y and groups ignored) in one pass: imgN (m x n,
+// entry_image_bytes(m, n)) and imgC (the op-C image, n x m,
+// entry_image_bytes(n, m)); device, 16-byte aligned.
 size_t entry_image_bytes(int64_t M, int64_t K);
 int64_t entry_image_chunks(int64_t K);
-int launch_entry_image(const SketchJob& j, void* img, cudaStream_t s);
+int launch_entry_images(const SketchJob& jn, void* imgN, void* imgC, cudaStream_t s);
 // whether job j may read an image: split 3, one segment, and every K range
 // (groups and their split-K parts) on chunk boundaries
 bool entry_image_fits(const SketchJob& j);

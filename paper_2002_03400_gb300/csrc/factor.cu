@@ -215,10 +215,8 @@ int make_images(Batch& B) {
       continue;
     }
     budget -= bN + bC;
-    for (int op : {BF_OP_N, BF_OP_C}) {
-      const SketchJob j = kernel_job(P, op, GemmGroups{1, nullptr, 1}, nullptr, 0, nullptr, 0);
-      BF_TRY(launch_entry_image(j, op == BF_OP_N ? o.imgN.p : o.imgC.p, B.s));
-    }
+    const SketchJob j = kernel_job(P, BF_OP_N, GemmGroups{1, nullptr, 1}, nullptr, 0, nullptr, 0);
+    BF_TRY(launch_entry_images(j, o.imgN.p, o.imgC.p, B.s));
     o.img_n = o.imgN.p;
     o.img_c = o.imgC.p;
   }

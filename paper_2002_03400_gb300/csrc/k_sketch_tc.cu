@@ -744,8 +744,8 @@ __global__ void tc_reduce_kernel(const TcRegion* __restrict__ regs, int nreg, co
 // ---------------------------------------------------------------------------
 // Entry images and the image-fed sketch kernel
 // ---------------------------------------------------------------------------
-// An entry image holds one orientation of a built-in operator's m x n
-// entries in complex64, as the tiles the sketch kernel consumes: tile
+// An entry image holds one orientation of a built-in operator's entries in
+// complex64, as the tiles the image-fed sketch kernel consumes: tile
 // (row tile rt, 16-column chunk kc) at img + (rt * nchi + kc) * IMG_TILE,
 // 128 rows of 128 bytes (16 complex entries, re/im interleaved); the 16-byte
 // segment q (2 entries) of row r sits at position q ^ (r & 7) so that the
@@ -757,26 +757,35 @@ constexpr uint32_t IMG_TILE = TM * 16 * 8;     // bytes of one tile
 
 __device__ __forceinline__ uint32_t img_seg(int r, int q) { return (uint32_t)r * 128u + (uint32_t)((q ^ (r & 7)) * 16); }
 
-__global__ void __launch_bounds__(256) entry_image_kernel(const SketchJob J, uint8_t* __restrict__ img,
-                                                          int64_t nchi) {
+// Both entry images in one pass (A for op N, A^H for op C): a CTA forms the
+// entries of one 128-target tile x IMG_CPB 16-source chunks (the on-the-fly
+// producers' formula and thread mapping) and writes them as A's tiles; every 4
+// chunks (64 sources) the entries also go through shared memory
+// (conflict-free row stride of 129 entries) and come back out transposed
+// and conjugated as rows 64 h .. 64 h + 63 of the A^H tiles of those sources
+// (the conjugate of A's entry is the op-C formula's value: the distance is
+// computed sign-symmetrically).  A^H tiles past the m targets are skipped.
+constexpr int IMG_PASS = 4;   // chunks (64 sources) per transpose pass
+__global__ void __launch_bounds__(256) entry_images_kernel(const SketchJob J, uint8_t* __restrict__ imgN,
+                                                           uint8_t* __restrict__ imgC, int64_t nchN,
+                                                           int64_t nchC) {
   using C = Cfg<16, 3>;
-  constexpr int KCH = C::KCH, VS = C::VS;
-  static_assert(NWARP * 32 == 256 && KCH == 16 && VS == 8, "producer mapping of 8 warps, 16-column chunks");
+  constexpr int KCH = C::KCH, VS = C::VS, SRC = IMG_PASS * KCH, LDS = TM + 1;
   __shared__ __align__(16) float pts[IMG_CPB * 6 * KCH];
+  extern __shared__ __align__(16) float2 stage[];   // [SRC][LDS]: (source, target)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int ek = formula_kind(J);
   const int npt = point_arrays(ek);
-  const int opN = J.op == BF_OP_N;
-  const int64_t row0 = (int64_t)blockIdx.x * TM, M = J.M, K = J.Ktot;
+  const int64_t row0 = (int64_t)blockIdx.x * TM, M = J.M, K = J.Ktot;   // targets, sources
   const int prow = 16 * warp + (lane & 7) + 8 * ((lane >> 4) & 1), kg = (lane >> 3) & 1;
   const int64_t gi = row0 + prow;
   const bool rvalid = gi < M;
   RowCtx R;
   row_ctx(J, ek, gi, rvalid, R);
-  const float* colp = opN ? J.srcF : J.tgtF;
-  const int64_t coln = opN ? J.n : J.m;
+  const float* colp = J.srcF;
+  const int64_t coln = J.n;
   const int64_t c0 = (int64_t)blockIdx.y * IMG_CPB;
-  const int nc = (int)(nchi - c0 < IMG_CPB ? nchi - c0 : IMG_CPB);
+  const int nc = (int)(nchN - c0 < IMG_CPB ? nchN - c0 : IMG_CPB);
   for (int idx = tid; idx < nc * npt * KCH; idx += 256) {
     const int c = idx / (npt * KCH), d = (idx / KCH) % npt, kk = idx % KCH;
     const int64_t gk = (c0 + c) * KCH + kk;
@@ -785,38 +794,62 @@ __global__ void __launch_bounds__(256) entry_image_kernel(const SketchJob J, uin
   __syncthreads();
   const uint32_t pb = smem_u32(pts);
 #pragma unroll 1
-  for (int c = 0; c < nc; ++c) {
-    const int64_t kb = (c0 + c) * KCH;
-    float re[VS], im[VS];
-    const int64_t gk0 = kb + VS * kg;
-    form_row<VS>(ek, R, pb + (uint32_t)(c * 6 * KCH * 4) + 4u * VS * (uint32_t)kg, KCH * 4, rvalid ? gi : row0, gk0,
-                 K, re, im);
-    if (kb + KCH > K || !rvalid) {
+  for (int p0 = 0; p0 < nc; p0 += IMG_PASS) {
+    const int np = nc - p0 < IMG_PASS ? nc - p0 : IMG_PASS;
+#pragma unroll 1
+    for (int c = p0; c < p0 + np; ++c) {
+      const int64_t kb = (c0 + c) * KCH;
+      float re[VS], im[VS];
+      const int64_t gk0 = kb + VS * kg;
+      form_row<VS>(ek, R, pb + (uint32_t)(c * 6 * KCH * 4) + 4u * VS * (uint32_t)kg, KCH * 4, rvalid ? gi : row0,
+                   gk0, K, re, im);
+      if (kb + KCH > K || !rvalid) {
 #pragma unroll
-      for (int j = 0; j < VS; ++j)
-        if (!rvalid || gk0 + j >= K) re[j] = 0.f, im[j] = 0.f;
+        for (int j = 0; j < VS; ++j)
+          if (!rvalid || gk0 + j >= K) re[j] = 0.f, im[j] = 0.f;
+      }
+      uint8_t* tile = imgN + ((int64_t)blockIdx.x * nchN + c0 + c) * IMG_TILE;
+#pragma unroll
+      for (int t = 0; t < VS / 2; ++t)
+        *(float4*)(tile + img_seg(prow, 4 * kg + t)) = make_float4(re[2 * t], im[2 * t], re[2 * t + 1], im[2 * t + 1]);
+      const int sl = (c - p0) * KCH + VS * kg;   // this thread's first source of the pass
+#pragma unroll
+      for (int j = 0; j < VS; ++j) stage[(sl + j) * LDS + prow] = make_float2(re[j], -im[j]);
     }
-    uint8_t* tile = img + ((int64_t)blockIdx.x * nchi + c0 + c) * IMG_TILE;
-#pragma unroll
-    for (int t = 0; t < VS / 2; ++t)
-      *(float4*)(tile + img_seg(prow, 4 * kg + t)) = make_float4(re[2 * t], im[2 * t], re[2 * t + 1], im[2 * t + 1]);
+    __syncthreads();
+    // A^H tiles: row = source, 16 targets per chunk; a thread writes 16-byte
+    // segments (2 targets), 8 consecutive lanes one 128-byte row
+    const int64_t s_first = (c0 + p0) * KCH;   // first source of the pass
+    for (int e = tid; e < np * KCH * (TM / 2); e += 256) {
+      const int q = e & 7, tc = (e >> 3) & 7, sl = e >> 6;   // segment, target chunk of the tile, source
+      const int64_t sg = s_first + sl, kcC = (int64_t)blockIdx.x * (TM / KCH) + tc;
+      if (kcC >= nchC) continue;
+      const int tl = tc * KCH + 2 * q;   // first target of the segment within the tile
+      const float2 a = stage[sl * LDS + tl], b = stage[sl * LDS + tl + 1];
+      uint8_t* tile = imgC + ((sg / TM) * nchC + kcC) * IMG_TILE;
+      *(float4*)(tile + img_seg((int)(sg % TM), q)) = make_float4(a.x, a.y, b.x, b.y);
+    }
+    __syncthreads();
   }
+}
+
+int launch_entry_images(const SketchJob& jn, void* imgN, void* imgC, cudaStream_t s) {
+  if (jn.kind != 1 || jn.op != BF_OP_N || jn.M <= 0 || jn.Ktot <= 0 || !imgN || !imgC)
+    return fail(BF_EINVAL, "entry images of a non-kernel job");
+  const int64_t nchN = entry_image_chunks(jn.Ktot), nchC = entry_image_chunks(jn.M);
+  const dim3 grid((unsigned)((jn.M + TM - 1) / TM), (unsigned)((nchN + IMG_CPB - 1) / IMG_CPB));
+  const size_t smem = (size_t)IMG_PASS * 16 * (TM + 1) * sizeof(float2);
+  BF_CUDA_TRY(cudaFuncSetAttribute(entry_images_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  note_launch();
+  entry_images_kernel<<<grid, 256, smem, s>>>(jn, (uint8_t*)imgN, (uint8_t*)imgC, nchN, nchC);
+  BF_CUDA_TRY(cudaGetLastError());
+  return BF_OK;
 }
 
 size_t entry_image_bytes(int64_t M, int64_t K) {
   return (size_t)((M + TM - 1) / TM) * (size_t)entry_image_chunks(K) * IMG_TILE;
 }
 int64_t entry_image_chunks(int64_t K) { return (K + 15) / 16; }
-
-int launch_entry_image(const SketchJob& j, void* img, cudaStream_t s) {
-  if (j.kind != 1 || j.M <= 0 || j.Ktot <= 0 || !img) return fail(BF_EINVAL, "entry image of a non-kernel job");
-  const int64_t nchi = entry_image_chunks(j.Ktot);
-  const dim3 grid((unsigned)((j.M + TM - 1) / TM), (unsigned)((nchi + IMG_CPB - 1) / IMG_CPB));
-  note_launch();
-  entry_image_kernel<<<grid, 256, 0, s>>>(j, (uint8_t*)img, nchi);
-  BF_CUDA_TRY(cudaGetLastError());
-  return BF_OK;
-}
 
 bool entry_image_fits(const SketchJob& j) {
   constexpr int64_t KCH = 16;
