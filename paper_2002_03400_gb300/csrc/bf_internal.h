@@ -248,6 +248,11 @@ struct StageBases {
 // (only when that kernel is itself a stage launch of the same chain).
 int launch_stage(const StageTask* d_tasks, int ntasks, int maxM, int maxN, int Noverride,
                  const StageBases& bases, int dtype, cudaStream_t s, int variant = -1, bool pdl = false);
+// Peel-stage launch (one CTA per task and 32-128-column block, blocks and
+// inputs staged in shared memory); *launched false when the blocks are too
+// large for it (then use launch_stage).
+int launch_peel(const StageTask* d_tasks, int ntasks, int maxM, int maxN, int maxK, const StageBases& bases,
+                int dtype, cudaStream_t s, bool* launched);
 // Times every stage-kernel variant on each stage of F's apply (direction,
 // dtype, nrhs) and keeps the fastest per stage for that right-hand-side
 // class; returns the tuned apply time in *ms (device, one call).

@@ -111,8 +111,14 @@ int run_tasks(Batch& B, const std::vector<StageTask>& tasks, const StageBases& b
   BF_TRY(d.alloc(&B.mem, tasks.size() * sizeof(StageTask)));
   BF_CUDA_TRY(cudaMemcpyAsync(d.p(), tasks.data(), tasks.size() * sizeof(StageTask),
                               cudaMemcpyHostToDevice, B.s));
-  int mM = 0, mN = 0;
-  for (const auto& t : tasks) mM = std::max(mM, t.M), mN = std::max(mN, t.N);
+  int mM = 0, mN = 0, mK = 0;
+  for (const auto& t : tasks) {
+    mM = std::max(mM, t.M), mN = std::max(mN, t.N);
+    for (int q = 0; q < t.nterms; ++q) mK = std::max(mK, t.t[q].K);
+  }
+  bool done = false;
+  BF_TRY(launch_peel((const StageTask*)d.p(), (int)tasks.size(), mM, mN, mK, bases, B.dt, B.s, &done));
+  if (done) return BF_OK;
   // per-task N in 32-column slices: the first peel stages of a level carry
   // k 2^(l-j) columns per block
   return launch_stage((const StageTask*)d.p(), (int)tasks.size(), mM, mN, -mN, bases, B.dt, B.s);

@@ -347,6 +347,102 @@ stage_block_kernel(const StageTask* __restrict__ tasks, int ntasks, StageBases b
 
 // Untuned choice: the many-warp variant for up to 16 complex64 columns, the
 // whole-block variant otherwise (and for per-task column counts: peeling).
+// Peel stages of Alg. 2's W and R steps (Sec. 4.2-4.3): a few thousand small
+// products out (M x N) = sum_t A_t (M x K_t) in_t (K_t x N) with M, K of a
+// block's rank and N up to k 2^(l-j) columns.  One CTA per (task, block of
+// CB columns): the factor blocks A_t and the input block go to shared memory
+// with coalesced loads (column-major inputs along K, row-major along N), the
+// outputs are formed from shared memory and stored along the output's
+// contiguous dimension.  Terms in order, K ascending (the stage kernels'
+// order of the sum).
+template <typename R>
+__global__ void __launch_bounds__(256) peel_kernel(const StageTask* __restrict__ tasks, StageBases bases, int CB,
+                                                   int MM, int KM) {
+  using V = typename Cx<R>::V;
+  extern __shared__ __align__(16) uint8_t peel_smem[];
+  const StageTask& tk = tasks[blockIdx.x];
+  const int M = tk.M, N = tk.N, nterms = tk.nterms, tid = threadIdx.x;
+  const int cb0 = blockIdx.y * CB;
+  if (cb0 >= N) return;
+  const int nc = N - cb0 < CB ? N - cb0 : CB;
+  V* sA = (V*)peel_smem;               // [term][k][i], KM x MM each
+  V* sX = sA + 2 * KM * MM;            // [term][k][c], KM x CB each
+  for (int t = 0; t < nterms; ++t) {
+    const StageTerm& T = tk.t[t];
+    const V* __restrict__ mat = (const V*)T.mat;
+    const int K = T.K, ldm = T.ldm;
+    V* a = sA + t * KM * MM;
+    if (T.conjT) {   // stored K x M: A(i, k) = conj(mat[k + i ldm])
+      for (int e = tid; e < K * M; e += blockDim.x) {
+        const int k = e % K, i = e / K;
+        V v = mat[k + (int64_t)i * ldm];
+        v.y = -v.y;
+        a[k * MM + i] = v;
+      }
+    } else {         // stored M x K: A(i, k) = mat[i + k ldm]
+      for (int e = tid; e < K * M; e += blockDim.x) {
+        const int i = e % M, k = e / M;
+        a[k * MM + i] = mat[i + (int64_t)k * ldm];
+      }
+    }
+    const Strides si = strides(T.in_off, T.ldi, N);
+    const V* __restrict__ in = (const V*)bases.p[T.in_base] + si.off;
+    V* x = sX + t * KM * CB;
+    if (si.rs == 1) {   // column-major: K contiguous per column
+      for (int e = tid; e < K * nc; e += blockDim.x) {
+        const int k = e % K, c = e / K;
+        x[k * CB + c] = in[k + (int64_t)(cb0 + c) * si.cs];
+      }
+    } else {            // row-major: columns contiguous per row
+      for (int e = tid; e < K * nc; e += blockDim.x) {
+        const int c = e % nc, k = e / nc;
+        x[k * CB + c] = in[(int64_t)k * si.rs + (cb0 + c) * si.cs];
+      }
+    }
+  }
+  __syncthreads();
+  const Strides so = strides(tk.out_off, tk.ldo, N);
+  V* __restrict__ out = (V*)bases.p[tk.out_base] + so.off;
+  const bool colmajor = so.rs == 1;
+  for (int e = tid; e < M * nc; e += blockDim.x) {
+    const int i = colmajor ? e % M : e / nc, c = colmajor ? e / M : e % nc;
+    V acc = Cx<R>::make(0, 0);
+    for (int t = 0; t < nterms; ++t) {
+      const int K = tk.t[t].K;
+      const V* a = sA + t * KM * MM + i;
+      const V* x = sX + t * KM * CB + c;
+      for (int k = 0; k < K; ++k) cmac(acc, a[k * MM], x[k * CB]);
+    }
+    out[(int64_t)i * so.rs + (int64_t)(cb0 + c) * so.cs] = acc;
+  }
+}
+
+int launch_peel(const StageTask* d_tasks, int ntasks, int maxM, int maxN, int maxK, const StageBases& bases,
+                int dtype, cudaStream_t s, bool* launched) {
+  *launched = false;
+  if (ntasks <= 0 || maxM <= 0 || maxN <= 0) {
+    *launched = true;
+    return BF_OK;
+  }
+  const size_t vs = dtype == BF_C128 ? sizeof(double2) : sizeof(float2);
+  int CB = 128;
+  auto bytes = [&](int cb) { return (size_t)2 * maxK * (maxM + cb) * vs; };
+  while (CB > 32 && bytes(CB) > 64 * 1024) CB /= 2;
+  if (bytes(CB) > 96 * 1024) return BF_OK;   // very large blocks: the stage kernels
+  const dim3 grid((unsigned)ntasks, (unsigned)((maxN + CB - 1) / CB));
+  note_launch();
+  if (dtype == BF_C128) {
+    BF_CUDA_TRY(cudaFuncSetAttribute(peel_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes(CB)));
+    peel_kernel<double><<<grid, 256, bytes(CB), s>>>(d_tasks, bases, CB, maxM, maxK);
+  } else {
+    BF_CUDA_TRY(cudaFuncSetAttribute(peel_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes(CB)));
+    peel_kernel<float><<<grid, 256, bytes(CB), s>>>(d_tasks, bases, CB, maxM, maxK);
+  }
+  BF_CUDA_TRY(cudaGetLastError());
+  *launched = true;
+  return BF_OK;
+}
+
 int stage_variant_default(int nrhs, int dtype) { return dtype == BF_C64 && nrhs > 0 && nrhs <= 16 ? 0 : 2; }
 
 int launch_stage(const StageTask* d_tasks, int ntasks, int maxM, int maxN, int Noverride,
