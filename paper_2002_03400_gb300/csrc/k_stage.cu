@@ -360,8 +360,11 @@ __global__ void __launch_bounds__(256) peel_kernel(const StageTask* __restrict__
                                                    int MM, int KM) {
   using V = typename Cx<R>::V;
   extern __shared__ __align__(16) uint8_t peel_smem[];
-  const StageTask& tk = tasks[blockIdx.x];
-  const int M = tk.M, N = tk.N, nterms = tk.nterms, tid = threadIdx.x;
+  __shared__ StageTask tk;   // the task's descriptor, read once
+  const int tid = threadIdx.x;
+  if (tid == 0) tk = tasks[blockIdx.x];
+  __syncthreads();
+  const int M = tk.M, N = tk.N, nterms = tk.nterms;
   const int cb0 = blockIdx.y * CB;
   if (cb0 >= N) return;
   const int nc = N - cb0 < CB ? N - cb0 : CB;
@@ -404,11 +407,12 @@ __global__ void __launch_bounds__(256) peel_kernel(const StageTask* __restrict__
   const Strides so = strides(tk.out_off, tk.ldo, N);
   V* __restrict__ out = (V*)bases.p[tk.out_base] + so.off;
   const bool colmajor = so.rs == 1;
+  const int K0 = tk.t[0].K, K1 = nterms > 1 ? tk.t[1].K : 0;
   for (int e = tid; e < M * nc; e += blockDim.x) {
     const int i = colmajor ? e % M : e / nc, c = colmajor ? e / M : e % nc;
     V acc = Cx<R>::make(0, 0);
     for (int t = 0; t < nterms; ++t) {
-      const int K = tk.t[t].K;
+      const int K = t == 0 ? K0 : K1;
       const V* a = sA + t * KM * MM + i;
       const V* x = sX + t * KM * CB + c;
       for (int k = 0; k < K; ++k) cmac(acc, a[k * MM], x[k * CB]);
