@@ -5,6 +5,7 @@
 #include <cmath>
 #include <atomic>
 #include <cstring>
+#include <map>
 #include <numeric>
 
 #include "bf_internal.h"
@@ -36,6 +37,74 @@ static void keep_pool(cudaStream_t s) {
   }
   done.fetch_or(1ull << dev);
   (void)s;
+}
+
+// ---- host-to-device uploads of task lists through pinned staging ----
+// A host vector copied with cudaMemcpyAsync from pageable memory may make the
+// driver wait for the stream to drain before staging it, which stalls the
+// host behind the kernels already queued (and leaves the GPU idle while the
+// host then enqueues the next ones).  Uploads go through a per-thread,
+// per-device ring of pinned slots instead; a slot is reused once the copy
+// that read it has completed (an event per slot).
+namespace {
+struct PinnedRing {
+  static constexpr int SLOTS = 32;
+  static constexpr size_t SLOT = 256 * 1024;
+  char* buf = nullptr;
+  cudaEvent_t ev[SLOTS] = {};
+  bool used[SLOTS] = {};
+  int next = 0;
+  int state = 0;   // 0: not set up, 1: ready, -1: unavailable (pageable copies)
+  ~PinnedRing() {
+    if (state != 1) return;
+    for (int i = 0; i < SLOTS; ++i) cudaEventDestroy(ev[i]);
+    cudaFreeHost(buf);
+  }
+  bool ready() {
+    if (state == 0) {
+      state = -1;
+      if (cudaMallocHost(&buf, SLOTS * SLOT) != cudaSuccess) {
+        buf = nullptr;
+        cudaGetLastError();
+        return false;
+      }
+      for (int i = 0; i < SLOTS; ++i)
+        if (cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming) != cudaSuccess) {
+          for (int j = 0; j < i; ++j) cudaEventDestroy(ev[j]);
+          cudaFreeHost(buf);
+          buf = nullptr;
+          cudaGetLastError();
+          return false;
+        }
+      state = 1;
+    }
+    return state == 1;
+  }
+};
+thread_local std::map<int, PinnedRing> t_rings;   // by device
+}  // namespace
+
+int upload_async(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) return BF_OK;
+  int dev = 0;
+  BF_CUDA_TRY(cudaGetDevice(&dev));
+  PinnedRing& R = t_rings[dev];
+  if (!R.ready()) {
+    BF_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s));
+    return BF_OK;
+  }
+  for (size_t off = 0; off < bytes; off += PinnedRing::SLOT) {
+    const size_t n = std::min(PinnedRing::SLOT, bytes - off);
+    const int i = R.next;
+    R.next = (R.next + 1) % PinnedRing::SLOTS;
+    if (R.used[i]) BF_CUDA_TRY(cudaEventSynchronize(R.ev[i]));
+    char* slot = R.buf + (size_t)i * PinnedRing::SLOT;
+    std::memcpy(slot, (const char*)src + off, n);
+    BF_CUDA_TRY(cudaMemcpyAsync((char*)dst + off, slot, n, cudaMemcpyHostToDevice, s));
+    BF_CUDA_TRY(cudaEventRecord(R.ev[i], s));
+    R.used[i] = true;
+  }
+  return BF_OK;
 }
 
 int dev_alloc(MemTracker* mt, void** p, size_t bytes, cudaStream_t s) {

@@ -43,6 +43,10 @@ struct MemTracker {
   size_t cap = 0, used = 0, peak = 0;
 };
 int dev_alloc(MemTracker* mt, void** p, size_t bytes, cudaStream_t s);
+// host -> device copy of a host buffer (e.g. a task list) that returns at
+// once: staged through pinned memory, ordered on s; src may be reused after
+// the call returns
+int upload_async(void* dst, const void* src, size_t bytes, cudaStream_t s);
 void dev_free(MemTracker* mt, void* p, size_t bytes, cudaStream_t s);
 
 struct DevBuf {

@@ -109,8 +109,7 @@ int run_tasks(Batch& B, const std::vector<StageTask>& tasks, const StageBases& b
   if (tasks.empty()) return BF_OK;
   Scratch d(B.s);
   BF_TRY(d.alloc(&B.mem, tasks.size() * sizeof(StageTask)));
-  BF_CUDA_TRY(cudaMemcpyAsync(d.p(), tasks.data(), tasks.size() * sizeof(StageTask),
-                              cudaMemcpyHostToDevice, B.s));
+  BF_TRY(upload_async(d.p(), tasks.data(), tasks.size() * sizeof(StageTask), B.s));
   int mM = 0, mN = 0, mK = 0;
   for (const auto& t : tasks) {
     mM = std::max(mM, t.M), mN = std::max(mN, t.N);
@@ -289,7 +288,7 @@ int qr_all(Batch& B, std::vector<QRJob>& jobs) {
   const size_t wbytes = qr_workspace_bytes(nt, maxS, maxK, B.dt, fp64);
   Scratch d(B.s), w(B.s);
   BF_TRY(d.alloc(&B.mem, nt * sizeof(QRTask) + nt * sizeof(int32_t)));
-  BF_CUDA_TRY(cudaMemcpyAsync(d.p(), tasks.data(), nt * sizeof(QRTask), cudaMemcpyHostToDevice, B.s));
+  BF_TRY(upload_async(d.p(), tasks.data(), nt * sizeof(QRTask), B.s));
   int32_t* d_r = (int32_t*)(d.p() + nt * sizeof(QRTask));
   if (wbytes) BF_TRY(w.alloc(&B.mem, wbytes));
   BF_TRY(launch_qr((const QRTask*)d.p(), nt, maxS, maxK, B.dt, fp64, d_r, w.p(), wbytes, B.s));
@@ -712,7 +711,7 @@ int r_phase(Batch& B, int t) {
   }
   Scratch d(B.s);
   BF_TRY(d.alloc(&B.mem, lt.size() * sizeof(LSQTask)));
-  BF_CUDA_TRY(cudaMemcpyAsync(d.p(), lt.data(), lt.size() * sizeof(LSQTask), cudaMemcpyHostToDevice, B.s));
+  BF_TRY(upload_async(d.p(), lt.data(), lt.size() * sizeof(LSQTask), B.s));
   BF_TRY(launch_lsq((const LSQTask*)d.p(), (int)lt.size(), maxS, maxK, maxR, B.dt, B.s));
   for (OpState* o : ctr) BF_TRY(make32(B, *o, o->F->st[o->F->stage_B()]));
   BF_CUDA_TRY(cudaStreamSynchronize(B.s));

@@ -202,8 +202,7 @@ int launch_sketch_jobs_simt(const std::vector<SketchJob>& jobs, int dtype, MemTr
   DevBuf d;
   BF_TRY(d.alloc(mt, jb + tb, s));
   int rc = BF_OK;
-  if (cudaMemcpyAsync(d.p, jobs.data(), jb, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemcpyAsync((char*)d.p + jb, tiles.data(), tb, cudaMemcpyHostToDevice, s) != cudaSuccess)
+  if (upload_async(d.p, jobs.data(), jb, s) != BF_OK || upload_async((char*)d.p + jb, tiles.data(), tb, s) != BF_OK)
     rc = fail(BF_ECUDA, "upload of sketch jobs failed");
   const SketchJob* dj = (const SketchJob*)d.p;
   const SketchTile* dt = (const SketchTile*)((char*)d.p + jb);

@@ -1488,9 +1488,8 @@ int launch_sketch_jobs_tc(const std::vector<SketchJob>& jobs_in, MemTracker* mt,
   if (wsz) BF_TRY(w.alloc(mt, wsz * sizeof(float4), s));
   int rc = BF_OK;
   char* p = (char*)d.p;
-  if (cudaMemcpyAsync(p, jobs.data(), jb, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemcpyAsync(p + jb, tiles.data(), tb, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      (rb && cudaMemcpyAsync(p + jb + tb, regs.data(), rb, cudaMemcpyHostToDevice, s) != cudaSuccess))
+  if (upload_async(p, jobs.data(), jb, s) != BF_OK || upload_async(p + jb, tiles.data(), tb, s) != BF_OK ||
+      (rb && upload_async(p + jb + tb, regs.data(), rb, s) != BF_OK))
     rc = fail(BF_ECUDA, "upload of sketch jobs failed");
   const SketchJob* dj = (const SketchJob*)p;
   const TcTile* dt = (const TcTile*)(p + jb);
