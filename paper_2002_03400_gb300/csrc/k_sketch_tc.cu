@@ -217,15 +217,35 @@ __device__ __forceinline__ bool mbar_try(uint32_t addr, uint32_t parity) {
       : "memory");
   return done != 0;
 }
-// waits for the phase of parity `parity` of the mbarrier at addr; the timer
-// is read only once the phase is found incomplete; false after 1 s
-__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
-  if (mbar_try(addr, parity)) return true;
+// the same, the thread suspended until the phase completes or about `ns`
+// nanoseconds have passed (so a waiting warp takes no issue slots from the
+// warps that share its scheduler)
+__device__ __forceinline__ bool mbar_try_sleep(uint32_t addr, uint32_t parity, uint32_t ns) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(done)
+      : "r"(addr), "r"(parity), "r"(ns)
+      : "memory");
+  return done != 0;
+}
+// the bounded part of a wait, out of line so that the inlined fast path is
+// one try_wait: false after 1 s, or as soon as *abort is set
+__device__ __noinline__ bool mbar_wait_slow(uint32_t addr, uint32_t parity, const volatile int* abort) {
   const uint64_t t0 = now_ns();
   for (;;) {
-    if (mbar_try(addr, parity)) return true;
-    if (now_ns() - t0 > 1000000000ull) return false;
+    if (mbar_try_sleep(addr, parity, 1000000u)) return true;
+    if ((abort && *abort) || now_ns() - t0 > 1000000000ull) return false;
   }
+}
+// waits for the phase of parity `parity` of the mbarrier at addr; the timer
+// is read only once the phase is found incomplete; false after 1 s (or once
+// *abort is set)
+__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity, const volatile int* abort = nullptr) {
+  return mbar_try(addr, parity) || mbar_wait_slow(addr, parity, abort);
+}
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -897,23 +917,33 @@ __global__ void __launch_bounds__(256) bimage_kernel(const SketchJob* __restrict
 }
 
 namespace {
-// Image-fed tile shape: one CTA per SM, 576 threads -- two groups of 8
+// tensor-memory columns of a chunk's A parts (3 parts x 2 K steps x 8) and
+// whether two such slots fit beside the accumulators of an NR-column tile
+constexpr int IMG_ACOLS = 48;
+__host__ __device__ constexpr bool img_tmem_a(int nr) { return 8 * nr + 2 * IMG_ACOLS <= 512; }
+
+// Image-fed tile shape: one CTA per SM, 608 threads -- two groups of 8
 // producer warps (even and odd chunks: bf16 split of the A tile; group 0
-// also drains the accumulators and writes the epilogue), an MMA warp and a
-// loader warp, synchronised by mbarriers only.  SF slots hold an image tile
-// and the chunk's B operand (bf16 parts, formed once per launch), S slots
-// the bf16 A parts.
+// also drains the accumulators and writes the epilogue), an MMA warp, a
+// tile loader warp and a B loader warp, synchronised by mbarriers only.
+// SF slots hold image tiles (freed once the producers have read them), SB
+// slots the chunks' B operands (bf16 parts formed once per launch, freed by
+// the MMAs), S slots the bf16 A parts (in tensor memory where they fit,
+// else in shared memory).
 template <int NR>
 struct ICfg {
   using C = Cfg<NR, 3>;
   static constexpr int KP = NR / 2;
-  static constexpr uint32_t F_SLOT = (IMG_TILE + C::B_BUF + 127) / 128 * 128;   // image tile + B operand
-  static constexpr uint32_t O_SLOT = C::A_BUF;                                    // bf16 A parts
-  static constexpr int SF = 4;
+  static constexpr bool TA = img_tmem_a(NR);                            // A parts in tensor memory
+  static constexpr uint32_t F_SLOT = IMG_TILE;                          // image tile
+  static constexpr uint32_t B_SLOT = (C::B_BUF + 127) / 128 * 128;      // B operand (bf16 parts)
+  static constexpr uint32_t O_SLOT = TA ? 0 : C::A_BUF;                 // bf16 A parts (shared memory)
+  static constexpr int SF = TA ? 8 : 4, SB = 4;
   static constexpr uint32_t LIMIT = 220 * 1024;
-  static constexpr uint32_t total(int s) { return SF * F_SLOT + s * O_SLOT; }
-  static constexpr int S = total(4) <= LIMIT ? 4 : total(3) <= LIMIT ? 3 : 2;
-  static constexpr uint32_t F0 = 0, O0 = SF * F_SLOT, TOTAL = O0 + S * O_SLOT;
+  static constexpr uint32_t total(int s) { return SF * F_SLOT + SB * B_SLOT + s * O_SLOT; }
+  static constexpr int S = TA ? 2 : total(4) <= LIMIT ? 4 : 2;
+  static constexpr uint32_t F0 = 0, B0 = SF * F_SLOT, O0 = B0 + SB * B_SLOT, TOTAL = O0 + S * O_SLOT;
+  static constexpr uint32_t ACOL = 8 * NR;                              // first A column in tensor memory
   static_assert(TOTAL <= LIMIT && C::PT == 1 && C::VS == 8, "image tile: shared memory, one 8-column group per thread");
   // a producer group waits on a slot's mbarrier by phase parity; with an
   // odd slot count, consecutive uses of a slot alternate between the two
@@ -924,8 +954,8 @@ struct ICfg {
   static_assert(C::DR == 4, "group 0 drains at the third chunk of the next group");
 };
 constexpr int IPG = 2;                                // producer groups
-constexpr int ITHREADS = 32 * (IPG * NWARP + 2);
-constexpr int IMMA_WARP = IPG * NWARP, ILOAD_WARP = IPG * NWARP + 1;
+constexpr int ITHREADS = 32 * (IPG * NWARP + 3);
+constexpr int IMMA_WARP = IPG * NWARP, ILOAD_WARP = IPG * NWARP + 1, IBLOAD_WARP = IPG * NWARP + 2;
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
@@ -938,6 +968,19 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
                : "r"(taddr));
 }
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, uint4 v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr), "r"(v.x), "r"(v.y),
+               "r"(v.z), "r"(v.w)
+               : "memory");
+}
+// kind::f16 MMA with A in tensor memory (K-major, M = 128 lanes), B in shared memory
+__device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}" ::"r"(
+          d),
+      "r"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
 __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
   asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(r[0]),
                "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
@@ -946,8 +989,16 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8])
 // Tensor memory of the image kernel: two accumulator sets (alternate
 // groups of DR chunks) of three NR-column blocks each -- main (a0 b0),
 // c1 (a0 b1 + a1 b0), c2 (a0 b2 + a1 b1 + a2 b0), adjacent so that one MMA
-// with the B parts stacked along N fills them -- then hi, lo.
-__host__ __device__ constexpr int img_cols(int nr) { return 8 * nr <= 128 ? 128 : 8 * nr <= 256 ? 256 : 512; }
+// with the B parts stacked along N fills them -- then hi, lo, and where
+// they fit two A slots of IMG_ACOLS columns: a chunk's three bf16 parts x
+// two K steps, each K step 8 columns (row i in lane i, 16 K values packed
+// in pairs, the even one in the low half).  With A in tensor memory the
+// MMAs read only B from shared memory.
+__host__ __device__ constexpr int img_cols(int nr) {
+  return 8 * nr + (img_tmem_a(nr) ? 2 * IMG_ACOLS : 0) <= 128   ? 128
+         : 8 * nr + (img_tmem_a(nr) ? 2 * IMG_ACOLS : 0) <= 256 ? 256
+                                                                 : 512;
+}
 // hi, lo += the set at column `set` (TwoSum of main into hi; the error and
 // the correction sums into lo), in 8-column slices
 template <int NR>
@@ -980,19 +1031,20 @@ __device__ __forceinline__ void drain_set(uint32_t tq, int sub, uint32_t set) {
 // costs about the same at N = 48 as at N = 144) and the correction sums
 // drained with each group -- equal to sketch_tc_kernel's results up to FP32
 // rounding order.  Per chunk c of a CTA's K range,
-//   loader  -- waits for F slot c % SF to be free (its tile read by the
-//              producers, its B operand by the MMAs of chunk c - SF) and
-//              bulk-copies the image tile and the chunk's B operand into it,
-//              completing on fullF;
+//   tile loader -- waits for tile slot c % SF to be free (read by the
+//              producers of chunk c - SF) and bulk-copies the image tile
+//              into it, completing on fullF;
+//   B loader -- waits for B slot c % SB (read by the MMAs of chunk c - SB)
+//              and bulk-copies the chunk's B operand into it (fullB);
 //   producer group c % 2 -- waits for fullF and for A slot c % S (its MMAs
 //              of chunk c - S done), reads the tile rows, releases the tile,
 //              splits the entries into bf16 parts, writes A, fences it to
 //              the async proxy and arrives on fullO; group 0, before the third chunk of group g + 1 (4
 //              chunks a group), drains group g's accumulator set into
 //              (hi, lo);
-//   MMA warp -- waits for fullO and fullF (and, at a group's first chunk,
+//   MMA warp -- waits for fullO and fullB (and, at a group's first chunk,
 //              for the drain of the group two back), issues the chunk's MMAs
-//              and commits them to emptyO and emptyF (and to accF at a
+//              and commits them to emptyO and emptyB (and to accF at a
 //              group's end).
 // Every wait is bounded (1 s); a role that gives up raises the abort flag
 // and the device status, and the others stop at their next wait.
@@ -1007,7 +1059,7 @@ sketch_img_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ SketchJob J;
   __shared__ TcTile T;
-  __shared__ __align__(8) uint64_t bars[2 * SF + 2 * S + 4];
+  __shared__ __align__(8) uint64_t bars[2 * SF + 2 * S + 4 + 2 * I::SB];
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -1015,13 +1067,17 @@ sketch_img_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__
   // fullF[i] = b0 + 8 i, emptyF[i] = +8 (SF + i), fullO[i] = +8 (2 SF + i),
   // emptyO[i] = +8 (2 SF + S + i), accF[b] = +8 (2 SF + 2 S + b), accE[b] = +8 (2 SF + 2 S + 2 + b)
   const uint32_t fullF = b0, emptyF = b0 + 8u * SF, fullO = b0 + 16u * SF, emptyO = fullO + 8u * S,
-                 accF = emptyO + 8u * S, accE = accF + 16u;
+                 accF = emptyO + 8u * S, accE = accF + 16u, fullB = accE + 16u, emptyB = fullB + 8u * I::SB;
   if (tid == 0) {
     T = tiles[blockIdx.x];
     J = jobs[T.job];
     for (int i = 0; i < SF; ++i) {
       mbar_init(fullF + 8u * i, 1);        // the loader's expect_tx arrive
-      mbar_init(emptyF + 8u * i, NWARP + 1);   // the producer group's warps + the MMA commit (B read)
+      mbar_init(emptyF + 8u * i, NWARP);   // the producer group's warps (tile read)
+    }
+    for (int i = 0; i < I::SB; ++i) {
+      mbar_init(fullB + 8u * i, 1);        // the B loader's expect_tx arrive
+      mbar_init(emptyB + 8u * i, 1);       // the MMA commit (B read)
     }
     for (int i = 0; i < S; ++i) {
       mbar_init(fullO + 8u * i, NWARP);
@@ -1070,7 +1126,6 @@ sketch_img_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__
   if (warp == ILOAD_WARP) {
     // ---------------------------------------------------------------- loader
     const uint8_t* imgp = (const uint8_t*)J.img + ((row0 / TM) * J.img_nch + k0 / KCH) * (int64_t)IMG_TILE;
-    const uint8_t* bimp = (const uint8_t*)J.bimg + (k0 / KCH) * (int64_t)C::B_BUF;
     int c = 0;
     for (; c < nch; ++c) {
       const int sf = c % SF;
@@ -1082,10 +1137,8 @@ sketch_img_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__
         break;
       }
       if (lane == 0) {
-        const uint32_t fb = sb + I::F0 + (uint32_t)sf * I::F_SLOT;
-        mbar_expect_tx(fullF + 8u * sf, IMG_TILE + C::B_BUF);
-        bulk_copy(fb, imgp + (int64_t)c * IMG_TILE, IMG_TILE, fullF + 8u * sf);
-        bulk_copy(fb + IMG_TILE, bimp + (int64_t)c * C::B_BUF, C::B_BUF, fullF + 8u * sf);
+        mbar_expect_tx(fullF + 8u * sf, IMG_TILE);
+        bulk_copy(sb + I::F0 + (uint32_t)sf * I::F_SLOT, imgp + (int64_t)c * IMG_TILE, IMG_TILE, fullF + 8u * sf);
       }
     }
     if (!ok && lane == 0) {
@@ -1096,50 +1149,83 @@ sketch_img_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__
     if (lane == 0)
       for (int q = c - SF < 0 ? 0 : c - SF; q < c; ++q) mbar_wait(fullF + 8u * (q % SF), (uint32_t)((q / SF) & 1));
     __syncwarp();
+  } else if (warp == IBLOAD_WARP) {
+    // -------------------------------------------------------------- B loader
+    if (lane == 0) {
+      const uint8_t* bimp = (const uint8_t*)J.bimg + (k0 / KCH) * (int64_t)C::B_BUF;
+      int c = 0;
+      for (; c < nch; ++c) {
+        const int sbi = c % I::SB;
+        if (*(volatile int*)&abort_flag) break;
+        if (c >= I::SB && !mbar_wait(emptyB + 8u * sbi, (uint32_t)(((c / I::SB) - 1) & 1))) {
+          *(volatile int*)&abort_flag = 1;
+          atomicExch(&g_tc_status, 1);
+          break;
+        }
+        mbar_expect_tx(fullB + 8u * sbi, C::B_BUF);
+        bulk_copy(sb + I::B0 + (uint32_t)sbi * I::B_SLOT, bimp + (int64_t)c * C::B_BUF, C::B_BUF, fullB + 8u * sbi);
+      }
+      for (int q = c - I::SB < 0 ? 0 : c - I::SB; q < c; ++q)   // copies still in flight (bounded)
+        mbar_wait(fullB + 8u * (q % I::SB), (uint32_t)((q / I::SB) & 1));
+    }
+    __syncwarp();
   } else if (warp == IMMA_WARP) {
     // ------------------------------------------------------------- MMA warp
+    // The chunk loop is unrolled over one period of the rings (8 chunks: S,
+    // SB and DR divide it; the accumulator set alternates every DR), so every
+    // slot, barrier and operand address is a compile-time offset and each
+    // phase parity a constant or a bit of the loop counter: the issuing
+    // thread then keeps pace with the tensor pipe (six MMAs, 288 cycles of
+    // M = 128 work per chunk at NR = 48).
     if (lane == 0) {
+      static_assert(8 % S == 0 && 8 % I::SB == 0 && DR == 4, "one unrolled period of the rings");
       constexpr uint32_t idesc = idesc_bf16(NR), idesc2 = idesc_bf16(2 * NR), idesc3 = idesc_bf16(3 * NR);
       constexpr uint64_t pa = C::A_PART >> 4;
+      const uint64_t dA0 = sdesc<KG>(sb + I::O0), dB0 = sdesc<KG>(sb + I::B0);
+      const volatile int* abortp = &abort_flag;
       int issued = -1;
-      for (int c = 0; c < nch; ++c) {
-        const int g = c / DR, s = c % S;
-        if (c % DR == 0 && g >= 2 && !mbar_wait(accE + 8u * (g & 1), (uint32_t)(((g - 2) / 2) & 1))) {
-          ok = false;
-          break;
-        }
-        const int sf = c % SF;
-        if (!mbar_wait(fullO + 8u * s, (uint32_t)((c / S) & 1)) ||
-            !mbar_wait(fullF + 8u * sf, (uint32_t)((c / SF) & 1)) || *(volatile int*)&abort_flag) {
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        const uint32_t aB = sb + I::O0 + (uint32_t)s * I::O_SLOT, bB = sb + I::F0 + (uint32_t)sf * I::F_SLOT + IMG_TILE;
-        const uint64_t dA = sdesc<KG>(aB), dB = sdesc<KG>(bB);
-        // set of this group: [main | c1 | c2]; a0 [b0; b1; b2] -> all three,
-        // a1 [b0; b1] -> c1, c2, a2 b0 -> c2 (the B parts are consecutive
-        // 8-row groups, so stacking them along N is a larger N)
-        const uint32_t tset = tm + (uint32_t)(g & 1) * 3 * NR;
-        const uint32_t carry = (c % DR) != 0 ? 1u : 0u;   // the set restarts with its group
+      for (int c8 = 0; c8 < nch && ok; c8 += 8) {
+        const uint32_t accE_par = (uint32_t)(((c8 >> 3) + 1) & 1);   // phase of the group two back
 #pragma unroll
-        for (int ks = 0; ks < C::KSTEPS; ++ks) {
-          const uint64_t o = (uint64_t)(ks * 2 * CORE) >> 4;
-          mma_step<2>(tset, dA + o, dB + o, idesc3, ks > 0 ? 1u : carry);
-          mma_step<2>(tset + NR, dA + pa + o, dB + o, idesc2, 1u);
-          mma_step<2>(tset + 2 * NR, dA + 2 * pa + o, dB + o, idesc, 1u);
+        for (int u = 0; u < 8; ++u) {
+          const int c = c8 + u;
+          if (c >= nch) break;
+          const int s = u % S, sbi = u % I::SB, set = (u / DR) & 1;
+          if (u % DR == 0 && c >= 2 * DR && !mbar_wait(accE + 8u * set, accE_par, abortp)) {
+            ok = false;
+            break;
+          }
+          if (!mbar_wait(fullO + 8u * s, (uint32_t)((u / S) & 1), abortp) ||
+              !mbar_wait(fullB + 8u * sbi, (uint32_t)((u / I::SB) & 1), abortp)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint64_t dA = dA0 + (uint64_t)((s * I::O_SLOT) >> 4), dB = dB0 + (uint64_t)((sbi * I::B_SLOT) >> 4);
+          const uint32_t aT = tm + I::ACOL + (uint32_t)(s * IMG_ACOLS);   // part p, K step ks: + 16 p + 8 ks
+          // set of this group: [main | c1 | c2]; a0 [b0; b1; b2] -> all three,
+          // a1 [b0; b1] -> c1, c2, a2 b0 -> c2 (the B parts are consecutive
+          // 8-row groups, so stacking them along N is a larger N)
+          const uint32_t tset = tm + (uint32_t)(set * 3 * NR);
+          const uint32_t carry = (u % DR) != 0 ? 1u : 0u;   // the set restarts with its group
+#pragma unroll
+          for (int ks = 0; ks < C::KSTEPS; ++ks) {
+            const uint64_t o = (uint64_t)(ks * 2 * CORE) >> 4;
+            if constexpr (I::TA) {
+              mma_ts(tset, aT + 8 * ks, dB + o, idesc3, ks > 0 ? 1u : carry);
+              mma_ts(tset + NR, aT + 16 + 8 * ks, dB + o, idesc2, 1u);
+              mma_ts(tset + 2 * NR, aT + 32 + 8 * ks, dB + o, idesc, 1u);
+            } else {
+              mma_step<2>(tset, dA + o, dB + o, idesc3, ks > 0 ? 1u : carry);
+              mma_step<2>(tset + NR, dA + pa + o, dB + o, idesc2, 1u);
+              mma_step<2>(tset + 2 * NR, dA + 2 * pa + o, dB + o, idesc, 1u);
+            }
+          }
+          tc_commit(emptyO + 8u * s);
+          tc_commit(emptyB + 8u * sbi);
+          if (u % DR == DR - 1 || c == nch - 1) tc_commit(accF + 8u * set);
+          issued = c;
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         emptyO + 8u * s)
-                     : "memory");
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         emptyF + 8u * sf)
-                     : "memory");
-        if (c % DR == DR - 1 || c == nch - 1)
-          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                           accF + 8u * (g & 1))
-                       : "memory");
-        issued = c;
       }
       if (!ok) {
         *(volatile int*)&abort_flag = 1;
@@ -1150,7 +1236,10 @@ sketch_img_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__
     __syncwarp();
   } else {
     // ------------------------------------------------------------ producers
-    const int prow = 16 * pw + (lane & 7) + 8 * ((lane >> 4) & 1), kg = (lane >> 3) & 1;
+    // with A in tensor memory a warp owns the 32 rows of its lane quarter
+    // (half the chunk's columns each); else 16 rows in core-matrix order
+    const int prow = I::TA ? 32 * quad + lane : 16 * pw + (lane & 7) + 8 * ((lane >> 4) & 1);
+    const int kg = I::TA ? sub : (lane >> 3) & 1;
     const uint32_t a_st = (uint32_t)(prow >> 3) * KG * CORE + (uint32_t)(prow & 7) * 16;
     int next_drain = 0;
     auto drain_group = [&](int g, bool last) -> bool {
@@ -1174,6 +1263,7 @@ sketch_img_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__
         ok = false;
         break;
       }
+      if constexpr (I::TA) tc_fence_after();   // the MMAs that read A slot s are complete
       const uint32_t fb = sb + I::F0 + (uint32_t)sf * I::F_SLOT;
       float re[VS], im[VS];
 #pragma unroll
@@ -1183,17 +1273,30 @@ sketch_img_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(emptyF + 8u * sf);   // this warp is done with the image tile
-      const uint32_t aB = sb + I::O0 + (uint32_t)s * I::O_SLOT;
       uint4 pr[3], pm[3];
       split_row<3, VS>(re, pr);
       split_row<3, VS>(im, pm);
-      const uint32_t ar = aB + a_st + (uint32_t)kg * CORE, ai = ar + (uint32_t)G * CORE;
+      if constexpr (I::TA) {
+        // part q: real parts at K step 0, imaginary at K step 1; this
+        // thread's 8 values are columns 4 kg .. 4 kg + 3 of each
+        const uint32_t ta = tq + I::ACOL + (uint32_t)s * IMG_ACOLS + 4u * kg;
 #pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        st_shared_v4(ar + q * C::A_PART, pr[q]);
-        st_shared_v4(ai + q * C::A_PART, pm[q]);
+        for (int q = 0; q < 3; ++q) {
+          tmem_st4(ta + 16 * q, pr[q]);
+          tmem_st4(ta + 16 * q + 8, pm[q]);
+        }
+        tmem_wait_st();
+        tc_fence_before();
+      } else {
+        const uint32_t aB = sb + I::O0 + (uint32_t)s * I::O_SLOT;
+        const uint32_t ar = aB + a_st + (uint32_t)kg * CORE, ai = ar + (uint32_t)G * CORE;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          st_shared_v4(ar + q * C::A_PART, pr[q]);
+          st_shared_v4(ai + q * C::A_PART, pm[q]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(fullO + 8u * s);
     }
