@@ -306,6 +306,26 @@ __device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_
                "l"(src), "r"(bytes), "r"(bar)
                : "memory");
 }
+// the same with an L2 eviction-priority policy (from l2_policy)
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar, uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(bar), "l"(policy)
+      : "memory");
+}
+// L2 policies: evict_first for data read once (entry images), evict_last
+// for data every row tile re-reads (the per-launch B operand)
+__device__ __forceinline__ uint64_t l2_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t l2_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
 // arrive on bar, adding `bytes` to its expected transaction count
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
@@ -922,10 +942,11 @@ namespace {
 constexpr int IMG_ACOLS = 48;
 __host__ __device__ constexpr bool img_tmem_a(int nr) { return 8 * nr + 2 * IMG_ACOLS <= 512; }
 
-// Image-fed tile shape: one CTA per SM, 608 threads -- two groups of 8
-// producer warps (even and odd chunks: bf16 split of the A tile; group 0
-// also drains the accumulators and writes the epilogue), an MMA warp, a
-// tile loader warp and a B loader warp, synchronised by mbarriers only.
+// Image-fed tile shape: one CTA per SM, 736 threads -- two groups of 8
+// producer warps (even and odd chunks: bf16 split of the A tile), an MMA
+// warp, a tile loader warp, a B loader warp and four drain warps (the
+// accumulator sets into (hi, lo), then the epilogue), synchronised by
+// mbarriers only.
 // SF slots hold image tiles (freed once the producers have read them), SB
 // slots the chunks' B operands (bf16 parts formed once per launch, freed by
 // the MMAs), S slots the bf16 A parts (in tensor memory where they fit,
@@ -938,7 +959,7 @@ struct ICfg {
   static constexpr uint32_t F_SLOT = IMG_TILE;                          // image tile
   static constexpr uint32_t B_SLOT = (C::B_BUF + 127) / 128 * 128;      // B operand (bf16 parts)
   static constexpr uint32_t O_SLOT = TA ? 0 : C::A_BUF;                 // bf16 A parts (shared memory)
-  static constexpr int SF = TA ? 8 : 4, SB = 4;
+  static constexpr int SF = TA ? 8 : 4, SB = TA ? 8 : 4;
   static constexpr uint32_t LIMIT = 220 * 1024;
   static constexpr uint32_t total(int s) { return SF * F_SLOT + SB * B_SLOT + s * O_SLOT; }
   static constexpr int S = TA ? 2 : total(4) <= LIMIT ? 4 : 2;
@@ -951,11 +972,13 @@ struct ICfg {
   // early.  Slot counts that are multiples of the group count make every
   // group observe every phase of the slots it uses.
   static_assert(S % 2 == 0 && SF % 2 == 0, "slot counts must be multiples of the producer groups");
-  static_assert(C::DR == 4, "group 0 drains at the third chunk of the next group");
+  static_assert(C::DR == 4, "accumulator sets alternate every 4 chunks");
 };
 constexpr int IPG = 2;                                // producer groups
-constexpr int ITHREADS = 32 * (IPG * NWARP + 3);
-constexpr int IMMA_WARP = IPG * NWARP, ILOAD_WARP = IPG * NWARP + 1, IBLOAD_WARP = IPG * NWARP + 2;
+constexpr int IDRAINW = 4;                            // drain warps (one per lane quarter)
+constexpr int ITHREADS = 32 * (IPG * NWARP + 3 + IDRAINW);
+constexpr int IMMA_WARP = IPG * NWARP, ILOAD_WARP = IPG * NWARP + 1, IBLOAD_WARP = IPG * NWARP + 2,
+              IDRAIN_WARP = IPG * NWARP + 3;
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
@@ -1002,9 +1025,9 @@ __host__ __device__ constexpr int img_cols(int nr) {
 // hi, lo += the set at column `set` (TwoSum of main into hi; the error and
 // the correction sums into lo), in 8-column slices
 template <int NR>
-__device__ __forceinline__ void drain_set(uint32_t tq, int sub, uint32_t set) {
+__device__ __forceinline__ void drain_set(uint32_t tq, int first, int step, uint32_t set) {
 #pragma unroll 1
-  for (int s = sub; s < NR / 8; s += NWARP / 4) {
+  for (int s = first; s < NR / 8; s += step) {
     uint32_t d[8], c1[8], c2[8], h[8], l[8];
     tmem_ld8(tq + set + s * 8, d);
     tmem_ld8(tq + set + NR + s * 8, c1);
@@ -1027,10 +1050,11 @@ __device__ __forceinline__ void drain_set(uint32_t tq, int sub, uint32_t set) {
 
 // Sketch product of image jobs: the same tiles, chunks, bf16 parts and six
 // products as sketch_tc_kernel, with the products of one A part issued as
-// one MMA over the stacked B parts (3 MMAs per 16 K instead of 6: an MMA
-// costs about the same at N = 48 as at N = 144) and the correction sums
-// drained with each group -- equal to sketch_tc_kernel's results up to FP32
-// rounding order.  Per chunk c of a CTA's K range,
+// one MMA over the stacked B parts (3 MMAs per 16 K instead of 6: one
+// thread issues an MMA no faster than every ~50 cycles, while M = 128, K =
+// 16 costs the tensor pipe N/2 cycles) and the correction sums drained with
+// each group -- equal to sketch_tc_kernel's results up to FP32 rounding
+// order.  Per chunk c of a CTA's K range,
 //   tile loader -- waits for tile slot c % SF to be free (read by the
 //              producers of chunk c - SF) and bulk-copies the image tile
 //              into it, completing on fullF;
@@ -1038,10 +1062,12 @@ __device__ __forceinline__ void drain_set(uint32_t tq, int sub, uint32_t set) {
 //              and bulk-copies the chunk's B operand into it (fullB);
 //   producer group c % 2 -- waits for fullF and for A slot c % S (its MMAs
 //              of chunk c - S done), reads the tile rows, releases the tile,
-//              splits the entries into bf16 parts, writes A, fences it to
-//              the async proxy and arrives on fullO; group 0, before the third chunk of group g + 1 (4
-//              chunks a group), drains group g's accumulator set into
-//              (hi, lo);
+//              splits the entries into bf16 parts, writes A (tensor memory,
+//              or shared memory fenced to the async proxy) and arrives on
+//              fullO;
+//   drain warps -- once the MMAs of group g (4 chunks) are complete (accF),
+//              move its accumulator set into (hi, lo) and release it
+//              (accE); after the last group, write the rows out;
 //   MMA warp -- waits for fullO and fullB (and, at a group's first chunk,
 //              for the drain of the group two back), issues the chunk's MMAs
 //              and commits them to emptyO and emptyB (and to accF at a
@@ -1085,7 +1111,7 @@ sketch_img_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(accF + 8u * b, 1);
-      mbar_init(accE + 8u * b, NWARP);
+      mbar_init(accE + 8u * b, IDRAINW);
     }
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -1126,6 +1152,7 @@ sketch_img_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__
   if (warp == ILOAD_WARP) {
     // ---------------------------------------------------------------- loader
     const uint8_t* imgp = (const uint8_t*)J.img + ((row0 / TM) * J.img_nch + k0 / KCH) * (int64_t)IMG_TILE;
+    const uint64_t pol = l2_evict_first();
     int c = 0;
     for (; c < nch; ++c) {
       const int sf = c % SF;
@@ -1138,7 +1165,8 @@ sketch_img_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__
       }
       if (lane == 0) {
         mbar_expect_tx(fullF + 8u * sf, IMG_TILE);
-        bulk_copy(sb + I::F0 + (uint32_t)sf * I::F_SLOT, imgp + (int64_t)c * IMG_TILE, IMG_TILE, fullF + 8u * sf);
+        bulk_copy(sb + I::F0 + (uint32_t)sf * I::F_SLOT, imgp + (int64_t)c * IMG_TILE, IMG_TILE, fullF + 8u * sf,
+                  pol);
       }
     }
     if (!ok && lane == 0) {
@@ -1153,6 +1181,7 @@ sketch_img_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__
     // -------------------------------------------------------------- B loader
     if (lane == 0) {
       const uint8_t* bimp = (const uint8_t*)J.bimg + (k0 / KCH) * (int64_t)C::B_BUF;
+      const uint64_t pol = l2_evict_last();
       int c = 0;
       for (; c < nch; ++c) {
         const int sbi = c % I::SB;
@@ -1163,7 +1192,8 @@ sketch_img_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__
           break;
         }
         mbar_expect_tx(fullB + 8u * sbi, C::B_BUF);
-        bulk_copy(sb + I::B0 + (uint32_t)sbi * I::B_SLOT, bimp + (int64_t)c * C::B_BUF, C::B_BUF, fullB + 8u * sbi);
+        bulk_copy(sb + I::B0 + (uint32_t)sbi * I::B_SLOT, bimp + (int64_t)c * C::B_BUF, C::B_BUF, fullB + 8u * sbi,
+                  pol);
       }
       for (int q = c - I::SB < 0 ? 0 : c - I::SB; q < c; ++q)   // copies still in flight (bounded)
         mbar_wait(fullB + 8u * (q % I::SB), (uint32_t)((q / I::SB) & 1));
@@ -1195,8 +1225,8 @@ sketch_img_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__
             ok = false;
             break;
           }
-          if (!mbar_wait(fullO + 8u * s, (uint32_t)((u / S) & 1), abortp) ||
-              !mbar_wait(fullB + 8u * sbi, (uint32_t)((u / I::SB) & 1), abortp)) {
+          if (!mbar_wait(fullO + 8u * s, (uint32_t)((c / S) & 1), abortp) ||
+              !mbar_wait(fullB + 8u * sbi, (uint32_t)((c / I::SB) & 1), abortp)) {
             ok = false;
             break;
           }
@@ -1234,6 +1264,56 @@ sketch_img_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__
       }
     }
     __syncwarp();
+  } else if (warp >= IDRAIN_WARP) {
+    // ------------------------------------------------------------- drainers
+    // each warp owns the 32 rows of its lane quarter: once the MMAs of group
+    // g are complete it moves set g & 1 into (hi, lo) and releases the set;
+    // after the last group it writes its rows out
+    const volatile int* abortp = &abort_flag;
+    for (int g = 0; g < ngroups && ok; ++g) {
+      if (!mbar_wait(accF + 8u * (g & 1), (uint32_t)((g / 2) & 1), abortp)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      drain_set<NR>(tq, 0, 1, (uint32_t)(g & 1) * 3 * NR);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(accE + 8u * (g & 1));
+    }
+    if (ok && nch > 0) {
+      // epilogue: (hi, lo) pairs of this warp's lanes to Y or to the split workspace
+      const int64_t row = row0 + quad * 32 + lane;
+#pragma unroll 1
+      for (int s = 0; s < (KP + 7) / 8; ++s) {
+        uint32_t hr[8], lr[8], hm[8], lm[8];
+        const int c0 = s * 8;
+        tmem_ld8(tq + 6 * NR + c0, hr);
+        tmem_ld8(tq + 7 * NR + c0, lr);
+        tmem_ld8(tq + 6 * NR + KP + c0, hm);
+        tmem_ld8(tq + 7 * NR + KP + c0, lm);
+        tmem_wait_ld();
+        if (row < M) {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int col = c0 + i;
+            if (col >= kcols || col >= KP) continue;
+            if (T.ws < 0) {
+              float2* __restrict__ Y = (float2*)J.Y;
+              Y[row + (T.group * ygs + col) * J.ldy] = make_float2(
+                  __uint_as_float(hr[i]) + __uint_as_float(lr[i]), __uint_as_float(hm[i]) + __uint_as_float(lm[i]));
+            } else {
+              ws[T.ws + col * M + row] = make_float4(__uint_as_float(hr[i]), __uint_as_float(lr[i]),
+                                                     __uint_as_float(hm[i]), __uint_as_float(lm[i]));
+            }
+          }
+        }
+      }
+    }
+    if (!ok && lane == 0) {
+      *(volatile int*)&abort_flag = 1;
+      atomicExch(&g_tc_status, 1);
+    }
   } else {
     // ------------------------------------------------------------ producers
     // with A in tensor memory a warp owns the 32 rows of its lane quarter
@@ -1241,25 +1321,11 @@ sketch_img_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__
     const int prow = I::TA ? 32 * quad + lane : 16 * pw + (lane & 7) + 8 * ((lane >> 4) & 1);
     const int kg = I::TA ? sub : (lane >> 3) & 1;
     const uint32_t a_st = (uint32_t)(prow >> 3) * KG * CORE + (uint32_t)(prow & 7) * 16;
-    int next_drain = 0;
-    auto drain_group = [&](int g, bool last) -> bool {
-      if (!mbar_wait(accF + 8u * (g & 1), (uint32_t)((g / 2) & 1))) return false;
-      tc_fence_after();
-      drain_set<NR>(tq, sub, (uint32_t)(g & 1) * 3 * NR);
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(accE + 8u * (g & 1));
-      return true;
-    };
+    const volatile int* abortp = &abort_flag;
     for (int c = pgrp; c < nch && ok; c += IPG) {
-      if (pgrp == 0 && c % DR == 2 && c > DR) {   // third chunk of group g + 1: drain group g
-        ok = drain_group(next_drain, false);
-        ++next_drain;
-        if (!ok) break;
-      }
       const int sf = c % SF, s = c % S;
-      if (!mbar_wait(fullF + 8u * sf, (uint32_t)((c / SF) & 1)) ||
-          (c >= S && !mbar_wait(emptyO + 8u * s, (uint32_t)(((c / S) - 1) & 1))) || *(volatile int*)&abort_flag) {
+      if (!mbar_wait(fullF + 8u * sf, (uint32_t)((c / SF) & 1), abortp) ||
+          (c >= S && !mbar_wait(emptyO + 8u * s, (uint32_t)(((c / S) - 1) & 1), abortp))) {
         ok = false;
         break;
       }
@@ -1299,38 +1365,6 @@ sketch_img_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(fullO + 8u * s);
-    }
-    if (pgrp == 0) {
-      for (; ok && next_drain < ngroups; ++next_drain) ok = drain_group(next_drain, next_drain == ngroups - 1);
-      if (ok && nch > 0) {
-        // epilogue: (hi, lo) pairs of this warp's lanes to Y or to the split workspace
-        const int64_t row = row0 + quad * 32 + lane;
-#pragma unroll 1
-        for (int s = sub; s < (KP + 7) / 8; s += NWARP / 4) {
-          uint32_t hr[8], lr[8], hm[8], lm[8];
-          const int c0 = s * 8;
-          tmem_ld8(tq + 6 * NR + c0, hr);
-          tmem_ld8(tq + 7 * NR + c0, lr);
-          tmem_ld8(tq + 6 * NR + KP + c0, hm);
-          tmem_ld8(tq + 7 * NR + KP + c0, lm);
-          tmem_wait_ld();
-          if (row < M) {
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              const int col = c0 + i;
-              if (col >= kcols || col >= KP) continue;
-              if (T.ws < 0) {
-                float2* __restrict__ Y = (float2*)J.Y;
-                Y[row + (T.group * ygs + col) * J.ldy] = make_float2(
-                    __uint_as_float(hr[i]) + __uint_as_float(lr[i]), __uint_as_float(hm[i]) + __uint_as_float(lm[i]));
-              } else {
-                ws[T.ws + col * M + row] = make_float4(__uint_as_float(hr[i]), __uint_as_float(lr[i]),
-                                                       __uint_as_float(hm[i]), __uint_as_float(lm[i]));
-              }
-            }
-          }
-        }
-      }
     }
     if (!ok && lane == 0) {
       *(volatile int*)&abort_flag = 1;
