@@ -300,13 +300,8 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 // bytes (a multiple of 16, both addresses 16-byte aligned) from global memory
 // into shared memory by the bulk-copy engine, completing on mbarrier bar
-// (whose expected transaction count must cover them)
-__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-               "l"(src), "r"(bytes), "r"(bar)
-               : "memory");
-}
-// the same with an L2 eviction-priority policy (from l2_policy)
+// (whose expected transaction count must cover them), with an L2
+// eviction-priority policy (l2_evict_first / l2_evict_last)
 __device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar, uint64_t policy) {
   asm volatile(
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
@@ -1058,20 +1053,24 @@ __device__ __forceinline__ void drain_set(uint32_t tq, int first, int step, uint
 //   tile loader -- waits for tile slot c % SF to be free (read by the
 //              producers of chunk c - SF) and bulk-copies the image tile
 //              into it, completing on fullF;
-//   B loader -- waits for B slot c % SB (read by the MMAs of chunk c - SB)
-//              and bulk-copies the chunk's B operand into it (fullB);
+//   B loader -- waits for B slot c % SB (read by the MMAs of chunk c - SB:
+//              done) and bulk-copies the chunk's B operand into it,
+//              completing on full;
 //   producer group c % 2 -- waits for fullF and for A slot c % S (its MMAs
 //              of chunk c - S done), reads the tile rows, releases the tile,
 //              splits the entries into bf16 parts, writes A (tensor memory,
 //              or shared memory fenced to the async proxy) and arrives on
-//              fullO;
+//              full;
 //   drain warps -- once the MMAs of group g (4 chunks) are complete (accF),
 //              move its accumulator set into (hi, lo) and release it
 //              (accE); after the last group, write the rows out;
-//   MMA warp -- waits for fullO and fullB (and, at a group's first chunk,
-//              for the drain of the group two back), issues the chunk's MMAs
-//              and commits them to emptyO and emptyB (and to accF at a
-//              group's end).
+//   MMA warp -- waits for full (the A parts and the B operand of the chunk;
+//              at a group's first chunk also for the drain of the group two
+//              back), issues the chunk's MMAs and commits them to done (and
+//              to accF at a group's end).
+// full and done are rings of NB = 8 barriers indexed by chunk (one wait and
+// one commit per chunk for the MMA thread); a slot ring of S or SB slots
+// reuses its slot after done of the chunk S or SB back.
 // Every wait is bounded (1 s); a role that gives up raises the abort flag
 // and the device status, and the others stop at their next wait.
 template <int NR>
@@ -1085,15 +1084,17 @@ sketch_img_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ SketchJob J;
   __shared__ TcTile T;
-  __shared__ __align__(8) uint64_t bars[2 * SF + 2 * S + 4 + 2 * I::SB];
+  constexpr int NB = 8;
+  static_assert(NB % S == 0 && NB % I::SB == 0, "slot rings divide the barrier ring");
+  __shared__ __align__(8) uint64_t bars[2 * SF + 2 * NB + 4];
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t b0 = smem_u32(&bars[0]);
-  // fullF[i] = b0 + 8 i, emptyF[i] = +8 (SF + i), fullO[i] = +8 (2 SF + i),
-  // emptyO[i] = +8 (2 SF + S + i), accF[b] = +8 (2 SF + 2 S + b), accE[b] = +8 (2 SF + 2 S + 2 + b)
-  const uint32_t fullF = b0, emptyF = b0 + 8u * SF, fullO = b0 + 16u * SF, emptyO = fullO + 8u * S,
-                 accF = emptyO + 8u * S, accE = accF + 16u, fullB = accE + 16u, emptyB = fullB + 8u * I::SB;
+  // fullF[i] = b0 + 8 i, emptyF[i] = +8 (SF + i), full[j] = +8 (2 SF + j),
+  // done[j] = +8 (2 SF + NB + j), accF[b] = +8 (2 SF + 2 NB + b), accE[b] = +8 (2 SF + 2 NB + 2 + b)
+  const uint32_t fullF = b0, emptyF = b0 + 8u * SF, full = b0 + 16u * SF, done = full + 8u * NB,
+                 accF = done + 8u * NB, accE = accF + 16u;
   if (tid == 0) {
     T = tiles[blockIdx.x];
     J = jobs[T.job];
@@ -1101,13 +1102,9 @@ sketch_img_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__
       mbar_init(fullF + 8u * i, 1);        // the loader's expect_tx arrive
       mbar_init(emptyF + 8u * i, NWARP);   // the producer group's warps (tile read)
     }
-    for (int i = 0; i < I::SB; ++i) {
-      mbar_init(fullB + 8u * i, 1);        // the B loader's expect_tx arrive
-      mbar_init(emptyB + 8u * i, 1);       // the MMA commit (B read)
-    }
-    for (int i = 0; i < S; ++i) {
-      mbar_init(fullO + 8u * i, NWARP);
-      mbar_init(emptyO + 8u * i, 1);
+    for (int j = 0; j < NB; ++j) {
+      mbar_init(full + 8u * j, NWARP + 1);   // the producer group's warps + the B loader's expect_tx arrive
+      mbar_init(done + 8u * j, 1);           // the MMA commit
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(accF + 8u * b, 1);
@@ -1184,19 +1181,20 @@ sketch_img_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__
       const uint64_t pol = l2_evict_last();
       int c = 0;
       for (; c < nch; ++c) {
-        const int sbi = c % I::SB;
+        const int sbi = c % I::SB, j = c % NB;
         if (*(volatile int*)&abort_flag) break;
-        if (c >= I::SB && !mbar_wait(emptyB + 8u * sbi, (uint32_t)(((c / I::SB) - 1) & 1))) {
+        if (c >= I::SB && !mbar_wait(done + 8u * ((c - I::SB) % NB), (uint32_t)(((c - I::SB) / NB) & 1))) {
           *(volatile int*)&abort_flag = 1;
           atomicExch(&g_tc_status, 1);
           break;
         }
-        mbar_expect_tx(fullB + 8u * sbi, C::B_BUF);
-        bulk_copy(sb + I::B0 + (uint32_t)sbi * I::B_SLOT, bimp + (int64_t)c * C::B_BUF, C::B_BUF, fullB + 8u * sbi,
-                  pol);
+        mbar_expect_tx(full + 8u * j, C::B_BUF);
+        bulk_copy(sb + I::B0 + (uint32_t)sbi * I::B_SLOT, bimp + (int64_t)c * C::B_BUF, C::B_BUF, full + 8u * j, pol);
       }
-      for (int q = c - I::SB < 0 ? 0 : c - I::SB; q < c; ++q)   // copies still in flight (bounded)
-        mbar_wait(fullB + 8u * (q % I::SB), (uint32_t)((q / I::SB) & 1));
+      // the copies still in flight land before the CTA ends (bounded; after
+      // an abort the producers' arrivals may be missing and each wait ends
+      // at its limit)
+      for (int q = c - I::SB < 0 ? 0 : c - I::SB; q < c; ++q) mbar_wait(full + 8u * (q % NB), (uint32_t)((q / NB) & 1));
     }
     __syncwarp();
   } else if (warp == IMMA_WARP) {
@@ -1208,7 +1206,7 @@ sketch_img_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__
     // thread then keeps pace with the tensor pipe (six MMAs, 288 cycles of
     // M = 128 work per chunk at NR = 48).
     if (lane == 0) {
-      static_assert(8 % S == 0 && 8 % I::SB == 0 && DR == 4, "one unrolled period of the rings");
+      static_assert(NB == 8 && DR == 4, "one unrolled period of the rings");
       constexpr uint32_t idesc = idesc_bf16(NR), idesc2 = idesc_bf16(2 * NR), idesc3 = idesc_bf16(3 * NR);
       constexpr uint64_t pa = C::A_PART >> 4;
       const uint64_t dA0 = sdesc<KG>(sb + I::O0), dB0 = sdesc<KG>(sb + I::B0);
@@ -1216,6 +1214,7 @@ sketch_img_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__
       int issued = -1;
       for (int c8 = 0; c8 < nch && ok; c8 += 8) {
         const uint32_t accE_par = (uint32_t)(((c8 >> 3) + 1) & 1);   // phase of the group two back
+        const uint32_t full_par = (uint32_t)((c8 >> 3) & 1);          // chunk c8 + u on full[u]
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           const int c = c8 + u;
@@ -1225,8 +1224,7 @@ sketch_img_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__
             ok = false;
             break;
           }
-          if (!mbar_wait(fullO + 8u * s, (uint32_t)((c / S) & 1), abortp) ||
-              !mbar_wait(fullB + 8u * sbi, (uint32_t)((c / I::SB) & 1), abortp)) {
+          if (!mbar_wait(full + 8u * u, full_par, abortp)) {
             ok = false;
             break;
           }
@@ -1251,8 +1249,7 @@ sketch_img_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__
               mma_step<2>(tset + 2 * NR, dA + 2 * pa + o, dB + o, idesc, 1u);
             }
           }
-          tc_commit(emptyO + 8u * s);
-          tc_commit(emptyB + 8u * sbi);
+          tc_commit(done + 8u * u);
           if (u % DR == DR - 1 || c == nch - 1) tc_commit(accF + 8u * set);
           issued = c;
         }
@@ -1260,7 +1257,7 @@ sketch_img_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__
       if (!ok) {
         *(volatile int*)&abort_flag = 1;
         atomicExch(&g_tc_status, 1);
-        if (issued >= 0) mbar_wait(emptyO + 8u * (issued % S), (uint32_t)((issued / S) & 1));
+        if (issued >= 0) mbar_wait(done + 8u * (issued % NB), (uint32_t)((issued / NB) & 1));
       }
     }
     __syncwarp();
@@ -1325,7 +1322,7 @@ sketch_img_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__
     for (int c = pgrp; c < nch && ok; c += IPG) {
       const int sf = c % SF, s = c % S;
       if (!mbar_wait(fullF + 8u * sf, (uint32_t)((c / SF) & 1), abortp) ||
-          (c >= S && !mbar_wait(emptyO + 8u * s, (uint32_t)(((c / S) - 1) & 1), abortp))) {
+          (c >= S && !mbar_wait(done + 8u * ((c - S) % NB), (uint32_t)(((c - S) / NB) & 1), abortp))) {
         ok = false;
         break;
       }
@@ -1364,7 +1361,7 @@ sketch_img_kernel(const SketchJob* __restrict__ jobs, const TcTile* __restrict__
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       }
       __syncwarp();
-      if (lane == 0) mbar_arrive(fullO + 8u * s);
+      if (lane == 0) mbar_arrive(full + 8u * (c % NB));
     }
     if (!ok && lane == 0) {
       *(volatile int*)&abort_flag = 1;

@@ -139,3 +139,28 @@ def test_repeated_factorizations_stay_within_bound():
         if first is None:
             first = r
         assert np.array_equal(r, first)
+
+
+@pytest.mark.parametrize("ncols", [3, 12, 20, 30])
+def test_cached_products_every_tile_width(ncols):
+    """Products of the cached operator at every tile width of the image
+    kernel (NR = 16, 32, 48 real columns with the A parts in tensor memory,
+    64 with them in shared memory), on a ragged grid (1000 rows: seven full
+    128-row tiles and a tail of 104; 1300 columns: a tail of 4 past the last
+    16-column chunk), against the FP64 kernel entries of the oracle: every
+    orientation within FP32 level."""
+    from oracle import operators as oo
+    n, m = 1300, 1000
+    g = inputs.line_pair(n, m)
+    plan = api.Plan(g.src, g.tgt, kernel="helmholtz2d", wavenumber=g.wavenumber, leaf=16, tol=1e-6,
+                    precision="mixed", r0=16)
+    A = oo.kernel_entries(oo.HELMHOLTZ_2D, g.wavenumber, g.tgt, g.src)
+    opc = api.Operator.kernel(plan, cached=True)
+    for opn, rows, ref_of in (("N", n, lambda x: A @ x), ("T", m, lambda x: A.T @ x), ("C", m, lambda x: A.conj().T @ x)):
+        x = inputs.random_rhs(rows, ncols, seed=ncols)
+        y = opc.apply(api.colmajor(torch.from_numpy(x).to(torch.complex64).cuda()), opn)
+        torch.cuda.synchronize()
+        got = y.cpu().numpy().astype(np.complex128)
+        ref = ref_of(x.astype(np.complex64).astype(np.complex128))
+        assert got.shape == ref.shape
+        assert np.linalg.norm(got - ref) <= 2e-6 * np.linalg.norm(ref), opn
