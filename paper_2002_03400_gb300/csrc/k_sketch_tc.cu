@@ -805,9 +805,9 @@ __global__ void __launch_bounds__(256) entry_images_kernel(const SketchJob J, ui
                                                            uint8_t* __restrict__ imgC, int64_t nchN,
                                                            int64_t nchC) {
   using C = Cfg<16, 3>;
-  constexpr int KCH = C::KCH, VS = C::VS, SRC = IMG_PASS * KCH, LDS = TM + 1;
+  constexpr int KCH = C::KCH, VS = C::VS, LDS = TM + 1;
   __shared__ __align__(16) float pts[IMG_CPB * 6 * KCH];
-  extern __shared__ __align__(16) float2 stage[];   // [SRC][LDS]: (source, target)
+  extern __shared__ __align__(16) float2 stage[];   // [IMG_PASS * KCH][LDS]: (source, target)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int ek = formula_kind(J);
   const int npt = point_arrays(ek);
