@@ -2,8 +2,10 @@
 
 Workload (the exact-recovery / precision configuration): the 2D Helmholtz
 kernel exp(-i k r)/r between two parallel unit segments at distance 1,
-n = m = 16384 points, 8 points per wavelength, entries formed on the fly,
-leaf 16 (L = 10), tol 1e-6, p = 2, r0 = 16, seed 0; plus the exact-recovery
+n = m = 16384 points, 8 points per wavelength, entries from the kernel's
+closed form (formed once per factorization into complex64 entry images of A
+and A^H, then streamed by every sketch), leaf 16 (L = 10), tol 1e-6, p = 2,
+r0 = 16, seed 0; plus the exact-recovery
 case (n = 16384 exactly-butterfly operator of rank 8, leaf 32) used as a
 black box through its own factors.
 
@@ -329,13 +331,26 @@ def configs_measure():
     return res
 
 
+def max_over_ranks(values, dist=None, device="cpu"):
+    """The slowest rank's value of each entry (the step-time rule for N
+    replicas: an all-reduce MAX over the process group); the values
+    unchanged on one rank (dist None)."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
 def run_reference(args):
-    """--impl reference: the FP64 oracle on the host cores, bounded sample."""
+    """--impl reference: the FP64 oracle on the host cores, bounded sample
+    (rank 0 only under torchrun; the other ranks exit without work)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    for _ in range(args.warmup):
-        pass
+    for _ in range(args.warmup):   # untimed
+        cpu_oracle_sample(256)
     samples = []
     for _ in range(args.steps):
         raw, scaled, cores = cpu_oracle_sample(1024)
@@ -442,10 +457,7 @@ def main():
     fac_ms = [s.elapsed_time(e) for s, e in zip(starts, mids)]
     ms = float(np.mean(step_ms))
     fms = float(np.mean(fac_ms))
-    if dist:
-        t = torch.tensor([ms, fms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, fms = float(t[0].item()), float(t[1].item())
+    ms, fms = max_over_ranks([ms, fms], dist, "cuda")
 
     # apply GB/s (resident factors, 64 RHS, complex64 and complex128), after
     # the apply autotuner has chosen the stage-kernel shapes
