@@ -46,6 +46,9 @@ R0 = 16
 # float-float square-root correction 8, phase 4, pi/2 reduction 5,
 # polynomial sin/cos 9, quadrant 6, scaling 2
 ALU_OPS_PER_ENTRY = 71
+# DRAM bytes (read + write) of one sketch_img_kernel<48> launch at n = 8192
+# (the image profile case), from ncu; the image read once, X and Y
+IMG_TRAFFIC_N8192 = 541691392 + 6331136
 
 
 def measured_peaks():
@@ -614,7 +617,11 @@ def main():
         "roofline": {"kernel": "sketch_img_kernel (tcgen05, complex64 entry image streamed, exact three-way "
                                "bf16 split, B parts stacked along N)", "bound": "hbm",
                      "achieved": img_bytes / t_img / 1e9, "peak": peaks.get("hbm_gbs", 6800.0), "unit": "GB/s",
-                     "frac": img_bytes / t_img / 1e9 / peaks.get("hbm_gbs", 6800.0), "traffic": None,
+                     "frac": img_bytes / t_img / 1e9 / peaks.get("hbm_gbs", 6800.0),
+                     "traffic": IMG_TRAFFIC_N8192 * (N / 8192) ** 2,
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch at "
+                                       "n = 8192 (profiles/sketch_img_kernel_helmholtz2d_n8192.md), scaled "
+                                       "by the entry count to n = 16384",
                      "peak_source": peak_src + " (burst copy)",
                      "work": f"8 B per entry of the m=n={N} image + the {kw}-column X and Y, once each; "
                              "the timed product is 3 launches (B operand, image sketch, split-K reduce)",
