@@ -71,7 +71,7 @@ class ClockSampler:
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                          "-lms", "200", "-i", "0"], stdout=self.f, stderr=subprocess.DEVNULL)
+                                          "-lms", "100", "-i", "0"], stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
         return self
@@ -373,7 +373,9 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    # 20 steps of ~14 ms: a timed region of ~0.3 s, long enough for the
+    # clock sampler (100 ms interval) to see it under load
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300")
     ap.add_argument("--no-cpu", action="store_true")
@@ -438,8 +440,8 @@ def main():
     mids = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     fac_s, errs = [], []
-    clk = ClockSampler(os.path.join(ROOT, "gpurun_out", "clocks_bench.csv") if os.path.isdir(
-        os.path.join(ROOT, "gpurun_out")) else "/tmp/clocks_bench.csv")
+    # nvidia-smi samples of the timed region: BF_CLOCKS_CSV names the file
+    clk = ClockSampler(os.environ.get("BF_CLOCKS_CSV", "/tmp/clocks_bench.csv"))
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
