@@ -12,7 +12,8 @@ Geometries stand in for the paper's integral-equation workloads:
   exp(-i k r)/r evaluated directly instead of the H-matrix inverse.
 * ``arc_pair``: two separated circular arcs (batched workload).
 * ``cap_points``: Fibonacci-sampled spherical caps (3D kernels, Sec. 7.3
-  style surfaces).
+  style surfaces); ``cap_pair`` two separated caps, ``hemisphere_pair``
+  the two adjacent hemispheres of the 3D experiment (Sec. 7.3).
 * ``exact_butterfly``: random orthonormal U, V, R, W blocks and Gaussian B
   blocks of constant rank r, as in the exact-recovery experiment (Sec. 7.1).
 """
@@ -131,6 +132,22 @@ def cap_pair(n: int, m: int | None = None, ppw: float = 8.0,
     k = 2.0 * math.pi / (ppw * h)
     return Geometry(src, tgt, KERNEL_HELMHOLTZ_3D, k, f"cap_pair_n{n}",
                     {"ppw": ppw})
+
+
+def hemisphere_pair(n: int, m: int | None = None, ppw: float = 10.0) -> Geometry:
+    """Two adjacent unit hemispheres (the 3D experiment, Sec. 7.3): sources
+    on the upper half of the unit sphere (z > 0), targets on the lower half
+    (z < 0), each Fibonacci-sampled with equal-area heights, so the two
+    surfaces meet along the equator (weak admissibility: every level has
+    blocks that touch).  No point lies on the equator (|z| >= 1/(2n)).  Each
+    half has area 2 pi; h = sqrt(2 pi / n) and k = 2 pi / (ppw h), ppw = 10
+    as the paper intends.  Kernel exp(i k r)/(4 pi r)."""
+    m = n if m is None else m
+    src = cap_points(n, (0.0, 0.0, 0.0), 90.0, axis=(0.0, 0.0, 1.0))
+    tgt = cap_points(m, (0.0, 0.0, 0.0), 90.0, axis=(0.0, 0.0, -1.0))
+    h = math.sqrt(2.0 * math.pi / n)
+    k = 2.0 * math.pi / (ppw * h)
+    return Geometry(src, tgt, KERNEL_HELMHOLTZ_3D, k, f"hemisphere_pair_n{n}", {"ppw": ppw})
 
 
 def dft_points(n: int) -> Geometry:

@@ -225,3 +225,32 @@ def test_planted_swapped_stacking_is_caught(monkeypatch):
     F = ob.factor(op, None, None, eb.L, 1e-12, 2, 4, seed=0)
     monkeypatch.setattr(ob, "VH", real_VH)
     assert ob.sketch_error(op, F, seed=9) > 1e-3
+
+
+def test_adjacent_hemispheres_weak_admissibility():
+    """The 3D experiment's geometry (Sec. 7.3): two hemispheres that meet
+    along the equator.  The generator puts every point on the unit sphere,
+    sources above and targets below the equator, equal-area (uniform z, mean
+    1/2 in |z|), none on the equator.  The factorization of the touching
+    surfaces reaches the Thm 5.3 accuracy against the dense matrix, with
+    middle-level ranks above those of two separated caps at the same
+    sampling and growing with n (the O(n^{1/4}) growth the paper reports
+    for this case), while the separated caps' ranks stay put."""
+    g = inputs.hemisphere_pair(2000)
+    assert np.allclose(np.linalg.norm(g.src, axis=1), 1.0) and np.allclose(np.linalg.norm(g.tgt, axis=1), 1.0)
+    assert g.src[:, 2].min() >= 0.5 / 2000 - 1e-15 and g.tgt[:, 2].max() <= -0.5 / 2000 + 1e-15
+    assert abs(g.src[:, 2].mean() - 0.5) < 1e-3 and abs(g.tgt[:, 2].mean() + 0.5) < 1e-3
+    assert math.isclose(g.wavenumber, 2 * math.pi / (10.0 * math.sqrt(2 * math.pi / 2000)))
+    eps = 1e-6
+    mid = {}
+    for n in (512, 1024):
+        for name, geo in (("hemi", inputs.hemisphere_pair(n)), ("caps", inputs.cap_pair(n, ppw=10.0))):
+            op = oo.KernelOp(oo.HELMHOLTZ_3D, geo.wavenumber, geo.tgt, geo.src)
+            L = inputs.leaf_levels(n, 16)
+            F = ob.factor(op, geo.src, geo.tgt, L, eps, 4, 16, seed=0)
+            A = op.dense()
+            assert np.linalg.norm(A - ob.dense(F)) <= 2 * math.sqrt(L + 2) * eps * np.linalg.norm(A)
+            mid[name, n] = int(np.max(F.rV[F.lm]))
+    assert mid["hemi", 512] > mid["caps", 512] and mid["hemi", 1024] > mid["caps", 1024]
+    assert mid["hemi", 1024] > mid["hemi", 512]
+    assert abs(mid["caps", 1024] - mid["caps", 512]) <= 2
