@@ -119,15 +119,24 @@ def UH(F: Factorization, j: int, sigma: int, mu: int, Z: np.ndarray) -> np.ndarr
 # ---------------------------------------------------------------------------
 
 def factor(op, src, tgt, leaf_levels: int, eps: float, p: int, r0: int, seed: int,
-           r_max: int = 4096) -> Factorization:
+           r_max: int = 4096, hybrid_level: int | None = None) -> Factorization:
     """Adaptive randomized hybrid butterfly factorization (Alg. 2).
 
     ``op`` is a black box (oracle.operators) in user order; ``src``/``tgt``
-    are the point sets (or None for index order) the trees are built on."""
+    are the point sets (or None for index order) the trees are built on.
+    ``hybrid_level`` is the level l of eq. hybrid_butterfly_mat where B sits
+    (Alg. 2 uses l_m = floor(L/2), the default); any 0 <= l <= L-1 runs the
+    same loops (W levels 1..l, R levels L-1..l, B at l).  l = 0 is the
+    column-wise factorization of Sec. 3.3.1 with its outer factor E^0 kept
+    as B^0 V^0^H (the "minor modification" of Sec. 4, at the cost of a
+    sketch with 2^(L-l) k columns at every R level); the row-wise one
+    (Sec. 3.3.2) is the transpose of the column-wise factorization of A^T."""
     n, m, L = op.n, op.m, leaf_levels
     if L < 1:
         raise ValueError("Alg. 2 needs L >= 1 (the B loop runs at l = l_m <= L-1)")
-    lm = L // 2
+    lm = L // 2 if hybrid_level is None else int(hybrid_level)
+    if not 0 <= lm <= L - 1:
+        raise ValueError("the hybrid level must satisfy 0 <= l <= L-1")
     permS, offS, permT, offT = make_trees(src, n, tgt, m, L)
     F = Factorization(n, m, L, lm, permS, offS, permT, offT)
     nb = 1 << L

@@ -254,3 +254,54 @@ def test_adjacent_hemispheres_weak_admissibility():
     assert mid["hemi", 512] > mid["caps", 512] and mid["hemi", 1024] > mid["caps", 1024]
     assert mid["hemi", 1024] > mid["hemi", 512]
     assert abs(mid["caps", 1024] - mid["caps", 512]) <= 2
+
+
+@pytest.mark.parametrize("level", [0, 1, 2, 3])
+def test_hybrid_level_column_and_row_wise(level):
+    """Sec. 3.3: the hybrid factorization at any level l (B at l, W levels
+    1..l, R levels L-1..l); l = 0 is the column-wise form of Sec. 3.3.1.  An
+    exactly-butterfly matrix (rank 4, L = 4) is recovered to machine
+    precision with rank 4 at every block for every l, and the black-box
+    column count follows the closed form of Sec. 4.1/4.5: the two leaf
+    loops take 10 columns each (r0 = 4 doubled once, p = 2), level j of the
+    W loop 2^j (4 + 4 + 2) and level j of the R loop 2^(L-j) (4 + 4 + 2) --
+    least at l = L/2 ("much higher cost" toward l = 0 and l = L-1)."""
+    eb, Ft, op = _exact(256, 16, 4, seed=1)
+    A = ob.dense(Ft)
+    F = ob.factor(op, None, None, eb.L, 1e-12, 2, 4, seed=0, hybrid_level=level)
+    assert F.lm == level
+    assert np.linalg.norm(A - ob.dense(F)) <= 1e-12 * np.linalg.norm(A)
+    assert all(np.all(F.rV[j] == 4) for j in F.rV) and all(np.all(F.rU[j] == 4) for j in F.rU)
+    L = eb.L
+    want = 20 + 10 * (sum(2 ** j for j in range(1, level + 1)) + sum(2 ** (L - j) for j in range(level, L)))
+    assert sum(F.bb_cols.values()) == want
+
+
+def test_column_wise_and_row_wise_kernel():
+    """Kernel matrix (line pair, n = 512, L = 5): the column-wise form (l = 0)
+    and the row-wise form (the transpose of the column-wise factorization of
+    A^T, applied with op T) both reach the Thm 5.3 accuracy; l outside
+    [0, L-1] is refused."""
+    g = inputs.line_pair(512)
+    op = oo.KernelOp(oo.HELMHOLTZ_2D, g.wavenumber, g.tgt, g.src)
+    A = op.dense()
+    L = inputs.leaf_levels(512, 16)
+    bound = 2 * math.sqrt(L + 2) * 1e-6
+    Fc = ob.factor(op, g.src, g.tgt, L, 1e-6, 2, 4, seed=0, hybrid_level=0)
+    assert np.linalg.norm(A - ob.dense(Fc)) <= bound * np.linalg.norm(A)
+
+    class Transposed:
+        def __init__(self, o):
+            self.o, self.n, self.m = o, o.m, o.n
+
+        def matvec(self, X):
+            return self.o.matvec_T(X)
+
+        def matvec_T(self, X):
+            return self.o.matvec(X)
+
+    Fr = ob.factor(Transposed(op), g.tgt, g.src, L, 1e-6, 2, 4, seed=0, hybrid_level=0)
+    x = inputs.random_rhs(512, 3, seed=2)
+    assert np.linalg.norm(ob.apply(Fr, x, "T") - A @ x) <= bound * np.linalg.norm(A @ x)
+    with pytest.raises(ValueError):
+        ob.factor(op, g.src, g.tgt, L, 1e-6, 2, 4, seed=0, hybrid_level=L)
