@@ -47,13 +47,15 @@ def test_options_defaults_and_error_string(libpath):
 
 
 @pytest.mark.parametrize("kind,count,L", [("line", 1024, 6), ("caps", 777, 5), ("arcs", 1000, 6),
-                                          ("index", 999, 4), ("dft", 256, 4)])
+                                          ("index", 999, 4), ("dft", 256, 4), ("hemi_src", 1500, 7),
+                                          ("hemi_tgt", 1023, 6)])
 def test_host_bisection_matches_oracle(libpath, kind, count, L):
     from oracle.tree import bisect as obisect
     from paper_2002_03400_gb300 import api, inputs
     g = {"line": lambda: inputs.line_pair(count).src, "caps": lambda: inputs.cap_pair(count).tgt,
          "arcs": lambda: inputs.arc_pair(count, 3).tgt, "index": lambda: None,
-         "dft": lambda: inputs.dft_points(count).tgt}[kind]()
+         "dft": lambda: inputs.dft_points(count).tgt, "hemi_src": lambda: inputs.hemisphere_pair(count).src,
+         "hemi_tgt": lambda: inputs.hemisphere_pair(count).tgt}[kind]()
     p, off = api.bisect(g, count, L)
     po, offo = obisect(g, count, L)
     assert np.array_equal(p, po)
