@@ -118,6 +118,13 @@ def UH(F: Factorization, j: int, sigma: int, mu: int, Z: np.ndarray) -> np.ndarr
 # Alg. 2
 # ---------------------------------------------------------------------------
 
+def leaf_loop_done(r: int, max_rank: int, k: int, leaf_max: int) -> bool:
+    """The adaptive stop of the leaf loops (Alg. 2, loops "V" and "U"): the
+    guess r exceeds every leaf rank the sketch revealed, or the sketch width
+    k = r + p already spans the largest leaf (the heuristic of Sec. 4.2)."""
+    return r > max_rank or k >= leaf_max
+
+
 def factor(op, src, tgt, leaf_levels: int, eps: float, p: int, r0: int, seed: int,
            r_max: int = 4096, hybrid_level: int | None = None) -> Factorization:
     """Adaptive randomized hybrid butterfly factorization (Alg. 2).
@@ -169,7 +176,7 @@ def factor(op, src, tgt, leaf_levels: int, eps: float, p: int, r0: int, seed: in
             Q, rk, _, _ = pivoted_qr_truncated(Y[offS[L][nu]:offS[L][nu + 1], :k], eps)
             F.V0.append(Q)
             ranks[nu] = rk
-        if r > ranks.max() or k >= leafS.max():
+        if leaf_loop_done(r, int(ranks.max()), k, int(leafS.max())):
             break
         r *= 2
         if r > r_max:
@@ -191,7 +198,7 @@ def factor(op, src, tgt, leaf_levels: int, eps: float, p: int, r0: int, seed: in
             Q, rk, _, _ = pivoted_qr_truncated(Z[offT[L][tau]:offT[L][tau + 1], :k], eps)
             F.U.append(Q)
             ranks[tau] = rk
-        if r > ranks.max() or k >= leafT.max():
+        if leaf_loop_done(r, int(ranks.max()), k, int(leafT.max())):
             break
         r *= 2
         if r > r_max:
@@ -373,6 +380,25 @@ def error_probe(n: int, seed: int, cols: int = 16) -> np.ndarray:
     """Test matrix of the error metric (Sec. 7, eq. error): complex Gaussian,
     ``cols`` columns, rows in user order, its own stream."""
     return rng.gaussian(seed, rng.stream_id(rng.STAGE_ERR), np.arange(n), 0, cols)
+
+
+def factor_checked(op, src, tgt, leaf_levels: int, eps: float, p: int, r0: int, seed: int,
+                   check_seed: int = 1009, retries: int = 4, **kw) -> tuple:
+    """Alg. 2 with an a-posteriori acceptance test: the sketch error of
+    Sec. 7 (eq. error) with fresh test columns must be within the Thm 5.3
+    bound 2 sqrt(L+2) eps; otherwise the factorization is redone with the
+    initial rank guess r0 doubled (at most `retries` times).  Returns the
+    factorization and the list of (r0, error) of every attempt."""
+    bound = 2.0 * np.sqrt(leaf_levels + 2) * eps
+    tried = []
+    for t in range(retries + 1):
+        F = factor(op, src, tgt, leaf_levels, eps, p, r0, seed, **kw)
+        e = sketch_error(op, F, check_seed + t)
+        tried.append((r0, e))
+        if e <= bound:
+            return F, tried
+        r0 *= 2
+    raise NotConverged(f"sketch error above {bound:.2e} after {retries} retries: {tried}")
 
 
 def sketch_error(op, F: Factorization, seed: int, cols: int = 16) -> float:

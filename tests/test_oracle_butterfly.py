@@ -305,3 +305,31 @@ def test_column_wise_and_row_wise_kernel():
     assert np.linalg.norm(ob.apply(Fr, x, "T") - A @ x) <= bound * np.linalg.norm(A @ x)
     with pytest.raises(ValueError):
         ob.factor(op, g.src, g.tgt, L, 1e-6, 2, 4, seed=0, hybrid_level=L)
+
+
+def test_a_posteriori_acceptance(monkeypatch):
+    """The heuristic stop of the leaf loops ("r > max rank", Sec. 4.2) backed
+    by an a-posteriori test: the sketch error (Sec. 7) with fresh columns
+    must meet the Thm 5.3 bound, else Alg. 2 reruns with r0 doubled.  A
+    converged run is accepted at once; with the stop planted to fire after
+    the first pass (leaf bases of rank <= r0 + p), the plain factorization
+    misses the bound, the checked one retries until the dense error is
+    within it, and without retries it reports non-convergence."""
+    g = inputs.line_pair(1024)
+    op = oo.KernelOp(oo.HELMHOLTZ_2D, g.wavenumber, g.tgt, g.src)
+    A = op.dense()
+    L = inputs.leaf_levels(1024, 16)
+    bound = 2 * math.sqrt(L + 2) * 1e-6
+    F, tried = ob.factor_checked(op, g.src, g.tgt, L, 1e-6, 2, 4, seed=0)
+    assert len(tried) == 1 and tried[0][1] <= bound
+    F0 = ob.factor(op, g.src, g.tgt, L, 1e-6, 2, 4, seed=0)
+    assert all(np.array_equal(F.rV[j], F0.rV[j]) for j in F0.rV)
+    monkeypatch.setattr(ob, "leaf_loop_done", lambda r, max_rank, k, leaf_max: True)
+    Fp = ob.factor(op, g.src, g.tgt, L, 1e-6, 2, 2, seed=0)
+    assert ob.sketch_error(op, Fp, 5) > bound and np.linalg.norm(A - ob.dense(Fp)) > bound * np.linalg.norm(A)
+    Fc, tried = ob.factor_checked(op, g.src, g.tgt, L, 1e-6, 2, 2, seed=0)
+    assert len(tried) >= 2 and [t[0] for t in tried] == [2 * 2 ** i for i in range(len(tried))]
+    assert all(e > bound for _, e in tried[:-1]) and tried[-1][1] <= bound
+    assert np.linalg.norm(A - ob.dense(Fc)) <= bound * np.linalg.norm(A)
+    with pytest.raises(ob.NotConverged):
+        ob.factor_checked(op, g.src, g.tgt, L, 1e-6, 2, 2, seed=0, retries=0)
