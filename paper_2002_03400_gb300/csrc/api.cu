@@ -7,6 +7,8 @@
 #include <cstring>
 #include <map>
 #include <numeric>
+#include <system_error>
+#include <thread>
 
 #include "bf_internal.h"
 
@@ -172,43 +174,45 @@ void DevBuf::release(cudaStream_t s) {
 // lowest index).
 static void bisect(const double* pts, int64_t count, int dim, int L, std::vector<int64_t>& perm,
                    std::vector<std::vector<int64_t>>& off) {
-  std::vector<std::vector<int64_t>> nodes(1);
-  nodes[0].resize(count);
-  std::iota(nodes[0].begin(), nodes[0].end(), 0);
+  // One index array split in place, level by level.  A node's lower half
+  // is the set of its ceil(s/2) smallest points under (coordinate on the
+  // axis of largest extent, index) -- a strict total order -- so above the
+  // last level a selection (nth_element) yields the same sets as a sort;
+  // the last split sorts, which fixes the order inside every leaf.
+  perm.resize(count);
+  std::iota(perm.begin(), perm.end(), 0);
   off.assign(1, {0, count});
   for (int lev = 0; lev < L; ++lev) {
-    std::vector<std::vector<int64_t>> nxt;
-    nxt.reserve(nodes.size() * 2);
-    for (auto& node : nodes) {
-      const int64_t s = (int64_t)node.size(), h = (s + 1) / 2;
+    const std::vector<int64_t> cur = off.back();
+    std::vector<int64_t> o(2 * (cur.size() - 1) + 1, 0);
+    for (size_t i = 0; i + 1 < cur.size(); ++i) {
+      const int64_t a = cur[i], b = cur[i + 1], s = b - a, h = (s + 1) / 2;
       if (pts && s > 1) {
         int ax = 0;
         double best = -1.0;
         for (int d = 0; d < dim; ++d) {
-          double lo = pts[node[0] * dim + d], hi = lo;
-          for (int64_t i : node) {
-            const double v = pts[i * dim + d];
+          double lo = pts[perm[a] * dim + d], hi = lo;
+          for (int64_t t = a; t < b; ++t) {
+            const double v = pts[perm[t] * dim + d];
             lo = std::min(lo, v);
             hi = std::max(hi, v);
           }
           if (hi - lo > best) best = hi - lo, ax = d;
         }
-        std::sort(node.begin(), node.end(), [&](int64_t a, int64_t b) {
-          const double va = pts[a * dim + ax], vb = pts[b * dim + ax];
-          return va < vb || (va == vb && a < b);
-        });
+        auto less = [&](int64_t x, int64_t y) {
+          const double vx = pts[x * dim + ax], vy = pts[y * dim + ax];
+          return vx < vy || (vx == vy && x < y);
+        };
+        if (lev == L - 1)
+          std::sort(perm.begin() + a, perm.begin() + b, less);
+        else
+          std::nth_element(perm.begin() + a, perm.begin() + a + h, perm.begin() + b, less);
       }
-      nxt.emplace_back(node.begin(), node.begin() + h);
-      nxt.emplace_back(node.begin() + h, node.end());
+      o[2 * i + 1] = a + h;
+      o[2 * i + 2] = b;
     }
-    nodes.swap(nxt);
-    std::vector<int64_t> o(nodes.size() + 1, 0);
-    for (size_t i = 0; i < nodes.size(); ++i) o[i + 1] = o[i] + (int64_t)nodes[i].size();
-    off.push_back(o);
+    off.push_back(std::move(o));
   }
-  perm.clear();
-  perm.reserve(count);
-  for (auto& node : nodes) perm.insert(perm.end(), node.begin(), node.end());
 }
 
 // ------------------------------------------------------------ operators ---
@@ -458,8 +462,22 @@ int bf_plan_create(const double* src, int64_t n, const double* tgt, int64_t m, i
   P->mem.cap = o.mem_cap;
   if (kern) P->kern = *kern;
   P->has_points = pts;
-  bisect(pts ? src : nullptr, n, dim, L, P->permS, P->offS);
-  bisect(pts ? tgt : nullptr, m, dim, L, P->permT, P->offT);
+  // the two trees are independent: for large point sets the target tree is
+  // built on a second thread (serially if no thread can be started)
+  bool trees = false;
+  if (pts && n + m >= 8192) {
+    try {
+      std::thread tt([&] { bisect(tgt, m, dim, L, P->permT, P->offT); });
+      bisect(src, n, dim, L, P->permS, P->offS);
+      tt.join();
+      trees = true;
+    } catch (const std::system_error&) {
+    }
+  }
+  if (!trees) {
+    bisect(pts ? src : nullptr, n, dim, L, P->permS, P->offS);
+    bisect(pts ? tgt : nullptr, m, dim, L, P->permT, P->offT);
+  }
   for (int b = 0; b < (1 << L); ++b)
     if (P->offS[L][b + 1] == P->offS[L][b] || P->offT[L][b + 1] == P->offT[L][b]) {
       delete P;
