@@ -467,10 +467,17 @@ int bf_plan_create(const double* src, int64_t n, const double* tgt, int64_t m, i
   bool trees = false;
   if (pts && n + m >= 8192) {
     try {
-      std::thread tt([&] { bisect(tgt, m, dim, L, P->permT, P->offT); });
+      bool ok_T = false;
+      std::thread tt([&] {
+        try {
+          bisect(tgt, m, dim, L, P->permT, P->offT);
+          ok_T = true;
+        } catch (...) {   // no exception may leave a thread: the serial path below redoes it
+        }
+      });
       bisect(src, n, dim, L, P->permS, P->offS);
       tt.join();
-      trees = true;
+      trees = ok_T;
     } catch (const std::system_error&) {
     }
   }
