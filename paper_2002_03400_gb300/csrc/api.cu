@@ -475,7 +475,12 @@ int bf_plan_create(const double* src, int64_t n, const double* tgt, int64_t m, i
         } catch (...) {   // no exception may leave a thread: the serial path below redoes it
         }
       });
-      bisect(src, n, dim, L, P->permS, P->offS);
+      try {
+        bisect(src, n, dim, L, P->permS, P->offS);
+      } catch (...) {
+        tt.join();   // a joinable thread must not be destroyed
+        throw;
+      }
       tt.join();
       trees = ok_T;
     } catch (const std::system_error&) {
