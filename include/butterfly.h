@@ -255,12 +255,18 @@ int bf_applier_run(bf_applier A, const void* x, int64_t ldx, void* y, int64_t ld
  * the caller still owns x and y.  All intermediates live in one file-scope
  * device array of BF_NOALLOC_SCRATCH_BYTES:
  *   - the first call on a device looks up that array's device address
- *     (cudaGetSymbolAddress) with the device current; make that first call
- *     before capturing the stream into a CUDA graph;
+ *     (cudaGetSymbolAddress) with the device current and keeps it for the
+ *     life of the process; make that first call before capturing the stream
+ *     into a CUDA graph.  Resetting the device (cudaDeviceReset) while the
+ *     library is loaded is not supported: the kept address would be stale;
+ *   - a call that finds no cached task lists for (op, dtype) builds them on
+ *     the host and copies them into the array; while the stream is being
+ *     captured that copy would outlive its source, so such a call returns
+ *     BF_EINVAL (bf_apply with the same op and dtype caches the lists);
  *   - a request that needs more scratch than the array holds (grows with
- *     nrhs and with the factorization's block ranks) returns BF_EINVAL with
- *     the byte counts in bf_last_error(); split the columns into smaller
- *     calls;
+ *     nrhs and with the factorization's block ranks; nrhs above INT32_MAX
+ *     included) returns BF_EINVAL with the byte counts in bf_last_error()
+ *     before any GPU work; split the columns into smaller calls;
  *   - every call shares the array and it keeps the last call's contents;
  *     nothing in it needs to start at zero (each call writes every element
  *     it later reads), but calls whose GPU work overlaps -- on different

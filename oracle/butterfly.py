@@ -20,7 +20,7 @@ trivial): every transpose in a projection becomes a conjugate transpose,
 K ~= U U^H K and K ~= K V V^H; the black box provides A and A^T and the
 oracle forms A^H X = conj(A^T conj(X)).
 
-Readings where the paper is silent or garbled (listed in the design doc):
+Readings where the paper is silent or garbled:
   * Alg. 1 truncation and pivoting: see oracle.qr.
   * adaptive leaf loops: r starts at r0 in both loops; each pass appends r
     new random columns to the previous ones (columns are indexed by the

@@ -6,6 +6,7 @@
 #include <atomic>
 #include <cstring>
 #include <map>
+#include <new>
 #include <numeric>
 #include <system_error>
 #include <thread>
@@ -463,32 +464,42 @@ int bf_plan_create(const double* src, int64_t n, const double* tgt, int64_t m, i
   if (kern) P->kern = *kern;
   P->has_points = pts;
   // the two trees are independent: for large point sets the target tree is
-  // built on a second thread (serially if no thread can be started)
-  bool trees = false;
-  if (pts && n + m >= 8192) {
-    try {
-      bool ok_T = false;
-      std::thread tt([&] {
-        try {
-          bisect(tgt, m, dim, L, P->permT, P->offT);
-          ok_T = true;
-        } catch (...) {   // no exception may leave a thread: the serial path below redoes it
-        }
-      });
+  // built on a second thread (serially if no thread can be started).  No
+  // exception may cross the C ABI: any failure of the build (e.g. bad_alloc
+  // on a large point set) frees the plan and returns a status.
+  try {
+    bool trees = false;
+    if (pts && n + m >= 8192) {
       try {
-        bisect(src, n, dim, L, P->permS, P->offS);
-      } catch (...) {
-        tt.join();   // a joinable thread must not be destroyed
-        throw;
+        bool ok_T = false;
+        std::thread tt([&] {
+          try {
+            bisect(tgt, m, dim, L, P->permT, P->offT);
+            ok_T = true;
+          } catch (...) {   // no exception may leave a thread: the serial path below redoes it
+          }
+        });
+        try {
+          bisect(src, n, dim, L, P->permS, P->offS);
+        } catch (...) {
+          tt.join();   // a joinable thread must not be destroyed
+          throw;
+        }
+        tt.join();
+        trees = ok_T;
+      } catch (const std::system_error&) {
       }
-      tt.join();
-      trees = ok_T;
-    } catch (const std::system_error&) {
     }
-  }
-  if (!trees) {
-    bisect(pts ? src : nullptr, n, dim, L, P->permS, P->offS);
-    bisect(pts ? tgt : nullptr, m, dim, L, P->permT, P->offT);
+    if (!trees) {
+      bisect(pts ? src : nullptr, n, dim, L, P->permS, P->offS);
+      bisect(pts ? tgt : nullptr, m, dim, L, P->permT, P->offT);
+    }
+  } catch (const std::bad_alloc&) {
+    delete P;
+    return fail(BF_ENOMEM, "host memory exhausted while building the bisection trees");
+  } catch (...) {
+    delete P;
+    return fail(BF_EINVAL, "the bisection trees could not be built");
   }
   for (int b = 0; b < (1 << L); ++b)
     if (P->offS[L][b + 1] == P->offS[L][b] || P->offT[L][b + 1] == P->offT[L][b]) {

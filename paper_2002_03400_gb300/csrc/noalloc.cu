@@ -2,6 +2,8 @@
 // allocation, for callers that may not allocate while they run (see the
 // declaration in include/butterfly.h).  All scratch lives in one file-scope
 // device array of BF_NOALLOC_SCRATCH_BYTES, shared by every call on a device.
+#include <algorithm>
+#include <climits>
 #include <mutex>
 
 #include "bf_internal.h"
@@ -79,14 +81,36 @@ extern "C" int bf_apply_noalloc(bf_fact Fh, int op, int64_t nrhs, const void* x,
   const int conj = op == BF_OP_T ? 1 : 0;
   const bool direct_in = (opC ? P->identT : P->identS) && !conj && ldx == in_rows;
   const bool direct_out = (opC ? P->identS : P->identT) && !conj && ldy == out_rows;
-  const size_t lvl = round256((size_t)ap->level_rows_max * nrhs * es);
-  const size_t xb = direct_in ? 0 : round256((size_t)in_rows * nrhs * es);
-  const size_t yb = direct_out ? 0 : round256((size_t)out_rows * nrhs * es);
-  const size_t need = task_bytes + 2 * lvl + xb + yb;
-  if (need > (size_t)BF_NOALLOC_SCRATCH_BYTES)
-    return fail(BF_EINVAL, "bf_apply_noalloc needs " + std::to_string(need) + " bytes of scratch for nrhs=" +
-                               std::to_string(nrhs) + ", above BF_NOALLOC_SCRATCH_BYTES (" +
-                               std::to_string((size_t)BF_NOALLOC_SCRATCH_BYTES) + "); use fewer columns per call");
+  // Sizes in a form that cannot wrap: every factor is checked against the
+  // array's size before it is multiplied, so a huge nrhs is refused here and
+  // never reaches a kernel (whose column count is an int).
+  const size_t cap = (size_t)BF_NOALLOC_SCRATCH_BYTES;
+  const size_t rows_max = std::max<size_t>({(size_t)ap->level_rows_max, (size_t)in_rows, (size_t)out_rows, 1});
+  size_t need = 0, lvl = 0, xb = 0, yb = 0;
+  bool over = nrhs > (int64_t)INT32_MAX || (uint64_t)nrhs > cap / (es * rows_max);
+  if (!over) {
+    lvl = round256((size_t)ap->level_rows_max * (size_t)nrhs * es);
+    xb = direct_in ? 0 : round256((size_t)in_rows * (size_t)nrhs * es);
+    yb = direct_out ? 0 : round256((size_t)out_rows * (size_t)nrhs * es);
+    need = task_bytes + 2 * lvl + xb + yb;
+    over = need > cap;
+  }
+  if (over)
+    return fail(BF_EINVAL, "bf_apply_noalloc needs " + (need ? std::to_string(need) : std::string("more")) +
+                               " bytes of scratch for nrhs=" + std::to_string(nrhs) +
+                               ", above BF_NOALLOC_SCRATCH_BYTES (" + std::to_string(cap) +
+                               "); use fewer columns per call");
+  // Without cached task lists the call copies them from host memory that
+  // lives only for this call; a stream capture would record a copy from
+  // memory that is gone when the graph runs, so that case is refused.
+  if (!cached.built) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    BF_CUDA_TRY(cudaStreamIsCapturing(s, &cs));
+    if (cs != cudaStreamCaptureStatusNone)
+      return fail(BF_EINVAL,
+                  "bf_apply_noalloc during stream capture needs this factorization's task lists for the op and "
+                  "dtype on the device: run bf_apply once with them first");
+  }
 
   void* base = nullptr;
   BF_TRY(scratch_address(&base));

@@ -8,6 +8,8 @@ intermediate from the library's fixed device array.  This file is collected
 last so that a failure here stops a -x run only after every other test; it
 passes alone in a fresh process and after the other tests."""
 import ctypes as C
+import ctypes.util
+import os
 
 import numpy as np
 import pytest
@@ -23,6 +25,35 @@ def _noalloc(F, op, x, y):
     s = torch.cuda.current_stream().cuda_stream
     return L.bf_apply_noalloc(F._h, api.OPS[op], x.shape[1], C.c_void_p(x.data_ptr()), api._ld(x),
                               C.c_void_p(y.data_ptr()), api._ld(y), api._dt(x), C.c_void_p(s))
+
+
+def _cudart():
+    """The CUDA runtime (for the device's default memory pool, where every
+    stream-ordered allocation of the library lands)."""
+    for name in ("/usr/local/cuda/lib64/libcudart.so", ctypes.util.find_library("cudart")):
+        if name and (os.path.exists(name) or not name.startswith("/")):
+            try:
+                return C.CDLL(name)
+            except OSError:
+                pass
+    pytest.skip("libcudart not found")
+
+
+def _pool_high(rt, reset):
+    """High-water mark of bytes in use in the current device's default pool
+    (cudaMemPoolAttrUsedMemHigh = 8); reset=True lowers it to the current use
+    first, so a later rise means something was allocated in between."""
+    dev = C.c_int(0)
+    assert rt.cudaGetDevice(C.byref(dev)) == 0
+    pool = C.c_void_p()
+    assert rt.cudaDeviceGetDefaultMemPool(C.byref(pool), dev) == 0
+    v = C.c_uint64(0)
+    if reset:
+        assert rt.cudaMemPoolSetAttribute(pool, 8, C.byref(v)) == 0
+    assert rt.cudaMemPoolGetAttribute(pool, 8, C.byref(v)) == 0
+    cur = C.c_uint64(0)
+    assert rt.cudaMemPoolGetAttribute(pool, 7, C.byref(cur)) == 0   # UsedMemCurrent
+    return v.value, cur.value
 
 
 def _rel(a, b):
@@ -75,3 +106,32 @@ def test_noalloc_permuted_plan_complex64_and_limits():
     F64 = api.exact_factorization(api.Plan(n=512, leaf=16), eb)
     x32 = api.empty_cm(512, 2, torch.complex64)
     assert _noalloc(F64, "N", x32, api.empty_cm(512, 2, torch.complex64)) == -1
+
+
+def test_noalloc_allocates_nothing_and_refuses_wrapping_sizes():
+    """The defining property: neither the uncached first call (task lists
+    built on the host and copied into the array) nor a cached call takes
+    memory from the device's pool -- its high-water mark does not move.
+    And a column count whose byte size would wrap a 64-bit product is
+    refused before any GPU work."""
+    rt = _cudart()
+    n, leaf, r, nrhs = 1024, 16, 6, 9
+    eb = inputs.exact_butterfly(n, leaf, r, seed=7)
+    F = api.exact_factorization(api.Plan(n=n, leaf=leaf), eb)
+    x = api.colmajor(torch.from_numpy(inputs.random_rhs(n, nrhs, seed=8)).cuda())
+    y = api.empty_cm(n, nrhs, torch.complex128)
+    for op in ("C", "N"):                  # C: uncached task lists, N: cached below
+        if op == "N":
+            F.apply(x)                         # caches the op-N lists (allocates, outside the window)
+        torch.cuda.synchronize()
+        _pool_high(rt, reset=True)
+        base_high, base_cur = _pool_high(rt, reset=False)
+        assert _noalloc(F, op, x, y) == 0, api.lib().bf_last_error()
+        torch.cuda.synchronize()
+        high, cur = _pool_high(rt, reset=False)
+        assert high <= max(base_high, base_cur) and cur == base_cur, (op, base_high, high, base_cur, cur)
+    L = api.lib()
+    for big in (1 << 60, (1 << 62) + 3, (1 << 31)):
+        rc = L.bf_apply_noalloc(F._h, 0, C.c_int64(big), C.c_void_p(x.data_ptr()), n, C.c_void_p(y.data_ptr()), n,
+                                api.BF_C128, None)
+        assert rc == -1 and b"BF_NOALLOC_SCRATCH_BYTES" in L.bf_last_error(), big
