@@ -1,21 +1,20 @@
 """Benchmark of the butterfly hot path on one GB300 (or N independent replicas).
 
-Workload (the exact-recovery / precision configuration): the 2D Helmholtz
-kernel exp(-i k r)/r between two parallel unit segments at distance 1,
-n = m = 16384 points, 8 points per wavelength, entries from the kernel's
-closed form (formed once per factorization into complex64 entry images of A
-and A^H, then streamed by every sketch), leaf 16 (L = 10), tol 1e-6, p = 2,
-r0 = 16, seed 0; plus the exact-recovery
-case (n = 16384 exactly-butterfly operator of rank 8, leaf 32) used as a
-black box through its own factors.
+Workload (the precision configuration at full size): the 2D Helmholtz kernel
+exp(-i k r)/r between two parallel unit segments at distance 1, n = m = 16384
+points, 8 points per wavelength, entries from the kernel's closed form
+(formed once per factorization into complex64 entry images of A and A^H, then
+streamed by every sketch), leaf 16 (L = 10), tol 1e-6, p = 2, r0 = 16, seed 0.
 
 One step = one pass of the whole hot path: bf_factor (sketch RNG, sketch
 products, adaptive leaf bases, peeling, batched QR, B least squares) in the
-mixed precision form, then bf_apply of 64 right-hand sides and the sketch
-error of Sec. 7.  `value` is the factor time in seconds (device-timed with
-CUDA events on the launching stream, L2 flushed before every step by writing
-a 512 MB buffer); the line also reports the plain FP64 factor time, apply
-GB/s, the roofline of the dominant kernel and the oracle timed on the host.
+mixed form -- complex64 sketches and peeling on the tensor cores, pivoted QR,
+truncation and the B least squares in FP64 -- then bf_apply of 64
+right-hand sides and the sketch error of Sec. 7.  `value` is the factor time
+in seconds (device-timed with CUDA events on the launching stream, L2 flushed
+before every step by writing a 512 MB buffer); the line also reports the
+plain FP64 factor time, the float-float-QR variant, apply GB/s, the roofline
+of the dominant kernel and the FP64 oracle timed on the host at the same size.
 """
 from __future__ import annotations
 
@@ -47,8 +46,11 @@ R0 = 16
 # polynomial sin/cos 9, quadrant 6, scaling 2
 ALU_OPS_PER_ENTRY = 71
 # DRAM bytes (read + write) of one sketch_img_kernel<48> launch at n = 8192
-# (the image profile case), from ncu; the image read once, X and Y
+# (the image profile case), from ncu; the image read once, X and Y.  Valid
+# only for the kernel source it was captured on (SHA-256 prefix below); after
+# any change to that file the line reports traffic null until a new capture.
 IMG_TRAFFIC_N8192 = 541691392 + 6331136
+IMG_TRAFFIC_SOURCE_SHA = "855dbb3477a2674a"
 
 
 def measured_peaks():
@@ -101,20 +103,40 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_oracle_sample(n_sample: int = 2048):
-    """The oracle (as it stands) on the same workload at n_sample points,
-    scaled to n = 16384 by the paper's O(n^1.5 log n) cost (Sec. 4.5)."""
+def img_traffic_valid() -> bool:
+    """Whether the image kernel's source is the one the DRAM traffic was
+    captured on."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_2002_03400_gb300", "csrc", "k_sketch_tc.cu")
+    with open(src, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16] == IMG_TRAFFIC_SOURCE_SHA
+
+
+def oracle_factor_seconds(n: int = N) -> float:
+    """Wall time of one oracle factorization (plain FP64 numpy, as it stands)
+    of the benchmark workload at n points: Alg. 2 with the kernel formed on
+    the fly by the oracle's black box, the same leaf, tol, p and r0."""
     from oracle import butterfly as ob
     from oracle import operators as oo
     from paper_2002_03400_gb300 import inputs
-    g = inputs.line_pair(n_sample)
+    g = inputs.line_pair(n)
     op = oo.KernelOp(oo.HELMHOLTZ_2D, g.wavenumber, g.tgt, g.src)
-    L = inputs.leaf_levels(n_sample, LEAF)
+    L = inputs.leaf_levels(n, LEAF)
     t0 = time.perf_counter()
     ob.factor(op, g.src, g.tgt, L, TOL, 2, R0, seed=0)
-    dt = time.perf_counter() - t0
-    scale = (N / n_sample) ** 1.5 * (math.log(N) / math.log(n_sample))
-    return dt, dt * scale, os.cpu_count()
+    return time.perf_counter() - t0
+
+
+def bench_config(n: int = N) -> dict:
+    """The workload both arms report (identical dicts at the default size)."""
+    from paper_2002_03400_gb300 import inputs
+    return {"workload": f"helmholtz2d_line_pair_n{n}_kernel", "n": n, "m": n, "leaf": LEAF,
+            "L": inputs.leaf_levels(n, LEAF), "tol": TOL, "p": 2, "r0": R0, "seed": 0, "nrhs": NRHS,
+            "l2": "flushed (512 MB write) before every step"}
+
+
+ORACLE_CORES_NOTE = ("numpy FP64 oracle: its GEMMs use the BLAS thread pool (all cores), its kernel-entry "
+                     "evaluation one thread")
 
 
 def profile_case(args):
@@ -239,7 +261,7 @@ def batched_measure(count: int = 64, reps: int = 2):
     for i, n in enumerate(sizes):
         g = inputs.arc_pair(n, seed=100 + i)
         plans.append(api.Plan(g.src, g.tgt, kernel=g.kernel, wavenumber=g.wavenumber, leaf=32, tol=1e-5,
-                              precision="mixed", seed=i))
+                              precision="mixed", seed=i, qr_fp64=True))
     ops = [api.Operator.kernel(p) for p in plans]
 
     def batched():
@@ -317,7 +339,7 @@ def configs_measure():
     P2 = inputs.cap_points(n, (0.0, 0.0, 0.0), 60.0, axis=(-1.0, 0.0, 0.0))
     P3 = inputs.cap_points(n, (3.0, 0.0, 0.0), 60.0, axis=(-1.0, 0.0, 0.0))
     k = 2.0 * math.pi / (8.0 * math.sqrt(math.pi / n))
-    kw = dict(leaf=64, tol=1e-6, precision="mixed", p=4, r0=64)
+    kw = dict(leaf=64, tol=1e-6, precision="mixed", p=4, r0=64, qr_fp64=True)
     pk1 = api.Plan(P1, P2, kernel="helmholtz3d", wavenumber=k, **kw)
     pk2 = api.Plan(P2, P3, kernel="helmholtz3d", wavenumber=k, **kw)
     ok1, ok2 = api.Operator.kernel(pk1), api.Operator.kernel(pk2)
@@ -347,25 +369,36 @@ def max_over_ranks(values, dist=None, device="cpu"):
 
 
 def run_reference(args):
-    """--impl reference: the FP64 oracle on the host cores, bounded sample
-    (rank 0 only under torchrun; the other ranks exit without work)."""
+    """--impl reference: the FP64 oracle on the host cores, timed on the
+    benchmark workload itself (n = 16384; rank 0 only under torchrun, the
+    other ranks exit without work).  Warm-up steps are small untimed oracle
+    runs (n = 256: imports, BLAS threads, page-in).  Each timed step is one
+    full oracle factorization (minutes); the arm runs as many of the
+    requested steps as fit in BF_REFERENCE_BUDGET_S seconds (default 600,
+    at least one) and prints the number it ran."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    # BF_REFERENCE_N: a smaller size for tests of this host path only
+    n_ref = int(os.environ.get("BF_REFERENCE_N", str(N)))
     for _ in range(args.warmup):   # untimed
-        cpu_oracle_sample(256)
+        oracle_factor_seconds(256)
+    budget = float(os.environ.get("BF_REFERENCE_BUDGET_S", "600"))
     samples = []
-    for _ in range(args.steps):
-        raw, scaled, cores = cpu_oracle_sample(1024)
-        samples.append(scaled)
+    t_start = time.perf_counter()
+    while len(samples) < args.steps:
+        samples.append(oracle_factor_seconds(n_ref))
+        spent = time.perf_counter() - t_start
+        if spent + samples[-1] > budget:
+            break
     v = float(np.mean(samples))
     line = {"impl": "reference", "metric": "factor time (s)", "value": v, "unit": "s",
-            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
-            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
-            "data": "synthetic",
-            "config": {"workload": "helmholtz2d_line_pair_n16384_kernel", "n": N, "leaf": LEAF, "tol": TOL},
+            "n_gpus": args.gpus, "steps": len(samples), "steps_requested": args.steps, "warmup": args.warmup,
+            "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c128", "data": "synthetic", "config": bench_config(n_ref),
             "cpu_baseline": {"kind": "oracle", "value": v, "unit": "s", "cores": os.cpu_count(),
-                             "sample": "oracle factorization at n=1024 per step, scaled to n=16384 by n^1.5 log n"},
+                             "sample": f"{len(samples)} full oracle factorization(s) of the benchmark workload "
+                                       f"(n = {n_ref}), each timed; {ORACLE_CORES_NOTE}"},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -405,8 +438,10 @@ def main():
 
     stream = torch.cuda.current_stream()
     g = inputs.line_pair(N)
+    # the measured form: complex64 sketches and peeling, FP64 pivoted QR,
+    # truncation and B least squares
     plan_mx = api.Plan(g.src, g.tgt, kernel="helmholtz2d", wavenumber=g.wavenumber, leaf=LEAF, tol=TOL,
-                       precision="mixed", r0=R0)
+                       precision="mixed", r0=R0, qr_fp64=True)
     plan_64 = api.Plan(g.src, g.tgt, kernel="helmholtz2d", wavenumber=g.wavenumber, leaf=LEAF, tol=TOL,
                        precision="fp64", r0=R0)
     op_mx = api.Operator.kernel(plan_mx)
@@ -485,22 +520,41 @@ def main():
     gbs32, t32, b32 = apply_gbs(F, x32)
     gbs64, t64, b64 = apply_gbs(F64, x)
 
-    # the mixed path with its pivoted QR and truncation in FP64
-    # (bf_options.qr_fp64) instead of float-float: factor time and error
-    plan_q = api.Plan(g.src, g.tgt, kernel="helmholtz2d", wavenumber=g.wavenumber, leaf=LEAF, tol=TOL,
-                      precision="mixed", r0=R0, qr_fp64=True)
-    op_q = api.Operator.kernel(plan_q)
-    q_s = []
-    for _ in range(3):
-        flush.fill_(1.0)
-        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        q0.record(stream)
-        Fq = api.Factorization.factor(plan_q, op_q)
-        q1.record(stream)
-        torch.cuda.synchronize()
-        q_s.append(q0.elapsed_time(q1) / 1e3)
-    qr64 = {"factor_s": float(np.mean(q_s[1:])),
-            "sketch_error": Fq.error(op_q, 16, seed=7, dtype=torch.complex64)}
+    # variants of the same factorization, each timed like the steps (3 runs,
+    # the first discarded): the pivoted QR and truncation in float-float
+    # (~2^-46, on the FP32 pipe) instead of FP64; and Alg. 2's initial rank
+    # guess r0 = 4 (the paper's value) instead of 16, which must give the
+    # same factorization (leaf passes append columns of one counter-based
+    # stream, so the final leaf sketch is the same)
+    def timed_factor(plan, op):
+        out = []
+        F = None
+        for _ in range(3):
+            flush.fill_(1.0)
+            q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            q0.record(stream)
+            F = api.Factorization.factor(plan, op)
+            q1.record(stream)
+            torch.cuda.synchronize()
+            out.append(q0.elapsed_time(q1) / 1e3)
+        return float(np.mean(out[1:])), F
+
+    plan_ff = api.Plan(g.src, g.tgt, kernel="helmholtz2d", wavenumber=g.wavenumber, leaf=LEAF, tol=TOL,
+                       precision="mixed", r0=R0)
+    op_ff = api.Operator.kernel(plan_ff)
+    t_ff, Fff = timed_factor(plan_ff, op_ff)
+    qr_ff = {"factor_s": t_ff, "sketch_error": Fff.error(op_ff, 16, seed=7, dtype=torch.complex64),
+             "dtype": "c64 products, float-float (~2^-46) QR and truncation, FP64 B"}
+    plan_r4 = api.Plan(g.src, g.tgt, kernel="helmholtz2d", wavenumber=g.wavenumber, leaf=LEAF, tol=TOL,
+                       precision="mixed", r0=4, qr_fp64=True)
+    t_r4, F4 = timed_factor(plan_r4, api.Operator.kernel(plan_r4))
+    same_ranks = all(np.array_equal(F4.ranks(0, j), F.ranks(0, j)) for j in range(plan_mx.lm + 1)) and all(
+        np.array_equal(F4.ranks(1, j), F.ranks(1, j)) for j in range(plan_mx.lm, plan_mx.L + 1))
+    r0_4 = {"factor_s": t_r4, "same_ranks_as_r0_16": bool(same_ranks),
+            "same_apply_as_r0_16": bool(same_ranks and torch.equal(F4.apply(x32), F.apply(x32))),
+            "black_box_columns": [F4.info()["cols_N"], F4.info()["cols_T"]],
+            "black_box_columns_r0_16": [F.info()["cols_N"], F.info()["cols_T"]]}
+    del F4, Fff
 
     # roofline of the dominant kernel of the factorization: the sketch
     # product fed by the complex64 entry image (sketch_img_kernel), one
@@ -596,13 +650,14 @@ def main():
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "c64+f64",
+        "dtype_detail": "complex64 sketch products and peeling (tensor cores, exact three-way bf16 split, "
+                        "FP32 accumulation), FP64 pivoted QR, truncation and B least squares",
         "data": "synthetic",
-        "config": {"workload": "helmholtz2d_line_pair_n16384_kernel", "n": N, "m": N, "leaf": LEAF,
-                   "L": plan_mx.L, "tol": TOL, "p": 2, "r0": R0, "precision": "mixed", "nrhs": NRHS,
-                   "l2": "flushed (512 MB write) before every step"},
+        "config": bench_config(),
         "factor_s_mixed": float(np.mean(fac_s)),
         "factor_s_fp64": fp64_factor_s,
-        "mixed_with_fp64_qr": qr64,
+        "mixed_with_float_float_qr": qr_ff,
+        "r0_4": r0_4,
         "sketch_error_mixed": float(np.mean(errs)),
         "sketch_error_fp64": err64,
         "apply_gbs_c64": gbs32,
@@ -620,10 +675,11 @@ def main():
                                "bf16 split, B parts stacked along N)", "bound": "hbm",
                      "achieved": img_bytes / t_img / 1e9, "peak": peaks.get("hbm_gbs", 6800.0), "unit": "GB/s",
                      "frac": img_bytes / t_img / 1e9 / peaks.get("hbm_gbs", 6800.0),
-                     "traffic": IMG_TRAFFIC_N8192 * (N / 8192) ** 2,
-                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch at "
-                                       "n = 8192 (profiles/sketch_img_kernel_helmholtz2d_n8192.md), scaled "
-                                       "by the entry count to n = 16384",
+                     "traffic": IMG_TRAFFIC_N8192 * (N / 8192) ** 2 if img_traffic_valid() else None,
+                     "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch at "
+                                        "n = 8192, scaled by the entry count to n = 16384"
+                                        if img_traffic_valid() else
+                                        "null: the kernel source changed since the last ncu capture"),
                      "peak_source": peak_src + " (burst copy)",
                      "work": f"8 B per entry of the m=n={N} image + the {kw}-column X and Y, once each; "
                              "the timed product is 3 launches (B operand, image sketch, split-K reduce)",
@@ -653,9 +709,12 @@ def main():
                                "work": "factor entries + 64 input and 64 output columns, once each"}},
     }
     if rank == 0 and not args.no_cpu:
-        raw, scaled, cores = cpu_oracle_sample()
-        line["cpu_baseline"] = {"value": scaled, "unit": "s", "cores": cores, "kind": "oracle",
-                                "sample": f"oracle factorization at n=2048 ({raw:.1f} s), scaled to n=16384 by n^1.5 log n"}
+        # the oracle as it stands, once, on the benchmark workload itself
+        # (after the GPU work: nothing else runs on the host meanwhile)
+        t_or = oracle_factor_seconds(N)
+        line["cpu_baseline"] = {"value": t_or, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"one full oracle factorization of the benchmark workload (n = {N}), "
+                                          f"timed; {ORACLE_CORES_NOTE}"}
     if rank == 0:
         print(json.dumps(line))
     if dist:

@@ -87,6 +87,24 @@ typedef struct {
   size_t mem_cap;      /* device-byte cap per handle, 0 = none              */
   int qr_fp64;         /* MIXED only: 1 = pivoted QR and truncation in FP64
                           instead of float-float (default 0)                */
+  int hybrid_level;    /* level l of B in eq. hybrid_butterfly_mat: -1 (default)
+                          = l_m = floor(L/2), Alg. 2's hybrid form; any
+                          0 <= l <= L-1 runs the same loops with W levels
+                          1..l and R levels L-1..l.  l = 0 is the
+                          column-wise factorization of Sec. 3.3.1 (its outer
+                          factor kept as B^0 V^0^H); the row-wise one of
+                          Sec. 3.3.2 is l = 0 applied to A^T            */
+  int accept_retries;  /* a-posteriori acceptance instead of trusting the
+                          heuristic stop of the leaf loops (Sec. 4.2): 0
+                          (default) = off; t > 0: after Alg. 2 the sketch
+                          error of Sec. 7 (16 fresh test columns, seed
+                          1009 + attempt) must be <= 2 sqrt(L+2) tol, else
+                          the factorization is redone with r0 doubled, at
+                          most t times, then BF_ENOTCONVERGED            */
+  int leaf_passes;     /* cap on the passes of each adaptive leaf loop: 0
+                          (default) = none; after that many passes the loop
+                          stops as if converged (bounds the black-box work
+                          of the leaf loops; accept_retries then decides) */
 } bf_options;
 
 /* Fills *opt with the defaults above. */
@@ -288,6 +306,11 @@ int bf_ranks(bf_fact F, int side, int level, int32_t* out);
 int bf_fact_info(bf_fact F, int64_t* stored_entries, int64_t* cols_N,
                  int64_t* cols_T, double* factor_seconds);
 
+/* A-posteriori acceptance record of bf_factor (bf_options.accept_retries;
+ * any pointer may be NULL): factorizations run (1 without the check), the
+ * r0 of the accepted one, and its sketch error (-1 without the check). */
+int bf_fact_accept(bf_fact F, int* attempts, int* r0_used, double* sketch_error);
+
 /* Import a factorization from host blocks (exactly-butterfly operators).
  * rV: (l_m+1) x 2^L ranks of the row bases at levels 0..l_m;
  * rU: (L-l_m+1) x 2^L ranks of the column bases at levels l_m..L.
@@ -332,6 +355,20 @@ int bf_set_sketch_engine(int engine);
  * on = 0 -- entries formed on the fly in every sketch.  Errors: BF_EINVAL
  * unless on is 0 or 1.  Not thread-safe against running factorizations. */
 int bf_set_entry_images(int on);
+
+/* Failure path of the tensor-core kernels' bounded waits, exercised without
+ * a fault.  Every mbarrier wait in those kernels gives up after 1 s, sets a
+ * device flag, frees its tensor memory and returns; the host then reports
+ * BF_ETIMEOUT.  This call lowers the limit to limit_ns (0 < limit_ns <= 1e9)
+ * for one launch of a one-warp kernel that waits, through the same wait
+ * routine, on an mbarrier that nothing completes, restores the limit,
+ * synchronizes `stream` and returns the status: BF_ETIMEOUT is the designed
+ * outcome (the wait gave up and the kernel returned; the context stays
+ * usable), BF_OK would mean the wait did not give up.  BF_EINVAL for a limit
+ * out of range; BF_ETIMEOUT without running if an earlier wait had already
+ * given up.  Diagnostic; not thread-safe against running factorizations
+ * (they would see the lowered limit). */
+int bf_debug_wait_timeout(uint64_t limit_ns, void* stream);
 
 /* ------------------------------------------------------------- common -- */
 /* Frees a bf_plan, bf_fact, bf_operator or bf_applier (NULL-safe). */

@@ -33,7 +33,8 @@ class BFError(RuntimeError):
 
 class Options(C.Structure):
     _fields_ = [("p", C.c_int), ("r0", C.c_int), ("r_max", C.c_int), ("seed", C.c_uint64),
-                ("precision", C.c_int), ("mem_cap", C.c_size_t), ("qr_fp64", C.c_int)]
+                ("precision", C.c_int), ("mem_cap", C.c_size_t), ("qr_fp64", C.c_int),
+                ("hybrid_level", C.c_int), ("accept_retries", C.c_int), ("leaf_passes", C.c_int)]
 
 
 class KernelDesc(C.Structure):
@@ -87,6 +88,8 @@ def lib():
         "bf_applier_create": (i32, [vp, i32, i64, i32, C.POINTER(vp)]),
         "bf_applier_run": (i32, [vp, vp, i64, vp, i64, vp]),
         "bf_gaussian": (i32, [C.c_uint64, C.c_uint32, i64, i64, i64, i64, vp, i64, i32, vp]),
+        "bf_fact_accept": (i32, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(dbl)]),
+        "bf_debug_wait_timeout": (i32, [C.c_uint64, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -104,7 +107,7 @@ def exported_symbols():
             "bf_factor_batch", "bf_apply",
             "bf_apply_T", "bf_apply_noalloc", "bf_ranks", "bf_fact_info", "bf_fact_import", "bf_fact_export", "bf_error",
             "bf_free", "bf_gaussian", "bf_set_sketch_engine", "bf_set_entry_images", "bf_launch_count", "bf_apply_tune",
-            "bf_applier_create", "bf_applier_run"]
+            "bf_applier_create", "bf_applier_run", "bf_fact_accept", "bf_debug_wait_timeout"]
 
 
 def launch_count() -> int:
@@ -124,6 +127,13 @@ def set_entry_images(on: bool):
     kernel operator forms its entries once, bf16-split, and every sketch reads
     them) or off (entries formed on the fly in every sketch)."""
     check(lib().bf_set_entry_images(1 if on else 0))
+
+
+def debug_wait_timeout(limit_ns: int, stream=None) -> int:
+    """Status of one bounded wait that nothing completes, run with its limit
+    lowered to limit_ns (bf_debug_wait_timeout): -6 (BF_ETIMEOUT) is the
+    designed outcome."""
+    return int(lib().bf_debug_wait_timeout(int(limit_ns), _stream(stream)))
 
 
 def check(rc: int):
@@ -185,7 +195,7 @@ class Plan(_Handle):
 
     def __init__(self, src=None, tgt=None, n=None, m=None, kernel="none", wavenumber=0.0, leaf=16,
                  tol=1e-6, p=2, r0=4, r_max=1024, seed=0, precision="fp64", mem_cap=0,
-                 qr_fp64=False):
+                 qr_fp64=False, hybrid_level=-1, accept_retries=0, leaf_passes=0):
         L = lib()
         opt = Options()
         L.bf_options_default(C.byref(opt))
@@ -193,6 +203,7 @@ class Plan(_Handle):
         opt.precision = PREC[precision] if isinstance(precision, str) else int(precision)
         opt.mem_cap = mem_cap
         opt.qr_fp64 = 1 if qr_fp64 else 0
+        opt.hybrid_level, opt.accept_retries, opt.leaf_passes = hybrid_level, accept_retries, leaf_passes
         kd = KernelDesc(KERNELS[kernel] if isinstance(kernel, str) else int(kernel), float(wavenumber))
         self._keep = []
         if src is not None:
@@ -379,6 +390,12 @@ class Factorization(_Handle):
         s, a, b, t = C.c_int64(), C.c_int64(), C.c_int64(), C.c_double()
         check(lib().bf_fact_info(self._h, C.byref(s), C.byref(a), C.byref(b), C.byref(t)))
         return {"stored_entries": s.value, "cols_N": a.value, "cols_T": b.value, "seconds": t.value}
+
+    def accept_info(self) -> dict:
+        """A-posteriori acceptance record (bf_fact_accept)."""
+        a, r, e = C.c_int(), C.c_int(), C.c_double()
+        check(lib().bf_fact_accept(self._h, C.byref(a), C.byref(r), C.byref(e)))
+        return {"attempts": a.value, "r0": r.value, "sketch_error": e.value}
 
     def export_stage(self, stage: int) -> np.ndarray:
         nb = C.c_size_t(0)

@@ -416,6 +416,86 @@ unsigned long long launches_so_far() { return g_launches.load(std::memory_order_
 
 using namespace bf;
 
+namespace bf {
+
+// Sketch error of Sec. 7 (eq. error): ||A W - F W||_F / ||A W||_F with W the
+// counter-based Gaussian test matrix (stream 5 << 8, user-order rows).
+int sketch_error(Fact* f, Operator* A, int ncols, uint64_t seed, int dtype, cudaStream_t s, double* err) {
+  const int64_t n = f->n, m = f->m;
+  const size_t es = elem_bytes(dtype);
+  DevBuf buf;
+  BF_TRY(buf.alloc(&f->mem, (n + 2 * m) * ncols * es + 16, s));
+  char* W = (char*)buf.p;
+  char* AW = W + n * ncols * es;
+  char* FW = AW + m * ncols * es;
+  double* red = (double*)(FW + m * ncols * es);
+  int rc = launch_gaussian(seed, 5u << 8, 0, n, 0, ncols, W, n, dtype, s);
+  if (!rc) rc = A->apply(BF_OP_N, ncols, W, n, AW, m, dtype, s);
+  if (!rc) rc = apply_fact(f, BF_OP_N, ncols, W, n, FW, m, dtype, s, false);
+  if (!rc) rc = launch_diff_norms(AW, FW, m, ncols, m, m, dtype, red, s);
+  double h[2] = {0, 0};
+  if (!rc && cudaMemcpyAsync(h, red, 16, cudaMemcpyDeviceToHost, s) != cudaSuccess) rc = fail(BF_ECUDA, "copy");
+  if (!rc && cudaStreamSynchronize(s) != cudaSuccess) rc = fail(BF_ECUDA, "sync");
+  buf.release(s);
+  if (rc) return rc;
+  *err = h[1] > 0 ? std::sqrt(h[0] / h[1]) : 0.0;
+  return BF_OK;
+}
+
+void destroy_fact(Fact* F) {
+  if (!F) return;
+  cudaDeviceSynchronize();
+  for (auto& S : F->st) S.d64.release(nullptr), S.d32.release(nullptr);
+  for (auto& a : F->ap)
+    for (auto& b : a) b.tasks.release(nullptr);
+  delete F;
+}
+
+// Alg. 2, then (bf_options.accept_retries > 0) the a-posteriori acceptance:
+// the sketch error with 16 fresh test columns (seed 1009 + attempt, in the
+// factorization's working precision) must be within the Thm 5.3 bound
+// 2 sqrt(L+2) tol; otherwise Alg. 2 is redone with r0 doubled.
+int factor_accepted(Plan* P, Operator* A, cudaStream_t s, Fact** out) {
+  *out = nullptr;
+  const int retries = P->opt.accept_retries;
+  const int r0 = P->opt.r0;
+  const int dtype = P->opt.precision == BF_PREC_MIXED ? BF_C64 : BF_C128;
+  const double bound = 2.0 * std::sqrt((double)P->L + 2.0) * P->tol;
+  int r = r0;
+  for (int t = 0;; ++t) {
+    Fact* F = nullptr;
+    P->opt.r0 = r;   // the plan is used by one thread at a time
+    int rc = factor(P, A, s, &F);
+    P->opt.r0 = r0;
+    if (rc) return rc;
+    F->attempts = t + 1;
+    F->r0_used = r;
+    if (retries <= 0) {
+      *out = F;
+      return BF_OK;
+    }
+    double e = 0.0;
+    rc = sketch_error(F, A, 16, 1009ull + (uint64_t)t, dtype, s, &e);
+    if (rc) {
+      destroy_fact(F);
+      return rc;
+    }
+    F->accept_err = e;
+    if (e <= bound) {
+      *out = F;
+      return BF_OK;
+    }
+    destroy_fact(F);
+    if (t >= retries || 2 * (int64_t)r > P->opt.r_max)
+      return fail(BF_ENOTCONVERGED, "sketch error " + std::to_string(e) + " above the bound " + std::to_string(bound) +
+                                        " after " + std::to_string(t + 1) + " factorizations (last r0 " +
+                                        std::to_string(r) + ")");
+    r *= 2;
+  }
+}
+
+}  // namespace bf
+
 extern "C" {
 
 void bf_options_default(bf_options* o) {
@@ -427,6 +507,9 @@ void bf_options_default(bf_options* o) {
   o->precision = BF_PREC_FP64;
   o->mem_cap = 0;
   o->qr_fp64 = 0;
+  o->hybrid_level = -1;
+  o->accept_retries = 0;
+  o->leaf_passes = 0;
 }
 
 const char* bf_last_error(void) { return g_err.c_str(); }
@@ -446,17 +529,21 @@ int bf_plan_create(const double* src, int64_t n, const double* tgt, int64_t m, i
   if (o.p < 0 || o.r0 < 1 || o.r_max < o.r0) return fail(BF_EINVAL, "bad p, r0 or r_max");
   if (o.precision != BF_PREC_FP64 && o.precision != BF_PREC_MIXED) return fail(BF_EINVAL, "bad precision");
   if (o.qr_fp64 != 0 && o.qr_fp64 != 1) return fail(BF_EINVAL, "bad qr_fp64");
+  if (o.accept_retries < 0 || o.accept_retries > 30 || o.leaf_passes < 0)
+    return fail(BF_EINVAL, "bad accept_retries or leaf_passes");
   int L = 0;
   const int64_t mx = std::max(n, m);
   while ((mx + ((int64_t)1 << L) - 1) >> L > leaf) ++L;
   if (L < 1) return fail(BF_EINVAL, "Alg. 2 needs at least one level below the root (L >= 1)");
   if (L > 24) return fail(BF_EINVAL, "tree too deep");
+  if (o.hybrid_level < -1 || o.hybrid_level > L - 1)
+    return fail(BF_EINVAL, "hybrid_level must be -1 or in [0, L-1] (L = " + std::to_string(L) + ")");
   Plan* P = new Plan();
   P->n = n;
   P->m = m;
   P->dim = pts ? dim : 0;
   P->L = L;
-  P->lm = L / 2;
+  P->lm = o.hybrid_level < 0 ? L / 2 : o.hybrid_level;
   P->leaf = leaf;
   P->tol = tol;
   P->opt = o;
@@ -738,7 +825,7 @@ int bf_factor(bf_plan plan, bf_operator A, void* stream, bf_fact* out) {
     op = tmp->impl;
   }
   Fact* F = nullptr;
-  const int rc = factor(hp->impl, op, user_stream(stream), &F);
+  const int rc = factor_accepted(hp->impl, op, user_stream(stream), &F);
   if (tmp) bf_free(tmp);
   if (rc) return rc;
   *out = new bf_fact_s{KIND_FACT, F};
@@ -954,28 +1041,19 @@ int bf_error(bf_fact F, bf_operator A, int ncols, uint64_t seed, int dtype, void
   auto* ho = check<bf_operator_s>(A, KIND_OP);
   if (!hf || !ho || !err || ncols < 1) return fail(BF_EINVAL, "bad arguments");
   if (dtype != BF_C64 && dtype != BF_C128) return fail(BF_EINVAL, "bad dtype");
-  Fact* f = hf->impl;
-  cudaStream_t s = user_stream(stream);
-  const int64_t n = f->n, m = f->m;
-  const size_t es = elem_bytes(dtype);
-  DevBuf buf;
-  BF_TRY(buf.alloc(&f->mem, (n + 2 * m) * ncols * es + 16, s));
-  char* W = (char*)buf.p;
-  char* AW = W + n * ncols * es;
-  char* FW = AW + m * ncols * es;
-  double* red = (double*)(FW + m * ncols * es);
-  int rc = launch_gaussian(seed, 5u << 8, 0, n, 0, ncols, W, n, dtype, s);
-  if (!rc) rc = ho->impl->apply(BF_OP_N, ncols, W, n, AW, m, dtype, s);
-  if (!rc) rc = apply_fact(f, BF_OP_N, ncols, W, n, FW, m, dtype, s, false);
-  if (!rc) rc = launch_diff_norms(AW, FW, m, ncols, m, m, dtype, red, s);
-  double h[2] = {0, 0};
-  if (!rc && cudaMemcpyAsync(h, red, 16, cudaMemcpyDeviceToHost, s) != cudaSuccess) rc = fail(BF_ECUDA, "copy");
-  if (!rc && cudaStreamSynchronize(s) != cudaSuccess) rc = fail(BF_ECUDA, "sync");
-  buf.release(s);
-  if (rc) return rc;
-  *err = h[1] > 0 ? std::sqrt(h[0] / h[1]) : 0.0;
+  return sketch_error(hf->impl, ho->impl, ncols, seed, dtype, user_stream(stream), err);
+}
+
+int bf_fact_accept(bf_fact F, int* attempts, int* r0_used, double* err) {
+  auto* h = check<bf_fact_s>(F, KIND_FACT);
+  if (!h) return fail(BF_EINVAL, "not a factorization");
+  if (attempts) *attempts = h->impl->attempts;
+  if (r0_used) *r0_used = h->impl->r0_used;
+  if (err) *err = h->impl->accept_err;
   return BF_OK;
 }
+
+int bf_debug_wait_timeout(uint64_t limit_ns, void* stream) { return wait_probe(limit_ns, user_stream(stream)); }
 
 void bf_free(void* handle) {
   if (!handle) return;
@@ -992,12 +1070,7 @@ void bf_free(void* handle) {
     delete h;
   } else if (kind == KIND_FACT) {
     auto* h = (bf_fact_s*)handle;
-    Fact* F = h->impl;
-    cudaDeviceSynchronize();
-    for (auto& S : F->st) S.d64.release(nullptr), S.d32.release(nullptr);
-    for (auto& a : F->ap)
-      for (auto& b : a) b.tasks.release(nullptr);
-    delete F;
+    destroy_fact(h->impl);
     h->kind = 0;
     delete h;
   } else if (kind == KIND_APPLIER) {

@@ -204,6 +204,8 @@ struct Fact {
   std::vector<std::vector<int32_t>> rU;  // index j - lm for levels lm..L
   int64_t cols_N = 0, cols_T = 0;
   double seconds = 0;
+  int attempts = 1, r0_used = 0;     // a-posteriori acceptance record (bf_fact_accept)
+  double accept_err = -1.0;
   MemTracker mem;
   ApplyPlan ap[2][2];                // [op N / C][dtype C64 / C128]
   int stage_V0() const { return 0; }
@@ -372,6 +374,9 @@ bool sketch_tc_applies(const std::vector<SketchJob>& jobs);
 int launch_sketch_jobs_tc(const std::vector<SketchJob>& jobs, MemTracker* mt, cudaStream_t s);
 // BF_ETIMEOUT if a tensor-core kernel's bounded wait gave up since the last reset
 int tc_status(bool reset);
+// runs one bounded wait that nothing completes, with the limit lowered to
+// limit_ns; BF_ETIMEOUT when it gave up and returned (the designed outcome)
+int wait_probe(uint64_t limit_ns, cudaStream_t s);
 // Entry images (see SketchJob::img): bytes for an M x K orientation, and the
 // launch that fills both of kernel job jn (op N: M = m targets, Ktot = n
 // sources; X, Y and groups ignored) in one pass: imgN (m x n,
@@ -448,6 +453,10 @@ void apply_tasks_host(const Fact* F, int opC, int dtype, ApplyPlan& ap, std::vec
 int apply_fact(Fact* F, int op, int64_t nrhs, const void* x, int64_t ldx,
                void* y, int64_t ldy, int dtype, cudaStream_t s, bool tree_order);
 int factor(Plan* P, Operator* A, cudaStream_t s, Fact** out);
+// factor() followed by the a-posteriori acceptance of bf_options.accept_retries
+int factor_accepted(Plan* P, Operator* A, cudaStream_t s, Fact** out);
+int sketch_error(Fact* f, Operator* A, int ncols, uint64_t seed, int dtype, cudaStream_t s, double* err);
+void destroy_fact(Fact* F);
 // Alg. 2 for `count` operators in lockstep (one launch per kernel per phase
 // across all of them); all plans must share one precision.
 int factor_batch(int count, Plan* const* P, Operator* const* A, cudaStream_t s, Fact** out);

@@ -51,7 +51,7 @@ struct OpState {
   Fact* F;
   int L, lm, nb;
   // leaf loops
-  int r = 0, k = 0;
+  int r = 0, k = 0, passes = 0;
   int64_t kcap = 0;
   bool done = false;
   DevBuf Y;
@@ -313,6 +313,7 @@ int leaf_phase(Batch& B, bool Vside) {
   for (auto& o : B.ops) {
     o.r = o.P->opt.r0;
     o.kcap = 0;
+    o.passes = 0;
     o.done = false;
   }
   int rc = BF_OK;
@@ -367,7 +368,9 @@ int leaf_phase(Batch& B, bool Vside) {
       int maxleaf = 0;
       for (int b = 0; b < nb; ++b) maxleaf = std::max<int>(maxleaf, (int)(off[b + 1] - off[b]));
       const int maxr = *std::max_element(o->ranks.begin(), o->ranks.end());
-      if (o->r > maxr || o->k >= maxleaf) {
+      ++o->passes;
+      const bool capped = P->opt.leaf_passes > 0 && o->passes >= P->opt.leaf_passes;
+      if (o->r > maxr || o->k >= maxleaf || capped) {
         o->done = true;
         o->Y.release(B.s);
         if (Vside)
@@ -734,6 +737,8 @@ int factor_batch(int count, Plan* const* P, Operator* const* A, cudaStream_t s, 
       return fail(BF_EINVAL, "operator shape does not match its plan (batch entry " + std::to_string(i) + ")");
     if (P[i]->opt.precision != prec) return fail(BF_EINVAL, "all plans of a batch must share one precision");
     if (P[i]->opt.qr_fp64 != P[0]->opt.qr_fp64) return fail(BF_EINVAL, "all plans of a batch must share qr_fp64");
+    if (P[i]->opt.accept_retries > 0 && count > 1)
+      return fail(BF_EUNSUPPORTED, "a-posteriori acceptance (accept_retries) is a bf_factor option");
   }
   const auto t0 = std::chrono::steady_clock::now();
   Batch B;

@@ -24,10 +24,14 @@
 // reflectors, backwards, one barrier per reflector.
 //
 // The complex128 blocks (and complex64 ones when FP64 is asked for) use the
-// FP64 kernel (qr_kernel): one thread per column, dot products and updates
-// sequential over the rows.  Either
-// kernel keeps its block in shared memory when it fits, else in a per-task
-// global workspace (same code, pointer switch).
+// FP64 kernel (qr64_kernel), laid out like the float-float one: RG lanes per
+// column of the trailing update (rows strided by RG, partial dot products
+// and column norms joined by shuffles), Q formed in place backwards.  The
+// FP64 pipe retires ~2 FMAs per clock per SM on this GPU, so the kernel's
+// time is its FP64 warp instructions: with one thread per column (the first
+// design) each instruction carried ~10 of 32 active lanes.  Either kernel
+// keeps its block in shared memory when it fits, else in a per-task global
+// workspace (same code, pointer switch).
 #include "bf_internal.h"
 #include "cx.cuh"
 #include "ff.cuh"
@@ -37,165 +41,7 @@ namespace bf {
 namespace {
 constexpr size_t QR_SMEM_LIMIT = 200 * 1024;
 constexpr int QR_MAX_THREADS = 256;
-
-__host__ __device__ inline int ld_of(int s) { return s | 1; }
-size_t meta_bytes(int maxK) { return (size_t)(2 * maxK + 8) * sizeof(double); }
-size_t block_bytes(int maxS, int maxK) {
-  // A (ld x k) and Q (ld x min(s,k)) in complex128
-  return (size_t)ld_of(maxS) * (maxK + (maxS < maxK ? maxS : maxK)) * sizeof(double2);
-}
-int threads_for(int maxK) {
-  int t = ((maxK + 31) / 32) * 32;
-  return t > QR_MAX_THREADS ? QR_MAX_THREADS : t;
-}
 }  // namespace
-
-template <typename VIn>
-__global__ void qr_kernel(const QRTask* __restrict__ tasks, int32_t* __restrict__ ranks,
-                          double2* __restrict__ gwork, int64_t work_stride, int maxK, int use_smem) {
-  extern __shared__ double smem_d[];
-  const QRTask t = tasks[blockIdx.x];
-  const int s = t.s, k = t.k, ld = ld_of(s);
-  const int nthr = blockDim.x;
-  double* nrm2 = smem_d;                    // k
-  double* tau = smem_d + maxK;              // k
-  double* misc = smem_d + 2 * maxK;         // [0]=nrm0 [1]=pivot [2]=stop
-  double2* A = use_smem ? (double2*)(smem_d + 2 * maxK + 8) : gwork + blockIdx.x * work_stride;
-  double2* Qs = A + (size_t)ld * k;         // ld x min(s,k)
-  const VIn* in = (const VIn*)t.in;
-
-  for (int idx = threadIdx.x; idx < s * k; idx += nthr) {
-    const int i = idx % s, c = idx / s;
-    A[i + c * ld] = to_d2(in[i + (int64_t)c * t.ldi]);
-  }
-  __syncthreads();
-  for (int c = threadIdx.x; c < k; c += nthr) {
-    double a = 0.0;
-    for (int i = 0; i < s; ++i) {
-      const double2 v = A[i + c * ld];
-      a = fma(v.x, v.x, fma(v.y, v.y, a));
-    }
-    nrm2[c] = a;
-  }
-  __syncthreads();
-
-  const int jmax = min(s, k);
-  int steps = 0;
-  for (int j = 0; j < jmax; ++j) {
-    if (threadIdx.x < 32) {              // pivot: largest trailing norm, ties -> lowest index
-      const int lane = threadIdx.x;
-      double best = -1.0;
-      int bi = k;
-      for (int c = j + lane; c < k; c += 32) {
-        const double v = nrm2[c];
-        if (v > best) best = v, bi = c;
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ob > best || (ob == best && oi < bi)) best = ob, bi = oi;
-      }
-      if (lane == 0) {
-        const double nrm = sqrt(fmax(best, 0.0));
-        if (j == 0) misc[0] = nrm;
-        misc[1] = (double)bi;
-        misc[2] = (nrm == 0.0 || nrm <= t.eps * misc[0]) ? 1.0 : 0.0;
-      }
-    }
-    __syncthreads();
-    if (misc[2] != 0.0) break;
-    const int p = (int)misc[1];
-    if (p != j) {
-      for (int i = threadIdx.x; i < s; i += nthr) {
-        const double2 a = A[i + j * ld];
-        A[i + j * ld] = A[i + p * ld];
-        A[i + p * ld] = a;
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        const double a = nrm2[j];
-        nrm2[j] = nrm2[p];
-        nrm2[p] = a;
-      }
-    }
-    if (threadIdx.x == 0) {              // reflector from column j, rows j..s-1
-      double sq = 0.0;
-      for (int i = j; i < s; ++i) {
-        const double2 v = A[i + j * ld];
-        sq = fma(v.x, v.x, fma(v.y, v.y, sq));
-      }
-      const double nrm = sqrt(sq);
-      const double2 x0 = A[j + j * ld];
-      const double ax0 = hypot(x0.x, x0.y);
-      double px = 1.0, py = 0.0;
-      if (ax0 != 0.0) px = x0.x / ax0, py = x0.y / ax0;
-      const double2 v0 = make_double2(x0.x + px * nrm, x0.y + py * nrm);   // x0 - alpha
-      const double beta = (v0.x * v0.x + v0.y * v0.y) + (sq - ax0 * ax0);  // v^H v
-      A[j + j * ld] = v0;
-      tau[j] = beta > 0.0 ? 2.0 / beta : 0.0;
-    }
-    __syncthreads();
-    const double tj = tau[j];
-    const double2* v = A + j * ld;
-    for (int c = j + 1 + threadIdx.x; c < k; c += nthr) {
-      double2* a = A + c * ld;
-      double wx = 0.0, wy = 0.0;             // w = v^H a
-      for (int i = j; i < s; ++i) {
-        const double2 vi = v[i], ai = a[i];
-        wx = fma(vi.x, ai.x, fma(vi.y, ai.y, wx));
-        wy = fma(vi.x, ai.y, fma(-vi.y, ai.x, wy));
-      }
-      wx *= tj;
-      wy *= tj;
-      double n2 = 0.0;
-      for (int i = j; i < s; ++i) {
-        const double2 vi = v[i];
-        double2 ai = a[i];
-        ai.x = fma(-vi.x, wx, fma(vi.y, wy, ai.x));
-        ai.y = fma(-vi.x, wy, fma(-vi.y, wx, ai.y));
-        a[i] = ai;
-        if (i > j) n2 = fma(ai.x, ai.x, fma(ai.y, ai.y, n2));
-      }
-      nrm2[c] = n2;
-    }
-    ++steps;
-    __syncthreads();
-  }
-  const int rank = steps > 0 ? steps : 1;
-  if (threadIdx.x == 0) ranks[blockIdx.x] = rank;
-
-  // Q e_c = H_0 ... H_c e_c (H_j leaves e_c unchanged for j > c); one column per thread
-  for (int c = threadIdx.x; c < rank; c += nthr) {
-    double2* q = Qs + c * ld;
-    for (int i = 0; i < s; ++i) q[i] = make_double2(i == c ? 1.0 : 0.0, 0.0);
-    for (int j = min(c, steps - 1); j >= 0; --j) {
-      const double2* vj = A + j * ld;
-      double wx = 0.0, wy = 0.0;
-      for (int i = j; i < s; ++i) {
-        const double2 vi = vj[i], qi = q[i];
-        wx = fma(vi.x, qi.x, fma(vi.y, qi.y, wx));
-        wy = fma(vi.x, qi.y, fma(-vi.y, qi.x, wy));
-      }
-      const double tj = tau[j];
-      wx *= tj;
-      wy *= tj;
-      for (int i = j; i < s; ++i) {
-        const double2 vi = vj[i];
-        double2 qi = q[i];
-        qi.x = fma(-vi.x, wx, fma(vi.y, wy, qi.x));
-        qi.y = fma(-vi.x, wy, fma(-vi.y, wx, qi.y));
-        q[i] = qi;
-      }
-    }
-  }
-  __syncthreads();
-  double2* out = (double2*)t.q;
-  for (int idx = threadIdx.x; idx < s * rank; idx += nthr) {
-    const int i = idx % s, c = idx / s;
-    out[i + (int64_t)c * s] = Qs[i + c * ld];
-  }
-}
 
 // ---------------------------------------------------------------------------
 // complex64 blocks: float-float factorization on the FP32 pipe
@@ -455,6 +301,204 @@ __global__ void qr_ff_kernel(const QRTask* __restrict__ tasks, int32_t* __restri
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// FP64 factorization (complex128 blocks, and complex64 ones on request)
+// ---------------------------------------------------------------------------
+namespace {
+// shared-memory head: squared norms and tau (double each), a stop flag,
+// then two reflector buffers of maxS entries
+__host__ __device__ inline int meta64_head(int maxK) { return (16 * maxK + 64 + 15) & ~15; }
+__host__ __device__ inline int meta64_bytes(int maxS, int maxK) { return meta64_head(maxK) + 32 * maxS; }
+size_t block64_bytes(int maxS, int maxK, int rg) { return (size_t)ld_ff(maxS, rg) * maxK * sizeof(double2); }
+}  // namespace
+
+namespace dev {
+template <int RG>
+__device__ __forceinline__ double group_sum(double a, unsigned gmask) {
+#pragma unroll
+  for (int o = RG / 2; o > 0; o >>= 1) a += __shfl_xor_sync(gmask, a, o);   // every lane gets the same sum
+  return a;
+}
+
+// col <- H col = col - v (tau v^H col) over rows j..s-1 by the RG lanes of one
+// group; UNIT: col is e_j (not read); NORM: squared norm of rows j+1..s-1 of
+// the result to *nrm_out.
+template <int RG, bool NORM, bool UNIT>
+__device__ __forceinline__ void reflect64(double2* __restrict__ col, const double2* __restrict__ v, double tau,
+                                          int j, int s, int g, unsigned gmask, double* nrm_out) {
+  double dr = 0.0, di = 0.0;   // v^H col
+  if (UNIT) {
+    dr = v[j].x;
+    di = -v[j].y;
+  } else {
+    for (int i = j + g; i < s; i += RG) {
+      const double2 a = v[i], b = col[i];
+      dr = fma(a.x, b.x, fma(a.y, b.y, dr));
+      di = fma(a.x, b.y, fma(-a.y, b.x, di));
+    }
+    dr = group_sum<RG>(dr, gmask);
+    di = group_sum<RG>(di, gmask);
+  }
+  const double wr = tau * dr, wi = tau * di;
+  double n = 0.0;
+  for (int i = j + g; i < s; i += RG) {
+    const double2 a = v[i];
+    double2 b = UNIT ? make_double2(i == j ? 1.0 : 0.0, 0.0) : col[i];
+    b.x = fma(-a.x, wr, fma(a.y, wi, b.x));    // re: b - (vx wr - vy wi)
+    b.y = fma(-a.x, wi, fma(-a.y, wr, b.y));   // im: b - (vx wi + vy wr)
+    col[i] = b;
+    if (NORM && i > j) n = fma(b.x, b.x, fma(b.y, b.y, n));
+  }
+  if (NORM) {
+    n = group_sum<RG>(n, gmask);
+    if (g == 0) *nrm_out = n;
+  }
+}
+}  // namespace dev
+
+template <typename VIn, int RG>
+__global__ void qr64_kernel(const QRTask* __restrict__ tasks, int32_t* __restrict__ ranks,
+                            double2* __restrict__ gwork, int64_t work_stride, int maxS, int maxK, int use_smem) {
+  using namespace dev;
+  extern __shared__ double2 smem64[];
+  char* base = (char*)smem64;
+  const QRTask t = tasks[blockIdx.x];
+  const int s = t.s, k = t.k, ld = ld_ff(s, RG);
+  const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31;
+  double* nrm = (double*)base;                                // k squared trailing column norms
+  double* taus = nrm + maxK;                                  // tau_j
+  int* flags = (int*)(base + 16 * maxK);                      // [0] stop
+  double2* vb = (double2*)(base + meta64_head(maxK));         // 2 x maxS reflector buffers
+  double2* A = use_smem ? (double2*)(base + meta64_bytes(maxS, maxK)) : gwork + blockIdx.x * work_stride;
+  const VIn* in = (const VIn*)t.in;
+  const int grp = tid / RG, g = tid % RG, G = nthr / RG;
+  const unsigned gmask = ((1u << RG) - 1u) << (lane & ~(RG - 1));
+  const double2 zero = make_double2(0.0, 0.0);
+
+  for (int idx = tid; idx < s * k; idx += nthr) {
+    const int i = idx % s, c = idx / s;
+    A[i + c * ld] = to_d2(in[i + (int64_t)c * t.ldi]);
+  }
+  __syncthreads();
+  for (int c = grp; c < k; c += G) {
+    double n = 0.0;
+    for (int i = g; i < s; i += RG) {
+      const double2 a = A[i + c * ld];
+      n = fma(a.x, a.x, fma(a.y, a.y, n));
+    }
+    n = group_sum<RG>(n, gmask);
+    if (g == 0) nrm[c] = n;
+  }
+  __syncthreads();
+
+  double nrm0 = 0.0;   // first pivot's norm (lane 0 of warp 0)
+  int steps = 0;
+  const int jmax = min(s, k);
+  for (int j = 0; j < jmax; ++j) {
+    if (tid < 32) {
+      // pivot: largest trailing norm, ties -> lowest index
+      double best = -1.0;
+      int bi = k;
+      for (int c = j + lane; c < k; c += 32) {
+        const double v = nrm[c];
+        if (v > best) best = v, bi = c;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) best = ob, bi = oi;
+      }
+      const int p = bi < k ? bi : j;   // (no finite norm: keep column j)
+      if (p != j) {
+        for (int i = lane; i < s; i += 32) {
+          const double2 a = A[i + j * ld];
+          A[i + j * ld] = A[i + p * ld];
+          A[i + p * ld] = a;
+        }
+        if (lane == 0) {
+          const double a = nrm[j];
+          nrm[j] = nrm[p];
+          nrm[p] = a;
+        }
+      }
+      __syncwarp();
+      double rest = 0.0;   // squared norm of the pivot column below row j
+      for (int i = j + 1 + lane; i < s; i += 32) {
+        const double2 a = A[i + j * ld];
+        rest = fma(a.x, a.x, fma(a.y, a.y, rest));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) rest += __shfl_xor_sync(0xffffffffu, rest, o);
+      if (lane == 0) {
+        const double2 x0 = A[j + j * ld];
+        const double ax2 = fma(x0.x, x0.x, x0.y * x0.y);
+        const double nu = sqrt(ax2 + rest);   // ||x||
+        if (j == 0) nrm0 = nu;
+        const bool stop = !(nu > 0.0) || nu <= t.eps * nrm0;
+        flags[0] = stop ? 1 : 0;
+        if (!stop) {
+          const double ax0 = sqrt(ax2);
+          double vr = nu, vi = 0.0;
+          if (ax0 > 0.0) {   // v0 = x0 - alpha = x0 (1 + ||x|| / |x0|)
+            const double f = 1.0 + nu / ax0;
+            vr = x0.x * f;
+            vi = x0.y * f;
+          }
+          A[j + j * ld] = make_double2(vr, vi);
+          taus[j] = 2.0 / (fma(vr, vr, vi * vi) + rest);   // 2 / (v^H v) from the stored v
+        }
+      }
+    }
+    __syncthreads();
+    if (flags[0]) break;
+    const double tau = taus[j];
+    for (int c = j + 1 + grp; c < k; c += G)
+      reflect64<RG, true, false>(A + c * ld, A + j * ld, tau, j, s, g, gmask, nrm + c);
+    ++steps;
+    __syncthreads();
+  }
+  const int rank = steps > 0 ? steps : 1;
+  if (tid == 0) ranks[blockIdx.x] = rank;
+
+  // Q in place of the reflectors, backwards (as in qr_ff_kernel)
+  if (steps == 0) {
+    for (int i = tid; i < s; i += nthr) A[i] = i == 0 ? make_double2(1.0, 0.0) : zero;
+    __syncthreads();
+  } else {
+    {
+      const int j = steps - 1;
+      double2* dst = vb + (j & 1) * maxS;
+      for (int i = j + tid; i < s; i += nthr) dst[i] = A[i + j * ld];
+    }
+    __syncthreads();
+    for (int j = steps - 1; j >= 0; --j) {
+      const double2* v = vb + (j & 1) * maxS;
+      if (j > 0) {
+        double2* dst = vb + ((j - 1) & 1) * maxS;
+        for (int i = j - 1 + tid; i < s; i += nthr) dst[i] = A[i + (j - 1) * ld];
+      }
+      const double tau = taus[j];
+      for (int c = j + grp; c < rank; c += G) {
+        double2* col = A + c * ld;
+        if (c == j) {
+          for (int i = g; i < j; i += RG) col[i] = zero;
+          reflect64<RG, false, true>(col, v, tau, j, s, g, gmask, nullptr);
+        } else {
+          reflect64<RG, false, false>(col, v, tau, j, s, g, gmask, nullptr);
+        }
+      }
+      __syncthreads();
+    }
+  }
+  double2* out = (double2*)t.q;
+  for (int idx = tid; idx < s * rank; idx += nthr) {
+    const int i = idx % s, c = idx / s;
+    out[i + (int64_t)c * s] = A[i + c * ld];
+  }
+}
+
 namespace {
 template <int RG>
 int launch_qr_ff(const QRTask* d_tasks, int ntasks, int maxS, int maxK, int32_t* d_ranks, void* d_work,
@@ -476,6 +520,36 @@ int launch_qr_ff(const QRTask* d_tasks, int ntasks, int maxS, int maxK, int32_t*
   BF_CUDA_TRY(cudaGetLastError());
   return BF_OK;
 }
+
+template <typename VIn, int RG>
+int launch_qr64(const QRTask* d_tasks, int ntasks, int maxS, int maxK, int32_t* d_ranks, void* d_work,
+                size_t work_bytes, cudaStream_t s) {
+  const size_t blk = block64_bytes(maxS, maxK, RG);
+  const size_t meta = (size_t)meta64_bytes(maxS, maxK);
+  const int use_smem = (blk + meta <= QR_SMEM_LIMIT) ? 1 : 0;
+  if (meta > QR_SMEM_LIMIT) return fail(BF_EINVAL, "QR block too large");
+  if (!use_smem && (d_work == nullptr || work_bytes < blk * (size_t)ntasks))
+    return fail(BF_EINVAL, "QR workspace too small");
+  const size_t smem = meta + (use_smem ? blk : 0);
+  int nthr = ((maxK * RG + 31) / 32) * 32;
+  nthr = nthr > QR_MAX_THREADS ? QR_MAX_THREADS : nthr;
+  BF_CUDA_TRY(cudaFuncSetAttribute(qr64_kernel<VIn, RG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(QR_SMEM_LIMIT + 4096)));
+  note_launch();
+  qr64_kernel<VIn, RG><<<ntasks, nthr, smem, s>>>(d_tasks, d_ranks, (double2*)d_work,
+                                                  (int64_t)(blk / sizeof(double2)), maxS, maxK, use_smem);
+  BF_CUDA_TRY(cudaGetLastError());
+  return BF_OK;
+}
+template <typename VIn>
+int launch_qr64_rg(const QRTask* d_tasks, int ntasks, int maxS, int maxK, int32_t* d_ranks, void* d_work,
+                   size_t work_bytes, cudaStream_t s) {
+  switch (rg_for(maxS)) {
+    case 2: return launch_qr64<VIn, 2>(d_tasks, ntasks, maxS, maxK, d_ranks, d_work, work_bytes, s);
+    case 4: return launch_qr64<VIn, 4>(d_tasks, ntasks, maxS, maxK, d_ranks, d_work, work_bytes, s);
+    default: return launch_qr64<VIn, 8>(d_tasks, ntasks, maxS, maxK, d_ranks, d_work, work_bytes, s);
+  }
+}
 }  // namespace
 
 size_t qr_workspace_bytes(int ntasks, int maxS, int maxK, int in_dtype, bool fp64) {
@@ -484,8 +558,8 @@ size_t qr_workspace_bytes(int ntasks, int maxS, int maxK, int in_dtype, bool fp6
     if (blk + (size_t)meta_ff_bytes(maxS, maxK) <= QR_SMEM_LIMIT) return 0;
     return blk * (size_t)ntasks;
   }
-  const size_t blk = block_bytes(maxS, maxK);
-  if (blk + meta_bytes(maxK) <= QR_SMEM_LIMIT) return 0;
+  const size_t blk = block64_bytes(maxS, maxK, rg_for(maxS));
+  if (blk + (size_t)meta64_bytes(maxS, maxK) <= QR_SMEM_LIMIT) return 0;
   return blk * (size_t)ntasks;
 }
 
@@ -499,25 +573,8 @@ int launch_qr(const QRTask* d_tasks, int ntasks, int maxS, int maxK, int in_dtyp
       default: return launch_qr_ff<8>(d_tasks, ntasks, maxS, maxK, d_ranks, d_work, work_bytes, s);
     }
   }
-  const size_t blk = block_bytes(maxS, maxK);
-  const int use_smem = (blk + meta_bytes(maxK) <= QR_SMEM_LIMIT) ? 1 : 0;
-  const size_t smem = meta_bytes(maxK) + (use_smem ? blk : 0);
-  if (!use_smem && (d_work == nullptr || work_bytes < blk * (size_t)ntasks))
-    return fail(BF_EINVAL, "QR workspace too small");
-  const int64_t stride = (int64_t)(blk / sizeof(double2));
-  const int nthr = threads_for(maxK);
-  note_launch();
-  if (in_dtype == BF_C128) {
-    BF_CUDA_TRY(cudaFuncSetAttribute(qr_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)(QR_SMEM_LIMIT + 4096)));
-    qr_kernel<double2><<<ntasks, nthr, smem, s>>>(d_tasks, d_ranks, (double2*)d_work, stride, maxK, use_smem);
-  } else {
-    BF_CUDA_TRY(cudaFuncSetAttribute(qr_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)(QR_SMEM_LIMIT + 4096)));
-    qr_kernel<float2><<<ntasks, nthr, smem, s>>>(d_tasks, d_ranks, (double2*)d_work, stride, maxK, use_smem);
-  }
-  BF_CUDA_TRY(cudaGetLastError());
-  return BF_OK;
+  if (in_dtype == BF_C128) return launch_qr64_rg<double2>(d_tasks, ntasks, maxS, maxK, d_ranks, d_work, work_bytes, s);
+  return launch_qr64_rg<float2>(d_tasks, ntasks, maxS, maxK, d_ranks, d_work, work_bytes, s);
 }
 
 }  // namespace bf

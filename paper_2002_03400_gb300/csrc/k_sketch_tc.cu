@@ -50,6 +50,8 @@ namespace bf {
 using namespace dev;
 
 __device__ int g_tc_status;   // 1 once a bounded wait has given up
+// limit of every bounded wait (1 s; lowered only by the wait probe below)
+__device__ unsigned long long g_wait_limit_ns = 1000000000ull;
 
 namespace {
 constexpr int TM = 128;            // rows per CTA (MMA M)
@@ -230,12 +232,13 @@ __device__ __forceinline__ bool mbar_try_sleep(uint32_t addr, uint32_t parity, u
   return done != 0;
 }
 // the bounded part of a wait, out of line so that the inlined fast path is
-// one try_wait: false after 1 s, or as soon as *abort is set
+// one try_wait: false after g_wait_limit_ns (1 s), or as soon as *abort is set
 __device__ __noinline__ bool mbar_wait_slow(uint32_t addr, uint32_t parity, const volatile int* abort) {
   const uint64_t t0 = now_ns();
+  const uint64_t limit = *(const volatile unsigned long long*)&g_wait_limit_ns;
   for (;;) {
     if (mbar_try_sleep(addr, parity, 1000000u)) return true;
-    if ((abort && *abort) || now_ns() - t0 > 1000000000ull) return false;
+    if ((abort && *abort) || now_ns() - t0 > limit) return false;
   }
 }
 // waits for the phase of parity `parity` of the mbarrier at addr; the timer
@@ -1644,6 +1647,39 @@ int launch_sketch_jobs_tc(const std::vector<SketchJob>& jobs_in, MemTracker* mt,
   d.release(s);
   bi.release(s);
   return rc;
+}
+
+// The failure path of the bounded waits, exercised without a fault: one
+// warp waits on an mbarrier that nothing arrives at, through the kernels'
+// own wait routine, with the limit lowered to limit_ns; the wait gives up,
+// the device flag is set, the kernel returns and the host reads the status.
+__global__ void wait_probe_kernel() {
+  __shared__ __align__(8) unsigned long long bar;
+  const uint32_t addr = smem_u32(&bar);
+  if (threadIdx.x == 0) {
+    mbar_init(addr, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait(addr, 0)) atomicExch(&g_tc_status, 1);
+}
+
+int wait_probe(uint64_t limit_ns, cudaStream_t s) {
+  if (limit_ns == 0 || limit_ns > 1000000000ull) return fail(BF_EINVAL, "limit_ns must be in (0, 1e9]");
+  int before = 0;
+  BF_CUDA_TRY(cudaMemcpyFromSymbol(&before, g_tc_status, sizeof(int)));
+  if (before) return fail(BF_ETIMEOUT, "an earlier tensor-core wait had already given up (device flag set)");
+  const unsigned long long lim = limit_ns, def = 1000000000ull;
+  BF_CUDA_TRY(cudaMemcpyToSymbolAsync(g_wait_limit_ns, &lim, sizeof(lim), 0, cudaMemcpyHostToDevice, s));
+  note_launch();
+  wait_probe_kernel<<<1, 32, 0, s>>>();
+  const cudaError_t e = cudaGetLastError();
+  const cudaError_t e2 = cudaMemcpyToSymbolAsync(g_wait_limit_ns, &def, sizeof(def), 0, cudaMemcpyHostToDevice, s);
+  const cudaError_t e3 = cudaStreamSynchronize(s);
+  if (e != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess)
+    return fail(BF_ECUDA, std::string("wait probe: ") +
+                              cudaGetErrorString(e != cudaSuccess ? e : e2 != cudaSuccess ? e2 : e3));
+  return tc_status(true);
 }
 
 int tc_status(bool reset) {

@@ -42,6 +42,7 @@ def test_options_defaults_and_error_string(libpath):
     o = api.Options()
     api.lib().bf_options_default(ctypes.byref(o))
     assert (o.p, o.r0, o.r_max, o.seed, o.precision, o.mem_cap, o.qr_fp64) == (2, 4, 1024, 0, 0, 0, 0)
+    assert (o.hybrid_level, o.accept_retries, o.leaf_passes) == (-1, 0, 0)
     rc = api.lib().bf_bisect(None, 0, 0, 3, None, None)
     assert rc == -1 and b"bad arguments" in api.lib().bf_last_error()
 

@@ -66,7 +66,7 @@ def test_max_over_ranks_single_rank():
 
 @pytest.mark.parametrize("rank", [0, 1])
 def test_reference_arm_rank0_only(rank):
-    env = dict(os.environ, RANK=str(rank), WORLD_SIZE="2", LOCAL_RANK=str(rank))
+    env = dict(os.environ, RANK=str(rank), WORLD_SIZE="2", LOCAL_RANK=str(rank), BF_REFERENCE_N="512")
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
                         "--steps", "1", "--warmup", "1"], env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
@@ -79,3 +79,4 @@ def test_reference_arm_rank0_only(rank):
     assert line["higher_is_better"] is False and line["n_gpus"] == 2
     assert line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle"
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+    assert line["steps"] == 1 and line["config"]["n"] == 512
