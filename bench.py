@@ -182,12 +182,15 @@ def profile_case(args):
     else:
         g = inputs.line_pair(N)
         plan = api.Plan(g.src, g.tgt, kernel="helmholtz2d", wavenumber=g.wavenumber, leaf=LEAF, tol=TOL,
-                        precision="mixed", r0=R0)
+                        precision="mixed", r0=R0, qr_fp64=True)
         F = api.Factorization.factor(plan, api.Operator.kernel(plan))
         if args.profile_case == "apply":
-            x = torch.from_numpy(inputs.random_rhs(N, NRHS, seed=1)).to(torch.complex64).cuda()
+            # the fused apply of 64 and of 1 complex64 right-hand sides
+            x = api.colmajor(torch.from_numpy(inputs.random_rhs(N, NRHS, seed=1)).to(torch.complex64).cuda())
             for _ in range(3):
                 F.apply(x)
+            for _ in range(3):
+                F.apply(x[:, :1])
     torch.cuda.synchronize()
     print("profile case done")
 
@@ -499,26 +502,35 @@ def main():
     fms = float(np.mean(fac_ms))
     ms, fms = max_over_ranks([ms, fms], dist, "cuda")
 
-    # apply GB/s (resident factors, 64 RHS, complex64 and complex128), after
-    # the apply autotuner has chosen the stage-kernel shapes
-    def apply_gbs(F, xin, reps=20):
-        info = F.info()
-        es = 8 if xin.dtype == torch.complex64 else 16
-        byts = info["stored_entries"] * es + NRHS * (2 * N) * es
-        F.tune(NRHS, xin.dtype)
-        y = F.apply(xin)
+    # apply GB/s (resident factors, complex64 and complex128), after the
+    # apply tuner has chosen engine, slice width and stage shapes; the stage
+    # engine (L + 3 launches) beside it
+    def apply_time(F, xin, reps=20):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        F.apply(xin)
         torch.cuda.synchronize()
         e0.record(stream)
         for _ in range(reps):
             F.apply(xin)
         e1.record(stream)
         torch.cuda.synchronize()
-        t = e0.elapsed_time(e1) / reps / 1e3
-        return byts / t / 1e9, t, byts
+        return e0.elapsed_time(e1) / reps / 1e3
 
-    gbs32, t32, b32 = apply_gbs(F, x32)
-    gbs64, t64, b64 = apply_gbs(F64, x)
+    def apply_gbs(F, xin):
+        info = F.info()
+        es = 8 if xin.dtype == torch.complex64 else 16
+        nr = xin.shape[1]
+        byts = info["stored_entries"] * es + nr * (2 * N) * es
+        F.tune(nr, xin.dtype)
+        t = apply_time(F, xin)
+        api.set_apply_engine("stages")
+        ts = apply_time(F, xin)
+        api.set_apply_engine("fused")
+        return byts / t / 1e9, t, byts, ts
+
+    gbs32, t32, b32, ts32 = apply_gbs(F, x32)
+    gbs64, t64, b64, ts64 = apply_gbs(F64, x)
+    gbs1, t1, b1, ts1 = apply_gbs(F, x32[:, :1])
 
     # variants of the same factorization, each timed like the steps (3 runs,
     # the first discarded): the pivoted QR and truncation in float-float
@@ -702,11 +714,16 @@ def main():
                                     "unit": "Tops/s", "frac": ALU_OPS_PER_ENTRY * N * N / t_sk / 1e12 / alu_peak,
                                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz",
                                     "tensor_frac": tc_flops / t_sk / 1e12 / tc_peak},
-                     "apply": {"bound": "hbm (latency-bound in practice: L+3 dependent stage launches)",
+                     "apply": {"kernel": "fused_half_kernel (2 launches: one CTA per subtree and column slice "
+                                         "on each side of the centre level)", "bound": "hbm",
                                "achieved_gbs_c64": gbs32, "peak_gbs": peaks.get("hbm_gbs"),
                                "frac_c64": gbs32 / peaks.get("hbm_gbs", 6800.0),
-                               "bytes_per_apply_c64": b32, "ms_c64": t32 * 1e3, "ms_c128": t64 * 1e3,
-                               "work": "factor entries + 64 input and 64 output columns, once each"}},
+                               "achieved_gbs_c128": gbs64, "frac_c128": gbs64 / peaks.get("hbm_gbs", 6800.0),
+                               "bytes_per_apply_c64": b32, "bytes_per_apply_c128": b64,
+                               "ms_c64": t32 * 1e3, "ms_c128": t64 * 1e3, "ms_c64_1rhs": t1 * 1e3,
+                               "gbs_c64_1rhs": gbs1,
+                               "stage_engine_ms": {"c64": ts32 * 1e3, "c128": ts64 * 1e3, "c64_1rhs": ts1 * 1e3},
+                               "work": f"factor entries + {NRHS} input and {NRHS} output columns, once each"}},
     }
     if rank == 0 and not args.no_cpu:
         # the oracle as it stands, once, on the benchmark workload itself

@@ -229,11 +229,13 @@ int bf_apply_T(bf_fact F, int op, int64_t nrhs, const void* x, int64_t ldx,
  * BF_OP_C; dtype BF_C64 or BF_C128; nrhs right-hand sides) is a batched
  * block product of eq. hybrid_butterfly_mat that the library can run with
  * several kernel shapes; all compute bit-identical results.  This call times
- * every shape on every stage (on internal scratch operands; no user data is
- * read or written), keeps the fastest per stage for all later applies of F
- * with a right-hand-side count in the same class (1, 2-4, 5-16, 17-32,
- * 33-64, >64), and writes the tuned device time of one apply in ms to
- * *ms_out (may be NULL).  Synchronises the stream; allocates scratch for
+ * every shape on every stage, and the fused apply (bf_set_apply_engine) at
+ * every column-slice width that fits, on internal scratch operands (no user
+ * data is read or written); it keeps the fastest shape per stage, the
+ * fastest slice width, and the faster of the two engines for all later
+ * applies of F with a right-hand-side count in the same class (1, 2-4,
+ * 5-16, 17-32, 33-64, >64), and writes the tuned device time of one apply
+ * in ms to *ms_out (may be NULL).  Synchronises the stream; allocates scratch for
  * its duration.  BF_EINVAL for a bad op/dtype/nrhs, BF_ENOMEM, BF_ECUDA. */
 int bf_apply_tune(bf_fact F, int op, int64_t nrhs, int dtype, void* stream, float* ms_out);
 
@@ -369,6 +371,23 @@ int bf_set_entry_images(int on);
  * given up.  Diagnostic; not thread-safe against running factorizations
  * (they would see the lowered limit). */
 int bf_debug_wait_timeout(uint64_t limit_ns, void* stream);
+
+/* Selects the apply engine for the whole process (bf_apply, bf_apply_T,
+ * bf_error; eq. hybrid_butterfly_mat): 0 (default) -- the fused apply: two
+ * launches, one CTA per (subtree, column slice) each; the first carries the
+ * input side of the factorization (V^0, W^1..W^(l_m), B, or for F^H / F^T
+ * U^H, R^H levels, B^H) for one subtree of the input-side tree in shared
+ * memory, the second the output side for one subtree of the output-side
+ * tree, with one exchange of the centre-level vectors between them (the
+ * split of the paper's hybrid layout, Sec. 6.2, on the CTAs of one GPU);
+ * the tree permutations and the conjugation of F^T are folded into the
+ * loads and stores.  Results equal the stage engine's bit for bit.  Used
+ * where a subtree's intermediates fit in shared memory (else the stage
+ * engine runs) and, after bf_apply_tune, where it was measured faster for
+ * the right-hand-side class.  1 -- the stage engine only: L + 3 batched
+ * block-product launches plus a gather and a scatter.  BF_EINVAL otherwise.
+ * Not thread-safe against running applies. */
+int bf_set_apply_engine(int engine);
 
 /* ------------------------------------------------------------- common -- */
 /* Frees a bf_plan, bf_fact, bf_operator or bf_applier (NULL-safe). */

@@ -83,6 +83,7 @@ def lib():
         "bf_free": (None, [vp]),
         "bf_set_sketch_engine": (i32, [i32]),
         "bf_set_entry_images": (i32, [i32]),
+        "bf_set_apply_engine": (i32, [i32]),
         "bf_launch_count": (C.c_ulonglong, []),
         "bf_apply_tune": (i32, [vp, i32, i64, i32, vp, C.POINTER(C.c_float)]),
         "bf_applier_create": (i32, [vp, i32, i64, i32, C.POINTER(vp)]),
@@ -107,7 +108,8 @@ def exported_symbols():
             "bf_factor_batch", "bf_apply",
             "bf_apply_T", "bf_apply_noalloc", "bf_ranks", "bf_fact_info", "bf_fact_import", "bf_fact_export", "bf_error",
             "bf_free", "bf_gaussian", "bf_set_sketch_engine", "bf_set_entry_images", "bf_launch_count", "bf_apply_tune",
-            "bf_applier_create", "bf_applier_run", "bf_fact_accept", "bf_debug_wait_timeout"]
+            "bf_applier_create", "bf_applier_run", "bf_fact_accept", "bf_debug_wait_timeout",
+            "bf_set_apply_engine"]
 
 
 def launch_count() -> int:
@@ -134,6 +136,12 @@ def debug_wait_timeout(limit_ns: int, stream=None) -> int:
     lowered to limit_ns (bf_debug_wait_timeout): -6 (BF_ETIMEOUT) is the
     designed outcome."""
     return int(lib().bf_debug_wait_timeout(int(limit_ns), _stream(stream)))
+
+
+def set_apply_engine(engine: str):
+    """'fused' (default: two launches, one CTA per subtree and column slice)
+    or 'stages' (one launch per factor stage)."""
+    check(lib().bf_set_apply_engine({"fused": 0, "stages": 1}[engine]))
 
 
 def check(rc: int):

@@ -448,6 +448,9 @@ void destroy_fact(Fact* F) {
   for (auto& S : F->st) S.d64.release(nullptr), S.d32.release(nullptr);
   for (auto& a : F->ap)
     for (auto& b : a) b.tasks.release(nullptr);
+  for (auto& a : F->fp)
+    for (auto& b : a)
+      for (auto& h : b.h) h.dev.release(nullptr);
   delete F;
 }
 
@@ -834,6 +837,7 @@ int bf_factor(bf_plan plan, bf_operator A, void* stream, bf_fact* out) {
 
 int bf_set_sketch_engine(int engine) { return set_sketch_engine(engine); }
 int bf_set_entry_images(int on) { return set_entry_images(on); }
+int bf_set_apply_engine(int engine) { return set_apply_engine(engine); }
 
 unsigned long long bf_launch_count(void) { return bf::launches_so_far(); }
 

@@ -165,6 +165,32 @@ struct Operator {
   }
 };
 
+// -------------------------------------------------------- stage products --
+// One output block (or column slice of it) of a block-sparse product:
+//   out[M x N] = sum_t op_t(mat_t)[M x K_t] * in_t[K_t x N]
+// op_t = 0: mat_t is M x K_t (ld ldm);  op_t = 1: mat_t is stored K_t x M and
+// conjugate-transposed.  `in` and `out` are element offsets into one of four
+// base pointers given at launch (so a task list can be reused with fresh
+// scratch buffers); `mat` is an absolute device pointer into factor storage.
+struct StageTerm {
+  int64_t in_off;
+  const void* mat;
+  int64_t ldi;
+  int32_t ldm;
+  int32_t K;
+  int16_t conjT;
+  int16_t in_base;
+  int32_t pad;
+};
+struct StageTask {
+  int64_t out_off;
+  int64_t ldo;
+  int32_t M, N;
+  int16_t nterms;
+  int16_t out_base;
+  int32_t pad;
+  StageTerm t[2];
+};
 // ---------------------------------------------------------------- factors --
 // One stage of the factorization in apply order: 2^L blocks, column-major,
 // block b has rows[b] x cols[b] with ld = rows[b] at element offset off[b].
@@ -195,6 +221,40 @@ struct ApplyPlan {
   }
 };
 
+// Fused apply (k_fused.cu): the stage apply's tasks regrouped per subtree.
+// A group is one subtree (one CTA per group and column slice); its levels
+// are the stages of one half of the apply, their rows local to the group.
+struct FusedGroup {
+  int32_t lev0, nlev;        // levels [lev0, lev0 + nlev) of the half's level table
+  int32_t io_row0, io_rows;  // tree-order rows of x (first half) / y (second half) of the subtree
+};
+struct FusedLevel {
+  int32_t task0, ntasks;     // tasks [task0, task0 + ntasks)
+  int32_t rows, map0;        // output rows; rowmap[map0 + r] = (task - task0) << 16 | row in task
+};
+struct FusedHalf {
+  std::vector<FusedGroup> groups;
+  std::vector<FusedLevel> levels;
+  std::vector<StageTask> tasks;
+  std::vector<int32_t> rowmap;
+  int io_max = 0;
+  int64_t lvl_max = 0;
+  DevBuf dev;                // device copies of the four tables
+  const FusedGroup* d_groups = nullptr;
+  const FusedLevel* d_levels = nullptr;
+  const StageTask* d_tasks = nullptr;
+  const int32_t* d_rowmap = nullptr;
+};
+struct FusedPlan {
+  bool built = false, ok = false;
+  FusedHalf h[2];
+  int64_t ex_rows = 0;       // rows of the centre-level exchange buffer
+  // per right-hand-side class: tuned column-slice width (0: default) and
+  // engine (-1 untuned: fused; 0 fused; 1 stage launches measured faster)
+  std::array<int, NRHS_CLASSES> cs{{0, 0, 0, 0, 0, 0}};
+  std::array<int, NRHS_CLASSES> engine{{-1, -1, -1, -1, -1, -1}};
+};
+
 struct Fact {
   Plan* plan = nullptr;
   int L = 0, lm = 0;
@@ -208,6 +268,7 @@ struct Fact {
   double accept_err = -1.0;
   MemTracker mem;
   ApplyPlan ap[2][2];                // [op N / C][dtype C64 / C128]
+  FusedPlan fp[2][2];                // fused apply, same indexing
   int stage_V0() const { return 0; }
   int stage_W(int j) const { return j; }
   int stage_B() const { return lm + 1; }
@@ -216,32 +277,6 @@ struct Fact {
   int ensure32(cudaStream_t s);
 };
 
-// -------------------------------------------------------- stage products --
-// One output block (or column slice of it) of a block-sparse product:
-//   out[M x N] = sum_t op_t(mat_t)[M x K_t] * in_t[K_t x N]
-// op_t = 0: mat_t is M x K_t (ld ldm);  op_t = 1: mat_t is stored K_t x M and
-// conjugate-transposed.  `in` and `out` are element offsets into one of four
-// base pointers given at launch (so a task list can be reused with fresh
-// scratch buffers); `mat` is an absolute device pointer into factor storage.
-struct StageTerm {
-  int64_t in_off;
-  const void* mat;
-  int64_t ldi;
-  int32_t ldm;
-  int32_t K;
-  int16_t conjT;
-  int16_t in_base;
-  int32_t pad;
-};
-struct StageTask {
-  int64_t out_off;
-  int64_t ldo;
-  int32_t M, N;
-  int16_t nterms;
-  int16_t out_base;
-  int32_t pad;
-  StageTerm t[2];
-};
 struct StageBases {
   void* p[4];
 };
@@ -263,6 +298,19 @@ int launch_peel(const StageTask* d_tasks, int ntasks, int maxM, int maxN, int ma
 // dtype, nrhs) and keeps the fastest per stage for that right-hand-side
 // class; returns the tuned apply time in *ms (device, one call).
 int tune_apply(Fact* F, int op, int dtype, int64_t nrhs, cudaStream_t s, float* ms);
+
+// Fused apply: builds F->fp[opC][dtype] once (ok stays false when the
+// subtree grouping does not apply or does not fit in shared memory); runs
+// y = op(F) x in two launches with a caller-provided exchange buffer of
+// fp.ex_rows * nrhs elements (cs_override > 0: that column-slice width).
+int build_fused(Fact* F, int opC, int dtype, cudaStream_t s);
+bool plan_fused(const Fact* F, int opC, int dtype, FusedPlan& fp);
+int fused_slice_width(const FusedPlan& fp, int64_t nrhs, int dtype);
+int run_fused(Fact* F, int opC, int dtype, int64_t nrhs, const void* x, int64_t ldx, void* y, int64_t ldy, int conj,
+              void* exch, cudaStream_t s, int cs_override = 0);
+// 0: fused apply where it applies (default); 1: stage launches only
+int set_apply_engine(int e);
+int apply_engine();
 
 // Graph-captured apply (bf_applier): the stage chain of one (F, op, dtype,
 // nrhs) on internal buffers, captured once into a CUDA graph.
@@ -296,6 +344,12 @@ struct QRTask {
 // Truncated column-pivoted Householder QR (Alg. 1 step 3); ranks[i] out.
 // in dtype: C128 (factored in FP64) or C64 (factored in float-float, or in
 // FP64 when fp64 is set); q is complex128 either way.
+// Both kernels give a block's column RG lanes, RG = qr_lanes(rows): a block's
+// arithmetic (the row striding of its partial sums) depends on its own size
+// only if every launch holds blocks of one qr_lanes class, so that the
+// result of a block does not depend on what else is in the launch (batched
+// factorizations equal individual ones bit for bit).  launch_qr requires it.
+int qr_lanes(int s);
 int launch_qr(const QRTask* d_tasks, int ntasks, int maxS, int maxK, int in_dtype, bool fp64,
               int32_t* d_ranks, void* d_work, size_t work_bytes, cudaStream_t s);
 size_t qr_workspace_bytes(int ntasks, int maxS, int maxK, int in_dtype, bool fp64);

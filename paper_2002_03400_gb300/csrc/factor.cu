@@ -265,7 +265,6 @@ struct QRJob {
 };
 int qr_all(Batch& B, std::vector<QRJob>& jobs) {
   std::vector<QRTask> tasks;
-  int maxS = 1, maxK = 1;
   for (auto& J : jobs) {
     const int nb = (int)J.S->rows.size();
     for (int b = 0; b < nb; ++b) {
@@ -278,23 +277,48 @@ int qr_all(Batch& B, std::vector<QRJob>& jobs) {
       t.q = (char*)J.S->d64.p + J.S->off[b] * 16;
       t.eps = J.o->P->tol;
       tasks.push_back(t);
-      maxS = std::max(maxS, t.s);
     }
-    maxK = std::max(maxK, J.k);
   }
   if (tasks.empty()) return BF_OK;
   const int nt = (int)tasks.size();
   const bool fp64 = B.ops[0].P->opt.qr_fp64 != 0;
-  const size_t wbytes = qr_workspace_bytes(nt, maxS, maxK, B.dt, fp64);
+  // one launch per lane class (qr_lanes of the block's rows), so that each
+  // block is factored with the same arithmetic alone and in a batch
+  std::vector<int> order(nt);
+  for (int i = 0; i < nt; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return qr_lanes(tasks[a].s) < qr_lanes(tasks[b].s); });
+  std::vector<QRTask> sorted(nt);
+  for (int i = 0; i < nt; ++i) sorted[i] = tasks[order[i]];
+  struct Range {
+    int a, b, maxS, maxK;
+  };
+  std::vector<Range> ranges;
+  size_t wbytes = 0;
+  for (int i = 0; i < nt;) {
+    const int cls = qr_lanes(sorted[i].s);
+    Range r{i, i, 1, 1};
+    while (r.b < nt && qr_lanes(sorted[r.b].s) == cls) {
+      r.maxS = std::max(r.maxS, (int)sorted[r.b].s);
+      r.maxK = std::max(r.maxK, (int)sorted[r.b].k);
+      ++r.b;
+    }
+    wbytes = std::max(wbytes, qr_workspace_bytes(r.b - r.a, r.maxS, r.maxK, B.dt, fp64));
+    ranges.push_back(r);
+    i = r.b;
+  }
   Scratch d(B.s), w(B.s);
   BF_TRY(d.alloc(&B.mem, nt * sizeof(QRTask) + nt * sizeof(int32_t)));
-  BF_TRY(upload_async(d.p(), tasks.data(), nt * sizeof(QRTask), B.s));
+  BF_TRY(upload_async(d.p(), sorted.data(), nt * sizeof(QRTask), B.s));
   int32_t* d_r = (int32_t*)(d.p() + nt * sizeof(QRTask));
   if (wbytes) BF_TRY(w.alloc(&B.mem, wbytes));
-  BF_TRY(launch_qr((const QRTask*)d.p(), nt, maxS, maxK, B.dt, fp64, d_r, w.p(), wbytes, B.s));
-  std::vector<int32_t> h(nt);
-  BF_CUDA_TRY(cudaMemcpyAsync(h.data(), d_r, nt * sizeof(int32_t), cudaMemcpyDeviceToHost, B.s));
+  for (const Range& r : ranges)
+    BF_TRY(launch_qr((const QRTask*)d.p() + r.a, r.b - r.a, r.maxS, r.maxK, B.dt, fp64, d_r + r.a, w.p(), wbytes,
+                     B.s));
+  std::vector<int32_t> hs(nt), h(nt);
+  BF_CUDA_TRY(cudaMemcpyAsync(hs.data(), d_r, nt * sizeof(int32_t), cudaMemcpyDeviceToHost, B.s));
   BF_CUDA_TRY(cudaStreamSynchronize(B.s));
+  for (int i = 0; i < nt; ++i) h[order[i]] = hs[i];
   BF_TRY(tc_status(true));
   size_t q = 0;
   for (auto& J : jobs) {

@@ -552,6 +552,8 @@ int launch_qr64_rg(const QRTask* d_tasks, int ntasks, int maxS, int maxK, int32_
 }
 }  // namespace
 
+int qr_lanes(int s) { return rg_for(s); }
+
 size_t qr_workspace_bytes(int ntasks, int maxS, int maxK, int in_dtype, bool fp64) {
   if (in_dtype == BF_C64 && !fp64) {
     const size_t blk = block_ff_bytes(maxS, maxK, rg_for(maxS));

@@ -203,7 +203,13 @@ def test_caps_n16384_against_stored_oracle(qr_fp64):
 
 def test_caps_composition_n16384_against_stored_oracle():
     """A = K(P3<-P2) K(P2<-P1), black box = the two GPU factorizations,
-    recompressed (FP64 QR, as the configuration states)."""
+    recompressed (FP64 QR, as the configuration states).  The oracle's
+    black box is its own two factorizations, so the two recompressions see
+    operators that already differ by the GPU-vs-oracle gaps of K1 and K2
+    (each within GAP_3D); with the recompression's own gap the comparison
+    bound is 3 GAP_3D.  Against the exact product (stored rows of
+    K(P3<-P2) K(P2<-P1) Omega) the error is within three Thm 5.3 bounds
+    (K1, K2 and the recompression at tol 1e-6)."""
     d = _golden("caps_composition_n16384.txt")
     P1, P2, P3, k = mg.cap_triple(mg.N)
     p1, p2 = _cap_plan(P1, P2, k, True), _cap_plan(P2, P3, k, True)
@@ -212,5 +218,8 @@ def test_caps_composition_n16384_against_stored_oracle():
     comp = api.Operator.composed(api.Operator.factored(K2), api.Operator.factored(K1))
     pa = api.Plan(P1, P3, leaf=64, tol=1e-6, precision="mixed", p=4, r0=64, qr_fp64=True)
     F = api.Factorization.factor(pa, comp)
-    worst, gap = _compare_stored(F, d, ob.error_probe(mg.N, mg.PROBE_SEED, mg.PROBE_COLS))
-    assert worst <= 1 and gap <= GAP_3D, (worst, gap)
+    Om = ob.error_probe(mg.N, mg.PROBE_SEED, mg.PROBE_COLS)
+    worst, gap = _compare_stored(F, d, Om)
+    assert worst <= 1 and gap <= 3 * GAP_3D, (worst, gap)
+    y = H(F.apply(T(Om)))[d["rows"]]
+    assert np.linalg.norm(y - d["A"]) <= 3 * bound(pa.L, 1e-6) * np.linalg.norm(d["A"])
