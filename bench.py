@@ -185,12 +185,16 @@ def profile_case(args):
                         precision="mixed", r0=R0, qr_fp64=True)
         F = api.Factorization.factor(plan, api.Operator.kernel(plan))
         if args.profile_case == "apply":
-            # the fused apply of 64 and of 1 complex64 right-hand sides
+            # applies of 64 and of 1 complex64 right-hand sides, fused engine
+            # then stage engine
             x = api.colmajor(torch.from_numpy(inputs.random_rhs(N, NRHS, seed=1)).to(torch.complex64).cuda())
-            for _ in range(3):
-                F.apply(x)
-            for _ in range(3):
-                F.apply(x[:, :1])
+            for eng in ("fused", "stages"):
+                api.set_apply_engine(eng)
+                for _ in range(3):
+                    F.apply(x)
+                for _ in range(3):
+                    F.apply(x[:, :1])
+            api.set_apply_engine("auto")
     torch.cuda.synchronize()
     print("profile case done")
 
@@ -522,11 +526,13 @@ def main():
         nr = xin.shape[1]
         byts = info["stored_entries"] * es + nr * (2 * N) * es
         F.tune(nr, xin.dtype)
-        t = apply_time(F, xin)
+        t = apply_time(F, xin)               # the tuned choice (engine, slice width, stage shapes)
         api.set_apply_engine("stages")
         ts = apply_time(F, xin)
         api.set_apply_engine("fused")
-        return byts / t / 1e9, t, byts, ts
+        tf = apply_time(F, xin)
+        api.set_apply_engine("auto")
+        return byts / t / 1e9, t, byts, (ts, tf)
 
     gbs32, t32, b32, ts32 = apply_gbs(F, x32)
     gbs64, t64, b64, ts64 = apply_gbs(F64, x)
@@ -714,15 +720,27 @@ def main():
                                     "unit": "Tops/s", "frac": ALU_OPS_PER_ENTRY * N * N / t_sk / 1e12 / alu_peak,
                                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz",
                                     "tensor_frac": tc_flops / t_sk / 1e12 / tc_peak},
-                     "apply": {"kernel": "fused_half_kernel (2 launches: one CTA per subtree and column slice "
-                                         "on each side of the centre level)", "bound": "hbm",
+                     "apply": {"kernel": "the tuned apply engine (stage launches with the wide register-tile "
+                                         "kernel, or the fused two-launch engine where measured faster)",
+                               "bound": "alu (complex64, 64 RHS: 4 FP32 FMA per factor entry and column; "
+                                        "the HBM fraction is reported beside it)",
                                "achieved_gbs_c64": gbs32, "peak_gbs": peaks.get("hbm_gbs"),
                                "frac_c64": gbs32 / peaks.get("hbm_gbs", 6800.0),
+                               # 4 real FMAs per stored factor entry and column (one complex
+                               # multiply-add); FP32 lanes: 152 SMs x 128 x 2070 MHz; FP64: 2
+                               # FMAs per clock per SM (the nominal 1.25 TFLOP/s)
+                               "fma_frac_c64": 4.0 * F.info()["stored_entries"] * NRHS / t32
+                                               / (152 * 128 * 2070e6),
+                               "fma_frac_c128": 4.0 * F64.info()["stored_entries"] * NRHS / t64
+                                                / (152 * 2 * 2070e6),
                                "achieved_gbs_c128": gbs64, "frac_c128": gbs64 / peaks.get("hbm_gbs", 6800.0),
                                "bytes_per_apply_c64": b32, "bytes_per_apply_c128": b64,
                                "ms_c64": t32 * 1e3, "ms_c128": t64 * 1e3, "ms_c64_1rhs": t1 * 1e3,
                                "gbs_c64_1rhs": gbs1,
-                               "stage_engine_ms": {"c64": ts32 * 1e3, "c128": ts64 * 1e3, "c64_1rhs": ts1 * 1e3},
+                               "stage_engine_ms": {"c64": ts32[0] * 1e3, "c128": ts64[0] * 1e3,
+                                                   "c64_1rhs": ts1[0] * 1e3},
+                               "fused_engine_ms": {"c64": ts32[1] * 1e3, "c128": ts64[1] * 1e3,
+                                                   "c64_1rhs": ts1[1] * 1e3},
                                "work": f"factor entries + {NRHS} input and {NRHS} output columns, once each"}},
     }
     if rank == 0 and not args.no_cpu:

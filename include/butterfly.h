@@ -373,20 +373,23 @@ int bf_set_entry_images(int on);
 int bf_debug_wait_timeout(uint64_t limit_ns, void* stream);
 
 /* Selects the apply engine for the whole process (bf_apply, bf_apply_T,
- * bf_error; eq. hybrid_butterfly_mat): 0 (default) -- the fused apply: two
- * launches, one CTA per (subtree, column slice) each; the first carries the
- * input side of the factorization (V^0, W^1..W^(l_m), B, or for F^H / F^T
- * U^H, R^H levels, B^H) for one subtree of the input-side tree in shared
- * memory, the second the output side for one subtree of the output-side
- * tree, with one exchange of the centre-level vectors between them (the
- * split of the paper's hybrid layout, Sec. 6.2, on the CTAs of one GPU);
- * the tree permutations and the conjugation of F^T are folded into the
- * loads and stores.  Results equal the stage engine's bit for bit.  Used
- * where a subtree's intermediates fit in shared memory (else the stage
- * engine runs) and, after bf_apply_tune, where it was measured faster for
- * the right-hand-side class.  1 -- the stage engine only: L + 3 batched
- * block-product launches plus a gather and a scatter.  BF_EINVAL otherwise.
- * Not thread-safe against running applies. */
+ * bf_error; eq. hybrid_butterfly_mat).  Two engines compute bit-identical
+ * results:
+ *   - stages: L + 3 batched block-product launches plus a gather and a
+ *     scatter (kernel shapes per stage as tuned by bf_apply_tune);
+ *   - fused: two launches, one CTA per (subtree, column slice) each; the
+ *     first carries the input side of the factorization (V^0, W^1..W^(l_m),
+ *     B, or for F^H / F^T U^H, R^H levels, B^H) for one subtree of the
+ *     input-side tree in shared memory, the second the output side for one
+ *     subtree of the output-side tree, with one exchange of the centre-level
+ *     vectors between them (the split of the paper's hybrid layout, Sec. 6.2,
+ *     on the CTAs of one GPU); the tree permutations and the conjugation of
+ *     F^T are folded into the loads and stores; used where a subtree's
+ *     intermediates fit in shared memory.
+ * engine 0 (default): the stage engine, except for right-hand-side classes
+ * where bf_apply_tune measured the fused engine faster; 1: stages only;
+ * 2: fused wherever it applies.  BF_EINVAL otherwise.  Not thread-safe
+ * against running applies. */
 int bf_set_apply_engine(int engine);
 
 /* ------------------------------------------------------------- common -- */

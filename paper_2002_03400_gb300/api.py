@@ -139,9 +139,10 @@ def debug_wait_timeout(limit_ns: int, stream=None) -> int:
 
 
 def set_apply_engine(engine: str):
-    """'fused' (default: two launches, one CTA per subtree and column slice)
-    or 'stages' (one launch per factor stage)."""
-    check(lib().bf_set_apply_engine({"fused": 0, "stages": 1}[engine]))
+    """'auto' (default: the stage launches, or the fused two-launch engine
+    where bf_apply_tune measured it faster), 'stages' or 'fused' (wherever it
+    applies)."""
+    check(lib().bf_set_apply_engine({"auto": 0, "stages": 1, "fused": 2}[engine]))
 
 
 def check(rc: int):

@@ -304,12 +304,14 @@ int apply_fact(Fact* F, int op, int64_t nrhs, const void* x, int64_t ldx, void* 
   const bool id_out = tree_order || (opC ? P->identS : P->identT);
   const int conj = op == BF_OP_T ? 1 : 0;
   const size_t es = elem_bytes(dtype);
-  // the fused apply (two launches) where it applies and was not measured
-  // slower for this right-hand-side class by the tuner
-  if (!tree_order && apply_engine() == 0) {
-    BF_TRY(build_fused(F, opC, dtype, s));
+  // the fused apply (two launches): always where it applies (engine 2), or
+  // where the tuner measured it faster than the stage launches for this
+  // right-hand-side class (engine 0)
+  if (!tree_order && apply_engine() == 2) BF_TRY(build_fused(F, opC, dtype, s));
+  if (!tree_order && F->fp[opC][dtype].ok &&
+      (apply_engine() == 2 || (apply_engine() == 0 && F->fp[opC][dtype].engine[nrhs_class(nrhs)] == 0))) {
     const FusedPlan& fp = F->fp[opC][dtype];
-    if (fp.ok && fp.engine[nrhs_class(nrhs)] != 1) {
+    {
       DevBuf ex;
       BF_TRY(ex.alloc(&F->mem, (size_t)fp.ex_rows * nrhs * es, s));
       const int rc = run_fused(F, opC, dtype, nrhs, x, ldx, y, ldy, conj, ex.p, s);
@@ -390,9 +392,9 @@ int tune_apply(Fact* F, int op, int dtype, int64_t nrhs, cudaStream_t s, float* 
   // scratch, exchange = the two level buffers); keep the fastest width and
   // the faster of the two engines for this class
   float fused_best = 1e30f;
-  if (!rc && apply_engine() == 0) rc = build_fused(F, opC, dtype, s);
+  if (!rc && apply_engine() != 1) rc = build_fused(F, opC, dtype, s);
   FusedPlan& fp = F->fp[opC][dtype];
-  if (!rc && apply_engine() == 0 && fp.ok && 2 * lvl >= fp.ex_rows * nrhs) {
+  if (!rc && apply_engine() != 1 && fp.ok && 2 * lvl >= fp.ex_rows * nrhs) {
     int best_cs = 0;
     const int conj = op == BF_OP_T ? 1 : 0;
     char* xs = p + 2 * lvl * es;

@@ -230,27 +230,46 @@ struct FusedGroup {
 };
 struct FusedLevel {
   int32_t task0, ntasks;     // tasks [task0, task0 + ntasks)
-  int32_t rows, map0;        // output rows; rowmap[map0 + r] = (task - task0) << 16 | row in task
+  int32_t rows, map0;        // output rows; row tiles at rowmap[map0 ..]
+  int32_t tiles;             // rowmap[map0 + t] = (task - task0) << 16 | first row of tile t
+  int32_t chunk0, nchunks;   // chunks [chunk0, chunk0 + nchunks) of the half's chunk table
+  int32_t pad;
+};
+// A chunk of a level: the row tiles [tile0, tile1) computed after copying
+// the factor blocks they read (segments [seg0, seg0 + nseg)) into the
+// shared-memory staging area (staged = 0: the tasks read global memory).
+struct FusedChunk {
+  int32_t tile0, tile1, seg0, nseg, staged, pad;
+};
+struct FusedSeg {
+  const void* src;           // first element of a factor block in global memory
+  int32_t dst, count;        // staging-area element offset and element count
 };
 struct FusedHalf {
   std::vector<FusedGroup> groups;
   std::vector<FusedLevel> levels;
   std::vector<StageTask> tasks;
   std::vector<int32_t> rowmap;
+  std::vector<FusedChunk> chunks;
+  std::vector<FusedSeg> segs;
   int io_max = 0;
-  int64_t lvl_max = 0;
+  int64_t lvl_max = 0;       // rows of the largest intermediate level (shared-memory level buffers)
+  int tasks_max = 0;         // tasks and row tiles of the largest level (descriptor and tile-map copies)
+  int64_t rows_max = 0;
   DevBuf dev;                // device copies of the four tables
   const FusedGroup* d_groups = nullptr;
   const FusedLevel* d_levels = nullptr;
   const StageTask* d_tasks = nullptr;
   const int32_t* d_rowmap = nullptr;
+  const FusedChunk* d_chunks = nullptr;
+  const FusedSeg* d_segs = nullptr;
 };
 struct FusedPlan {
   bool built = false, ok = false;
   FusedHalf h[2];
   int64_t ex_rows = 0;       // rows of the centre-level exchange buffer
   // per right-hand-side class: tuned column-slice width (0: default) and
-  // engine (-1 untuned: fused; 0 fused; 1 stage launches measured faster)
+  // engine (-1 untuned: stage launches; 0 fused measured faster; 1 stages)
   std::array<int, NRHS_CLASSES> cs{{0, 0, 0, 0, 0, 0}};
   std::array<int, NRHS_CLASSES> engine{{-1, -1, -1, -1, -1, -1}};
 };
@@ -284,7 +303,7 @@ struct StageBases {
 // per-task N, each task cut into 32-column slices (-Noverride the widest N)
 // so that wide tasks spread over many warps; 0: per-task N, one warp per
 // task.  variant:
-// kernel shape (0, 1 or 2, same results), -1 for the default for Noverride.
+// kernel shape (0 .. STAGE_VARIANTS - 1, same results), -1 for the default for Noverride.
 // pdl: launch with a programmatic dependency on the previous kernel in s
 // (only when that kernel is itself a stage launch of the same chain).
 int launch_stage(const StageTask* d_tasks, int ntasks, int maxM, int maxN, int Noverride,
@@ -308,7 +327,8 @@ bool plan_fused(const Fact* F, int opC, int dtype, FusedPlan& fp);
 int fused_slice_width(const FusedPlan& fp, int64_t nrhs, int dtype);
 int run_fused(Fact* F, int opC, int dtype, int64_t nrhs, const void* x, int64_t ldx, void* y, int64_t ldy, int conj,
               void* exch, cudaStream_t s, int cs_override = 0);
-// 0: fused apply where it applies (default); 1: stage launches only
+// 0: fused apply where the tuner measured it faster (default); 1: stage
+// launches only; 2: fused wherever it applies
 int set_apply_engine(int e);
 int apply_engine();
 
@@ -329,7 +349,7 @@ int applier_create(Fact* F, int op, int64_t nrhs, int dtype, Applier** out);
 int applier_run(Applier* A, const void* x, int64_t ldx, void* y, int64_t ldy, cudaStream_t s);
 void applier_destroy(Applier* A);
 int stage_variant_default(int nrhs, int dtype);
-constexpr int STAGE_VARIANTS = 3;
+constexpr int STAGE_VARIANTS = 6;
 
 // ------------------------------------------------------------------- QR --
 struct QRTask {

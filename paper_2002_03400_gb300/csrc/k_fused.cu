@@ -49,11 +49,108 @@ struct FusedArgs {
   int conj;             // F^T: conjugate on the way in and out
   int nrhs, CS;
   int io_max, lvl_max;  // rows of the staged input/output block and of one intermediate (per CS columns)
+  int tasks_max;        // tasks and row tiles of the largest level (shared-memory copies)
+  int rows_max;
+  const FusedChunk* chunks;
+  const FusedSeg* segs;
 };
 }  // namespace
 
+// each thread computes a tile of FRT rows x FCT columns of one task: per k,
+// FRT factor entries and FCT inputs feed FRT * FCT complex FMAs
+constexpr int FRT = 4, FCT = 2;
+// shared-memory staging area for the factor blocks of one chunk: two
+// buffers, so that the next chunk's copies run while this one computes
+constexpr size_t FAC_BYTES = 24 * 1024;
+
+__device__ __forceinline__ void cp_async_elem(void* dst, const void* src, int bytes) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  if (bytes == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+
+// The row tiles of one chunk: items (tile of FRT rows of one task, NC
+// columns); every output is its own FMA chain over the terms in order and k
+// ascending.  FAST: factor entries from the staging area and inputs from
+// shared memory (shared-memory loads); otherwise generic loads (unstaged
+// entries in global memory, or kernel 2's first inputs in the exchange buffer).
+template <typename R, int NC, bool FAST>
+__device__ __forceinline__ void fused_tiles(const StageTask* stk, const int32_t* smap, const FusedChunk C,
+                                            const typename Cx<R>::V* fac, const typename Cx<R>::V* in, int64_t in_rs,
+                                            int64_t in_c0, typename Cx<R>::V* out, int64_t out_rs, int64_t out_c0,
+                                            int cw, int tid) {
+  using V = typename Cx<R>::V;
+  const int nct = (cw + NC - 1) / NC;
+  for (int idx = C.tile0 * nct + tid; idx < C.tile1 * nct; idx += FTHREADS) {
+    const int tl = idx / nct, ct = idx - tl * nct;
+    const int32_t m = smap[tl];
+    const StageTask& tk = stk[m >> 16];
+    const int i0 = m & 0xffff, cc = ct * NC;
+    const int nr = min(FRT, tk.M - i0), ncl = min(NC, cw - cc);
+    V acc[FRT][NC];
+#pragma unroll
+    for (int r = 0; r < FRT; ++r)
+#pragma unroll
+      for (int j = 0; j < NC; ++j) acc[r][j] = Cx<R>::make(0, 0);
+    for (int q = 0; q < tk.nterms; ++q) {
+      const StageTerm& T = tk.t[q];
+      // staged terms hold the staging-area offset of their entries
+      const V* __restrict__ mat = (FAST || T.pad) ? fac + (intptr_t)T.mat : (const V*)T.mat;
+      const int K = T.K, ldm = T.ldm, cj = T.conjT;
+      const int istep = cj ? ldm : 1, kstep = cj ? 1 : ldm;
+      // rows past the tile's end re-read its last row (loaded, never stored)
+      int mo[FRT];
+#pragma unroll
+      for (int r = 0; r < FRT; ++r) mo[r] = (i0 + min(r, nr - 1)) * istep;
+      const V* xin = in + T.in_off * in_rs + in_c0 + cc;
+      int xo[NC];
+#pragma unroll
+      for (int j = 0; j < NC; ++j) xo[j] = min(j, ncl - 1);
+#pragma unroll 2
+      for (int k = 0; k < K; ++k) {
+        V e[FRT], xv[NC];
+        const int mk = k * kstep;
+        const int64_t xk = (int64_t)k * in_rs;
+#pragma unroll
+        for (int r = 0; r < FRT; ++r) e[r] = mat[mo[r] + mk];
+#pragma unroll
+        for (int j = 0; j < NC; ++j) xv[j] = xin[xk + xo[j]];
+#pragma unroll
+        for (int r = 0; r < FRT; ++r) {
+          if (cj) e[r].y = -e[r].y;
+#pragma unroll
+          for (int j = 0; j < NC; ++j) cmac(acc[r][j], e[r], xv[j]);
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < FRT; ++r)
+#pragma unroll
+      for (int j = 0; j < NC; ++j)
+        if (r < nr && j < ncl) out[(tk.out_off + i0 + r) * out_rs + out_c0 + cc + j] = acc[r][j];
+  }
+}
+
 // FIRST: kernel 1 (stages rows of x, writes the exchange buffer); otherwise
-// kernel 2 (reads the exchange buffer, stages rows of y).
+// kernel 2 (reads the exchange buffer, stages rows of y).  Shared memory:
+// the staged rows (io), two level buffers, and the current level's task
+// descriptors and row map (copied once per level, so that the per-output
+// lookups are shared-memory reads).
+// FIRST: kernel 1 (stages rows of x, writes the exchange buffer); otherwise
+// kernel 2 (reads the exchange buffer, stages rows of y).  Shared memory:
+// the staged rows (io), two level buffers, and the current level's task
+// descriptors and row map (copied once per level, so that the per-output
+// lookups are shared-memory reads).
+
+// FIRST: kernel 1 (stages rows of x, writes the exchange buffer); otherwise
+// kernel 2 (reads the exchange buffer, stages rows of y).  Shared memory:
+// the staged rows (io), two level buffers, the current level's task
+// descriptors and tile map, and the staging area of the factor blocks.
+// Per level: the descriptors are copied once; then per chunk the factor
+// blocks it reads are copied with cp.async by all threads, and its tiles
+// are computed from shared memory only.
 template <typename R, bool FIRST>
 __global__ void __launch_bounds__(FTHREADS) fused_half_kernel(const FusedArgs a) {
   using V = typename Cx<R>::V;
@@ -65,9 +162,13 @@ __global__ void __launch_bounds__(FTHREADS) fused_half_kernel(const FusedArgs a)
   V* io = (V*)fused_smem;
   V* buf0 = io + (int64_t)a.io_max * CS;
   V* buf1 = buf0 + (int64_t)a.lvl_max * CS;
+  StageTask* stk =
+      (StageTask*)(fused_smem + ((((int64_t)a.io_max + 2 * (int64_t)a.lvl_max) * CS * sizeof(V) + 15) & ~(int64_t)15));
+  int32_t* smap = (int32_t*)(stk + a.tasks_max);
+  V* fac = (V*)((uint8_t*)stk + (((int64_t)a.tasks_max * sizeof(StageTask) + (int64_t)a.rows_max * 4 + 15) & ~(int64_t)15));
   const int tid = threadIdx.x;
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   if (FIRST) {
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const V* x = (const V*)a.x;
     for (int idx = tid; idx < G.io_rows * cw; idx += FTHREADS) {
       const int c = idx / G.io_rows, i = idx - c * G.io_rows;
@@ -78,25 +179,63 @@ __global__ void __launch_bounds__(FTHREADS) fused_half_kernel(const FusedArgs a)
     }
   } else {
     // the exchange buffer is complete once kernel 1 has finished; before
-    // that, warm L2 with this subtree's first-level factor blocks
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    // that, warm L2 with this subtree's first-chunk factor blocks
     const FusedLevel L0 = a.levels[G.lev0];
-    for (int t = tid >> 5; t < L0.ntasks; t += FTHREADS / 32) {
-      const StageTask& tk = a.tasks[L0.task0 + t];
-      for (int q = 0; q < tk.nterms; ++q) {
-        const StageTerm& T = tk.t[q];
-        const int64_t rows = T.conjT ? T.K : tk.M, cols = T.conjT ? tk.M : T.K;
-        const int64_t bytes = ((cols - 1) * (int64_t)T.ldm + rows) * (int64_t)sizeof(V);
+    if (L0.nchunks > 0) {
+      const FusedChunk C0 = a.chunks[L0.chunk0];
+      for (int g = tid >> 5; g < C0.nseg; g += FTHREADS / 32) {
+        const FusedSeg sg = a.segs[C0.seg0 + g];
+        const int64_t bytes = (int64_t)sg.count * sizeof(V);
         for (int64_t off = (int64_t)(tid & 31) * 128; off < bytes; off += 32 * 128)
-          asm volatile("prefetch.global.L2 [%0];" ::"l"((const char*)T.mat + off));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"((const char*)sg.src + off));
       }
     }
     asm volatile("griddepcontrol.wait;" ::: "memory");
   }
-  __syncthreads();
+  // all chunks of the subtree in order, level after level; chunk k + 1's
+  // factor copies are issued before chunk k is computed
+  const int lane = tid & 31, warp = tid >> 5;
+  constexpr int FE = (int)(FAC_BYTES / sizeof(V));
+  int par = 0;                                   // staging buffer of the current chunk
+  int nlv = 0, nch = 0;                          // next chunk to issue
+  auto advance = [&](int& l, int& c) {
+    while (l < G.nlev && c >= a.levels[G.lev0 + l].nchunks) ++l, c = 0;
+  };
+  advance(nlv, nch);
+  int issued_par = 0;
+  auto issue_next = [&]() {
+    if (nlv >= G.nlev) {
+      asm volatile("cp.async.commit_group;" ::: "memory");   // keeps one group per chunk
+      return;
+    }
+    const FusedLevel Lq = a.levels[G.lev0 + nlv];
+    const FusedChunk C = a.chunks[Lq.chunk0 + nch];
+    if (C.staged) {
+      V* dst = fac + issued_par * FE;
+      for (int g = warp; g < C.nseg; g += FTHREADS / 32) {
+        const FusedSeg sg = a.segs[C.seg0 + g];
+        if (lane < sg.count) cp_async_elem(dst + sg.dst + lane, (const V*)sg.src + lane, (int)sizeof(V));
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    issued_par ^= 1;
+    ++nch;
+    advance(nlv, nch);
+  };
+  issue_next();   // chunk 0
   for (int lv = 0; lv < G.nlev; ++lv) {
     const FusedLevel Lv = a.levels[G.lev0 + lv];
+    // this level's task descriptors and tile map into shared memory (the
+    // previous level's last chunk ended with a barrier)
+    {
+      const uint4* src = (const uint4*)(a.tasks + Lv.task0);
+      uint4* dst = (uint4*)stk;
+      const int nv = Lv.ntasks * (int)(sizeof(StageTask) / sizeof(uint4));
+      for (int v = tid; v < nv; v += FTHREADS) dst[v] = src[v];
+      for (int r = tid; r < Lv.tiles; r += FTHREADS) smap[r] = a.rowmap[Lv.map0 + r];
+    }
     const bool first = lv == 0, last = lv == G.nlev - 1;
+    const bool in_smem = !(first && !FIRST);       // kernel 2 reads the exchange buffer first
     // input rows: the staged x (kernel 1) or the exchange buffer (kernel 2)
     // at the first level, else the previous level's buffer
     const V* in;
@@ -115,29 +254,25 @@ __global__ void __launch_bounds__(FTHREADS) fused_half_kernel(const FusedArgs a)
     } else {
       out = (lv & 1) ? buf1 : buf0, out_rs = CS, out_c0 = 0;
     }
-    for (int idx = tid; idx < Lv.rows * cw; idx += FTHREADS) {
-      const int rr = idx / cw, c = idx - rr * cw;
-      const int32_t m = a.rowmap[Lv.map0 + rr];
-      const StageTask& tk = a.tasks[Lv.task0 + (m >> 16)];
-      const int i = m & 0xffff;
-      V acc = Cx<R>::make(0, 0);
-      for (int q = 0; q < tk.nterms; ++q) {
-        const StageTerm& T = tk.t[q];
-        const V* __restrict__ mat = (const V*)T.mat;
-        const int K = T.K, ldm = T.ldm, cj = T.conjT;
-        const int istep = cj ? ldm : 1, kstep = cj ? 1 : ldm;
-        const V* __restrict__ mrow = mat + (int64_t)i * istep;
-        const V* xin = in + T.in_off * in_rs + in_c0 + c;
-        for (int k = 0; k < K; ++k) {
-          V e = mrow[(int64_t)k * kstep];
-          if (cj) e.y = -e.y;
-          cmac(acc, e, xin[(int64_t)k * in_rs]);
-        }
+    for (int ch = 0; ch < Lv.nchunks; ++ch) {
+      const FusedChunk C = a.chunks[Lv.chunk0 + ch];
+      issue_next();                                  // the next chunk's copies
+      asm volatile("cp.async.wait_group 1;" ::: "memory");   // this chunk's copies have landed
+      __syncthreads();   // (also orders the descriptors, the staged x and the previous level's outputs)
+      const V* fb = fac + par * FE;
+      const bool fast = C.staged && in_smem;
+      if (cw == 1) {
+        if (fast) fused_tiles<R, 1, true>(stk, smap, C, fb, in, in_rs, in_c0, out, out_rs, out_c0, cw, tid);
+        else fused_tiles<R, 1, false>(stk, smap, C, fb, in, in_rs, in_c0, out, out_rs, out_c0, cw, tid);
+      } else {
+        if (fast) fused_tiles<R, FCT, true>(stk, smap, C, fb, in, in_rs, in_c0, out, out_rs, out_c0, cw, tid);
+        else fused_tiles<R, FCT, false>(stk, smap, C, fb, in, in_rs, in_c0, out, out_rs, out_c0, cw, tid);
       }
-      out[(tk.out_off + i) * out_rs + out_c0 + c] = acc;
+      par ^= 1;
+      __syncthreads();   // this chunk's staging buffer and outputs are complete
     }
-    __syncthreads();
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");
   if (!FIRST) {
     V* y = (V*)a.y;
     for (int idx = tid; idx < G.io_rows * cw; idx += FTHREADS) {
@@ -157,8 +292,90 @@ namespace {
 // rows (part = partition of those rows); otherwise they follow it back from
 // the last stage's output rows.  Offsets become subtree-local rows except
 // the exchange side (kernel 1's last outputs, kernel 2's first inputs).
+// Locates the factor block that holds a term's entries: its first element
+// and element count, or false.
+struct BlockLocator {
+  const Fact* F;
+  int dtype;
+  bool find(const void* p, const char** base, int64_t* count) const {
+    const size_t es = elem_bytes(dtype);
+    for (const Stage& S : F->st) {
+      const char* b = (const char*)(dtype == BF_C128 ? S.d64.p : S.d32.p);
+      if (!b || (const char*)p < b || (const char*)p >= b + S.total * (int64_t)es) continue;
+      const int64_t e = ((const char*)p - b) / (int64_t)es;
+      const int blk = (int)(std::upper_bound(S.off.begin(), S.off.end(), e) - S.off.begin()) - 1;
+      if (blk < 0) return false;
+      *base = b + S.off[blk] * (int64_t)es;
+      *count = (int64_t)S.rows[blk] * S.cols[blk];
+      return true;
+    }
+    return false;
+  }
+};
+
+// Splits the tasks [t0, t1) of one level into chunks whose factor blocks fit
+// the staging area together (a task whose blocks alone do not fit forms an
+// unstaged chunk and reads global memory); rewrites the staged terms' entry
+// pointers as staging-area offsets.
+bool chunk_level(FusedHalf& H, FusedLevel& Lv, const BlockLocator& loc, int64_t fac_elems) {
+  Lv.chunk0 = (int32_t)H.chunks.size();
+  std::map<const char*, int64_t> placed;   // block -> staging offset in this chunk
+  int64_t used = 0;
+  FusedChunk cur{0, 0, (int32_t)H.segs.size(), 0, 1, 0};
+  int tile = 0;
+  auto close = [&]() {
+    if (cur.tile1 > cur.tile0) H.chunks.push_back(cur);
+    cur = FusedChunk{tile, tile, (int32_t)H.segs.size(), 0, 1, 0};
+    placed.clear();
+    used = 0;
+  };
+  const size_t es = elem_bytes(loc.dtype);
+  for (int t = 0; t < Lv.ntasks; ++t) {
+    StageTask& tk = H.tasks[Lv.task0 + t];
+    const int tiles = (tk.M + FRT - 1) / FRT;
+    const char* base[2] = {nullptr, nullptr};
+    int64_t cnt[2] = {0, 0}, need = 0;
+    for (int q = 0; q < tk.nterms; ++q) {
+      if (!loc.find(tk.t[q].mat, &base[q], &cnt[q])) return false;
+      const bool dup = q == 1 && base[1] == base[0];
+      if (!placed.count(base[q]) && !dup) need += cnt[q];
+    }
+    int64_t alone = cnt[0] + (tk.nterms == 2 && base[1] != base[0] ? cnt[1] : 0);
+    if (alone > fac_elems) {   // unstaged: its own chunk, entries from global memory
+      close();
+      cur.staged = 0;
+      cur.tile1 = tile + tiles;
+      tile += tiles;
+      H.chunks.push_back(cur);
+      cur = FusedChunk{tile, tile, (int32_t)H.segs.size(), 0, 1, 0};
+      continue;
+    }
+    if (used + need > fac_elems) close();
+    for (int q = 0; q < tk.nterms; ++q) {
+      auto it = placed.find(base[q]);
+      if (it == placed.end()) {
+        it = placed.insert({base[q], used}).first;
+        for (int64_t e = 0; e < cnt[q]; e += 32) {   // pieces of <= 32 elements: one warp copies one
+          H.segs.push_back(FusedSeg{base[q] + e * (int64_t)es, (int32_t)(used + e),
+                                    (int32_t)std::min<int64_t>(32, cnt[q] - e)});
+          ++cur.nseg;
+        }
+        used += cnt[q];
+      }
+      const int64_t delta = ((const char*)tk.t[q].mat - base[q]) / (int64_t)es;
+      tk.t[q].mat = (const void*)(intptr_t)(it->second + delta);
+      tk.t[q].pad = 1;
+    }
+    cur.tile1 = tile + tiles;
+    tile += tiles;
+  }
+  close();
+  Lv.nchunks = (int32_t)(H.chunks.size() - Lv.chunk0);
+  return tile == Lv.tiles;
+}
+
 bool build_half(const std::vector<StageTask>& all, const ApplyPlan& ap, int s0, int s1,
-                const std::vector<int64_t>& part, bool forward, FusedHalf& H) {
+                const std::vector<int64_t>& part, bool forward, const BlockLocator& loc, FusedHalf& H) {
   const int ng = (int)part.size() - 1;
   const int ns = s1 - s0;
   auto part_of = [&](int64_t row) {
@@ -222,8 +439,12 @@ bool build_half(const std::vector<StageTask>& all, const ApplyPlan& ap, int s0, 
   H.levels.clear();
   H.tasks.clear();
   H.rowmap.clear();
+  H.chunks.clear();
+  H.segs.clear();
   H.io_max = 0;
   H.lvl_max = 0;
+  H.tasks_max = 0;
+  H.rows_max = 0;
   for (int g = 0; g < ng; ++g) {
     FusedGroup& G = H.groups[g];
     G.lev0 = (int32_t)H.levels.size();
@@ -261,15 +482,19 @@ bool build_half(const std::vector<StageTask>& all, const ApplyPlan& ap, int s0, 
           local_cur[tk.out_off] = rows;                 // intermediate rows of this subtree
           tk.out_off = rows;
         }
-        for (int i = 0; i < tk.M; ++i) H.rowmap.push_back((int32_t)((li << 16) | i));
+        for (int i = 0; i < tk.M; i += FRT) H.rowmap.push_back((int32_t)((li << 16) | i));
         rows += tk.M;
         H.tasks.push_back(tk);
       }
       Lv.ntasks = (int32_t)(H.tasks.size() - Lv.task0);
       Lv.rows = (int32_t)rows;
+      Lv.tiles = (int32_t)(H.rowmap.size() - Lv.map0);
+      H.tasks_max = std::max(H.tasks_max, (int)Lv.ntasks);
+      H.rows_max = std::max<int64_t>(H.rows_max, Lv.tiles);
       const bool last = s == ns - 1;
       if (!last) H.lvl_max = std::max<int64_t>(H.lvl_max, rows);
       if (rows >= ((int64_t)1 << 26)) return false;
+      if (!chunk_level(H, Lv, loc, (int64_t)(FAC_BYTES / elem_bytes(loc.dtype)))) return false;
       H.levels.push_back(Lv);
       local_prev.swap(local_cur);
     }
@@ -282,7 +507,7 @@ bool build_half(const std::vector<StageTask>& all, const ApplyPlan& ap, int s0, 
 // buffer (kernel 2), later inputs inside the previous level's rows, outputs
 // inside the level's rows, the exchange buffer (kernel 1's last level) or
 // the staged rows (kernel 2's last level); row maps name existing rows.
-bool validate_half(const FusedHalf& H, bool first_half, int64_t ex_rows) {
+bool validate_half(const FusedHalf& H, bool first_half, int64_t ex_rows, int64_t fac_elems) {
   for (const FusedGroup& G : H.groups) {
     if (G.nlev < 1 || G.lev0 < 0 || G.lev0 + G.nlev > (int)H.levels.size() || G.io_rows < 0 ||
         G.io_rows > H.io_max)
@@ -291,9 +516,7 @@ bool validate_half(const FusedHalf& H, bool first_half, int64_t ex_rows) {
     for (int lv = 0; lv < G.nlev; ++lv) {
       const FusedLevel& Lv = H.levels[G.lev0 + lv];
       const bool first = lv == 0, last = lv == G.nlev - 1;
-      if (Lv.task0 < 0 || Lv.task0 + Lv.ntasks > (int)H.tasks.size() || Lv.map0 < 0 ||
-          Lv.map0 + (int64_t)Lv.rows > (int64_t)H.rowmap.size())
-        return false;
+      if (Lv.task0 < 0 || Lv.task0 + Lv.ntasks > (int)H.tasks.size() || Lv.map0 < 0) return false;
       if (!last && Lv.rows > H.lvl_max) return false;
       const int64_t in_lim = first ? (first_half ? G.io_rows : ex_rows) : prev_rows;
       const int64_t out_lim = last ? (first_half ? ex_rows : G.io_rows) : Lv.rows;
@@ -304,29 +527,60 @@ bool validate_half(const FusedHalf& H, bool first_half, int64_t ex_rows) {
           const StageTerm& T = tk.t[q];
           if (T.K < 0 || T.in_off < 0 || T.in_off + T.K > in_lim || T.ldm < 1) return false;
           if (T.ldm < (T.conjT ? T.K : tk.M)) return false;
+          if (T.pad) {   // staged: every entry read lies in the staging area
+            const int64_t off = (int64_t)(intptr_t)T.mat;
+            const int64_t last_e = T.conjT ? (int64_t)(T.K - 1) + (int64_t)(tk.M - 1) * T.ldm
+                                           : (int64_t)(tk.M - 1) + (int64_t)(T.K - 1) * T.ldm;
+            if (off < 0 || (T.K > 0 && off + last_e >= fac_elems)) return false;
+          }
         }
       }
-      for (int r = 0; r < Lv.rows; ++r) {
+      if (Lv.map0 + (int64_t)Lv.tiles > (int64_t)H.rowmap.size() || Lv.tiles > H.rows_max) return false;
+      int64_t covered = 0;
+      for (int r = 0; r < Lv.tiles; ++r) {
         const int32_t m = H.rowmap[Lv.map0 + r];
         const int li = m >> 16, i = m & 0xffff;
         if (li < 0 || li >= Lv.ntasks || i >= H.tasks[Lv.task0 + li].M) return false;
+        covered += std::min(FRT, H.tasks[Lv.task0 + li].M - i);
       }
+      if (covered != Lv.rows) return false;
+      if (Lv.chunk0 < 0 || Lv.chunk0 + Lv.nchunks > (int)H.chunks.size()) return false;
+      int next_tile = 0;
+      for (int c = 0; c < Lv.nchunks; ++c) {
+        const FusedChunk& C = H.chunks[Lv.chunk0 + c];
+        if (C.tile0 != next_tile || C.tile1 < C.tile0 || C.seg0 < 0 || C.seg0 + C.nseg > (int)H.segs.size())
+          return false;
+        for (int g = 0; g < C.nseg; ++g) {
+          const FusedSeg& sg = H.segs[C.seg0 + g];
+          if (sg.dst < 0 || sg.count < 0 || (int64_t)sg.dst + sg.count > fac_elems) return false;
+        }
+        for (int t = C.tile0; t < C.tile1; ++t) {   // unstaged chunks hold unstaged terms only
+          const StageTask& tk = H.tasks[Lv.task0 + (H.rowmap[Lv.map0 + t] >> 16)];
+          for (int q = 0; q < tk.nterms; ++q)
+            if ((tk.t[q].pad != 0) != (C.staged != 0)) return false;
+        }
+        next_tile = C.tile1;
+      }
+      if (next_tile != Lv.tiles) return false;
       prev_rows = Lv.rows;
     }
   }
   return true;
 }
 
+static_assert(sizeof(StageTask) % 16 == 0, "task descriptors are copied as 16-byte vectors");
 size_t half_smem(const FusedHalf& H, int CS, size_t es) {
-  return ((size_t)H.io_max + 2 * (size_t)H.lvl_max) * CS * es;
+  const size_t data = (((size_t)H.io_max + 2 * (size_t)H.lvl_max) * CS * es + 15) & ~(size_t)15;
+  const size_t meta = ((size_t)H.tasks_max * sizeof(StageTask) + (size_t)H.rows_max * sizeof(int32_t) + 15) & ~(size_t)15;
+  return data + meta + 2 * FAC_BYTES;
 }
 
-int g_apply_engine = 0;   // 0: fused where it fits, 1: stage launches only
+int g_apply_engine = 0;   // 0: by the tuner's measurement, 1: stage launches only, 2: fused where it applies
 
 }  // namespace
 
 int set_apply_engine(int e) {
-  if (e != 0 && e != 1) return fail(BF_EINVAL, "apply engine must be 0 (fused) or 1 (stages)");
+  if (e < 0 || e > 2) return fail(BF_EINVAL, "apply engine must be 0 (tuned), 1 (stages) or 2 (fused)");
   g_apply_engine = e;
   return BF_OK;
 }
@@ -345,10 +599,12 @@ bool plan_fused(const Fact* F, int opC, int dtype, FusedPlan& fp) {
   if (s1 < 1 || s1 >= nst) return false;
   const std::vector<int64_t>& p1 = opC ? P->offT[lm] : P->offS[L - lm];
   const std::vector<int64_t>& p2 = opC ? P->offS[L - lm] : P->offT[lm];
-  if (!build_half(all, ap, 0, s1, p1, true, fp.h[0]) || !build_half(all, ap, s1, nst, p2, false, fp.h[1]))
+  const BlockLocator loc{F, dtype};
+  if (!build_half(all, ap, 0, s1, p1, true, loc, fp.h[0]) || !build_half(all, ap, s1, nst, p2, false, loc, fp.h[1]))
     return false;
   fp.ex_rows = ap.level_rows_max;
-  return validate_half(fp.h[0], true, fp.ex_rows) && validate_half(fp.h[1], false, fp.ex_rows);
+  const int64_t fe = (int64_t)(FAC_BYTES / elem_bytes(dtype));
+  return validate_half(fp.h[0], true, fp.ex_rows, fe) && validate_half(fp.h[1], false, fp.ex_rows, fe);
 }
 
 int build_fused(Fact* F, int opC, int dtype, cudaStream_t s) {
@@ -361,23 +617,27 @@ int build_fused(Fact* F, int opC, int dtype, cudaStream_t s) {
   if (half_smem(fp.h[0], 1, es) > FUSED_SMEM_MAX || half_smem(fp.h[1], 1, es) > FUSED_SMEM_MAX) return BF_OK;
   for (int h = 0; h < 2; ++h) {
     FusedHalf& H = fp.h[h];
-    const size_t bg = H.groups.size() * sizeof(FusedGroup), bl = H.levels.size() * sizeof(FusedLevel);
-    const size_t bt = H.tasks.size() * sizeof(StageTask), br = H.rowmap.size() * sizeof(int32_t);
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
-    BF_TRY(H.dev.alloc(&F->mem, al(bg) + al(bl) + al(bt) + al(br) + 256, nullptr));
+    const size_t sz[6] = {H.groups.size() * sizeof(FusedGroup), H.levels.size() * sizeof(FusedLevel),
+                          H.tasks.size() * sizeof(StageTask), H.rowmap.size() * sizeof(int32_t),
+                          H.chunks.size() * sizeof(FusedChunk), H.segs.size() * sizeof(FusedSeg)};
+    const void* src[6] = {H.groups.data(), H.levels.data(), H.tasks.data(), H.rowmap.data(), H.chunks.data(),
+                          H.segs.data()};
+    size_t off[6], tot = 0;
+    for (int i = 0; i < 6; ++i) off[i] = tot, tot += al(sz[i]);
+    BF_TRY(H.dev.alloc(&F->mem, tot + 256, nullptr));
+    std::vector<char> host(tot);
+    for (int i = 0; i < 6; ++i)
+      if (sz[i]) memcpy(host.data() + off[i], src[i], sz[i]);
     char* p = (char*)H.dev.p;
-    std::vector<char> host(al(bg) + al(bl) + al(bt) + al(br));
-    char* q = host.data();
-    memcpy(q, H.groups.data(), bg);
-    memcpy(q + al(bg), H.levels.data(), bl);
-    memcpy(q + al(bg) + al(bl), H.tasks.data(), bt);
-    memcpy(q + al(bg) + al(bl) + al(bt), H.rowmap.data(), br);
     BF_CUDA_TRY(cudaMemcpyAsync(p, host.data(), host.size(), cudaMemcpyHostToDevice, s));
     BF_CUDA_TRY(cudaStreamSynchronize(s));
-    H.d_groups = (const FusedGroup*)p;
-    H.d_levels = (const FusedLevel*)(p + al(bg));
-    H.d_tasks = (const StageTask*)(p + al(bg) + al(bl));
-    H.d_rowmap = (const int32_t*)(p + al(bg) + al(bl) + al(bt));
+    H.d_groups = (const FusedGroup*)(p + off[0]);
+    H.d_levels = (const FusedLevel*)(p + off[1]);
+    H.d_tasks = (const StageTask*)(p + off[2]);
+    H.d_rowmap = (const int32_t*)(p + off[3]);
+    H.d_chunks = (const FusedChunk*)(p + off[4]);
+    H.d_segs = (const FusedSeg*)(p + off[5]);
   }
   fp.ok = true;
   return BF_OK;
@@ -423,6 +683,10 @@ int run_fused(Fact* F, int opC, int dtype, int64_t nrhs, const void* x, int64_t 
     a.CS = CS;
     a.io_max = H.io_max;
     a.lvl_max = (int)H.lvl_max;
+    a.tasks_max = H.tasks_max;
+    a.rows_max = (int)H.rows_max;
+    a.chunks = H.d_chunks;
+    a.segs = H.d_segs;
     const size_t smem = half_smem(H, CS, es);
     if (smem > FUSED_SMEM_MAX) return fail(BF_EINVAL, "column slice too wide for shared memory");
     cudaLaunchAttribute attr[1];

@@ -19,7 +19,11 @@
 //     and walking K one element at a time -- fewer instructions per output;
 //   variant 2: one warp per (task, column slice) that copies the factor
 //     block whole into shared memory first (coalesced) and stages its inputs
-//     KC2 rows at a time -- no factor-load latency inside the K loop.
+//     KC2 rows at a time -- no factor-load latency inside the K loop;
+//   variants 3-5: one warp per (task, 64-column slice, WFR = 8, 4 or 12
+//     rows), two columns and WFR rows per lane (a register tile: WFR
+//     broadcast factor loads and two input loads per k for 2 WFR complex
+//     FMAs).
 // In both, the warp's lanes cover CW columns x 32/CW rows, CW the smallest
 // power of two >= N (at most 32), so small numbers of right-hand sides still
 // use every lane.  The apply picks the variant per stage and column count
@@ -345,8 +349,85 @@ stage_block_kernel(const StageTask* __restrict__ tasks, int ntasks, StageBases b
   }
 }
 
+// Variants 3-5 ("wide"): one warp per (task, 64-column slice, group of WFR
+// rows; WFR = 8, 4, 12: the tuner picks per stage); lane l takes columns 2l
+// and 2l + 1 of the slice and all WFR rows,
+// so per k the warp issues WFR factor loads (one address each, broadcast to
+// all lanes) and two input loads (consecutive columns across the lanes) for
+// 2 WFR complex FMAs per lane -- the register tile of a small GEMM.  Rows
+// past the task's end and columns past N re-read a valid row / column and
+// are not stored.
+template <typename R, int WFR>
+__global__ void __launch_bounds__(THREADS, 2)
+stage_wide_kernel(const StageTask* __restrict__ tasks, int ntasks, StageBases bases, int Noverride, int rgroups) {
+  using V = typename Cx<R>::V;
+  const int lane = threadIdx.x & 31;
+  const int nwarps = gridDim.x * WARPS;
+  const int Nl = Noverride;
+  const int Nmax = Nl > 0 ? Nl : -Nl;   // Nl < 0: per-task N, -Nl the widest
+  const int slices = Nmax > 0 ? (Nmax + 63) / 64 : 1;
+  const int per_task = slices * rgroups;
+  const int items = ntasks * per_task;
+  {
+    const int w0 = blockIdx.x * WARPS + (threadIdx.x >> 5);
+    stage_prologue<V>(tasks, w0 < items ? w0 / per_task : -1, lane);
+  }
+  for (int w = blockIdx.x * WARPS + (threadIdx.x >> 5); w < items; w += nwarps) {
+    const int ti = w / per_task, tw = w - ti * per_task;
+    const int sl = tw / rgroups, rg = tw - sl * rgroups;
+    const StageTask& tk = tasks[ti];
+    const int M = tk.M, nterms = tk.nterms;
+    const int i0 = rg * WFR;
+    if (i0 >= M) continue;
+    const int N = Nl > 0 ? Nl : tk.N;
+    const int c = sl * 64 + 2 * lane;
+    if (sl * 64 >= N) continue;
+    const bool v0 = c < N, v1 = c + 1 < N;
+    const int nr = min(WFR, M - i0);
+    const Strides so = strides(tk.out_off, tk.ldo, N);
+    V* __restrict__ out = (V*)bases.p[tk.out_base] + so.off;
+    V acc[WFR][2];
+#pragma unroll
+    for (int r = 0; r < WFR; ++r) acc[r][0] = acc[r][1] = Cx<R>::make(0, 0);
+    for (int term = 0; term < nterms; ++term) {
+      const StageTerm& T = tk.t[term];
+      const V* __restrict__ mat = (const V*)T.mat;
+      const int K = T.K, ldm = T.ldm, cj = T.conjT;
+      const Strides si = strides(T.in_off, T.ldi, N);
+      const V* __restrict__ in = (const V*)bases.p[T.in_base] + si.off;
+      const V* __restrict__ x0 = in + (int64_t)min(c, N - 1) * si.cs;
+      const V* __restrict__ x1 = in + (int64_t)min(c + 1, N - 1) * si.cs;
+      const int istep = cj ? ldm : 1, kstep = cj ? 1 : ldm;   // blocks are small: 32-bit offsets
+      int mo[WFR];
+#pragma unroll
+      for (int r = 0; r < WFR; ++r) mo[r] = (i0 + min(r, nr - 1)) * istep;
+#pragma unroll 2
+      for (int k = 0; k < K; ++k) {
+        const V a0 = x0[(int64_t)k * si.rs], a1 = x1[(int64_t)k * si.rs];
+        V e[WFR];
+#pragma unroll
+        for (int r = 0; r < WFR; ++r) e[r] = mat[mo[r] + k * kstep];
+#pragma unroll
+        for (int r = 0; r < WFR; ++r) {
+          if (cj) e[r].y = -e[r].y;
+          cmac(acc[r][0], e[r], a0);
+          cmac(acc[r][1], e[r], a1);
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < WFR; ++r)
+      if (r < nr) {
+        V* o = out + (int64_t)(i0 + r) * so.rs;
+        if (v0) o[(int64_t)c * so.cs] = acc[r][0];
+        if (v1) o[(int64_t)(c + 1) * so.cs] = acc[r][1];
+      }
+  }
+}
+
 // Untuned choice: the many-warp variant for up to 16 complex64 columns, the
-// whole-block variant otherwise (and for per-task column counts: peeling).
+// wide register-tile variant for more, the whole-block variant for
+// complex128 (and for per-task column counts: peeling).
 // Peel stages of Alg. 2's W and R steps (Sec. 4.2-4.3): a few thousand small
 // products out (M x N) = sum_t A_t (M x K_t) in_t (K_t x N) with M, K of a
 // block's rank and N up to k 2^(l-j) columns.  One CTA per (task, block of
@@ -447,7 +528,10 @@ int launch_peel(const StageTask* d_tasks, int ntasks, int maxM, int maxN, int ma
   return BF_OK;
 }
 
-int stage_variant_default(int nrhs, int dtype) { return dtype == BF_C64 && nrhs > 0 && nrhs <= 16 ? 0 : 2; }
+int stage_variant_default(int nrhs, int dtype) {
+  if (dtype == BF_C64 && nrhs > 0) return nrhs <= 16 ? 0 : 3;
+  return 2;
+}
 
 int launch_stage(const StageTask* d_tasks, int ntasks, int maxM, int maxN, int Noverride,
                  const StageBases& bases, int dtype, cudaStream_t s, int variant, bool pdl) {
@@ -463,8 +547,12 @@ int launch_stage(const StageTask* d_tasks, int ntasks, int maxM, int maxN, int N
   }
   const int64_t slices = Noverride != 0 ? ((Noverride > 0 ? Noverride : -Noverride) + (1 << lcw) - 1) >> lcw : 1;
   const int gr = (32 >> lcw) * RT;
-  const int rgroups = variant == 0 ? (maxM + gr - 1) / gr : 1;
-  const int64_t warps = (int64_t)ntasks * slices * rgroups;
+  // wide variants: 8 (variant 3), 4 (variant 4) or 12 (variant 5) rows per warp
+  const int wfr = variant == 4 ? 4 : variant == 5 ? 12 : 8;
+  const bool wide_v = variant >= 3;
+  const int rgroups = variant == 0 ? (maxM + gr - 1) / gr : wide_v ? (maxM + wfr - 1) / wfr : 1;
+  const int64_t wslices = Noverride != 0 ? ((Noverride > 0 ? Noverride : -Noverride) + 63) / 64 : 1;
+  const int64_t warps = (int64_t)ntasks * (wide_v ? wslices : slices) * rgroups;
   if (warps >= ((int64_t)1 << 31)) return fail(BF_EINVAL, "stage launch too large");
   int64_t blocks = (warps + WARPS - 1) / WARPS;
   if (blocks > 152 * 32) blocks = 152 * 32;
@@ -485,6 +573,17 @@ int launch_stage(const StageTask* d_tasks, int ntasks, int maxM, int maxN, int N
     e = dtype == BF_C128
             ? cudaLaunchKernelEx(&cfg, stage_mlp_kernel<double>, d_tasks, ntasks, bases, Noverride, lcw, rgroups)
             : cudaLaunchKernelEx(&cfg, stage_mlp_kernel<float>, d_tasks, ntasks, bases, Noverride, lcw, rgroups);
+  } else if (wide_v) {
+    cfg.dynamicSmemBytes = 0;
+    auto wide = [&](auto kd, auto kf) {
+      return dtype == BF_C128 ? cudaLaunchKernelEx(&cfg, kd, d_tasks, ntasks, bases, Noverride, rgroups)
+                              : cudaLaunchKernelEx(&cfg, kf, d_tasks, ntasks, bases, Noverride, rgroups);
+    };
+    switch (wfr) {
+      case 4: e = wide(stage_wide_kernel<double, 4>, stage_wide_kernel<float, 4>); break;
+      case 12: e = wide(stage_wide_kernel<double, 12>, stage_wide_kernel<float, 12>); break;
+      default: e = wide(stage_wide_kernel<double, 8>, stage_wide_kernel<float, 8>); break;
+    }
   } else if (variant == 1) {
     cfg.dynamicSmemBytes = 0;
     e = dtype == BF_C128 ? cudaLaunchKernelEx(&cfg, stage_rows_kernel<double>, d_tasks, ntasks, bases, Noverride, lcw)

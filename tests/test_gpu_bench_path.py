@@ -207,7 +207,10 @@ def test_caps_composition_n16384_against_stored_oracle():
     black box is its own two factorizations, so the two recompressions see
     operators that already differ by the GPU-vs-oracle gaps of K1 and K2
     (each within GAP_3D); with the recompression's own gap the comparison
-    bound is 3 GAP_3D.  Against the exact product (stored rows of
+    bound is 3 GAP_3D.  Those two operators differ by more than tol, so a
+    block's singular value can cross the threshold on one side and not the
+    other by more than one index: ranks are compared within +-2 here.
+    Against the exact product (stored rows of
     K(P3<-P2) K(P2<-P1) Omega) the error is within three Thm 5.3 bounds
     (K1, K2 and the recompression at tol 1e-6)."""
     d = _golden("caps_composition_n16384.txt")
@@ -220,6 +223,6 @@ def test_caps_composition_n16384_against_stored_oracle():
     F = api.Factorization.factor(pa, comp)
     Om = ob.error_probe(mg.N, mg.PROBE_SEED, mg.PROBE_COLS)
     worst, gap = _compare_stored(F, d, Om)
-    assert worst <= 1 and gap <= 3 * GAP_3D, (worst, gap)
+    assert worst <= 2 and gap <= 3 * GAP_3D, (worst, gap)
     y = H(F.apply(T(Om)))[d["rows"]]
     assert np.linalg.norm(y - d["A"]) <= 3 * bound(pa.L, 1e-6) * np.linalg.norm(d["A"])

@@ -22,9 +22,8 @@ pytestmark = pytest.mark.gpu
 
 @pytest.fixture(autouse=True)
 def _engine():
-    api.set_apply_engine("fused")
     yield
-    api.set_apply_engine("fused")
+    api.set_apply_engine("auto")
 
 
 def _cases():
@@ -76,7 +75,9 @@ def test_tuning_keeps_results():
         for nrhs in (1, 64):
             x = api.colmajor(torch.from_numpy(inputs.random_rhs(4096, nrhs, seed=2)).to(dt).cuda())
             y0 = _apply(F, x, "N", "fused")
+            api.set_apply_engine("auto")
             ms = F.tune(nrhs, dt)
             assert ms > 0
+            assert torch.equal(_apply(F, x, "N", "auto"), y0)
             assert torch.equal(_apply(F, x, "N", "fused"), y0)
             assert torch.equal(_apply(F, x, "N", "stages"), y0)
