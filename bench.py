@@ -355,6 +355,25 @@ def configs_measure():
     comp = api.Operator.composed(api.Operator.factored(K2), api.Operator.factored(K1))
     pa = api.Plan(P1, P3, **kw)
     ta, FA = timed(lambda: api.Factorization.factor(pa, comp))
+    # adjacent hemispheres (Sec. 7.3, Table 2's geometry): touching unit
+    # hemispheres, 10 points per wavelength, p 4, r0 64, leaf 64, tol 1e-4
+    # (Table 2's tightest), mixed with FP64 QR; factor time, the largest rank
+    # per level (the weak-admissibility growth) and the sketch error
+    hemi = {}
+    for nh in (16384, 65536):
+        gh = inputs.hemisphere_pair(nh)
+        ph = api.Plan(gh.src, gh.tgt, kernel="helmholtz3d", wavenumber=gh.wavenumber, leaf=64, tol=1e-4, p=4, r0=64,
+                      precision="mixed", qr_fp64=True)
+        oh = api.Operator.kernel(ph)
+        timed(lambda: api.Factorization.factor(ph, oh))
+        th, Fh = timed(lambda: api.Factorization.factor(ph, oh))
+        hemi[str(nh)] = {"factor_s": th, "L": ph.L,
+                         "max_rank_V": [int(Fh.ranks(0, j).max()) for j in range(ph.lm + 1)],
+                         "max_rank_U": [int(Fh.ranks(1, j).max()) for j in range(ph.lm, ph.L + 1)],
+                         "sketch_error": Fh.error(oh, 16, seed=7, dtype=torch.complex64),
+                         "bound": 2 * math.sqrt(ph.L + 2) * 1e-4}
+        del Fh, oh, ph
+    res["hemispheres_tol1e-4"] = hemi
     res["c4_composition"] = {"n": n, "k1_factor_s": tk1, "k2_factor_s": tk2, "recompress_s": ta,
                              "k1_error": K1.error(ok1, 16, seed=7), "k2_error": K2.error(ok2, 16, seed=7),
                              "recompress_error": FA.error(comp, 16, seed=7),

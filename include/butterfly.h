@@ -392,6 +392,18 @@ int bf_debug_wait_timeout(uint64_t limit_ns, void* stream);
  * against running applies. */
 int bf_set_apply_engine(int engine);
 
+/* Factorization schedule for the whole process: on = 1 (default) -- the
+ * two sides of Alg. 2, the row bases (loop "V" and the W levels) and the
+ * column bases (loop "U" and the R levels above the centre), which do not
+ * depend on each other until the centre level l_m (Secs. 4.2-4.3), run on
+ * two host threads and two streams, joined before the centre level (R^(l_m),
+ * X = V^H Omega, the B solve); every phase's launches are the same as in
+ * the sequential order, so results are identical.  Used for operators bound
+ * to the plan (dense and built-in kernel operators) without a memory cap;
+ * others run sequentially.  on = 0 -- always sequential.  BF_EINVAL
+ * otherwise.  Not thread-safe against running factorizations. */
+int bf_set_parallel_sides(int on);
+
 /* ------------------------------------------------------------- common -- */
 /* Frees a bf_plan, bf_fact, bf_operator or bf_applier (NULL-safe). */
 void bf_free(void* handle);

@@ -84,6 +84,7 @@ def lib():
         "bf_set_sketch_engine": (i32, [i32]),
         "bf_set_entry_images": (i32, [i32]),
         "bf_set_apply_engine": (i32, [i32]),
+        "bf_set_parallel_sides": (i32, [i32]),
         "bf_launch_count": (C.c_ulonglong, []),
         "bf_apply_tune": (i32, [vp, i32, i64, i32, vp, C.POINTER(C.c_float)]),
         "bf_applier_create": (i32, [vp, i32, i64, i32, C.POINTER(vp)]),
@@ -109,7 +110,7 @@ def exported_symbols():
             "bf_apply_T", "bf_apply_noalloc", "bf_ranks", "bf_fact_info", "bf_fact_import", "bf_fact_export", "bf_error",
             "bf_free", "bf_gaussian", "bf_set_sketch_engine", "bf_set_entry_images", "bf_launch_count", "bf_apply_tune",
             "bf_applier_create", "bf_applier_run", "bf_fact_accept", "bf_debug_wait_timeout",
-            "bf_set_apply_engine"]
+            "bf_set_apply_engine", "bf_set_parallel_sides"]
 
 
 def launch_count() -> int:
@@ -136,6 +137,12 @@ def debug_wait_timeout(limit_ns: int, stream=None) -> int:
     lowered to limit_ns (bf_debug_wait_timeout): -6 (BF_ETIMEOUT) is the
     designed outcome."""
     return int(lib().bf_debug_wait_timeout(int(limit_ns), _stream(stream)))
+
+
+def set_parallel_sides(on: bool):
+    """Run the two sides of Alg. 2 (row bases and column bases) concurrently
+    on two host threads and streams (default) or one after the other."""
+    check(lib().bf_set_parallel_sides(1 if on else 0))
 
 
 def set_apply_engine(engine: str):

@@ -6,6 +6,7 @@
 #include <atomic>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
 #include <numeric>
 #include <system_error>
@@ -110,11 +111,18 @@ int upload_async(void* dst, const void* src, size_t bytes, cudaStream_t s) {
   return BF_OK;
 }
 
+// MemTracker counters may be updated from the two sides of a factorization
+// running on two host threads (factor.cu)
+static std::mutex g_mem_mu;
+
 int dev_alloc(MemTracker* mt, void** p, size_t bytes, cudaStream_t s) {
   *p = nullptr;
   if (bytes == 0) bytes = 16;
-  if (mt && mt->cap && mt->used + bytes > mt->cap)
-    return fail(BF_ENOMEM, "allocation of " + std::to_string(bytes) + " bytes exceeds mem_cap");
+  {
+    std::lock_guard<std::mutex> lk(g_mem_mu);
+    if (mt && mt->cap && mt->used + bytes > mt->cap)
+      return fail(BF_ENOMEM, "allocation of " + std::to_string(bytes) + " bytes exceeds mem_cap");
+  }
   if (s) keep_pool(s);
   cudaError_t e = s ? cudaMallocAsync(p, bytes, s) : cudaMalloc(p, bytes);
   if (e != cudaSuccess) {
@@ -123,6 +131,7 @@ int dev_alloc(MemTracker* mt, void** p, size_t bytes, cudaStream_t s) {
     return fail(BF_ENOMEM, std::string("device allocation failed: ") + cudaGetErrorString(e));
   }
   if (mt) {
+    std::lock_guard<std::mutex> lk(g_mem_mu);
     mt->used += bytes;
     mt->peak = std::max(mt->peak, mt->used);
   }
@@ -135,7 +144,10 @@ void dev_free(MemTracker* mt, void* p, size_t bytes, cudaStream_t s) {
     cudaFreeAsync(p, s);
   else
     cudaFree(p);
-  if (mt) mt->used -= std::min(mt->used, bytes);
+  if (mt) {
+    std::lock_guard<std::mutex> lk(g_mem_mu);
+    mt->used -= std::min(mt->used, bytes);
+  }
 }
 
 int DevBuf::alloc(MemTracker* t, size_t b, cudaStream_t s) {
@@ -838,6 +850,7 @@ int bf_factor(bf_plan plan, bf_operator A, void* stream, bf_fact* out) {
 int bf_set_sketch_engine(int engine) { return set_sketch_engine(engine); }
 int bf_set_entry_images(int on) { return set_entry_images(on); }
 int bf_set_apply_engine(int engine) { return set_apply_engine(engine); }
+int bf_set_parallel_sides(int on) { return set_parallel_sides(on); }
 
 unsigned long long bf_launch_count(void) { return bf::launches_so_far(); }
 

@@ -382,8 +382,11 @@ struct LSQTask {
   void* B;            // rU x rV  output (complex128, ld rU)
   int32_t s, k, rU, rV;
 };
+// X^H and C^H live in shared memory when they fit, else in d_work
+// (lsq_workspace_bytes, 0 when not needed)
+size_t lsq_workspace_bytes(int ntasks, int maxK, int maxR);
 int launch_lsq(const LSQTask* d_tasks, int ntasks, int maxS, int maxK, int maxR,
-               int in_dtype, cudaStream_t s);
+               int in_dtype, void* d_work, size_t work_bytes, cudaStream_t s);
 
 // ------------------------------------------------------------- sketches --
 // Counter-based Gaussian generator (Philox-4x32-10 + Box-Muller).
@@ -527,6 +530,8 @@ void apply_tasks_host(const Fact* F, int opC, int dtype, ApplyPlan& ap, std::vec
 int apply_fact(Fact* F, int op, int64_t nrhs, const void* x, int64_t ldx,
                void* y, int64_t ldy, int dtype, cudaStream_t s, bool tree_order);
 int factor(Plan* P, Operator* A, cudaStream_t s, Fact** out);
+// 1 (default): the two sides of Alg. 2 on two host threads and streams; 0: one after the other
+int set_parallel_sides(int on);
 // factor() followed by the a-posteriori acceptance of bf_options.accept_retries
 int factor_accepted(Plan* P, Operator* A, cudaStream_t s, Fact** out);
 int sketch_error(Fact* f, Operator* A, int ncols, uint64_t seed, int dtype, cudaStream_t s, double* err);

@@ -22,8 +22,15 @@
 // r + p reaches the largest leaf; one sketch width per level; at l_m the
 // width also covers max r^V + p; B = (U^H K Omega)(V^H Omega)^+.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <memory>
+#include <string>
+#include <condition_variable>
+#include <functional>
+#include <mutex>
+#include <system_error>
+#include <thread>
 
 #include "bf_internal.h"
 
@@ -736,13 +743,186 @@ int r_phase(Batch& B, int t) {
       lt.push_back(tk);
     }
   }
-  Scratch d(B.s);
+  Scratch d(B.s), lw(B.s);
   BF_TRY(d.alloc(&B.mem, lt.size() * sizeof(LSQTask)));
   BF_TRY(upload_async(d.p(), lt.data(), lt.size() * sizeof(LSQTask), B.s));
-  BF_TRY(launch_lsq((const LSQTask*)d.p(), (int)lt.size(), maxS, maxK, maxR, B.dt, B.s));
+  const size_t lwb = lsq_workspace_bytes((int)lt.size(), maxK, maxR);
+  if (lwb) BF_TRY(lw.alloc(&B.mem, lwb));
+  BF_TRY(launch_lsq((const LSQTask*)d.p(), (int)lt.size(), maxS, maxK, maxR, B.dt, lw.p(), lwb, B.s));
   for (OpState* o : ctr) BF_TRY(make32(B, *o, o->F->st[o->F->stage_B()]));
   BF_CUDA_TRY(cudaStreamSynchronize(B.s));
   return BF_OK;
+}
+
+// A side's own copy of the batch: the same operators, plans and
+// factorizations, its own stream, phase state and arenas (the entry images
+// stay owned by the original batch; their device pointers are shared).
+Batch side_copy(const Batch& B, cudaStream_t s) {
+  Batch S;
+  S.s = s;
+  S.dt = B.dt;
+  S.es = B.es;
+  S.mem.cap = B.mem.cap;
+  S.ops.resize(B.ops.size());
+  for (size_t i = 0; i < B.ops.size(); ++i) {
+    const OpState& o = B.ops[i];
+    OpState& q = S.ops[i];
+    q.P = o.P;
+    q.A = o.A;
+    q.F = o.F;
+    q.L = o.L;
+    q.lm = o.lm;
+    q.nb = o.nb;
+    q.img_n = o.img_n;
+    q.img_c = o.img_c;
+  }
+  return S;
+}
+
+std::atomic<int> g_parallel_sides{1};
+
+// One persistent host thread for the W side of factorizations (its pinned
+// upload ring and CUDA state stay set up between calls); one factorization
+// uses it at a time, others run their sides sequentially.
+class SideWorker {
+ public:
+  static SideWorker* get() {
+    static SideWorker* w = make();
+    return w;
+  }
+  std::mutex use;   // held by the factorization whose W side runs here
+  void submit(std::function<void()> f) {
+    std::lock_guard<std::mutex> lk(mu_);
+    job_ = std::move(f);
+    has_ = true;
+    done_ = false;
+    cv_.notify_one();
+  }
+  void wait() {
+    std::unique_lock<std::mutex> lk(mu_);
+    done_cv_.wait(lk, [&] { return done_; });
+  }
+
+ private:
+  static SideWorker* make() {
+    SideWorker* w = new SideWorker();   // lives until the process exits
+    try {
+      std::thread([w] { w->loop(); }).detach();
+    } catch (const std::system_error&) {
+      delete w;
+      return nullptr;
+    }
+    return w;
+  }
+  void loop() {
+    for (;;) {
+      std::function<void()> f;
+      {
+        std::unique_lock<std::mutex> lk(mu_);
+        cv_.wait(lk, [&] { return has_; });
+        f = std::move(job_);
+        has_ = false;
+      }
+      f();
+      {
+        std::lock_guard<std::mutex> lk(mu_);
+        done_ = true;
+      }
+      done_cv_.notify_all();
+    }
+  }
+  std::mutex mu_;
+  std::condition_variable cv_, done_cv_;
+  std::function<void()> job_;
+  bool has_ = false, done_ = true;
+};
+
+// Alg. 2's loops for all operators.  The row-basis side (loop "V", then the
+// W levels) and the column-basis side (loop "U", then the R levels above
+// the centre) do not depend on each other (Sec. 4.2-4.3); only the centre
+// level (R at l_m, X = V^H Omega, the B solve) needs both.  So the W side
+// runs on a second host thread and stream while this thread runs the R
+// side, and joins it before the first centre level: each side's host
+// synchronisations and latency-bound phases (QR, peeling) overlap the other
+// side's sketches.  The launches of every phase are the same as when the
+// sides run one after the other, so the results are identical.  Operators
+// not bound to the plan (callbacks, factored and composed operators, whose
+// products may share state) and memory-capped batches run sequentially.
+int run_sides(Batch& B, int maxlm, int maxr) {
+  bool parallel = g_parallel_sides.load() != 0 && B.mem.cap == 0;
+  for (const auto& o : B.ops) parallel = parallel && o.A->plan == o.P && o.F->mem.cap == 0;
+  if (!parallel) {
+    int rc = leaf_phase(B, true);
+    if (!rc) rc = leaf_phase(B, false);
+    for (int t = 1; !rc && t <= maxlm; ++t) rc = w_phase(B, t);
+    for (int t = 1; !rc && t <= maxr; ++t) rc = r_phase(B, t);
+    return rc;
+  }
+  cudaStream_t sw = nullptr;
+  cudaEvent_t ev = nullptr;
+  BF_CUDA_TRY(cudaStreamCreateWithFlags(&sw, cudaStreamNonBlocking));
+  if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess || cudaEventRecord(ev, B.s) != cudaSuccess ||
+      cudaStreamWaitEvent(sw, ev, 0) != cudaSuccess) {   // the W side starts after the entry images
+    if (ev) cudaEventDestroy(ev);
+    cudaStreamDestroy(sw);
+    return fail(BF_ECUDA, "side stream set-up failed");
+  }
+  Batch BW = side_copy(B, sw), BR = side_copy(B, B.s);
+  int rcw = BF_OK;
+  std::string errw;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  auto w_side = [&]() {
+    int rc = cudaSetDevice(dev) == cudaSuccess ? BF_OK : fail(BF_ECUDA, "W side: cudaSetDevice failed");
+    try {
+      if (!rc) rc = leaf_phase(BW, true);
+      for (int t = 1; !rc && t <= maxlm; ++t) rc = w_phase(BW, t);
+    } catch (...) {   // no exception may leave the worker
+      rc = fail(BF_ENOMEM, "host allocation failed on the W side");
+    }
+    const cudaError_t e = cudaStreamSynchronize(sw);   // (the last factor copies)
+    if (!rc && e != cudaSuccess) rc = fail(BF_ECUDA, std::string("W side: ") + cudaGetErrorString(e));
+    if (rc) errw = bf_last_error();
+    rcw = rc;
+  };
+  SideWorker* worker = SideWorker::get();
+  std::unique_lock<std::mutex> held;
+  if (worker) held = std::unique_lock<std::mutex>(worker->use, std::try_to_lock);
+  const bool threaded = worker && held.owns_lock();
+  if (threaded)
+    worker->submit(w_side);
+  else
+    w_side();   // no worker free: the W side first, here
+  bool joined = !threaded;
+  auto join = [&]() {
+    if (!joined) worker->wait(), joined = true;
+  };
+  int rc = BF_OK;
+  try {
+    rc = leaf_phase(BR, false);
+    for (int t = 1; !rc && t <= maxr; ++t) {
+      bool centre = false;
+      for (const auto& o : BR.ops) centre = centre || o.L - t == o.lm;
+      if (centre) {
+        join();
+        if (rcw) break;
+      }
+      rc = r_phase(BR, t);
+    }
+  } catch (...) {
+    rc = fail(BF_ENOMEM, "host allocation failed on the R side");
+  }
+  join();
+  for (auto& o : BW.ops) o.Y.release(sw);
+  for (auto& o : BR.ops) o.Y.release(B.s);
+  cudaStreamSynchronize(sw);
+  cudaEventDestroy(ev);
+  cudaStreamDestroy(sw);
+  if (rcw) {
+    set_error(errw);
+    return rcw;
+  }
+  return rc;
 }
 
 void destroy(Fact* F) {
@@ -800,10 +980,7 @@ int factor_batch(int count, Plan* const* P, Operator* const* A, cudaStream_t s, 
     maxr = std::max(maxr, o.L - o.lm);
   }
   int rc = make_images(B);
-  if (!rc) rc = leaf_phase(B, true);
-  if (!rc) rc = leaf_phase(B, false);
-  for (int t = 1; !rc && t <= maxlm; ++t) rc = w_phase(B, t);
-  for (int t = 1; !rc && t <= maxr; ++t) rc = r_phase(B, t);
+  if (!rc) rc = run_sides(B, maxlm, maxr);
   if (!rc) {
     const cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) rc = fail(BF_ECUDA, cudaGetErrorString(e));
@@ -825,6 +1002,12 @@ int factor_batch(int count, Plan* const* P, Operator* const* A, cudaStream_t s, 
     F->seconds = secs;
     out[i] = F;
   }
+  return BF_OK;
+}
+
+int set_parallel_sides(int on) {
+  if (on != 0 && on != 1) return fail(BF_EINVAL, "parallel sides: 0 or 1");
+  g_parallel_sides.store(on);
   return BF_OK;
 }
 

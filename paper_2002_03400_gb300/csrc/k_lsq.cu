@@ -4,7 +4,9 @@
 //   X = V_{tau,nu}^H Omega_nu              (r^V x k, k >= r^V + p)
 //   B = argmin ||C - B X||_F = C X^+
 // solved through the Householder QR X^H = Qx Rx:  B^H = Rx^{-1} Qx^H C^H.
-// One CTA per block; everything in shared memory.
+// One CTA per block; X^H and C^H in shared memory when they fit, else in a
+// per-task global workspace (same code, pointer switch: weakly admissible
+// geometries reach centre ranks of hundreds).
 #include "bf_internal.h"
 #include "cx.cuh"
 
@@ -30,13 +32,13 @@ __device__ __forceinline__ double wsum(double v) {
 
 template <typename VIn>
 __global__ void __launch_bounds__(LSQ_THREADS)
-lsq_kernel(const LSQTask* __restrict__ tasks, int maxK, int maxR) {
+lsq_kernel(const LSQTask* __restrict__ tasks, int maxK, int maxR, double2* __restrict__ gwork, int use_smem) {
   extern __shared__ double2 sm[];
   const LSQTask t = tasks[blockIdx.x];
   const int s = t.s, k = t.k, rU = t.rU, rV = t.rV;
-  double2* XH = sm;                        // k x rV   (ld k)
-  double2* CH = sm + maxK * maxR;          // k x rU   (ld k)
-  double* tau = (double*)(CH + maxK * maxR);   // rV
+  double2* XH = use_smem ? sm : gwork + (int64_t)blockIdx.x * 2 * maxK * maxR;   // k x rV (ld k)
+  double2* CH = XH + (int64_t)maxK * maxR;                                       // k x rU (ld k)
+  double* tau = (double*)(use_smem ? CH + (int64_t)maxK * maxR : sm);             // rV
   double* rdiag = tau + maxR;                  // rV (real part of alpha unused)
   double2* alpha = (double2*)(rdiag + maxR);   // rV
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -130,18 +132,34 @@ lsq_kernel(const LSQTask* __restrict__ tasks, int maxK, int maxR) {
   }
 }
 
-int launch_lsq(const LSQTask* d_tasks, int ntasks, int maxS, int maxK, int maxR, int in_dtype,
-               cudaStream_t s) {
+namespace {
+size_t lsq_block_bytes(int maxK, int maxR) { return (size_t)2 * maxK * maxR * sizeof(double2); }
+size_t lsq_meta_bytes(int maxR) { return (size_t)maxR * (2 * sizeof(double) + sizeof(double2)); }
+constexpr size_t LSQ_SMEM_LIMIT = 220 * 1024;
+}  // namespace
+
+size_t lsq_workspace_bytes(int ntasks, int maxK, int maxR) {
+  if (lsq_block_bytes(maxK, maxR) + lsq_meta_bytes(maxR) <= LSQ_SMEM_LIMIT) return 0;
+  return lsq_block_bytes(maxK, maxR) * (size_t)ntasks;
+}
+
+int launch_lsq(const LSQTask* d_tasks, int ntasks, int maxS, int maxK, int maxR, int in_dtype, void* d_work,
+               size_t work_bytes, cudaStream_t s) {
   if (ntasks <= 0) return BF_OK;
-  const size_t smem = (size_t)2 * maxK * maxR * sizeof(double2) + (size_t)maxR * (2 * sizeof(double) + sizeof(double2));
-  if (smem > 220 * 1024) return fail(BF_EUNSUPPORTED, "B least-squares block too large for shared memory");
+  const int use_smem = lsq_block_bytes(maxK, maxR) + lsq_meta_bytes(maxR) <= LSQ_SMEM_LIMIT ? 1 : 0;
+  const size_t smem = (use_smem ? lsq_block_bytes(maxK, maxR) : 0) + lsq_meta_bytes(maxR);
+  if (smem > LSQ_SMEM_LIMIT) return fail(BF_EUNSUPPORTED, "B least-squares ranks too large");
+  if (!use_smem && (d_work == nullptr || work_bytes < lsq_block_bytes(maxK, maxR) * (size_t)ntasks))
+    return fail(BF_EINVAL, "B least-squares workspace too small");
   note_launch();
   if (in_dtype == BF_C128) {
-    BF_CUDA_TRY(cudaFuncSetAttribute(lsq_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    lsq_kernel<double2><<<ntasks, LSQ_THREADS, smem, s>>>(d_tasks, maxK, maxR);
+    BF_CUDA_TRY(cudaFuncSetAttribute(lsq_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)LSQ_SMEM_LIMIT));   // the largest size, whatever this launch needs
+    lsq_kernel<double2><<<ntasks, LSQ_THREADS, smem, s>>>(d_tasks, maxK, maxR, (double2*)d_work, use_smem);
   } else {
-    BF_CUDA_TRY(cudaFuncSetAttribute(lsq_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    lsq_kernel<float2><<<ntasks, LSQ_THREADS, smem, s>>>(d_tasks, maxK, maxR);
+    BF_CUDA_TRY(cudaFuncSetAttribute(lsq_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)LSQ_SMEM_LIMIT));
+    lsq_kernel<float2><<<ntasks, LSQ_THREADS, smem, s>>>(d_tasks, maxK, maxR, (double2*)d_work, use_smem);
   }
   BF_CUDA_TRY(cudaGetLastError());
   return BF_OK;

@@ -516,11 +516,14 @@ int launch_peel(const StageTask* d_tasks, int ntasks, int maxM, int maxN, int ma
   if (bytes(CB) > 96 * 1024) return BF_OK;   // very large blocks: the stage kernels
   const dim3 grid((unsigned)ntasks, (unsigned)((maxN + CB - 1) / CB));
   note_launch();
+  // the attribute is the kernel's largest size, not this launch's: launches
+  // from two host threads (the two sides of a factorization) must not lower
+  // it under each other
   if (dtype == BF_C128) {
-    BF_CUDA_TRY(cudaFuncSetAttribute(peel_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes(CB)));
+    BF_CUDA_TRY(cudaFuncSetAttribute(peel_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
     peel_kernel<double><<<grid, 256, bytes(CB), s>>>(d_tasks, bases, CB, maxM, maxK);
   } else {
-    BF_CUDA_TRY(cudaFuncSetAttribute(peel_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes(CB)));
+    BF_CUDA_TRY(cudaFuncSetAttribute(peel_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
     peel_kernel<float><<<grid, 256, bytes(CB), s>>>(d_tasks, bases, CB, maxM, maxK);
   }
   BF_CUDA_TRY(cudaGetLastError());

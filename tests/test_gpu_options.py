@@ -146,3 +146,50 @@ def test_bounded_wait_gives_up_and_reports_timeout():
     plan = api.Plan(g.src, g.tgt, kernel="helmholtz2d", wavenumber=g.wavenumber, leaf=16, precision="mixed")
     Fk = api.Factorization.factor(plan, api.Operator.kernel(plan))    # tensor-core kernels, bounded waits
     assert Fk.error(api.Operator.kernel(plan), 16, seed=3, dtype=torch.complex64) <= 2 * math.sqrt(plan.L + 2) * 1e-6
+
+
+@pytest.mark.parametrize("case", ["line-mixed-fp64qr", "cap-ragged-mixed", "line-fp64-dense", "arc-batch"])
+def test_parallel_sides_equal_sequential(case):
+    """The two sides of Alg. 2 on two threads and streams (default) give the
+    factorization the sequential schedule gives, bit for bit."""
+    def build():
+        if case == "line-mixed-fp64qr":
+            g = inputs.line_pair(4096)
+            p = api.Plan(g.src, g.tgt, kernel="helmholtz2d", wavenumber=g.wavenumber, leaf=16, tol=1e-6,
+                         precision="mixed", r0=16, qr_fp64=True)
+            return [p], [api.Operator.kernel(p)]
+        if case == "cap-ragged-mixed":
+            g = inputs.cap_pair(777, m=700)
+            p = api.Plan(g.src, g.tgt, kernel=g.kernel, wavenumber=g.wavenumber, leaf=24, tol=1e-6, precision="mixed")
+            return [p], [api.Operator.kernel(p)]
+        if case == "line-fp64-dense":
+            g = inputs.line_pair(1024)
+            A = oo.kernel_entries(oo.HELMHOLTZ_2D, g.wavenumber, g.tgt, g.src)
+            p = api.Plan(g.src, g.tgt, kernel="helmholtz2d", wavenumber=g.wavenumber, leaf=16, tol=1e-6)
+            return [p], [api.Operator.dense(p, T(A))]
+        plans, ops = [], []
+        for i, n in enumerate((1024, 2048, 1024, 4096)):
+            g = inputs.arc_pair(n, seed=40 + i)
+            p = api.Plan(g.src, g.tgt, kernel=g.kernel, wavenumber=g.wavenumber, leaf=32, tol=1e-5,
+                         precision="mixed", seed=i, qr_fp64=True)
+            plans.append(p)
+            ops.append(api.Operator.kernel(p))
+        return plans, ops
+
+    plans, ops = build()
+    out = {}
+    for on in (True, False):
+        api.set_parallel_sides(on)
+        if len(plans) == 1:
+            out[on] = [api.Factorization.factor(plans[0], ops[0])]
+        else:
+            out[on] = api.Factorization.factor_batch(plans, ops)
+    api.set_parallel_sides(True)
+    for Fp, Fs, p in zip(out[True], out[False], plans):
+        for j in range(p.lm + 1):
+            assert np.array_equal(Fp.ranks(0, j), Fs.ranks(0, j))
+        for j in range(p.lm, p.L + 1):
+            assert np.array_equal(Fp.ranks(1, j), Fs.ranks(1, j))
+        x = T(inputs.random_rhs(p.n, 3, seed=7), torch.complex128)
+        assert torch.equal(Fp.apply(x), Fs.apply(x))
+        assert Fp.info()["cols_N"] == Fs.info()["cols_N"] and Fp.info()["cols_T"] == Fs.info()["cols_T"]
