@@ -49,8 +49,8 @@ ALU_OPS_PER_ENTRY = 71
 # (the image profile case), from ncu; the image read once, X and Y.  Valid
 # only for the kernel source it was captured on (SHA-256 prefix below); after
 # any change to that file the line reports traffic null until a new capture.
-IMG_TRAFFIC_N8192 = 541691392 + 6331136
-IMG_TRAFFIC_SOURCE_SHA = "855dbb3477a2674a"
+IMG_TRAFFIC_N8192 = 541692672 + 6614272
+IMG_TRAFFIC_SOURCE_SHA = "d8d6861de3c0c4e2"
 
 
 def measured_peaks():

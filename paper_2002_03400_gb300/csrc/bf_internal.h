@@ -364,12 +364,12 @@ struct QRTask {
 // Truncated column-pivoted Householder QR (Alg. 1 step 3); ranks[i] out.
 // in dtype: C128 (factored in FP64) or C64 (factored in float-float, or in
 // FP64 when fp64 is set); q is complex128 either way.
-// Both kernels give a block's column RG lanes, RG = qr_lanes(rows): a block's
+// Both kernels give a block's column RG lanes, RG = qr_lanes(rows, ...): a block's
 // arithmetic (the row striding of its partial sums) depends on its own size
 // only if every launch holds blocks of one qr_lanes class, so that the
 // result of a block does not depend on what else is in the launch (batched
 // factorizations equal individual ones bit for bit).  launch_qr requires it.
-int qr_lanes(int s);
+int qr_lanes(int s, int in_dtype, bool fp64);
 int launch_qr(const QRTask* d_tasks, int ntasks, int maxS, int maxK, int in_dtype, bool fp64,
               int32_t* d_ranks, void* d_work, size_t work_bytes, cudaStream_t s);
 size_t qr_workspace_bytes(int ntasks, int maxS, int maxK, int in_dtype, bool fp64);

@@ -294,7 +294,7 @@ int qr_all(Batch& B, std::vector<QRJob>& jobs) {
   std::vector<int> order(nt);
   for (int i = 0; i < nt; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(),
-                   [&](int a, int b) { return qr_lanes(tasks[a].s) < qr_lanes(tasks[b].s); });
+                   [&](int a, int b) { return qr_lanes(tasks[a].s, B.dt, fp64) < qr_lanes(tasks[b].s, B.dt, fp64); });
   std::vector<QRTask> sorted(nt);
   for (int i = 0; i < nt; ++i) sorted[i] = tasks[order[i]];
   struct Range {
@@ -303,9 +303,9 @@ int qr_all(Batch& B, std::vector<QRJob>& jobs) {
   std::vector<Range> ranges;
   size_t wbytes = 0;
   for (int i = 0; i < nt;) {
-    const int cls = qr_lanes(sorted[i].s);
+    const int cls = qr_lanes(sorted[i].s, B.dt, fp64);
     Range r{i, i, 1, 1};
-    while (r.b < nt && qr_lanes(sorted[r.b].s) == cls) {
+    while (r.b < nt && qr_lanes(sorted[r.b].s, B.dt, fp64) == cls) {
       r.maxS = std::max(r.maxS, (int)sorted[r.b].s);
       r.maxK = std::max(r.maxK, (int)sorted[r.b].k);
       ++r.b;

