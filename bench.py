@@ -199,18 +199,48 @@ def profile_case(args):
     print("profile case done")
 
 
-def serving_measure(seconds: float = 4.0):
-    """Serving: resident factorizations (arcs n = 4096 and 16384, caps
-    n = 4096), Poisson requests (80% applies of 1..64 complex64/complex128
-    right-hand sides, 20% factor requests n in {4096, 16384} on arcs/caps)
-    at 0.5x and 2x the capacity of a one-request-at-a-time plain FP64
-    baseline; p50/p99 latency and applies/s of both."""
+def serving_measure(seconds: float = 4.0, saturation_requests: int = 200):
+    """Serving (continuous batching over resident factorizations: arcs n =
+    4096 and 16384, caps n = 4096 and 16384; mixed precision, FP64 QR).
+
+    * capacity of the served form: `saturation_requests` requests of the
+      serving mix (80% applies of 1..64 complex64/complex128 right-hand
+      sides, 20% factor requests n in {4096, 16384, 65536} on arcs/caps) all
+      queued at once; requests, applies and factorizations per second over
+      the makespan, with the latency percentiles of that backlog;
+    * Poisson arrivals at 0.5x and 2x the capacity of a one-request-at-a-
+      time plain FP64 baseline (FP64 factors, complex128 products), served
+      and baseline replays of the same trace; factor sizes there are 4096
+      and 16384 (an FP64 factorization at n = 65536 takes tens of seconds,
+      too long for a bounded run)."""
     import torch
     from paper_2002_03400_gb300 import inputs, serve
-    sizes = {"arc4k": (4096, "arc"), "arc16k": (16384, "arc"), "cap4k": (4096, "cap")}
+    sizes = {"arc4k": (4096, "arc"), "arc16k": (16384, "arc"), "cap4k": (4096, "cap"), "cap16k": (16384, "cap")}
     res = {k: serve.build_factor(serve.factor_spec(n, geo, seed=i)) for i, (k, (n, geo)) in enumerate(sizes.items())}
     names = list(res)
     nof = {k: sizes[k][0] for k in res}
+    out = {"resident": {k: sizes[k][0] for k in sizes}}
+
+    # capacity of the served form: the whole backlog at t = 0
+    # (unit rate: about 1.5 x saturation_requests arrivals, the first kept)
+    tr = inputs.serving_trace(1.5 * saturation_requests + 50, 1.0, seed=31, resident=len(names),
+                              factor_sizes=(4096, 16384, 65536))[:saturation_requests]
+    jobs = serve.make_jobs(tr, names, nof, seed=9)
+    for j in jobs:
+        j.t_arrive = 0.0
+    srv = serve.Server(mem_cap=150e9, factor_workers=2)
+    for k, F in res.items():
+        srv.add_resident(k, F)
+    t0 = time.perf_counter()
+    done = srv.run(jobs, realtime=False)
+    torch.cuda.synchronize()
+    span = time.perf_counter() - t0
+    srv.close()
+    for j in done:   # new factorizations are not kept
+        if j.kind == "factor" and j.result is not None:
+            j.result.free()
+            j.result = None
+    out["capacity"] = dict(serve.throughput_stats(done, span), **{"backlog": serve.latency_stats(done)})
 
     def baseline(jobs):
         """one request at a time, FP64 factors and complex128 products"""
@@ -230,17 +260,18 @@ def serving_measure(seconds: float = 4.0):
         return jobs
 
     # capacity of the baseline: mean service time on a short sample
-    probe = serve.make_jobs(inputs.serving_trace(1.0, 40.0, seed=11, resident=3, factor_sizes=(4096, 16384)),
+    probe = serve.make_jobs(inputs.serving_trace(1.0, 40.0, seed=11, resident=len(names), factor_sizes=(4096, 16384)),
                             names, nof, seed=5)
     for j in probe:
         j.t_arrive = 0.0
     t0 = time.perf_counter()
     baseline(probe)
     cap = len(probe) / (time.perf_counter() - t0)
-    out = {"baseline_capacity_req_per_s": cap, "seconds": seconds}
+    out["baseline_capacity_req_per_s"] = cap
+    out["seconds"] = seconds
     for mult in (0.5, 2.0):
         rate = cap * mult
-        tr = inputs.serving_trace(seconds, rate, seed=21, resident=3, factor_sizes=(4096, 16384))
+        tr = inputs.serving_trace(seconds, rate, seed=21, resident=len(names), factor_sizes=(4096, 16384))
         jobs = serve.make_jobs(tr, names, nof, seed=6)
         srv = serve.Server(mem_cap=150e9, factor_workers=2)
         for k, F in res.items():
@@ -288,11 +319,17 @@ def batched_measure(count: int = 64, reps: int = 2):
     batched(), sequential()   # warm-up
     tb = min(batched()[0] for _ in range(reps))
     ts, Fs_seq = min((sequential() for _ in range(reps)), key=lambda r: r[0])
+    s0 = api.sync_count()
     _, Fs = batched()
+    syncs_b = api.sync_count() - s0
+    s0 = api.sync_count()
+    sequential()
+    syncs_s = api.sync_count() - s0
     errs = [F.error(o, 16, seed=5) for F, o in zip(Fs, ops)]
     bound = max(2 * math.sqrt(p.L + 2) * 1e-5 for p in plans)
     return {"operators": count, "n_total": int(sum(sizes)), "sizes": {str(k): sizes.count(k) for k in sorted(set(sizes))},
             "batched_s": tb, "sequential_s": ts, "speedup": ts / tb,
+            "host_syncs_batched": syncs_b, "host_syncs_sequential": syncs_s,
             "max_sketch_error": float(max(errs)), "error_bound": bound,
             "all_within_bound": bool(all(e <= 2 * math.sqrt(p.L + 2) * 1e-5 for e, p in zip(errs, plans)))}
 
@@ -400,7 +437,7 @@ def run_reference(args):
     other ranks exit without work).  Warm-up steps are small untimed oracle
     runs (n = 256: imports, BLAS threads, page-in).  Each timed step is one
     full oracle factorization (minutes); the arm runs as many of the
-    requested steps as fit in BF_REFERENCE_BUDGET_S seconds (default 600,
+    requested steps as fit in BF_REFERENCE_BUDGET_S seconds (default 300,
     at least one) and prints the number it ran."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -409,7 +446,7 @@ def run_reference(args):
     n_ref = int(os.environ.get("BF_REFERENCE_N", str(N)))
     for _ in range(args.warmup):   # untimed
         oracle_factor_seconds(256)
-    budget = float(os.environ.get("BF_REFERENCE_BUDGET_S", "600"))
+    budget = float(os.environ.get("BF_REFERENCE_BUDGET_S", "300"))
     samples = []
     t_start = time.perf_counter()
     while len(samples) < args.steps:
@@ -507,6 +544,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     launches0 = api.launch_count()
+    syncs0 = api.sync_count()
     with clk:
         for i in range(args.steps):
             flush.fill_(1.0)
@@ -517,6 +555,7 @@ def main():
             errs.append(err)
         torch.cuda.synchronize()
     gpu_launches = api.launch_count() - launches0
+    host_syncs = api.sync_count() - syncs0
     if dist:
         dist.barrier()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
@@ -704,6 +743,7 @@ def main():
         "clocks": clocks,
         "gpu_launches": gpu_launches,
         "gpu_launches_per_step": gpu_launches / max(1, args.steps),
+        "host_syncs_per_step": host_syncs / max(1, args.steps),
         "peaks_source": peak_src,
         "serving": serving,
         "batched": batched,

@@ -417,6 +417,13 @@ const char* bf_last_error(void);
  * Never fails. */
 unsigned long long bf_launch_count(void);
 
+/* Number of host synchronisations factorizations of this library have made
+ * in this process so far (all threads; monotone): one per phase of Alg. 2
+ * (the ranks a phase reveals size the next phase's sketch), the centre
+ * level's solve and the end of each factorization (and of its second side).
+ * Diagnostic, like bf_launch_count; never fails. */
+unsigned long long bf_sync_count(void);
+
 /* Device-side Gaussian test/sketch matrix of the counter-based generator:
  * G[i, c - col0] for rows row0..row0+rows-1, columns col0..col1-1 of
  * (seed, stream) into a device buffer (ld >= rows), dtype C64/C128. */

@@ -86,6 +86,7 @@ def lib():
         "bf_set_apply_engine": (i32, [i32]),
         "bf_set_parallel_sides": (i32, [i32]),
         "bf_launch_count": (C.c_ulonglong, []),
+        "bf_sync_count": (C.c_ulonglong, []),
         "bf_apply_tune": (i32, [vp, i32, i64, i32, vp, C.POINTER(C.c_float)]),
         "bf_applier_create": (i32, [vp, i32, i64, i32, C.POINTER(vp)]),
         "bf_applier_run": (i32, [vp, vp, i64, vp, i64, vp]),
@@ -110,12 +111,17 @@ def exported_symbols():
             "bf_apply_T", "bf_apply_noalloc", "bf_ranks", "bf_fact_info", "bf_fact_import", "bf_fact_export", "bf_error",
             "bf_free", "bf_gaussian", "bf_set_sketch_engine", "bf_set_entry_images", "bf_launch_count", "bf_apply_tune",
             "bf_applier_create", "bf_applier_run", "bf_fact_accept", "bf_debug_wait_timeout",
-            "bf_set_apply_engine", "bf_set_parallel_sides"]
+            "bf_set_apply_engine", "bf_set_parallel_sides", "bf_sync_count"]
 
 
 def launch_count() -> int:
     """Kernels the library has launched in this process so far."""
     return int(lib().bf_launch_count())
+
+
+def sync_count() -> int:
+    """Host synchronisations the library's factorizations have made so far."""
+    return int(lib().bf_sync_count())
 
 
 def set_sketch_engine(engine: str):

@@ -421,9 +421,11 @@ int upload(MemTracker* mt, DevBuf& b, const void* src, size_t bytes) {
 
 }  // namespace
 
-static std::atomic<unsigned long long> g_launches{0};
+static std::atomic<unsigned long long> g_launches{0}, g_syncs{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 unsigned long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+void note_sync() { g_syncs.fetch_add(1, std::memory_order_relaxed); }
+unsigned long long syncs_so_far() { return g_syncs.load(std::memory_order_relaxed); }
 }  // namespace bf
 
 using namespace bf;
@@ -853,6 +855,7 @@ int bf_set_apply_engine(int engine) { return set_apply_engine(engine); }
 int bf_set_parallel_sides(int on) { return set_parallel_sides(on); }
 
 unsigned long long bf_launch_count(void) { return bf::launches_so_far(); }
+unsigned long long bf_sync_count(void) { return bf::syncs_so_far(); }
 
 int bf_factor_batch(int count, const bf_plan* plans, const bf_operator* ops, void* stream, bf_fact* out) {
   if (!out || !plans || count < 1) return fail(BF_EINVAL, "bad batch arguments");

@@ -472,6 +472,9 @@ int entry_images_enabled();
 // counts one kernel launch of this library (bf_launch_count)
 void note_launch();
 unsigned long long launches_so_far();
+// counts one host synchronisation of a factorization (bf_sync_count)
+void note_sync();
+unsigned long long syncs_so_far();
 // 0: tensor-core sketch where it applies (default), 1: SIMT sketch only
 int set_sketch_engine(int e);
 struct GemmGroups;

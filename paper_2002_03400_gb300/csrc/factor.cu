@@ -750,6 +750,7 @@ int r_phase(Batch& B, int t) {
   if (lwb) BF_TRY(lw.alloc(&B.mem, lwb));
   BF_TRY(launch_lsq((const LSQTask*)d.p(), (int)lt.size(), maxS, maxK, maxR, B.dt, lw.p(), lwb, B.s));
   for (OpState* o : ctr) BF_TRY(make32(B, *o, o->F->st[o->F->stage_B()]));
+  note_sync();
   BF_CUDA_TRY(cudaStreamSynchronize(B.s));
   return BF_OK;
 }
@@ -880,6 +881,7 @@ int run_sides(Batch& B, int maxlm, int maxr) {
     } catch (...) {   // no exception may leave the worker
       rc = fail(BF_ENOMEM, "host allocation failed on the W side");
     }
+    note_sync();
     const cudaError_t e = cudaStreamSynchronize(sw);   // (the last factor copies)
     if (!rc && e != cudaSuccess) rc = fail(BF_ECUDA, std::string("W side: ") + cudaGetErrorString(e));
     if (rc) errw = bf_last_error();
@@ -982,6 +984,7 @@ int factor_batch(int count, Plan* const* P, Operator* const* A, cudaStream_t s, 
   int rc = make_images(B);
   if (!rc) rc = run_sides(B, maxlm, maxr);
   if (!rc) {
+    note_sync();
     const cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) rc = fail(BF_ECUDA, cudaGetErrorString(e));
   }

@@ -58,9 +58,11 @@ class _Rows:
         return self.yh[c0:c0 + nc].numpy().T.copy()
 
 
-def factor_spec(n: int, geometry: str, seed: int, precision: str = "mixed", tol: float = 1e-6) -> dict:
-    """Plan parameters of a factor request: arcs (leaf 32) or caps (leaf 64)."""
-    return {"n": n, "geometry": geometry, "seed": seed, "precision": precision, "tol": tol}
+def factor_spec(n: int, geometry: str, seed: int, precision: str = "mixed", tol: float = 1e-6,
+                qr_fp64: bool = True) -> dict:
+    """Plan parameters of a factor request: arcs (leaf 32) or caps (leaf 64);
+    mixed precision with the pivoted QR in FP64 by default."""
+    return {"n": n, "geometry": geometry, "seed": seed, "precision": precision, "tol": tol, "qr_fp64": qr_fp64}
 
 
 def build_factor(spec: dict, stream=None) -> api.Factorization:
@@ -73,7 +75,8 @@ def build_factor(spec: dict, stream=None) -> api.Factorization:
         leaf = 64
     plan = api.Plan(g.src, g.tgt, kernel=g.kernel, wavenumber=g.wavenumber, leaf=leaf, tol=spec["tol"],
                     precision=spec["precision"], p=2 if spec["geometry"] == "arc" else 4,
-                    r0=4 if spec["geometry"] == "arc" else 64, seed=spec["seed"])
+                    r0=4 if spec["geometry"] == "arc" else 64, seed=spec["seed"],
+                    qr_fp64=bool(spec.get("qr_fp64", False)) and spec["precision"] == "mixed")
     return api.Factorization.factor(plan, api.Operator.kernel(plan), stream=stream)
 
 
@@ -254,6 +257,18 @@ def latency_stats(jobs: list[Job]) -> dict:
             "applies_per_s": len(ap) / span if span > 0 else None,
             "apply_rhs_per_s": sum(j.x.shape[1] for j in ap) / span if span > 0 else None,
             "errors": sum(1 for j in jobs if j.error)}
+
+
+def throughput_stats(jobs: list[Job], makespan: float) -> dict:
+    """Capacity figures of a run whose requests were all queued at once:
+    requests, applies, right-hand sides and factorizations per second over
+    the makespan."""
+    ok = [j for j in jobs if j.t_done >= 0 and not j.error]
+    ap = [j for j in ok if j.kind == "apply"]
+    fa = [j for j in ok if j.kind == "factor"]
+    return {"makespan_s": makespan, "requests_per_s": len(ok) / makespan, "applies_per_s": len(ap) / makespan,
+            "apply_rhs_per_s": sum(j.x.shape[1] for j in ap) / makespan, "factors_per_s": len(fa) / makespan,
+            "factor_sizes": sorted({int(j.spec["n"]) for j in fa}), "errors": sum(1 for j in jobs if j.error)}
 
 
 def make_jobs(trace, names: list[str], n_resident_of: dict, seed: int = 0) -> list[Job]:
