@@ -417,11 +417,15 @@ const char* bf_last_error(void);
  * Never fails. */
 unsigned long long bf_launch_count(void);
 
-/* Number of host synchronisations factorizations of this library have made
- * in this process so far (all threads; monotone): one per phase of Alg. 2
- * (the ranks a phase reveals size the next phase's sketch), the centre
- * level's solve and the end of each factorization (and of its second side).
- * Diagnostic, like bf_launch_count; never fails. */
+/* Number of host synchronisations this library has made in this process so
+ * far (all threads; monotone): every stream or device synchronisation and
+ * every synchronous copy to or from the device.  A factorization makes one
+ * per QR phase of Alg. 2 (the ranks a phase reveals size the next phase's
+ * sketch; the phase's tensor-core wait flag comes back with them), one after
+ * the centre level's solve and one at the end of each side; building an
+ * apply plan or a tuner run adds its own.  Waits for a slot of the
+ * library's pinned upload staging ring (a copy enqueued earlier in the same
+ * thread) are not counted.  Diagnostic, like bf_launch_count; never fails. */
 unsigned long long bf_sync_count(void);
 
 /* Device-side Gaussian test/sketch matrix of the counter-based generator:

@@ -415,6 +415,7 @@ H* check(void* h, uint32_t kind) {
 
 int upload(MemTracker* mt, DevBuf& b, const void* src, size_t bytes) {
   BF_TRY(b.alloc(mt, bytes, nullptr));
+  note_sync();
   BF_CUDA_TRY(cudaMemcpy(b.p, src, bytes, cudaMemcpyHostToDevice));
   return BF_OK;
 }
@@ -449,7 +450,7 @@ int sketch_error(Fact* f, Operator* A, int ncols, uint64_t seed, int dtype, cuda
   if (!rc) rc = launch_diff_norms(AW, FW, m, ncols, m, m, dtype, red, s);
   double h[2] = {0, 0};
   if (!rc && cudaMemcpyAsync(h, red, 16, cudaMemcpyDeviceToHost, s) != cudaSuccess) rc = fail(BF_ECUDA, "copy");
-  if (!rc && cudaStreamSynchronize(s) != cudaSuccess) rc = fail(BF_ECUDA, "sync");
+  if (!rc && host_sync(s) != cudaSuccess) rc = fail(BF_ECUDA, "sync");
   buf.release(s);
   if (rc) return rc;
   *err = h[1] > 0 ? std::sqrt(h[0] / h[1]) : 0.0;
@@ -458,6 +459,7 @@ int sketch_error(Fact* f, Operator* A, int ncols, uint64_t seed, int dtype, cuda
 
 void destroy_fact(Fact* F) {
   if (!F) return;
+  note_sync();
   cudaDeviceSynchronize();
   for (auto& S : F->st) S.d64.release(nullptr), S.d32.release(nullptr);
   for (auto& a : F->ap)
@@ -719,7 +721,7 @@ int bf_operator_dense(bf_plan plan, const void* A, int64_t lda, int dtype, void*
     rc = launch_gather2d((const int64_t*)P->d_permT.p, (const int64_t*)P->d_permS.p, P->m, P->n, A, lda,
                          dtype, op->A.p, P->m, op->dt, user_stream(stream));
   if (!rc) {
-    cudaError_t e = cudaStreamSynchronize(user_stream(stream));
+    cudaError_t e = host_sync(user_stream(stream));
     if (e != cudaSuccess) rc = fail(BF_ECUDA, cudaGetErrorString(e));
   }
   if (rc) {
@@ -1015,6 +1017,7 @@ int bf_fact_import(bf_plan plan, const int32_t* rV, const int32_t* rU, const voi
     }
     S.total = tot;
     if (!rc) rc = S.d64.alloc(&F->mem, tot * 16, nullptr);
+    if (!rc) note_sync();
     if (!rc && cudaMemcpy(S.d64.p, blocks[s], tot * 16, cudaMemcpyHostToDevice) != cudaSuccess)
       rc = fail(BF_ECUDA, "copy of imported blocks failed");
   }
@@ -1042,6 +1045,7 @@ int bf_fact_export(bf_fact F, int stage, void* host_out, size_t* bytes) {
   char* o = (char*)host_out;
   for (size_t b = 0; b < S.rows.size(); ++b) {
     const size_t sz = (size_t)S.rows[b] * S.cols[b] * 16;
+    note_sync();
     BF_CUDA_TRY(cudaMemcpy(o, (const char*)S.d64.p + S.off[b] * 16, sz, cudaMemcpyDeviceToHost));
     o += sz;
   }
@@ -1081,6 +1085,7 @@ void bf_free(void* handle) {
   if (kind == KIND_PLAN) {
     auto* h = (bf_plan_s*)handle;
     Plan* P = h->impl;
+    note_sync();
     cudaDeviceSynchronize();
     P->d_permS.release(nullptr), P->d_permT.release(nullptr), P->d_offS.release(nullptr);
     P->d_offT.release(nullptr), P->d_src.release(nullptr), P->d_tgt.release(nullptr);
@@ -1100,6 +1105,7 @@ void bf_free(void* handle) {
     delete h;
   } else if (kind == KIND_OP) {
     auto* h = (bf_operator_s*)handle;
+    note_sync();
     cudaDeviceSynchronize();
     delete h->impl;
     h->kind = 0;

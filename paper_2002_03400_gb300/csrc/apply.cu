@@ -249,7 +249,7 @@ static int build_apply(Fact* F, int opC, int dtype, cudaStream_t s) {
   BF_TRY(ap.tasks.alloc(&F->mem, all.size() * sizeof(StageTask), nullptr));
   BF_CUDA_TRY(cudaMemcpyAsync(ap.tasks.p, all.data(), all.size() * sizeof(StageTask),
                               cudaMemcpyHostToDevice, s));
-  BF_CUDA_TRY(cudaStreamSynchronize(s));
+  BF_CUDA_TRY(host_sync(s));
   ap.variant.assign(ap.first.size(), std::array<int8_t, NRHS_CLASSES>{-1, -1, -1, -1, -1, -1});
   ap.built = true;
   return BF_OK;
@@ -376,6 +376,7 @@ int tune_apply(Fact* F, int op, int dtype, int64_t nrhs, cudaStream_t s, float* 
       rc = launch_stage(d, ap.count[i], ap.maxM[i], (int)nrhs, (int)nrhs, bases, dtype, s, v);
       if (!rc && cudaEventRecord(e[0], s) != cudaSuccess) rc = fail(BF_ECUDA, "event record failed");
       for (int r = 0; r < 3 && !rc; ++r) rc = launch_stage(d, ap.count[i], ap.maxM[i], (int)nrhs, (int)nrhs, bases, dtype, s, v);
+      if (!rc) note_sync();
       if (!rc && (cudaEventRecord(e[1], s) != cudaSuccess || cudaEventSynchronize(e[1]) != cudaSuccess))
         rc = fail(BF_ECUDA, "event timing failed");
       float t = 0.f;
@@ -410,6 +411,7 @@ int tune_apply(Fact* F, int op, int dtype, int64_t nrhs, cudaStream_t s, float* 
       }
       if (cudaEventRecord(e[0], s) != cudaSuccess) rc = fail(BF_ECUDA, "event record failed");
       for (int r = 0; r < 3 && !rc; ++r) rc = run_fused(F, opC, dtype, nrhs, xs, in_rows, ys, out_rows, conj, p, s, cs);
+      if (!rc) note_sync();
       if (!rc && (cudaEventRecord(e[1], s) != cudaSuccess || cudaEventSynchronize(e[1]) != cudaSuccess))
         rc = fail(BF_ECUDA, "event timing failed");
       float t = 0.f;
@@ -461,7 +463,7 @@ int applier_create(Fact* F, int op, int64_t nrhs, int dtype, Applier** out) {
     A->yt = p + A->in_rows * nrhs * es;
     char* ping = p + (A->in_rows + A->out_rows) * nrhs * es;
     char* pong = ping + lvl * es;
-    if (cudaStreamSynchronize(cs) != cudaSuccess ||
+    if (host_sync(cs) != cudaSuccess ||
         cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
       rc = fail(BF_ECUDA, "graph capture could not start");
     } else {
@@ -504,6 +506,7 @@ int applier_run(Applier* A, const void* x, int64_t ldx, void* y, int64_t ldy, cu
 
 void applier_destroy(Applier* A) {
   if (!A) return;
+  note_sync();
   cudaDeviceSynchronize();
   if (A->exec) cudaGraphExecDestroy(A->exec);
   if (A->graph) cudaGraphDestroy(A->graph);

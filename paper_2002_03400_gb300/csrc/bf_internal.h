@@ -451,6 +451,10 @@ bool sketch_tc_applies(const std::vector<SketchJob>& jobs);
 int launch_sketch_jobs_tc(const std::vector<SketchJob>& jobs, MemTracker* mt, cudaStream_t s);
 // BF_ETIMEOUT if a tensor-core kernel's bounded wait gave up since the last reset
 int tc_status(bool reset);
+// enqueues a copy of the device wait flag into dst (device memory) on s
+int tc_status_copy(int32_t* dst, cudaStream_t s);
+// the status of a flag value read back by tc_status_copy (resets it if asked)
+int tc_status_value(int v, bool reset);
 // runs one bounded wait that nothing completes, with the limit lowered to
 // limit_ns; BF_ETIMEOUT when it gave up and returned (the designed outcome)
 int wait_probe(uint64_t limit_ns, cudaStream_t s);
@@ -472,9 +476,14 @@ int entry_images_enabled();
 // counts one kernel launch of this library (bf_launch_count)
 void note_launch();
 unsigned long long launches_so_far();
-// counts one host synchronisation of a factorization (bf_sync_count)
+// counts one host-blocking CUDA call of this library (bf_sync_count)
 void note_sync();
 unsigned long long syncs_so_far();
+// cudaStreamSynchronize, counted by bf_sync_count
+inline cudaError_t host_sync(cudaStream_t s) {
+  note_sync();
+  return cudaStreamSynchronize(s);
+}
 // 0: tensor-core sketch where it applies (default), 1: SIMT sketch only
 int set_sketch_engine(int e);
 struct GemmGroups;

@@ -315,18 +315,20 @@ int qr_all(Batch& B, std::vector<QRJob>& jobs) {
     i = r.b;
   }
   Scratch d(B.s), w(B.s);
-  BF_TRY(d.alloc(&B.mem, nt * sizeof(QRTask) + nt * sizeof(int32_t)));
+  // the ranks, then the tensor-core wait flag: one read-back, one host wait
+  BF_TRY(d.alloc(&B.mem, nt * sizeof(QRTask) + (nt + 1) * sizeof(int32_t)));
   BF_TRY(upload_async(d.p(), sorted.data(), nt * sizeof(QRTask), B.s));
   int32_t* d_r = (int32_t*)(d.p() + nt * sizeof(QRTask));
   if (wbytes) BF_TRY(w.alloc(&B.mem, wbytes));
   for (const Range& r : ranges)
     BF_TRY(launch_qr((const QRTask*)d.p() + r.a, r.b - r.a, r.maxS, r.maxK, B.dt, fp64, d_r + r.a, w.p(), wbytes,
                      B.s));
-  std::vector<int32_t> hs(nt), h(nt);
-  BF_CUDA_TRY(cudaMemcpyAsync(hs.data(), d_r, nt * sizeof(int32_t), cudaMemcpyDeviceToHost, B.s));
-  BF_CUDA_TRY(cudaStreamSynchronize(B.s));
+  BF_TRY(tc_status_copy(d_r + nt, B.s));
+  std::vector<int32_t> hs(nt + 1), h(nt);
+  BF_CUDA_TRY(cudaMemcpyAsync(hs.data(), d_r, (nt + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, B.s));
+  BF_CUDA_TRY(host_sync(B.s));
   for (int i = 0; i < nt; ++i) h[order[i]] = hs[i];
-  BF_TRY(tc_status(true));
+  BF_TRY(tc_status_value(hs[nt], true));
   size_t q = 0;
   for (auto& J : jobs) {
     const size_t nb = J.S->rows.size();
@@ -750,8 +752,7 @@ int r_phase(Batch& B, int t) {
   if (lwb) BF_TRY(lw.alloc(&B.mem, lwb));
   BF_TRY(launch_lsq((const LSQTask*)d.p(), (int)lt.size(), maxS, maxK, maxR, B.dt, lw.p(), lwb, B.s));
   for (OpState* o : ctr) BF_TRY(make32(B, *o, o->F->st[o->F->stage_B()]));
-  note_sync();
-  BF_CUDA_TRY(cudaStreamSynchronize(B.s));
+  BF_CUDA_TRY(host_sync(B.s));
   return BF_OK;
 }
 
@@ -881,8 +882,7 @@ int run_sides(Batch& B, int maxlm, int maxr) {
     } catch (...) {   // no exception may leave the worker
       rc = fail(BF_ENOMEM, "host allocation failed on the W side");
     }
-    note_sync();
-    const cudaError_t e = cudaStreamSynchronize(sw);   // (the last factor copies)
+    const cudaError_t e = host_sync(sw);   // (the last factor copies)
     if (!rc && e != cudaSuccess) rc = fail(BF_ECUDA, std::string("W side: ") + cudaGetErrorString(e));
     if (rc) errw = bf_last_error();
     rcw = rc;
@@ -917,7 +917,7 @@ int run_sides(Batch& B, int maxlm, int maxr) {
   join();
   for (auto& o : BW.ops) o.Y.release(sw);
   for (auto& o : BR.ops) o.Y.release(B.s);
-  cudaStreamSynchronize(sw);
+  host_sync(sw);
   cudaEventDestroy(ev);
   cudaStreamDestroy(sw);
   if (rcw) {
@@ -984,8 +984,7 @@ int factor_batch(int count, Plan* const* P, Operator* const* A, cudaStream_t s, 
   int rc = make_images(B);
   if (!rc) rc = run_sides(B, maxlm, maxr);
   if (!rc) {
-    note_sync();
-    const cudaError_t e = cudaStreamSynchronize(s);
+    const cudaError_t e = host_sync(s);
     if (e != cudaSuccess) rc = fail(BF_ECUDA, cudaGetErrorString(e));
   }
   for (auto& o : B.ops) {

@@ -620,7 +620,7 @@ int build_fused(Fact* F, int opC, int dtype, cudaStream_t s) {
       if (sz[i]) memcpy(host.data() + off[i], src[i], sz[i]);
     char* p = (char*)H.dev.p;
     BF_CUDA_TRY(cudaMemcpyAsync(p, host.data(), host.size(), cudaMemcpyHostToDevice, s));
-    BF_CUDA_TRY(cudaStreamSynchronize(s));
+    BF_CUDA_TRY(host_sync(s));
     H.d_groups = (const FusedGroup*)(p + off[0]);
     H.d_levels = (const FusedLevel*)(p + off[1]);
     H.d_tasks = (const StageTask*)(p + off[2]);

@@ -1667,6 +1667,7 @@ __global__ void wait_probe_kernel() {
 int wait_probe(uint64_t limit_ns, cudaStream_t s) {
   if (limit_ns == 0 || limit_ns > 1000000000ull) return fail(BF_EINVAL, "limit_ns must be in (0, 1e9]");
   int before = 0;
+  note_sync();
   BF_CUDA_TRY(cudaMemcpyFromSymbol(&before, g_tc_status, sizeof(int)));
   if (before) return fail(BF_ETIMEOUT, "an earlier tensor-core wait had already given up (device flag set)");
   const unsigned long long lim = limit_ns, def = 1000000000ull;
@@ -1675,21 +1676,32 @@ int wait_probe(uint64_t limit_ns, cudaStream_t s) {
   wait_probe_kernel<<<1, 32, 0, s>>>();
   const cudaError_t e = cudaGetLastError();
   const cudaError_t e2 = cudaMemcpyToSymbolAsync(g_wait_limit_ns, &def, sizeof(def), 0, cudaMemcpyHostToDevice, s);
-  const cudaError_t e3 = cudaStreamSynchronize(s);
+  const cudaError_t e3 = host_sync(s);
   if (e != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess)
     return fail(BF_ECUDA, std::string("wait probe: ") +
                               cudaGetErrorString(e != cudaSuccess ? e : e2 != cudaSuccess ? e2 : e3));
   return tc_status(true);
 }
 
-int tc_status(bool reset) {
-  int v = 0;
-  BF_CUDA_TRY(cudaMemcpyFromSymbol(&v, g_tc_status, sizeof(int)));
+int tc_status_copy(int32_t* dst, cudaStream_t s) {
+  BF_CUDA_TRY(cudaMemcpyFromSymbolAsync(dst, g_tc_status, sizeof(int), 0, cudaMemcpyDeviceToDevice, s));
+  return BF_OK;
+}
+
+int tc_status_value(int v, bool reset) {
   if (v && reset) {
     const int z = 0;
+    note_sync();
     BF_CUDA_TRY(cudaMemcpyToSymbol(g_tc_status, &z, sizeof(int)));
   }
   return v ? fail(BF_ETIMEOUT, "a tensor-core sketch wait gave up (device flag set)") : BF_OK;
+}
+
+int tc_status(bool reset) {
+  int v = 0;
+  note_sync();
+  BF_CUDA_TRY(cudaMemcpyFromSymbol(&v, g_tc_status, sizeof(int)));
+  return tc_status_value(v, reset);
 }
 
 }  // namespace bf
