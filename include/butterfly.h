@@ -53,7 +53,8 @@ typedef enum {
   BF_ENOTCONVERGED = -4,   /* adaptive leaf rank exceeded r_max             */
   BF_ECUDA = -5,           /* a CUDA runtime call failed                    */
   BF_ETIMEOUT = -6,        /* a bounded device wait gave up                 */
-  BF_EUNSUPPORTED = -7     /* combination not built                         */
+  BF_EUNSUPPORTED = -7,    /* combination not built                         */
+  BF_EINTERNAL = -8        /* an internal consistency check failed          */
 } bf_status;
 
 typedef enum { BF_C64 = 0, BF_C128 = 1 } bf_dtype;
@@ -358,18 +359,20 @@ int bf_set_sketch_engine(int engine);
  * unless on is 0 or 1.  Not thread-safe against running factorizations. */
 int bf_set_entry_images(int on);
 
-/* Failure path of the tensor-core kernels' bounded waits, exercised without
- * a fault.  Every mbarrier wait in those kernels gives up after 1 s, sets a
- * device flag, frees its tensor memory and returns; the host then reports
- * BF_ETIMEOUT.  This call lowers the limit to limit_ns (0 < limit_ns <= 1e9)
- * for one launch of a one-warp kernel that waits, through the same wait
- * routine, on an mbarrier that nothing completes, restores the limit,
- * synchronizes `stream` and returns the status: BF_ETIMEOUT is the designed
- * outcome (the wait gave up and the kernel returned; the context stays
- * usable), BF_OK would mean the wait did not give up.  BF_EINVAL for a limit
- * out of range; BF_ETIMEOUT without running if an earlier wait had already
- * given up.  Diagnostic; not thread-safe against running factorizations
- * (they would see the lowered limit). */
+/* Failure path of the library's bounded device waits, exercised without a
+ * fault.  Every mbarrier wait in the tensor-core kernels and every
+ * dependency wait of the persistent apply gives up after 1 s, sets a device
+ * flag and returns (freeing its tensor memory); the host then reports
+ * BF_ETIMEOUT.  This call runs one wait of each kind with the limit lowered
+ * to limit_ns (0 < limit_ns <= 1e9): a one-warp kernel waiting, through the
+ * same wait routine, on an mbarrier that nothing completes, then a one-task
+ * persistent apply whose task waits on its own flag; it synchronizes
+ * `stream` and returns BF_ETIMEOUT when both waits gave up (the designed
+ * outcome: the kernels returned and the context stays usable), BF_OK or
+ * BF_EINTERNAL when a wait did not give up.  BF_EINVAL for a limit out of
+ * range; BF_ETIMEOUT without running if an earlier wait had already given
+ * up.  Diagnostic; not thread-safe against running factorizations (they
+ * would see the lowered limit). */
 int bf_debug_wait_timeout(uint64_t limit_ns, void* stream);
 
 /* Selects the apply engine for the whole process (bf_apply, bf_apply_T,
@@ -386,11 +389,41 @@ int bf_debug_wait_timeout(uint64_t limit_ns, void* stream);
  *     on the CTAs of one GPU); the tree permutations and the conjugation of
  *     F^T are folded into the loads and stores; used where a subtree's
  *     intermediates fit in shared memory.
- * engine 0 (default): the stage engine, except for right-hand-side classes
- * where bf_apply_tune measured the fused engine faster; 1: stages only;
- * 2: fused wherever it applies.  BF_EINVAL otherwise.  Not thread-safe
- * against running applies. */
+ *   - persistent: one cooperative launch over all stages; each output
+ *     block starts once the blocks it reads are written (per-block flags,
+ *     bounded waits), every stage writes its own rows of one stacked buffer,
+ *     and each block's factor entries are staged in shared memory while it
+ *     waits; results equal the stage engine's bit for bit.
+ *   - grouped: the stages in runs of 1-4 consecutive stages, one launch
+ *     per run; the blocks of a run fall into small connected groups (for
+ *     the W levels and depth 3: 4 + 4 + 4 blocks reading 8 blocks of the
+ *     level below), one CTA per (group, column slice) stages the group's
+ *     factor blocks (before waiting for the previous launch) and input
+ *     rows in shared memory and computes the run's inner stages there;
+ *     ceil((L + 3) / depth) launches, results equal to the stage engine's
+ *     bit for bit; the tuner picks the depth.
+ * engine 0 (default): the engine bf_apply_tune measured fastest for the
+ * right-hand-side class (untuned: stages); 1: stages only; 2: fused
+ * wherever it applies; 3: persistent wherever it applies (not when x and y
+ * overlap); 4: grouped wherever it applies.  BF_EINVAL otherwise.  Not
+ * thread-safe against running applies. */
 int bf_set_apply_engine(int engine);
+
+/* Run depth of the grouped apply engine (diagnostic): 0 (default) the depth
+ * bf_apply_tune chose (untuned: 3); 1-4 that many stages per launch for
+ * every later grouped apply.  BF_EINVAL otherwise.  Not thread-safe against
+ * running applies. */
+int bf_set_grouped_depth(int depth);
+
+/* Stage-kernel shape for every apply stage launch in this process
+ * (diagnostic): v = -1 (default) uses the shapes bf_apply_tune chose, else
+ * the untuned default; v = 0..7 forces that shape (0 many-warp, 1 rows,
+ * 2 block, 3-5 wide register tiles, 6-7 staged in shared memory).  Every
+ * shape computes the same sums in the same order, so results do not change,
+ * bit for bit.  Applies captured in an applier keep the shapes of their
+ * capture.  BF_EINVAL outside -1..7.  Not thread-safe against running
+ * applies. */
+int bf_set_stage_variant(int v);
 
 /* Factorization schedule for the whole process: on = 1 (default) -- the
  * two sides of Alg. 2, the row bases (loop "V" and the W levels) and the

@@ -22,7 +22,7 @@ OPS = {"N": 0, "T": 1, "C": 2}
 PREC = {"fp64": 0, "mixed": 1}
 KERNELS = {"none": 0, "helmholtz2d": 1, "helmholtz3d": 2, "dft": 3}
 STATUS = {0: "BF_OK", -1: "BF_EINVAL", -2: "BF_ENOMEM", -3: "BF_ECALLBACK", -4: "BF_ENOTCONVERGED",
-          -5: "BF_ECUDA", -6: "BF_ETIMEOUT", -7: "BF_EUNSUPPORTED"}
+          -5: "BF_ECUDA", -6: "BF_ETIMEOUT", -7: "BF_EUNSUPPORTED", -8: "BF_EINTERNAL"}
 
 
 class BFError(RuntimeError):
@@ -84,6 +84,8 @@ def lib():
         "bf_set_sketch_engine": (i32, [i32]),
         "bf_set_entry_images": (i32, [i32]),
         "bf_set_apply_engine": (i32, [i32]),
+        "bf_set_stage_variant": (i32, [i32]),
+        "bf_set_grouped_depth": (i32, [i32]),
         "bf_set_parallel_sides": (i32, [i32]),
         "bf_launch_count": (C.c_ulonglong, []),
         "bf_sync_count": (C.c_ulonglong, []),
@@ -111,7 +113,7 @@ def exported_symbols():
             "bf_apply_T", "bf_apply_noalloc", "bf_ranks", "bf_fact_info", "bf_fact_import", "bf_fact_export", "bf_error",
             "bf_free", "bf_gaussian", "bf_set_sketch_engine", "bf_set_entry_images", "bf_launch_count", "bf_apply_tune",
             "bf_applier_create", "bf_applier_run", "bf_fact_accept", "bf_debug_wait_timeout",
-            "bf_set_apply_engine", "bf_set_parallel_sides", "bf_sync_count"]
+            "bf_set_apply_engine", "bf_set_stage_variant", "bf_set_grouped_depth", "bf_set_parallel_sides", "bf_sync_count"]
 
 
 def launch_count() -> int:
@@ -152,10 +154,25 @@ def set_parallel_sides(on: bool):
 
 
 def set_apply_engine(engine: str):
-    """'auto' (default: the stage launches, or the fused two-launch engine
-    where bf_apply_tune measured it faster), 'stages' or 'fused' (wherever it
-    applies)."""
-    check(lib().bf_set_apply_engine({"auto": 0, "stages": 1, "fused": 2}[engine]))
+    """'auto' (default: the engine bf_apply_tune measured fastest for the
+    right-hand-side class; untuned: the stage launches), 'stages', 'fused',
+    'persistent' or 'grouped' (the last three wherever they apply)."""
+    check(lib().bf_set_apply_engine({"auto": 0, "stages": 1, "fused": 2, "persistent": 3, "grouped": 4}[engine]))
+
+
+def set_stage_variant(v: int):
+    """Stage-kernel shape for every apply stage: -1 (default) tuned or
+    default shapes, 0..7 that shape everywhere (results do not change)."""
+    check(lib().bf_set_stage_variant(int(v)))
+
+
+STAGE_VARIANTS = 8
+
+
+def set_grouped_depth(depth: int):
+    """Stages per launch of the grouped apply engine: 0 (default) the tuned
+    depth (untuned: 3), 1..4 that depth for every later grouped apply."""
+    check(lib().bf_set_grouped_depth(int(depth)))
 
 
 def check(rc: int):

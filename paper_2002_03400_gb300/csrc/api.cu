@@ -467,6 +467,10 @@ void destroy_fact(Fact* F) {
   for (auto& a : F->fp)
     for (auto& b : a)
       for (auto& h : b.h) h.dev.release(nullptr);
+  for (auto& a : F->fl)
+    for (auto& b : a) b.dev.release(nullptr);
+  for (auto& a : F->gp)
+    for (auto& b : a) b.dev.release(nullptr);
   delete F;
 }
 
@@ -854,6 +858,8 @@ int bf_factor(bf_plan plan, bf_operator A, void* stream, bf_fact* out) {
 int bf_set_sketch_engine(int engine) { return set_sketch_engine(engine); }
 int bf_set_entry_images(int on) { return set_entry_images(on); }
 int bf_set_apply_engine(int engine) { return set_apply_engine(engine); }
+int bf_set_stage_variant(int v) { return set_stage_variant(v); }
+int bf_set_grouped_depth(int depth) { return set_grouped_depth(depth); }
 int bf_set_parallel_sides(int on) { return set_parallel_sides(on); }
 
 unsigned long long bf_launch_count(void) { return bf::launches_so_far(); }
@@ -1077,7 +1083,17 @@ int bf_fact_accept(bf_fact F, int* attempts, int* r0_used, double* err) {
   return BF_OK;
 }
 
-int bf_debug_wait_timeout(uint64_t limit_ns, void* stream) { return wait_probe(limit_ns, user_stream(stream)); }
+int bf_debug_wait_timeout(uint64_t limit_ns, void* stream) {
+  const cudaStream_t s = user_stream(stream);
+  int rc = wait_probe(limit_ns, s);
+  if (rc != BF_ETIMEOUT) return rc;
+  // the persistent apply's dependency wait, on a flag nothing sets
+  rc = flow_wait_probe(limit_ns, s);
+  if (rc) return rc;
+  rc = tc_status(true);
+  if (rc == BF_OK) return fail(BF_EINTERNAL, "the apply's dependency wait did not give up");
+  return rc;
+}
 
 void bf_free(void* handle) {
   if (!handle) return;

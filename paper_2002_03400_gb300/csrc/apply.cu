@@ -321,21 +321,47 @@ int apply_fact(Fact* F, int op, int64_t nrhs, const void* x, int64_t ldx, void* 
   }
   const bool direct_in = id_in && !conj && ldx == in_rows;
   const bool direct_out = id_out && !conj && ldy == out_rows;
-  const int64_t lvl = F->ap[opC][dtype].level_rows_max * nrhs;
-  const size_t bytes = (2 * lvl + (direct_in ? 0 : in_rows * nrhs) + (direct_out ? 0 : out_rows * nrhs)) * es;
+  // the persistent engine: forced (engine 3), or measured fastest for this
+  // right-hand-side class; its stages may run while the first still reads
+  // x, so not when x and y overlap
+  const int cls = nrhs_class(nrhs);
+  bool overlap = false;
+  if (direct_in && direct_out) {
+    const char *xa = (const char*)x, *ya = (const char*)y;
+    const char* xb = xa + (size_t)(ldx * (nrhs - 1) + in_rows) * es;
+    const char* yb = ya + (size_t)(ldy * (nrhs - 1) + out_rows) * es;
+    overlap = !(xb <= ya || yb <= xa);
+  }
+  bool flow = !overlap && (apply_engine() == 3 || (apply_engine() == 0 && F->fl[opC][dtype].pick[cls]));
+  if (flow) BF_TRY(build_flow(F, opC, dtype, s));
+  flow = flow && F->fl[opC][dtype].ok;
+  // the grouped engine (runs of stages per launch): forced (engine 4), or
+  // measured fastest for this class
+  GroupedPlan& gp = F->gp[opC][dtype];
+  bool grouped = !flow && (apply_engine() == 4 || (apply_engine() == 0 && gp.pick[cls]));
+  if (grouped)
+    BF_TRY(build_grouped(F, opC, dtype, grouped_depth() > 0 ? grouped_depth() : gp.built ? gp.depth : 3, s));
+  // one run reads x and writes y in the same launch
+  grouped = grouped && gp.ok && !(overlap && gp.runs.size() < 2);
+  const int64_t lvl = (grouped ? gp.level_rows_max : F->ap[opC][dtype].level_rows_max) * nrhs;
+  const size_t inner = flow ? flow_scratch_bytes(F->fl[opC][dtype], nrhs, dtype) : (size_t)(2 * lvl) * es;
+  const size_t bytes = inner + ((direct_in ? 0 : in_rows * nrhs) + (direct_out ? 0 : out_rows * nrhs)) * es;
   DevBuf scratch;
   BF_TRY(scratch.alloc(&F->mem, bytes, s));
   char* p = (char*)scratch.p;
   void* ping = p;
   void* pong = p + lvl * es;
-  char* q = p + 2 * lvl * es;
+  char* q = p + inner;
   void* xt = direct_in ? const_cast<void*>(x) : (void*)q;
   if (!direct_in) q += in_rows * nrhs * es;
   void* yt = direct_out ? y : (void*)q;
   int rc = BF_OK;
   if (!direct_in)
     rc = launch_gather_rows(id_in ? nullptr : perm_in, in_rows, nrhs, x, ldx, xt, in_rows, conj, dtype, s);
-  if (rc == BF_OK) rc = run_apply_stages(F, opC, dtype, nrhs, xt, ping, pong, yt, s);
+  if (rc == BF_OK)
+    rc = flow      ? run_flow(F, opC, dtype, nrhs, xt, yt, p, s)
+         : grouped ? run_grouped(F, opC, dtype, nrhs, xt, yt, ping, pong, s)
+                   : run_apply_stages(F, opC, dtype, nrhs, xt, ping, pong, yt, s);
   if (rc == BF_OK && !direct_out)
     rc = launch_scatter_rows(id_out ? nullptr : perm_out, out_rows, nrhs, yt, out_rows, y, ldy, conj, dtype, s);
   scratch.release(s);
@@ -418,15 +444,75 @@ int tune_apply(Fact* F, int op, int dtype, int64_t nrhs, cudaStream_t s, float* 
       if (!rc && cudaEventElapsedTime(&t, e[0], e[1]) != cudaSuccess) rc = fail(BF_ECUDA, "event timing failed");
       if (!rc && t / 3.f < fused_best) fused_best = t / 3.f, best_cs = cs;
     }
-    if (!rc && best_cs > 0) {
-      fp.cs[cls] = best_cs;
-      fp.engine[cls] = fused_best <= total ? 0 : 1;
+    if (!rc && best_cs > 0) fp.cs[cls] = best_cs;
+  }
+  // the persistent apply, on its own scratch (x and y: the input and output
+  // rows of the stage scratch)
+  float flow_best = 1e30f;
+  if (!rc && apply_engine() != 1 && apply_engine() != 2) rc = build_flow(F, opC, dtype, s);
+  FlowPlan& fl = F->fl[opC][dtype];
+  if (!rc && apply_engine() != 1 && apply_engine() != 2 && fl.ok) {
+    DevBuf fs;
+    rc = fs.alloc(&F->mem, flow_scratch_bytes(fl, nrhs, dtype), s);
+    char* xs = p + 2 * lvl * es;
+    char* ys = xs + rows * nrhs * es;
+    if (!rc) rc = run_flow(F, opC, dtype, nrhs, xs, ys, fs.p, s);
+    if (!rc && cudaEventRecord(e[0], s) != cudaSuccess) rc = fail(BF_ECUDA, "event record failed");
+    for (int r = 0; r < 3 && !rc; ++r) rc = run_flow(F, opC, dtype, nrhs, xs, ys, fs.p, s);
+    if (!rc) note_sync();
+    if (!rc && (cudaEventRecord(e[1], s) != cudaSuccess || cudaEventSynchronize(e[1]) != cudaSuccess))
+      rc = fail(BF_ECUDA, "event timing failed");
+    float t = 0.f;
+    if (!rc && cudaEventElapsedTime(&t, e[0], e[1]) != cudaSuccess) rc = fail(BF_ECUDA, "event timing failed");
+    if (!rc) flow_best = t / 3.f;
+    if (!rc) rc = tc_status(true);   // a dependency wait that gave up (never expected)
+    fs.release(s);
+  }
+  // the grouped apply at each run depth, on its own level buffers; the
+  // plan keeps the fastest depth
+  float grouped_best = 1e30f;
+  GroupedPlan& gp = F->gp[opC][dtype];
+  if (!rc && (apply_engine() == 0 || apply_engine() == 4)) {
+    int best_depth = 0, best_cw = 0;
+    char* xs = p + 2 * lvl * es;
+    char* ys = xs + rows * nrhs * es;
+    for (int depth = 2; depth <= GR_MAXD && !rc; ++depth) {
+      rc = build_grouped(F, opC, dtype, depth, s);
+      if (rc || !gp.ok) break;
+      DevBuf lb;
+      rc = lb.alloc(&F->mem, (size_t)2 * gp.level_rows_max * nrhs * es, s);
+      char* lp = (char*)lb.p;
+      char* lq = lp + gp.level_rows_max * nrhs * es;
+      for (int cw = 16; cw <= 64 && !rc; cw *= 2) {
+        if (cw > 16 && cw / 2 >= nrhs) break;   // wider slices than the columns change nothing
+        rc = run_grouped(F, opC, dtype, nrhs, xs, ys, lp, lq, s, cw);
+        if (!rc && cudaEventRecord(e[0], s) != cudaSuccess) rc = fail(BF_ECUDA, "event record failed");
+        for (int r = 0; r < 3 && !rc; ++r) rc = run_grouped(F, opC, dtype, nrhs, xs, ys, lp, lq, s, cw);
+        if (!rc) note_sync();
+        if (!rc && (cudaEventRecord(e[1], s) != cudaSuccess || cudaEventSynchronize(e[1]) != cudaSuccess))
+          rc = fail(BF_ECUDA, "event timing failed");
+        float t = 0.f;
+        if (!rc && cudaEventElapsedTime(&t, e[0], e[1]) != cudaSuccess) rc = fail(BF_ECUDA, "event timing failed");
+        if (!rc && t / 3.f < grouped_best) grouped_best = t / 3.f, best_depth = depth, best_cw = cw;
+      }
+      lb.release(s);
     }
+    if (!rc && best_depth > 0) {
+      rc = build_grouped(F, opC, dtype, best_depth, s);
+      gp.cw[cls] = (int16_t)best_cw;
+    }
+  }
+  // the fastest engine serves this class from now on
+  if (!rc) {
+    const float best = std::min(std::min(total, fused_best), std::min(flow_best, grouped_best));
+    fl.pick[cls] = flow_best == best && best < total ? 1 : 0;
+    gp.pick[cls] = !fl.pick[cls] && grouped_best == best && best < total ? 1 : 0;
+    if (fused_best < 1e30f) fp.engine[cls] = !fl.pick[cls] && !gp.pick[cls] && fused_best <= total ? 0 : 1;
   }
   cudaEventDestroy(e[0]);
   cudaEventDestroy(e[1]);
   scratch.release(s);
-  if (ms) *ms = fused_best < total ? fused_best : total;
+  if (ms) *ms = std::min(std::min(total, fused_best), std::min(flow_best, grouped_best));
   return rc;
 }
 

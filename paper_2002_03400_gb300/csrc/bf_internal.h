@@ -274,6 +274,77 @@ struct FusedPlan {
   std::array<int, NRHS_CLASSES> engine{{-1, -1, -1, -1, -1, -1}};
 };
 
+// Persistent apply (one cooperative launch over all stages): the stage
+// lists with stacked, stage-private intermediates and each task's producers.
+struct FlowPlan {
+  bool built = false, ok = false;
+  DevBuf dev;                              // tasks | dep_ptr | dep_idx
+  const StageTask* d_tasks = nullptr;
+  const int32_t* d_dep_ptr = nullptr;
+  const int32_t* d_dep_idx = nullptr;
+  int ntasks = 0;
+  int64_t inter_rows = 0;                  // rows of the stacked intermediates
+  // per right-hand-side class: 1 when the tuner measured it fastest
+  std::array<int8_t, NRHS_CLASSES> pick{{0, 0, 0, 0, 0, 0}};
+};
+
+// Grouped apply: the stages in runs of up to GR_MAXD, one launch per run.
+// Within a run the tasks fall into groups (the connected components of
+// "reads the output of"); one CTA per (group, column slice) computes all of
+// its group's tasks, the run's inner stages in shared memory.
+constexpr int GR_MAXD = 4;
+struct GroupedTerm {
+  const void* mat;          // factor entries in global memory
+  int32_t fac_off;          // element offset in the group's staged factors (-1: read mat)
+  int32_t K, ldm;
+  int16_t conjT, in_reg;    // input: shared-memory region in_reg (0: the staged run inputs)
+  int32_t in_row;           // first local row of the input in that region
+};
+struct GroupedTask {
+  int32_t M;
+  int16_t nterms, out_reg;  // out_reg > 0: shared-memory region; 0: global (the run's output)
+  int64_t out_row;          // local row (out_reg > 0) or global row offset (out_reg == 0)
+  int64_t ldo;              // global output: 0 row-major (N columns), > 0 column-major
+  GroupedTerm t[2];
+};
+struct GroupedSpan {        // global input rows [g0, g0 + rows) -> region-0 rows [l0, l0 + rows)
+  int64_t g0;
+  int32_t l0, rows;
+};
+struct GroupedSeg {         // a factor block copied whole into the staged factors
+  const void* src;
+  int32_t dst, count;
+};
+constexpr int GR_RB = 4;              // rows of a work item (a thread's register tile: GR_RB rows x 2 columns)
+struct GroupedGroup {
+  int32_t task0, ntasks, span0, nspans, seg0, nseg, chunk0;
+  int32_t fac_elems;                    // staged factor elements (0: none staged)
+  int32_t nst;                          // stages of this run
+  int32_t st_chunk[GR_MAXD + 1];        // row chunks of stage k: [chunk0 + st_chunk[k], chunk0 + st_chunk[k + 1])
+  int32_t reg_row[GR_MAXD + 1];         // region r: local rows [reg_row[r], reg_row[r + 1])
+};
+struct GroupedRun {
+  int32_t group0, ngroups;
+  int32_t in_base, out_base;            // StageBases indices
+  int64_t in_ld;                        // 0: row-major intermediates; > 0: column-major (x)
+  int32_t fac_max, rows_max;            // largest staged-factor and row counts over the run's groups
+  int32_t tasks_max, chunks_max;        // largest task and row-chunk counts over the run's groups
+};
+struct GroupedPlan {
+  bool built = false, ok = false;
+  int depth = 0;                        // stages per run
+  DevBuf dev;                           // groups | tasks | spans | segs
+  std::vector<GroupedRun> runs;
+  const GroupedGroup* d_groups = nullptr;
+  const GroupedTask* d_tasks = nullptr;
+  const GroupedSpan* d_spans = nullptr;
+  const GroupedSeg* d_segs = nullptr;
+  const int32_t* d_chunks = nullptr;    // (first row << 16) | task index within the group
+  int64_t level_rows_max = 0;           // rows of the largest run output (the two level buffers)
+  std::array<int16_t, NRHS_CLASSES> cw{{0, 0, 0, 0, 0, 0}};   // tuned column-slice width (0: default)
+  std::array<int8_t, NRHS_CLASSES> pick{{0, 0, 0, 0, 0, 0}};   // 1: the tuner measured it fastest
+};
+
 struct Fact {
   Plan* plan = nullptr;
   int L = 0, lm = 0;
@@ -288,6 +359,8 @@ struct Fact {
   MemTracker mem;
   ApplyPlan ap[2][2];                // [op N / C][dtype C64 / C128]
   FusedPlan fp[2][2];                // fused apply, same indexing
+  FlowPlan fl[2][2];                 // persistent apply, same indexing
+  GroupedPlan gp[2][2];              // grouped apply, same indexing
   int stage_V0() const { return 0; }
   int stage_W(int j) const { return j; }
   int stage_B() const { return lm + 1; }
@@ -327,8 +400,27 @@ bool plan_fused(const Fact* F, int opC, int dtype, FusedPlan& fp);
 int fused_slice_width(const FusedPlan& fp, int64_t nrhs, int dtype);
 int run_fused(Fact* F, int opC, int dtype, int64_t nrhs, const void* x, int64_t ldx, void* y, int64_t ldy, int conj,
               void* exch, cudaStream_t s, int cs_override = 0);
-// 0: fused apply where the tuner measured it faster (default); 1: stage
-// launches only; 2: fused wherever it applies
+// Persistent apply: builds F->fl[opC][dtype] once (ok false: not
+// applicable); run_flow computes y = op(F) x on tree-order x and y (no
+// conjugation) with scratch of flow_scratch_bytes.
+int build_flow(Fact* F, int opC, int dtype, cudaStream_t s);
+size_t flow_scratch_bytes(const FlowPlan& fl, int64_t nrhs, int dtype);
+int run_flow(Fact* F, int opC, int dtype, int64_t nrhs, const void* xt, void* yt, void* scratch, cudaStream_t s);
+// one bounded dependency wait on a flag nothing sets (sets the status flag)
+int flow_wait_probe(uint64_t limit_ns, cudaStream_t s);
+// Grouped apply: builds F->gp[opC][dtype] with runs of `depth` stages
+// (rebuilt when the depth changes; ok false: not applicable); run_grouped
+// computes y = op(F) x on tree-order x and y with two level buffers of
+// gp.level_rows_max * nrhs elements each.
+int build_grouped(Fact* F, int opC, int dtype, int depth, cudaStream_t s);
+int run_grouped(Fact* F, int opC, int dtype, int64_t nrhs, const void* xt, void* yt, void* ping, void* pong,
+                cudaStream_t s, int cw_override = 0);
+// 0: the tuned depth (untuned: 3); 1 .. GR_MAXD: that depth for every grouped apply
+int set_grouped_depth(int depth);
+int grouped_depth();
+// 0: the fastest engine the tuner measured for the right-hand-side class
+// (default; untuned: stage launches); 1: stage launches only; 2: fused
+// wherever it applies; 3: persistent wherever it applies; 4: grouped
 int set_apply_engine(int e);
 int apply_engine();
 
@@ -349,7 +441,10 @@ int applier_create(Fact* F, int op, int64_t nrhs, int dtype, Applier** out);
 int applier_run(Applier* A, const void* x, int64_t ldx, void* y, int64_t ldy, cudaStream_t s);
 void applier_destroy(Applier* A);
 int stage_variant_default(int nrhs, int dtype);
-constexpr int STAGE_VARIANTS = 6;
+// -1: tuned or default shapes; 0 .. STAGE_VARIANTS - 1: that shape for every
+// launch with a fixed column count (the apply's)
+int set_stage_variant(int v);
+constexpr int STAGE_VARIANTS = 8;
 
 // ------------------------------------------------------------------- QR --
 struct QRTask {
@@ -451,6 +546,8 @@ bool sketch_tc_applies(const std::vector<SketchJob>& jobs);
 int launch_sketch_jobs_tc(const std::vector<SketchJob>& jobs, MemTracker* mt, cudaStream_t s);
 // BF_ETIMEOUT if a tensor-core kernel's bounded wait gave up since the last reset
 int tc_status(bool reset);
+// device address of the status flag (set by any bounded wait that gave up)
+int* tc_status_ptr();
 // enqueues a copy of the device wait flag into dst (device memory) on s
 int tc_status_copy(int32_t* dst, cudaStream_t s);
 // the status of a flag value read back by tc_status_copy (resets it if asked)

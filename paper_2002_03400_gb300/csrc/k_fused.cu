@@ -564,12 +564,15 @@ size_t half_smem(const FusedHalf& H, int CS, size_t es) {
   return data + meta + 2 * FAC_BYTES;
 }
 
-int g_apply_engine = 0;   // 0: by the tuner's measurement, 1: stage launches only, 2: fused where it applies
+// 0: by the tuner's measurement, 1: stage launches only, 2: fused where it
+// applies, 3: persistent where it applies, 4: grouped where it applies
+int g_apply_engine = 0;
 
 }  // namespace
 
 int set_apply_engine(int e) {
-  if (e < 0 || e > 2) return fail(BF_EINVAL, "apply engine must be 0 (tuned), 1 (stages) or 2 (fused)");
+  if (e < 0 || e > 4)
+    return fail(BF_EINVAL, "apply engine must be 0 (tuned), 1 (stages), 2 (fused), 3 (persistent) or 4 (grouped)");
   g_apply_engine = e;
   return BF_OK;
 }

@@ -1683,6 +1683,11 @@ int wait_probe(uint64_t limit_ns, cudaStream_t s) {
   return tc_status(true);
 }
 
+int* tc_status_ptr() {
+  void* p = nullptr;
+  return cudaGetSymbolAddress(&p, g_tc_status) == cudaSuccess ? (int*)p : nullptr;
+}
+
 int tc_status_copy(int32_t* dst, cudaStream_t s) {
   BF_CUDA_TRY(cudaMemcpyFromSymbolAsync(dst, g_tc_status, sizeof(int), 0, cudaMemcpyDeviceToDevice, s));
   return BF_OK;

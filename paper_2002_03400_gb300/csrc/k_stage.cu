@@ -23,10 +23,14 @@
 //   variants 3-5: one warp per (task, 64-column slice, WFR = 8, 4 or 12
 //     rows), two columns and WFR rows per lane (a register tile: WFR
 //     broadcast factor loads and two input loads per k for 2 WFR complex
-//     FMAs).
-// In both, the warp's lanes cover CW columns x 32/CW rows, CW the smallest
-// power of two >= N (at most 32), so small numbers of right-hand sides still
-// use every lane.  The apply picks the variant per stage and column count
+//     FMAs);
+//   variants 6-7: one CTA per (task, 64-column slice, block of 16 or 32
+//     rows) that stages each round of input rows and factor entries in
+//     shared memory with asynchronous copies, all in flight at once, and
+//     computes from there (one load latency per round, not per k).
+// In variants 0-2 the warp's lanes cover CW columns x 32/CW rows, CW the
+// smallest power of two >= N (at most 32), so small numbers of right-hand
+// sides still use every lane.  The apply picks the variant per stage and column count
 // as measured by the apply tuner, else by stage_variant_default.
 // Operand layouts (per StageTerm/StageTask):
 //   ld > 0: column-major, element (k, c) at off + k + c*ld
@@ -35,6 +39,8 @@
 //           element (k, c) at (off + k)*N + c  (apply intermediates)
 // Row-major intermediates make the loads of one k and the stores of one
 // output row contiguous across the lanes.
+#include <atomic>
+
 #include "bf_internal.h"
 #include "cx.cuh"
 
@@ -425,6 +431,135 @@ stage_wide_kernel(const StageTask* __restrict__ tasks, int ntasks, StageBases ba
   }
 }
 
+// Variants 6-7 ("staged"): one CTA per (task, 64-column slice, block of
+// 8 SRR rows; SRR = 2 or 4).  The K range is walked in rounds of up to SKR
+// rows: every thread issues its share of the round's asynchronous copies
+// (the input rows of the slice, 16 bytes per copy where aligned, and the
+// factor entries of the CTA's rows), all in flight together, then one wait;
+// the products read shared memory.  Lane l holds columns 2l and 2l + 1,
+// warp w rows w SRR .. w SRR + SRR - 1 of the block, so per k a lane reads
+// one input pair and SRR factor entries (a broadcast) for 2 SRR complex
+// FMAs.  Load latency is paid once per round instead of once per k step.
+template <typename V>
+__host__ __device__ constexpr int staged_kr() {
+  return sizeof(V) == 8 ? 48 : 24;
+}
+template <typename V, int SRR>
+__host__ __device__ constexpr size_t staged_smem() {
+  return (size_t)staged_kr<V>() * (64 + 8 * SRR) * sizeof(V);
+}
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async_to_shared(void* dst, const void* src) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  if constexpr (BYTES == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+
+template <typename R, int SRR>
+__global__ void __launch_bounds__(THREADS)
+stage_staged_kernel(const StageTask* __restrict__ tasks, int ntasks, StageBases bases, int Noverride,
+                    int rblocks) {
+  using V = typename Cx<R>::V;
+  constexpr int KR = staged_kr<V>(), RB = 8 * SRR;
+  extern __shared__ __align__(16) uint8_t staged_smem_raw[];
+  V* __restrict__ xs = (V*)staged_smem_raw;   // [KR][64]: input rows of the round
+  V* __restrict__ fs = xs + KR * 64;          // [KR][RB]: factor entries (k, row)
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int Nl = Noverride;
+  const int Nmax = Nl > 0 ? Nl : -Nl;   // Nl < 0: per-task N, -Nl the widest
+  const int slices = Nmax > 0 ? (Nmax + 63) / 64 : 1;
+  const int per_task = slices * rblocks;
+  const int items = ntasks * per_task;
+  stage_prologue<V>(tasks, warp == 0 && (int)blockIdx.x < items ? (int)blockIdx.x / per_task : -1, lane);
+  for (int it = blockIdx.x; it < items; it += gridDim.x) {
+    const int ti = it / per_task, tw = it - ti * per_task;
+    const int sl = tw / rblocks, rb = tw - sl * rblocks;
+    const StageTask& tk = tasks[ti];
+    const int M = tk.M, nterms = tk.nterms;
+    const int N = Nl > 0 ? Nl : tk.N;
+    const int c0 = sl * 64, r0 = rb * RB;
+    if (c0 >= N || r0 >= M) continue;   // uniform over the CTA
+    const int cw = min(64, N - c0), mr = min(RB, M - r0);
+    const int c = 2 * lane, i0 = warp * SRR;
+    V acc[SRR][2];
+#pragma unroll
+    for (int r = 0; r < SRR; ++r) acc[r][0] = acc[r][1] = Cx<R>::make(0, 0);
+    for (int term = 0; term < nterms; ++term) {
+      const StageTerm& T = tk.t[term];
+      const V* __restrict__ mat = (const V*)T.mat;
+      const int K = T.K, ldm = T.ldm, cj = T.conjT;
+      const Strides si = strides(T.in_off, T.ldi, N);
+      const V* __restrict__ in = (const V*)bases.p[T.in_base] + si.off + c0 * si.cs;
+      // pairs of columns in one 16-byte copy: row-major rows of even length
+      // starting 16-byte aligned (complex128: every element)
+      const bool pair16 = sizeof(V) == 16 || (si.cs == 1 && (si.rs & 1) == 0 && (cw & 1) == 0 &&
+                                              ((uintptr_t)in & 15) == 0);
+      for (int k0 = 0; k0 < K; k0 += KR) {
+        const int kn = min(KR, K - k0);
+        __syncthreads();   // the previous round's reads are done
+        if (sizeof(V) == 8 && pair16) {
+          const int pw = cw >> 1;   // column pairs per row
+          for (int e = tid; e < kn * pw; e += THREADS) {
+            const int k = e / pw, p = e - k * pw;
+            cp_async_to_shared<16>(xs + k * 64 + 2 * p, in + (int64_t)(k0 + k) * si.rs + 2 * p);
+          }
+        } else {
+          for (int e = tid; e < kn * cw; e += THREADS) {
+            const int k = e / cw, cc = e - k * cw;
+            cp_async_to_shared<sizeof(V)>(xs + k * 64 + cc, in + (int64_t)(k0 + k) * si.rs + (int64_t)cc * si.cs);
+          }
+        }
+        // factor entry (row r0 + i, k0 + k) of op(mat): conj ? mat[i ldm + k] : mat[i + k ldm]
+        if (cj) {
+          for (int e = tid; e < mr * kn; e += THREADS) {
+            const int i = e / kn, k = e - i * kn;
+            cp_async_to_shared<sizeof(V)>(fs + k * RB + i, mat + (int64_t)(r0 + i) * ldm + k0 + k);
+          }
+        } else {
+          for (int e = tid; e < mr * kn; e += THREADS) {
+            const int k = e / mr, i = e - k * mr;
+            cp_async_to_shared<sizeof(V)>(fs + k * RB + i, mat + (r0 + i) + (int64_t)(k0 + k) * ldm);
+          }
+        }
+        asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+        __syncthreads();
+        if (i0 < mr) {
+          // rows past the block's end re-read its last row (never stored)
+          int ro[SRR];
+#pragma unroll
+          for (int r = 0; r < SRR; ++r) ro[r] = min(i0 + r, mr - 1);
+          const int cl = min(c, cw - 1), cr = min(c + 1, cw - 1);
+#pragma unroll 4
+          for (int k = 0; k < kn; ++k) {
+            const V a0 = xs[k * 64 + cl], a1 = xs[k * 64 + cr];
+#pragma unroll
+            for (int r = 0; r < SRR; ++r) {
+              V e = fs[k * RB + ro[r]];
+              if (cj) e.y = -e.y;
+              cmac(acc[r][0], e, a0);
+              cmac(acc[r][1], e, a1);
+            }
+          }
+        }
+      }
+    }
+    if (i0 < mr) {
+      const Strides so = strides(tk.out_off, tk.ldo, N);
+      V* __restrict__ out = (V*)bases.p[tk.out_base] + so.off;
+#pragma unroll
+      for (int r = 0; r < SRR; ++r)
+        if (i0 + r < mr) {
+          V* o = out + (int64_t)(r0 + i0 + r) * so.rs;
+          if (c < cw) o[(int64_t)(c0 + c) * so.cs] = acc[r][0];
+          if (c + 1 < cw) o[(int64_t)(c0 + c + 1) * so.cs] = acc[r][1];
+        }
+    }
+  }
+}
+
 // Untuned choice: the many-warp variant for up to 16 complex64 columns, the
 // wide register-tile variant for more, the whole-block variant for
 // complex128 (and for per-task column counts: peeling).
@@ -531,6 +666,13 @@ int launch_peel(const StageTask* d_tasks, int ntasks, int maxM, int maxN, int ma
   return BF_OK;
 }
 
+static std::atomic<int> g_stage_variant{-1};
+int set_stage_variant(int v) {
+  if (v < -1 || v >= STAGE_VARIANTS) return fail(BF_EINVAL, "stage variant must be -1 .. 7");
+  g_stage_variant.store(v);
+  return BF_OK;
+}
+
 int stage_variant_default(int nrhs, int dtype) {
   if (dtype == BF_C64 && nrhs > 0) return nrhs <= 16 ? 0 : 3;
   return 2;
@@ -540,6 +682,7 @@ int launch_stage(const StageTask* d_tasks, int ntasks, int maxM, int maxN, int N
                  const StageBases& bases, int dtype, cudaStream_t s, int variant, bool pdl) {
   if (Noverride > 0) maxN = Noverride;
   if (ntasks <= 0 || maxM <= 0 || maxN <= 0) return BF_OK;
+  if (Noverride > 0 && g_stage_variant.load() >= 0) variant = g_stage_variant.load();
   if (variant < 0) variant = stage_variant_default(Noverride, dtype);
   // lanes along columns: the smallest power of two >= N, at most 32 (per-task
   // N without an override: 32)
@@ -552,12 +695,18 @@ int launch_stage(const StageTask* d_tasks, int ntasks, int maxM, int maxN, int N
   const int gr = (32 >> lcw) * RT;
   // wide variants: 8 (variant 3), 4 (variant 4) or 12 (variant 5) rows per warp
   const int wfr = variant == 4 ? 4 : variant == 5 ? 12 : 8;
-  const bool wide_v = variant >= 3;
-  const int rgroups = variant == 0 ? (maxM + gr - 1) / gr : wide_v ? (maxM + wfr - 1) / wfr : 1;
+  const bool wide_v = variant >= 3 && variant <= 5;
+  // staged variants: blocks of 16 (variant 6) or 32 (variant 7) rows per CTA
+  const bool staged_v = variant >= 6;
+  const int srb = variant == 7 ? 32 : 16;
+  const int rgroups = variant == 0 ? (maxM + gr - 1) / gr
+                      : wide_v     ? (maxM + wfr - 1) / wfr
+                      : staged_v   ? (maxM + srb - 1) / srb
+                                   : 1;
   const int64_t wslices = Noverride != 0 ? ((Noverride > 0 ? Noverride : -Noverride) + 63) / 64 : 1;
-  const int64_t warps = (int64_t)ntasks * (wide_v ? wslices : slices) * rgroups;
+  const int64_t warps = (int64_t)ntasks * (wide_v || staged_v ? wslices : slices) * rgroups;
   if (warps >= ((int64_t)1 << 31)) return fail(BF_EINVAL, "stage launch too large");
-  int64_t blocks = (warps + WARPS - 1) / WARPS;
+  int64_t blocks = staged_v ? warps : (warps + WARPS - 1) / WARPS;   // staged: one CTA per item
   if (blocks > 152 * 32) blocks = 152 * 32;
   // launch with a programmatic dependency on the previous kernel when asked
   cudaLaunchAttribute attr[1];
@@ -587,6 +736,16 @@ int launch_stage(const StageTask* d_tasks, int ntasks, int maxM, int maxN, int N
       case 12: e = wide(stage_wide_kernel<double, 12>, stage_wide_kernel<float, 12>); break;
       default: e = wide(stage_wide_kernel<double, 8>, stage_wide_kernel<float, 8>); break;
     }
+  } else if (staged_v) {
+    auto staged = [&](auto kd, auto kf, size_t smd, size_t smf) {
+      cfg.dynamicSmemBytes = dtype == BF_C128 ? smd : smf;
+      return dtype == BF_C128 ? cudaLaunchKernelEx(&cfg, kd, d_tasks, ntasks, bases, Noverride, rgroups)
+                              : cudaLaunchKernelEx(&cfg, kf, d_tasks, ntasks, bases, Noverride, rgroups);
+    };
+    e = variant == 7 ? staged(stage_staged_kernel<double, 4>, stage_staged_kernel<float, 4>,
+                              staged_smem<double2, 4>(), staged_smem<float2, 4>())
+                     : staged(stage_staged_kernel<double, 2>, stage_staged_kernel<float, 2>,
+                              staged_smem<double2, 2>(), staged_smem<float2, 2>());
   } else if (variant == 1) {
     cfg.dynamicSmemBytes = 0;
     e = dtype == BF_C128 ? cudaLaunchKernelEx(&cfg, stage_rows_kernel<double>, d_tasks, ntasks, bases, Noverride, lcw)
