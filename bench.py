@@ -565,12 +565,16 @@ def main():
     ms, fms = max_over_ranks([ms, fms], dist, "cuda")
 
     # apply GB/s (resident factors, complex64 and complex128), after the
-    # apply tuner has chosen engine, slice width and stage shapes; the stage
-    # engine (L + 3 launches) beside it
+    # apply tuner has chosen engine, depth, slice width and stage shapes;
+    # each engine beside it.  Device time: a device-side sleep queued ahead
+    # of the first event lets the host enqueue every apply before the GPU
+    # reaches it, so host launch costs stay outside the timed region.
     def apply_time(F, xin, reps=20):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         F.apply(xin)
         torch.cuda.synchronize()
+        if hasattr(torch.cuda, "_sleep"):
+            torch.cuda._sleep(20_000_000)   # ~10 ms at 2 GHz
         e0.record(stream)
         for _ in range(reps):
             F.apply(xin)
@@ -584,13 +588,13 @@ def main():
         nr = xin.shape[1]
         byts = info["stored_entries"] * es + nr * (2 * N) * es
         F.tune(nr, xin.dtype)
-        t = apply_time(F, xin)               # the tuned choice (engine, slice width, stage shapes)
-        api.set_apply_engine("stages")
-        ts = apply_time(F, xin)
-        api.set_apply_engine("fused")
-        tf = apply_time(F, xin)
+        t = apply_time(F, xin)               # the tuned choice (engine, depth, slice width, stage shapes)
+        other = []
+        for eng in ("stages", "fused", "persistent", "grouped"):
+            api.set_apply_engine(eng)
+            other.append(apply_time(F, xin))
         api.set_apply_engine("auto")
-        return byts / t / 1e9, t, byts, (ts, tf)
+        return byts / t / 1e9, t, byts, tuple(other)
 
     gbs32, t32, b32, ts32 = apply_gbs(F, x32)
     gbs64, t64, b64, ts64 = apply_gbs(F64, x)
@@ -779,8 +783,9 @@ def main():
                                     "unit": "Tops/s", "frac": ALU_OPS_PER_ENTRY * N * N / t_sk / 1e12 / alu_peak,
                                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz",
                                     "tensor_frac": tc_flops / t_sk / 1e12 / tc_peak},
-                     "apply": {"kernel": "the tuned apply engine (stage launches with the wide register-tile "
-                                         "kernel, or the fused two-launch engine where measured faster)",
+                     "apply": {"kernel": "the tuned apply engine (the fastest measured of: grouped runs of stages "
+                                         "per launch, stage launches, the fused two-launch engine, the "
+                                         "persistent cooperative launch)",
                                "bound": "alu (complex64, 64 RHS: 4 FP32 FMA per factor entry and column; "
                                         "the HBM fraction is reported beside it)",
                                "achieved_gbs_c64": gbs32, "peak_gbs": peaks.get("hbm_gbs"),
@@ -800,6 +805,10 @@ def main():
                                                    "c64_1rhs": ts1[0] * 1e3},
                                "fused_engine_ms": {"c64": ts32[1] * 1e3, "c128": ts64[1] * 1e3,
                                                    "c64_1rhs": ts1[1] * 1e3},
+                               "persistent_engine_ms": {"c64": ts32[2] * 1e3, "c128": ts64[2] * 1e3,
+                                                        "c64_1rhs": ts1[2] * 1e3},
+                               "grouped_engine_ms": {"c64": ts32[3] * 1e3, "c128": ts64[3] * 1e3,
+                                                     "c64_1rhs": ts1[3] * 1e3},
                                "work": f"factor entries + {NRHS} input and {NRHS} output columns, once each"}},
     }
     if rank == 0 and not args.no_cpu:

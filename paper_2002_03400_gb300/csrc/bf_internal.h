@@ -294,9 +294,9 @@ struct FlowPlan {
 // its group's tasks, the run's inner stages in shared memory.
 constexpr int GR_MAXD = 4;
 struct GroupedTerm {
-  const void* mat;          // factor entries in global memory
-  int32_t fac_off;          // element offset in the group's staged factors (-1: read mat)
-  int32_t K, ldm;
+  const void* mat;          // factor entries in global memory (entry (i, k) at mat[i ldm + k] when conjT, else mat[i + k ldm])
+  int32_t fac_off;          // staged tile: element offset, entry (i, k) at fac_off + k tld + i (-1: read mat)
+  int32_t K, ldm, tld;      // tld: the tile's row pitch (M rounded up to even)
   int16_t conjT, in_reg;    // input: shared-memory region in_reg (0: the staged run inputs)
   int32_t in_row;           // first local row of the input in that region
 };
@@ -311,11 +311,11 @@ struct GroupedSpan {        // global input rows [g0, g0 + rows) -> region-0 row
   int64_t g0;
   int32_t l0, rows;
 };
-struct GroupedSeg {         // a factor block copied whole into the staged factors
-  const void* src;
-  int32_t dst, count;
+struct GroupedSeg {         // one term's entries staged as a tile (entry (i, k) -> dst + k tld + i)
+  const void* src;          // entry (i, k) at src[i ldm + k] when conj, else src[i + k ldm]
+  int32_t dst, M, K, ldm, tld, conj;
 };
-constexpr int GR_RB = 4;              // rows of a work item (a thread's register tile: GR_RB rows x 2 columns)
+constexpr int GR_RB = 16;             // rows of a work item (a lane's register tile: up to GR_RB rows x 1 column)
 struct GroupedGroup {
   int32_t task0, ntasks, span0, nspans, seg0, nseg, chunk0;
   int32_t fac_elems;                    // staged factor elements (0: none staged)

@@ -31,7 +31,6 @@
 namespace bf {
 
 namespace {
-constexpr int GT = 256;
 constexpr size_t GR_SMEM_LIMIT = 110 * 1024;   // two CTAs per SM
 constexpr size_t GR_FAC_LIMIT = 40 * 1024;     // staged factor bytes per group (more: read in place)
 
@@ -61,91 +60,115 @@ __device__ __forceinline__ void gr_cp_async(void* dst, const void* src) {
 __host__ __device__ constexpr size_t gr_align16(size_t b) { return (b + 15) & ~(size_t)15; }
 static_assert(sizeof(GroupedTask) % 8 == 0, "task descriptors are copied in 8-byte words");
 
-// columns c and c + 1 of one row (16-byte aligned for complex64)
-__device__ __forceinline__ void gr_ld_pair(const float2* p, float2& a, float2& b) {
-  const float4 v = *(const float4*)p;
-  a = make_float2(v.x, v.y);
-  b = make_float2(v.z, v.w);
-}
-__device__ __forceinline__ void gr_ld_pair(const double2* p, double2& a, double2& b) {
-  a = p[0];
-  b = p[1];
-}
-
 // shared-memory bytes of one CTA: task descriptors, row chunks, staged
-// factor blocks, the rows of every region (CW columns each)
+// factor tiles, the rows of every region (CW columns each)
 template <typename V>
 __host__ __device__ size_t gr_smem_bytes(int tasks_max, int chunks_max, int fac_max, int rows_max, int CW) {
   return gr_align16((size_t)tasks_max * sizeof(GroupedTask)) + gr_align16((size_t)chunks_max * 4) +
          (size_t)fac_max * sizeof(V) + (size_t)rows_max * CW * sizeof(V);
 }
 
-// one work item: rows r0 .. r0 + nr - 1 of task T for columns cl, cr of
-// the slice; terms in order, k ascending (the stage kernels' FMA chains)
-template <typename R, bool PAIR>
-__device__ __forceinline__ void gr_item(const GroupedTask& T, int r0, const typename Cx<R>::V* __restrict__ rsm,
-                                        const typename Cx<R>::V* __restrict__ fsm, const int32_t* reg_row, int CW,
-                                        int cl, int cr, typename Cx<R>::V (&acc)[GR_RB][2]) {
-  using V = typename Cx<R>::V;
-  const int nr = min(GR_RB, T.M - r0);
-#pragma unroll
-  for (int r = 0; r < GR_RB; ++r) acc[r][0] = acc[r][1] = Cx<R>::make(0, 0);
-  for (int q = 0; q < T.nterms; ++q) {
-    const GroupedTerm& Q = T.t[q];
-    const V* __restrict__ in = rsm + (int64_t)(reg_row[Q.in_reg] + Q.in_row) * CW;
-    const V* __restrict__ mat = Q.fac_off >= 0 ? fsm + Q.fac_off : (const V*)Q.mat;
-    const int K = Q.K, ldm = Q.ldm;
-    // rows past the task's end re-read its last row (never stored)
-    int ro[GR_RB];
-    if (Q.conjT) {
-#pragma unroll
-      for (int r = 0; r < GR_RB; ++r) ro[r] = (r0 + min(r, nr - 1)) * ldm;
+template <typename V, bool CJ>
+__device__ __forceinline__ void gr_fma(V& acc, const V e, const V x) {
+  if constexpr (CJ) cmac_conj(acc, e, x);
+  else cmac(acc, e, x);
+}
+
+// Rows r0 .. r0 + NR - 1 of a staged term for the lane's column c (x: the
+// term's input rows, CW columns each; t: the tile, entry (i, k) at
+// t[k tld + i]): acc[r] += op(A)(r0 + r, k) x(k, c), k ascending -- the
+// stage kernels' FMA chain (CJ: op(A) = conj(A)^T, the staged entries are
+// A's, the conjugate is taken in the multiply).  Complex64 tiles have an
+// even pitch and even r0, so row pairs are single 16-byte loads.
+template <typename V, int NR, bool CJ>
+__device__ __forceinline__ void gr_tile_s(const V* __restrict__ x, int CW, const V* __restrict__ t, int tld, int K,
+                                          V* acc) {
 #pragma unroll 2
-      for (int kk = 0; kk < K; ++kk) {
-        V x0, x1;
-        if constexpr (PAIR) {
-          gr_ld_pair(in + kk * CW + cl, x0, x1);
-        } else {
-          x0 = in[kk * CW + cl], x1 = in[kk * CW + cr];
-        }
+  for (int kk = 0; kk < K; ++kk) {
+    const V xv = *x;
+    if constexpr (sizeof(V) == 8) {
 #pragma unroll
-        for (int r = 0; r < GR_RB; ++r) {
-          const V e = mat[ro[r] + kk];
-          cmac_conj(acc[r][0], e, x0);
-          cmac_conj(acc[r][1], e, x1);
-        }
+      for (int r = 0; r + 1 < NR; r += 2) {
+        const float4 e2 = *(const float4*)(t + r);
+        gr_fma<V, CJ>(acc[r], make_float2(e2.x, e2.y), xv);
+        gr_fma<V, CJ>(acc[r + 1], make_float2(e2.z, e2.w), xv);
       }
+      if constexpr (NR & 1) gr_fma<V, CJ>(acc[NR - 1], t[NR - 1], xv);
     } else {
 #pragma unroll
-      for (int r = 0; r < GR_RB; ++r) ro[r] = r0 + min(r, nr - 1);
+      for (int r = 0; r < NR; ++r) gr_fma<V, CJ>(acc[r], t[r], xv);
+    }
+    x += CW;
+    t += tld;
+  }
+}
+
+// the same for a term read in place (global memory, the factor's layout)
+template <typename V, int NR, bool CJ>
+__device__ __forceinline__ void gr_tile_g(const V* __restrict__ x, int CW, const V* __restrict__ mat, int ldm, int K,
+                                          int r0, V* acc) {
 #pragma unroll 2
-      for (int kk = 0; kk < K; ++kk) {
-        V x0, x1;
-        if constexpr (PAIR) {
-          gr_ld_pair(in + kk * CW + cl, x0, x1);
-        } else {
-          x0 = in[kk * CW + cl], x1 = in[kk * CW + cr];
-        }
-        const V* __restrict__ mk = mat + (int64_t)kk * ldm;
+  for (int kk = 0; kk < K; ++kk) {
+    const V xv = x[kk * CW];
+    if constexpr (CJ) {
+      const V* __restrict__ m = mat + (int64_t)r0 * ldm + kk;
 #pragma unroll
-        for (int r = 0; r < GR_RB; ++r) {
-          const V e = mk[ro[r]];
-          cmac(acc[r][0], e, x0);
-          cmac(acc[r][1], e, x1);
-        }
-      }
+      for (int r = 0; r < NR; ++r) cmac_conj(acc[r], m[r * ldm], xv);
+    } else {
+      const V* __restrict__ m = mat + (int64_t)kk * ldm + r0;
+#pragma unroll
+      for (int r = 0; r < NR; ++r) cmac(acc[r], m[r], xv);
+    }
+  }
+}
+
+// one term for nr (<= MR) rows, nr known at run time and uniform over the
+// warp: one fully unrolled body per count, no work on absent rows
+template <typename V, int MR>
+__device__ __forceinline__ void gr_term(const GroupedTerm& Q, const V* __restrict__ fsm, const V* __restrict__ x,
+                                        int CW, int r0, int nr, V* acc) {
+  const bool cj = Q.conjT != 0;
+  if (Q.fac_off >= 0) {
+    const V* t = fsm + Q.fac_off + r0;
+    switch (nr) {
+#define GR_CASE(n)                                                                           \
+  case n:                                                                                    \
+    if constexpr (n <= MR) {                                                                 \
+      if (cj) gr_tile_s<V, n, true>(x, CW, t, Q.tld, Q.K, acc);                             \
+      else gr_tile_s<V, n, false>(x, CW, t, Q.tld, Q.K, acc);                               \
+    }                                                                                        \
+    break;
+      GR_CASE(1) GR_CASE(2) GR_CASE(3) GR_CASE(4) GR_CASE(5) GR_CASE(6) GR_CASE(7) GR_CASE(8)
+      GR_CASE(9) GR_CASE(10) GR_CASE(11) GR_CASE(12) GR_CASE(13) GR_CASE(14) GR_CASE(15) GR_CASE(16)
+#undef GR_CASE
+      default: break;
+    }
+  } else {
+    const V* mat = (const V*)Q.mat;
+    switch (nr) {
+#define GR_CASE(n)                                                                           \
+  case n:                                                                                    \
+    if constexpr (n <= MR) {                                                                 \
+      if (cj) gr_tile_g<V, n, true>(x, CW, mat, Q.ldm, Q.K, r0, acc);                       \
+      else gr_tile_g<V, n, false>(x, CW, mat, Q.ldm, Q.K, r0, acc);                         \
+    }                                                                                        \
+    break;
+      GR_CASE(1) GR_CASE(2) GR_CASE(3) GR_CASE(4) GR_CASE(5) GR_CASE(6) GR_CASE(7) GR_CASE(8)
+      GR_CASE(9) GR_CASE(10) GR_CASE(11) GR_CASE(12) GR_CASE(13) GR_CASE(14) GR_CASE(15) GR_CASE(16)
+#undef GR_CASE
+      default: break;
     }
   }
 }
 }  // namespace
 
-template <typename R>
-__global__ void __launch_bounds__(GT) grouped_kernel(const GroupedArgs a) {
+template <typename R, int NT>
+__device__ __forceinline__ void grouped_body(const GroupedArgs& a) {
   using V = typename Cx<R>::V;
   extern __shared__ __align__(16) uint8_t gr_smem[];
   GroupedTask* __restrict__ stask = (GroupedTask*)gr_smem;
   int32_t* __restrict__ schunk = (int32_t*)(gr_smem + gr_align16((size_t)a.tasks_max * sizeof(GroupedTask)));
-  V* __restrict__ fsm = (V*)((uint8_t*)schunk + gr_align16((size_t)a.chunks_max * 4));   // staged factor blocks
+  V* __restrict__ fsm = (V*)((uint8_t*)schunk + gr_align16((size_t)a.chunks_max * 4));   // staged factor tiles
   V* __restrict__ rsm = fsm + a.fac_max;                                                 // rows, CW columns each
   const GroupedGroup& G = a.groups[a.group0 + blockIdx.x];
   const int tid = threadIdx.x;
@@ -153,18 +176,32 @@ __global__ void __launch_bounds__(GT) grouped_kernel(const GroupedArgs a) {
   const int c0 = blockIdx.y * CW;
   const int cw = min(CW, N - c0);
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  // descriptors, row chunks and factor blocks: independent of the previous launch
+  // descriptors, row chunks and factor tiles: independent of the previous launch
   {
     const int nw = G.ntasks * (int)(sizeof(GroupedTask) / 8);
     const uint2* src = (const uint2*)(a.tasks + G.task0);
     uint2* dst = (uint2*)stask;
-    for (int v = tid; v < nw; v += GT) dst[v] = src[v];
+    for (int v = tid; v < nw; v += NT) dst[v] = src[v];
     const int nc = G.st_chunk[G.nst];
-    for (int v = tid; v < nc; v += GT) schunk[v] = a.chunks[G.chunk0 + v];
+    for (int v = tid; v < nc; v += NT) schunk[v] = a.chunks[G.chunk0 + v];
   }
+  // every thread copies a share of each tile (all copies in flight at once)
   for (int g = 0; g < G.nseg; ++g) {
     const GroupedSeg sg = a.segs[G.seg0 + g];
-    for (int e = tid; e < sg.count; e += GT) gr_cp_async<sizeof(V)>(fsm + sg.dst + e, (const V*)sg.src + e);
+    const V* src = (const V*)sg.src;
+    V* dst = fsm + sg.dst;
+    const int n = sg.M * sg.K;
+    if (sg.conj) {   // A^T's rows are A's columns: consecutive k are consecutive in memory
+      for (int e = tid; e < n; e += NT) {
+        const int i = e / sg.K, k = e - i * sg.K;
+        gr_cp_async<sizeof(V)>(dst + k * sg.tld + i, src + (int64_t)i * sg.ldm + k);
+      }
+    } else {
+      for (int e = tid; e < n; e += NT) {
+        const int k = e / sg.M, i = e - k * sg.M;
+        gr_cp_async<sizeof(V)>(dst + k * sg.tld + i, src + i + (int64_t)k * sg.ldm);
+      }
+    }
   }
   asm volatile("cp.async.commit_group;" ::: "memory");
   asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -173,12 +210,12 @@ __global__ void __launch_bounds__(GT) grouped_kernel(const GroupedArgs a) {
   for (int sp = 0; sp < G.nspans; ++sp) {
     const GroupedSpan S = a.spans[G.span0 + sp];
     if (a.in_ld == 0) {
-      for (int e = tid; e < S.rows * cw; e += GT) {
+      for (int e = tid; e < S.rows * cw; e += NT) {
         const int i = e / cw, c = e - i * cw;
         gr_cp_async<sizeof(V)>(rsm + (int64_t)(S.l0 + i) * CW + c, x + (S.g0 + i) * N + c0 + c);
       }
     } else {
-      for (int e = tid; e < S.rows * cw; e += GT) {
+      for (int e = tid; e < S.rows * cw; e += NT) {
         const int c = e / S.rows, i = e - c * S.rows;
         gr_cp_async<sizeof(V)>(rsm + (int64_t)(S.l0 + i) * CW + c, x + (S.g0 + i) + (int64_t)(c0 + c) * a.in_ld);
       }
@@ -186,44 +223,67 @@ __global__ void __launch_bounds__(GT) grouped_kernel(const GroupedArgs a) {
   }
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
   __syncthreads();
-  const int pairs = (cw + 1) >> 1;
-  // 16-byte input pairs: complex64 with an even slice width
-  const bool pair = sizeof(V) == 8 && (CW & 1) == 0;
   V* __restrict__ y = (V*)a.y;
+  const int lane = tid & 31, warp = tid >> 5;
+  // complex128: chunks in tiles of 8 rows (registers)
+  constexpr int MR = sizeof(V) == 16 ? 8 : GR_RB;
   for (int k = 0; k < G.nst; ++k) {
-    const int ch0 = G.st_chunk[k], items = (G.st_chunk[k + 1] - ch0) * pairs;
-    for (int idx = tid; idx < items; idx += GT) {
-      const int ch = idx / pairs, p = idx - ch * pairs;
+    const int ch0 = G.st_chunk[k], nch = G.st_chunk[k + 1] - ch0;
+    // one warp per (row chunk, 32-column slice), lane = column; with few
+    // columns one lane per (row, column) instead
+    const bool wide = cw >= 16;
+    const int ncs = (cw + 31) >> 5;
+    const int items = wide ? nch * ncs : nch * GR_RB * cw;
+    for (int it = wide ? warp : tid; it < items; it += wide ? NT / 32 : NT) {
+      int ch, c, rsub = 0, rcount;
+      if (wide) {
+        ch = it / ncs;
+        c = (it - ch * ncs) * 32 + lane;
+      } else {
+        c = it % cw;
+        const int rr = it / cw;
+        ch = rr / GR_RB;
+        rsub = rr - ch * GR_RB;
+      }
       const int32_t cp = schunk[ch0 + ch];
       const GroupedTask& T = stask[cp & 0xffff];
-      const int r0 = cp >> 16;
-      const int cl = 2 * p, cr = min(2 * p + 1, cw - 1);
-      V acc[GR_RB][2];
-      if (pair) gr_item<R, true>(T, r0, rsm, fsm, G.reg_row, CW, cl, cr, acc);
-      else gr_item<R, false>(T, r0, rsm, fsm, G.reg_row, CW, cl, cr, acc);
-      const int nr = min(GR_RB, T.M - r0);
-      if (T.out_reg > 0) {
-        V* o = rsm + (int64_t)(G.reg_row[T.out_reg] + T.out_row + r0) * CW;
+      const int rbase = (cp >> 16) + rsub;
+      rcount = wide ? min(GR_RB, T.M - (cp >> 16)) : (rbase < T.M ? 1 : 0);
+      if (c >= cw || rcount <= 0) continue;
+      for (int h = 0; h < rcount; h += MR) {
+        const int r0 = rbase + h, nr = min(MR, rcount - h);
+        V acc[MR];
 #pragma unroll
-        for (int r = 0; r < GR_RB; ++r)
-          if (r < nr) {
-            o[r * CW + cl] = acc[r][0];
-            if (cl + 1 < cw) o[r * CW + cl + 1] = acc[r][1];
-          }
-      } else {
-        const int64_t rs = T.ldo > 0 ? 1 : N, cs = T.ldo > 0 ? T.ldo : 1;
-        V* o = y + (T.ldo > 0 ? T.out_row : T.out_row * N) + (int64_t)r0 * rs;
+        for (int r = 0; r < MR; ++r) acc[r] = Cx<R>::make(0, 0);
+        for (int q = 0; q < T.nterms; ++q) {
+          const GroupedTerm& Q = T.t[q];
+          const V* xin = rsm + (int64_t)(G.reg_row[Q.in_reg] + Q.in_row) * CW + c;
+          gr_term<V, MR>(Q, fsm, xin, CW, r0, nr, acc);
+        }
+        if (T.out_reg > 0) {
+          V* o = rsm + (int64_t)(G.reg_row[T.out_reg] + T.out_row + r0) * CW + c;
 #pragma unroll
-        for (int r = 0; r < GR_RB; ++r)
-          if (r < nr) {
-            o[r * rs + (int64_t)(c0 + cl) * cs] = acc[r][0];
-            if (cl + 1 < cw) o[r * rs + (int64_t)(c0 + cl + 1) * cs] = acc[r][1];
-          }
+          for (int r = 0; r < MR; ++r)
+            if (r < nr) o[r * CW] = acc[r];
+        } else {
+          const int64_t rs = T.ldo > 0 ? 1 : N, cs = T.ldo > 0 ? T.ldo : 1;
+          V* o = y + (T.ldo > 0 ? T.out_row : T.out_row * N) + (int64_t)r0 * rs + (int64_t)(c0 + c) * cs;
+#pragma unroll
+          for (int r = 0; r < MR; ++r)
+            if (r < nr) o[r * rs] = acc[r];
+        }
       }
     }
     __syncthreads();   // this stage's blocks are complete
   }
 }
+
+// complex64 within 128 registers (no spills), 256 threads for slices of 64
+// columns and 128 for narrower ones; complex128 (FP64-bound) 256 threads at
+// the compiler's register choice.
+__global__ void __launch_bounds__(256, 2) grouped_kernel_c64_256(const GroupedArgs a) { grouped_body<float, 256>(a); }
+__global__ void __launch_bounds__(128, 4) grouped_kernel_c64_128(const GroupedArgs a) { grouped_body<float, 128>(a); }
+__global__ void __launch_bounds__(256) grouped_kernel_c128_256(const GroupedArgs a) { grouped_body<double, 256>(a); }
 
 // ------------------------------------------------------------------ host --
 namespace {
@@ -245,22 +305,6 @@ struct DSU {
     if (a != b) p[std::max(a, b)] = std::min(a, b);
   }
 };
-
-// the factor block (first element, element count) holding a term's entries
-bool locate_block(const Fact* F, int dtype, const void* ptr, const char** base, int64_t* count) {
-  const size_t es = elem_bytes(dtype);
-  for (const Stage& S : F->st) {
-    const char* b = (const char*)(dtype == BF_C128 ? S.d64.p : S.d32.p);
-    if (!b || (const char*)ptr < b || (const char*)ptr >= b + S.total * (int64_t)es) continue;
-    const int64_t e = ((const char*)ptr - b) / (int64_t)es;
-    const int blk = (int)(std::upper_bound(S.off.begin(), S.off.end(), e) - S.off.begin()) - 1;
-    if (blk < 0) return false;
-    *base = b + S.off[blk] * (int64_t)es;
-    *count = (int64_t)S.rows[blk] * S.cols[blk];
-    return true;
-  }
-  return false;
-}
 
 // sorted, disjoint row ranges [a, b) -> consecutive local rows
 struct RowMap {
@@ -370,8 +414,9 @@ bool build_run(const Fact* F, int dtype, const std::vector<StageTask>& all, cons
     for (size_t sp = 0; sp < reg[0].r.size(); ++sp)
       T.spans.push_back({reg[0].r[sp].first, reg[0].l0[sp], (int32_t)(reg[0].r[sp].second - reg[0].r[sp].first)});
     G.nspans = (int32_t)reg[0].r.size();
-    // factor blocks of the group (each once)
-    std::map<const char*, int32_t> placed;
+    // each term's entries as a tile of the group's staged factors (entry
+    // (i, k) at dst + k tld + i, tld = M rounded up to even; every tile
+    // starts at an even element, so complex64 row pairs are 16-byte aligned)
     std::vector<GroupedSeg> segs;
     int64_t fac = 0;
     std::vector<GroupedTask> gt;
@@ -393,27 +438,22 @@ bool build_run(const Fact* F, int dtype, const std::vector<StageTask>& all, cons
           g.out_row = tk.out_off;
           g.ldo = tk.ldo;
         }
+        const int tld = tk.M + (tk.M & 1);
         for (int q = 0; q < tk.nterms; ++q) {
           const StageTerm& S = tk.t[q];
           GroupedTerm& Q = g.t[q];
           Q.mat = S.mat;
           Q.K = S.K;
           Q.ldm = S.ldm;
+          Q.tld = tld;
           Q.conjT = S.conjT;
           Q.in_reg = (int16_t)k;
           const int64_t lr = reg[k].at(S.in_off);
           if (S.K > 0 && (lr < 0 || reg[k].at(S.in_off + S.K - 1) != lr + S.K - 1)) return false;
           Q.in_row = (int32_t)std::max<int64_t>(lr, 0);
-          const char* b = nullptr;
-          int64_t cnt = 0;
-          if (!locate_block(F, dtype, S.mat, &b, &cnt)) return false;
-          auto it = placed.find(b);
-          if (it == placed.end()) {
-            it = placed.emplace(b, (int32_t)fac).first;
-            segs.push_back({b, (int32_t)fac, (int32_t)cnt});
-            fac += cnt + (cnt & 1);   // keep every block 16-byte aligned for complex64
-          }
-          Q.fac_off = it->second + (int32_t)(((const char*)S.mat - b) / (int64_t)es);
+          Q.fac_off = (int32_t)fac;
+          if (tk.M > 0 && S.K > 0) segs.push_back({S.mat, (int32_t)fac, tk.M, S.K, S.ldm, tld, S.conjT});
+          fac += (int64_t)S.K * tld;
         }
         if (gt.size() >= 0x10000 || tk.M >= 0x8000) return false;
         for (int r0 = 0; r0 < tk.M; r0 += GR_RB) chunks.push_back((r0 << 16) | (int32_t)gt.size());
@@ -581,31 +621,36 @@ int run_grouped(Fact* F, int opC, int dtype, int64_t nrhs, const void* xt, void*
     a.y = bases[run.out_base];
     a.fac_max = run.fac_max;
     const int slices = (int)((nrhs + CW - 1) / CW);
+    // 256 threads (8 warps) for 64-column slices, 128 for narrower ones
+    // (complex128: 256)
+    const int NT = CW > 32 || dtype == BF_C128 ? 256 : 128;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)run.ngroups, (unsigned)slices);
-    cfg.blockDim = dim3(GT);
+    cfg.blockDim = dim3(NT);
     cfg.dynamicSmemBytes = bytes(CW);
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = r > 0 ? 1 : 0;
-    // the attribute is the kernel's largest size, set once per process
+    // the attribute is each kernel's largest size, set once per process
     // (never lowered under a launch of another host thread)
-    static std::once_flag attr_once[2];
-    static cudaError_t attr_err[2] = {cudaSuccess, cudaSuccess};
-    const int di = dtype == BF_C128 ? 1 : 0;
-    std::call_once(attr_once[di], [&] {
-      attr_err[di] = di ? cudaFuncSetAttribute(grouped_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)GR_SMEM_LIMIT)
-                        : cudaFuncSetAttribute(grouped_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)GR_SMEM_LIMIT);
+    static std::once_flag attr_once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(attr_once, [&] {
+      const void* k[3] = {(const void*)grouped_kernel_c64_256, (const void*)grouped_kernel_c64_128,
+                          (const void*)grouped_kernel_c128_256};
+      for (int i = 0; i < 3 && attr_err == cudaSuccess; ++i)
+        attr_err = cudaFuncSetAttribute(k[i], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GR_SMEM_LIMIT);
     });
-    BF_CUDA_TRY(attr_err[di]);
+    BF_CUDA_TRY(attr_err);
     note_launch();
-    const cudaError_t e = dtype == BF_C128 ? cudaLaunchKernelEx(&cfg, grouped_kernel<double>, a)
-                                           : cudaLaunchKernelEx(&cfg, grouped_kernel<float>, a);
+    cudaError_t e;
+    if (dtype == BF_C128)
+      e = cudaLaunchKernelEx(&cfg, grouped_kernel_c128_256, a);
+    else
+      e = NT == 256 ? cudaLaunchKernelEx(&cfg, grouped_kernel_c64_256, a) : cudaLaunchKernelEx(&cfg, grouped_kernel_c64_128, a);
     if (e != cudaSuccess) return fail(BF_ECUDA, std::string("grouped apply launch: ") + cudaGetErrorString(e));
     BF_CUDA_TRY(cudaGetLastError());
   }
