@@ -241,12 +241,13 @@ int bf_apply_T(bf_fact F, int op, int64_t nrhs, const void* x, int64_t ldx,
 int bf_apply_tune(bf_fact F, int op, int64_t nrhs, int dtype, void* stream, float* ms_out);
 
 /* Graph-captured apply (eq. hybrid_butterfly_mat).  bf_applier_create
- * captures the stage chain of y = F x (op BF_OP_N), F^T x (BF_OP_T) or
+ * captures the launches of y = F x (op BF_OP_N), F^T x (BF_OP_T) or
  * F^H x (BF_OP_C) for nrhs right-hand sides of dtype BF_C64/BF_C128, on
- * buffers the applier owns, once into a CUDA graph (stage-kernel shapes as
- * tuned by bf_apply_tune before the call, else the defaults).  F must
- * outlive the applier; free it with bf_free.  BF_EINVAL, BF_ENOMEM,
- * BF_ECUDA. */
+ * buffers the applier owns, once into a CUDA graph: the engine bf_apply
+ * would use at the time of the call (bf_set_apply_engine, bf_apply_tune;
+ * the fused engine, which works on user-order x and y, is replaced by the
+ * grouped or the stage launches).  F must outlive the applier; free it
+ * with bf_free.  BF_EINVAL, BF_ENOMEM, BF_ECUDA. */
 typedef struct bf_applier_s* bf_applier;
 int bf_applier_create(bf_fact F, int op, int64_t nrhs, int dtype, bf_applier* out);
 
@@ -403,14 +404,16 @@ int bf_debug_wait_timeout(uint64_t limit_ns, void* stream);
  *     ceil((L + 3) / depth) launches, results equal to the stage engine's
  *     bit for bit; the tuner picks the depth.
  * engine 0 (default): the engine bf_apply_tune measured fastest for the
- * right-hand-side class (untuned: stages); 1: stages only; 2: fused
+ * right-hand-side class (untuned: grouped, depth 3 for complex64 and 2 for
+ * complex128, where it applies; else stages); 1: stages only; 2: fused
  * wherever it applies; 3: persistent wherever it applies (not when x and y
  * overlap); 4: grouped wherever it applies.  BF_EINVAL otherwise.  Not
  * thread-safe against running applies. */
 int bf_set_apply_engine(int engine);
 
 /* Run depth of the grouped apply engine (diagnostic): 0 (default) the depth
- * bf_apply_tune chose (untuned: 3); 1-4 that many stages per launch for
+ * bf_apply_tune chose (untuned: 3 for complex64, 2 for complex128); 1-4
+ * that many stages per launch for
  * every later grouped apply.  BF_EINVAL otherwise.  Not thread-safe against
  * running applies. */
 int bf_set_grouped_depth(int depth);

@@ -282,6 +282,35 @@ int run_apply_stages(Fact* F, int opC, int dtype, int64_t nrhs, void* xt, void* 
   return BF_OK;
 }
 
+// The engine for the stages of one apply on tree-order buffers: 0 the stage
+// launches, 1 the persistent launch, 2 the grouped launches.  Forced by
+// bf_set_apply_engine (3, 4), else the tuner's measurement for the
+// right-hand-side class, else (untuned) the grouped engine, which is faster
+// than the stage launches for every column count measured (depth 3 for
+// complex64, 2 for complex128).  Builds what it picks; falls back to the
+// stage launches where an engine does not apply.  overlap: x and y share
+// memory (the persistent engine's stages overlap in time, and a grouped
+// apply of one run reads x and writes y in the same launch).
+int pick_inner_engine(Fact* F, int opC, int dtype, int64_t nrhs, bool overlap, cudaStream_t s, int* out) {
+  *out = 0;
+  const int cls = nrhs_class(nrhs), eng = apply_engine();
+  if (eng == 1 || eng == 2) return BF_OK;
+  GroupedPlan& gp = F->gp[opC][dtype];
+  if (!overlap && (eng == 3 || (eng == 0 && F->fl[opC][dtype].pick[cls]))) {
+    BF_TRY(build_flow(F, opC, dtype, s));
+    if (F->fl[opC][dtype].ok) {
+      *out = 1;
+      return BF_OK;
+    }
+  }
+  if (eng == 4 || (eng == 0 && (gp.pick[cls] || !gp.tuned[cls]))) {
+    const int depth = grouped_depth() > 0 ? grouped_depth() : gp.built ? gp.depth : dtype == BF_C128 ? 2 : 3;
+    BF_TRY(build_grouped(F, opC, dtype, depth, s));
+    if (gp.ok && !(overlap && gp.runs.size() < 2)) *out = 2;
+  }
+  return BF_OK;
+}
+
 int prepare_apply(Fact* F, int opC, int dtype, cudaStream_t s) {
   if (dtype == BF_C64) BF_TRY(F->ensure32(s));
   if (!F->ap[opC][dtype].built) BF_TRY(build_apply(F, opC, dtype, s));
@@ -321,10 +350,8 @@ int apply_fact(Fact* F, int op, int64_t nrhs, const void* x, int64_t ldx, void* 
   }
   const bool direct_in = id_in && !conj && ldx == in_rows;
   const bool direct_out = id_out && !conj && ldy == out_rows;
-  // the persistent engine: forced (engine 3), or measured fastest for this
-  // right-hand-side class; its stages may run while the first still reads
-  // x, so not when x and y overlap
-  const int cls = nrhs_class(nrhs);
+  // the engine of the stages (pick_inner_engine); x and y overlapping rule
+  // out the engines whose stages overlap in time
   bool overlap = false;
   if (direct_in && direct_out) {
     const char *xa = (const char*)x, *ya = (const char*)y;
@@ -332,17 +359,10 @@ int apply_fact(Fact* F, int op, int64_t nrhs, const void* x, int64_t ldx, void* 
     const char* yb = ya + (size_t)(ldy * (nrhs - 1) + out_rows) * es;
     overlap = !(xb <= ya || yb <= xa);
   }
-  bool flow = !overlap && (apply_engine() == 3 || (apply_engine() == 0 && F->fl[opC][dtype].pick[cls]));
-  if (flow) BF_TRY(build_flow(F, opC, dtype, s));
-  flow = flow && F->fl[opC][dtype].ok;
-  // the grouped engine (runs of stages per launch): forced (engine 4), or
-  // measured fastest for this class
+  int engine = 0;
+  BF_TRY(pick_inner_engine(F, opC, dtype, nrhs, overlap, s, &engine));
+  const bool flow = engine == 1, grouped = engine == 2;
   GroupedPlan& gp = F->gp[opC][dtype];
-  bool grouped = !flow && (apply_engine() == 4 || (apply_engine() == 0 && gp.pick[cls]));
-  if (grouped)
-    BF_TRY(build_grouped(F, opC, dtype, grouped_depth() > 0 ? grouped_depth() : gp.built ? gp.depth : 3, s));
-  // one run reads x and writes y in the same launch
-  grouped = grouped && gp.ok && !(overlap && gp.runs.size() < 2);
   const int64_t lvl = (grouped ? gp.level_rows_max : F->ap[opC][dtype].level_rows_max) * nrhs;
   const size_t inner = flow ? flow_scratch_bytes(F->fl[opC][dtype], nrhs, dtype) : (size_t)(2 * lvl) * es;
   const size_t bytes = inner + ((direct_in ? 0 : in_rows * nrhs) + (direct_out ? 0 : out_rows * nrhs)) * es;
@@ -507,6 +527,7 @@ int tune_apply(Fact* F, int op, int dtype, int64_t nrhs, cudaStream_t s, float* 
     const float best = std::min(std::min(total, fused_best), std::min(flow_best, grouped_best));
     fl.pick[cls] = flow_best == best && best < total ? 1 : 0;
     gp.pick[cls] = !fl.pick[cls] && grouped_best == best && best < total ? 1 : 0;
+    gp.tuned[cls] = 1;
     if (fused_best < 1e30f) fp.engine[cls] = !fl.pick[cls] && !gp.pick[cls] && fused_best <= total ? 0 : 1;
   }
   cudaEventDestroy(e[0]);
@@ -541,8 +562,15 @@ int applier_create(Fact* F, int op, int64_t nrhs, int dtype, Applier** out) {
   if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) rc = fail(BF_ECUDA, "stream create failed");
   if (!rc) rc = prepare_apply(F, A->opC, dtype, cs);
   const size_t es = elem_bytes(dtype);
-  const int64_t lvl = rc ? 0 : F->ap[A->opC][dtype].level_rows_max * nrhs;
-  if (!rc) rc = A->scratch.alloc(&F->mem, (size_t)(A->in_rows * nrhs + A->out_rows * nrhs + 2 * lvl) * es, nullptr);
+  // the engine bf_apply would use for this column count (internal x and y
+  // never overlap)
+  int inner = 0;
+  if (!rc) rc = pick_inner_engine(F, A->opC, dtype, nrhs, false, cs, &inner);
+  const int64_t lvl = rc ? 0
+                         : (inner == 2 ? F->gp[A->opC][dtype].level_rows_max
+                                       : F->ap[A->opC][dtype].level_rows_max) * nrhs;
+  const size_t inner_bytes = inner == 1 ? flow_scratch_bytes(F->fl[A->opC][dtype], nrhs, dtype) : (size_t)(2 * lvl) * es;
+  if (!rc) rc = A->scratch.alloc(&F->mem, (size_t)(A->in_rows * nrhs + A->out_rows * nrhs) * es + inner_bytes, nullptr);
   if (!rc) {
     char* p = (char*)A->scratch.p;
     A->xt = p;
@@ -553,7 +581,9 @@ int applier_create(Fact* F, int op, int64_t nrhs, int dtype, Applier** out) {
         cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
       rc = fail(BF_ECUDA, "graph capture could not start");
     } else {
-      rc = run_apply_stages(F, A->opC, dtype, nrhs, A->xt, ping, pong, A->yt, cs);
+      rc = inner == 1   ? run_flow(F, A->opC, dtype, nrhs, A->xt, A->yt, ping, cs)
+           : inner == 2 ? run_grouped(F, A->opC, dtype, nrhs, A->xt, A->yt, ping, pong, cs)
+                        : run_apply_stages(F, A->opC, dtype, nrhs, A->xt, ping, pong, A->yt, cs);
       cudaGraph_t g = nullptr;
       const cudaError_t e = cudaStreamEndCapture(cs, &g);
       if (!rc && e != cudaSuccess) rc = fail(BF_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));

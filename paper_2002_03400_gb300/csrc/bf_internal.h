@@ -342,7 +342,8 @@ struct GroupedPlan {
   const int32_t* d_chunks = nullptr;    // (first row << 16) | task index within the group
   int64_t level_rows_max = 0;           // rows of the largest run output (the two level buffers)
   std::array<int16_t, NRHS_CLASSES> cw{{0, 0, 0, 0, 0, 0}};   // tuned column-slice width (0: default)
-  std::array<int8_t, NRHS_CLASSES> pick{{0, 0, 0, 0, 0, 0}};   // 1: the tuner measured it fastest
+  std::array<int8_t, NRHS_CLASSES> pick{{0, 0, 0, 0, 0, 0}};    // 1: the tuner measured it fastest
+  std::array<int8_t, NRHS_CLASSES> tuned{{0, 0, 0, 0, 0, 0}};   // 1: the tuner has measured this class
 };
 
 struct Fact {
@@ -415,11 +416,15 @@ int flow_wait_probe(uint64_t limit_ns, cudaStream_t s);
 int build_grouped(Fact* F, int opC, int dtype, int depth, cudaStream_t s);
 int run_grouped(Fact* F, int opC, int dtype, int64_t nrhs, const void* xt, void* yt, void* ping, void* pong,
                 cudaStream_t s, int cw_override = 0);
-// 0: the tuned depth (untuned: 3); 1 .. GR_MAXD: that depth for every grouped apply
+// 0: the tuned depth (untuned: 3 for complex64, 2 for complex128); 1 .. GR_MAXD:
+// that depth for every grouped apply
 int set_grouped_depth(int depth);
+// the engine of an apply's stages on tree-order buffers (0 stage launches,
+// 1 persistent, 2 grouped), built as needed
+int pick_inner_engine(Fact* F, int opC, int dtype, int64_t nrhs, bool overlap, cudaStream_t s, int* out);
 int grouped_depth();
 // 0: the fastest engine the tuner measured for the right-hand-side class
-// (default; untuned: stage launches); 1: stage launches only; 2: fused
+// (default; untuned: grouped where it applies); 1: stage launches only; 2: fused
 // wherever it applies; 3: persistent wherever it applies; 4: grouped
 int set_apply_engine(int e);
 int apply_engine();
