@@ -404,16 +404,19 @@ int bf_debug_wait_timeout(uint64_t limit_ns, void* stream);
  *     ceil((L + 3) / depth) launches, results equal to the stage engine's
  *     bit for bit; the tuner picks the depth.
  * engine 0 (default): the engine bf_apply_tune measured fastest for the
- * right-hand-side class (untuned: grouped, depth 3 for complex64 and 2 for
- * complex128, where it applies; else stages); 1: stages only; 2: fused
+ * right-hand-side class; untuned, the stage launches for the first two
+ * applies of a factorization in each direction and dtype, then grouped
+ * where it applies (its plan takes about a millisecond of host time to
+ * build once), at a depth set by the largest block rank (<= 16: 3 for
+ * complex64, 2 for complex128; <= 32: 2; else 1); 1: stages only; 2: fused
  * wherever it applies; 3: persistent wherever it applies (not when x and y
  * overlap); 4: grouped wherever it applies.  BF_EINVAL otherwise.  Not
  * thread-safe against running applies. */
 int bf_set_apply_engine(int engine);
 
 /* Run depth of the grouped apply engine (diagnostic): 0 (default) the depth
- * bf_apply_tune chose (untuned: 3 for complex64, 2 for complex128); 1-4
- * that many stages per launch for
+ * bf_apply_tune chose (untuned: from the largest block rank, see
+ * bf_set_apply_engine); 1-4 that many stages per launch for
  * every later grouped apply.  BF_EINVAL otherwise.  Not thread-safe against
  * running applies. */
 int bf_set_grouped_depth(int depth);

@@ -155,9 +155,10 @@ def set_parallel_sides(on: bool):
 
 def set_apply_engine(engine: str):
     """'auto' (default: the engine bf_apply_tune measured fastest for the
-    right-hand-side class; untuned: the grouped engine where it applies),
-    'stages', 'fused', 'persistent' or 'grouped' (the last three wherever
-    they apply)."""
+    right-hand-side class; untuned: the stage launches for a factorization's
+    first two applies, then the grouped engine where it applies), 'stages',
+    'fused', 'persistent' or 'grouped' (the last three wherever they
+    apply)."""
     check(lib().bf_set_apply_engine({"auto": 0, "stages": 1, "fused": 2, "persistent": 3, "grouped": 4}[engine]))
 
 
@@ -172,8 +173,8 @@ STAGE_VARIANTS = 8
 
 def set_grouped_depth(depth: int):
     """Stages per launch of the grouped apply engine: 0 (default) the tuned
-    depth (untuned: 3 for complex64, 2 for complex128), 1..4 that depth for
-    every later grouped apply."""
+    depth (untuned: set by the largest block rank), 1..4 that depth for every
+    later grouped apply."""
     check(lib().bf_set_grouped_depth(int(depth)))
 
 

@@ -286,11 +286,32 @@ int run_apply_stages(Fact* F, int opC, int dtype, int64_t nrhs, void* xt, void* 
 // launches, 1 the persistent launch, 2 the grouped launches.  Forced by
 // bf_set_apply_engine (3, 4), else the tuner's measurement for the
 // right-hand-side class, else (untuned) the grouped engine, which is faster
-// than the stage launches for every column count measured (depth 3 for
-// complex64, 2 for complex128).  Builds what it picks; falls back to the
-// stage launches where an engine does not apply.  overlap: x and y share
-// memory (the persistent engine's stages overlap in time, and a grouped
-// apply of one run reads x and writes y in the same launch).
+// than the stage launches for every column count measured on the 2-D line
+// pair and from 16 columns on for the 3-D caps (at default_grouped_depth)
+// -- from the GR_BUILD_AFTER-th untuned apply
+// of (F, op, dtype) on: its plan costs more host time to build than a few
+// applies save, so a factorization applied once or twice keeps the stage
+// launches.  Builds what it picks; falls back to the stage launches where
+// an engine does not apply.  overlap: x and y share memory (the persistent
+// engine's stages overlap in time, and a grouped apply of one run reads x
+// and writes y in the same launch).
+// Untuned run depth of the grouped engine from the factorization's largest
+// block rank: small blocks (the 2-D line pair, ranks ~10) gain most from
+// keeping three stages in shared memory; with ranks ~55 (3-D caps) a group
+// of two or three stages no longer fits in shared memory with wide column
+// slices, and one stage per launch (staged tiles, one warp per row chunk)
+// is fastest (measured 1.4-2x faster than the stage launches there, two to
+// three stages 1.1-3x slower).
+static int default_grouped_depth(const Fact* F, int dtype) {
+  int rmax = 0;
+  for (const auto& v : F->rV)
+    for (int r : v) rmax = std::max(rmax, r);
+  for (const auto& v : F->rU)
+    for (int r : v) rmax = std::max(rmax, r);
+  if (rmax <= 16) return dtype == BF_C128 ? 2 : 3;
+  return rmax <= 32 ? 2 : 1;
+}
+
 int pick_inner_engine(Fact* F, int opC, int dtype, int64_t nrhs, bool overlap, cudaStream_t s, int* out) {
   *out = 0;
   const int cls = nrhs_class(nrhs), eng = apply_engine();
@@ -303,8 +324,12 @@ int pick_inner_engine(Fact* F, int opC, int dtype, int64_t nrhs, bool overlap, c
       return BF_OK;
     }
   }
-  if (eng == 4 || (eng == 0 && (gp.pick[cls] || !gp.tuned[cls]))) {
-    const int depth = grouped_depth() > 0 ? grouped_depth() : gp.built ? gp.depth : dtype == BF_C128 ? 2 : 3;
+  bool want = eng == 4 || (eng == 0 && gp.pick[cls]);
+  if (eng == 0 && !gp.tuned[cls]) want = ++gp.untuned_uses >= GR_BUILD_AFTER;
+  if (want) {
+    const int depth = grouped_depth() > 0   ? grouped_depth()
+                      : gp.tuned_depth > 0 ? gp.tuned_depth
+                                           : default_grouped_depth(F, dtype);
     BF_TRY(build_grouped(F, opC, dtype, depth, s));
     if (gp.ok && !(overlap && gp.runs.size() < 2)) *out = 2;
   }
@@ -323,7 +348,8 @@ int apply_fact(Fact* F, int op, int64_t nrhs, const void* x, int64_t ldx, void* 
   if (dtype != BF_C64 && dtype != BF_C128) return fail(BF_EINVAL, "dtype must be BF_C64 or BF_C128");
   if (op != BF_OP_N && op != BF_OP_T && op != BF_OP_C) return fail(BF_EINVAL, "bad op");
   const int opC = op == BF_OP_N ? 0 : 1;
-  BF_TRY(prepare_apply(F, opC, dtype, s));
+  // the stage launches' device task lists are built below only when they run
+  if (dtype == BF_C64) BF_TRY(F->ensure32(s));
   const Plan* P = F->plan;
   const int64_t in_rows = opC ? P->m : P->n, out_rows = opC ? P->n : P->m;
   if (ldx < in_rows || ldy < out_rows) return fail(BF_EINVAL, "leading dimension too small");
@@ -362,6 +388,7 @@ int apply_fact(Fact* F, int op, int64_t nrhs, const void* x, int64_t ldx, void* 
   int engine = 0;
   BF_TRY(pick_inner_engine(F, opC, dtype, nrhs, overlap, s, &engine));
   const bool flow = engine == 1, grouped = engine == 2;
+  if (!flow && !grouped) BF_TRY(prepare_apply(F, opC, dtype, s));
   GroupedPlan& gp = F->gp[opC][dtype];
   const int64_t lvl = (grouped ? gp.level_rows_max : F->ap[opC][dtype].level_rows_max) * nrhs;
   const size_t inner = flow ? flow_scratch_bytes(F->fl[opC][dtype], nrhs, dtype) : (size_t)(2 * lvl) * es;
@@ -520,6 +547,7 @@ int tune_apply(Fact* F, int op, int dtype, int64_t nrhs, cudaStream_t s, float* 
     if (!rc && best_depth > 0) {
       rc = build_grouped(F, opC, dtype, best_depth, s);
       gp.cw[cls] = (int16_t)best_cw;
+      gp.tuned_depth = best_depth;
     }
   }
   // the fastest engine serves this class from now on

@@ -315,6 +315,7 @@ struct GroupedSeg {         // one term's entries staged as a tile (entry (i, k)
   const void* src;          // entry (i, k) at src[i ldm + k] when conj, else src[i + k ldm]
   int32_t dst, M, K, ldm, tld, conj;
 };
+constexpr int GR_BUILD_AFTER = 3;     // untuned applies of (F, op, dtype) before the grouped engine takes over
 constexpr int GR_RB = 16;             // rows of a work item (a lane's register tile: up to GR_RB rows x 1 column)
 struct GroupedGroup {
   int32_t task0, ntasks, span0, nspans, seg0, nseg, chunk0;
@@ -344,6 +345,9 @@ struct GroupedPlan {
   std::array<int16_t, NRHS_CLASSES> cw{{0, 0, 0, 0, 0, 0}};   // tuned column-slice width (0: default)
   std::array<int8_t, NRHS_CLASSES> pick{{0, 0, 0, 0, 0, 0}};    // 1: the tuner measured it fastest
   std::array<int8_t, NRHS_CLASSES> tuned{{0, 0, 0, 0, 0, 0}};   // 1: the tuner has measured this class
+  int tuned_depth = 0;                  // the depth the tuner measured fastest (0: none)
+  int64_t untuned_uses = 0;             // applies that found no tuned choice (the plan is built from the
+                                        // GR_BUILD_AFTER-th on: it costs ~1.5 ms of host time at n = 16384)
 };
 
 struct Fact {
@@ -416,7 +420,7 @@ int flow_wait_probe(uint64_t limit_ns, cudaStream_t s);
 int build_grouped(Fact* F, int opC, int dtype, int depth, cudaStream_t s);
 int run_grouped(Fact* F, int opC, int dtype, int64_t nrhs, const void* xt, void* yt, void* ping, void* pong,
                 cudaStream_t s, int cw_override = 0);
-// 0: the tuned depth (untuned: 3 for complex64, 2 for complex128); 1 .. GR_MAXD:
+// 0: the tuned depth (untuned: set by the largest block rank); 1 .. GR_MAXD:
 // that depth for every grouped apply
 int set_grouped_depth(int depth);
 // the engine of an apply's stages on tree-order buffers (0 stage launches,

@@ -21,7 +21,6 @@
 #include <algorithm>
 #include <atomic>
 #include <cstring>
-#include <map>
 #include <mutex>
 #include <numeric>
 
@@ -339,71 +338,94 @@ struct RunTables {
   std::vector<int32_t> chunks;
 };
 
-// Builds the groups of stages [s0, s0 + d) into T; false when a group does
-// not fit (then the caller retries with a shorter run).
-bool build_run(const Fact* F, int dtype, const std::vector<StageTask>& all, const ApplyPlan& tmp, int s0, int d,
-               GroupedRun& run, RunTables& T) {
+// Builds the groups of stages [s0, s0 + d) into T (cleared first; every
+// index is absolute: `base` holds the sizes of the tables already built);
+// false when a group does not fit (the caller retries with a shorter run).
+bool build_run(int dtype, const std::vector<StageTask>& all, const ApplyPlan& tmp, int s0, int d,
+               const RunTables& base, GroupedRun& run, RunTables& T) {
+  T.groups.clear();
+  T.tasks.clear();
+  T.spans.clear();
+  T.segs.clear();
+  T.chunks.clear();
   const size_t es = elem_bytes(dtype);
-  // tasks of the run, local numbering
-  std::vector<int> first(d + 1, 0);
+  // tasks of the run, local numbering (stage by stage)
+  int first[GR_MAXD + 1];
+  first[0] = 0;
   for (int k = 0; k < d; ++k) first[k + 1] = first[k] + tmp.count[s0 + k];
   const int nt = first[d];
-  auto gidx = [&](int k, int j) { return tmp.first[s0 + k] + j; };
+  auto task = [&](int i) -> const StageTask& {
+    int k = 0;
+    while (i >= first[k + 1]) ++k;
+    return all[tmp.first[s0 + k] + (i - first[k])];
+  };
   DSU dsu(nt);
   // producers inside the run: stage k's terms read stage k - 1's outputs
+  std::vector<std::pair<int64_t, int>> outs;   // (out_off, local index) of stage k - 1
   for (int k = 1; k < d; ++k) {
-    std::vector<std::pair<int64_t, int>> outs;   // (out_off, local index) of stage k - 1
-    for (int j = 0; j < tmp.count[s0 + k - 1]; ++j) outs.push_back({all[gidx(k - 1, j)].out_off, first[k - 1] + j});
+    outs.clear();
+    for (int i = first[k - 1]; i < first[k]; ++i) outs.push_back({task(i).out_off, i});
     std::sort(outs.begin(), outs.end());
-    for (int j = 0; j < tmp.count[s0 + k]; ++j) {
-      const StageTask& tk = all[gidx(k, j)];
+    for (int i = first[k]; i < first[k + 1]; ++i) {
+      const StageTask& tk = task(i);
       for (int q = 0; q < tk.nterms; ++q) {
-        const int64_t a = tk.t[q].in_off, b = a + tk.t[q].K;
-        auto it = std::upper_bound(outs.begin(), outs.end(), std::make_pair(a, INT32_MAX));
+        const int64_t lo = tk.t[q].in_off, hi = lo + tk.t[q].K;
+        auto it = std::upper_bound(outs.begin(), outs.end(), std::make_pair(lo, INT32_MAX));
         if (it != outs.begin()) --it;
-        for (; it != outs.end() && it->first < b; ++it) {
-          const StageTask& pr = all[tmp.first[s0 + k - 1] + (it->second - first[k - 1])];
-          if (it->first + pr.M > a) dsu.join(first[k] + j, it->second);
-        }
+        for (; it != outs.end() && it->first < hi; ++it)
+          if (it->first + task(it->second).M > lo) dsu.join(i, it->second);
       }
     }
   }
-  // components in order of their first task
-  std::map<int, std::vector<int>> comp;
-  for (int i = 0; i < nt; ++i) comp[dsu.find(i)].push_back(i);
-  run.group0 = (int32_t)T.groups.size();
-  run.ngroups = (int32_t)comp.size();
+  // components in order of their smallest task (the root), members
+  // ascending (so stage by stage): a counting sort by component
+  std::vector<int> gid(nt), cnt, mem(nt);
+  int ng = 0;
+  for (int i = 0; i < nt; ++i) {
+    const int r = dsu.find(i);
+    gid[i] = r == i ? ng++ : gid[r];
+  }
+  cnt.assign(ng + 1, 0);
+  for (int i = 0; i < nt; ++i) ++cnt[gid[i] + 1];
+  for (int g = 0; g < ng; ++g) cnt[g + 1] += cnt[g];
+  {
+    std::vector<int> pos(cnt.begin(), cnt.end() - 1);
+    for (int i = 0; i < nt; ++i) mem[pos[gid[i]]++] = i;
+  }
+  run.group0 = (int32_t)(base.groups.size());
+  run.ngroups = ng;
   run.fac_max = 0;
   run.rows_max = 0;
   run.tasks_max = 0;
   run.chunks_max = 0;
-  for (auto& kv : comp) {
-    const std::vector<int>& mem = kv.second;   // ascending: stage by stage
+  RowMap reg[GR_MAXD];
+  std::vector<std::pair<int64_t, int64_t>> v;
+  for (int g = 0; g < ng; ++g) {
+    const int m0 = cnt[g], m1 = cnt[g + 1];
+    // members of stage k: [sb[k], sb[k + 1]) within mem
+    int sb[GR_MAXD + 1];
+    for (int k = 0, m = m0; k < d; ++k) {
+      sb[k] = m;
+      while (m < m1 && mem[m] < first[k + 1]) ++m;
+    }
+    sb[d] = m1;
     GroupedGroup G{};
-    G.task0 = (int32_t)T.tasks.size();
-    G.span0 = (int32_t)T.spans.size();
-    G.seg0 = (int32_t)T.segs.size();
-    G.chunk0 = (int32_t)T.chunks.size();
+    G.task0 = (int32_t)(base.tasks.size() + T.tasks.size());
+    G.span0 = (int32_t)(base.spans.size() + T.spans.size());
+    G.seg0 = (int32_t)(base.segs.size() + T.segs.size());
+    G.chunk0 = (int32_t)(base.chunks.size() + T.chunks.size());
     G.nst = d;
-    std::vector<std::vector<int>> byst(d);
-    for (int i : mem) {
-      const int k = (int)(std::upper_bound(first.begin(), first.end(), i) - first.begin()) - 1;
-      byst[k].push_back(i);
-    }
     // regions: 0 = the stage-0 inputs, k = the outputs of stage k - 1
-    std::vector<RowMap> reg(d);
-    {
-      std::vector<std::pair<int64_t, int64_t>> v;
-      for (int i : byst[0]) {
-        const StageTask& tk = all[gidx(0, i - first[0])];
-        for (int q = 0; q < tk.nterms; ++q) v.push_back({tk.t[q].in_off, tk.t[q].in_off + tk.t[q].K});
-      }
-      reg[0].build(v);
+    v.clear();
+    for (int m = sb[0]; m < sb[1]; ++m) {
+      const StageTask& tk = task(mem[m]);
+      for (int q = 0; q < tk.nterms; ++q) v.push_back({tk.t[q].in_off, tk.t[q].in_off + tk.t[q].K});
     }
+    reg[0].build(v);
     for (int k = 1; k < d; ++k) {
-      std::vector<std::pair<int64_t, int64_t>> v;
-      for (int i : byst[k - 1]) {
-        const StageTask& tk = all[gidx(k - 1, i - first[k - 1])];
+      v.clear();
+      for (int m = sb[k - 1]; m < sb[k]; ++m) {
+        const StageTask& tk = task(mem[m]);
         v.push_back({tk.out_off, tk.out_off + tk.M});
       }
       reg[k].build(v);
@@ -417,31 +439,29 @@ bool build_run(const Fact* F, int dtype, const std::vector<StageTask>& all, cons
     // each term's entries as a tile of the group's staged factors (entry
     // (i, k) at dst + k tld + i, tld = M rounded up to even; every tile
     // starts at an even element, so complex64 row pairs are 16-byte aligned)
-    std::vector<GroupedSeg> segs;
+    const size_t t0 = T.tasks.size(), seg0 = T.segs.size(), ch0 = T.chunks.size();
     int64_t fac = 0;
-    std::vector<GroupedTask> gt;
-    std::vector<int32_t> chunks;
     G.st_chunk[0] = 0;
     for (int k = 0; k < d; ++k) {
-      for (int i : byst[k]) {
-        const StageTask& tk = all[gidx(k, i - first[k])];
-        GroupedTask g{};
-        g.M = tk.M;
-        g.nterms = tk.nterms;
+      for (int m = sb[k]; m < sb[k + 1]; ++m) {
+        const StageTask& tk = task(mem[m]);
+        GroupedTask gt{};
+        gt.M = tk.M;
+        gt.nterms = tk.nterms;
         if (k < d - 1) {
-          g.out_reg = (int16_t)(k + 1);
-          g.out_row = reg[k + 1].at(tk.out_off);
-          if (g.out_row < 0) return false;
-          g.ldo = 0;
+          gt.out_reg = (int16_t)(k + 1);
+          gt.out_row = reg[k + 1].at(tk.out_off);
+          if (gt.out_row < 0) return false;
+          gt.ldo = 0;
         } else {
-          g.out_reg = 0;
-          g.out_row = tk.out_off;
-          g.ldo = tk.ldo;
+          gt.out_reg = 0;
+          gt.out_row = tk.out_off;
+          gt.ldo = tk.ldo;
         }
         const int tld = tk.M + (tk.M & 1);
         for (int q = 0; q < tk.nterms; ++q) {
           const StageTerm& S = tk.t[q];
-          GroupedTerm& Q = g.t[q];
+          GroupedTerm& Q = gt.t[q];
           Q.mat = S.mat;
           Q.K = S.K;
           Q.ldm = S.ldm;
@@ -452,28 +472,26 @@ bool build_run(const Fact* F, int dtype, const std::vector<StageTask>& all, cons
           if (S.K > 0 && (lr < 0 || reg[k].at(S.in_off + S.K - 1) != lr + S.K - 1)) return false;
           Q.in_row = (int32_t)std::max<int64_t>(lr, 0);
           Q.fac_off = (int32_t)fac;
-          if (tk.M > 0 && S.K > 0) segs.push_back({S.mat, (int32_t)fac, tk.M, S.K, S.ldm, tld, S.conjT});
+          if (tk.M > 0 && S.K > 0) T.segs.push_back({S.mat, (int32_t)fac, tk.M, S.K, S.ldm, tld, S.conjT});
           fac += (int64_t)S.K * tld;
         }
-        if (gt.size() >= 0x10000 || tk.M >= 0x8000) return false;
-        for (int r0 = 0; r0 < tk.M; r0 += GR_RB) chunks.push_back((r0 << 16) | (int32_t)gt.size());
-        gt.push_back(g);
+        const size_t li = T.tasks.size() - t0;
+        if (li >= 0x10000 || tk.M >= 0x8000) return false;
+        for (int r0 = 0; r0 < tk.M; r0 += GR_RB) T.chunks.push_back((r0 << 16) | (int32_t)li);
+        T.tasks.push_back(gt);
       }
-      G.st_chunk[k + 1] = (int32_t)chunks.size();
+      G.st_chunk[k + 1] = (int32_t)(T.chunks.size() - ch0);
     }
     for (int k = d + 1; k <= GR_MAXD; ++k) G.st_chunk[k] = G.st_chunk[d];
-    G.ntasks = (int32_t)gt.size();
+    G.ntasks = (int32_t)(T.tasks.size() - t0);
     if ((size_t)fac * es > GR_FAC_LIMIT) {   // read the factors in place
-      for (auto& g : gt)
-        for (int q = 0; q < g.nterms; ++q) g.t[q].fac_off = -1;
-      segs.clear();
+      for (size_t t = t0; t < T.tasks.size(); ++t)
+        for (int q = 0; q < T.tasks[t].nterms; ++q) T.tasks[t].t[q].fac_off = -1;
+      T.segs.resize(seg0);
       fac = 0;
     }
     G.fac_elems = (int32_t)fac;
-    G.nseg = (int32_t)segs.size();
-    T.segs.insert(T.segs.end(), segs.begin(), segs.end());
-    T.tasks.insert(T.tasks.end(), gt.begin(), gt.end());
-    T.chunks.insert(T.chunks.end(), chunks.begin(), chunks.end());
+    G.nseg = (int32_t)(T.segs.size() - seg0);
     T.groups.push_back(G);
     run.fac_max = std::max(run.fac_max, (int32_t)fac);
     run.rows_max = std::max(run.rows_max, G.reg_row[d]);
@@ -498,14 +516,19 @@ int build_grouped(Fact* F, int opC, int dtype, int depth, cudaStream_t s) {
   GroupedPlan& gp = F->gp[opC][dtype];
   if (gp.built && gp.depth == depth) return BF_OK;
   if (depth < 1 || depth > GR_MAXD) return fail(BF_EINVAL, "grouped apply depth must be 1 .. 4");
-  const auto pick = gp.pick;
+  const auto pick = gp.pick, tuned = gp.tuned;
   const auto cws = gp.cw;
+  const int tuned_depth = gp.tuned_depth;
+  const int64_t uses = gp.untuned_uses;
   gp.dev.release(s);
   gp = GroupedPlan();
   gp.built = true;
   gp.depth = depth;
   gp.pick = pick;
+  gp.tuned = tuned;
   gp.cw = cws;
+  gp.tuned_depth = tuned_depth;
+  gp.untuned_uses = uses;
   ApplyPlan tmp;
   std::vector<StageTask> all;
   apply_tasks_host(F, opC, dtype, tmp, all);
@@ -536,16 +559,19 @@ int build_grouped(Fact* F, int opC, int dtype, int depth, cudaStream_t s) {
     prev_out = out;
   }
   if (in_ld0 < 0) in_ld0 = 0;
-  RunTables T;
+  RunTables T, R;
   int64_t lvl_max = 0;
   int buf = 1;
   for (int s0 = 0; s0 < nst;) {
     int d = std::min(depth, nst - s0);
     GroupedRun run{};
     for (;; --d) {
-      RunTables trial = T;
-      if (build_run(F, dtype, all, tmp, s0, d, run, trial)) {
-        T = std::move(trial);
+      if (build_run(dtype, all, tmp, s0, d, T, run, R)) {
+        T.groups.insert(T.groups.end(), R.groups.begin(), R.groups.end());
+        T.tasks.insert(T.tasks.end(), R.tasks.begin(), R.tasks.end());
+        T.spans.insert(T.spans.end(), R.spans.begin(), R.spans.end());
+        T.segs.insert(T.segs.end(), R.segs.begin(), R.segs.end());
+        T.chunks.insert(T.chunks.end(), R.chunks.begin(), R.chunks.end());
         break;
       }
       if (d == 1) return BF_OK;   // a single stage does not fit: not applicable
