@@ -49,8 +49,8 @@ ALU_OPS_PER_ENTRY = 71
 # (the image profile case), from ncu; the image read once, X and Y.  Valid
 # only for the kernel source it was captured on (SHA-256 prefix below); after
 # any change to that file the line reports traffic null until a new capture.
-IMG_TRAFFIC_N8192 = 541692672 + 6614272
-IMG_TRAFFIC_SOURCE_SHA = "d8d6861de3c0c4e2"
+IMG_TRAFFIC_N8192 = 541691392 + 6283008
+IMG_TRAFFIC_SOURCE_SHA = "729e94c36183ee54"
 
 
 def measured_peaks():
@@ -143,7 +143,8 @@ def profile_case(args):
     """Small cases of one kernel family, sized for ncu captures (a few GB on
     the device at most): the on-the-fly sketch product (n = 8192, 22
     columns, all rows against all sources), the apply of a factorization
-    (n = 16384, 64 right-hand sides), one factorization (its QR levels) or
+    (n = 16384, 64 and 1 right-hand sides, grouped engine then stage
+    launches), one factorization (its QR levels) or
     factorizations at n = 8192 with entry images."""
     import torch
     from paper_2002_03400_gb300 import api, inputs
@@ -185,15 +186,26 @@ def profile_case(args):
                         precision="mixed", r0=R0, qr_fp64=True)
         F = api.Factorization.factor(plan, api.Operator.kernel(plan))
         if args.profile_case == "apply":
-            # applies of 64 and of 1 complex64 right-hand sides, fused engine
-            # then stage engine
+            # applies of 64 and of 1 complex64 right-hand sides, grouped
+            # engine (untuned depth) then stage launches, each engine warmed
+            # first; only the applies run between cudaProfilerStart and Stop
+            # (ncu --profile-from-start off captures them alone)
             x = api.colmajor(torch.from_numpy(inputs.random_rhs(N, NRHS, seed=1)).to(torch.complex64).cuda())
-            for eng in ("fused", "stages"):
+            x1 = api.colmajor(x[:, :1].clone())
+            for eng in ("grouped", "stages"):
+                api.set_apply_engine(eng)
+                F.apply(x)
+                F.apply(x1)
+            torch.cuda.synchronize()
+            torch.cuda.profiler.start()
+            for eng in ("grouped", "stages"):
                 api.set_apply_engine(eng)
                 for _ in range(3):
                     F.apply(x)
                 for _ in range(3):
-                    F.apply(x[:, :1])
+                    F.apply(x1)
+            torch.cuda.synchronize()
+            torch.cuda.profiler.stop()
             api.set_apply_engine("auto")
     torch.cuda.synchronize()
     print("profile case done")
