@@ -390,11 +390,12 @@ int bf_debug_wait_timeout(uint64_t limit_ns, void* stream);
  *     on the CTAs of one GPU); the tree permutations and the conjugation of
  *     F^T are folded into the loads and stores; used where a subtree's
  *     intermediates fit in shared memory.
- *   - persistent: one cooperative launch over all stages; each output
- *     block starts once the blocks it reads are written (per-block flags,
- *     bounded waits), every stage writes its own rows of one stacked buffer,
- *     and each block's factor entries are staged in shared memory while it
- *     waits; results equal the stage engine's bit for bit.
+ *   - persistent: the grouped engine's runs (below) in one cooperative
+ *     launch: a (group, column slice) task starts once the groups it reads
+ *     have written their rows (per-task flags, bounded waits), every run
+ *     writes its own rows of one stacked buffer, and a task's factor tiles
+ *     are staged while it waits; results equal the stage engine's bit for
+ *     bit.
  *   - grouped: the stages in runs of 1-4 consecutive stages, one launch
  *     per run; the blocks of a run fall into small connected groups (for
  *     the W levels and depth 3: 4 + 4 + 4 blocks reading 8 blocks of the

@@ -467,8 +467,6 @@ void destroy_fact(Fact* F) {
   for (auto& a : F->fp)
     for (auto& b : a)
       for (auto& h : b.h) h.dev.release(nullptr);
-  for (auto& a : F->fl)
-    for (auto& b : a) b.dev.release(nullptr);
   for (auto& a : F->gp)
     for (auto& b : a) b.dev.release(nullptr);
   delete F;
@@ -1088,7 +1086,7 @@ int bf_debug_wait_timeout(uint64_t limit_ns, void* stream) {
   int rc = wait_probe(limit_ns, s);
   if (rc != BF_ETIMEOUT) return rc;
   // the persistent apply's dependency wait, on a flag nothing sets
-  rc = flow_wait_probe(limit_ns, s);
+  rc = grouped_wait_probe(limit_ns, s);
   if (rc) return rc;
   rc = tc_status(true);
   if (rc == BF_OK) return fail(BF_EINTERNAL, "the apply's dependency wait did not give up");

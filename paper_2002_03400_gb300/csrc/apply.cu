@@ -317,9 +317,12 @@ int pick_inner_engine(Fact* F, int opC, int dtype, int64_t nrhs, bool overlap, c
   const int cls = nrhs_class(nrhs), eng = apply_engine();
   if (eng == 1 || eng == 2) return BF_OK;
   GroupedPlan& gp = F->gp[opC][dtype];
-  if (!overlap && (eng == 3 || (eng == 0 && F->fl[opC][dtype].pick[cls]))) {
-    BF_TRY(build_flow(F, opC, dtype, s));
-    if (F->fl[opC][dtype].ok) {
+  const int depth = grouped_depth() > 0   ? grouped_depth()
+                    : gp.tuned_depth > 0 ? gp.tuned_depth
+                                         : default_grouped_depth(F, dtype);
+  if (!overlap && (eng == 3 || (eng == 0 && gp.ppick[cls]))) {
+    BF_TRY(build_grouped(F, opC, dtype, depth, s));
+    if (gp.ok) {
       *out = 1;
       return BF_OK;
     }
@@ -327,9 +330,6 @@ int pick_inner_engine(Fact* F, int opC, int dtype, int64_t nrhs, bool overlap, c
   bool want = eng == 4 || (eng == 0 && gp.pick[cls]);
   if (eng == 0 && !gp.tuned[cls]) want = ++gp.untuned_uses >= GR_BUILD_AFTER;
   if (want) {
-    const int depth = grouped_depth() > 0   ? grouped_depth()
-                      : gp.tuned_depth > 0 ? gp.tuned_depth
-                                           : default_grouped_depth(F, dtype);
     BF_TRY(build_grouped(F, opC, dtype, depth, s));
     if (gp.ok && !(overlap && gp.runs.size() < 2)) *out = 2;
   }
@@ -391,7 +391,7 @@ int apply_fact(Fact* F, int op, int64_t nrhs, const void* x, int64_t ldx, void* 
   if (!flow && !grouped) BF_TRY(prepare_apply(F, opC, dtype, s));
   GroupedPlan& gp = F->gp[opC][dtype];
   const int64_t lvl = (grouped ? gp.level_rows_max : F->ap[opC][dtype].level_rows_max) * nrhs;
-  const size_t inner = flow ? flow_scratch_bytes(F->fl[opC][dtype], nrhs, dtype) : (size_t)(2 * lvl) * es;
+  const size_t inner = flow ? grouped_persist_scratch_bytes(gp, nrhs, dtype) : (size_t)(2 * lvl) * es;
   const size_t bytes = inner + ((direct_in ? 0 : in_rows * nrhs) + (direct_out ? 0 : out_rows * nrhs)) * es;
   DevBuf scratch;
   BF_TRY(scratch.alloc(&F->mem, bytes, s));
@@ -406,7 +406,7 @@ int apply_fact(Fact* F, int op, int64_t nrhs, const void* x, int64_t ldx, void* 
   if (!direct_in)
     rc = launch_gather_rows(id_in ? nullptr : perm_in, in_rows, nrhs, x, ldx, xt, in_rows, conj, dtype, s);
   if (rc == BF_OK)
-    rc = flow      ? run_flow(F, opC, dtype, nrhs, xt, yt, p, s)
+    rc = flow      ? run_grouped_persist(F, opC, dtype, nrhs, xt, yt, p, s)
          : grouped ? run_grouped(F, opC, dtype, nrhs, xt, yt, ping, pong, s)
                    : run_apply_stages(F, opC, dtype, nrhs, xt, ping, pong, yt, s);
   if (rc == BF_OK && !direct_out)
@@ -493,34 +493,24 @@ int tune_apply(Fact* F, int op, int dtype, int64_t nrhs, cudaStream_t s, float* 
     }
     if (!rc && best_cs > 0) fp.cs[cls] = best_cs;
   }
-  // the persistent apply, on its own scratch (x and y: the input and output
-  // rows of the stage scratch)
-  float flow_best = 1e30f;
-  if (!rc && apply_engine() != 1 && apply_engine() != 2) rc = build_flow(F, opC, dtype, s);
-  FlowPlan& fl = F->fl[opC][dtype];
-  if (!rc && apply_engine() != 1 && apply_engine() != 2 && fl.ok) {
-    DevBuf fs;
-    rc = fs.alloc(&F->mem, flow_scratch_bytes(fl, nrhs, dtype), s);
-    char* xs = p + 2 * lvl * es;
-    char* ys = xs + rows * nrhs * es;
-    if (!rc) rc = run_flow(F, opC, dtype, nrhs, xs, ys, fs.p, s);
-    if (!rc && cudaEventRecord(e[0], s) != cudaSuccess) rc = fail(BF_ECUDA, "event record failed");
-    for (int r = 0; r < 3 && !rc; ++r) rc = run_flow(F, opC, dtype, nrhs, xs, ys, fs.p, s);
-    if (!rc) note_sync();
-    if (!rc && (cudaEventRecord(e[1], s) != cudaSuccess || cudaEventSynchronize(e[1]) != cudaSuccess))
-      rc = fail(BF_ECUDA, "event timing failed");
-    float t = 0.f;
-    if (!rc && cudaEventElapsedTime(&t, e[0], e[1]) != cudaSuccess) rc = fail(BF_ECUDA, "event timing failed");
-    if (!rc) flow_best = t / 3.f;
-    if (!rc) rc = tc_status(true);   // a dependency wait that gave up (never expected)
-    fs.release(s);
-  }
-  // the grouped apply at each run depth, on its own level buffers; the
+  // the grouped apply at each run depth and slice width, as launches per
+  // run (own level buffers) and as one persistent launch (own scratch); the
   // plan keeps the fastest depth
-  float grouped_best = 1e30f;
+  float grouped_best = 1e30f, persist_best = 1e30f;
   GroupedPlan& gp = F->gp[opC][dtype];
-  if (!rc && (apply_engine() == 0 || apply_engine() == 4)) {
-    int best_depth = 0, best_cw = 0;
+  if (!rc && (apply_engine() == 0 || apply_engine() == 3 || apply_engine() == 4)) {
+    int best_depth = 0, best_cw = 0, pbest_depth = 0, pbest_cw = 0;
+    auto time3 = [&](auto&& run_once, float* best, int depth, int cw, int* bd, int* bc) {
+      rc = run_once();
+      if (!rc && cudaEventRecord(e[0], s) != cudaSuccess) rc = fail(BF_ECUDA, "event record failed");
+      for (int r = 0; r < 3 && !rc; ++r) rc = run_once();
+      if (!rc) note_sync();
+      if (!rc && (cudaEventRecord(e[1], s) != cudaSuccess || cudaEventSynchronize(e[1]) != cudaSuccess))
+        rc = fail(BF_ECUDA, "event timing failed");
+      float t = 0.f;
+      if (!rc && cudaEventElapsedTime(&t, e[0], e[1]) != cudaSuccess) rc = fail(BF_ECUDA, "event timing failed");
+      if (!rc && t / 3.f < *best) *best = t / 3.f, *bd = depth, *bc = cw;
+    };
     char* xs = p + 2 * lvl * es;
     char* ys = xs + rows * nrhs * es;
     for (int depth = 2; depth <= GR_MAXD && !rc; ++depth) {
@@ -530,38 +520,40 @@ int tune_apply(Fact* F, int op, int dtype, int64_t nrhs, cudaStream_t s, float* 
       rc = lb.alloc(&F->mem, (size_t)2 * gp.level_rows_max * nrhs * es, s);
       char* lp = (char*)lb.p;
       char* lq = lp + gp.level_rows_max * nrhs * es;
+      DevBuf ps;
+      if (!rc) rc = ps.alloc(&F->mem, grouped_persist_scratch_bytes(gp, nrhs, dtype), s);
       for (int cw = 16; cw <= 64 && !rc; cw *= 2) {
         if (cw > 16 && cw / 2 >= nrhs) break;   // wider slices than the columns change nothing
-        rc = run_grouped(F, opC, dtype, nrhs, xs, ys, lp, lq, s, cw);
-        if (!rc && cudaEventRecord(e[0], s) != cudaSuccess) rc = fail(BF_ECUDA, "event record failed");
-        for (int r = 0; r < 3 && !rc; ++r) rc = run_grouped(F, opC, dtype, nrhs, xs, ys, lp, lq, s, cw);
-        if (!rc) note_sync();
-        if (!rc && (cudaEventRecord(e[1], s) != cudaSuccess || cudaEventSynchronize(e[1]) != cudaSuccess))
-          rc = fail(BF_ECUDA, "event timing failed");
-        float t = 0.f;
-        if (!rc && cudaEventElapsedTime(&t, e[0], e[1]) != cudaSuccess) rc = fail(BF_ECUDA, "event timing failed");
-        if (!rc && t / 3.f < grouped_best) grouped_best = t / 3.f, best_depth = depth, best_cw = cw;
+        time3([&] { return run_grouped(F, opC, dtype, nrhs, xs, ys, lp, lq, s, cw); }, &grouped_best, depth, cw,
+              &best_depth, &best_cw);
+        if (!rc)
+          time3([&] { return run_grouped_persist(F, opC, dtype, nrhs, xs, ys, ps.p, s, cw); }, &persist_best, depth,
+                cw, &pbest_depth, &pbest_cw);
       }
+      if (!rc) rc = tc_status(true);   // a persistent wait that gave up (never expected)
+      ps.release(s);
       lb.release(s);
     }
-    if (!rc && best_depth > 0) {
-      rc = build_grouped(F, opC, dtype, best_depth, s);
-      gp.cw[cls] = (int16_t)best_cw;
-      gp.tuned_depth = best_depth;
+    const bool pw = persist_best < grouped_best;
+    const int bd = pw ? pbest_depth : best_depth, bc = pw ? pbest_cw : best_cw;
+    if (!rc && bd > 0) {
+      rc = build_grouped(F, opC, dtype, bd, s);
+      gp.cw[cls] = (int16_t)bc;
+      gp.tuned_depth = bd;
     }
   }
   // the fastest engine serves this class from now on
   if (!rc) {
-    const float best = std::min(std::min(total, fused_best), std::min(flow_best, grouped_best));
-    fl.pick[cls] = flow_best == best && best < total ? 1 : 0;
-    gp.pick[cls] = !fl.pick[cls] && grouped_best == best && best < total ? 1 : 0;
+    const float best = std::min(std::min(total, fused_best), std::min(persist_best, grouped_best));
+    gp.ppick[cls] = persist_best == best && best < total ? 1 : 0;
+    gp.pick[cls] = !gp.ppick[cls] && grouped_best == best && best < total ? 1 : 0;
     gp.tuned[cls] = 1;
-    if (fused_best < 1e30f) fp.engine[cls] = !fl.pick[cls] && !gp.pick[cls] && fused_best <= total ? 0 : 1;
+    if (fused_best < 1e30f) fp.engine[cls] = !gp.ppick[cls] && !gp.pick[cls] && fused_best <= total ? 0 : 1;
   }
   cudaEventDestroy(e[0]);
   cudaEventDestroy(e[1]);
   scratch.release(s);
-  if (ms) *ms = std::min(std::min(total, fused_best), std::min(flow_best, grouped_best));
+  if (ms) *ms = std::min(std::min(total, fused_best), std::min(persist_best, grouped_best));
   return rc;
 }
 
@@ -597,7 +589,8 @@ int applier_create(Fact* F, int op, int64_t nrhs, int dtype, Applier** out) {
   const int64_t lvl = rc ? 0
                          : (inner == 2 ? F->gp[A->opC][dtype].level_rows_max
                                        : F->ap[A->opC][dtype].level_rows_max) * nrhs;
-  const size_t inner_bytes = inner == 1 ? flow_scratch_bytes(F->fl[A->opC][dtype], nrhs, dtype) : (size_t)(2 * lvl) * es;
+  const size_t inner_bytes =
+      inner == 1 ? grouped_persist_scratch_bytes(F->gp[A->opC][dtype], nrhs, dtype) : (size_t)(2 * lvl) * es;
   if (!rc) rc = A->scratch.alloc(&F->mem, (size_t)(A->in_rows * nrhs + A->out_rows * nrhs) * es + inner_bytes, nullptr);
   if (!rc) {
     char* p = (char*)A->scratch.p;
@@ -609,7 +602,7 @@ int applier_create(Fact* F, int op, int64_t nrhs, int dtype, Applier** out) {
         cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
       rc = fail(BF_ECUDA, "graph capture could not start");
     } else {
-      rc = inner == 1   ? run_flow(F, A->opC, dtype, nrhs, A->xt, A->yt, ping, cs)
+      rc = inner == 1   ? run_grouped_persist(F, A->opC, dtype, nrhs, A->xt, A->yt, ping, cs)
            : inner == 2 ? run_grouped(F, A->opC, dtype, nrhs, A->xt, A->yt, ping, pong, cs)
                         : run_apply_stages(F, A->opC, dtype, nrhs, A->xt, ping, pong, A->yt, cs);
       cudaGraph_t g = nullptr;

@@ -274,20 +274,6 @@ struct FusedPlan {
   std::array<int, NRHS_CLASSES> engine{{-1, -1, -1, -1, -1, -1}};
 };
 
-// Persistent apply (one cooperative launch over all stages): the stage
-// lists with stacked, stage-private intermediates and each task's producers.
-struct FlowPlan {
-  bool built = false, ok = false;
-  DevBuf dev;                              // tasks | dep_ptr | dep_idx
-  const StageTask* d_tasks = nullptr;
-  const int32_t* d_dep_ptr = nullptr;
-  const int32_t* d_dep_idx = nullptr;
-  int ntasks = 0;
-  int64_t inter_rows = 0;                  // rows of the stacked intermediates
-  // per right-hand-side class: 1 when the tuner measured it fastest
-  std::array<int8_t, NRHS_CLASSES> pick{{0, 0, 0, 0, 0, 0}};
-};
-
 // Grouped apply: the stages in runs of up to GR_MAXD, one launch per run.
 // Within a run the tasks fall into groups (the connected components of
 // "reads the output of"); one CTA per (group, column slice) computes all of
@@ -330,6 +316,7 @@ struct GroupedRun {
   int64_t in_ld;                        // 0: row-major intermediates; > 0: column-major (x)
   int32_t fac_max, rows_max;            // largest staged-factor and row counts over the run's groups
   int32_t tasks_max, chunks_max;        // largest task and row-chunk counts over the run's groups
+  int64_t out_rows;                     // rows of the run's output (its last stage's level)
 };
 struct GroupedPlan {
   bool built = false, ok = false;
@@ -341,9 +328,13 @@ struct GroupedPlan {
   const GroupedSpan* d_spans = nullptr;
   const GroupedSeg* d_segs = nullptr;
   const int32_t* d_chunks = nullptr;    // (first row << 16) | task index within the group
+  const int32_t* d_dep_ptr = nullptr;   // persistent launch: the groups a group reads (CSR over groups)
+  const int32_t* d_dep_idx = nullptr;
+  int32_t ngroups = 0;
   int64_t level_rows_max = 0;           // rows of the largest run output (the two level buffers)
   std::array<int16_t, NRHS_CLASSES> cw{{0, 0, 0, 0, 0, 0}};   // tuned column-slice width (0: default)
   std::array<int8_t, NRHS_CLASSES> pick{{0, 0, 0, 0, 0, 0}};    // 1: the tuner measured it fastest
+  std::array<int8_t, NRHS_CLASSES> ppick{{0, 0, 0, 0, 0, 0}};   // 1: ... in one persistent launch
   std::array<int8_t, NRHS_CLASSES> tuned{{0, 0, 0, 0, 0, 0}};   // 1: the tuner has measured this class
   int tuned_depth = 0;                  // the depth the tuner measured fastest (0: none)
   int64_t untuned_uses = 0;             // applies that found no tuned choice (the plan is built from the
@@ -364,7 +355,6 @@ struct Fact {
   MemTracker mem;
   ApplyPlan ap[2][2];                // [op N / C][dtype C64 / C128]
   FusedPlan fp[2][2];                // fused apply, same indexing
-  FlowPlan fl[2][2];                 // persistent apply, same indexing
   GroupedPlan gp[2][2];              // grouped apply, same indexing
   int stage_V0() const { return 0; }
   int stage_W(int j) const { return j; }
@@ -405,14 +395,6 @@ bool plan_fused(const Fact* F, int opC, int dtype, FusedPlan& fp);
 int fused_slice_width(const FusedPlan& fp, int64_t nrhs, int dtype);
 int run_fused(Fact* F, int opC, int dtype, int64_t nrhs, const void* x, int64_t ldx, void* y, int64_t ldy, int conj,
               void* exch, cudaStream_t s, int cs_override = 0);
-// Persistent apply: builds F->fl[opC][dtype] once (ok false: not
-// applicable); run_flow computes y = op(F) x on tree-order x and y (no
-// conjugation) with scratch of flow_scratch_bytes.
-int build_flow(Fact* F, int opC, int dtype, cudaStream_t s);
-size_t flow_scratch_bytes(const FlowPlan& fl, int64_t nrhs, int dtype);
-int run_flow(Fact* F, int opC, int dtype, int64_t nrhs, const void* xt, void* yt, void* scratch, cudaStream_t s);
-// one bounded dependency wait on a flag nothing sets (sets the status flag)
-int flow_wait_probe(uint64_t limit_ns, cudaStream_t s);
 // Grouped apply: builds F->gp[opC][dtype] with runs of `depth` stages
 // (rebuilt when the depth changes; ok false: not applicable); run_grouped
 // computes y = op(F) x on tree-order x and y with two level buffers of
@@ -420,6 +402,16 @@ int flow_wait_probe(uint64_t limit_ns, cudaStream_t s);
 int build_grouped(Fact* F, int opC, int dtype, int depth, cudaStream_t s);
 int run_grouped(Fact* F, int opC, int dtype, int64_t nrhs, const void* xt, void* yt, void* ping, void* pong,
                 cudaStream_t s, int cw_override = 0);
+// The same runs in one cooperative launch: a (group, column slice) task
+// starts once the groups it reads have written their rows (per-task flags,
+// bounded waits); every run writes its own rows of scratch, which holds
+// grouped_persist_scratch_bytes.
+size_t grouped_persist_scratch_bytes(const GroupedPlan& gp, int64_t nrhs, int dtype);
+int run_grouped_persist(Fact* F, int opC, int dtype, int64_t nrhs, const void* xt, void* yt, void* scratch,
+                        cudaStream_t s, int cw_override = 0);
+// one bounded dependency wait of the persistent launch on a flag nothing
+// sets (sets the status flag)
+int grouped_wait_probe(uint64_t limit_ns, cudaStream_t s);
 // 0: the tuned depth (untuned: set by the largest block rank); 1 .. GR_MAXD:
 // that depth for every grouped apply
 int set_grouped_depth(int depth);

@@ -159,22 +159,66 @@ __device__ __forceinline__ void gr_term(const GroupedTerm& Q, const V* __restric
     }
   }
 }
+// ---- persistent launch: per-task flags and bounded waits ----
+__device__ __forceinline__ unsigned long long gr_now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ int gr_ld_acquire(const int32_t* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void gr_st_release(int32_t* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// true once *flag is set; false when the time limit passed or another CTA
+// has already given up (the status flag), so one failure ends every wait
+__device__ bool gr_wait_flag(const int32_t* flag, const int* status, unsigned long long limit_ns) {
+  if (gr_ld_acquire(flag)) return true;
+  const unsigned long long t0 = gr_now_ns();
+  for (unsigned it = 0;; ++it) {
+    if (gr_ld_acquire(flag)) return true;
+    if ((it & 15) == 15) {
+      if (gr_ld_acquire(status)) return false;
+      if (gr_now_ns() - t0 > limit_ns) return false;
+    }
+    __nanosleep(32);
+  }
+}
+
+// What a persistent task waits for: the tasks of the same column slice of
+// the groups it reads (dep_ptr / dep_idx index groups)
+struct GroupedWait {
+  const int32_t* dep_ptr;
+  const int32_t* dep_idx;
+  int32_t* flags;       // one per (group, slice) task, zero at launch
+  int* status;          // device status flag: set when a wait gave up
+  unsigned long long limit_ns;
+  int slices;
+};
 }  // namespace
 
-template <typename R, int NT>
-__device__ __forceinline__ void grouped_body(const GroupedArgs& a) {
+// One group of a run for one column slice.  PERSIST: inside the persistent
+// launch (task = the group's (group, slice) index): wait for the producer
+// tasks' flags where the plain launch waits for the previous grid, read the
+// producers' rows around L1 (another SM wrote them in this launch), release
+// this task's flag at the end; returns false when a wait gave up.
+template <typename R, int NT, bool PERSIST>
+__device__ __forceinline__ bool grouped_group(const GroupedArgs& a, int gi, int sl, const GroupedWait* w, int task) {
   using V = typename Cx<R>::V;
   extern __shared__ __align__(16) uint8_t gr_smem[];
   GroupedTask* __restrict__ stask = (GroupedTask*)gr_smem;
   int32_t* __restrict__ schunk = (int32_t*)(gr_smem + gr_align16((size_t)a.tasks_max * sizeof(GroupedTask)));
   V* __restrict__ fsm = (V*)((uint8_t*)schunk + gr_align16((size_t)a.chunks_max * 4));   // staged factor tiles
   V* __restrict__ rsm = fsm + a.fac_max;                                                 // rows, CW columns each
-  const GroupedGroup& G = a.groups[a.group0 + blockIdx.x];
+  const GroupedGroup& G = a.groups[gi];
   const int tid = threadIdx.x;
   const int CW = a.CW, N = a.N;
-  const int c0 = blockIdx.y * CW;
+  const int c0 = sl * CW;
   const int cw = min(CW, N - c0);
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  if constexpr (!PERSIST) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   // descriptors, row chunks and factor tiles: independent of the previous launch
   {
     const int nw = G.ntasks * (int)(sizeof(GroupedTask) / 8);
@@ -203,20 +247,43 @@ __device__ __forceinline__ void grouped_body(const GroupedArgs& a) {
     }
   }
   asm volatile("cp.async.commit_group;" ::: "memory");
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  // the group's input rows (region 0)
+  if constexpr (PERSIST) {
+    __shared__ int s_abort;
+    if (tid == 0) {
+      bool ok = true;
+      const int g = gi;
+      for (int q = w->dep_ptr[g]; q < w->dep_ptr[g + 1] && ok; ++q)
+        ok = gr_wait_flag(w->flags + (int64_t)w->dep_idx[q] * w->slices + sl, w->status, w->limit_ns);
+      if (!ok) atomicExch(w->status, 1);
+      s_abort = ok ? 0 : 1;
+    }
+    __syncthreads();
+    if (s_abort) {
+      asm volatile("cp.async.wait_all;" ::: "memory");
+      return false;
+    }
+  } else {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+  }
+  // the group's input rows (region 0); inside the persistent launch rows
+  // another SM wrote are read around L1
   const V* __restrict__ x = (const V*)a.x;
+  auto in_copy = [&](V* dst, const V* src) {
+    if constexpr (PERSIST && sizeof(V) == 8) *dst = __ldcg(src);
+    else if constexpr (PERSIST) gr_cp_async<16>(dst, src);
+    else gr_cp_async<sizeof(V)>(dst, src);
+  };
   for (int sp = 0; sp < G.nspans; ++sp) {
     const GroupedSpan S = a.spans[G.span0 + sp];
     if (a.in_ld == 0) {
       for (int e = tid; e < S.rows * cw; e += NT) {
         const int i = e / cw, c = e - i * cw;
-        gr_cp_async<sizeof(V)>(rsm + (int64_t)(S.l0 + i) * CW + c, x + (S.g0 + i) * N + c0 + c);
+        in_copy(rsm + (int64_t)(S.l0 + i) * CW + c, x + (S.g0 + i) * N + c0 + c);
       }
     } else {
       for (int e = tid; e < S.rows * cw; e += NT) {
         const int c = e / S.rows, i = e - c * S.rows;
-        gr_cp_async<sizeof(V)>(rsm + (int64_t)(S.l0 + i) * CW + c, x + (S.g0 + i) + (int64_t)(c0 + c) * a.in_ld);
+        in_copy(rsm + (int64_t)(S.l0 + i) * CW + c, x + (S.g0 + i) + (int64_t)(c0 + c) * a.in_ld);
       }
     }
   }
@@ -275,14 +342,58 @@ __device__ __forceinline__ void grouped_body(const GroupedArgs& a) {
     }
     __syncthreads();   // this stage's blocks are complete
   }
+  if constexpr (PERSIST) {
+    if (tid == 0) {
+      __threadfence();
+      gr_st_release(w->flags + task, 1);
+    }
+  }
+  return true;
 }
 
 // complex64 within 128 registers (no spills), 256 threads for slices of 64
 // columns and 128 for narrower ones; complex128 (FP64-bound) 256 threads at
 // the compiler's register choice.
-__global__ void __launch_bounds__(256, 2) grouped_kernel_c64_256(const GroupedArgs a) { grouped_body<float, 256>(a); }
-__global__ void __launch_bounds__(128, 4) grouped_kernel_c64_128(const GroupedArgs a) { grouped_body<float, 128>(a); }
-__global__ void __launch_bounds__(256) grouped_kernel_c128_256(const GroupedArgs a) { grouped_body<double, 256>(a); }
+__global__ void __launch_bounds__(256, 2) grouped_kernel_c64_256(const GroupedArgs a) {
+  grouped_group<float, 256, false>(a, a.group0 + blockIdx.x, blockIdx.y, nullptr, 0);
+}
+__global__ void __launch_bounds__(128, 4) grouped_kernel_c64_128(const GroupedArgs a) {
+  grouped_group<float, 128, false>(a, a.group0 + blockIdx.x, blockIdx.y, nullptr, 0);
+}
+__global__ void __launch_bounds__(256) grouped_kernel_c128_256(const GroupedArgs a) {
+  grouped_group<double, 256, false>(a, a.group0 + blockIdx.x, blockIdx.y, nullptr, 0);
+}
+
+// Persistent launch: every run's groups, task t = (group t / slices, slice
+// t % slices) in run order, CTA c taking tasks c, c + G, ... (all CTAs
+// resident: a cooperative launch, so the lowest unfinished task never
+// waits).  run_group0[r] is the first group of run r (nruns + 1 entries),
+// args[r] that run's arguments (one shared-memory layout for all runs).
+struct GroupedPersistArgs {
+  const GroupedArgs* args;
+  const int32_t* run_group0;
+  int nruns, ntasks;
+  GroupedWait w;
+};
+template <typename R, int NT>
+__device__ __forceinline__ void grouped_persist_body(const GroupedPersistArgs& p) {
+  for (int t = blockIdx.x; t < p.ntasks; t += gridDim.x) {
+    const int g = t / p.w.slices, sl = t - g * p.w.slices;
+    int r = 0;
+    while (r + 1 < p.nruns && g >= p.run_group0[r + 1]) ++r;
+    __syncthreads();   // the previous task's shared memory is free
+    if (!grouped_group<R, NT, true>(p.args[r], g, sl, &p.w, t)) return;
+  }
+}
+__global__ void __launch_bounds__(256, 2) grouped_persist_c64_256(const GroupedPersistArgs p) {
+  grouped_persist_body<float, 256>(p);
+}
+__global__ void __launch_bounds__(128, 4) grouped_persist_c64_128(const GroupedPersistArgs p) {
+  grouped_persist_body<float, 128>(p);
+}
+__global__ void __launch_bounds__(256) grouped_persist_c128_256(const GroupedPersistArgs p) {
+  grouped_persist_body<double, 256>(p);
+}
 
 // ------------------------------------------------------------------ host --
 namespace {
@@ -516,7 +627,7 @@ int build_grouped(Fact* F, int opC, int dtype, int depth, cudaStream_t s) {
   GroupedPlan& gp = F->gp[opC][dtype];
   if (gp.built && gp.depth == depth) return BF_OK;
   if (depth < 1 || depth > GR_MAXD) return fail(BF_EINVAL, "grouped apply depth must be 1 .. 4");
-  const auto pick = gp.pick, tuned = gp.tuned;
+  const auto pick = gp.pick, ppick = gp.ppick, tuned = gp.tuned;
   const auto cws = gp.cw;
   const int tuned_depth = gp.tuned_depth;
   const int64_t uses = gp.untuned_uses;
@@ -525,6 +636,7 @@ int build_grouped(Fact* F, int opC, int dtype, int depth, cudaStream_t s) {
   gp.built = true;
   gp.depth = depth;
   gp.pick = pick;
+  gp.ppick = ppick;
   gp.tuned = tuned;
   gp.cw = cws;
   gp.tuned_depth = tuned_depth;
@@ -580,21 +692,63 @@ int build_grouped(Fact* F, int opC, int dtype, int depth, cudaStream_t s) {
     run.in_ld = s0 == 0 ? in_ld0 : 0;
     const bool last = s0 + d == nst;
     run.out_base = last ? 3 : buf;
+    run.out_rows = 0;
+    for (int t = tmp.first[s0 + d - 1]; t < tmp.first[s0 + d - 1] + tmp.count[s0 + d - 1]; ++t)
+      run.out_rows = std::max(run.out_rows, all[t].out_off + all[t].M);
     if (!last) {
-      for (int t = tmp.first[s0 + d - 1]; t < tmp.first[s0 + d - 1] + tmp.count[s0 + d - 1]; ++t)
-        lvl_max = std::max(lvl_max, all[t].out_off + all[t].M);
+      lvl_max = std::max(lvl_max, run.out_rows);
       buf = 3 - buf;
     }
     gp.runs.push_back(run);
     s0 += d;
   }
   gp.level_rows_max = std::max<int64_t>(lvl_max, 1);
+  // persistent launch: a group of run r reads rows written by the last
+  // stage of run r - 1; its producers are the groups whose last-stage
+  // blocks meet one of its input spans
+  std::vector<int32_t> dep_ptr(T.groups.size() + 1, 0), dep_idx;
+  {
+    std::vector<int32_t> dg;
+    for (size_t r = 0; r < gp.runs.size(); ++r) {
+      const GroupedRun& run = gp.runs[r];
+      std::vector<std::pair<int64_t, std::pair<int64_t, int32_t>>> outs;   // (first row, (end, group))
+      if (r > 0) {
+        const GroupedRun& pr = gp.runs[r - 1];
+        for (int g = pr.group0; g < pr.group0 + pr.ngroups; ++g) {
+          const GroupedGroup& G = T.groups[g];
+          for (int t = G.task0; t < G.task0 + G.ntasks; ++t)
+            if (T.tasks[t].out_reg == 0) outs.push_back({T.tasks[t].out_row, {T.tasks[t].out_row + T.tasks[t].M, g}});
+        }
+        std::sort(outs.begin(), outs.end());
+      }
+      for (int g = run.group0; g < run.group0 + run.ngroups; ++g) {
+        dg.clear();
+        const GroupedGroup& G = T.groups[g];
+        for (int sp = G.span0; r > 0 && sp < G.span0 + G.nspans; ++sp) {
+          const int64_t lo = T.spans[sp].g0, hi = lo + T.spans[sp].rows;
+          // blocks are disjoint and sorted: the first that can meet [lo, hi)
+          auto it = std::upper_bound(outs.begin(), outs.end(), std::make_pair(lo, std::make_pair(INT64_MAX, INT32_MAX)));
+          if (it != outs.begin()) --it;
+          for (; it != outs.end() && it->first < hi; ++it)
+            if (it->second.first > lo) dg.push_back(it->second.second);
+        }
+        std::sort(dg.begin(), dg.end());
+        dg.erase(std::unique(dg.begin(), dg.end()), dg.end());
+        for (int32_t x : dg)
+          if (x >= g) return fail(BF_EINTERNAL, "grouped apply: a group depends on a later group");
+        dep_idx.insert(dep_idx.end(), dg.begin(), dg.end());
+        dep_ptr[g + 1] = (int32_t)dep_idx.size();
+      }
+    }
+  }
+  gp.ngroups = (int32_t)T.groups.size();
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const size_t b0 = T.groups.size() * sizeof(GroupedGroup), b1 = T.tasks.size() * sizeof(GroupedTask),
                b2 = std::max<size_t>(1, T.spans.size()) * sizeof(GroupedSpan),
                b3 = std::max<size_t>(1, T.segs.size()) * sizeof(GroupedSeg),
-               b4 = std::max<size_t>(1, T.chunks.size()) * sizeof(int32_t);
-  std::vector<char> host(al(b0) + al(b1) + al(b2) + al(b3) + b4, 0);
+               b4 = std::max<size_t>(1, T.chunks.size()) * sizeof(int32_t),
+               b5 = dep_ptr.size() * sizeof(int32_t), b6 = std::max<size_t>(1, dep_idx.size()) * sizeof(int32_t);
+  std::vector<char> host(al(b0) + al(b1) + al(b2) + al(b3) + al(b4) + al(b5) + b6, 0);
   memcpy(host.data(), T.groups.data(), b0);
   memcpy(host.data() + al(b0), T.tasks.data(), b1);
   if (!T.spans.empty()) memcpy(host.data() + al(b0) + al(b1), T.spans.data(), T.spans.size() * sizeof(GroupedSpan));
@@ -602,6 +756,9 @@ int build_grouped(Fact* F, int opC, int dtype, int depth, cudaStream_t s) {
     memcpy(host.data() + al(b0) + al(b1) + al(b2), T.segs.data(), T.segs.size() * sizeof(GroupedSeg));
   if (!T.chunks.empty())
     memcpy(host.data() + al(b0) + al(b1) + al(b2) + al(b3), T.chunks.data(), T.chunks.size() * sizeof(int32_t));
+  const size_t o5 = al(b0) + al(b1) + al(b2) + al(b3) + al(b4), o6 = o5 + al(b5);
+  memcpy(host.data() + o5, dep_ptr.data(), b5);
+  if (!dep_idx.empty()) memcpy(host.data() + o6, dep_idx.data(), dep_idx.size() * sizeof(int32_t));
   BF_TRY(gp.dev.alloc(&F->mem, host.size(), nullptr));
   BF_CUDA_TRY(cudaMemcpyAsync(gp.dev.p, host.data(), host.size(), cudaMemcpyHostToDevice, s));
   BF_CUDA_TRY(host_sync(s));
@@ -611,6 +768,8 @@ int build_grouped(Fact* F, int opC, int dtype, int depth, cudaStream_t s) {
   gp.d_spans = (const GroupedSpan*)(p + al(b0) + al(b1));
   gp.d_segs = (const GroupedSeg*)(p + al(b0) + al(b1) + al(b2));
   gp.d_chunks = (const int32_t*)(p + al(b0) + al(b1) + al(b2) + al(b3));
+  gp.d_dep_ptr = (const int32_t*)(p + o5);
+  gp.d_dep_idx = (const int32_t*)(p + o6);
   gp.ok = true;
   return BF_OK;
 }
@@ -681,6 +840,178 @@ int run_grouped(Fact* F, int opC, int dtype, int64_t nrhs, const void* xt, void*
     BF_CUDA_TRY(cudaGetLastError());
   }
   return BF_OK;
+}
+
+// ----------------------------------------------------- persistent launch --
+namespace {
+size_t gr_al256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// one column-slice width for every run: the widest (<= 64, or the tuned /
+// asked width) at which the largest layout fits
+int persist_cw(const GroupedPlan& gp, int64_t nrhs, int dtype, int cw_override, GroupedRun* layout) {
+  GroupedRun L{};
+  for (const GroupedRun& r : gp.runs) {
+    L.tasks_max = std::max(L.tasks_max, r.tasks_max);
+    L.chunks_max = std::max(L.chunks_max, r.chunks_max);
+    L.fac_max = std::max(L.fac_max, r.fac_max);
+    L.rows_max = std::max(L.rows_max, r.rows_max);
+  }
+  if (layout) *layout = L;
+  const size_t es = elem_bytes(dtype);
+  const int tuned = cw_override > 0 ? cw_override : gp.cw[nrhs_class(nrhs)];
+  int CW = (int)std::min<int64_t>(nrhs, tuned > 0 ? tuned : 64);
+  while (CW > 1 && grouped_smem(L, CW, es) > GR_SMEM_LIMIT) CW = (CW + 1) / 2;
+  return grouped_smem(L, CW, es) <= GR_SMEM_LIMIT ? CW : 0;
+}
+
+int launch_persist(const GroupedPersistArgs& pa, int dtype, int NT, size_t smem, cudaStream_t s) {
+  const void* k = dtype == BF_C128 ? (const void*)grouped_persist_c128_256
+                  : NT == 256      ? (const void*)grouped_persist_c64_256
+                                   : (const void*)grouped_persist_c64_128;
+  static std::once_flag attr_once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(attr_once, [&] {
+    const void* ks[3] = {(const void*)grouped_persist_c64_256, (const void*)grouped_persist_c64_128,
+                         (const void*)grouped_persist_c128_256};
+    for (int i = 0; i < 3 && attr_err == cudaSuccess; ++i)
+      attr_err = cudaFuncSetAttribute(ks[i], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GR_SMEM_LIMIT);
+  });
+  BF_CUDA_TRY(attr_err);
+  int dev = 0, sms = 0, per_sm = 0;
+  BF_CUDA_TRY(cudaGetDevice(&dev));
+  BF_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  BF_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NT, smem));
+  if (per_sm < 1) return fail(BF_ECUDA, "persistent apply: no CTA fits on an SM");
+  const int grid = std::max(1, std::min(pa.ntasks, per_sm * sms));   // all resident
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  note_launch();
+  cudaError_t e;
+  if (dtype == BF_C128) e = cudaLaunchKernelEx(&cfg, grouped_persist_c128_256, pa);
+  else if (NT == 256) e = cudaLaunchKernelEx(&cfg, grouped_persist_c64_256, pa);
+  else e = cudaLaunchKernelEx(&cfg, grouped_persist_c64_128, pa);
+  if (e != cudaSuccess) return fail(BF_ECUDA, std::string("persistent apply launch: ") + cudaGetErrorString(e));
+  BF_CUDA_TRY(cudaGetLastError());
+  return BF_OK;
+}
+}  // namespace
+
+// scratch: every run's output rows but the last (stacked), the task flags,
+// the per-run arguments and the runs' first groups
+size_t grouped_persist_scratch_bytes(const GroupedPlan& gp, int64_t nrhs, int dtype) {
+  int64_t rows = 0;
+  for (size_t r = 0; r + 1 < gp.runs.size(); ++r) rows += gp.runs[r].out_rows;
+  const size_t nr = gp.runs.size();
+  return gr_al256((size_t)rows * nrhs * elem_bytes(dtype)) + gr_al256((size_t)gp.ngroups * nrhs * 4) +
+         gr_al256(nr * sizeof(GroupedArgs)) + gr_al256((nr + 1) * 4);
+}
+
+int run_grouped_persist(Fact* F, int opC, int dtype, int64_t nrhs, const void* xt, void* yt, void* scratch,
+                        cudaStream_t s, int cw_override) {
+  const GroupedPlan& gp = F->gp[opC][dtype];
+  if (!gp.ok) return fail(BF_EINTERNAL, "grouped apply not built");
+  if (nrhs > INT32_MAX) return fail(BF_EINVAL, "too many right-hand sides");
+  GroupedRun L{};
+  const int CW = persist_cw(gp, nrhs, dtype, cw_override, &L);
+  if (CW < 1) return fail(BF_EINTERNAL, "persistent apply: a group does not fit");
+  const size_t es = elem_bytes(dtype);
+  const int slices = (int)((nrhs + CW - 1) / CW);
+  const int nruns = (int)gp.runs.size();
+  int64_t rows = 0;
+  for (int r = 0; r + 1 < nruns; ++r) rows += gp.runs[r].out_rows;
+  char* p = (char*)scratch;
+  char* inter = p;
+  int32_t* flags = (int32_t*)(p + gr_al256((size_t)rows * nrhs * es));
+  char* argp = (char*)flags + gr_al256((size_t)gp.ngroups * nrhs * 4);
+  int32_t* rg0 = (int32_t*)(argp + gr_al256(nruns * sizeof(GroupedArgs)));
+  std::vector<GroupedArgs> args(nruns);
+  std::vector<int32_t> g0(nruns + 1);
+  int64_t row0 = 0;
+  for (int r = 0; r < nruns; ++r) {
+    const GroupedRun& run = gp.runs[r];
+    GroupedArgs& a = args[r];
+    a.groups = gp.d_groups;
+    a.tasks = gp.d_tasks;
+    a.spans = gp.d_spans;
+    a.segs = gp.d_segs;
+    a.chunks = gp.d_chunks;
+    a.tasks_max = L.tasks_max;   // one layout for every run
+    a.chunks_max = L.chunks_max;
+    a.fac_max = L.fac_max;
+    a.group0 = run.group0;
+    a.N = (int)nrhs;
+    a.CW = CW;
+    // run r reads run r - 1's rows (x for the first) and writes its own (y for the last)
+    a.x = r == 0 ? xt : (const void*)(inter + (size_t)(row0 - gp.runs[r - 1].out_rows) * nrhs * es);
+    a.in_ld = run.in_ld;
+    a.y = r + 1 == nruns ? yt : (void*)(inter + (size_t)row0 * nrhs * es);
+    if (r + 1 < nruns) row0 += run.out_rows;
+    g0[r] = run.group0;
+  }
+  g0[nruns] = gp.ngroups;
+  BF_CUDA_TRY(cudaMemsetAsync(flags, 0, (size_t)gp.ngroups * slices * 4, s));
+  BF_TRY(upload_async(argp, args.data(), nruns * sizeof(GroupedArgs), s));
+  BF_TRY(upload_async(rg0, g0.data(), (nruns + 1) * sizeof(int32_t), s));
+  GroupedPersistArgs pa{};
+  pa.args = (const GroupedArgs*)argp;
+  pa.run_group0 = rg0;
+  pa.nruns = nruns;
+  pa.ntasks = gp.ngroups * slices;
+  pa.w.dep_ptr = gp.d_dep_ptr;
+  pa.w.dep_idx = gp.d_dep_idx;
+  pa.w.flags = flags;
+  pa.w.status = tc_status_ptr();
+  pa.w.limit_ns = 1000000000ull;
+  pa.w.slices = slices;
+  if (!pa.w.status) return fail(BF_ECUDA, "device status flag not found");
+  const int NT = CW > 32 || dtype == BF_C128 ? 256 : 128;
+  return launch_persist(pa, dtype, NT, grouped_smem(L, CW, es), s);
+}
+
+// One task whose group (empty: no rows, no tiles) depends on itself, so its
+// wait runs out after limit_ns, sets the status flag and the kernel returns.
+int grouped_wait_probe(uint64_t limit_ns, cudaStream_t s) {
+  DevBuf buf;
+  BF_TRY(buf.alloc(nullptr, 4096, s));
+  char* p = (char*)buf.p;
+  GroupedGroup G{};
+  const int32_t dep[3] = {0, 1, 0};   // dep_ptr {0, 1}, dep_idx {0}: the group reads itself
+  GroupedArgs a{};
+  a.groups = (const GroupedGroup*)p;
+  a.N = 1;
+  a.CW = 1;
+  int rc = BF_OK;
+  const int32_t g0[2] = {0, 1};
+  if (cudaMemsetAsync(p, 0, 4096, s) != cudaSuccess ||
+      cudaMemcpyAsync(p, &G, sizeof(G), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(p + 1024, dep, sizeof(dep), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(p + 2048, &a, sizeof(a), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(p + 3072, g0, sizeof(g0), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    rc = fail(BF_ECUDA, "probe set-up copy failed");
+  GroupedPersistArgs pa{};
+  pa.args = (const GroupedArgs*)(p + 2048);
+  pa.run_group0 = (const int32_t*)(p + 3072);
+  pa.nruns = 1;
+  pa.ntasks = 1;
+  pa.w.dep_ptr = (const int32_t*)(p + 1024);
+  pa.w.dep_idx = (const int32_t*)(p + 1024) + 2;
+  pa.w.flags = (int32_t*)(p + 1536);
+  pa.w.status = tc_status_ptr();
+  pa.w.limit_ns = limit_ns;
+  pa.w.slices = 1;
+  if (!rc && !pa.w.status) rc = fail(BF_ECUDA, "device status flag not found");
+  if (!rc) rc = launch_persist(pa, BF_C64, 128, grouped_smem(GroupedRun{}, 1, 8), s);
+  if (!rc && host_sync(s) != cudaSuccess) rc = fail(BF_ECUDA, "probe synchronisation failed");
+  buf.release(s);
+  return rc;
 }
 
 }  // namespace bf
