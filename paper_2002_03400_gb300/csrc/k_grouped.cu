@@ -59,12 +59,25 @@ __device__ __forceinline__ void gr_cp_async(void* dst, const void* src) {
 __host__ __device__ constexpr size_t gr_align16(size_t b) { return (b + 15) & ~(size_t)15; }
 static_assert(sizeof(GroupedTask) % 8 == 0, "task descriptors are copied in 8-byte words");
 
-// shared-memory bytes of one CTA: task descriptors, row chunks, staged
-// factor tiles, the rows of every region (CW columns each)
+// shared-memory layout of one CTA: task descriptors, tile and span
+// descriptors (a group has at most two of each per task: one per term),
+// row chunks, staged factor tiles, the rows of every region (CW columns
+// each)
+static_assert(sizeof(GroupedSeg) % 8 == 0 && sizeof(GroupedSpan) % 8 == 0 && sizeof(GroupedGroup) % 4 == 0,
+              "descriptors are copied in 8-byte (group header: 4-byte) words");
+__host__ __device__ constexpr size_t gr_off_segs(int tasks_max) {
+  return gr_align16((size_t)tasks_max * sizeof(GroupedTask));
+}
+__host__ __device__ constexpr size_t gr_off_spans(int tasks_max) {
+  return gr_off_segs(tasks_max) + gr_align16((size_t)2 * tasks_max * sizeof(GroupedSeg));
+}
+__host__ __device__ constexpr size_t gr_off_chunks(int tasks_max) {
+  return gr_off_spans(tasks_max) + gr_align16((size_t)2 * tasks_max * sizeof(GroupedSpan));
+}
 template <typename V>
 __host__ __device__ size_t gr_smem_bytes(int tasks_max, int chunks_max, int fac_max, int rows_max, int CW) {
-  return gr_align16((size_t)tasks_max * sizeof(GroupedTask)) + gr_align16((size_t)chunks_max * 4) +
-         (size_t)fac_max * sizeof(V) + (size_t)rows_max * CW * sizeof(V);
+  return gr_off_chunks(tasks_max) + gr_align16((size_t)chunks_max * 4) + (size_t)fac_max * sizeof(V) +
+         (size_t)rows_max * CW * sizeof(V);
 }
 
 template <typename V, bool CJ>
@@ -210,11 +223,28 @@ __device__ __forceinline__ bool grouped_group(const GroupedArgs& a, int gi, int 
   using V = typename Cx<R>::V;
   extern __shared__ __align__(16) uint8_t gr_smem[];
   GroupedTask* __restrict__ stask = (GroupedTask*)gr_smem;
-  int32_t* __restrict__ schunk = (int32_t*)(gr_smem + gr_align16((size_t)a.tasks_max * sizeof(GroupedTask)));
+  GroupedSeg* __restrict__ sseg = (GroupedSeg*)(gr_smem + gr_off_segs(a.tasks_max));
+  GroupedSpan* __restrict__ sspan = (GroupedSpan*)(gr_smem + gr_off_spans(a.tasks_max));
+  int32_t* __restrict__ schunk = (int32_t*)(gr_smem + gr_off_chunks(a.tasks_max));
   V* __restrict__ fsm = (V*)((uint8_t*)schunk + gr_align16((size_t)a.chunks_max * 4));   // staged factor tiles
   V* __restrict__ rsm = fsm + a.fac_max;                                                 // rows, CW columns each
-  const GroupedGroup& G = a.groups[gi];
+  __shared__ GroupedGroup sG;
+  const GroupedGroup& G = sG;
   const int tid = threadIdx.x;
+  // the group's header and descriptors, read in parallel (a loop that read
+  // each descriptor from global memory before issuing its copies would wait
+  // one memory round trip per descriptor)
+  {
+    const GroupedGroup& Gg = a.groups[gi];
+    constexpr int gw = (int)(sizeof(GroupedGroup) / 4);
+    if (tid < gw) ((int32_t*)&sG)[tid] = ((const int32_t*)&Gg)[tid];
+    const int nseg = Gg.nseg, nspans = Gg.nspans;
+    const uint2* s1 = (const uint2*)(a.segs + Gg.seg0);
+    for (int v = tid; v < nseg * (int)(sizeof(GroupedSeg) / 8); v += NT) ((uint2*)sseg)[v] = s1[v];
+    const uint2* s2 = (const uint2*)(a.spans + Gg.span0);
+    for (int v = tid; v < nspans * (int)(sizeof(GroupedSpan) / 8); v += NT) ((uint2*)sspan)[v] = s2[v];
+  }
+  __syncthreads();
   const int CW = a.CW, N = a.N;
   const int c0 = sl * CW;
   const int cw = min(CW, N - c0);
@@ -230,7 +260,7 @@ __device__ __forceinline__ bool grouped_group(const GroupedArgs& a, int gi, int 
   }
   // every thread copies a share of each tile (all copies in flight at once)
   for (int g = 0; g < G.nseg; ++g) {
-    const GroupedSeg sg = a.segs[G.seg0 + g];
+    const GroupedSeg sg = sseg[g];
     const V* src = (const V*)sg.src;
     V* dst = fsm + sg.dst;
     const int n = sg.M * sg.K;
@@ -274,7 +304,7 @@ __device__ __forceinline__ bool grouped_group(const GroupedArgs& a, int gi, int 
     else gr_cp_async<sizeof(V)>(dst, src);
   };
   for (int sp = 0; sp < G.nspans; ++sp) {
-    const GroupedSpan S = a.spans[G.span0 + sp];
+    const GroupedSpan S = sspan[sp];
     if (a.in_ld == 0) {
       for (int e = tid; e < S.rows * cw; e += NT) {
         const int i = e / cw, c = e - i * cw;
@@ -603,6 +633,8 @@ bool build_run(int dtype, const std::vector<StageTask>& all, const ApplyPlan& tm
     }
     G.fac_elems = (int32_t)fac;
     G.nseg = (int32_t)(T.segs.size() - seg0);
+    // the kernel's descriptor areas hold two of each per task
+    if (G.nseg > 2 * G.ntasks || G.nspans > 2 * G.ntasks) return false;
     T.groups.push_back(G);
     run.fac_max = std::max(run.fac_max, (int32_t)fac);
     run.rows_max = std::max(run.rows_max, G.reg_row[d]);
