@@ -27,6 +27,12 @@
  *   - Handles (bf_plan, bf_fact, bf_operator) are used by one host thread at
  *     a time; concurrent bf_apply calls on one bf_fact from different
  *     streams are allowed (factors are read-only after bf_factor returns).
+ *   - Debug checks: with BF_DEBUG=1 in the environment when the library
+ *     loads (or a build with -DBF_DEBUG), every block product's task list
+ *     is checked on the host before its launch -- every block offset inside
+ *     its buffer, ranks and term counts in range, factor entries inside
+ *     their block -- and a violation returns BF_EINTERNAL naming the task.
+ *     Results do not change.  Off by default (a few microseconds per list).
  *   - Memory: device memory is taken with cudaMallocAsync on the call's
  *     stream (or cudaMalloc) and is counted against bf_options.mem_cap;
  *     exceeding the cap returns BF_ENOMEM before any allocation.

@@ -12,6 +12,8 @@
 #include <system_error>
 #include <thread>
 
+#include <cstdlib>
+
 #include "bf_internal.h"
 
 namespace bf {
@@ -426,6 +428,17 @@ static std::atomic<unsigned long long> g_launches{0}, g_syncs{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 unsigned long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 void note_sync() { g_syncs.fetch_add(1, std::memory_order_relaxed); }
+bool debug_checks() {
+#ifdef BF_DEBUG
+  return true;
+#else
+  static const bool on = [] {
+    const char* v = std::getenv("BF_DEBUG");
+    return v && v[0] == '1';
+  }();
+  return on;
+#endif
+}
 unsigned long long syncs_so_far() { return g_syncs.load(std::memory_order_relaxed); }
 }  // namespace bf
 

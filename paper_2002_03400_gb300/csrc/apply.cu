@@ -241,11 +241,21 @@ void apply_tasks_host(const Fact* F, int opC, int dtype, ApplyPlan& ap, std::vec
   all.swap(B.all);
 }
 
+// Bounds of an apply's task lists for one column (the row-major level
+// buffers' rows scale with the column count, a column-major operand's rows
+// do not depend on it): x, the two level buffers, y.
+int check_apply_tasks(const Fact* F, int opC, int dtype, const ApplyPlan& ap, const std::vector<StageTask>& all) {
+  const Plan* P = F->plan;
+  const int64_t ext[4] = {opC ? P->m : P->n, ap.level_rows_max, ap.level_rows_max, opC ? P->n : P->m};
+  return check_stage_tasks("apply task list", all, 1, ext, F, dtype);
+}
+
 static int build_apply(Fact* F, int opC, int dtype, cudaStream_t s) {
   ApplyPlan& ap = F->ap[opC][dtype];
   ap = ApplyPlan();
   std::vector<StageTask> all;
   apply_tasks_host(F, opC, dtype, ap, all);
+  if (debug_checks()) BF_TRY(check_apply_tasks(F, opC, dtype, ap, all));
   BF_TRY(ap.tasks.alloc(&F->mem, all.size() * sizeof(StageTask), nullptr));
   BF_CUDA_TRY(cudaMemcpyAsync(ap.tasks.p, all.data(), all.size() * sizeof(StageTask),
                               cudaMemcpyHostToDevice, s));
@@ -261,6 +271,53 @@ int Fact::ensure32(cudaStream_t s) {
     BF_TRY(S.d32.alloc(&mem, S.total * 8, nullptr));
     BF_TRY(launch_convert(S.d64.p, S.d32.p, S.total, BF_C128, BF_C64, s));
     S.have32 = true;
+  }
+  return BF_OK;
+}
+
+int check_stage_tasks(const char* what, const std::vector<StageTask>& tasks, int64_t N, const int64_t ext[4],
+                      const Fact* F, int dtype) {
+  const size_t es = elem_bytes(dtype);
+  // first and last element an operand of `rows` rows and n columns touches
+  auto span = [](int64_t off, int64_t ld, int64_t rows, int64_t n, int64_t* lo, int64_t* hi) {
+    if (ld > 0) *lo = off, *hi = off + (rows - 1) + (n - 1) * ld;
+    else if (ld < 0) *lo = off, *hi = off + (rows - 1) * (-ld) + (n - 1);
+    else *lo = off * n, *hi = (off + rows - 1) * n + n - 1;
+  };
+  auto bad = [&](size_t i, const std::string& why) {
+    return fail(BF_EINTERNAL, std::string(what) + ": task " + std::to_string(i) + " " + why);
+  };
+  for (size_t i = 0; i < tasks.size(); ++i) {
+    const StageTask& t = tasks[i];
+    const int64_t n = N > 0 ? N : t.N;
+    if (t.M < 0 || t.nterms < 0 || t.nterms > 2 || n < 0) return bad(i, "has a negative size or too many terms");
+    if (t.M == 0 || n == 0) continue;
+    if (t.out_base < 0 || t.out_base > 3) return bad(i, "writes an unknown buffer");
+    int64_t lo, hi;
+    span(t.out_off, t.ldo, t.M, n, &lo, &hi);
+    if (lo < 0 || (ext[t.out_base] > 0 && hi >= ext[t.out_base]))
+      return bad(i, "writes outside buffer " + std::to_string(t.out_base));
+    for (int q = 0; q < t.nterms; ++q) {
+      const StageTerm& T = t.t[q];
+      if (T.K < 0 || T.in_base < 0 || T.in_base > 3) return bad(i, "has a bad term");
+      if (T.K == 0) continue;
+      span(T.in_off, T.ldi, T.K, n, &lo, &hi);
+      if (lo < 0 || (ext[T.in_base] > 0 && hi >= ext[T.in_base]))
+        return bad(i, "reads outside buffer " + std::to_string(T.in_base));
+      // entry (i, k) of op(mat): mat[i ldm + k] (adjoint) or mat[i + k ldm]
+      if (T.ldm < (T.conjT ? T.K : t.M)) return bad(i, "has a leading dimension below its block's");
+      if (!F) continue;
+      const int64_t last = T.conjT ? (int64_t)(t.M - 1) * T.ldm + T.K - 1 : (t.M - 1) + (int64_t)(T.K - 1) * T.ldm;
+      for (const Stage& S : F->st) {
+        const char* b = (const char*)(dtype == BF_C128 ? S.d64.p : S.d32.p);
+        if (!b || (const char*)T.mat < b || (const char*)T.mat >= b + S.total * (int64_t)es) continue;
+        const int64_t e = ((const char*)T.mat - b) / (int64_t)es;
+        const int blk = (int)(std::upper_bound(S.off.begin(), S.off.end(), e) - S.off.begin()) - 1;
+        if (blk < 0 || e + last >= S.off[blk] + (int64_t)S.rows[blk] * S.cols[blk])
+          return bad(i, "reads past its factor block");
+        break;
+      }
+    }
   }
   return BF_OK;
 }
@@ -388,6 +445,9 @@ int apply_fact(Fact* F, int op, int64_t nrhs, const void* x, int64_t ldx, void* 
   int engine = 0;
   BF_TRY(pick_inner_engine(F, opC, dtype, nrhs, overlap, s, &engine));
   const bool flow = engine == 1, grouped = engine == 2;
+  NvtxRange nv(flow ? "bf_apply: persistent launch, columns: %d" : grouped ? "bf_apply: grouped launches, columns: %d"
+                                                                          : "bf_apply: stage launches, columns: %d",
+               (int)std::min<int64_t>(nrhs, INT32_MAX));
   if (!flow && !grouped) BF_TRY(prepare_apply(F, opC, dtype, s));
   GroupedPlan& gp = F->gp[opC][dtype];
   const int64_t lvl = (grouped ? gp.level_rows_max : F->ap[opC][dtype].level_rows_max) * nrhs;
@@ -421,6 +481,7 @@ int apply_fact(Fact* F, int op, int64_t nrhs, const void* x, int64_t ldx, void* 
 // all data); the fastest variant per stage is kept for this right-hand-side
 // class.  Synchronises the stream.
 int tune_apply(Fact* F, int op, int dtype, int64_t nrhs, cudaStream_t s, float* ms) {
+  NvtxRange nv("bf_apply_tune, columns: %d", (int)std::min<int64_t>(nrhs, INT32_MAX));
   if (nrhs <= 0) return fail(BF_EINVAL, "nrhs must be positive");
   if (dtype != BF_C64 && dtype != BF_C128) return fail(BF_EINVAL, "dtype must be BF_C64 or BF_C128");
   if (op != BF_OP_N && op != BF_OP_T && op != BF_OP_C) return fail(BF_EINVAL, "bad op");
@@ -598,11 +659,14 @@ int applier_create(Fact* F, int op, int64_t nrhs, int dtype, Applier** out) {
     A->yt = p + A->in_rows * nrhs * es;
     char* ping = p + (A->in_rows + A->out_rows) * nrhs * es;
     char* pong = ping + lvl * es;
-    if (host_sync(cs) != cudaSuccess ||
-        cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    // the persistent launch's arguments name the applier's own buffers:
+    // uploaded once, before the capture
+    if (inner == 1) rc = run_grouped_persist(F, A->opC, dtype, nrhs, A->xt, A->yt, ping, cs, 0, 1);
+    if (!rc && (host_sync(cs) != cudaSuccess ||
+                cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess)) {
       rc = fail(BF_ECUDA, "graph capture could not start");
-    } else {
-      rc = inner == 1   ? run_grouped_persist(F, A->opC, dtype, nrhs, A->xt, A->yt, ping, cs)
+    } else if (!rc) {
+      rc = inner == 1   ? run_grouped_persist(F, A->opC, dtype, nrhs, A->xt, A->yt, ping, cs, 0, 2)
            : inner == 2 ? run_grouped(F, A->opC, dtype, nrhs, A->xt, A->yt, ping, pong, cs)
                         : run_apply_stages(F, A->opC, dtype, nrhs, A->xt, ping, pong, A->yt, cs);
       cudaGraph_t g = nullptr;

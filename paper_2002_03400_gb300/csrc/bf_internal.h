@@ -8,9 +8,30 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
+#include <cstdio>
+
 #include "../../include/butterfly.h"
 
 namespace bf {
+
+// A named NVTX range over one scope (Alg. 2's phases, an apply and its
+// engine, the tuner): profilers show them on the timeline; without a tool
+// attached a push or pop costs a few nanoseconds.  Ranges are per host
+// thread, so the two sides of a factorization nest separately.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  NvtxRange(const char* fmt, int v) {
+    char buf[64];
+    std::snprintf(buf, sizeof(buf), fmt, v);
+    nvtxRangePushA(buf);
+  }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 
 // ---------------------------------------------------------------- errors --
 void set_error(const std::string& msg);
@@ -407,8 +428,11 @@ int run_grouped(Fact* F, int opC, int dtype, int64_t nrhs, const void* xt, void*
 // bounded waits); every run writes its own rows of scratch, which holds
 // grouped_persist_scratch_bytes.
 size_t grouped_persist_scratch_bytes(const GroupedPlan& gp, int64_t nrhs, int dtype);
+// mode 0: upload the per-run arguments into scratch and launch; 1: upload
+// only; 2: launch on arguments uploaded before (a graph capture, whose
+// buffers never change, uploads once outside the capture)
 int run_grouped_persist(Fact* F, int opC, int dtype, int64_t nrhs, const void* xt, void* yt, void* scratch,
-                        cudaStream_t s, int cw_override = 0);
+                        cudaStream_t s, int cw_override = 0, int mode = 0);
 // one bounded dependency wait of the persistent launch on a flag nothing
 // sets (sets the status flag)
 int grouped_wait_probe(uint64_t limit_ns, cudaStream_t s);
@@ -571,6 +595,20 @@ bool entry_image_fits(const SketchJob& j);
 // images when they fit in device memory (default); 0: never
 int set_entry_images(int on);
 int entry_images_enabled();
+// Bounds checks of every stage task list before its launch: on when the
+// library is built with -DBF_DEBUG or when BF_DEBUG=1 is in the environment
+// as the library loads.
+bool debug_checks();
+// Every task's output rows and every term's input rows lie inside their
+// buffers (ext: elements of StageBases p[0..3], 0 = unknown, skipped) for a
+// launch of N columns (N <= 0: each task's own N), ranks and term counts are
+// in range, and a term whose entries lie in one of F's factor stages stays
+// inside its block; BF_EINTERNAL names the first task that breaks a bound.
+int check_stage_tasks(const char* what, const std::vector<struct StageTask>& tasks, int64_t N, const int64_t ext[4],
+                      const struct Fact* F, int dtype);
+// check_stage_tasks for an apply's lists (built by apply_tasks_host into ap)
+int check_apply_tasks(const struct Fact* F, int opC, int dtype, const struct ApplyPlan& ap,
+                      const std::vector<struct StageTask>& all);
 // counts one kernel launch of this library (bf_launch_count)
 void note_launch();
 unsigned long long launches_so_far();

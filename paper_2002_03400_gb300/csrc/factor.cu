@@ -112,8 +112,17 @@ void term(StageTask& t, int in_base, int64_t in_off, int64_t ldi, const void* ma
   T.conjT = (int16_t)conjT;
 }
 
-int run_tasks(Batch& B, const std::vector<StageTask>& tasks, const StageBases& bases) {
+// One stage launch of a phase's block products on bases {b0, b1, b2, b3}.
+int run_tasks(Batch& B, const std::vector<StageTask>& tasks, const Scratch& b0, const Scratch& b1,
+              const Scratch& b2, const Scratch& b3) {
   if (tasks.empty()) return BF_OK;
+  const StageBases bases{{b0.p(), b1.p(), b2.p(), b3.p()}};
+  if (debug_checks()) {
+    const int64_t es = (int64_t)B.es;
+    const int64_t ext[4] = {(int64_t)b0.b.bytes / es, (int64_t)b1.b.bytes / es, (int64_t)b2.b.bytes / es,
+                            (int64_t)b3.b.bytes / es};
+    BF_TRY(check_stage_tasks("factorization task list", tasks, 0, ext, nullptr, B.dt));
+  }
   Scratch d(B.s);
   BF_TRY(d.alloc(&B.mem, tasks.size() * sizeof(StageTask)));
   BF_TRY(upload_async(d.p(), tasks.data(), tasks.size() * sizeof(StageTask), B.s));
@@ -206,6 +215,7 @@ int sketch_all(Batch& B, const std::vector<SketchReq>& reqs) {
 // leaves (the rest is for the factorization); the others form entries on
 // the fly.
 int make_images(Batch& B) {
+  NvtxRange nv("entry images");
   if (B.dt != BF_C64 || !entry_images_enabled()) return BF_OK;
   size_t free_b = 0, total_b = 0;
   if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return BF_OK;
@@ -343,6 +353,7 @@ int qr_all(Batch& B, std::vector<QRJob>& jobs) {
 // Adaptive leaf loops (Alg. 2 loops "V" and "U") for all operators.  Vside:
 // Y = A^H Gamma_t, leaves of T_S; else Z = A Omega_s, leaves of T_T.
 int leaf_phase(Batch& B, bool Vside) {
+  NvtxRange nv(Vside ? "Alg. 2 leaf bases V0 (loop V)" : "Alg. 2 leaf bases UL (loop U)");
   for (auto& o : B.ops) {
     o.r = o.P->opt.r0;
     o.kcap = 0;
@@ -422,6 +433,7 @@ int leaf_phase(Batch& B, bool Vside) {
 
 // W^l for every operator with l_m >= t (l = t).
 int w_phase(Batch& B, int t) {
+  NvtxRange nv("Alg. 2 W step %d", t);
   std::vector<OpState*> act;
   for (auto& o : B.ops)
     if (o.lm >= t) act.push_back(&o);
@@ -521,8 +533,7 @@ int w_phase(Batch& B, int t) {
       o->prev.swap(o->cur);
       o->in_base = outb;
     }
-    StageBases bases{{Y.p(), SA.p(), SB.p(), Pb.p()}};
-    BF_TRY(run_tasks(B, tasks, bases));
+    BF_TRY(run_tasks(B, tasks, Y, SA, SB, Pb));
   }
   std::vector<QRJob> jobs;
   for (OpState* o : act) {
@@ -539,6 +550,7 @@ int w_phase(Batch& B, int t) {
 
 // R^l for every operator with L - t >= l_m (l = L - t); X and B at l_m.
 int r_phase(Batch& B, int t) {
+  NvtxRange nv("Alg. 2 R step %d (centre level at the last)", t);
   std::vector<OpState*> act;
   for (auto& o : B.ops)
     if (o.L - t >= o.lm) act.push_back(&o);
@@ -646,8 +658,7 @@ int r_phase(Batch& B, int t) {
       o->prev.swap(o->cur);
       o->in_base = outb;
     }
-    StageBases bases{{Z.p(), SA.p(), SB.p(), Pb.p()}};
-    BF_TRY(run_tasks(B, tasks, bases));
+    BF_TRY(run_tasks(B, tasks, Z, SA, SB, Pb));
   }
   std::vector<QRJob> jobs;
   for (OpState* o : act) {
@@ -711,8 +722,7 @@ int r_phase(Batch& B, int t) {
       o->prev.swap(o->cur);
       o->in_base = outb;
     }
-    StageBases bases{{G.p(), SA.p(), SB.p(), Xb.p()}};
-    BF_TRY(run_tasks(B, tasks, bases));
+    BF_TRY(run_tasks(B, tasks, G, SA, SB, Xb));
   }
   // B = argmin ||C - B X||_F, C = R^H P (eq. Bij)
   std::vector<LSQTask> lt;
@@ -935,6 +945,7 @@ void destroy(Fact* F) {
 }  // namespace
 
 int factor_batch(int count, Plan* const* P, Operator* const* A, cudaStream_t s, Fact** out) {
+  NvtxRange nv("bf_factor (Alg. 2), operators: %d", count);
   for (int i = 0; i < count; ++i) out[i] = nullptr;
   if (count < 1) return fail(BF_EINVAL, "empty batch");
   const int prec = P[0]->opt.precision;

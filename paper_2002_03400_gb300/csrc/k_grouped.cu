@@ -676,6 +676,7 @@ int build_grouped(Fact* F, int opC, int dtype, int depth, cudaStream_t s) {
   ApplyPlan tmp;
   std::vector<StageTask> all;
   apply_tasks_host(F, opC, dtype, tmp, all);
+  if (debug_checks()) BF_TRY(check_apply_tasks(F, opC, dtype, tmp, all));
   const int nst = (int)tmp.first.size();
   // the chain the runs rely on: stage 0 reads x (base 0), stage i > 0 reads
   // only stage i - 1's output buffer (row-major), the last stage writes y
@@ -947,7 +948,7 @@ size_t grouped_persist_scratch_bytes(const GroupedPlan& gp, int64_t nrhs, int dt
 }
 
 int run_grouped_persist(Fact* F, int opC, int dtype, int64_t nrhs, const void* xt, void* yt, void* scratch,
-                        cudaStream_t s, int cw_override) {
+                        cudaStream_t s, int cw_override, int mode) {
   const GroupedPlan& gp = F->gp[opC][dtype];
   if (!gp.ok) return fail(BF_EINTERNAL, "grouped apply not built");
   if (nrhs > INT32_MAX) return fail(BF_EINVAL, "too many right-hand sides");
@@ -989,9 +990,12 @@ int run_grouped_persist(Fact* F, int opC, int dtype, int64_t nrhs, const void* x
     g0[r] = run.group0;
   }
   g0[nruns] = gp.ngroups;
+  if (mode != 2) {   // the per-run arguments (this call's buffers)
+    BF_TRY(upload_async(argp, args.data(), nruns * sizeof(GroupedArgs), s));
+    BF_TRY(upload_async(rg0, g0.data(), (nruns + 1) * sizeof(int32_t), s));
+  }
+  if (mode == 1) return BF_OK;
   BF_CUDA_TRY(cudaMemsetAsync(flags, 0, (size_t)gp.ngroups * slices * 4, s));
-  BF_TRY(upload_async(argp, args.data(), nruns * sizeof(GroupedArgs), s));
-  BF_TRY(upload_async(rg0, g0.data(), (nruns + 1) * sizeof(int32_t), s));
   GroupedPersistArgs pa{};
   pa.args = (const GroupedArgs*)argp;
   pa.run_group0 = rg0;
