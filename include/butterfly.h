@@ -337,6 +337,19 @@ int bf_fact_import(bf_plan plan, const int32_t* rV, const int32_t* rU,
  * *bytes in: capacity of host_out, out: bytes written (or needed). */
 int bf_fact_export(bf_fact F, int stage, void* host_out, size_t* bytes);
 
+/* Checkpoint of a finished factorization (for restarting a server without
+ * refactoring; the paper has no counterpart).  bf_fact_save writes F's
+ * ranks, every stage's block shapes and entries (complex128, plus the
+ * complex64 copy where F has one, so that the reloaded factorization applies
+ * bit for bit as F does) and its black-box column counts to `path`;
+ * synchronizes the device.  bf_fact_load reads such a file for `plan` (the
+ * plan the factorization was built on, or one made with the same geometry
+ * and options): BF_EINVAL when the file does not match the plan's n, m, L
+ * and l_m, or is truncated or inconsistent; BF_ENOMEM, BF_ECUDA.  The file
+ * is native-endian and versioned. */
+int bf_fact_save(bf_fact F, const char* path);
+int bf_fact_load(bf_plan plan, const char* path, bf_fact* out);
+
 /* Sketch error of Sec. 7 (eq. error): ||A W - F W||_F / ||A W||_F with W a
  * complex Gaussian n x ncols test matrix drawn from the counter-based
  * generator (stream 5<<8, user-order rows); both products are computed in

@@ -79,6 +79,8 @@ def lib():
         "bf_fact_info": (i32, [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(dbl)]),
         "bf_fact_import": (i32, [vp, vp, vp, C.POINTER(vp), i32, C.POINTER(vp)]),
         "bf_fact_export": (i32, [vp, i32, vp, C.POINTER(C.c_size_t)]),
+        "bf_fact_save": (i32, [vp, C.c_char_p]),
+        "bf_fact_load": (i32, [vp, C.c_char_p, C.POINTER(vp)]),
         "bf_error": (i32, [vp, vp, i32, C.c_uint64, i32, vp, C.POINTER(dbl)]),
         "bf_free": (None, [vp]),
         "bf_set_sketch_engine": (i32, [i32]),
@@ -110,7 +112,7 @@ def exported_symbols():
             "bf_operator_dense", "bf_operator_kernel", "bf_operator_kernel_cached", "bf_operator_factored", "bf_operator_composed",
             "bf_operator_callback", "bf_operator_apply", "bf_operator_counts", "bf_factor",
             "bf_factor_batch", "bf_apply",
-            "bf_apply_T", "bf_apply_noalloc", "bf_ranks", "bf_fact_info", "bf_fact_import", "bf_fact_export", "bf_error",
+            "bf_apply_T", "bf_apply_noalloc", "bf_ranks", "bf_fact_info", "bf_fact_import", "bf_fact_export", "bf_fact_save", "bf_fact_load", "bf_error",
             "bf_free", "bf_gaussian", "bf_set_sketch_engine", "bf_set_entry_images", "bf_launch_count", "bf_apply_tune",
             "bf_applier_create", "bf_applier_run", "bf_fact_accept", "bf_debug_wait_timeout",
             "bf_set_apply_engine", "bf_set_stage_variant", "bf_set_grouped_depth", "bf_set_parallel_sides", "bf_sync_count"]
@@ -363,6 +365,17 @@ class Factorization(_Handle):
         F = cls(h, plan)
         F._op = A
         return F
+
+    def save(self, path: str):
+        """bf_fact_save: a checkpoint file of this factorization."""
+        check(lib().bf_fact_save(self._h, str(path).encode()))
+
+    @classmethod
+    def load(cls, plan: Plan, path: str):
+        """bf_fact_load: a factorization saved by save(), for `plan`."""
+        h = C.c_void_p()
+        check(lib().bf_fact_load(plan._h, str(path).encode(), C.byref(h)))
+        return cls(h, plan)
 
     @classmethod
     def factor_batch(cls, plans: list, ops: list | None = None, stream=None) -> list:

@@ -12,6 +12,7 @@
 #include <system_error>
 #include <thread>
 
+#include <cstdio>
 #include <cstdlib>
 
 #include "bf_internal.h"
@@ -1041,6 +1042,139 @@ int bf_fact_import(bf_plan plan, const int32_t* rV, const int32_t* rU, const voi
   if (rc) {
     for (auto& S : F->st) S.d64.release(nullptr);
     delete F;
+    return rc;
+  }
+  *out = new bf_fact_s{KIND_FACT, F};
+  return BF_OK;
+}
+
+// ---- checkpoint files: a factorization's ranks, block shapes and factor
+// entries (complex128, and the complex64 copy where it exists, so that a
+// reloaded factorization applies bit for bit as the saved one) ----
+namespace {
+struct FactFileHeader {
+  char magic[8];          // "BFFACT01"
+  int32_t version, L, lm, nstages, nb, have32;
+  int64_t n, m, cols_N, cols_T;
+  double seconds;
+};
+constexpr int FACT_FILE_VERSION = 1;
+
+struct FileCloser {
+  FILE* f;
+  ~FileCloser() {
+    if (f) std::fclose(f);
+  }
+};
+}  // namespace
+
+int bf_fact_save(bf_fact F, const char* path) {
+  auto* h = check<bf_fact_s>(F, KIND_FACT);
+  if (!h || !path) return fail(BF_EINVAL, "bad arguments");
+  Fact* f = h->impl;
+  const int nb = 1 << f->L;
+  bool have32 = true;
+  for (const Stage& S : f->st) have32 = have32 && S.have32;
+  FactFileHeader hd{};
+  std::memcpy(hd.magic, "BFFACT01", 8);
+  hd.version = FACT_FILE_VERSION;
+  hd.L = f->L;
+  hd.lm = f->lm;
+  hd.nstages = (int32_t)f->st.size();
+  hd.nb = nb;
+  hd.have32 = have32 ? 1 : 0;
+  hd.n = f->n;
+  hd.m = f->m;
+  hd.cols_N = f->cols_N;
+  hd.cols_T = f->cols_T;
+  hd.seconds = f->seconds;
+  FileCloser fc{std::fopen(path, "wb")};
+  if (!fc.f) return fail(BF_EINVAL, std::string("cannot open ") + path + " for writing");
+  bool ok = std::fwrite(&hd, sizeof(hd), 1, fc.f) == 1;
+  for (const auto& v : f->rV) ok = ok && std::fwrite(v.data(), 4, nb, fc.f) == (size_t)nb;
+  for (const auto& v : f->rU) ok = ok && std::fwrite(v.data(), 4, nb, fc.f) == (size_t)nb;
+  std::vector<char> buf;
+  for (const Stage& S : f->st) {
+    ok = ok && std::fwrite(S.rows.data(), 4, nb, fc.f) == (size_t)nb &&
+         std::fwrite(S.cols.data(), 4, nb, fc.f) == (size_t)nb && std::fwrite(S.off.data(), 8, nb, fc.f) == (size_t)nb &&
+         std::fwrite(&S.total, 8, 1, fc.f) == 1;
+    for (int w = 0; w < (have32 ? 2 : 1) && ok; ++w) {
+      const size_t bytes = (size_t)S.total * (w ? 8 : 16);
+      buf.resize(bytes);
+      note_sync();
+      if (bytes && cudaMemcpy(buf.data(), w ? S.d32.p : S.d64.p, bytes, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(BF_ECUDA, "copy of the factors to the host failed");
+      ok = std::fwrite(buf.data(), 1, bytes, fc.f) == bytes;
+    }
+  }
+  if (!ok) return fail(BF_EINVAL, std::string("write to ") + path + " failed");
+  return std::fclose(fc.f) == 0 ? (fc.f = nullptr, BF_OK) : (fc.f = nullptr, fail(BF_EINVAL, "close failed"));
+}
+
+int bf_fact_load(bf_plan plan, const char* path, bf_fact* out) {
+  if (!out) return fail(BF_EINVAL, "out is NULL");
+  *out = nullptr;
+  auto* hp = check<bf_plan_s>(plan, KIND_PLAN);
+  if (!hp || !path) return fail(BF_EINVAL, "bad arguments");
+  Plan* P = hp->impl;
+  FileCloser fc{std::fopen(path, "rb")};
+  if (!fc.f) return fail(BF_EINVAL, std::string("cannot open ") + path);
+  FactFileHeader hd{};
+  if (std::fread(&hd, sizeof(hd), 1, fc.f) != 1 || std::memcmp(hd.magic, "BFFACT01", 8) != 0 ||
+      hd.version != FACT_FILE_VERSION)
+    return fail(BF_EINVAL, std::string(path) + " is not a factorization file of this version");
+  if (hd.n != P->n || hd.m != P->m || hd.L != P->L || hd.lm != P->lm || hd.nb != (1 << P->L) ||
+      hd.nstages != P->L + 3)
+    return fail(BF_EINVAL, "the file's factorization does not match the plan (n, m, L or l_m)");
+  const int nb = hd.nb;
+  Fact* F = new Fact();
+  F->plan = P;
+  F->L = hd.L;
+  F->lm = hd.lm;
+  F->n = hd.n;
+  F->m = hd.m;
+  F->cols_N = hd.cols_N;
+  F->cols_T = hd.cols_T;
+  F->seconds = hd.seconds;
+  F->mem.cap = P->opt.mem_cap;
+  F->st.resize(hd.nstages);
+  F->rV.assign(hd.lm + 1, std::vector<int32_t>(nb));
+  F->rU.assign(hd.L - hd.lm + 1, std::vector<int32_t>(nb));
+  int rc = BF_OK;
+  bool ok = true;
+  for (auto& v : F->rV) ok = ok && std::fread(v.data(), 4, nb, fc.f) == (size_t)nb;
+  for (auto& v : F->rU) ok = ok && std::fread(v.data(), 4, nb, fc.f) == (size_t)nb;
+  std::vector<char> buf;
+  for (Stage& S : F->st) {
+    if (!ok || rc) break;
+    S.rows.resize(nb);
+    S.cols.resize(nb);
+    S.off.resize(nb);
+    ok = std::fread(S.rows.data(), 4, nb, fc.f) == (size_t)nb && std::fread(S.cols.data(), 4, nb, fc.f) == (size_t)nb &&
+         std::fread(S.off.data(), 8, nb, fc.f) == (size_t)nb && std::fread(&S.total, 8, 1, fc.f) == 1;
+    // blocks in order, inside the stage, not overlapping (a block may be
+    // laid out at a capacity above its final rank, leaving a gap)
+    int64_t end = 0;
+    for (int b = 0; ok && b < nb; ++b) {
+      ok = S.rows[b] >= 0 && S.cols[b] >= 0 && S.off[b] >= end;
+      end = S.off[b] + (int64_t)S.rows[b] * S.cols[b];
+    }
+    ok = ok && end <= S.total;
+    for (int w = 0; w < (hd.have32 ? 2 : 1) && ok && !rc; ++w) {
+      const size_t bytes = (size_t)S.total * (w ? 8 : 16);
+      buf.resize(bytes);
+      ok = std::fread(buf.data(), 1, bytes, fc.f) == bytes;
+      DevBuf& d = w ? S.d32 : S.d64;
+      if (ok) rc = d.alloc(&F->mem, bytes ? bytes : 16, nullptr);
+      if (ok && !rc) note_sync();
+      if (ok && !rc && bytes && cudaMemcpy(d.p, buf.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+        rc = fail(BF_ECUDA, "copy of the loaded factors failed");
+      if (w) S.have32 = true;
+    }
+  }
+  if (!rc && !ok) rc = fail(BF_EINVAL, std::string(path) + " is truncated or inconsistent");
+  if (rc) {
+    destroy_fact(F);
     return rc;
   }
   *out = new bf_fact_s{KIND_FACT, F};
