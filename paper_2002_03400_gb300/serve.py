@@ -11,7 +11,9 @@ factorizations (bf_factor of a kernel operator on some geometry).  The loop
   multi-right-hand-side bf_apply on the apply stream, so requests that arrive
   while earlier work is on the GPU join the next launch;
 * runs factorizations on worker threads, each with its own CUDA stream (the
-  library releases the interpreter lock), overlapping them with the applies;
+  library releases the interpreter lock), overlapping them with the applies,
+  which run on a high-priority stream so that they do not queue behind a
+  factorization's long launches;
 * completes requests through CUDA events and reports per-request latency
   (arrival to result on the host) with p50/p99 and throughput.
 
@@ -102,7 +104,10 @@ class Server:
         self.res_bytes: dict[str, int] = {}
         self.inflight_bytes = 0
         self.peak_inflight = 0
-        self.apply_stream = torch.cuda.Stream()
+        # applies on a high-priority stream: while a factorization's kernels
+        # hold the SMs, the block scheduler places an apply's CTAs first as
+        # SMs free up (priorities order scheduling only, never results)
+        self.apply_stream = torch.cuda.Stream(priority=-16)
         self.pool = cf.ThreadPoolExecutor(max_workers=factor_workers)
         self.worker_streams = {}
         self.lock = threading.Lock()
@@ -157,7 +162,7 @@ class Server:
         done: list[Job] = []
         i = 0
         while i < len(pending) or queue or futures or inflight:
-            time.sleep(0.0002)
+            time.sleep(0.00005)
             t = self.now()
             while i < len(pending) and (not realtime or pending[i].t_arrive <= t):
                 queue.append(pending[i])
@@ -226,12 +231,17 @@ class Server:
         F = self.resident[name]
         self.resident.move_to_end(name)
         tdt = torch.complex64 if dt == "c64" else torch.complex128
-        ndt = np.complex64 if dt == "c64" else np.complex128
-        # right-hand sides as rows of a pinned buffer: its transpose is the
-        # column-major n x ncols matrix the library takes
-        xT = np.concatenate([j.x.T for j in jobs], axis=0).astype(ndt, copy=False)
-        xh = torch.from_numpy(np.ascontiguousarray(xT)).pin_memory()
-        yh = torch.empty((xT.shape[0], F.m), dtype=tdt).pin_memory()
+        # right-hand sides as rows of a pinned buffer (its transpose is the
+        # column-major n x ncols matrix the library takes), each request's
+        # columns copied straight into it (one host copy; the pinned blocks
+        # come from torch's caching host allocator)
+        ncols = sum(j.x.shape[1] for j in jobs)
+        xh = torch.empty((ncols, F.n), dtype=tdt, pin_memory=True)
+        r0 = 0
+        for j in jobs:
+            xh[r0:r0 + j.x.shape[1]].numpy()[...] = j.x.T
+            r0 += j.x.shape[1]
+        yh = torch.empty((ncols, F.m), dtype=tdt, pin_memory=True)
         with torch.cuda.stream(self.apply_stream):
             xd = xh.to("cuda", non_blocking=True)
             yd = F.apply(xd.t(), stream=self.apply_stream)
