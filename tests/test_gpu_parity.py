@@ -84,6 +84,33 @@ def test_apply_exact_butterfly(n, leaf, r):
             assert np.linalg.norm(y32 - yo) <= 1e-5 * np.linalg.norm(yo)
 
 
+@pytest.mark.parametrize("engine", ["stages", "grouped-1", "grouped-2", "grouped-3", "grouped-4", "persistent",
+                                    "fused"])
+def test_every_apply_engine_matches_oracle(engine):
+    """Each apply engine against the oracle's apply of the same exact
+    butterfly (eq. hybrid_butterfly_mat), every op, both dtypes."""
+    n, leaf, r = 1024, 16, 6
+    eb = inputs.exact_butterfly(n, leaf, r, seed=4)
+    F = api.exact_factorization(api.Plan(n=n, leaf=leaf), eb)
+    Fo = ob.from_blocks(eb)
+    if engine.startswith("grouped"):
+        api.set_apply_engine("grouped")
+        api.set_grouped_depth(int(engine.split("-")[1]))
+    else:
+        api.set_apply_engine(engine)
+    try:
+        for nrhs in (1, 33, 70):
+            x = inputs.random_rhs(n, nrhs, seed=nrhs + 3)
+            for op in ("N", "T", "C"):
+                yo = ob.apply(Fo, x, op)
+                assert np.linalg.norm(H(F.apply(T(x), op)) - yo) <= 1e-13 * np.linalg.norm(yo), (engine, op)
+                y32 = H(F.apply(T(x, torch.complex64), op))
+                assert np.linalg.norm(y32 - yo) <= 1e-5 * np.linalg.norm(yo), (engine, op)
+    finally:
+        api.set_apply_engine("auto")
+        api.set_grouped_depth(0)
+
+
 def test_apply_strided_and_empty():
     n = 512
     eb = inputs.exact_butterfly(n, 16, 4, seed=2)
