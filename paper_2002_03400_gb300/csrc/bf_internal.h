@@ -318,37 +318,39 @@ struct GroupedSpan {        // global input rows [g0, g0 + rows) -> region-0 row
   int64_t g0;
   int32_t l0, rows;
 };
-struct GroupedSeg {         // one term's entries staged as a tile (entry (i, k) -> dst + k tld + i)
+struct GroupedSeg {         // one term's entries packed as a tile (entry (i, k) -> dst + (k tld + i) elements)
   const void* src;          // entry (i, k) at src[i ldm + k] when conj, else src[i + k ldm]
-  int32_t dst, M, K, ldm, tld, conj;
+  int64_t dst;              // byte offset in the group images
+  int32_t M, K, ldm, tld, conj, pad;
 };
 constexpr int GR_BUILD_AFTER = 3;     // untuned applies of (F, op, dtype) before the grouped engine takes over
 constexpr int GR_RB = 16;             // rows of a work item (a lane's register tile: up to GR_RB rows x 1 column)
-struct GroupedGroup {
-  int32_t task0, ntasks, span0, nspans, seg0, nseg, chunk0;
+struct GroupedGroup {                   // the head of a group's image
+  int32_t task0, ntasks, span0, nspans, seg0, nseg, chunk0;   // host tables (absolute indices)
   int32_t fac_elems;                    // staged factor elements (0: none staged)
   int32_t nst;                          // stages of this run
-  int32_t st_chunk[GR_MAXD + 1];        // row chunks of stage k: [chunk0 + st_chunk[k], chunk0 + st_chunk[k + 1])
+  int32_t st_chunk[GR_MAXD + 1];        // row chunks of stage k: [st_chunk[k], st_chunk[k + 1]) of the image's chunks
   int32_t reg_row[GR_MAXD + 1];         // region r: local rows [reg_row[r], reg_row[r + 1])
+  int32_t off_tasks, off_spans, off_chunks, off_fac;   // byte offsets of the image's parts
 };
+// A group's image -- the head, its task descriptors, input spans and row
+// chunks, then its factor tiles, 16-byte aligned parts -- is what the CTA
+// holds in shared memory; the images of a run sit at a fixed stride, so a
+// CTA copies its own with one coalesced pass and no descriptor read first.
 struct GroupedRun {
   int32_t group0, ngroups;
   int32_t in_base, out_base;            // StageBases indices
   int64_t in_ld;                        // 0: row-major intermediates; > 0: column-major (x)
-  int32_t fac_max, rows_max;            // largest staged-factor and row counts over the run's groups
-  int32_t tasks_max, chunks_max;        // largest task and row-chunk counts over the run's groups
+  int64_t img_off, img_stride;          // the run's first image (bytes into the images) and the stride
+  int32_t desc_max, rows_max;           // largest descriptor part (bytes) and row count over the run's groups
   int64_t out_rows;                     // rows of the run's output (its last stage's level)
 };
 struct GroupedPlan {
   bool built = false, ok = false;
   int depth = 0;                        // stages per run
-  DevBuf dev;                           // groups | tasks | spans | segs
+  DevBuf dev;                           // images | dependency lists | tile list (packing)
   std::vector<GroupedRun> runs;
-  const GroupedGroup* d_groups = nullptr;
-  const GroupedTask* d_tasks = nullptr;
-  const GroupedSpan* d_spans = nullptr;
-  const GroupedSeg* d_segs = nullptr;
-  const int32_t* d_chunks = nullptr;    // (first row << 16) | task index within the group
+  const uint8_t* d_img = nullptr;       // every run's group images
   const int32_t* d_dep_ptr = nullptr;   // persistent launch: the groups a group reads (CSR over groups)
   const int32_t* d_dep_idx = nullptr;
   int32_t ngroups = 0;

@@ -6,11 +6,13 @@
 // two children of a column-tree node; R^j and the adjoints likewise), so the
 // tasks of a few consecutive stages fall into small connected groups (for
 // the W levels with depth 3: 4 + 4 + 4 blocks whose inputs are 8 blocks of
-// the level below).  One CTA per (group, column slice):
-//   - copies the group's factor blocks into shared memory before waiting
-//     for the previous launch (they do not depend on it; programmatic
-//     dependent launch), then the group's input rows of the previous run's
-//     output (or of x);
+// the level below).  Each group has an image, built once per plan: its
+// descriptors and its factor blocks packed as tiles, contiguous and
+// 16-byte aligned.  One CTA per (group, column slice):
+//   - copies the group's image into shared memory in one coalesced pass
+//     while it waits for the previous launch (the image does not depend on
+//     it; programmatic dependent launch), then the group's input rows of the
+//     previous run's output (or of x);
 //   - computes the run's stages one after another, the inner stages' blocks
 //     in shared memory, and writes only the last stage's blocks to global
 //     memory (one of two level buffers, or y).
@@ -34,17 +36,13 @@ constexpr size_t GR_SMEM_LIMIT = 110 * 1024;   // two CTAs per SM
 constexpr size_t GR_FAC_LIMIT = 40 * 1024;     // staged factor bytes per group (more: read in place)
 
 struct GroupedArgs {
-  const GroupedGroup* groups;
-  const GroupedTask* tasks;
-  const GroupedSpan* spans;
-  const GroupedSeg* segs;
-  const int32_t* chunks;
+  const uint8_t* img;   // the run's group images: group (group0 + i) at img + i * stride bytes
+  int64_t stride;       // bytes per image (a multiple of 16); the rows follow it in shared memory
   int group0;           // the run's first group
   int N, CW;            // right-hand sides, column-slice width
   const void* x;        // the run's input (row-major N columns when in_ld == 0, else column-major)
   int64_t in_ld;
   void* y;              // the run's output base
-  int tasks_max, chunks_max, fac_max;   // shared-memory layout of the run
 };
 
 template <int BYTES>
@@ -57,27 +55,12 @@ __device__ __forceinline__ void gr_cp_async(void* dst, const void* src) {
 }
 
 __host__ __device__ constexpr size_t gr_align16(size_t b) { return (b + 15) & ~(size_t)15; }
-static_assert(sizeof(GroupedTask) % 8 == 0, "task descriptors are copied in 8-byte words");
+static_assert(sizeof(GroupedTask) % 8 == 0 && sizeof(GroupedSpan) % 8 == 0, "image parts keep 8-byte alignment");
 
-// shared-memory layout of one CTA: task descriptors, tile and span
-// descriptors (a group has at most two of each per task: one per term),
-// row chunks, staged factor tiles, the rows of every region (CW columns
-// each)
-static_assert(sizeof(GroupedSeg) % 8 == 0 && sizeof(GroupedSpan) % 8 == 0 && sizeof(GroupedGroup) % 4 == 0,
-              "descriptors are copied in 8-byte (group header: 4-byte) words");
-__host__ __device__ constexpr size_t gr_off_segs(int tasks_max) {
-  return gr_align16((size_t)tasks_max * sizeof(GroupedTask));
-}
-__host__ __device__ constexpr size_t gr_off_spans(int tasks_max) {
-  return gr_off_segs(tasks_max) + gr_align16((size_t)2 * tasks_max * sizeof(GroupedSeg));
-}
-__host__ __device__ constexpr size_t gr_off_chunks(int tasks_max) {
-  return gr_off_spans(tasks_max) + gr_align16((size_t)2 * tasks_max * sizeof(GroupedSpan));
-}
-template <typename V>
-__host__ __device__ size_t gr_smem_bytes(int tasks_max, int chunks_max, int fac_max, int rows_max, int CW) {
-  return gr_off_chunks(tasks_max) + gr_align16((size_t)chunks_max * 4) + (size_t)fac_max * sizeof(V) +
-         (size_t)rows_max * CW * sizeof(V);
+// shared memory of one CTA: the group's image, then the rows of every
+// region (CW columns each)
+inline size_t gr_smem_bytes(int64_t stride, int rows_max, int CW, size_t es) {
+  return (size_t)stride + (size_t)rows_max * CW * es;
 }
 
 template <typename V, bool CJ>
@@ -222,61 +205,19 @@ template <typename R, int NT, bool PERSIST>
 __device__ __forceinline__ bool grouped_group(const GroupedArgs& a, int gi, int sl, const GroupedWait* w, int task) {
   using V = typename Cx<R>::V;
   extern __shared__ __align__(16) uint8_t gr_smem[];
-  GroupedTask* __restrict__ stask = (GroupedTask*)gr_smem;
-  GroupedSeg* __restrict__ sseg = (GroupedSeg*)(gr_smem + gr_off_segs(a.tasks_max));
-  GroupedSpan* __restrict__ sspan = (GroupedSpan*)(gr_smem + gr_off_spans(a.tasks_max));
-  int32_t* __restrict__ schunk = (int32_t*)(gr_smem + gr_off_chunks(a.tasks_max));
-  V* __restrict__ fsm = (V*)((uint8_t*)schunk + gr_align16((size_t)a.chunks_max * 4));   // staged factor tiles
-  V* __restrict__ rsm = fsm + a.fac_max;                                                 // rows, CW columns each
-  __shared__ GroupedGroup sG;
-  const GroupedGroup& G = sG;
   const int tid = threadIdx.x;
-  // the group's header and descriptors, read in parallel (a loop that read
-  // each descriptor from global memory before issuing its copies would wait
-  // one memory round trip per descriptor)
+  // the group's image (head, task descriptors, spans, row chunks, factor
+  // tiles) in one coalesced pass of 16-byte copies; it does not depend on
+  // the previous launch, so it is in flight while this CTA waits for it
   {
-    const GroupedGroup& Gg = a.groups[gi];
-    constexpr int gw = (int)(sizeof(GroupedGroup) / 4);
-    if (tid < gw) ((int32_t*)&sG)[tid] = ((const int32_t*)&Gg)[tid];
-    const int nseg = Gg.nseg, nspans = Gg.nspans;
-    const uint2* s1 = (const uint2*)(a.segs + Gg.seg0);
-    for (int v = tid; v < nseg * (int)(sizeof(GroupedSeg) / 8); v += NT) ((uint2*)sseg)[v] = s1[v];
-    const uint2* s2 = (const uint2*)(a.spans + Gg.span0);
-    for (int v = tid; v < nspans * (int)(sizeof(GroupedSpan) / 8); v += NT) ((uint2*)sspan)[v] = s2[v];
+    const uint8_t* img = a.img + (int64_t)(gi - a.group0) * a.stride;
+    const int n16 = (int)(a.stride >> 4);
+    for (int v = tid; v < n16; v += NT) gr_cp_async<16>(gr_smem + 16 * v, img + 16 * v);
+    asm volatile("cp.async.commit_group;" ::: "memory");
   }
-  __syncthreads();
   const int CW = a.CW, N = a.N;
   const int c0 = sl * CW;
   const int cw = min(CW, N - c0);
-  if constexpr (!PERSIST) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  // descriptors, row chunks and factor tiles: independent of the previous launch
-  {
-    const int nw = G.ntasks * (int)(sizeof(GroupedTask) / 8);
-    const uint2* src = (const uint2*)(a.tasks + G.task0);
-    uint2* dst = (uint2*)stask;
-    for (int v = tid; v < nw; v += NT) dst[v] = src[v];
-    const int nc = G.st_chunk[G.nst];
-    for (int v = tid; v < nc; v += NT) schunk[v] = a.chunks[G.chunk0 + v];
-  }
-  // every thread copies a share of each tile (all copies in flight at once)
-  for (int g = 0; g < G.nseg; ++g) {
-    const GroupedSeg sg = sseg[g];
-    const V* src = (const V*)sg.src;
-    V* dst = fsm + sg.dst;
-    const int n = sg.M * sg.K;
-    if (sg.conj) {   // A^T's rows are A's columns: consecutive k are consecutive in memory
-      for (int e = tid; e < n; e += NT) {
-        const int i = e / sg.K, k = e - i * sg.K;
-        gr_cp_async<sizeof(V)>(dst + k * sg.tld + i, src + (int64_t)i * sg.ldm + k);
-      }
-    } else {
-      for (int e = tid; e < n; e += NT) {
-        const int k = e / sg.M, i = e - k * sg.M;
-        gr_cp_async<sizeof(V)>(dst + k * sg.tld + i, src + i + (int64_t)k * sg.ldm);
-      }
-    }
-  }
-  asm volatile("cp.async.commit_group;" ::: "memory");
   if constexpr (PERSIST) {
     __shared__ int s_abort;
     if (tid == 0) {
@@ -293,8 +234,17 @@ __device__ __forceinline__ bool grouped_group(const GroupedArgs& a, int gi, int 
       return false;
     }
   } else {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     asm volatile("griddepcontrol.wait;" ::: "memory");
   }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  __syncthreads();
+  const GroupedGroup& G = *(const GroupedGroup*)gr_smem;
+  const GroupedTask* __restrict__ stask = (const GroupedTask*)(gr_smem + G.off_tasks);
+  const GroupedSpan* __restrict__ sspan = (const GroupedSpan*)(gr_smem + G.off_spans);
+  const int32_t* __restrict__ schunk = (const int32_t*)(gr_smem + G.off_chunks);   // (first row << 16) | task
+  const V* __restrict__ fsm = (const V*)(gr_smem + G.off_fac);                      // staged factor tiles
+  V* __restrict__ rsm = (V*)(gr_smem + a.stride);                                   // rows, CW columns each
   // the group's input rows (region 0); inside the persistent launch rows
   // another SM wrote are read around L1
   const V* __restrict__ x = (const V*)a.x;
@@ -303,12 +253,26 @@ __device__ __forceinline__ bool grouped_group(const GroupedArgs& a, int gi, int 
     else if constexpr (PERSIST) gr_cp_async<16>(dst, src);
     else gr_cp_async<sizeof(V)>(dst, src);
   };
+  // row-major inputs: a row's cw columns to a group of lanes (16-byte
+  // units where rows and slice allow), the span rows round robin over the
+  // CTA's row slots in local-row order
+  constexpr int VPU = 16 / (int)sizeof(V);
+  const bool vec = N % VPU == 0 && CW % VPU == 0 && cw % VPU == 0;   // 16-byte copies bypass L1 (cg)
+  const int upr = vec ? cw / VPU : cw;
+  int lg = 0;
+  while ((1 << lg) < upr && lg < 5) ++lg;
+  const int rslots = (NT / 32) << (5 - lg);
+  const int rslot = ((tid >> 5) << (5 - lg)) + ((tid & 31) >> lg), u0 = tid & ((1 << lg) - 1);
   for (int sp = 0; sp < G.nspans; ++sp) {
     const GroupedSpan S = sspan[sp];
     if (a.in_ld == 0) {
-      for (int e = tid; e < S.rows * cw; e += NT) {
-        const int i = e / cw, c = e - i * cw;
-        in_copy(rsm + (int64_t)(S.l0 + i) * CW + c, x + (S.g0 + i) * N + c0 + c);
+      for (int i = (rslot - S.l0) & (rslots - 1); i < S.rows; i += rslots) {
+        V* d = rsm + (int64_t)(S.l0 + i) * CW;
+        const V* s = x + (S.g0 + i) * N + c0;
+        for (int u = u0; u < upr; u += 1 << lg) {
+          if (vec) gr_cp_async<16>(d + u * VPU, s + u * VPU);
+          else in_copy(d + u, s + u);
+        }
       }
     } else {
       for (int e = tid; e < S.rows * cw; e += NT) {
@@ -425,12 +389,37 @@ __global__ void __launch_bounds__(256) grouped_persist_c128_256(const GroupedPer
   grouped_persist_body<double, 256>(p);
 }
 
+// Packs each term's factor entries into its group's image (once per plan):
+// entry (i, k) of tile q at dst + (k tld + i) elements.
+__global__ void grouped_pack_kernel(const GroupedSeg* __restrict__ segs, int nseg, uint8_t* __restrict__ img,
+                                    int es) {
+  for (int q = blockIdx.x; q < nseg; q += gridDim.x) {
+    const GroupedSeg sg = segs[q];
+    const int n = sg.M * sg.K;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+      int i, k;
+      int64_t so;
+      if (sg.conj) {
+        i = e / sg.K;
+        k = e - i * sg.K;
+        so = (int64_t)i * sg.ldm + k;
+      } else {
+        k = e / sg.M;
+        i = e - k * sg.M;
+        so = i + (int64_t)k * sg.ldm;
+      }
+      uint8_t* d = img + sg.dst + ((int64_t)k * sg.tld + i) * es;
+      if (es == 16) *(double2*)d = ((const double2*)sg.src)[so];
+      else *(float2*)d = ((const float2*)sg.src)[so];
+    }
+  }
+}
+
 // ------------------------------------------------------------------ host --
 namespace {
 
 size_t grouped_smem(const GroupedRun& run, int CW, size_t es) {
-  return es == 16 ? gr_smem_bytes<double2>(run.tasks_max, run.chunks_max, run.fac_max, run.rows_max, CW)
-                  : gr_smem_bytes<float2>(run.tasks_max, run.chunks_max, run.fac_max, run.rows_max, CW);
+  return gr_smem_bytes(run.img_stride, run.rows_max, CW, es);
 }
 
 struct DSU {
@@ -535,10 +524,9 @@ bool build_run(int dtype, const std::vector<StageTask>& all, const ApplyPlan& tm
   }
   run.group0 = (int32_t)(base.groups.size());
   run.ngroups = ng;
-  run.fac_max = 0;
+  run.img_stride = 0;
+  run.desc_max = 0;
   run.rows_max = 0;
-  run.tasks_max = 0;
-  run.chunks_max = 0;
   RowMap reg[GR_MAXD];
   std::vector<std::pair<int64_t, int64_t>> v;
   for (int g = 0; g < ng; ++g) {
@@ -613,7 +601,8 @@ bool build_run(int dtype, const std::vector<StageTask>& all, const ApplyPlan& tm
           if (S.K > 0 && (lr < 0 || reg[k].at(S.in_off + S.K - 1) != lr + S.K - 1)) return false;
           Q.in_row = (int32_t)std::max<int64_t>(lr, 0);
           Q.fac_off = (int32_t)fac;
-          if (tk.M > 0 && S.K > 0) T.segs.push_back({S.mat, (int32_t)fac, tk.M, S.K, S.ldm, tld, S.conjT});
+          // (dst: the element offset in the group's tiles until the images are placed)
+          if (tk.M > 0 && S.K > 0) T.segs.push_back({S.mat, fac, tk.M, S.K, S.ldm, tld, S.conjT, 0});
           fac += (int64_t)S.K * tld;
         }
         const size_t li = T.tasks.size() - t0;
@@ -633,13 +622,21 @@ bool build_run(int dtype, const std::vector<StageTask>& all, const ApplyPlan& tm
     }
     G.fac_elems = (int32_t)fac;
     G.nseg = (int32_t)(T.segs.size() - seg0);
-    // the kernel's descriptor areas hold two of each per task
-    if (G.nseg > 2 * G.ntasks || G.nspans > 2 * G.ntasks) return false;
+    // the image: head, tasks, spans, chunks, tiles (16-byte aligned parts)
+    const size_t o_tasks = gr_align16(sizeof(GroupedGroup));
+    const size_t o_spans = o_tasks + gr_align16((size_t)G.ntasks * sizeof(GroupedTask));
+    const size_t o_chunks = o_spans + gr_align16((size_t)G.nspans * sizeof(GroupedSpan));
+    const size_t o_fac = o_chunks + gr_align16((size_t)G.st_chunk[d] * 4);
+    const size_t bytes = gr_align16(o_fac + (size_t)fac * es);
+    if (bytes > GR_SMEM_LIMIT) return false;
+    G.off_tasks = (int32_t)o_tasks;
+    G.off_spans = (int32_t)o_spans;
+    G.off_chunks = (int32_t)o_chunks;
+    G.off_fac = (int32_t)o_fac;
     T.groups.push_back(G);
-    run.fac_max = std::max(run.fac_max, (int32_t)fac);
+    run.img_stride = std::max<int64_t>(run.img_stride, (int64_t)bytes);
+    run.desc_max = std::max(run.desc_max, (int32_t)o_fac);
     run.rows_max = std::max(run.rows_max, G.reg_row[d]);
-    run.tasks_max = std::max(run.tasks_max, G.ntasks);
-    run.chunks_max = std::max(run.chunks_max, G.st_chunk[d]);
   }
   // the smallest slice width (8 columns) must fit
   return grouped_smem(run, 8, es) <= GR_SMEM_LIMIT;
@@ -775,34 +772,72 @@ int build_grouped(Fact* F, int opC, int dtype, int depth, cudaStream_t s) {
     }
   }
   gp.ngroups = (int32_t)T.groups.size();
+  // place the images: run r's groups at img_off + i * img_stride; each
+  // tile's destination becomes a byte offset into the images
+  int64_t img_bytes = 0;
+  for (GroupedRun& run : gp.runs) {
+    run.img_off = img_bytes;
+    img_bytes += (int64_t)run.ngroups * run.img_stride;
+  }
+  const size_t es = elem_bytes(dtype);
+  for (const GroupedRun& run : gp.runs)
+    for (int g = run.group0; g < run.group0 + run.ngroups; ++g) {
+      const GroupedGroup& G = T.groups[g];
+      const int64_t base = run.img_off + (int64_t)(g - run.group0) * run.img_stride + G.off_fac;
+      for (int q = G.seg0; q < G.seg0 + G.nseg; ++q) {
+        GroupedSeg& sg = T.segs[q];
+        // every tile inside its group's staged elements, every image inside its slot
+        if (sg.dst < 0 || sg.dst + (int64_t)sg.K * sg.tld > G.fac_elems ||
+            G.off_fac + (int64_t)G.fac_elems * (int64_t)es > run.img_stride)
+          return fail(BF_EINTERNAL, "grouped apply: a factor tile outside its image");
+        sg.dst = base + sg.dst * (int64_t)es;
+      }
+    }
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
-  const size_t b0 = T.groups.size() * sizeof(GroupedGroup), b1 = T.tasks.size() * sizeof(GroupedTask),
-               b2 = std::max<size_t>(1, T.spans.size()) * sizeof(GroupedSpan),
-               b3 = std::max<size_t>(1, T.segs.size()) * sizeof(GroupedSeg),
-               b4 = std::max<size_t>(1, T.chunks.size()) * sizeof(int32_t),
-               b5 = dep_ptr.size() * sizeof(int32_t), b6 = std::max<size_t>(1, dep_idx.size()) * sizeof(int32_t);
-  std::vector<char> host(al(b0) + al(b1) + al(b2) + al(b3) + al(b4) + al(b5) + b6, 0);
-  memcpy(host.data(), T.groups.data(), b0);
-  memcpy(host.data() + al(b0), T.tasks.data(), b1);
-  if (!T.spans.empty()) memcpy(host.data() + al(b0) + al(b1), T.spans.data(), T.spans.size() * sizeof(GroupedSpan));
-  if (!T.segs.empty())
-    memcpy(host.data() + al(b0) + al(b1) + al(b2), T.segs.data(), T.segs.size() * sizeof(GroupedSeg));
-  if (!T.chunks.empty())
-    memcpy(host.data() + al(b0) + al(b1) + al(b2) + al(b3), T.chunks.data(), T.chunks.size() * sizeof(int32_t));
-  const size_t o5 = al(b0) + al(b1) + al(b2) + al(b3) + al(b4), o6 = o5 + al(b5);
-  memcpy(host.data() + o5, dep_ptr.data(), b5);
-  if (!dep_idx.empty()) memcpy(host.data() + o6, dep_idx.data(), dep_idx.size() * sizeof(int32_t));
-  BF_TRY(gp.dev.alloc(&F->mem, host.size(), nullptr));
-  BF_CUDA_TRY(cudaMemcpyAsync(gp.dev.p, host.data(), host.size(), cudaMemcpyHostToDevice, s));
-  BF_CUDA_TRY(host_sync(s));
+  const size_t b0 = al((size_t)std::max<int64_t>(img_bytes, 16)), b1 = dep_ptr.size() * sizeof(int32_t),
+               b2 = std::max<size_t>(1, dep_idx.size()) * sizeof(int32_t),
+               b3 = std::max<size_t>(1, T.segs.size()) * sizeof(GroupedSeg);
+  std::vector<char> tail(al(b1) + al(b2) + b3, 0);
+  memcpy(tail.data(), dep_ptr.data(), b1);
+  if (!dep_idx.empty()) memcpy(tail.data() + al(b1), dep_idx.data(), dep_idx.size() * sizeof(int32_t));
+  if (!T.segs.empty()) memcpy(tail.data() + al(b1) + al(b2), T.segs.data(), T.segs.size() * sizeof(GroupedSeg));
+  // over the memory cap the plan stays unusable and the applies use the
+  // stage launches
+  const int arc = gp.dev.alloc(&F->mem, b0 + tail.size(), nullptr);
+  if (arc == BF_ENOMEM) return BF_OK;
+  BF_TRY(arc);
   char* p = (char*)gp.dev.p;
-  gp.d_groups = (const GroupedGroup*)p;
-  gp.d_tasks = (const GroupedTask*)(p + al(b0));
-  gp.d_spans = (const GroupedSpan*)(p + al(b0) + al(b1));
-  gp.d_segs = (const GroupedSeg*)(p + al(b0) + al(b1) + al(b2));
-  gp.d_chunks = (const int32_t*)(p + al(b0) + al(b1) + al(b2) + al(b3));
-  gp.d_dep_ptr = (const int32_t*)(p + o5);
-  gp.d_dep_idx = (const int32_t*)(p + o6);
+  BF_CUDA_TRY(cudaMemsetAsync(p, 0, b0, s));
+  BF_CUDA_TRY(cudaMemcpyAsync(p + b0, tail.data(), tail.size(), cudaMemcpyHostToDevice, s));
+  // the descriptor parts of each run's images (one strided copy per run),
+  // then the factor tiles packed on the device
+  std::vector<char> desc;
+  for (const GroupedRun& run : gp.runs) {
+    const size_t dm = (size_t)run.desc_max;
+    if (dm == 0 || run.ngroups == 0) continue;
+    desc.assign(dm * run.ngroups, 0);
+    for (int g = run.group0; g < run.group0 + run.ngroups; ++g) {
+      const GroupedGroup& G = T.groups[g];
+      char* d = desc.data() + (size_t)(g - run.group0) * dm;
+      memcpy(d, &G, sizeof(GroupedGroup));
+      if (G.ntasks) memcpy(d + G.off_tasks, &T.tasks[G.task0], (size_t)G.ntasks * sizeof(GroupedTask));
+      if (G.nspans) memcpy(d + G.off_spans, &T.spans[G.span0], (size_t)G.nspans * sizeof(GroupedSpan));
+      if (G.st_chunk[G.nst]) memcpy(d + G.off_chunks, &T.chunks[G.chunk0], (size_t)G.st_chunk[G.nst] * 4);
+    }
+    BF_CUDA_TRY(cudaMemcpy2DAsync(p + run.img_off, (size_t)run.img_stride, desc.data(), dm, dm,
+                                  (size_t)run.ngroups, cudaMemcpyHostToDevice, s));
+  }
+  if (!T.segs.empty()) {
+    const int grid = (int)std::min<size_t>(T.segs.size(), 4096);
+    note_launch();
+    grouped_pack_kernel<<<grid, 128, 0, s>>>((const GroupedSeg*)(p + b0 + al(b1) + al(b2)), (int)T.segs.size(),
+                                             (uint8_t*)p, (int)es);
+    BF_CUDA_TRY(cudaGetLastError());
+  }
+  BF_CUDA_TRY(host_sync(s));
+  gp.d_img = (const uint8_t*)p;
+  gp.d_dep_ptr = (const int32_t*)(p + b0);
+  gp.d_dep_idx = (const int32_t*)(p + b0 + al(b1));
   gp.ok = true;
   return BF_OK;
 }
@@ -824,20 +859,14 @@ int run_grouped(Fact* F, int opC, int dtype, int64_t nrhs, const void* xt, void*
     while (CW > 1 && bytes(CW) > GR_SMEM_LIMIT) CW = (CW + 1) / 2;
     if (bytes(CW) > GR_SMEM_LIMIT) return fail(BF_EINTERNAL, "grouped apply: a group does not fit");
     GroupedArgs a{};
-    a.groups = gp.d_groups;
-    a.tasks = gp.d_tasks;
-    a.spans = gp.d_spans;
-    a.segs = gp.d_segs;
-    a.chunks = gp.d_chunks;
-    a.tasks_max = run.tasks_max;
-    a.chunks_max = run.chunks_max;
+    a.img = gp.d_img + run.img_off;
+    a.stride = run.img_stride;
     a.group0 = run.group0;
     a.N = (int)nrhs;
     a.CW = CW;
     a.x = bases[run.in_base];
     a.in_ld = run.in_ld;
     a.y = bases[run.out_base];
-    a.fac_max = run.fac_max;
     const int slices = (int)((nrhs + CW - 1) / CW);
     // 256 threads (8 warps) for 64-column slices, 128 for narrower ones
     // (complex128: 256)
@@ -880,21 +909,20 @@ namespace {
 size_t gr_al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // one column-slice width for every run: the widest (<= 64, or the tuned /
-// asked width) at which the largest layout fits
-int persist_cw(const GroupedPlan& gp, int64_t nrhs, int dtype, int cw_override, GroupedRun* layout) {
-  GroupedRun L{};
-  for (const GroupedRun& r : gp.runs) {
-    L.tasks_max = std::max(L.tasks_max, r.tasks_max);
-    L.chunks_max = std::max(L.chunks_max, r.chunks_max);
-    L.fac_max = std::max(L.fac_max, r.fac_max);
-    L.rows_max = std::max(L.rows_max, r.rows_max);
-  }
-  if (layout) *layout = L;
+// asked width) at which every run's image and rows fit; *smem: the largest
+// run's shared memory at that width
+int persist_cw(const GroupedPlan& gp, int64_t nrhs, int dtype, int cw_override, size_t* smem) {
   const size_t es = elem_bytes(dtype);
+  auto bytes = [&](int cw) {
+    size_t b = 0;
+    for (const GroupedRun& r : gp.runs) b = std::max(b, grouped_smem(r, cw, es));
+    return b;
+  };
   const int tuned = cw_override > 0 ? cw_override : gp.cw[nrhs_class(nrhs)];
   int CW = (int)std::min<int64_t>(nrhs, tuned > 0 ? tuned : 64);
-  while (CW > 1 && grouped_smem(L, CW, es) > GR_SMEM_LIMIT) CW = (CW + 1) / 2;
-  return grouped_smem(L, CW, es) <= GR_SMEM_LIMIT ? CW : 0;
+  while (CW > 1 && bytes(CW) > GR_SMEM_LIMIT) CW = (CW + 1) / 2;
+  if (smem) *smem = bytes(CW);
+  return bytes(CW) <= GR_SMEM_LIMIT ? CW : 0;
 }
 
 int launch_persist(const GroupedPersistArgs& pa, int dtype, int NT, size_t smem, cudaStream_t s) {
@@ -952,8 +980,8 @@ int run_grouped_persist(Fact* F, int opC, int dtype, int64_t nrhs, const void* x
   const GroupedPlan& gp = F->gp[opC][dtype];
   if (!gp.ok) return fail(BF_EINTERNAL, "grouped apply not built");
   if (nrhs > INT32_MAX) return fail(BF_EINVAL, "too many right-hand sides");
-  GroupedRun L{};
-  const int CW = persist_cw(gp, nrhs, dtype, cw_override, &L);
+  size_t smem = 0;
+  const int CW = persist_cw(gp, nrhs, dtype, cw_override, &smem);
   if (CW < 1) return fail(BF_EINTERNAL, "persistent apply: a group does not fit");
   const size_t es = elem_bytes(dtype);
   const int slices = (int)((nrhs + CW - 1) / CW);
@@ -971,14 +999,8 @@ int run_grouped_persist(Fact* F, int opC, int dtype, int64_t nrhs, const void* x
   for (int r = 0; r < nruns; ++r) {
     const GroupedRun& run = gp.runs[r];
     GroupedArgs& a = args[r];
-    a.groups = gp.d_groups;
-    a.tasks = gp.d_tasks;
-    a.spans = gp.d_spans;
-    a.segs = gp.d_segs;
-    a.chunks = gp.d_chunks;
-    a.tasks_max = L.tasks_max;   // one layout for every run
-    a.chunks_max = L.chunks_max;
-    a.fac_max = L.fac_max;
+    a.img = gp.d_img + run.img_off;
+    a.stride = run.img_stride;
     a.group0 = run.group0;
     a.N = (int)nrhs;
     a.CW = CW;
@@ -1009,7 +1031,7 @@ int run_grouped_persist(Fact* F, int opC, int dtype, int64_t nrhs, const void* x
   pa.w.slices = slices;
   if (!pa.w.status) return fail(BF_ECUDA, "device status flag not found");
   const int NT = CW > 32 || dtype == BF_C128 ? 256 : 128;
-  return launch_persist(pa, dtype, NT, grouped_smem(L, CW, es), s);
+  return launch_persist(pa, dtype, NT, smem, s);
 }
 
 // One task whose group (empty: no rows, no tiles) depends on itself, so its
@@ -1021,7 +1043,8 @@ int grouped_wait_probe(uint64_t limit_ns, cudaStream_t s) {
   GroupedGroup G{};
   const int32_t dep[3] = {0, 1, 0};   // dep_ptr {0, 1}, dep_idx {0}: the group reads itself
   GroupedArgs a{};
-  a.groups = (const GroupedGroup*)p;
+  a.img = (const uint8_t*)p;           // one image: the empty head
+  a.stride = (int64_t)gr_align16(sizeof(GroupedGroup));
   a.N = 1;
   a.CW = 1;
   int rc = BF_OK;
@@ -1044,7 +1067,7 @@ int grouped_wait_probe(uint64_t limit_ns, cudaStream_t s) {
   pa.w.limit_ns = limit_ns;
   pa.w.slices = 1;
   if (!rc && !pa.w.status) rc = fail(BF_ECUDA, "device status flag not found");
-  if (!rc) rc = launch_persist(pa, BF_C64, 128, grouped_smem(GroupedRun{}, 1, 8), s);
+  if (!rc) rc = launch_persist(pa, BF_C64, 128, gr_smem_bytes(a.stride, 0, 1, 8), s);
   if (!rc && host_sync(s) != cudaSuccess) rc = fail(BF_ECUDA, "probe synchronisation failed");
   buf.release(s);
   return rc;
