@@ -418,11 +418,16 @@ int bf_debug_wait_timeout(uint64_t limit_ns, void* stream);
  *   - grouped: the stages in runs of 1-4 consecutive stages, one launch
  *     per run; the blocks of a run fall into small connected groups (for
  *     the W levels and depth 3: 4 + 4 + 4 blocks reading 8 blocks of the
- *     level below), one CTA per (group, column slice) stages the group's
- *     factor blocks (before waiting for the previous launch) and input
- *     rows in shared memory and computes the run's inner stages there;
- *     ceil((L + 3) / depth) launches, results equal to the stage engine's
- *     bit for bit; the tuner picks the depth.
+ *     level below; complex64 groups with fewer last-stage blocks merged up
+ *     to 4), one CTA per (group, column slice) copies the group's image --
+ *     its descriptors and factor blocks, packed once per plan -- while it
+ *     waits for the previous launch, then its input rows, and computes the
+ *     run's inner stages in shared memory; ceil((L + 3) / depth) launches,
+ *     results equal to the stage engine's bit for bit; the tuner picks the
+ *     depth, the merging and the slice width.  The plan's images hold a
+ *     packed copy of the factor entries of the direction and dtype plus
+ *     descriptors; over mem_cap the plan is not built and the stage
+ *     launches serve.
  * engine 0 (default): the engine bf_apply_tune measured fastest for the
  * right-hand-side class; untuned, the stage launches for the first two
  * applies of a factorization in each direction and dtype, then grouped

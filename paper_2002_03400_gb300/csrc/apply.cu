@@ -554,14 +554,16 @@ int tune_apply(Fact* F, int op, int dtype, int64_t nrhs, cudaStream_t s, float* 
     }
     if (!rc && best_cs > 0) fp.cs[cls] = best_cs;
   }
-  // the grouped apply at each run depth and slice width, as launches per
-  // run (own level buffers) and as one persistent launch (own scratch); the
-  // plan keeps the fastest depth
+  // the grouped apply at each run depth, group merging (complex64: merged
+  // up to GR_MERGE_MIN last-stage blocks, or not) and slice width, as
+  // launches per run (own level buffers) and as one persistent launch (own
+  // scratch); the plan keeps the fastest depth and merging
   float grouped_best = 1e30f, persist_best = 1e30f;
   GroupedPlan& gp = F->gp[opC][dtype];
   if (!rc && (apply_engine() == 0 || apply_engine() == 3 || apply_engine() == 4)) {
-    int best_depth = 0, best_cw = 0, pbest_depth = 0, pbest_cw = 0;
-    auto time3 = [&](auto&& run_once, float* best, int depth, int cw, int* bd, int* bc) {
+    // tags: depth * 8 + merge
+    int best_tag = 0, best_cw = 0, pbest_tag = 0, pbest_cw = 0;
+    auto time3 = [&](auto&& run_once, float* best, int tag, int cw, int* bt, int* bc) {
       rc = run_once();
       if (!rc && cudaEventRecord(e[0], s) != cudaSuccess) rc = fail(BF_ECUDA, "event record failed");
       for (int r = 0; r < 3 && !rc; ++r) rc = run_once();
@@ -570,13 +572,18 @@ int tune_apply(Fact* F, int op, int dtype, int64_t nrhs, cudaStream_t s, float* 
         rc = fail(BF_ECUDA, "event timing failed");
       float t = 0.f;
       if (!rc && cudaEventElapsedTime(&t, e[0], e[1]) != cudaSuccess) rc = fail(BF_ECUDA, "event timing failed");
-      if (!rc && t / 3.f < *best) *best = t / 3.f, *bd = depth, *bc = cw;
+      if (!rc && t / 3.f < *best) *best = t / 3.f, *bt = tag, *bc = cw;
     };
     char* xs = p + 2 * lvl * es;
     char* ys = xs + rows * nrhs * es;
-    for (int depth = 2; depth <= GR_MAXD && !rc; ++depth) {
-      rc = build_grouped(F, opC, dtype, depth, s);
-      if (rc || !gp.ok) break;
+    const int merges[2] = {dtype == BF_C64 ? GR_MERGE_MIN : 1, 1};
+    for (int v = 0; v < 2 * (GR_MAXD - 1) && !rc; ++v) {
+      const int depth = 2 + v / 2, merge = merges[v % 2];
+      if (v % 2 == 1 && merge == merges[0]) continue;   // complex128: no merged variant
+      rc = build_grouped(F, opC, dtype, depth, s, merge);
+      if (rc) break;
+      if (!gp.ok) continue;
+      const int tag = depth * 8 + merge;
       DevBuf lb;
       rc = lb.alloc(&F->mem, (size_t)2 * gp.level_rows_max * nrhs * es, s);
       char* lp = (char*)lb.p;
@@ -585,22 +592,23 @@ int tune_apply(Fact* F, int op, int dtype, int64_t nrhs, cudaStream_t s, float* 
       if (!rc) rc = ps.alloc(&F->mem, grouped_persist_scratch_bytes(gp, nrhs, dtype), s);
       for (int cw = 16; cw <= 64 && !rc; cw *= 2) {
         if (cw > 16 && cw / 2 >= nrhs) break;   // wider slices than the columns change nothing
-        time3([&] { return run_grouped(F, opC, dtype, nrhs, xs, ys, lp, lq, s, cw); }, &grouped_best, depth, cw,
-              &best_depth, &best_cw);
+        time3([&] { return run_grouped(F, opC, dtype, nrhs, xs, ys, lp, lq, s, cw); }, &grouped_best, tag, cw,
+              &best_tag, &best_cw);
         if (!rc)
-          time3([&] { return run_grouped_persist(F, opC, dtype, nrhs, xs, ys, ps.p, s, cw); }, &persist_best, depth,
-                cw, &pbest_depth, &pbest_cw);
+          time3([&] { return run_grouped_persist(F, opC, dtype, nrhs, xs, ys, ps.p, s, cw); }, &persist_best, tag,
+                cw, &pbest_tag, &pbest_cw);
       }
       if (!rc) rc = tc_status(true);   // a persistent wait that gave up (never expected)
       ps.release(s);
       lb.release(s);
     }
     const bool pw = persist_best < grouped_best;
-    const int bd = pw ? pbest_depth : best_depth, bc = pw ? pbest_cw : best_cw;
-    if (!rc && bd > 0) {
-      rc = build_grouped(F, opC, dtype, bd, s);
+    const int bt = pw ? pbest_tag : best_tag, bc = pw ? pbest_cw : best_cw;
+    if (!rc && bt > 0) {
+      rc = build_grouped(F, opC, dtype, bt / 8, s, bt % 8);
       gp.cw[cls] = (int16_t)bc;
-      gp.tuned_depth = bd;
+      gp.tuned_depth = bt / 8;
+      gp.tuned_merge = bt % 8;
     }
   }
   // the fastest engine serves this class from now on

@@ -313,6 +313,8 @@ struct GroupedTask {
   int64_t out_row;          // local row (out_reg > 0) or global row offset (out_reg == 0)
   int64_t ldo;              // global output: 0 row-major (N columns), > 0 column-major
   GroupedTerm t[2];
+  int32_t out_loc;          // column-major output: the first row in the group's output staging area
+  int32_t pad;
 };
 struct GroupedSpan {        // global input rows [g0, g0 + rows) -> region-0 rows [l0, l0 + rows)
   int64_t g0;
@@ -332,6 +334,13 @@ struct GroupedGroup {                   // the head of a group's image
   int32_t st_chunk[GR_MAXD + 1];        // row chunks of stage k: [st_chunk[k], st_chunk[k + 1]) of the image's chunks
   int32_t reg_row[GR_MAXD + 1];         // region r: local rows [reg_row[r], reg_row[r + 1])
   int32_t off_tasks, off_spans, off_chunks, off_fac;   // byte offsets of the image's parts
+  // column-major x and y (the first and the last run): region 0 held
+  // column by column with pitch in_pitch (odd), the last stage's outputs
+  // staged column by column at rows [out_row0, out_row0 + out_pitch) with
+  // pitch out_pitch (odd) and written out along columns from the image's
+  // output spans; 0: row-major
+  int32_t in_pitch, out_row0, out_pitch, off_ospans, nospans, ospan0;
+  int32_t out_ld;                       // y's leading dimension (column-major output)
 };
 // A group's image -- the head, its task descriptors, input spans and row
 // chunks, then its factor tiles, 16-byte aligned parts -- is what the CTA
@@ -360,6 +369,8 @@ struct GroupedPlan {
   std::array<int8_t, NRHS_CLASSES> ppick{{0, 0, 0, 0, 0, 0}};   // 1: ... in one persistent launch
   std::array<int8_t, NRHS_CLASSES> tuned{{0, 0, 0, 0, 0, 0}};   // 1: the tuner has measured this class
   int tuned_depth = 0;                  // the depth the tuner measured fastest (0: none)
+  int merge = 1;                        // the built plan's groups: at least this many last-stage blocks
+  int tuned_merge = 0;                  // the merge the tuner measured fastest (0: none)
   int64_t untuned_uses = 0;             // applies that found no tuned choice (the plan is built from the
                                         // GR_BUILD_AFTER-th on: it costs ~1.5 ms of host time at n = 16384)
 };
@@ -418,11 +429,14 @@ bool plan_fused(const Fact* F, int opC, int dtype, FusedPlan& fp);
 int fused_slice_width(const FusedPlan& fp, int64_t nrhs, int dtype);
 int run_fused(Fact* F, int opC, int dtype, int64_t nrhs, const void* x, int64_t ldx, void* y, int64_t ldy, int conj,
               void* exch, cudaStream_t s, int cs_override = 0);
-// Grouped apply: builds F->gp[opC][dtype] with runs of `depth` stages
-// (rebuilt when the depth changes; ok false: not applicable); run_grouped
-// computes y = op(F) x on tree-order x and y with two level buffers of
-// gp.level_rows_max * nrhs elements each.
-int build_grouped(Fact* F, int opC, int dtype, int depth, cudaStream_t s);
+// Grouped apply: builds F->gp[opC][dtype] with runs of `depth` stages,
+// independent groups merged until each holds `merge` blocks of its run's
+// last stage (0: the tuned choice, else GR_MERGE_MIN for complex64 and none
+// for complex128; rebuilt when either changes; ok false: not applicable);
+// run_grouped computes y = op(F) x on tree-order x and y with two level
+// buffers of gp.level_rows_max * nrhs elements each.
+constexpr int GR_MERGE_MIN = 4;
+int build_grouped(Fact* F, int opC, int dtype, int depth, cudaStream_t s, int merge = 0);
 int run_grouped(Fact* F, int opC, int dtype, int64_t nrhs, const void* xt, void* yt, void* ping, void* pong,
                 cudaStream_t s, int cw_override = 0);
 // The same runs in one cooperative launch: a (group, column slice) task

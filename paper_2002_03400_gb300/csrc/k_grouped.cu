@@ -69,42 +69,32 @@ __device__ __forceinline__ void gr_fma(V& acc, const V e, const V x) {
   else cmac(acc, e, x);
 }
 
-// Rows r0 .. r0 + NR - 1 of a staged term for the lane's column c (x: the
-// term's input rows, CW columns each; t: the tile, entry (i, k) at
-// t[k tld + i]): acc[r] += op(A)(r0 + r, k) x(k, c), k ascending -- the
+// Rows r0 .. r0 + NR - 1 of a staged complex128 term for the lane's column
+// c (x: the lane's input column, consecutive k xs elements apart; t: the
+// tile, entry (i, k) at t[k tld + i]): acc[r] += op(A)(r0 + r, k) x(k, c),
+// k ascending -- the
 // stage kernels' FMA chain (CJ: op(A) = conj(A)^T, the staged entries are
-// A's, the conjugate is taken in the multiply).  Complex64 tiles have an
-// even pitch and even r0, so row pairs are single 16-byte loads.
+// A's, the conjugate is taken in the multiply).
 template <typename V, int NR, bool CJ>
-__device__ __forceinline__ void gr_tile_s(const V* __restrict__ x, int CW, const V* __restrict__ t, int tld, int K,
+__device__ __forceinline__ void gr_tile_s(const V* __restrict__ x, int xs, const V* __restrict__ t, int tld, int K,
                                           V* acc) {
 #pragma unroll 2
   for (int kk = 0; kk < K; ++kk) {
     const V xv = *x;
-    if constexpr (sizeof(V) == 8) {
 #pragma unroll
-      for (int r = 0; r + 1 < NR; r += 2) {
-        const float4 e2 = *(const float4*)(t + r);
-        gr_fma<V, CJ>(acc[r], make_float2(e2.x, e2.y), xv);
-        gr_fma<V, CJ>(acc[r + 1], make_float2(e2.z, e2.w), xv);
-      }
-      if constexpr (NR & 1) gr_fma<V, CJ>(acc[NR - 1], t[NR - 1], xv);
-    } else {
-#pragma unroll
-      for (int r = 0; r < NR; ++r) gr_fma<V, CJ>(acc[r], t[r], xv);
-    }
-    x += CW;
+    for (int r = 0; r < NR; ++r) gr_fma<V, CJ>(acc[r], t[r], xv);
+    x += xs;
     t += tld;
   }
 }
 
 // the same for a term read in place (global memory, the factor's layout)
 template <typename V, int NR, bool CJ>
-__device__ __forceinline__ void gr_tile_g(const V* __restrict__ x, int CW, const V* __restrict__ mat, int ldm, int K,
+__device__ __forceinline__ void gr_tile_g(const V* __restrict__ x, int xs, const V* __restrict__ mat, int ldm, int K,
                                           int r0, V* acc) {
 #pragma unroll 2
   for (int kk = 0; kk < K; ++kk) {
-    const V xv = x[kk * CW];
+    const V xv = x[kk * xs];
     if constexpr (CJ) {
       const V* __restrict__ m = mat + (int64_t)r0 * ldm + kk;
 #pragma unroll
@@ -117,11 +107,112 @@ __device__ __forceinline__ void gr_tile_g(const V* __restrict__ x, int CW, const
   }
 }
 
+// Complex64 tiles are planar: column k of a tile holds the real parts of
+// its tq rows (tq = M rounded up to 4), then their imaginary parts.  A
+// lane's accumulators pair rows (2p, 2p + 1): ax[p] their real parts, ay[p]
+// their imaginary parts, so one packed FP32 FMA (__ffma2_rn) serves two rows.
+// Each component takes the products in the order of cmac / cmac_conj, so
+// every output is still the stage kernels' FMA chain.
+template <bool CJ>
+__device__ __forceinline__ void gr_pair(float2& ax, float2& ay, const float2 ex, const float2 ey, const float2 XX,
+                                        const float2 YY, const float2 NEG) {
+  // NEG: (-x.y, -x.y) for A, (-x.x, -x.x) for conj(A)
+  ax = __ffma2_rn(ex, XX, ax);
+  ax = __ffma2_rn(ey, CJ ? YY : NEG, ax);
+  ay = __ffma2_rn(ex, YY, ay);
+  ay = __ffma2_rn(ey, CJ ? NEG : XX, ay);
+}
+template <bool CJ>
+__device__ __forceinline__ void gr_one(float& ax, float& ay, const float ex, const float ey, const float2 xv) {
+  if constexpr (CJ) {
+    ax = fmaf(ex, xv.x, ax);
+    ax = fmaf(ey, xv.y, ax);
+    ay = fmaf(ex, xv.y, ay);
+    ay = fmaf(-ey, xv.x, ay);
+  } else {
+    ax = fmaf(ex, xv.x, ax);
+    ax = fmaf(-ey, xv.y, ax);
+    ay = fmaf(ex, xv.y, ay);
+    ay = fmaf(ey, xv.x, ay);
+  }
+}
+template <int NR, bool CJ>
+__device__ __forceinline__ void gr_tile_p(const float2* __restrict__ x, int xs, const float* __restrict__ t, int tq,
+                                          int K, float2* ax, float2* ay) {
+#pragma unroll 2
+  for (int kk = 0; kk < K; ++kk) {
+    const float2 xv = *x;
+    const float2 XX = make_float2(xv.x, xv.x), YY = make_float2(xv.y, xv.y);
+    const float2 NEG = CJ ? make_float2(-xv.x, -xv.x) : make_float2(-xv.y, -xv.y);
+#pragma unroll
+    for (int r = 0; r + 3 < NR; r += 4) {   // four rows: two 16-byte loads
+      const float4 ex = *(const float4*)(t + r), ey = *(const float4*)(t + tq + r);
+      gr_pair<CJ>(ax[r / 2], ay[r / 2], make_float2(ex.x, ex.y), make_float2(ey.x, ey.y), XX, YY, NEG);
+      gr_pair<CJ>(ax[r / 2 + 1], ay[r / 2 + 1], make_float2(ex.z, ex.w), make_float2(ey.z, ey.w), XX, YY, NEG);
+    }
+    if constexpr ((NR & 3) >= 2) {
+      constexpr int r = NR & ~3;
+      gr_pair<CJ>(ax[r / 2], ay[r / 2], *(const float2*)(t + r), *(const float2*)(t + tq + r), XX, YY, NEG);
+    }
+    if constexpr (NR & 1) gr_one<CJ>(ax[NR / 2].x, ay[NR / 2].x, t[NR - 1], t[tq + NR - 1], xv);
+    x += xs;
+    t += 2 * tq;
+  }
+}
+// the same for a term read in place (global memory, the factor's layout)
+template <int NR, bool CJ>
+__device__ __forceinline__ void gr_tile_gp(const float2* __restrict__ x, int xs, const float2* __restrict__ mat,
+                                           int ldm, int K, int r0, float2* ax, float2* ay) {
+#pragma unroll 2
+  for (int kk = 0; kk < K; ++kk) {
+    const float2 xv = x[kk * xs];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      const float2 e = CJ ? mat[(int64_t)(r0 + r) * ldm + kk] : mat[(int64_t)kk * ldm + r0 + r];
+      if (r & 1) gr_one<CJ>(ax[r / 2].y, ay[r / 2].y, e.x, e.y, xv);
+      else gr_one<CJ>(ax[r / 2].x, ay[r / 2].x, e.x, e.y, xv);
+    }
+  }
+}
+// one complex64 term for nr (<= GR_RB) rows into the paired accumulators
+__device__ __forceinline__ void gr_term_p(const GroupedTerm& Q, const float2* __restrict__ fsm,
+                                          const float2* __restrict__ x, int xs, int r0, int nr, float2* ax,
+                                          float2* ay) {
+  const bool cj = Q.conjT != 0;
+  if (Q.fac_off >= 0) {
+    const float* t = (const float*)fsm + 2 * (int64_t)Q.fac_off + r0;
+    switch (nr) {
+#define GR_CASE(n)                                                      \
+  case n:                                                               \
+    if (cj) gr_tile_p<n, true>(x, xs, t, Q.tld, Q.K, ax, ay);           \
+    else gr_tile_p<n, false>(x, xs, t, Q.tld, Q.K, ax, ay);             \
+    break;
+      GR_CASE(1) GR_CASE(2) GR_CASE(3) GR_CASE(4) GR_CASE(5) GR_CASE(6) GR_CASE(7) GR_CASE(8)
+      GR_CASE(9) GR_CASE(10) GR_CASE(11) GR_CASE(12) GR_CASE(13) GR_CASE(14) GR_CASE(15) GR_CASE(16)
+#undef GR_CASE
+      default: break;
+    }
+  } else {
+    const float2* mat = (const float2*)Q.mat;
+    switch (nr) {
+#define GR_CASE(n)                                                      \
+  case n:                                                               \
+    if (cj) gr_tile_gp<n, true>(x, xs, mat, Q.ldm, Q.K, r0, ax, ay);    \
+    else gr_tile_gp<n, false>(x, xs, mat, Q.ldm, Q.K, r0, ax, ay);      \
+    break;
+      GR_CASE(1) GR_CASE(2) GR_CASE(3) GR_CASE(4) GR_CASE(5) GR_CASE(6) GR_CASE(7) GR_CASE(8)
+      GR_CASE(9) GR_CASE(10) GR_CASE(11) GR_CASE(12) GR_CASE(13) GR_CASE(14) GR_CASE(15) GR_CASE(16)
+#undef GR_CASE
+      default: break;
+    }
+  }
+}
+
 // one term for nr (<= MR) rows, nr known at run time and uniform over the
 // warp: one fully unrolled body per count, no work on absent rows
 template <typename V, int MR>
 __device__ __forceinline__ void gr_term(const GroupedTerm& Q, const V* __restrict__ fsm, const V* __restrict__ x,
-                                        int CW, int r0, int nr, V* acc) {
+                                        int xs, int r0, int nr, V* acc) {
   const bool cj = Q.conjT != 0;
   if (Q.fac_off >= 0) {
     const V* t = fsm + Q.fac_off + r0;
@@ -129,8 +220,8 @@ __device__ __forceinline__ void gr_term(const GroupedTerm& Q, const V* __restric
 #define GR_CASE(n)                                                                           \
   case n:                                                                                    \
     if constexpr (n <= MR) {                                                                 \
-      if (cj) gr_tile_s<V, n, true>(x, CW, t, Q.tld, Q.K, acc);                             \
-      else gr_tile_s<V, n, false>(x, CW, t, Q.tld, Q.K, acc);                               \
+      if (cj) gr_tile_s<V, n, true>(x, xs, t, Q.tld, Q.K, acc);                             \
+      else gr_tile_s<V, n, false>(x, xs, t, Q.tld, Q.K, acc);                               \
     }                                                                                        \
     break;
       GR_CASE(1) GR_CASE(2) GR_CASE(3) GR_CASE(4) GR_CASE(5) GR_CASE(6) GR_CASE(7) GR_CASE(8)
@@ -144,8 +235,8 @@ __device__ __forceinline__ void gr_term(const GroupedTerm& Q, const V* __restric
 #define GR_CASE(n)                                                                           \
   case n:                                                                                    \
     if constexpr (n <= MR) {                                                                 \
-      if (cj) gr_tile_g<V, n, true>(x, CW, mat, Q.ldm, Q.K, r0, acc);                       \
-      else gr_tile_g<V, n, false>(x, CW, mat, Q.ldm, Q.K, r0, acc);                         \
+      if (cj) gr_tile_g<V, n, true>(x, xs, mat, Q.ldm, Q.K, r0, acc);                       \
+      else gr_tile_g<V, n, false>(x, xs, mat, Q.ldm, Q.K, r0, acc);                         \
     }                                                                                        \
     break;
       GR_CASE(1) GR_CASE(2) GR_CASE(3) GR_CASE(4) GR_CASE(5) GR_CASE(6) GR_CASE(7) GR_CASE(8)
@@ -255,9 +346,12 @@ __device__ __forceinline__ bool grouped_group(const GroupedArgs& a, int gi, int 
   };
   // row-major inputs: a row's cw columns to a group of lanes (16-byte
   // units where rows and slice allow), the span rows round robin over the
-  // CTA's row slots in local-row order
+  // CTA's row slots in local-row order; column-major x: column by column
+  // column-major x and y staged column by column from 32 columns per slice
+  // on (with fewer, a lane's column is read and written in place)
+  const bool cmi = G.in_pitch > 0 && cw >= 32, cmo = G.out_pitch > 0 && cw >= 32;
   constexpr int VPU = 16 / (int)sizeof(V);
-  const bool vec = N % VPU == 0 && CW % VPU == 0 && cw % VPU == 0;   // 16-byte copies bypass L1 (cg)
+  const bool vec = a.in_ld == 0 && N % VPU == 0 && CW % VPU == 0 && cw % VPU == 0;   // 16-byte copies (cg)
   const int upr = vec ? cw / VPU : cw;
   int lg = 0;
   while ((1 << lg) < upr && lg < 5) ++lg;
@@ -274,7 +368,14 @@ __device__ __forceinline__ bool grouped_group(const GroupedArgs& a, int gi, int 
           else in_copy(d + u, s + u);
         }
       }
-    } else {
+    } else if (cmi) {   // column-major x, held column by column: lanes along a column's rows
+      const int P0 = G.in_pitch;
+      for (int c = tid >> 5; c < cw; c += NT / 32) {
+        const V* s = x + S.g0 + (int64_t)(c0 + c) * a.in_ld;
+        V* d = rsm + (int64_t)c * P0 + S.l0;
+        for (int i = tid & 31; i < S.rows; i += 32) in_copy(d + i, s + i);
+      }
+    } else {   // column-major x into rows (few columns): consecutive threads along a column's rows
       for (int e = tid; e < S.rows * cw; e += NT) {
         const int c = e / S.rows, i = e - c * S.rows;
         in_copy(rsm + (int64_t)(S.l0 + i) * CW + c, x + (S.g0 + i) + (int64_t)(c0 + c) * a.in_ld);
@@ -312,29 +413,79 @@ __device__ __forceinline__ bool grouped_group(const GroupedArgs& a, int gi, int 
       if (c >= cw || rcount <= 0) continue;
       for (int h = 0; h < rcount; h += MR) {
         const int r0 = rbase + h, nr = min(MR, rcount - h);
-        V acc[MR];
+        if constexpr (sizeof(V) == 8) {   // complex64: planar tiles, paired rows
+          float2 ax[GR_RB / 2], ay[GR_RB / 2];
 #pragma unroll
-        for (int r = 0; r < MR; ++r) acc[r] = Cx<R>::make(0, 0);
-        for (int q = 0; q < T.nterms; ++q) {
-          const GroupedTerm& Q = T.t[q];
-          const V* xin = rsm + (int64_t)(G.reg_row[Q.in_reg] + Q.in_row) * CW + c;
-          gr_term<V, MR>(Q, fsm, xin, CW, r0, nr, acc);
-        }
-        if (T.out_reg > 0) {
-          V* o = rsm + (int64_t)(G.reg_row[T.out_reg] + T.out_row + r0) * CW + c;
+          for (int p = 0; p < GR_RB / 2; ++p) ax[p] = ay[p] = make_float2(0.f, 0.f);
+          for (int q = 0; q < T.nterms; ++q) {
+            const GroupedTerm& Q = T.t[q];
+            const bool cm = Q.in_reg == 0 && cmi;
+            const V* xin = cm ? rsm + (int64_t)c * G.in_pitch + Q.in_row
+                              : rsm + (int64_t)(G.reg_row[Q.in_reg] + Q.in_row) * CW + c;
+            gr_term_p(Q, fsm, xin, cm ? 1 : CW, r0, nr, ax, ay);
+          }
+          V* o;
+          int64_t rs;
+          if (T.out_reg > 0) {
+            o = rsm + (int64_t)(G.reg_row[T.out_reg] + T.out_row + r0) * CW + c;
+            rs = CW;
+          } else if (cmo) {   // staged column by column
+            o = rsm + (int64_t)G.out_row0 * CW + (int64_t)c * G.out_pitch + T.out_loc + r0;
+            rs = 1;
+          } else {
+            rs = T.ldo > 0 ? 1 : N;
+            const int64_t cs = T.ldo > 0 ? T.ldo : 1;
+            o = y + (T.ldo > 0 ? T.out_row : T.out_row * N) + (int64_t)r0 * rs + (int64_t)(c0 + c) * cs;
+          }
 #pragma unroll
-          for (int r = 0; r < MR; ++r)
-            if (r < nr) o[r * CW] = acc[r];
-        } else {
-          const int64_t rs = T.ldo > 0 ? 1 : N, cs = T.ldo > 0 ? T.ldo : 1;
-          V* o = y + (T.ldo > 0 ? T.out_row : T.out_row * N) + (int64_t)r0 * rs + (int64_t)(c0 + c) * cs;
+          for (int r = 0; r < GR_RB; ++r)
+            if (r < nr)
+              o[r * rs] = (r & 1) ? make_float2(ax[r / 2].y, ay[r / 2].y) : make_float2(ax[r / 2].x, ay[r / 2].x);
+        } else {   // complex128: interleaved tiles, a register tile of MR rows
+          V acc[MR];
 #pragma unroll
-          for (int r = 0; r < MR; ++r)
-            if (r < nr) o[r * rs] = acc[r];
+          for (int r = 0; r < MR; ++r) acc[r] = Cx<R>::make(0, 0);
+          for (int q = 0; q < T.nterms; ++q) {
+            const GroupedTerm& Q = T.t[q];
+            const bool cm = Q.in_reg == 0 && cmi;
+            const V* xin = cm ? rsm + (int64_t)c * G.in_pitch + Q.in_row
+                              : rsm + (int64_t)(G.reg_row[Q.in_reg] + Q.in_row) * CW + c;
+            gr_term<V, MR>(Q, fsm, xin, cm ? 1 : CW, r0, nr, acc);
+          }
+          if (T.out_reg > 0) {
+            V* o = rsm + (int64_t)(G.reg_row[T.out_reg] + T.out_row + r0) * CW + c;
+#pragma unroll
+            for (int r = 0; r < MR; ++r)
+              if (r < nr) o[r * CW] = acc[r];
+          } else if (cmo) {   // staged column by column
+            V* o = rsm + (int64_t)G.out_row0 * CW + (int64_t)c * G.out_pitch + T.out_loc + r0;
+#pragma unroll
+            for (int r = 0; r < MR; ++r)
+              if (r < nr) o[r] = acc[r];
+          } else {
+            const int64_t rs = T.ldo > 0 ? 1 : N, cs = T.ldo > 0 ? T.ldo : 1;
+            V* o = y + (T.ldo > 0 ? T.out_row : T.out_row * N) + (int64_t)r0 * rs + (int64_t)(c0 + c) * cs;
+#pragma unroll
+            for (int r = 0; r < MR; ++r)
+              if (r < nr) o[r * rs] = acc[r];
+          }
         }
       }
     }
     __syncthreads();   // this stage's blocks are complete
+  }
+  if (cmo && G.nospans > 0) {   // staged column-major outputs: lanes along a column's rows
+    const GroupedSpan* __restrict__ osp = (const GroupedSpan*)(gr_smem + G.off_ospans);
+    const int64_t ldo = G.out_ld;
+    const V* __restrict__ so = rsm + (int64_t)G.out_row0 * CW;
+    for (int sp = 0; sp < G.nospans; ++sp) {
+      const GroupedSpan S = osp[sp];
+      for (int c = tid >> 5; c < cw; c += NT / 32) {
+        V* d = y + S.g0 + (int64_t)(c0 + c) * ldo;
+        const V* s = so + (int64_t)c * G.out_pitch + S.l0;
+        for (int i = tid & 31; i < S.rows; i += 32) d[i] = s[i];
+      }
+    }
   }
   if constexpr (PERSIST) {
     if (tid == 0) {
@@ -390,7 +541,9 @@ __global__ void __launch_bounds__(256) grouped_persist_c128_256(const GroupedPer
 }
 
 // Packs each term's factor entries into its group's image (once per plan):
-// entry (i, k) of tile q at dst + (k tld + i) elements.
+// complex128 entry (i, k) of a tile at dst + (k tld + i) elements;
+// complex64 planar, its real part at float k 2 tld + i and its imaginary
+// part tld floats later.
 __global__ void grouped_pack_kernel(const GroupedSeg* __restrict__ segs, int nseg, uint8_t* __restrict__ img,
                                     int es) {
   for (int q = blockIdx.x; q < nseg; q += gridDim.x) {
@@ -408,9 +561,14 @@ __global__ void grouped_pack_kernel(const GroupedSeg* __restrict__ segs, int nse
         i = e - k * sg.M;
         so = i + (int64_t)k * sg.ldm;
       }
-      uint8_t* d = img + sg.dst + ((int64_t)k * sg.tld + i) * es;
-      if (es == 16) *(double2*)d = ((const double2*)sg.src)[so];
-      else *(float2*)d = ((const float2*)sg.src)[so];
+      if (es == 16) {
+        *(double2*)(img + sg.dst + ((int64_t)k * sg.tld + i) * 16) = ((const double2*)sg.src)[so];
+      } else {   // planar: real parts, then imaginary parts, per column
+        const float2 v = ((const float2*)sg.src)[so];
+        float* d = (float*)(img + sg.dst) + (int64_t)k * 2 * sg.tld + i;
+        d[0] = v.x;
+        d[sg.tld] = v.y;
+      }
     }
   }
 }
@@ -466,13 +624,18 @@ struct RunTables {
   std::vector<GroupedSpan> spans;
   std::vector<GroupedSeg> segs;
   std::vector<int32_t> chunks;
+  std::vector<GroupedSpan> ospans;   // column-major output: staging rows -> global rows
 };
 
 // Builds the groups of stages [s0, s0 + d) into T (cleared first; every
 // index is absolute: `base` holds the sizes of the tables already built);
 // false when a group does not fit (the caller retries with a shorter run).
-bool build_run(int dtype, const std::vector<StageTask>& all, const ApplyPlan& tmp, int s0, int d,
-               const RunTables& base, GroupedRun& run, RunTables& T) {
+// cm_in: the run reads x column-major (region 0 is then held column by
+// column); a last stage writing y column-major stages its outputs the same
+// way.
+bool build_run(int dtype, const std::vector<StageTask>& all, const ApplyPlan& tmp, int s0, int d, int merge_min,
+               bool cm_in, const RunTables& base, GroupedRun& run, RunTables& T) {
+  T.ospans.clear();
   T.groups.clear();
   T.tasks.clear();
   T.spans.clear();
@@ -514,6 +677,24 @@ bool build_run(int dtype, const std::vector<StageTask>& all, const ApplyPlan& tm
   for (int i = 0; i < nt; ++i) {
     const int r = dsu.find(i);
     gid[i] = r == i ? ng++ : gid[r];
+  }
+  // consecutive components merged until each group holds merge_min blocks
+  // of the run's last stage (independent components share a CTA: fewer,
+  // fuller CTAs where the components are single blocks or pairs)
+  if (merge_min > 1 && ng > 1) {
+    std::vector<int> last(ng, 0), nid(ng);
+    for (int i = first[d - 1]; i < nt; ++i) ++last[gid[i]];
+    int m = 0, acc = 0;
+    for (int g = 0; g < ng; ++g) {
+      nid[g] = m;
+      acc += last[g];
+      if (acc >= merge_min) {
+        ++m;
+        acc = 0;
+      }
+    }
+    ng = m + (acc > 0 ? 1 : 0);
+    for (int i = 0; i < nt; ++i) gid[i] = nid[gid[i]];
   }
   cnt.assign(ng + 1, 0);
   for (int i = 0; i < nt; ++i) ++cnt[gid[i] + 1];
@@ -559,9 +740,37 @@ bool build_run(int dtype, const std::vector<StageTask>& all, const ApplyPlan& tm
       }
       reg[k].build(v);
     }
+    // region 0 of a column-major input: one column after another with an
+    // odd pitch (lanes = columns read it without bank conflicts)
     G.reg_row[0] = 0;
-    for (int k = 0; k < d; ++k) G.reg_row[k + 1] = G.reg_row[k] + (int32_t)reg[k].rows();
+    for (int k = 0; k < d; ++k)
+      G.reg_row[k + 1] = G.reg_row[k] + (int32_t)reg[k].rows() + (k == 0 && cm_in && !(reg[0].rows() & 1) ? 1 : 0);
     for (int k = d + 1; k <= GR_MAXD; ++k) G.reg_row[k] = G.reg_row[d];
+    G.in_pitch = cm_in ? G.reg_row[1] : 0;
+    // column-major output: the last stage's blocks staged column by column
+    // (odd pitch), written out along columns
+    RowMap ro;
+    bool cm_out = false;
+    v.clear();
+    for (int m = sb[d - 1]; m < sb[d]; ++m) {
+      const StageTask& tk = task(mem[m]);
+      cm_out = cm_out || tk.ldo > 0;
+      v.push_back({tk.out_off, tk.out_off + tk.M});
+    }
+    G.ospan0 = (int32_t)(base.ospans.size() + T.ospans.size());
+    if (cm_out) {
+      const int64_t ldo = task(mem[sb[d - 1]]).ldo;
+      for (int m = sb[d - 1]; m < sb[d]; ++m)
+        if (task(mem[m]).ldo != ldo) return false;
+      if (ldo > INT32_MAX) return false;
+      G.out_ld = (int32_t)ldo;
+      ro.build(v);
+      G.out_row0 = G.reg_row[d];
+      G.out_pitch = (int32_t)(ro.rows() | 1);
+      for (size_t sp = 0; sp < ro.r.size(); ++sp)
+        T.ospans.push_back({ro.r[sp].first, ro.l0[sp], (int32_t)(ro.r[sp].second - ro.r[sp].first)});
+      G.nospans = (int32_t)ro.r.size();
+    }
     for (size_t sp = 0; sp < reg[0].r.size(); ++sp)
       T.spans.push_back({reg[0].r[sp].first, reg[0].l0[sp], (int32_t)(reg[0].r[sp].second - reg[0].r[sp].first)});
     G.nspans = (int32_t)reg[0].r.size();
@@ -586,8 +795,13 @@ bool build_run(int dtype, const std::vector<StageTask>& all, const ApplyPlan& tm
           gt.out_reg = 0;
           gt.out_row = tk.out_off;
           gt.ldo = tk.ldo;
+          gt.out_loc = cm_out && tk.M > 0 ? (int32_t)ro.at(tk.out_off) : 0;
+          if (gt.out_loc < 0) return false;
         }
-        const int tld = tk.M + (tk.M & 1);
+        // tile pitch: complex64 tiles are planar with M rounded up to 4
+        // (16-byte row quads), complex128 tiles interleaved with M rounded
+        // up to even
+        const int tld = es == 8 ? (tk.M + 3) & ~3 : tk.M + (tk.M & 1);
         for (int q = 0; q < tk.nterms; ++q) {
           const StageTerm& S = tk.t[q];
           GroupedTerm& Q = gt.t[q];
@@ -625,18 +839,20 @@ bool build_run(int dtype, const std::vector<StageTask>& all, const ApplyPlan& tm
     // the image: head, tasks, spans, chunks, tiles (16-byte aligned parts)
     const size_t o_tasks = gr_align16(sizeof(GroupedGroup));
     const size_t o_spans = o_tasks + gr_align16((size_t)G.ntasks * sizeof(GroupedTask));
-    const size_t o_chunks = o_spans + gr_align16((size_t)G.nspans * sizeof(GroupedSpan));
+    const size_t o_ospans = o_spans + gr_align16((size_t)G.nspans * sizeof(GroupedSpan));
+    const size_t o_chunks = o_ospans + gr_align16((size_t)G.nospans * sizeof(GroupedSpan));
     const size_t o_fac = o_chunks + gr_align16((size_t)G.st_chunk[d] * 4);
     const size_t bytes = gr_align16(o_fac + (size_t)fac * es);
     if (bytes > GR_SMEM_LIMIT) return false;
     G.off_tasks = (int32_t)o_tasks;
     G.off_spans = (int32_t)o_spans;
+    G.off_ospans = (int32_t)o_ospans;
     G.off_chunks = (int32_t)o_chunks;
     G.off_fac = (int32_t)o_fac;
     T.groups.push_back(G);
     run.img_stride = std::max<int64_t>(run.img_stride, (int64_t)bytes);
     run.desc_max = std::max(run.desc_max, (int32_t)o_fac);
-    run.rows_max = std::max(run.rows_max, G.reg_row[d]);
+    run.rows_max = std::max(run.rows_max, G.reg_row[d] + G.out_pitch);
   }
   // the smallest slice width (8 columns) must fit
   return grouped_smem(run, 8, es) <= GR_SMEM_LIMIT;
@@ -652,13 +868,14 @@ int set_grouped_depth(int depth) {
 }
 int grouped_depth() { return g_grouped_depth.load(); }
 
-int build_grouped(Fact* F, int opC, int dtype, int depth, cudaStream_t s) {
+int build_grouped(Fact* F, int opC, int dtype, int depth, cudaStream_t s, int merge) {
   GroupedPlan& gp = F->gp[opC][dtype];
-  if (gp.built && gp.depth == depth) return BF_OK;
+  if (merge <= 0) merge = gp.tuned_merge > 0 ? gp.tuned_merge : (dtype == BF_C64 ? GR_MERGE_MIN : 1);
+  if (gp.built && gp.depth == depth && gp.merge == merge) return BF_OK;
   if (depth < 1 || depth > GR_MAXD) return fail(BF_EINVAL, "grouped apply depth must be 1 .. 4");
   const auto pick = gp.pick, ppick = gp.ppick, tuned = gp.tuned;
   const auto cws = gp.cw;
-  const int tuned_depth = gp.tuned_depth;
+  const int tuned_depth = gp.tuned_depth, tuned_merge = gp.tuned_merge;
   const int64_t uses = gp.untuned_uses;
   gp.dev.release(s);
   gp = GroupedPlan();
@@ -669,6 +886,8 @@ int build_grouped(Fact* F, int opC, int dtype, int depth, cudaStream_t s) {
   gp.tuned = tuned;
   gp.cw = cws;
   gp.tuned_depth = tuned_depth;
+  gp.tuned_merge = tuned_merge;
+  gp.merge = merge;
   gp.untuned_uses = uses;
   ApplyPlan tmp;
   std::vector<StageTask> all;
@@ -707,13 +926,18 @@ int build_grouped(Fact* F, int opC, int dtype, int depth, cudaStream_t s) {
   for (int s0 = 0; s0 < nst;) {
     int d = std::min(depth, nst - s0);
     GroupedRun run{};
+    // groups merged up to `merge` last-stage blocks; unmerged when that does
+    // not fit, then shorter runs
     for (;; --d) {
-      if (build_run(dtype, all, tmp, s0, d, T, run, R)) {
+      const bool cm_in = s0 == 0 && in_ld0 > 0;
+      if (build_run(dtype, all, tmp, s0, d, merge, cm_in, T, run, R) ||
+          (merge > 1 && build_run(dtype, all, tmp, s0, d, 1, cm_in, T, run, R))) {
         T.groups.insert(T.groups.end(), R.groups.begin(), R.groups.end());
         T.tasks.insert(T.tasks.end(), R.tasks.begin(), R.tasks.end());
         T.spans.insert(T.spans.end(), R.spans.begin(), R.spans.end());
         T.segs.insert(T.segs.end(), R.segs.begin(), R.segs.end());
         T.chunks.insert(T.chunks.end(), R.chunks.begin(), R.chunks.end());
+        T.ospans.insert(T.ospans.end(), R.ospans.begin(), R.ospans.end());
         break;
       }
       if (d == 1) return BF_OK;   // a single stage does not fit: not applicable
@@ -822,6 +1046,7 @@ int build_grouped(Fact* F, int opC, int dtype, int depth, cudaStream_t s) {
       memcpy(d, &G, sizeof(GroupedGroup));
       if (G.ntasks) memcpy(d + G.off_tasks, &T.tasks[G.task0], (size_t)G.ntasks * sizeof(GroupedTask));
       if (G.nspans) memcpy(d + G.off_spans, &T.spans[G.span0], (size_t)G.nspans * sizeof(GroupedSpan));
+      if (G.nospans) memcpy(d + G.off_ospans, &T.ospans[G.ospan0], (size_t)G.nospans * sizeof(GroupedSpan));
       if (G.st_chunk[G.nst]) memcpy(d + G.off_chunks, &T.chunks[G.chunk0], (size_t)G.st_chunk[G.nst] * 4);
     }
     BF_CUDA_TRY(cudaMemcpy2DAsync(p + run.img_off, (size_t)run.img_stride, desc.data(), dm, dm,
