@@ -446,6 +446,15 @@ int bf_set_apply_engine(int engine);
  * running applies. */
 int bf_set_grouped_depth(int depth);
 
+/* Group merging of the grouped apply engine (diagnostic): 0 (default) the
+ * merging bf_apply_tune chose (untuned: complex64 groups merged until they
+ * hold 4 blocks of their run's last stage, complex128 groups unmerged);
+ * 1-16 groups merged until they hold that many (1: unmerged) in every
+ * grouped plan built later (a plan is rebuilt when its depth or merging
+ * changes).  Results do not depend on it.  BF_EINVAL otherwise.  Not
+ * thread-safe against running applies. */
+int bf_set_grouped_merge(int merge);
+
 /* Stage-kernel shape for every apply stage launch in this process
  * (diagnostic): v = -1 (default) uses the shapes bf_apply_tune chose, else
  * the untuned default; v = 0..7 forces that shape (0 many-warp, 1 rows,

@@ -88,6 +88,7 @@ def lib():
         "bf_set_apply_engine": (i32, [i32]),
         "bf_set_stage_variant": (i32, [i32]),
         "bf_set_grouped_depth": (i32, [i32]),
+        "bf_set_grouped_merge": (i32, [i32]),
         "bf_set_parallel_sides": (i32, [i32]),
         "bf_launch_count": (C.c_ulonglong, []),
         "bf_sync_count": (C.c_ulonglong, []),
@@ -115,7 +116,7 @@ def exported_symbols():
             "bf_apply_T", "bf_apply_noalloc", "bf_ranks", "bf_fact_info", "bf_fact_import", "bf_fact_export", "bf_fact_save", "bf_fact_load", "bf_error",
             "bf_free", "bf_gaussian", "bf_set_sketch_engine", "bf_set_entry_images", "bf_launch_count", "bf_apply_tune",
             "bf_applier_create", "bf_applier_run", "bf_fact_accept", "bf_debug_wait_timeout",
-            "bf_set_apply_engine", "bf_set_stage_variant", "bf_set_grouped_depth", "bf_set_parallel_sides", "bf_sync_count"]
+            "bf_set_apply_engine", "bf_set_stage_variant", "bf_set_grouped_depth", "bf_set_grouped_merge", "bf_set_parallel_sides", "bf_sync_count"]
 
 
 def launch_count() -> int:
@@ -178,6 +179,14 @@ def set_grouped_depth(depth: int):
     depth (untuned: set by the largest block rank), 1..4 that depth for every
     later grouped apply."""
     check(lib().bf_set_grouped_depth(int(depth)))
+
+
+def set_grouped_merge(merge: int):
+    """Group merging of the grouped apply engine: 0 (default) the tuned
+    choice (untuned: complex64 groups merged up to 4 last-stage blocks),
+    1..16 groups merged up to that many blocks (1: unmerged) in every grouped
+    plan built later; results do not depend on it."""
+    check(lib().bf_set_grouped_merge(int(merge)))
 
 
 def check(rc: int):

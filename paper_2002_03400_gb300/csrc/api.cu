@@ -872,6 +872,7 @@ int bf_set_entry_images(int on) { return set_entry_images(on); }
 int bf_set_apply_engine(int engine) { return set_apply_engine(engine); }
 int bf_set_stage_variant(int v) { return set_stage_variant(v); }
 int bf_set_grouped_depth(int depth) { return set_grouped_depth(depth); }
+int bf_set_grouped_merge(int merge) { return set_grouped_merge(merge); }
 int bf_set_parallel_sides(int on) { return set_parallel_sides(on); }
 
 unsigned long long bf_launch_count(void) { return bf::launches_so_far(); }

@@ -455,6 +455,11 @@ int grouped_wait_probe(uint64_t limit_ns, cudaStream_t s);
 // 0: the tuned depth (untuned: set by the largest block rank); 1 .. GR_MAXD:
 // that depth for every grouped apply
 int set_grouped_depth(int depth);
+// 0: the tuned group merging (untuned: GR_MERGE_MIN for complex64, none for
+// complex128); 1 .. 16: groups merged until they hold that many last-stage
+// blocks (1: unmerged) for every grouped plan built later
+int set_grouped_merge(int merge);
+int grouped_merge();
 // the engine of an apply's stages on tree-order buffers (0 stage launches,
 // 1 persistent, 2 grouped), built as needed
 int pick_inner_engine(Fact* F, int opC, int dtype, int64_t nrhs, bool overlap, cudaStream_t s, int* out);

@@ -868,8 +868,17 @@ int set_grouped_depth(int depth) {
 }
 int grouped_depth() { return g_grouped_depth.load(); }
 
+static std::atomic<int> g_grouped_merge{0};
+int set_grouped_merge(int merge) {
+  if (merge < 0 || merge > 16) return fail(BF_EINVAL, "grouped merge must be 0 .. 16");
+  g_grouped_merge.store(merge);
+  return BF_OK;
+}
+int grouped_merge() { return g_grouped_merge.load(); }
+
 int build_grouped(Fact* F, int opC, int dtype, int depth, cudaStream_t s, int merge) {
   GroupedPlan& gp = F->gp[opC][dtype];
+  if (merge <= 0) merge = grouped_merge();
   if (merge <= 0) merge = gp.tuned_merge > 0 ? gp.tuned_merge : (dtype == BF_C64 ? GR_MERGE_MIN : 1);
   if (gp.built && gp.depth == depth && gp.merge == merge) return BF_OK;
   if (depth < 1 || depth > GR_MAXD) return fail(BF_EINVAL, "grouped apply depth must be 1 .. 4");

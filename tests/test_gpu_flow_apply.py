@@ -28,6 +28,7 @@ def _reset_engine():
     yield
     api.set_apply_engine("auto")
     api.set_grouped_depth(0)
+    api.set_grouped_merge(0)
 
 
 _CACHE = {}
@@ -75,6 +76,37 @@ def test_engine_equals_stage_apply(engine, case, dtype):
         got = {"N": F.apply(x), "T": F.apply(xm, op="T"), "C": F.apply(xm, op="C")}
         for op in ("N", "T", "C"):
             assert torch.equal(got[op], ref[op]), (engine, case, nrhs, op)
+
+
+@pytest.mark.parametrize("merge", [1, 2, 4, 8])
+@pytest.mark.parametrize("depth", [1, 2, 3])
+@pytest.mark.parametrize("dtype", [torch.complex64, torch.complex128])
+def test_group_merging_keeps_results(merge, depth, dtype):
+    """Independent groups merged into one CTA (up to 1, 2, 4, 8 blocks of a
+    run's last stage) change which CTA computes a block, never its FMA
+    chain: grouped and persistent applies equal the stage launches bit for
+    bit on the ragged arc tree, 1 to 130 columns (slices of 32 columns and
+    more take the column-major staging of x and y)."""
+    plan, F = _factor("arc", dtype)
+    api.set_grouped_merge(merge)
+    api.set_grouped_depth(depth)
+    for nrhs in (1, 37, 64, 130):
+        x = api.colmajor(torch.from_numpy(inputs.random_rhs(plan.n, nrhs, seed=nrhs + 1)).to(dtype).cuda())
+        xm = api.colmajor(torch.from_numpy(inputs.random_rhs(plan.m, nrhs, seed=nrhs + 9)).to(dtype).cuda())
+        api.set_apply_engine("stages")
+        ref = {"N": F.apply(x), "C": F.apply(xm, op="C")}
+        for eng in ("grouped", "persistent"):
+            api.set_apply_engine(eng)
+            got = {"N": F.apply(x), "C": F.apply(xm, op="C")}
+            for op in ("N", "C"):
+                assert torch.equal(got[op], ref[op]), (eng, merge, depth, nrhs, op)
+
+
+def test_group_merging_knob_range():
+    with pytest.raises(api.BFError):
+        api.set_grouped_merge(-1)
+    with pytest.raises(api.BFError):
+        api.set_grouped_merge(17)
 
 
 @pytest.mark.parametrize("engine", ["persistent", "grouped-3"])
