@@ -16,6 +16,11 @@
 //   - computes the run's stages one after another, the inner stages' blocks
 //     in shared memory, and writes only the last stage's blocks to global
 //     memory (one of two level buffers, or y).
+// Column-major x and y (the first run's input, the last run's output) are
+// held column by column in shared memory from 32 columns per slice on, so
+// both move along a column's contiguous rows; complex64 products use packed
+// FP32 FMAs over pairs of rows; independent single-block groups are merged
+// (complex64) so that a CTA has several blocks to work on.
 // So an apply takes ceil((L + 3) / depth) launches, each reading its inputs
 // once and writing its outputs once.  Every output is the same FMA chain as
 // in the stage kernels (terms in order, k ascending): results equal the
@@ -72,9 +77,8 @@ __device__ __forceinline__ void gr_fma(V& acc, const V e, const V x) {
 // Rows r0 .. r0 + NR - 1 of a staged complex128 term for the lane's column
 // c (x: the lane's input column, consecutive k xs elements apart; t: the
 // tile, entry (i, k) at t[k tld + i]): acc[r] += op(A)(r0 + r, k) x(k, c),
-// k ascending -- the
-// stage kernels' FMA chain (CJ: op(A) = conj(A)^T, the staged entries are
-// A's, the conjugate is taken in the multiply).
+// k ascending -- the stage kernels' FMA chain (CJ: op(A) = conj(A)^T, the
+// staged entries are A's, the conjugate is taken in the multiply).
 template <typename V, int NR, bool CJ>
 __device__ __forceinline__ void gr_tile_s(const V* __restrict__ x, int xs, const V* __restrict__ t, int tld, int K,
                                           V* acc) {
