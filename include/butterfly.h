@@ -418,8 +418,9 @@ int bf_debug_wait_timeout(uint64_t limit_ns, void* stream);
  *   - grouped: the stages in runs of 1-4 consecutive stages, one launch
  *     per run; the blocks of a run fall into small connected groups (for
  *     the W levels and depth 3: 4 + 4 + 4 blocks reading 8 blocks of the
- *     level below; complex64 groups with fewer last-stage blocks merged up
- *     to 4), one CTA per (group, column slice) copies the group's image --
+ *     level below; complex64 groups of blocks of rank <= 16 with fewer
+ *     last-stage blocks merged up to 4), one CTA per (group, column slice)
+ *     copies the group's image --
  *     its descriptors and factor blocks, packed once per plan -- while it
  *     waits for the previous launch, then its input rows, and computes the
  *     run's inner stages in shared memory; ceil((L + 3) / depth) launches,
@@ -448,7 +449,8 @@ int bf_set_grouped_depth(int depth);
 
 /* Group merging of the grouped apply engine (diagnostic): 0 (default) the
  * merging bf_apply_tune chose (untuned: complex64 groups merged until they
- * hold 4 blocks of their run's last stage, complex128 groups unmerged);
+ * hold 4 blocks of their run's last stage when every rank is <= 16, else
+ * and for complex128 unmerged);
  * 1-16 groups merged until they hold that many (1: unmerged) in every
  * grouped plan built later (a plan is rebuilt when its depth or merging
  * changes).  Results do not depend on it.  BF_EINVAL otherwise.  Not

@@ -183,7 +183,8 @@ def set_grouped_depth(depth: int):
 
 def set_grouped_merge(merge: int):
     """Group merging of the grouped apply engine: 0 (default) the tuned
-    choice (untuned: complex64 groups merged up to 4 last-stage blocks),
+    choice (untuned: complex64 groups merged up to 4 last-stage blocks when
+    every rank is <= 16),
     1..16 groups merged up to that many blocks (1: unmerged) in every grouped
     plan built later; results do not depend on it."""
     check(lib().bf_set_grouped_merge(int(merge)))

@@ -554,8 +554,8 @@ int tune_apply(Fact* F, int op, int dtype, int64_t nrhs, cudaStream_t s, float* 
     }
     if (!rc && best_cs > 0) fp.cs[cls] = best_cs;
   }
-  // the grouped apply at each run depth, group merging (complex64: merged
-  // up to GR_MERGE_MIN last-stage blocks, or not) and slice width, as
+  // the grouped apply at each run depth (1-4), group merging (complex64:
+  // merged up to GR_MERGE_MIN last-stage blocks, or not) and slice width, as
   // launches per run (own level buffers) and as one persistent launch (own
   // scratch); the plan keeps the fastest depth and merging
   float grouped_best = 1e30f, persist_best = 1e30f;
@@ -577,8 +577,8 @@ int tune_apply(Fact* F, int op, int dtype, int64_t nrhs, cudaStream_t s, float* 
     char* xs = p + 2 * lvl * es;
     char* ys = xs + rows * nrhs * es;
     const int merges[2] = {dtype == BF_C64 ? GR_MERGE_MIN : 1, 1};
-    for (int v = 0; v < 2 * (GR_MAXD - 1) && !rc; ++v) {
-      const int depth = 2 + v / 2, merge = merges[v % 2];
+    for (int v = 0; v < 2 * GR_MAXD && !rc; ++v) {
+      const int depth = 1 + v / 2, merge = merges[v % 2];
       if (v % 2 == 1 && merge == merges[0]) continue;   // complex128: no merged variant
       rc = build_grouped(F, opC, dtype, depth, s, merge);
       if (rc) break;

@@ -431,8 +431,9 @@ int run_fused(Fact* F, int opC, int dtype, int64_t nrhs, const void* x, int64_t 
               void* exch, cudaStream_t s, int cs_override = 0);
 // Grouped apply: builds F->gp[opC][dtype] with runs of `depth` stages,
 // independent groups merged until each holds `merge` blocks of its run's
-// last stage (0: the tuned choice, else GR_MERGE_MIN for complex64 and none
-// for complex128; rebuilt when either changes; ok false: not applicable);
+// last stage (0: the forced or tuned choice, else GR_MERGE_MIN for
+// complex64 factorizations whose ranks are <= 16, none otherwise; rebuilt
+// when either changes; ok false: not applicable);
 // run_grouped computes y = op(F) x on tree-order x and y with two level
 // buffers of gp.level_rows_max * nrhs elements each.
 constexpr int GR_MERGE_MIN = 4;

@@ -883,7 +883,19 @@ int grouped_merge() { return g_grouped_merge.load(); }
 int build_grouped(Fact* F, int opC, int dtype, int depth, cudaStream_t s, int merge) {
   GroupedPlan& gp = F->gp[opC][dtype];
   if (merge <= 0) merge = grouped_merge();
-  if (merge <= 0) merge = gp.tuned_merge > 0 ? gp.tuned_merge : (dtype == BF_C64 ? GR_MERGE_MIN : 1);
+  if (merge <= 0 && gp.tuned_merge > 0) merge = gp.tuned_merge;
+  if (merge <= 0) {
+    // untuned: complex64 groups of small blocks (ranks <= 16) merged; large
+    // blocks fill a CTA alone (merged, their tiles outgrow shared memory
+    // and are read in place: 3-D caps with ranks ~53 at 64 columns took
+    // 0.83 ms merged against 0.20 ms unmerged)
+    int rmax = 0;
+    for (const auto& v : F->rV)
+      for (int r : v) rmax = std::max(rmax, r);
+    for (const auto& v : F->rU)
+      for (int r : v) rmax = std::max(rmax, r);
+    merge = dtype == BF_C64 && rmax <= 16 ? GR_MERGE_MIN : 1;
+  }
   if (gp.built && gp.depth == depth && gp.merge == merge) return BF_OK;
   if (depth < 1 || depth > GR_MAXD) return fail(BF_EINVAL, "grouped apply depth must be 1 .. 4");
   const auto pick = gp.pick, ppick = gp.ppick, tuned = gp.tuned;
